@@ -1,0 +1,161 @@
+"""FP64 CPU oracle for the HARP fill and MBF solve -- TEST INFRASTRUCTURE.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this package. The product path (the CUDA library and its binding)
+never imports it, and it never imports the product path.
+
+Thin ctypes wrapper over liboracle.so (harp_oracle.c); numpy arrays in and
+out. Matrices cross the boundary column-major (Fortran order).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        # ORACLE_LIB points the wrapper at another build of harp_oracle.c
+        # (the mutation tests load deliberately broken copies this way).
+        path = os.environ.get("ORACLE_LIB") or _build.build(quiet=True)
+        L = ct.CDLL(path)
+        dp, ip, vp = ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.c_void_p
+        L.oracle_fill.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, vp, ct.c_double, vp, vp,
+                                  ct.c_int, vp, ct.c_long, vp, ct.c_long]
+        L.oracle_fill.restype = ct.c_int
+        L.oracle_lu.argtypes = [ct.c_int, vp, ct.c_long, vp]
+        L.oracle_lu.restype = ct.c_int
+        L.oracle_lu_solve.argtypes = [ct.c_int, vp, ct.c_long, vp, ct.c_int, vp, ct.c_long, ct.c_char]
+        L.oracle_lu_solve.restype = None
+        L.oracle_port_objective.argtypes = [ct.c_int, ct.c_int, vp, ct.c_long, vp]
+        L.oracle_port_objective.restype = ct.c_double
+        L.oracle_grad_from_adjoint.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, vp, ct.c_double,
+                                               vp, ct.c_int, vp, vp, ct.c_long, ct.c_int, vp]
+        L.oracle_grad_from_adjoint.restype = None
+        L.oracle_port_objective_grad.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, vp,
+                                                 ct.c_double, vp, ct.c_int, vp, ct.c_long, vp, vp]
+        L.oracle_port_objective_grad.restype = ct.c_int
+        L.oracle_wavenumber.argtypes = [ct.c_double]
+        L.oracle_wavenumber.restype = ct.c_double
+        L.oracle_num_threads.restype = ct.c_int
+        L.oracle_set_threads.argtypes = [ct.c_int]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ct.c_void_p) if a is not None else None
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def wavenumber(freq_hz: float) -> float:
+    return float(lib().oracle_wavenumber(freq_hz))
+
+
+def _self_cm(self_blocks: np.ndarray) -> tuple[np.ndarray, int]:
+    """(Na, Nm, Nm) [a, T, S] -> column-major per antenna, stride Nm*Nm.
+    A single (Nm, Nm) block is shared by every antenna (stride 0)."""
+    if self_blocks.ndim == 2:
+        return np.ascontiguousarray(self_blocks.T, dtype=np.complex128), 0
+    sb = np.ascontiguousarray(self_blocks.transpose(0, 2, 1), dtype=np.complex128)
+    return sb, sb.shape[1] * sb.shape[2]
+
+
+def fill(pos, freq_hz, coef, self_blocks, ff=None, dvar: int = 1) -> np.ndarray:
+    """Reduced matrix Z (N x N complex128, Fortran order): Eq. 1, 3, 4."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.complex128)
+    Nm, _, np_, nq = coef.shape
+    P, Q = (np_ - 1) // 2, nq - 1
+    Na = pos.shape[0]
+    N = Na * Nm
+    sb, stride = _self_cm(self_blocks)
+    ffa = None if ff is None else np.ascontiguousarray(ff, dtype=np.complex128)
+    Z = np.zeros((N, N), dtype=np.complex128, order="F")
+    rc = lib().oracle_fill(Na, Nm, P, Q, _p(pos), float(freq_hz), _p(coef), _p(ffa), int(dvar),
+                           _p(sb), stride, _p(Z), N)
+    if rc != 0:
+        raise ValueError("oracle_fill: coincident antennas (r == 0)")
+    return Z
+
+
+def lu(Z: np.ndarray):
+    """(LU, ipiv, info): partial-pivot LU of a copy of Z."""
+    A = np.array(Z, dtype=np.complex128, order="F", copy=True)
+    N = A.shape[0]
+    ipiv = np.zeros(N, dtype=np.int32)
+    info = lib().oracle_lu(N, _p(A), N, _p(ipiv))
+    return A, ipiv, int(info)
+
+
+def lu_solve(LU, ipiv, B, trans: str = "N") -> np.ndarray:
+    X = np.array(B, dtype=np.complex128, order="F", copy=True)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    N = LU.shape[0]
+    lib().oracle_lu_solve(N, _p(LU), N, _p(ipiv), X.shape[1], _p(X), N, trans.encode())
+    return X
+
+
+def solve(Z, V, trans: str = "N") -> np.ndarray:
+    A, ipiv, info = lu(Z)
+    if info:
+        raise np.linalg.LinAlgError(f"oracle_lu: zero pivot at column {info - 1}")
+    return lu_solve(A, ipiv, V, trans)
+
+
+def port_objective(X, Na: int, Nm: int):
+    X = np.asarray(X, dtype=np.complex128, order="F")
+    Pm = np.zeros((Na, Na), dtype=np.complex128, order="F")
+    J = lib().oracle_port_objective(Na, Nm, _p(X), X.shape[0], _p(Pm))
+    return float(J), Pm
+
+
+def grad_from_adjoint(pos, freq_hz, coef, Lam, X, dvar: int = 1) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.complex128)
+    Nm, _, np_, nq = coef.shape
+    Lam = np.asarray(Lam, dtype=np.complex128, order="F")
+    X = np.asarray(X, dtype=np.complex128, order="F")
+    g = np.zeros((pos.shape[0], 2), dtype=np.float64)
+    lib().oracle_grad_from_adjoint(pos.shape[0], Nm, (np_ - 1) // 2, nq - 1, _p(pos), float(freq_hz),
+                                   _p(coef), int(dvar), _p(Lam), _p(X), X.shape[0], X.shape[1], _p(g))
+    return g
+
+
+def port_objective_grad(pos, freq_hz, coef, self_blocks, dvar: int = 1, want_grad: bool = True):
+    """(J, grad (Na, 2) or None) for J = sum |(E^T Z^{-1} E)_mn|^2."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.complex128)
+    Nm, _, np_, nq = coef.shape
+    sb, stride = _self_cm(self_blocks)
+    J = ct.c_double(0.0)
+    g = np.zeros((pos.shape[0], 2), dtype=np.float64) if want_grad else None
+    rc = lib().oracle_port_objective_grad(pos.shape[0], Nm, (np_ - 1) // 2, nq - 1, _p(pos),
+                                          float(freq_hz), _p(coef), int(dvar), _p(sb), stride,
+                                          ct.byref(J), _p(g))
+    if rc != 0:
+        raise ValueError(f"oracle_port_objective_grad failed: {rc}")
+    return J.value, g
+
+
+def relerr(a, b) -> float:
+    """Frobenius relative error ||a - b|| / ||b||."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))

@@ -1,0 +1,54 @@
+"""The oracle's pins must be strong enough to catch a plausible mistake.
+
+Each case copies harp_oracle.c, plants one mistake (a dropped sign, a wrong
+index, a transposed operand), compiles the copy on the CPU and runs the pin
+suite against it: the suite has to fail. The real oracle is never edited.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "harp_oracle.c")
+PINS = ["tests/test_oracle_fill.py", "tests/test_oracle_solve.py", "tests/test_oracle_grad.py"]
+
+MUTATIONS = {
+    "phase_sign": ("const cplx phase = cexp(-I * k * r); /* e^{-jkr}",
+                   "const cplx phase = cexp(I * k * r); /* e^{-jkr}"),
+    "harmonic_sign": ("for (int p = -P; p <= P; ++p) eh[p + P] = cexp(I * (double)p * alpha);",
+                      "for (int p = -P; p <= P; ++p) eh[p + P] = cexp(-I * (double)p * alpha);"),
+    "power_off_by_one": ("for (int q = 0; q <= Q; ++q) dq[q] = pow(d, (double)q);",
+                         "for (int q = 0; q <= Q; ++q) dq[q] = pow(d, (double)(q + 1));"),
+    "coef_T_S_transposed": ("const cplx* c = coef + ((size_t)T * Nm + S) * np * nq;\n      cplx B",
+                            "const cplx* c = coef + ((size_t)S * Nm + T) * np * nq;\n      cplx B"),
+    "alpha_reversed": ("      const double dx = pos[2 * m] - pos[2 * n];\n      const double dy = pos[2 * m + 1] - pos[2 * n + 1];\n      if (dx == 0.0",
+                       "      const double dx = pos[2 * n] - pos[2 * m];\n      const double dy = pos[2 * n + 1] - pos[2 * m + 1];\n      if (dx == 0.0"),
+    "far_field_power": ("gpat * phase / r;", "gpat * phase / (r * r);"),
+    "lu_update_sign": ("for (int i = k + 1; i < N; ++i) aj[i] -= l[i] * u;",
+                       "for (int i = k + 1; i < N; ++i) aj[i] += l[i] * u;"),
+    "pivot_not_largest": ("      if (v > best) {", "      if (best == 0.0 && v > best) {"),
+    "transpose_swap_order": ("/* x = P^T z: undo the swaps in reverse order. */\n      for (int k = N - 1; k >= 0; --k) {",
+                             "/* x = P^T z: undo the swaps in reverse order. */\n      for (int k = 0; k < N; ++k) {"),
+    "grad_alpha_sign": ("const cplx zx = a * (dx / r) + b * (-dy / (r * r));",
+                        "const cplx zx = a * (dx / r) + b * (dy / (r * r));"),
+    "grad_dr_power": ("(double)q * pow(d, (double)(q - 1)) * dd_dr", "(double)q * pow(d, (double)q) * dd_dr"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique/found"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", str(mutated), "-o", str(lib), "-lm"])
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"
