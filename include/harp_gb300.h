@@ -1,0 +1,174 @@
+/*
+ * harp_gb300.h -- C ABI of the GB300 (sm_103a) HARP fill and MBF solve.
+ *
+ * The library computes the data-parallel hot path of the Macro Basis
+ * Function (MBF) analysis of a large irregular array (Bui-Van et al.,
+ * "Fast and Accurate Simulation Technique for Large Irregular Arrays",
+ * Section II):
+ *
+ *   1. harp_fill: the reduced MBF impedance matrix Z, one Nm x Nm block per
+ *      ordered antenna pair, from the harmonic-polynomial (HARP) model
+ *        Z_TS = e^{-jkr} sum_{p=-P..P} e^{j p alpha} sum_{q=0..Q} c_pq^{TS} d^q,
+ *      d = 1/r (Eq. 3 with the improved change of variables of Section
+ *      II-B, inserted in Eq. 4). The far-field term of Eq. 1 with d = 1/r is
+ *      a q = 1 term and is passed folded into c_p1 by the caller.
+ *      Diagonal blocks are the caller's self blocks, copied.
+ *   2. mbf_solve: Z X = V for every port excitation (the O((Na Nm)^3) direct
+ *      solve of Section II-B), LU with partial pivoting.
+ *   3. harp_fill_adjoint: the gradient of a real objective with respect to
+ *      the antenna positions (array synthesis, Section V), from the adjoint
+ *      Lambda and the forward solution X, with the fill recomputed.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers are DEVICE pointers owned by the caller unless stated. The
+ *    library never frees caller memory.
+ *  - Complex numbers are interleaved (re, im). "c128" = two doubles, "c64" =
+ *    two floats.
+ *  - Matrices are column-major with a leading dimension in elements.
+ *  - Row i = m*Nm + T carries testing MBF T of antenna m; column
+ *    j = n*Nm + S carries source MBF S of antenna n. alpha is the direction
+ *    from source antenna n to testing antenna m, anticlockwise from +x.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream). Calls that must read a device result (mixed-precision
+ *    refinement, status checks) synchronise that stream before returning.
+ *  - Return value: HARP_OK (0) on success; -i when argument i (1-based) is
+ *    invalid (LAPACK convention); +i (1 <= i <= N) when the LU met an
+ *    exactly zero pivot in column i (X is not written); or one of the
+ *    HARP_E_* codes below. No C++ exception crosses this boundary.
+ */
+#ifndef HARP_GB300_H
+#define HARP_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct harp_ctx harp_ctx;
+
+/* Arithmetic of a call.
+ * HARP_FP64:          everything in FP64 (the plain double-precision path).
+ * HARP_MIXED_3XTF32:  FP32 storage, LU trailing updates and triangular
+ *                     solves on the tensor cores with a three-term TF32
+ *                     split (FP32-level accuracy), FP64-accurate residual
+ *                     and iterative refinement.
+ * HARP_MIXED_TF32:    as above with single-term TF32 products (faster,
+ *                     10-bit mantissa; refinement may not converge when
+ *                     cond(Z) * 2^-11 is not small).
+ * HARP_FP32:          FP32 fill (c64 only) and FP32-accurate solve
+ *                     (three-term TF32 tensor-core LU), no refinement. */
+typedef enum {
+  HARP_FP64 = 0,
+  HARP_MIXED_3XTF32 = 1,
+  HARP_MIXED_TF32 = 2,
+  HARP_FP32 = 3
+} harp_prec;
+
+#define HARP_OK 0
+#define HARP_E_COINCIDENT 0x40000001 /* two antennas at the same position (r == 0)          */
+#define HARP_E_NOCONV 0x40000002     /* refinement missed tol within max_iter               */
+#define HARP_E_TIMEOUT 0x40000003    /* a bounded device wait gave up                       */
+#define HARP_E_CUDA 0x40000004       /* a CUDA runtime error (see harp_last_cuda_error)     */
+#define HARP_E_NOMEM 0x40000005      /* device allocation failed in harp_ctx_create         */
+#define HARP_E_UNSUPPORTED 0x40000006 /* sizes beyond what this build supports              */
+#define HARP_E_STATE 0x40000007      /* call order violated (e.g. 'T' solve before 'N')     */
+#define HARP_E_NONFINITE 0x40000008  /* NaN or Inf met in the inputs or the factorisation   */
+
+/* Human-readable text for a status code (static storage). */
+const char* harp_status_string(int status);
+
+/* Last CUDA error code seen by the library in this process (0 if none). */
+int harp_last_cuda_error(void);
+
+/* Create a context on CUDA device `device` with workspace for systems up to
+ * max_N unknowns and max_nrhs right-hand sides. The context owns its device
+ * workspace (about 40 max_N^2 + 64 max_N max_nrhs bytes): the FP64 copy of
+ * the reduced matrix used by the refinement, the LU factors and pivots of
+ * the last factorisation, and solve buffers. Returns HARP_E_NOMEM when the
+ * allocation fails. One context serves one stream at a time. */
+int harp_ctx_create(harp_ctx** ctx, int device, int max_N, int max_nrhs);
+
+/* Release the context and its workspace (synchronises the device). */
+int harp_ctx_destroy(harp_ctx* ctx);
+
+/* Device pointer and leading dimension of the context's FP64 reduced
+ * matrix (c128, max_N x max_N). harp_fill writes it in the mixed modes; a
+ * caller may also write its own FP64 matrix there before a mixed solve. */
+int harp_ctx_z64(harp_ctx* ctx, void** z64, int* ld);
+
+/* Fill the reduced MBF matrix (Eq. 3 and 4 for every ordered pair m != n,
+ * self blocks on the diagonal).
+ *   ctx          context (workspace for the mixed modes)          [1]
+ *   Na, Nm       antennas, MBFs per antenna; N = Na*Nm <= max_N   [2, 3]
+ *   P, Q         harmonic order and polynomial degree (>= 0)      [4, 5]
+ *   pos          double [Na][2], metres                           [6]
+ *   freq_hz      frequency (> 0); k = 2 pi f / c0                 [7]
+ *   coef         c128 [Nm][Nm][2P+1][Q+1], index (T, S, p+P, q)   [8]
+ *   self_blocks  c128, element (T, S) of antenna a at
+ *                self_blocks[a*self_stride + T + S*Nm]            [9]
+ *   self_stride  complex elements between antennas; 0 = one block
+ *                shared by all antennas                           [10]
+ *   Z            output, N x N column-major: c128 for HARP_FP64, c64 for
+ *                the mixed modes (then the context's FP64 matrix is
+ *                written too)                                      [11]
+ *   ldz          leading dimension of Z (>= N)                    [12]
+ *   prec         harp_prec                                        [13]
+ * Coincident antennas (r == 0) are detected on the device: the entries of
+ * that pair are written as zero and HARP_E_COINCIDENT is returned (the call
+ * synchronises the stream to read the flag). */
+int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
+              const double* coef, const double* self_blocks, long self_stride, void* Z, int ldz,
+              int prec, void* stream);
+
+/* Solve Z X = V (trans 'N') or Z^T X = V (trans 'T', plain transpose).
+ *   N            system size (<= max_N)                          [2]
+ *   Z, ldz       the matrix for trans 'N': c128 (HARP_FP64) or c64 (mixed)
+ *                N x N; it is copied, factorised (PZ = LU) and the factors
+ *                are kept in the context. For trans 'T' Z is ignored (may
+ *                be NULL) and the cached factors of the last 'N' call of
+ *                the same N and prec are reused.                  [3, 4]
+ *   V, ldv       c128 N x nrhs right-hand sides; NULL = the port
+ *                excitations E (unit entry at row m*Nm of column m, with
+ *                Nm = N / nrhs)                                    [5, 6]
+ *   nrhs         right-hand sides (<= max_nrhs)                   [7]
+ *   X, ldx       c128 N x nrhs output                             [8, 9]
+ *   trans        'N' or 'T'                                       [10]
+ *   prec         harp_prec                                        [11]
+ *   tol          mixed modes: stop when ||V - Z64 X||_inf <=
+ *                tol (||Z64||_inf ||X||_inf + ||V||_inf); <= 0 selects
+ *                sqrt(N) * 2^-53                                   [12]
+ *   max_iter     mixed modes: at most this many refinement steps  [13]
+ *   iters_out    host int, refinement steps taken (may be NULL)   [14]
+ *   resid_out    host double, final normwise backward error of the mixed
+ *                modes (may be NULL; not computed for HARP_FP64)  [15]
+ * The mixed modes refine against the context's FP64 matrix (written by the
+ * last mixed harp_fill, or by the caller through harp_ctx_z64) and
+ * synchronise the stream once per step. Returns +i on an exactly zero pivot
+ * in column i, HARP_E_NOCONV when tol was not met (X then holds the best
+ * iterate). */
+int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int ldv, int nrhs,
+              double* X, int ldx, char trans, int prec, double tol, int max_iter, int* iters_out,
+              double* resid_out, void* stream);
+
+/* Position gradient of a real objective J(X) of the solution of Z X = V:
+ *   grad[m] = -2 Re sum over pairs (m, n) and (n, m) of
+ *             sum_TS G_TS dZ_TS/dx_m,       G = Lambda X^T,
+ * where Lambda solves Z^T Lambda = (dJ/dX)^* (for the port objective
+ * J = sum |E^T X|^2, Lambda = Z^{-T} E conj(E^T X)). The derivative of each
+ * block (Eq. 3, 4 differentiated in r and alpha) is recomputed, not stored.
+ *   Na, Nm, P, Q, pos, freq_hz, coef  as in harp_fill         [2..8]
+ *   Lambda, X    c128 N x nrhs, same leading dimension ld     [9, 10, 11]
+ *   nrhs                                                       [12]
+ *   grad_pos     double [Na][2], overwritten                   [13]
+ *   prec         HARP_FP64, or a mixed mode (FP32 contraction with
+ *                FP64 accumulation of the per-pair sums)       [14] */
+int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
+                      double freq_hz, const double* coef, const double* Lambda, const double* X,
+                      int ld, int nrhs, double* grad_pos, int prec, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HARP_GB300_H */

@@ -1,0 +1,283 @@
+// adjoint.cu -- harp_fill_adjoint: position gradient of a real objective of the
+// solution X of Z X = V, with the fill recomputed rather than stored.
+//
+// With G = Lambda X^T (Lambda the adjoint solution), dJ = -2 Re sum_ij G_ij dZ_ij.
+// Block (m, n) of Z depends only on Delta = x_m - x_n through r and alpha
+// (Eq. 3, 4), so per ordered pair
+//   H_k   = sum_TS G^{mn}_TS c_k^{TS}                 (k = (p, q))
+//   dZ/dr contraction     = sum_k H_k phi_k (-j kw - q d)
+//   dZ/dalpha contraction = sum_k H_k phi_k (j p)
+// with phi_k = e^{-j kw r} e^{j p alpha} d^q, d = 1/r (d d^q/dr = -q d^{q+1}),
+// and g = -2 Re(dr_sum Delta/r + dalpha_sum (-Delta_y, Delta_x)/r^2);
+// grad[m] += g, grad[n] -= g. Per-pair results go to a buffer and are
+// summed in a fixed order, so the gradient is deterministic.
+//
+// Work item = (source antenna n, tile of BA testing antennas). Per item the
+// CTA forms G for the tile (contraction over the right-hand sides, X rows of
+// antenna n staged in shared memory in chunks), then H (contraction over
+// (T, S) with the coefficient table), then the per-pair derivative sums.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace harp {
+
+constexpr double kC0a = 299792458.0;
+constexpr double kPia = 3.14159265358979323846;
+constexpr int kAdjThreads = 256;
+constexpr int kRChunk = 16;
+
+struct AdjArgs {
+  int Na, Nm, P, Q, K, nq, nrhs;
+  const double* pos;
+  double k;
+  const double2* coef;
+  const double2* Lam;
+  const double2* X;
+  long ld;
+  double* gpair;  // [m][n][2]
+  int BA, n_mtiles, n_items;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
+  using C = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Nm = a.Nm, Nm2 = Nm * Nm, K = a.K, BA = a.BA;
+  C* Gs = reinterpret_cast<C*>(smem_raw);  // [BA][Nm2], entry T + Nm*S
+  C* Hs = Gs + (size_t)BA * Nm2;           // [BA][K]
+  C* Xs = Hs + (size_t)BA * K;             // [kRChunk][Nm]
+  double* geo = reinterpret_cast<double*>(Xs + (size_t)kRChunk * Nm);  // [BA][4]
+
+  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int n = item / a.n_mtiles;
+    const int m0 = (item - n * a.n_mtiles) * BA;
+    const int nG = BA * Nm2;
+    // G tile = Lambda rows of the tile times X rows of antenna n (transposed)
+    // Each thread owns outputs e = tid + j*blockDim (T fastest).
+    constexpr int kMaxOut = 24;
+    C acc[kMaxOut];
+    const int nmine = (nG - (int)threadIdx.x + kAdjThreads - 1) / kAdjThreads;
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j) acc[j] = mk<R>(0, 0);
+    for (int r0 = 0; r0 < a.nrhs; r0 += kRChunk) {
+      const int rc = min(kRChunk, a.nrhs - r0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rc * Nm; e += blockDim.x) {
+        const int rr = e / Nm, S = e - rr * Nm;
+        const double2 v = a.X[(size_t)n * Nm + S + (size_t)(r0 + rr) * a.ld];
+        Xs[rr * Nm + S] = mk<R>((R)v.x, (R)v.y);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kMaxOut; ++j) {
+        if (j >= nmine) break;
+        const int e = threadIdx.x + j * kAdjThreads;
+        const int T = e % Nm, rest = e / Nm;
+        const int S = rest % Nm, mi = rest / Nm;
+        const int m = m0 + mi;
+        if (m >= a.Na) continue;
+        const double2* lrow = a.Lam + (size_t)m * Nm + T;
+        C s = acc[j];
+        for (int rr = 0; rr < rc; ++rr) {
+          const double2 l = lrow[(size_t)(r0 + rr) * a.ld];
+          cfma(s, mk<R>((R)l.x, (R)l.y), Xs[rr * Nm + S]);
+        }
+        acc[j] = s;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j) {
+      if (j >= nmine) break;
+      const int e = threadIdx.x + j * kAdjThreads;
+      const int T = e % Nm, rest = e / Nm;
+      const int S = rest % Nm, mi = rest / Nm;
+      Gs[(size_t)mi * Nm2 + T + Nm * S] = acc[j];
+    }
+    // geometry of the tile's pairs
+    for (int mi = threadIdx.x; mi < BA; mi += blockDim.x) {
+      const int m = m0 + mi;
+      double dx = 0, dy = 0, r = 1;
+      if (m < a.Na && m != n) {
+        dx = a.pos[2 * m] - a.pos[2 * n];
+        dy = a.pos[2 * m + 1] - a.pos[2 * n + 1];
+        r = hypot(dx, dy);
+      }
+      geo[4 * mi + 0] = dx;
+      geo[4 * mi + 1] = dy;
+      geo[4 * mi + 2] = r;
+    }
+    __syncthreads();
+    // H[mi][k] = sum_TS G[mi][TS] c_k^{TS}
+    for (int e = threadIdx.x; e < BA * K; e += blockDim.x) {
+      const int mi = e / K, kk = e - mi * K;
+      C h = mk<R>(0, 0);
+      const C* g = Gs + (size_t)mi * Nm2;
+      for (int S = 0; S < Nm; ++S)
+        for (int T = 0; T < Nm; ++T) {
+          const double2 c = a.coef[((size_t)T * Nm + S) * K + kk];
+          cfma(h, g[T + Nm * S], mk<R>((R)c.x, (R)c.y));
+        }
+      Hs[(size_t)mi * K + kk] = h;
+    }
+    __syncthreads();
+    // per-pair derivative sums (FP64), one thread per pair
+    for (int mi = threadIdx.x; mi < BA; mi += blockDim.x) {
+      const int m = m0 + mi;
+      if (m >= a.Na || m == n) continue;
+      const double dx = geo[4 * mi], dy = geo[4 * mi + 1], r = geo[4 * mi + 2];
+      double gx = 0.0, gy = 0.0;
+      if (r > 0.0) {
+        const double d = 1.0 / r;
+        double s, c;
+        sincos(a.k * r, &s, &c);
+        const double2 ph = make_double2(c, -s);
+        const double2 z = make_double2(dx * d, dy * d);
+        double2 zp = make_double2(1.0, 0.0);
+        double2 sum_r = make_double2(0, 0), sum_a = make_double2(0, 0);
+        const C* h = Hs + (size_t)mi * K;
+        for (int p = 0; p <= a.P; ++p) {
+          const double2 bp = cmul(ph, zp), bn = cmul(ph, cconj(zp));
+          double dq = 1.0;
+          for (int q = 0; q <= a.Q; ++q) {
+            // weight for dZ/dr: (-j kw - q d); for dZ/dalpha: (j p)
+            const double2 wr = make_double2(-(double)q * d, -a.k);
+            {
+              const C hv = h[(a.P + p) * a.nq + q];
+              const double2 hp = make_double2((double)hv.x * dq, (double)hv.y * dq);
+              const double2 t = cmul(hp, bp);
+              const double2 tr = cmul(t, wr);
+              sum_r.x += tr.x;
+              sum_r.y += tr.y;
+              sum_a.x += -(double)p * t.y;  // t * (j p)
+              sum_a.y += (double)p * t.x;
+            }
+            if (p > 0) {
+              const C hv = h[(a.P - p) * a.nq + q];
+              const double2 hp = make_double2((double)hv.x * dq, (double)hv.y * dq);
+              const double2 t = cmul(hp, bn);
+              const double2 tr = cmul(t, wr);
+              sum_r.x += tr.x;
+              sum_r.y += tr.y;
+              sum_a.x += (double)p * t.y;  // t * (-j p)
+              sum_a.y += -(double)p * t.x;
+            }
+            dq *= d;
+          }
+          zp = cmul(zp, z);
+        }
+        // dZ/dDx = dZ/dr dx/r + dZ/dalpha (-dy/r^2); dZ/dDy = dZ/dr dy/r + dZ/dalpha dx/r^2
+        gx = -2.0 * (sum_r.x * (dx * d) + sum_a.x * (-dy * d * d));
+        gy = -2.0 * (sum_r.x * (dy * d) + sum_a.x * (dx * d * d));
+      }
+      double* out = a.gpair + 2 * ((size_t)m * a.Na + n);
+      out[0] = gx;
+      out[1] = gy;
+    }
+  }
+}
+
+// grad[m] = sum_n g(m, n) - sum_n g(n, m), fixed order.
+__global__ void adjoint_reduce_kernel(int Na, const double* gpair, double* grad) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= Na) return;
+  double gx = 0.0, gy = 0.0;
+  for (int n = 0; n < Na; ++n) {
+    if (n == m) continue;
+    const double* a = gpair + 2 * ((size_t)m * Na + n);
+    const double* b = gpair + 2 * ((size_t)n * Na + m);
+    gx += a[0] - b[0];
+    gy += a[1] - b[1];
+  }
+  grad[2 * m] = gx;
+  grad[2 * m + 1] = gy;
+}
+
+template <typename R>
+static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st) {
+  using C = cplx_t<R>;
+  const int Nm2 = a.Nm * a.Nm;
+  int BA = 32;
+  size_t smem = 0;
+  for (; BA >= 1; BA /= 2) {
+    smem = ((size_t)BA * Nm2 + (size_t)BA * a.K + (size_t)kRChunk * a.Nm) * sizeof(C) +
+           (size_t)BA * 4 * sizeof(double);
+    if (smem <= std::min<size_t>(ctx->smem_optin, 200 * 1024) && BA * Nm2 <= 24 * kAdjThreads) break;
+  }
+  if (BA < 1) return HARP_E_UNSUPPORTED;
+  a.BA = BA;
+  a.n_mtiles = (a.Na + BA - 1) / BA;
+  a.n_items = a.Na * a.n_mtiles;
+  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R>, kAdjThreads,
+                                                smem);
+  const int grid = std::min(a.n_items, ctx->num_sms * std::max(1, per_sm));
+  adjoint_pairs_kernel<R><<<grid, kAdjThreads, smem, st>>>(a);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+}  // namespace harp
+
+using namespace harp;
+
+extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
+                                 double freq_hz, const double* coef, const double* Lambda,
+                                 const double* X, int ld, int nrhs, double* grad_pos, int prec,
+                                 void* stream) {
+  if (!ctx) return -1;
+  if (Na < 1) return -2;
+  if (Nm < 1) return -3;
+  if (P < 0 || P > 64) return -4;
+  if (Q < 0 || Q > 64) return -5;
+  if (!pos) return -6;
+  if (!(freq_hz > 0.0) || freq_hz > 1e15) return -7;
+  if (!coef) return -8;
+  if (!Lambda) return -9;
+  if (!X) return -10;
+  if (ld < (long)Na * Nm) return -11;
+  if (nrhs < 1) return -12;
+  if (!grad_pos) return -13;
+  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32 && prec != HARP_FP32)
+    return -14;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = (size_t)Na * Na * 2 * sizeof(double);
+  if (ctx->gpair_bytes < need) {
+    if (ctx->gpair) cudaFree(ctx->gpair);
+    ctx->gpair = nullptr;
+    ctx->gpair_bytes = 0;
+    if (cudaMalloc((void**)&ctx->gpair, need) != cudaSuccess) {
+      cudaGetLastError();
+      return HARP_E_NOMEM;
+    }
+    ctx->gpair_bytes = need;
+  }
+  AdjArgs a;
+  a.Na = Na;
+  a.Nm = Nm;
+  a.P = P;
+  a.Q = Q;
+  a.nq = Q + 1;
+  a.K = (2 * P + 1) * (Q + 1);
+  a.nrhs = nrhs;
+  a.pos = pos;
+  a.k = 2.0 * kPia * freq_hz / kC0a;
+  a.coef = reinterpret_cast<const double2*>(coef);
+  a.Lam = reinterpret_cast<const double2*>(Lambda);
+  a.X = reinterpret_cast<const double2*>(X);
+  a.ld = ld;
+  a.gpair = ctx->gpair;
+  HARP_CUDA(cudaMemsetAsync(ctx->gpair, 0, need, st));
+  if (prec == HARP_FP64)
+    HARP_TRY(launch_adjoint<double>(ctx, a, st));
+  else
+    HARP_TRY(launch_adjoint<float>(ctx, a, st));
+  adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, ctx->gpair, grad_pos);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}

@@ -1,0 +1,149 @@
+// common.cuh -- shared definitions of the GB300 HARP/MBF library.
+//
+// Complex helpers, status plumbing and the context structure. Everything
+// here is internal to the shared library; the public surface is
+// include/harp_gb300.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/harp_gb300.h"
+
+namespace harp {
+
+// ---------------------------------------------------------------------------
+// Complex types: interleaved storage (float2 / double2) at the ABI, split
+// real/imaginary planes inside the dense kernels.
+template <typename R> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename R> using cplx_t = typename cplx_of<R>::type;
+
+template <typename R> __host__ __device__ __forceinline__ cplx_t<R> mk(R re, R im) {
+  cplx_t<R> z;
+  z.x = re;
+  z.y = im;
+  return z;
+}
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C z;
+  z.x = a.x * b.x - a.y * b.y;
+  z.y = a.x * b.y + a.y * b.x;
+  return z;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) {
+  a.y = -a.y;
+  return a;
+}
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// A complex matrix view with arbitrary element strides: element (i, j) has
+// its real part at re[i*rs + j*cs] and its imaginary part at im[i*rs + j*cs].
+// Split planes use rs = 1, cs = ld; interleaved storage uses re = base,
+// im = base + 1, rs = 2, cs = 2*ld. A transposed view swaps rs and cs.
+template <typename R> struct CView {
+  R* re;
+  R* im;
+  long rs, cs;
+  __host__ __device__ R& r(long i, long j) const { return re[i * rs + j * cs]; }
+  __host__ __device__ R& m(long i, long j) const { return im[i * rs + j * cs]; }
+  __host__ __device__ CView sub(long i, long j) const {
+    return CView{re + i * rs + j * cs, im + i * rs + j * cs, rs, cs};
+  }
+  __host__ __device__ CView t() const { return CView{re, im, cs, rs}; }
+};
+template <typename R> inline CView<R> planes(R* re, R* im, long ld) { return CView<R>{re, im, 1, ld}; }
+template <typename R> inline CView<R> interleaved(R* base, long ld) {
+  return CView<R>{base, base + 1, 2, 2 * ld};
+}
+
+// ---------------------------------------------------------------------------
+// Status plumbing.
+extern int g_last_cuda_error;
+
+inline int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HARP_OK;
+  g_last_cuda_error = (int)e;
+  return HARP_E_CUDA;
+}
+#define HARP_CUDA(...)                             \
+  do {                                             \
+    int _s = ::harp::cuda_status((__VA_ARGS__));   \
+    if (_s != HARP_OK) return _s;                  \
+  } while (0)
+#define HARP_LAUNCHED() HARP_CUDA(cudaGetLastError())
+#define HARP_TRY(...)                              \
+  do {                                             \
+    int _s = (__VA_ARGS__);                        \
+    if (_s != HARP_OK) return _s;                  \
+  } while (0)
+
+// Device status word bits (ctx->dstatus[0]); dstatus[1] holds the smallest
+// 1-based column with an exactly zero pivot (INT32_MAX when none).
+enum : int { ST_COINCIDENT = 1, ST_NONFINITE = 2 };
+
+// Switch to the context's device for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace harp
+
+// ---------------------------------------------------------------------------
+// The context: device workspace sized at creation.
+struct harp_ctx {
+  int device;
+  int max_N, max_nrhs;
+  int num_sms;
+  size_t smem_optin;  // max dynamic shared memory per block (bytes)
+
+  // FP64 reduced matrix for the refinement residual (c128, ld = max_N).
+  double2* z64;
+  int ld64;
+
+  // LU factors in split planes (room for doubles), pivots, state.
+  void* lu_re;
+  void* lu_im;
+  int ld_lu;
+  int* ipiv;
+  int* perm;  // net row permutation of the cached factorisation
+  int lu_N;
+  int lu_prec;  // -1 = none
+  int lu_valid;
+
+  // Solve buffers (room for doubles), N x nrhs planes, ld = max_N.
+  void* w_re;
+  void* w_im;
+  double* x_re;
+  double* x_im;
+  double* r_re;
+  double* r_im;
+  double* v_re;
+  double* v_im;
+  void* t_re;  // scratch for the row permutation of the triangular solves
+  void* t_im;
+
+  // Adjoint per-pair partial gradients, Na x Na x 2 doubles (lazily sized).
+  double* gpair;
+  size_t gpair_bytes;
+
+  // Reductions and status.
+  double* red;      // device scratch, 16 doubles
+  double* red_host; // pinned host mirror, 16 doubles
+  int* dstatus;     // device status words [0] bits, [1] zero-pivot column
+  int* hstatus;     // pinned host mirror
+};

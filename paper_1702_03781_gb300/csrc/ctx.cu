@@ -1,0 +1,129 @@
+// ctx.cu -- context creation, workspace ownership, status strings.
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace harp {
+int g_last_cuda_error = 0;
+}
+
+using namespace harp;
+
+extern "C" const char* harp_status_string(int s) {
+  if (s == HARP_OK) return "ok";
+  if (s < 0) return "invalid argument";
+  switch (s) {
+    case HARP_E_COINCIDENT: return "coincident antennas (r == 0)";
+    case HARP_E_NOCONV: return "iterative refinement did not reach tol";
+    case HARP_E_TIMEOUT: return "bounded device wait gave up";
+    case HARP_E_CUDA: return "CUDA runtime error";
+    case HARP_E_NOMEM: return "device allocation failed";
+    case HARP_E_UNSUPPORTED: return "size not supported by this build";
+    case HARP_E_STATE: return "call order violated (no cached factorisation)";
+    case HARP_E_NONFINITE: return "non-finite value in inputs or factors";
+    default: return "exactly zero pivot (singular matrix)";
+  }
+}
+
+extern "C" int harp_last_cuda_error(void) { return g_last_cuda_error; }
+
+static void free_all(harp_ctx* c) {
+  void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->gpair, c->red, c->dstatus};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->hstatus) cudaFreeHost(c->hstatus);
+}
+
+extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nrhs) {
+  if (!out) return -1;
+  *out = nullptr;
+  int ndev = 0;
+  HARP_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return -2;
+  if (max_N < 1 || max_N > (1 << 17)) return -3;
+  if (max_nrhs < 1 || max_nrhs > (1 << 20)) return -4;
+  DeviceGuard g(device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+
+  harp_ctx* c = (harp_ctx*)calloc(1, sizeof(harp_ctx));
+  if (!c) return HARP_E_NOMEM;
+  c->device = device;
+  c->max_N = max_N;
+  c->max_nrhs = max_nrhs;
+  c->lu_prec = -1;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = (size_t)optin;
+
+  const size_t NN = (size_t)max_N * max_N;
+  const size_t NR = (size_t)max_N * max_nrhs;
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (!ok) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      ok = false;
+      cudaGetLastError();
+    }
+  };
+  alloc((void**)&c->z64, NN * sizeof(double2));
+  c->ld64 = max_N;
+  alloc(&c->lu_re, NN * sizeof(double));
+  alloc(&c->lu_im, NN * sizeof(double));
+  c->ld_lu = max_N;
+  alloc((void**)&c->ipiv, (size_t)max_N * sizeof(int));
+  alloc((void**)&c->perm, (size_t)max_N * sizeof(int));
+  alloc(&c->w_re, NR * sizeof(double));
+  alloc(&c->w_im, NR * sizeof(double));
+  alloc((void**)&c->x_re, NR * sizeof(double));
+  alloc((void**)&c->x_im, NR * sizeof(double));
+  alloc((void**)&c->r_re, NR * sizeof(double));
+  alloc((void**)&c->r_im, NR * sizeof(double));
+  alloc((void**)&c->v_re, NR * sizeof(double));
+  alloc((void**)&c->v_im, NR * sizeof(double));
+  alloc(&c->t_re, NR * sizeof(double));
+  alloc(&c->t_im, NR * sizeof(double));
+  alloc((void**)&c->red, 16 * sizeof(double));
+  alloc((void**)&c->dstatus, 4 * sizeof(int));
+  if (ok && cudaMallocHost((void**)&c->red_host, 16 * sizeof(double)) != cudaSuccess) ok = false;
+  if (ok && cudaMallocHost((void**)&c->hstatus, 4 * sizeof(int)) != cudaSuccess) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(c);
+    free(c);
+    return HARP_E_NOMEM;
+  }
+  int init[4] = {0, INT_MAX, 0, 0};
+  if (cudaMemcpy(c->dstatus, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) {
+    int s = cuda_status(cudaGetLastError());
+    free_all(c);
+    free(c);
+    return s;
+  }
+  *out = c;
+  return HARP_OK;
+}
+
+extern "C" int harp_ctx_destroy(harp_ctx* c) {
+  if (!c) return -1;
+  {
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    free_all(c);
+  }
+  free(c);
+  return HARP_OK;
+}
+
+extern "C" int harp_ctx_z64(harp_ctx* c, void** z64, int* ld) {
+  if (!c) return -1;
+  if (!z64) return -2;
+  if (!ld) return -3;
+  *z64 = c->z64;
+  *ld = c->ld64;
+  return HARP_OK;
+}

@@ -1,0 +1,65 @@
+// dense.cuh -- internal interface of the dense complex kernels (LU with
+// partial pivoting, triangular solves, GEMM, conversions, norms).
+#pragma once
+
+#include "common.cuh"
+
+namespace harp {
+
+// How the FP32 contractions of the mixed path run.
+enum GemmMode : int {
+  GEMM_SIMT = 0,       // CUDA-core FMA (FP32 or FP64 by type)
+  GEMM_TC_3XTF32 = 1,  // tcgen05 kind::tf32, hi/lo split, three products
+  GEMM_TC_TF32 = 2,    // tcgen05 kind::tf32, one product
+};
+
+// C = beta*C + alpha*A*B for complex views (A: M x K, B: K x N).
+template <typename R>
+int cgemm(int M, int N, int K, R alpha, CView<R> A, CView<R> B, R beta, CView<R> C, int mode,
+          cudaStream_t st);
+template <>
+int cgemm<float>(int M, int N, int K, float alpha, CView<float> A, CView<float> B, float beta,
+                 CView<float> C, int mode, cudaStream_t st);
+template <>
+int cgemm<double>(int M, int N, int K, double alpha, CView<double> A, CView<double> B, double beta,
+                  CView<double> C, int mode, cudaStream_t st);
+
+// PA = LU in place on split planes (N x N, leading dimension ld).
+// ipiv[k] = row swapped with row k (0-based, global). The smallest
+// 1-based column with an exactly zero pivot is atomically min-ed into
+// *zero_col (device). perm (device, N ints) receives the net row
+// permutation: row i of PA is row perm[i] of A.
+template <typename R>
+int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm, int* zero_col,
+              int mode, cudaStream_t st);
+
+// Solve op(A) X = B with the factors of lu_factor; B (N x nrhs split
+// planes, leading dimension ldb) is overwritten. tmp has room for N x nrhs
+// (leading dimension ldb) of each plane.
+template <typename R>
+int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, R* bim, long ldb,
+             R* tre, R* tim, char trans, int mode, cudaStream_t st);
+
+// Elementwise conversions between interleaved complex storage and planes.
+template <typename Rin, typename Rout>
+int interleaved_to_planes(int M, int N, const Rin* src, long lds, Rout* re, Rout* im, long ldd,
+                          cudaStream_t st);
+template <typename Rin, typename Rout>
+int planes_to_planes(int M, int N, const Rin* sre, const Rin* sim, long lds, Rout* dre, Rout* dim,
+                     long ldd, cudaStream_t st);
+int planes_to_interleaved(int M, int N, const double* re, const double* im, long lds, double* dst,
+                          long ldd, cudaStream_t st);
+// dst (planes, M x N) = E: unit entry at row c*Nm of column c.
+template <typename R>
+int port_rhs_planes(int M, int N, int Nm, R* re, R* im, long ld, cudaStream_t st);
+// X += D (FP64 planes += R planes)
+template <typename R>
+int add_planes(int M, int N, double* xre, double* xim, long ldx, const R* dre, const R* dim,
+               long ldd, cudaStream_t st);
+// out[slot] = max_i sum_j |A_ij| (matrix infinity norm), A given as a view.
+// out must be zeroed first (zero_doubles).
+template <typename R>
+int norm_inf(int M, int N, CView<R> A, double* out, cudaStream_t st);
+int zero_doubles(double* p, int n, cudaStream_t st);
+
+}  // namespace harp

@@ -1,0 +1,279 @@
+// fill.cu -- the HARP fill of the reduced MBF matrix (Eq. 3 and 4).
+//
+// For every ordered antenna pair (m, n), m != n, with Delta = x_m - x_n,
+// r = |Delta|, e^{j alpha} = Delta / r and d = 1/r:
+//   Z^{mn}_TS = sum_k c_k^{TS} phi_k,   phi_{p,q} = e^{-jkr} e^{j p alpha} d^q,
+// k running over the K = (2P+1)(Q+1) harmonic/power pairs (Eq. 3 inserted
+// in Eq. 4; the far-field term of Eq. 1 arrives folded into q = 1).
+//
+// Work item = (source antenna n, a tile of 32 testing antennas, a chunk of
+// source MBFs S). A CTA stages the coefficient chunk C[k][S,T] in shared
+// memory once and loops over work items (persistent grid, one CTA per SM
+// at the shared-memory sizes used here). Per item, one warp computes the
+// basis phi[k][pair] (geometry and e^{-jkr} in FP64, powers of e^{j alpha}
+// and d by repeated multiplication in the kernel's precision), then all 8
+// warps run the contraction Z[pair, (S,T)] = sum_k phi[k][pair] C[k][(S,T)]
+// with a 4-pair x TN-entry register tile per thread. Lanes run along (S,T)
+// with T fastest, so stores are runs of Nm consecutive rows of a column.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace harp {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+
+struct FillArgs {
+  int Na, Nm, P, Q, K, nq;
+  const double* pos;
+  double k;
+  const double2* coef;  // [T][S][p+P][q]
+  const double2* self;
+  long self_stride;
+  void* Z;  // cplx_t<R>, ldz
+  long ldz;
+  float2* Z32;  // optional rounded copy (dual store), ld32
+  long ld32;
+  int* status;
+  int s_chunk;
+  int n_mtiles;
+  int n_items;
+  int Wp;  // padded row length of the staged coefficient chunk (32*TN)
+};
+
+constexpr int kPairsPerTile = 32;
+constexpr int kFillThreads = 256;
+
+template <typename R, int TN, bool DUAL>
+__global__ void __launch_bounds__(kFillThreads, 1) fill_kernel(FillArgs a) {
+  using C = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, Nm = a.Nm, nq = a.nq, P = a.P, Q = a.Q;
+  const int s0 = blockIdx.y * a.s_chunk;
+  const int sc = min(a.s_chunk, Nm - s0);
+  const int W = sc * Nm;
+  const int Wp = a.Wp;
+  C* Cs = reinterpret_cast<C*>(smem_raw);  // [K][Wp], entry (S - s0)*Nm + T
+  C* Phi = Cs + (size_t)K * Wp;            // [K][32]
+
+  for (int idx = threadIdx.x; idx < K * Wp; idx += blockDim.x) {
+    const int kk = idx / Wp, e = idx - kk * Wp;
+    C v = mk<R>(0, 0);
+    if (e < W) {
+      const int sl = e / Nm, T = e - sl * Nm;
+      const double2 c = a.coef[((size_t)T * Nm + (s0 + sl)) * K + kk];
+      v = mk<R>((R)c.x, (R)c.y);
+    }
+    Cs[idx] = v;
+  }
+
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int n = item / a.n_mtiles;
+    const int m0 = (item - n * a.n_mtiles) * kPairsPerTile;
+    __syncthreads();  // Cs staged / previous item's Phi consumed
+    if (threadIdx.x < kPairsPerTile) {
+      const int t = threadIdx.x;
+      const int m = m0 + t;
+      bool valid = (m < a.Na) && (m != n);
+      double dx = 0.0, dy = 0.0, r = 0.0;
+      if (valid) {
+        dx = a.pos[2 * m] - a.pos[2 * n];
+        dy = a.pos[2 * m + 1] - a.pos[2 * n + 1];
+        r = hypot(dx, dy);
+        if (r == 0.0) {
+          atomicOr(a.status, ST_COINCIDENT);
+          valid = false;
+        }
+      }
+      if (!valid) {
+        for (int kk = 0; kk < K; ++kk) Phi[kk * kPairsPerTile + t] = mk<R>(0, 0);
+      } else {
+        const double d = 1.0 / r;
+        double s, c;
+        sincos(a.k * r, &s, &c);  // FP64: kr reaches a few hundred radians
+        const C ph = mk<R>((R)c, (R)(-s));             // e^{-jkr}
+        const C z = mk<R>((R)(dx * d), (R)(dy * d));  // e^{j alpha}
+        const R dR = (R)d;
+        C zp = mk<R>(1, 0);
+        for (int p = 0; p <= P; ++p) {
+          const C bp = cmul(ph, zp);
+          const C bn = cmul(ph, cconj(zp));
+          R dq = 1;
+          for (int q = 0; q <= Q; ++q) {
+            Phi[((P + p) * nq + q) * kPairsPerTile + t] = mk<R>(bp.x * dq, bp.y * dq);
+            if (p > 0) Phi[((P - p) * nq + q) * kPairsPerTile + t] = mk<R>(bn.x * dq, bn.y * dq);
+            dq *= dR;
+          }
+          zp = cmul(zp, z);
+        }
+      }
+    }
+    __syncthreads();
+
+    C acc[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = mk<R>(0, 0);
+
+    const C* phrow = Phi + ty * 4;
+#pragma unroll 2
+    for (int kk = 0; kk < K; ++kk) {
+      C f[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f[i] = phrow[kk * kPairsPerTile + i];
+      const C* crow = Cs + (size_t)kk * Wp + tx;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const C cv = crow[32 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cfma(acc[i][j], f[i], cv);
+      }
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty * 4 + i;
+      if (m >= a.Na) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int e = tx + 32 * j;
+        if (e >= W) continue;
+        const int sl = e / Nm, T = e - sl * Nm, S = s0 + sl;
+        const size_t row = (size_t)m * Nm + T, col = (size_t)n * Nm + S;
+        C v = acc[i][j];
+        double2 dv = make_double2((double)v.x, (double)v.y);
+        if (m == n) {
+          dv = a.self[(size_t)m * a.self_stride + T + (size_t)S * Nm];
+          v = mk<R>((R)dv.x, (R)dv.y);
+        }
+        reinterpret_cast<C*>(a.Z)[row + col * a.ldz] = v;
+        if (DUAL) a.Z32[row + col * a.ld32] = make_float2((float)dv.x, (float)dv.y);
+      }
+    }
+  }
+}
+
+template <typename R, bool DUAL>
+static int launch_fill(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int nchunks,
+                       cudaStream_t st) {
+  void (*kern)(FillArgs) = nullptr;
+  switch (TN) {
+    case 1: kern = fill_kernel<R, 1, DUAL>; break;
+    case 2: kern = fill_kernel<R, 2, DUAL>; break;
+    case 3: kern = fill_kernel<R, 3, DUAL>; break;
+    case 4: kern = fill_kernel<R, 4, DUAL>; break;
+    case 5: kern = fill_kernel<R, 5, DUAL>; break;
+    case 6: kern = fill_kernel<R, 6, DUAL>; break;
+    case 7: kern = fill_kernel<R, 7, DUAL>; break;
+    case 8: kern = fill_kernel<R, 8, DUAL>; break;
+    default: return HARP_E_UNSUPPORTED;
+  }
+  HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int per_chunk = std::max(1, (ctx->num_sms + nchunks - 1) / nchunks);
+  dim3 grid(std::min(a.n_items, per_chunk), nchunks);
+  kern<<<grid, kFillThreads, smem, st>>>(a);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// Largest source-MBF chunk whose staged coefficients fit in shared memory.
+static bool plan_fill(const harp_ctx* ctx, int Nm, int K, size_t csz, int* s_chunk, int* TN,
+                      size_t* smem) {
+  for (int sc = Nm; sc >= 1; --sc) {
+    const int W = sc * Nm;
+    const int tn = (W + 31) / 32;
+    if (tn > 8) continue;
+    const size_t bytes = ((size_t)K * 32 * tn + (size_t)K * kPairsPerTile) * csz;
+    if (bytes <= ctx->smem_optin) {
+      *s_chunk = sc;
+      *TN = tn;
+      *smem = bytes;
+      return true;
+    }
+  }
+  return false;
+}
+
+int fill_dispatch(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
+                  const double* coef, const double* self_blocks, long self_stride, void* Z,
+                  long ldz, float2* Z32, long ld32, int prec_kind, cudaStream_t st) {
+  // prec_kind: 0 = FP64 only, 1 = FP64 with rounded c64 copy, 2 = FP32 only
+  FillArgs a;
+  a.Na = Na;
+  a.Nm = Nm;
+  a.P = P;
+  a.Q = Q;
+  a.nq = Q + 1;
+  a.K = (2 * P + 1) * (Q + 1);
+  a.pos = pos;
+  a.k = 2.0 * kPi * freq_hz / kC0;
+  a.coef = reinterpret_cast<const double2*>(coef);
+  a.self = reinterpret_cast<const double2*>(self_blocks);
+  a.self_stride = self_stride;
+  a.Z = Z;
+  a.ldz = ldz;
+  a.Z32 = Z32;
+  a.ld32 = ld32;
+  a.status = ctx->dstatus;
+  a.n_mtiles = (Na + kPairsPerTile - 1) / kPairsPerTile;
+  a.n_items = Na * a.n_mtiles;
+  const size_t csz = (prec_kind == 2) ? sizeof(float2) : sizeof(double2);
+  int sc, TN;
+  size_t smem;
+  if (!plan_fill(ctx, Nm, a.K, csz, &sc, &TN, &smem)) return HARP_E_UNSUPPORTED;
+  a.s_chunk = sc;
+  a.Wp = 32 * TN;
+  const int nchunks = (Nm + sc - 1) / sc;
+  if (prec_kind == 2) return launch_fill<float, false>(ctx, a, TN, smem, nchunks, st);
+  if (prec_kind == 1) return launch_fill<double, true>(ctx, a, TN, smem, nchunks, st);
+  return launch_fill<double, false>(ctx, a, TN, smem, nchunks, st);
+}
+
+}  // namespace harp
+
+using namespace harp;
+
+extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
+                         double freq_hz, const double* coef, const double* self_blocks,
+                         long self_stride, void* Z, int ldz, int prec, void* stream) {
+  if (!ctx) return -1;
+  if (Na < 1) return -2;
+  if (Nm < 1) return -3;
+  if (P < 0 || P > 64) return -4;
+  if (Q < 0 || Q > 64) return -5;
+  if (!pos) return -6;
+  if (!(freq_hz > 0.0) || freq_hz > 1e15) return -7;
+  if (!coef) return -8;
+  if (!self_blocks) return -9;
+  if (self_stride < 0) return -10;
+  if (!Z) return -11;
+  const long N = (long)Na * Nm;
+  if (N > (1L << 30)) return HARP_E_UNSUPPORTED;
+  if (ldz < N) return -12;
+  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32 && prec != HARP_FP32)
+    return -13;
+  const bool mixed = (prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32);
+  if (mixed && N > ctx->max_N) return HARP_E_UNSUPPORTED;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  HARP_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), st));
+  int s;
+  if (prec == HARP_FP64)
+    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, Z, ldz,
+                      nullptr, 0, 0, st);
+  else if (prec == HARP_FP32)
+    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, Z, ldz,
+                      nullptr, 0, 2, st);
+  else
+    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, ctx->z64,
+                      ctx->ld64, reinterpret_cast<float2*>(Z), ldz, 1, st);
+  if (s != HARP_OK) return s;
+  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HARP_CUDA(cudaStreamSynchronize(st));
+  if (ctx->hstatus[0] & ST_COINCIDENT) return HARP_E_COINCIDENT;
+  return HARP_OK;
+}

@@ -1,0 +1,173 @@
+// solve.cu -- mbf_solve: the direct solve of the reduced MBF system for every
+// port excitation (Section II-B), in FP64, in FP32, or in mixed precision
+// with FP64-accurate iterative refinement.
+//
+// Mixed refinement (classical iterative refinement, Wilkinson/Moler; the
+// stopping rule follows LAPACK's zcgesv):
+//   X0 = (LU32)^{-1} V
+//   repeat: R = V - Z64 X (FP64); stop when ||R||_inf <= tol (||Z64||_inf
+//           ||X||_inf + ||V||_inf); D = (LU32)^{-1} R; X += D.
+// The LU factors live in the context so that an adjoint solve (trans 'T')
+// reuses them.
+#include <cmath>
+#include <climits>
+
+#include "dense.cuh"
+
+namespace harp {
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
+static bool is_mixed(int prec) { return prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32; }
+static int gemm_mode(int prec) {
+  if (prec == HARP_MIXED_TF32) return GEMM_TC_TF32;
+  if (prec == HARP_MIXED_3XTF32 || prec == HARP_FP32) return GEMM_TC_3XTF32;
+  return GEMM_SIMT;
+}
+// Factorisations are shared between the modes that store the same type.
+static int lu_class(int prec) { return prec == HARP_FP64 ? 0 : 1; }
+
+// Copy the right-hand sides (or the port excitations) into FP64 planes.
+static int load_rhs(harp_ctx* c, int N, int nrhs, const double* V, int ldv, double* re, double* im,
+                    cudaStream_t st) {
+  if (V) return interleaved_to_planes<double, double>(N, nrhs, V, ldv, re, im, c->max_N, st);
+  return port_rhs_planes<double>(N, nrhs, N / nrhs, re, im, c->max_N, st);
+}
+
+static int read_back(harp_ctx* c, int nd, cudaStream_t st) {
+  HARP_CUDA(cudaMemcpyAsync(c->red_host, c->red, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
+  HARP_CUDA(cudaStreamSynchronize(st));
+  return HARP_OK;
+}
+
+}  // namespace harp
+
+using namespace harp;
+
+extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int ldv,
+                         int nrhs, double* X, int ldx, char trans, int prec, double tol,
+                         int max_iter, int* iters_out, double* resid_out, void* stream) {
+  if (!ctx) return -1;
+  if (N < 1 || N > ctx->max_N) return -2;
+  const bool tr = (trans == 'T' || trans == 't');
+  if (!tr && trans != 'N' && trans != 'n') return -10;
+  if (!tr && !Z) return -3;
+  if (!tr && ldz < N) return -4;
+  if (V && ldv < N) return -6;
+  if (nrhs < 1 || nrhs > ctx->max_nrhs || nrhs > 65535) return -7;
+  if (!V && (N % nrhs) != 0) return -5;
+  if (!X) return -8;
+  if (ldx < N) return -9;
+  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32 && prec != HARP_FP32)
+    return -11;
+  if (!(tol == tol)) return -12;
+  if (max_iter < 0) return -13;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  const int mode = gemm_mode(prec);
+  const long ldw = ctx->max_N;
+  if (iters_out) *iters_out = 0;
+  if (resid_out) *resid_out = -1.0;
+
+  // ---- factorisation (trans 'N') or reuse of the cached one (trans 'T')
+  if (!tr) {
+    ctx->lu_valid = 0;
+    set_int_kernel<<<1, 1, 0, st>>>(ctx->dstatus + 1, INT_MAX);
+    HARP_LAUNCHED();
+    if (lu_class(prec) == 0) {
+      double* re = (double*)ctx->lu_re;
+      double* im = (double*)ctx->lu_im;
+      HARP_TRY(interleaved_to_planes<double, double>(N, N, (const double*)Z, ldz, re, im,
+                                                     ctx->ld_lu, st));
+      HARP_TRY(lu_factor<double>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
+                                 ctx->dstatus + 1, mode, st));
+    } else {
+      float* re = (float*)ctx->lu_re;
+      float* im = (float*)ctx->lu_im;
+      HARP_TRY(interleaved_to_planes<float, float>(N, N, (const float*)Z, ldz, re, im, ctx->ld_lu,
+                                                   st));
+      HARP_TRY(lu_factor<float>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
+                                ctx->dstatus + 1, mode, st));
+    }
+    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, sizeof(int),
+                              cudaMemcpyDeviceToHost, st));
+    HARP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->hstatus[1] != INT_MAX) return ctx->hstatus[1];
+    ctx->lu_N = N;
+    ctx->lu_prec = lu_class(prec);
+    ctx->lu_valid = 1;
+  } else if (!ctx->lu_valid || ctx->lu_N != N || ctx->lu_prec != lu_class(prec)) {
+    return HARP_E_STATE;
+  }
+
+  // ---- FP64: direct solve
+  if (prec == HARP_FP64) {
+    double* wre = (double*)ctx->w_re;
+    double* wim = (double*)ctx->w_im;
+    HARP_TRY(load_rhs(ctx, N, nrhs, V, ldv, wre, wim, st));
+    HARP_TRY(lu_solve<double>(N, nrhs, (double*)ctx->lu_re, (double*)ctx->lu_im, ctx->ld_lu,
+                              ctx->perm, wre, wim, ldw, (double*)ctx->t_re, (double*)ctx->t_im,
+                              tr ? 'T' : 'N', mode, st));
+    HARP_TRY(planes_to_interleaved(N, nrhs, wre, wim, ldw, X, ldx, st));
+    return HARP_OK;
+  }
+
+  float* lre = (float*)ctx->lu_re;
+  float* lim = (float*)ctx->lu_im;
+  float* wre = (float*)ctx->w_re;
+  float* wim = (float*)ctx->w_im;
+  float* tre = (float*)ctx->t_re;
+  float* tim = (float*)ctx->t_im;
+  HARP_TRY(load_rhs(ctx, N, nrhs, V, ldv, ctx->v_re, ctx->v_im, st));
+  HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->v_re, ctx->v_im, ldw, wre, wim, ldw, st));
+  HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
+                           tr ? 'T' : 'N', mode, st));
+  HARP_TRY(planes_to_planes<float, double>(N, nrhs, wre, wim, ldw, ctx->x_re, ctx->x_im, ldw, st));
+
+  // ---- FP32: no refinement
+  if (prec == HARP_FP32) {
+    HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
+    return HARP_OK;
+  }
+
+  // ---- mixed: FP64 residual against the context's FP64 matrix
+  CView<double> Z64 = interleaved<double>((double*)ctx->z64, ctx->ld64);
+  if (tr) Z64 = Z64.t();
+  if (tol <= 0.0) tol = std::sqrt((double)N) * std::ldexp(1.0, -53);
+  HARP_TRY(zero_doubles(ctx->red, 4, st));
+  HARP_TRY(norm_inf<double>(N, N, Z64, ctx->red + 0, st));
+  HARP_TRY(norm_inf<double>(N, nrhs, planes<double>(ctx->v_re, ctx->v_im, ldw), ctx->red + 1, st));
+  CView<double> Rv = planes<double>(ctx->r_re, ctx->r_im, ldw);
+  CView<double> Xv = planes<double>(ctx->x_re, ctx->x_im, ldw);
+  double bwd = INFINITY;
+  int it = 0;
+  bool converged = false;
+  for (;;) {
+    HARP_TRY(planes_to_planes<double, double>(N, nrhs, ctx->v_re, ctx->v_im, ldw, ctx->r_re,
+                                              ctx->r_im, ldw, st));
+    HARP_TRY(cgemm<double>(N, nrhs, N, -1.0, Z64, Xv, 1.0, Rv, GEMM_SIMT, st));
+    HARP_TRY(zero_doubles(ctx->red + 2, 2, st));
+    HARP_TRY(norm_inf<double>(N, nrhs, Rv, ctx->red + 2, st));
+    HARP_TRY(norm_inf<double>(N, nrhs, Xv, ctx->red + 3, st));
+    HARP_TRY(read_back(ctx, 4, st));
+    const double* h = ctx->red_host;
+    bwd = h[2] / (h[0] * h[3] + h[1]);
+    if (!(bwd == bwd)) return HARP_E_NONFINITE;
+    if (bwd <= tol) {
+      converged = true;
+      break;
+    }
+    if (it >= max_iter) break;
+    HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->r_re, ctx->r_im, ldw, wre, wim, ldw, st));
+    HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
+                             tr ? 'T' : 'N', mode, st));
+    HARP_TRY(add_planes<float>(N, nrhs, ctx->x_re, ctx->x_im, ldw, wre, wim, ldw, st));
+    ++it;
+  }
+  HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
+  if (iters_out) *iters_out = it;
+  if (resid_out) *resid_out = bwd;
+  HARP_CUDA(cudaStreamSynchronize(st));
+  return converged ? HARP_OK : HARP_E_NOCONV;
+}

@@ -1,0 +1,245 @@
+"""Python binding of libharp_gb300.so (argument marshalling only).
+
+Every step of the fill, the solve and the adjoint runs in the library's CUDA
+kernels; this module only moves torch tensors (device memory) and streams
+across the C ABI declared in include/harp_gb300.h. It never falls back to a
+CPU path: if the library is missing or fails to load, `lib()` raises.
+
+Matrices are column-major at the ABI. A column-major N x N buffer appears in
+torch as the transpose view of a row-major tensor, so the tensors returned
+here index naturally (Z[i, j] is row i, column j) with strides (1, ld).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libharp_gb300.so")
+
+FP64, MIXED_3XTF32, MIXED_TF32, FP32 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "mixed": MIXED_3XTF32, "mixed_3xtf32": MIXED_3XTF32,
+        "mixed_tf32": MIXED_TF32, "fp32": FP32}
+
+HARP_OK = 0
+HARP_E_COINCIDENT = 0x40000001
+HARP_E_NOCONV = 0x40000002
+HARP_E_TIMEOUT = 0x40000003
+HARP_E_CUDA = 0x40000004
+HARP_E_NOMEM = 0x40000005
+HARP_E_UNSUPPORTED = 0x40000006
+HARP_E_STATE = 0x40000007
+HARP_E_NONFINITE = 0x40000008
+
+_lib = None
+
+
+class HarpError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = lib().harp_status_string(status).decode()
+        extra = ""
+        if status == HARP_E_CUDA:
+            extra = f" (cuda error {lib().harp_last_cuda_error()})"
+        super().__init__(f"{fn} returned {status:#x}: {msg}{extra}")
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -m paper_1702_03781_gb300.build)")
+        L = ct.CDLL(LIB_PATH)
+        vp, i, d, l = ct.c_void_p, ct.c_int, ct.c_double, ct.c_long
+        L.harp_status_string.argtypes = [i]
+        L.harp_status_string.restype = ct.c_char_p
+        L.harp_last_cuda_error.restype = i
+        L.harp_ctx_create.argtypes = [ct.POINTER(vp), i, i, i]
+        L.harp_ctx_destroy.argtypes = [vp]
+        L.harp_ctx_z64.argtypes = [vp, ct.POINTER(vp), ct.POINTER(i)]
+        L.harp_fill.argtypes = [vp, i, i, i, i, vp, d, vp, vp, l, vp, i, i, vp]
+        L.mbf_solve.argtypes = [vp, i, vp, i, vp, i, i, vp, i, ct.c_char, i, d, i,
+                                ct.POINTER(i), ct.POINTER(d), vp]
+        L.harp_fill_adjoint.argtypes = [vp, i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
+        for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_z64", "harp_fill",
+                   "mbf_solve", "harp_fill_adjoint"):
+            getattr(L, fn).restype = i
+        _lib = L
+    return _lib
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _stream(stream) -> ct.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ct.c_void_p:
+    return ct.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def colmajor_empty(rows: int, cols: int, dtype, device) -> torch.Tensor:
+    """An uninitialised column-major (rows x cols) tensor (strides (1, rows))."""
+    return torch.empty((cols, rows), dtype=dtype, device=device).T
+
+
+def as_colmajor(x: torch.Tensor) -> torch.Tensor:
+    """x itself if it is column-major with unit row stride, else a copy."""
+    if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.T.contiguous().T
+
+
+def _ld(x: torch.Tensor) -> int:
+    return max(int(x.stride(1)), int(x.shape[0]), 1)
+
+
+def _check(fn: str, status: int, ok=(HARP_OK,)):
+    if status not in ok:
+        raise HarpError(fn, status)
+    return status
+
+
+class Harp:
+    """A library context on one CUDA device: owns the device workspace for
+    systems of up to max_N unknowns and max_nrhs right-hand sides."""
+
+    def __init__(self, device: int | None = None, max_N: int = 3072, max_nrhs: int = 256):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self.max_N = int(max_N)
+        self.max_nrhs = int(max_nrhs)
+        h = ct.c_void_p()
+        _check("harp_ctx_create", lib().harp_ctx_create(ct.byref(h), self.device, self.max_N,
+                                                         self.max_nrhs))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().harp_ctx_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ct.c_void_p:
+        return self._h
+
+    def z64(self, N: int) -> torch.Tensor:
+        """The context's FP64 reduced matrix as a column-major (N x N) view."""
+        p, ld = ct.c_void_p(), ct.c_int()
+        _check("harp_ctx_z64", lib().harp_ctx_z64(self._h, ct.byref(p), ct.byref(ld)))
+        # Wrap the raw device pointer without copying.
+        storage = _alias_storage(p.value, ld.value * self.max_N * 16, self.device)
+        full = torch.empty(0, dtype=torch.complex128, device=f"cuda:{self.device}")
+        full.set_(storage, 0, (self.max_N, ld.value), (ld.value, 1))
+        return full.T[:N, :N]
+
+    # -- fill ---------------------------------------------------------------
+    def fill(self, pos: torch.Tensor, freq_hz: float, coef: torch.Tensor,
+             self_blocks: torch.Tensor, prec="fp64", out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+        """Reduced MBF matrix: complex128 (fp64) or complex64 (other modes),
+        column-major N x N. self_blocks: (Na, Nm, Nm) [antenna, T, S] or one
+        shared (Nm, Nm) block."""
+        pr = _prec(prec)
+        pos = pos.to(torch.float64).contiguous()
+        coef = coef.to(torch.complex128).contiguous()
+        Nm = coef.shape[0]
+        P = (coef.shape[2] - 1) // 2
+        Q = coef.shape[3] - 1
+        Na = pos.shape[0]
+        N = Na * Nm
+        if self_blocks.dim() == 2:
+            sb = self_blocks.to(torch.complex128).T.contiguous()
+            stride = 0
+        else:
+            sb = self_blocks.to(torch.complex128).transpose(1, 2).contiguous()
+            stride = Nm * Nm
+        dt = torch.complex128 if pr == FP64 else torch.complex64
+        Z = colmajor_empty(N, N, dt, pos.device) if out is None else out
+        _check("harp_fill", lib().harp_fill(self._h, Na, Nm, P, Q, _ptr(pos), float(freq_hz),
+                                            _ptr(coef), _ptr(sb), stride, _ptr(Z), _ld(Z), pr,
+                                            _stream(stream)))
+        return Z
+
+    # -- solve --------------------------------------------------------------
+    def solve(self, Z: torch.Tensor | None, V: torch.Tensor | None = None, nrhs: int | None = None,
+              prec="fp64", trans: str = "N", tol: float = 0.0, max_iter: int = 10,
+              out: torch.Tensor | None = None, stream=None, allow_noconv: bool = False):
+        """X (complex128, column-major N x nrhs) and {'iters', 'resid', 'status'}.
+        V = None solves for the port excitations (nrhs ports)."""
+        pr = _prec(prec)
+        if Z is not None:
+            Z = as_colmajor(Z)
+            N = Z.shape[0]
+        elif V is not None:
+            N = V.shape[0]
+        else:
+            raise ValueError("need Z or V to know N")
+        if V is not None:
+            V = as_colmajor(V.to(torch.complex128))
+            nrhs = V.shape[1]
+        if nrhs is None:
+            raise ValueError("nrhs is required when V is None")
+        dev = Z.device if Z is not None else V.device
+        X = colmajor_empty(N, nrhs, torch.complex128, dev) if out is None else out
+        it, res = ct.c_int(0), ct.c_double(0.0)
+        st = lib().mbf_solve(self._h, N, _ptr(Z), _ld(Z) if Z is not None else N, _ptr(V),
+                             _ld(V) if V is not None else N, nrhs, _ptr(X), _ld(X),
+                             trans.encode(), pr, float(tol), int(max_iter), ct.byref(it),
+                             ct.byref(res), _stream(stream))
+        ok = (HARP_OK, HARP_E_NOCONV) if allow_noconv else (HARP_OK,)
+        _check("mbf_solve", st, ok)
+        return X, {"iters": it.value, "resid": res.value, "status": st}
+
+    # -- adjoint ------------------------------------------------------------
+    def fill_adjoint(self, pos: torch.Tensor, freq_hz: float, coef: torch.Tensor,
+                     Lam: torch.Tensor, X: torch.Tensor, prec="fp64", stream=None) -> torch.Tensor:
+        """grad (Na, 2) float64 of J from the adjoint Lambda and solution X."""
+        pr = _prec(prec)
+        pos = pos.to(torch.float64).contiguous()
+        coef = coef.to(torch.complex128).contiguous()
+        Nm = coef.shape[0]
+        P = (coef.shape[2] - 1) // 2
+        Q = coef.shape[3] - 1
+        Na = pos.shape[0]
+        Lam = as_colmajor(Lam.to(torch.complex128))
+        X = as_colmajor(X.to(torch.complex128))
+        if _ld(Lam) != _ld(X):
+            Lam, X = Lam.T.contiguous().T, X.T.contiguous().T
+        ld = _ld(X)
+        grad = torch.empty((Na, 2), dtype=torch.float64, device=pos.device)
+        _check("harp_fill_adjoint", lib().harp_fill_adjoint(
+            self._h, Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(Lam), _ptr(X), ld,
+            X.shape[1], _ptr(grad), pr, _stream(stream)))
+        return grad
+
+
+def _alias_storage(ptr: int, nbytes: int, device: int):
+    # torch.from_dlpack over a DLPack capsule would also work; a cuda array
+    # interface dict is the simplest zero-copy alias.
+    class _A:
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    t = torch.as_tensor(_A(), device=f"cuda:{device}")
+    return t.untyped_storage()
