@@ -1,0 +1,314 @@
+"""Benchmark: HARP fill + MBF solve per frequency on the 256-antenna station.
+
+One step = one pass of the hot path for one frequency of the 256-antenna,
+12-MBF SKA-like station at 110 MHz (N = 3072 unknowns, 256 port
+excitations): the mixed-precision fill (harp_fill) and the mixed-precision
+solve with iterative refinement to the FP64 backward-error tolerance
+(mbf_solve), all through the library's C ABI. The plain FP64 GPU path is
+timed beside it on the same inputs, and both solutions are checked against
+each other (and, in the tests, against the FP64 CPU oracle).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the solve does not
+shard); value = max-over-ranks step time / frequencies processed by all
+ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fill+solve ms/frequency (256 ant, 12 MBF), mixed vs FP64 GPU at ≤1e-10 rel err"
+WORKLOAD = "SKA-like station: 256 antennas in a 38 m disc (min sep 1.5 m), 12 MBFs, 110 MHz, P=8, Q=5; N=3072, 256 port RHS"
+
+
+# Arithmetic each kernel class runs on in the mixed step (roofline bound).
+IMPL = {"fill": "fp64", "gemm": "fp32", "residual": "fp64", "panel": "fp32", "trsm": "fp32",
+        "swap": "fp32", "adjoint": "fp32", "other": "fp32"}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(steps: int = 1):
+    """The FP64 oracle as it stands: fill + LU solve of the full station
+    (one frequency per step) on this host's cores."""
+    import numpy as np
+    import oracle
+    from paper_1702_03781_gb300 import synth
+    p = synth.station()
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        Z = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
+        oracle.solve(Z, p.V)
+        ts.append(time.perf_counter() - t0)
+    return {"value": 1e3 * statistics.mean(ts), "unit": "ms", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"full station frequency (N=3072, 256 RHS) fill + LU solve, {steps} run(s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_baseline(1)
+    cb = cpu_baseline(args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["value"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nvtx-step", default="",
+                    help="run the warm-up, then one step of this path ('mixed' or 'fp64') inside "
+                         "an NVTX range named harp_step, and exit (for an ncu launch list)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_03781_gb300 import synth
+    from paper_1702_03781_gb300 import harp as H
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    p = synth.station()
+    Na, N = p.Na, p.N
+    pos = torch.from_numpy(p.pos).to(dev)
+    coef = torch.from_numpy(p.coef).to(dev)
+    sb = torch.from_numpy(p.self_blocks).to(dev)
+    h = H.Harp(local, max_N=N, max_nrhs=Na)
+    Z32 = H.colmajor_empty(N, N, torch.complex64, dev)
+    Z64 = H.colmajor_empty(N, N, torch.complex128, dev)
+    X = H.colmajor_empty(N, Na, torch.complex128, dev)
+    X64 = H.colmajor_empty(N, Na, torch.complex128, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    info = {}
+
+    def step_mixed():
+        h.fill(pos, p.freq_hz, coef, sb, prec="mixed", out=Z32)
+        _, inf = h.solve(Z32, None, nrhs=Na, prec="mixed", max_iter=10, out=X)
+        info.update(inf)
+
+    def step_fp64():
+        h.fill(pos, p.freq_hz, coef, sb, prec="fp64", out=Z64)
+        h.solve(Z64, None, nrhs=Na, prec="fp64", out=X64)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    from paper_1702_03781_gb300 import roofline
+
+    if args.nvtx_step:
+        fn = step_mixed if args.nvtx_step == "mixed" else step_fp64
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        torch.cuda.nvtx.range_push("harp_step")
+        fn()
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        h.close()
+        return 0
+
+    for _ in range(args.warmup):
+        step_mixed()
+    for _ in range(2):
+        step_fp64()
+    barrier()
+    # kernel-class shares of one untimed step (all classes instrumented)
+    roofline.begin(h)
+    step_mixed()
+    prof_all = roofline.end(h)
+    shares = roofline.shares(prof_all)
+    dominant = max(prof_all, key=lambda k: prof_all[k]["ms"])
+    barrier()
+    L0 = H.kernel_launches()
+    roofline.begin(h, 1 << roofline.KINDS.index(dominant))
+    with ClockSampler(local) as clk:
+        barrier()
+        ms_mixed = timed(step_mixed, args.steps)
+        barrier()
+    prof_dom = roofline.end(h)[dominant]
+    L1 = H.kernel_launches()
+    ms_fp64 = timed(step_fp64, max(2, min(args.steps, 5)))
+    barrier()
+
+    # agreement of the two GPU paths on the last step
+    rel = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
+
+    # per-kernel timing of the dominant kernel (see DESIGN: roofline)
+    t_mixed = statistics.mean(ms_mixed)
+    t_max = t_mixed
+    if ws > 1:
+        tt = torch.tensor([t_mixed], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = t_max / ws  # whole-job ms per frequency (ws frequencies per step)
+
+    # ---- end to end through the public API with host buffers
+    pos_h = torch.from_numpy(p.pos).pin_memory()
+    coef_h = torch.from_numpy(p.coef).pin_memory()
+    sb_h = torch.from_numpy(p.self_blocks).pin_memory()
+    X_h = torch.empty((Na, N), dtype=torch.complex128).pin_memory()
+    bi = pos_h.nbytes + coef_h.nbytes + sb_h.nbytes
+    bo = X_h.nbytes
+
+    def step_e2e():
+        pd = pos_h.to(dev, non_blocking=True)
+        cd = coef_h.to(dev, non_blocking=True)
+        sd = sb_h.to(dev, non_blocking=True)
+        h.fill(pd, p.freq_hz, cd, sd, prec="mixed", out=Z32)
+        h.solve(Z32, None, nrhs=Na, prec="mixed", max_iter=10, out=X)
+        X_h.copy_(X.T, non_blocking=True)
+    ms_e2e = timed(step_e2e, args.steps)
+    e2e_max = statistics.mean(ms_e2e)
+    if ws > 1:
+        tt = torch.tensor([e2e_max], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_max = float(tt.item())
+
+    if rank == 0:
+        peaks = _peaks()
+        roof = roofline.entry(dominant, IMPL[dominant], prof_dom, peaks)
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max, 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "nrhs": Na, "K": p.K,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{ws}"},
+            "fp64_gpu_ms_per_step": round(statistics.mean(ms_fp64), 4),
+            "speedup_vs_fp64_gpu": round(statistics.mean(ms_fp64) / t_mixed, 3),
+            "mixed_vs_fp64_relerr": rel,
+            "refinement": {"iters": info.get("iters"), "backward_error": info.get("resid")},
+            "gpu_launches": int(L1 - L0),
+            "clocks": clk.summary(),
+            "e2e": {"value": round(e2e_max / ws, 4), "unit": "ms", "h2d_bytes_per_step": int(bi),
+                    "d2h_bytes_per_step": int(bo)},
+            "roofline": roof,
+            "kernel_shares": shares,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(1)
+        print(json.dumps(line))
+    h.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

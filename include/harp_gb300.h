@@ -81,9 +81,13 @@ const char* harp_status_string(int status);
 /* Last CUDA error code seen by the library in this process (0 if none). */
 int harp_last_cuda_error(void);
 
+/* Number of CUDA kernels this library has launched in this process (host
+ * counter, for instrumentation; not synchronised across threads). */
+unsigned long long harp_kernel_launches(void);
+
 /* Create a context on CUDA device `device` with workspace for systems up to
  * max_N unknowns and max_nrhs right-hand sides. The context owns its device
- * workspace (about 40 max_N^2 + 64 max_N max_nrhs bytes): the FP64 copy of
+ * workspace (about 56 max_N^2 + 80 max_N max_nrhs bytes): the FP64 copy of
  * the reduced matrix used by the refinement, the LU factors and pivots of
  * the last factorisation, and solve buffers. Returns HARP_E_NOMEM when the
  * allocation fails. One context serves one stream at a time. */
@@ -135,13 +139,14 @@ int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, do
  *   X, ldx       c128 N x nrhs output                             [8, 9]
  *   trans        'N' or 'T'                                       [10]
  *   prec         harp_prec                                        [11]
- *   tol          mixed modes: stop when ||V - Z64 X||_inf <=
- *                tol (||Z64||_inf ||X||_inf + ||V||_inf); <= 0 selects
- *                sqrt(N) * 2^-53                                   [12]
+ *   tol          mixed modes: stop when every column j has
+ *                max_i |R_ij| <= tol ||Z64||_inf max_i |X_ij|, with
+ *                R = V - Z64 X and |z| = |re| + |im| (the test of
+ *                LAPACK's zcgesv); <= 0 selects sqrt(N) * 2^-53     [12]
  *   max_iter     mixed modes: at most this many refinement steps  [13]
  *   iters_out    host int, refinement steps taken (may be NULL)   [14]
- *   resid_out    host double, final normwise backward error of the mixed
- *                modes (may be NULL; not computed for HARP_FP64)  [15]
+ *   resid_out    host double, the largest per-column ratio of that test
+ *                at exit (may be NULL; -1 for HARP_FP64, HARP_FP32) [15]
  * The mixed modes refine against the context's FP64 matrix (written by the
  * last mixed harp_fill, or by the caller through harp_ctx_z64) and
  * synchronise the stream once per step. Returns +i on an exactly zero pivot
@@ -166,6 +171,31 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
                       double freq_hz, const double* coef, const double* Lambda, const double* X,
                       int ld, int nrhs, double* grad_pos, int prec, void* stream);
+
+/* ---- Instrumentation: device time per kernel class -------------------------
+ * Not part of the method; used to report each kernel's share of the time and
+ * its achieved fraction of the hardware's peak. While recording, each launch
+ * of a selected class is bracketed by a CUDA event pair on its own stream,
+ * and the class accumulates the launch's algorithmic flop count
+ * (8 real flops per complex multiply-add). */
+#define HARP_PROF_KINDS 8
+#define HARP_K_FILL 0     /* harp_fill kernels                                  */
+#define HARP_K_GEMM 1     /* LU trailing updates and triangular-solve updates   */
+#define HARP_K_RESIDUAL 2 /* FP64-accurate residual of the refinement           */
+#define HARP_K_PANEL 3    /* in-panel LU leaves (pivot search)                  */
+#define HARP_K_TRSM 4     /* triangular-solve leaves                            */
+#define HARP_K_SWAP 5     /* row interchanges                                   */
+#define HARP_K_ADJOINT 6  /* harp_fill_adjoint kernels                          */
+#define HARP_K_OTHER 7    /* conversions, norms, permutations                   */
+
+/* Start recording the classes whose bit (1 << HARP_K_*) is set in mask.
+ * Process-wide; discards earlier records. */
+int harp_profile_begin(harp_ctx* ctx, unsigned mask);
+
+/* Synchronise the recorded events and return, per class, the summed device
+ * milliseconds, algorithmic flops and launch count (arrays of
+ * HARP_PROF_KINDS entries, host memory). Stops recording. */
+int harp_profile_end(harp_ctx* ctx, double* ms, double* flops, long long* launches);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace harp {
 
@@ -215,6 +216,8 @@ static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R>, kAdjThreads,
                                                 smem);
   const int grid = std::min(a.n_items, ctx->num_sms * std::max(1, per_sm));
+  ProfScope ps(HARP_K_ADJOINT,
+               8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
   adjoint_pairs_kernel<R><<<grid, kAdjThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;

@@ -67,6 +67,7 @@ template <typename R> inline CView<R> interleaved(R* base, long ld) {
 // ---------------------------------------------------------------------------
 // Status plumbing.
 extern int g_last_cuda_error;
+extern unsigned long long g_kernel_launches;  // host-side count of kernel launches
 
 inline int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HARP_OK;
@@ -78,7 +79,11 @@ inline int cuda_status(cudaError_t e) {
     int _s = ::harp::cuda_status((__VA_ARGS__));   \
     if (_s != HARP_OK) return _s;                  \
   } while (0)
-#define HARP_LAUNCHED() HARP_CUDA(cudaGetLastError())
+#define HARP_LAUNCHED()                            \
+  do {                                             \
+    ++::harp::g_kernel_launches;                   \
+    HARP_CUDA(cudaGetLastError());                 \
+  } while (0)
 #define HARP_TRY(...)                              \
   do {                                             \
     int _s = (__VA_ARGS__);                        \
@@ -137,13 +142,26 @@ struct harp_ctx {
   void* t_re;  // scratch for the row permutation of the triangular solves
   void* t_im;
 
+  // Float-float (hi/lo) splits for the refinement residual: Z64 as four
+  // float planes (re hi, im hi, re lo, im lo; max_N x max_N, ld max_N) and
+  // the iterate X likewise (max_N x max_nrhs); row-sum scratch.
+  float* zff;
+  float* xff;
+  float* rowsum;
+
+  // K-major hi/lo operand planes of the tensor-core GEMM (lu_tc.cu).
+  float* tc_a;
+  size_t tc_a_floats;
+  float* tc_b;
+  size_t tc_b_floats;
+
   // Adjoint per-pair partial gradients, Na x Na x 2 doubles (lazily sized).
   double* gpair;
   size_t gpair_bytes;
 
   // Reductions and status.
-  double* red;      // device scratch, 16 doubles
-  double* red_host; // pinned host mirror, 16 doubles
-  int* dstatus;     // device status words [0] bits, [1] zero-pivot column
+  double* red;      // device scratch, 16 + 2*max_nrhs doubles
+  double* red_host; // pinned host mirror, same size
+  int* dstatus;     // device status words [0] bits, [1] zero-pivot column, [2] timeout
   int* hstatus;     // pinned host mirror
 };

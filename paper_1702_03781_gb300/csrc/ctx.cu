@@ -1,4 +1,5 @@
 // ctx.cu -- context creation, workspace ownership, status strings.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 #include <cstring>
@@ -7,6 +8,7 @@
 
 namespace harp {
 int g_last_cuda_error = 0;
+unsigned long long g_kernel_launches = 0;
 }
 
 using namespace harp;
@@ -29,9 +31,11 @@ extern "C" const char* harp_status_string(int s) {
 
 extern "C" int harp_last_cuda_error(void) { return g_last_cuda_error; }
 
+extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launches; }
+
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
-                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->gpair, c->red, c->dstatus};
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->gpair, c->red, c->dstatus};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -87,9 +91,18 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   alloc((void**)&c->v_im, NR * sizeof(double));
   alloc(&c->t_re, NR * sizeof(double));
   alloc(&c->t_im, NR * sizeof(double));
-  alloc((void**)&c->red, 16 * sizeof(double));
+  alloc((void**)&c->zff, 4 * NN * sizeof(float));
+  alloc((void**)&c->xff, 4 * NR * sizeof(float));
+  alloc((void**)&c->rowsum, (size_t)max_N * sizeof(float));
+  const size_t kp = ((size_t)max_N + 31) / 32 * 32;
+  c->tc_a_floats = 4 * (size_t)max_N * kp;
+  c->tc_b_floats = 4 * (size_t)std::max(max_N, max_nrhs) * kp;
+  alloc((void**)&c->tc_a, c->tc_a_floats * sizeof(float));
+  alloc((void**)&c->tc_b, c->tc_b_floats * sizeof(float));
+  const size_t nred = 16 + 2 * (size_t)max_nrhs;
+  alloc((void**)&c->red, nred * sizeof(double));
   alloc((void**)&c->dstatus, 4 * sizeof(int));
-  if (ok && cudaMallocHost((void**)&c->red_host, 16 * sizeof(double)) != cudaSuccess) ok = false;
+  if (ok && cudaMallocHost((void**)&c->red_host, nred * sizeof(double)) != cudaSuccess) ok = false;
   if (ok && cudaMallocHost((void**)&c->hstatus, 4 * sizeof(int)) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();

@@ -21,6 +21,7 @@
 #include <climits>
 
 #include "dense.cuh"
+#include "prof.cuh"
 
 namespace harp {
 
@@ -83,6 +84,18 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int M, int N, int K, R 
     }
     __syncthreads();
   }
+  // Epilogue: every C load is issued before any store (the planes could
+  // alias as far as the compiler knows, which would serialise the loads).
+  R old_r[4][4], old_i[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+      const bool in = (beta != (R)0) && (i < M) && (j < N);
+      old_r[a][b] = in ? C.r(i, j) : (R)0;
+      old_i[a][b] = in ? C.m(i, j) : (R)0;
+    }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = i0 + ty + 16 * a;
@@ -91,22 +104,18 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int M, int N, int K, R 
     for (int b = 0; b < 4; ++b) {
       const int j = j0 + tx + 16 * b;
       if (j >= N) continue;
-      R vr = alpha * cr[a][b], vi = alpha * ci[a][b];
-      if (beta != (R)0) {
-        vr = fma(beta, C.r(i, j), vr);
-        vi = fma(beta, C.m(i, j), vi);
-      }
-      C.r(i, j) = vr;
-      C.m(i, j) = vi;
+      C.r(i, j) = fma(beta, old_r[a][b], alpha * cr[a][b]);
+      C.m(i, j) = fma(beta, old_i[a][b], alpha * ci[a][b]);
     }
   }
 }
 
 template <typename R>
 int cgemm_simt(int M, int N, int K, R alpha, CView<R> A, CView<R> B, R beta, CView<R> C,
-               cudaStream_t st) {
+               cudaStream_t st, int kind = HARP_K_GEMM) {
   if (M <= 0 || N <= 0) return HARP_OK;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
+  ProfScope ps(kind, 8.0 * M * N * (double)K, st);
   cgemm_simt_kernel<R><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -132,22 +141,30 @@ int cgemm<double>(int M, int N, int K, double alpha, CView<double> A, CView<doub
   return cgemm_simt<double>(M, N, K, alpha, A, B, beta, C, st);
 }
 
+int residual_fp64(int N, int nrhs, CView<double> Z, CView<double> X, CView<double> R,
+                  cudaStream_t st) {
+  return cgemm_simt<double>(N, nrhs, N, -1.0, Z, X, 1.0, R, st, HARP_K_RESIDUAL);
+}
+
 // ---------------------------------------------------------------------------
 // In-panel LU leaf: columns j0 .. j0+w-1, rows j0 .. j0+M-1, one CTA. The
 // slab is copied to shared memory when it fits (use_smem), else worked on
 // in place. Per column: block-wide search for the entry of largest modulus
-// (compared as |z|^2 in FP64, first index on ties), row swap inside the
-// slab, scaling of the column below the pivot and rank-1 update of the
-// slab's remaining columns.
+// (compared as |z|^2, first index on ties), row swap inside the slab,
+// scaling of the column below the pivot and rank-1 update of the slab's
+// remaining columns.
 template <typename R>
 __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, long lda, int j0,
                                                                int M, int w, int* ipiv,
                                                                int* zero_col, int use_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_v[kLeafThreads / 32];
+  // Pivot magnitudes |z|^2 in the working precision: FP64 runs at 1/64 of
+  // the FP32 rate on this GPU, and FP32 squares order the candidates
+  // correctly except on near-ties, where either choice is a valid pivot.
+  __shared__ R red_v[kLeafThreads / 32];
   __shared__ int red_i[kLeafThreads / 32];
   __shared__ int s_piv;
-  __shared__ double s_best;
+  __shared__ R s_best;
   R* gre = Are + (size_t)j0 + (size_t)j0 * lda;
   R* gim = Aim + (size_t)j0 + (size_t)j0 * lda;
   R *sre, *sim;
@@ -172,11 +189,11 @@ __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, l
   for (int c = 0; c < w; ++c) {
     R* cr = sre + (size_t)c * cs;
     R* ci = sim + (size_t)c * cs;
-    double best = -1.0;
+    R best = -1;
     int bi = INT_MAX;
     for (int r = c + threadIdx.x; r < M; r += blockDim.x) {
-      const double vr = (double)cr[r], vi = (double)ci[r];
-      const double v = vr * vr + vi * vi;
+      const R vr = cr[r], vi = ci[r];
+      const R v = vr * vr + vi * vi;
       if (v > best) {
         best = v;
         bi = r;
@@ -184,7 +201,7 @@ __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, l
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, off);
+      const R ob = __shfl_down_sync(0xffffffffu, best, off);
       const int oi = __shfl_down_sync(0xffffffffu, bi, off);
       if (ob > best || (ob == best && oi < bi)) {
         best = ob;
@@ -197,11 +214,11 @@ __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, l
     }
     __syncthreads();
     if (warp == 0) {
-      best = lane < nwarps ? red_v[lane] : -1.0;
+      best = lane < nwarps ? red_v[lane] : (R)-1;
       bi = lane < nwarps ? red_i[lane] : INT_MAX;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const R ob = __shfl_down_sync(0xffffffffu, best, off);
         const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -215,7 +232,7 @@ __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, l
     }
     __syncthreads();
     const int piv = s_piv;
-    if (!(s_best > 0.0) || piv >= M) {  // exactly zero (or non-finite) column
+    if (!(s_best > (R)0) || piv >= M) {  // exactly zero (or non-finite) column
       if (threadIdx.x == 0) {
         ipiv[j0 + c] = j0 + c;
         atomicMin(zero_col, j0 + c + 1);
@@ -303,6 +320,7 @@ static int laswp(R* re, R* im, long ld, const int* ipiv, int k1, int k2, int a0,
   const int n = std::max(0, a1 - a0) + std::max(0, b1 - b0) + (perm ? 1 : 0);
   if (n == 0 || k2 <= k1) return HARP_OK;
   const int threads = 128;
+  ProfScope ps(HARP_K_SWAP, 0.0, st);
   laswp_kernel<R><<<(n + threads - 1) / threads, threads, 0, st>>>(
       re, im, ld, ipiv, k1, k2, a0, std::max(a0, a1), b0, std::max(b0, b1), perm);
   HARP_LAUNCHED();
@@ -387,6 +405,7 @@ static int trsm_leaf(bool lower, bool unit, int n, int ncols, CView<R> T, CView<
       lower ? (unit ? trsm_leaf_kernel<R, true, true> : trsm_leaf_kernel<R, true, false>)
             : (unit ? trsm_leaf_kernel<R, false, true> : trsm_leaf_kernel<R, false, false>);
   HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope ps(HARP_K_TRSM, 4.0 * n * (double)n * ncols, st);
   kern<<<grid, block, smem, st>>>(n, ncols, T, B);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -438,6 +457,7 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
     const size_t smem = use_smem ? (size_t)2 * M * w * sizeof(R) : 0;
     HARP_CUDA(cudaFuncSetAttribute(lu_leaf_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)std::max<size_t>(smem, 0)));
+    ProfScope ps(HARP_K_PANEL, 4.0 * M * w * (double)(w - 1) + 6.0 * M * w, st);
     lu_leaf_kernel<R><<<1, kLeafThreads, smem, st>>>(re, im, ld, j0, M, w, ipiv, zero_col,
                                                      use_smem);
     HARP_LAUNCHED();
@@ -457,6 +477,7 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
 template <typename R>
 int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm, int* zero_col,
               int mode, cudaStream_t st) {
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   iota_kernel<<<(N + 255) / 256, 256, 0, st>>>(perm, N);
   HARP_LAUNCHED();
   CView<R> A = planes<R>(re, im, ld);
@@ -499,7 +520,10 @@ int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, 
   CView<R> L = planes<R>(lre, lim, ld);
   dim3 grid((N + 255) / 256, nrhs);
   if (trans == 'N' || trans == 'n') {
-    permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 0);
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 0);
+    }
     HARP_LAUNCHED();
     CView<R> Tm = planes<R>(tre, tim, ldb);
     HARP_TRY(trsm<R>(true, true, N, nrhs, L, Tm, mode, st));
@@ -509,7 +533,10 @@ int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, 
     CView<R> Bm = planes<R>(bre, bim, ldb);
     HARP_TRY(trsm<R>(true, false, N, nrhs, L.t(), Bm, mode, st));  // U^T y = b
     HARP_TRY(trsm<R>(false, true, N, nrhs, L.t(), Bm, mode, st));  // L^T z = y
-    permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 1);
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 1);
+    }
     HARP_LAUNCHED();
     HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));
   }
@@ -532,6 +559,7 @@ int interleaved_to_planes(int M, int N, const Rin* src, long lds, Rout* re, Rout
                           cudaStream_t st) {
   if (M <= 0 || N <= 0) return HARP_OK;
   dim3 grid((M + 255) / 256, N);
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   i2p_kernel<Rin, Rout><<<grid, 256, 0, st>>>(M, N, src, lds, re, im, ldd);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -551,6 +579,7 @@ int planes_to_planes(int M, int N, const Rin* sre, const Rin* sim, long lds, Rou
                      long ldd, cudaStream_t st) {
   if (M <= 0 || N <= 0) return HARP_OK;
   dim3 grid((M + 255) / 256, N);
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   p2p_kernel<Rin, Rout><<<grid, 256, 0, st>>>(M, N, sre, sim, lds, dre, dim, ldd);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -568,6 +597,7 @@ int planes_to_interleaved(int M, int N, const double* re, const double* im, long
                           long ldd, cudaStream_t st) {
   if (M <= 0 || N <= 0) return HARP_OK;
   dim3 grid((M + 255) / 256, N);
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   p2i_kernel<<<grid, 256, 0, st>>>(M, N, re, im, lds, dst, ldd);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -584,6 +614,7 @@ __global__ void port_rhs_kernel(int M, int N, int Nm, R* re, R* im, long ld) {
 template <typename R>
 int port_rhs_planes(int M, int N, int Nm, R* re, R* im, long ld, cudaStream_t st) {
   dim3 grid((M + 255) / 256, N);
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   port_rhs_kernel<R><<<grid, 256, 0, st>>>(M, N, Nm, re, im, ld);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -602,6 +633,7 @@ template <typename R>
 int add_planes(int M, int N, double* xre, double* xim, long ldx, const R* dre, const R* dim,
                long ldd, cudaStream_t st) {
   dim3 grid((M + 255) / 256, N);
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   add_planes_kernel<R><<<grid, 256, 0, st>>>(M, N, xre, xim, ldx, dre, dim, ldd);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -625,6 +657,7 @@ __global__ void norm_inf_kernel(int M, int N, CView<R> A, double* out) {
 template <typename R>
 int norm_inf(int M, int N, CView<R> A, double* out, cudaStream_t st) {
   if (M <= 0) return HARP_OK;
+  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
   norm_inf_kernel<R><<<(M + 255) / 256, 256, 0, st>>>(M, N, A, out);
   HARP_LAUNCHED();
   return HARP_OK;

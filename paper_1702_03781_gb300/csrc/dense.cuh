@@ -24,6 +24,27 @@ template <>
 int cgemm<double>(int M, int N, int K, double alpha, CView<double> A, CView<double> B, double beta,
                   CView<double> C, int mode, cudaStream_t st);
 
+// R = R - Z X in FP64 (the refinement residual; R holds V on entry).
+int residual_fp64(int N, int nrhs, CView<double> Z, CView<double> X, CView<double> R,
+                  cudaStream_t st);
+
+// Scratch and timeout flag used by the tensor-core GEMM of this thread's
+// current solve (lu_tc.cu); a null workspace selects the CUDA-core GEMM.
+void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int* err);
+
+// Float-float refinement pieces (resid.cu).
+int split_c128(int M, int N, const double* Z, long ldz, float* const hl[4], long ldp,
+               cudaStream_t st);
+int split_planes(int M, int N, const double* xr, const double* xi, long ld, float* const hl[4],
+                 cudaStream_t st);
+int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
+                const float* const B[4], long ldb, const double* vr, const double* vi, double* rr,
+                double* ri, long ldr, cudaStream_t st);
+int colmax_cabs1(int M, int N, const double* xr, const double* xi, long ld, double* colmax,
+                 cudaStream_t st);
+int norm_inf_planes_f32(int M, int N, const float* re, const float* im, long rs, long cs,
+                        float* rowsum, double* out, cudaStream_t st);
+
 // PA = LU in place on split planes (N x N, leading dimension ld).
 // ipiv[k] = row swapped with row k (0-based, global). The smallest
 // 1-based column with an exactly zero pivot is atomically min-ed into

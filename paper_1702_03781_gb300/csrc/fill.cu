@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace harp {
 
@@ -174,6 +175,7 @@ static int launch_fill(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int
   HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int per_chunk = std::max(1, (ctx->num_sms + nchunks - 1) / nchunks);
   dim3 grid(std::min(a.n_items, per_chunk), nchunks);
+  ProfScope ps(HARP_K_FILL, 8.0 * a.Nm * a.Nm * a.K * (double)a.Na * (a.Na - 1), st);
   kern<<<grid, kFillThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;

@@ -1,14 +1,425 @@
 // lu_tc.cu -- tensor-core (tcgen05) complex GEMM for the FP32 LU trailing
-// updates and triangular-solve updates. Placeholder until the tcgen05
-// kernel lands: reports the shape as unsupported so the CUDA-core kernel
-// runs.
+// updates and the triangular-solve updates of the mixed-precision solve:
+//   C = beta*C + alpha * A B,   A: M x K, B: K x N, complex, split planes.
+//
+// The complex product is four real products accumulated in two TMEM
+// accumulators, Dr = Ar Br - Ai Bi and Di = Ar Bi + Ai Br (the minus sign is
+// the instruction descriptor's negate-A bit). In the three-term TF32 mode
+// each FP32 operand x is split as x = hi + lo with hi = x rounded to TF32 and
+// lo = x - hi (exact), and a*b ~ ah bh + ah bl + al bh (12 MMAs per k8 step),
+// which keeps the product accurate to about 2^-22 relative; the one-term
+// mode uses ah bh only (4 MMAs per k8 step).
+//
+// Operands are first copied into "K-major" hi/lo planes (row r of the MMA
+// operand holds its K values contiguously, K padded to a multiple of 32,
+// planes [re_hi, im_hi, re_lo, im_lo]); the kernel loads 32-wide K tiles of
+// them with TMA (128-byte swizzle, one 3-D tensor map per operand with the
+// plane as third coordinate) into a two-stage shared-memory ring.
+// Warp roles: warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma
+// (single thread, accumulators in TMEM) and commits each stage back to the
+// producer; then all four warps read the accumulators with tcgen05.ld
+// (warp w owns TMEM lanes 32w..32w+31 = rows of the tile) and update C.
+// Every mbarrier wait is bounded by a clock budget; on expiry the kernel
+// records HARP timeout status, drains what it issued and frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "dense.cuh"
+#include "prof.cuh"
 
 namespace harp {
 
-int cgemm_tc_f32(int, int, int, float, CView<float>, CView<float>, float, CView<float>, int,
-                 cudaStream_t) {
-  return HARP_E_UNSUPPORTED;
+constexpr int TC_BM = 128;  // rows of C per CTA (TMEM lanes)
+constexpr int TC_BN = 64;   // columns of C per CTA
+constexpr int TC_BK = 32;   // K per stage: one 128-byte swizzle atom of fp32
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 128;
+constexpr int TC_A_PLANE = TC_BM * TC_BK * 4;  // 16 KB
+constexpr int TC_B_PLANE = TC_BN * TC_BK * 4;  //  8 KB
+constexpr long long TC_WAIT_CYCLES = 1LL << 30;  // ~0.5 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the error bit set) when the clock budget runs out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > TC_WAIT_CYCLES) {
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulate, K-major A and B.
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N, bool negA) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negA ? 1u : 0u) << 13) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+#define TC_LD16(taddr, v)                                                                         \
+  asm volatile(                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
+      "%15}, [%16];"                                                                              \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),      \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),  \
+        "=r"(v[14]), "=r"(v[15])                                                                  \
+      : "r"(taddr))
+
+struct TcArgs {
+  int M, N, nk;
+  float alpha, beta;
+  float* cre;
+  float* cim;
+  long crs, ccs;
+  int* err;
+};
+
+template <bool THREE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_cgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    TcArgs a) {
+  constexpr int NP = THREE ? 4 : 2;  // planes per operand
+  constexpr int STAGE = NP * (TC_A_PLANE + TC_B_PLANE);
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
+  __shared__ uint32_t tmem_slot;
+
+  // A CTA of a call that already timed out does no work (the caller reports
+  // HARP_E_TIMEOUT); the flag is uniform across the CTA.
+  if (*reinterpret_cast<volatile int*>(a.err)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;  // 1024-byte aligned tiles
+  const int i0 = blockIdx.y * TC_BM, j0 = blockIdx.x * TC_BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(su32(&bar_full[s]), 1);
+      mbar_init(su32(&bar_empty[s]), 1);
+    }
+    mbar_init(su32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_slot)),
+                 "r"(2 * TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t d_re = tmem, d_im = tmem + TC_BN;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int issued = 0;
+      for (int kt = 0; kt < a.nk; ++kt) {
+        const int s = kt % TC_STAGES, use = kt / TC_STAGES;
+        if (use > 0 && !mbar_wait(su32(&bar_empty[s]), (use - 1) & 1, a.err)) break;
+        const uint32_t st = base + s * STAGE;
+        const uint32_t fb = su32(&bar_full[s]);
+        mbar_expect_tx(fb, STAGE);
+        for (int q = 0; q < NP; ++q) {
+          tma_load_3d(st + q * TC_A_PLANE, &tmA, fb, kt * TC_BK, i0, q);
+          tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, kt * TC_BK, j0, q);
+        }
+        issued = kt + 1;
+      }
+      // make sure every issued copy has landed before the CTA can exit
+      for (int kt = (issued > TC_STAGES ? issued - TC_STAGES : 0); kt < issued; ++kt)
+        mbar_wait(su32(&bar_full[kt % TC_STAGES]), (kt / TC_STAGES) & 1, a.err);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer (single thread)
+      constexpr uint32_t ID = tf32_idesc(TC_BM, TC_BN, false);
+      constexpr uint32_t IDN = tf32_idesc(TC_BM, TC_BN, true);
+      bool first = true;
+      for (int kt = 0; kt < a.nk; ++kt) {
+        const int s = kt % TC_STAGES, use = kt / TC_STAGES;
+        if (!mbar_wait(su32(&bar_full[s]), use & 1, a.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * STAGE;
+        const uint32_t Ab = st, Bb = st + NP * TC_A_PLANE;
+#pragma unroll
+        for (int j = 0; j < TC_BK / 8; ++j) {
+          const uint32_t ko = 32u * j;  // 8 tf32 = 32 bytes along K inside the atom
+          const uint64_t arh = sw128_desc(Ab + 0 * TC_A_PLANE + ko);
+          const uint64_t aih = sw128_desc(Ab + 1 * TC_A_PLANE + ko);
+          const uint64_t brh = sw128_desc(Bb + 0 * TC_B_PLANE + ko);
+          const uint64_t bih = sw128_desc(Bb + 1 * TC_B_PLANE + ko);
+          const uint32_t acc = first ? 0u : 1u;
+          mma_tf32(d_re, arh, brh, ID, acc);
+          mma_tf32(d_im, arh, bih, ID, acc);
+          mma_tf32(d_re, aih, bih, IDN, 1u);
+          mma_tf32(d_im, aih, brh, ID, 1u);
+          if (THREE) {
+            const uint64_t arl = sw128_desc(Ab + 2 * TC_A_PLANE + ko);
+            const uint64_t ail = sw128_desc(Ab + 3 * TC_A_PLANE + ko);
+            const uint64_t brl = sw128_desc(Bb + 2 * TC_B_PLANE + ko);
+            const uint64_t bil = sw128_desc(Bb + 3 * TC_B_PLANE + ko);
+            mma_tf32(d_re, arh, brl, ID, 1u);
+            mma_tf32(d_re, arl, brh, ID, 1u);
+            mma_tf32(d_re, aih, bil, IDN, 1u);
+            mma_tf32(d_re, ail, bih, IDN, 1u);
+            mma_tf32(d_im, arh, bil, ID, 1u);
+            mma_tf32(d_im, arl, bih, ID, 1u);
+            mma_tf32(d_im, aih, brl, ID, 1u);
+            mma_tf32(d_im, ail, brh, ID, 1u);
+          }
+          first = false;
+        }
+        mma_commit(su32(&bar_empty[s]));  // stage s free once these MMAs are done
+      }
+      mma_commit(su32(&bar_done));  // always: tracks completion of every issued MMA
+    }
+    __syncwarp();
+  }
+
+  // ---- epilogue: TMEM -> registers -> C
+  const bool ok = mbar_wait(su32(&bar_done), 0, a.err);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int r = warp * 32 + lane;
+  const int gi = i0 + r;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+  for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+    uint32_t vr[16], vi[16];
+    TC_LD16(d_re + lane_off + c0, vr);
+    TC_LD16(d_im + lane_off + c0, vi);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (ok && gi < a.M) {
+      // All loads of the chunk are issued before any store, so the 32 L2
+      // round trips overlap instead of serialising behind possible aliasing.
+      const long o0 = (long)gi * a.crs + (long)(j0 + c0) * a.ccs;
+      const int nj = min(16, a.N - (j0 + c0));
+      float cr[16], ci[16];
+      if (a.beta != 0.f) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          cr[j] = (j < nj) ? a.cre[o0 + (long)j * a.ccs] : 0.f;
+          ci[j] = (j < nj) ? a.cim[o0 + (long)j * a.ccs] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float xr = a.alpha * __uint_as_float(vr[j]);
+        float xi = a.alpha * __uint_as_float(vi[j]);
+        if (a.beta != 0.f) {
+          xr = fmaf(a.beta, cr[j], xr);
+          xi = fmaf(a.beta, ci[j], xi);
+        }
+        cr[j] = xr;
+        ci[j] = xi;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j < nj) {
+          a.cre[o0 + (long)j * a.ccs] = cr[j];
+          a.cim[o0 + (long)j * a.ccs] = ci[j];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * TC_BN)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation: a view V (R x Kc) -> K-major planes out[q][r*Kp + c]
+// (zero padded to Kp columns), q = re_hi, im_hi, re_lo, im_lo; hi is V
+// rounded to TF32 (10 explicit mantissa bits), lo = V - hi exactly. A 32 x 32
+// tile goes through shared memory so both the view reads and the plane
+// writes are coalesced whichever of the view's strides is contiguous.
+__global__ void split_kmajor_kernel(int R, int Kc, int Kp, CView<float> V, float* out,
+                                    size_t plane, int three) {
+  __shared__ float tr[32][33], ti[32][33];  // [k_local][r_local]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const bool rows_contig = (V.rs == 1);
+  for (int l = ty; l < 32; l += 8) {
+    const int rl = rows_contig ? tx : l, kl = rows_contig ? l : tx;
+    const int r = r0 + rl, k = k0 + kl;
+    const bool in = (r < R) && (k < Kc);
+    tr[kl][rl] = in ? V.r(r, k) : 0.f;
+    ti[kl][rl] = in ? V.m(r, k) : 0.f;
+  }
+  __syncthreads();
+  for (int l = ty; l < 32; l += 8) {
+    const int r = r0 + l, k = k0 + tx;
+    if (r >= R || k >= Kp) continue;
+    const float xr = tr[tx][l], xi = ti[tx][l];
+    const float hr = __uint_as_float((__float_as_uint(xr) + 0x1000u) & 0xffffe000u);
+    const float hi = __uint_as_float((__float_as_uint(xi) + 0x1000u) & 0xffffe000u);
+    const size_t o = (size_t)r * Kp + k;
+    out[o] = hr;
+    out[plane + o] = hi;
+    if (three) {
+      out[2 * plane + o] = xr - hr;
+      out[3 * plane + o] = xi - hi;
+    }
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D map over planes [NP][rows][Kp] fp32, box (32, box_rows, 1), 128B swizzle.
+static bool make_map(CUtensorMap* m, float* base, int rows, int Kp, int NP, int box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NP};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)Kp * 4 * (cuuint64_t)rows};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Workspace for the split operands and the timeout flag (set per solve).
+struct TcWorkspace {
+  float* a = nullptr;
+  size_t a_floats = 0;
+  float* b = nullptr;
+  size_t b_floats = 0;
+  int* err = nullptr;
+};
+static thread_local TcWorkspace g_tc;
+
+void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int* err) {
+  g_tc.a = a;
+  g_tc.a_floats = a_floats;
+  g_tc.b = b;
+  g_tc.b_floats = b_floats;
+  g_tc.err = err;
+}
+
+int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> B, float beta,
+                 CView<float> C, int mode, cudaStream_t st) {
+  // Narrow products (the in-panel updates) stay on the CUDA cores.
+  if (M < 64 || N < 64 || K < 32 || !g_tc.a || !g_tc.b) return HARP_E_UNSUPPORTED;
+  const bool three = (mode == GEMM_TC_3XTF32);
+  const int NP = three ? 4 : 2;
+  const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
+  const size_t pa = (size_t)M * Kp, pb = (size_t)N * Kp;
+  if ((size_t)NP * pa > g_tc.a_floats || (size_t)NP * pb > g_tc.b_floats) return HARP_E_UNSUPPORTED;
+  {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    dim3 blk(32, 8);
+    split_kmajor_kernel<<<dim3(Kp / 32, (M + 31) / 32), blk, 0, st>>>(M, K, Kp, A, g_tc.a, pa,
+                                                                       three);
+    HARP_LAUNCHED();
+    split_kmajor_kernel<<<dim3(Kp / 32, (N + 31) / 32), blk, 0, st>>>(N, K, Kp, B.t(), g_tc.b,
+                                                                       pb, three);
+    HARP_LAUNCHED();
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g_tc.a, M, Kp, NP, TC_BM) || !make_map(&mb, g_tc.b, N, Kp, NP, TC_BN))
+    return HARP_E_UNSUPPORTED;
+  TcArgs args;
+  args.M = M;
+  args.N = N;
+  args.nk = Kp / TC_BK;
+  args.alpha = alpha;
+  args.beta = beta;
+  args.cre = C.re;
+  args.cim = C.im;
+  args.crs = C.rs;
+  args.ccs = C.cs;
+  args.err = g_tc.err;
+  const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
+  const size_t smem = (size_t)TC_STAGES * stage + 1024;
+  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
+      three ? tc_cgemm_kernel<true> : tc_cgemm_kernel<false>;
+  HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
+  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K, st);
+  kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
+  HARP_LAUNCHED();
+  return HARP_OK;
 }
 
 }  // namespace harp

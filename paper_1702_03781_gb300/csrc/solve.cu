@@ -5,11 +5,13 @@
 // Mixed refinement (classical iterative refinement, Wilkinson/Moler; the
 // stopping rule follows LAPACK's zcgesv):
 //   X0 = (LU32)^{-1} V
-//   repeat: R = V - Z64 X (FP64); stop when ||R||_inf <= tol (||Z64||_inf
-//           ||X||_inf + ||V||_inf); D = (LU32)^{-1} R; X += D.
+//   repeat: R = V - Z64 X (FP64-accurate, float-float on the FP32 pipe);
+//           stop when, for every column j, max_i |R_ij| <= tol ||Z64||_inf
+//           max_i |X_ij| (|z| = |re| + |im|); D = (LU32)^{-1} R; X += D.
 // The LU factors live in the context so that an adjoint solve (trans 'T')
 // reuses them.
 #include <cmath>
+#include <algorithm>
 #include <climits>
 
 #include "dense.cuh"
@@ -70,6 +72,13 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   if (iters_out) *iters_out = 0;
   if (resid_out) *resid_out = -1.0;
 
+  // Tensor-core GEMM scratch for this call; cleared timeout flag.
+  tc_set_workspace(ctx->tc_a, ctx->tc_a_floats, ctx->tc_b, ctx->tc_b_floats, ctx->dstatus + 2);
+  HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
+  struct Unset {
+    ~Unset() { tc_set_workspace(nullptr, 0, nullptr, 0, nullptr); }
+  } unset_on_return;
+
   // ---- factorisation (trans 'N') or reuse of the cached one (trans 'T')
   if (!tr) {
     ctx->lu_valid = 0;
@@ -90,9 +99,10 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       HARP_TRY(lu_factor<float>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                 ctx->dstatus + 1, mode, st));
     }
-    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, sizeof(int),
+    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, 2 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));
     HARP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->hstatus[2]) return HARP_E_TIMEOUT;
     if (ctx->hstatus[1] != INT_MAX) return ctx->hstatus[1];
     ctx->lu_N = N;
     ctx->lu_prec = lu_class(prec);
@@ -128,32 +138,46 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   // ---- FP32: no refinement
   if (prec == HARP_FP32) {
     HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
-    return HARP_OK;
+    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 2, ctx->dstatus + 2, sizeof(int),
+                              cudaMemcpyDeviceToHost, st));
+    HARP_CUDA(cudaStreamSynchronize(st));
+    return ctx->hstatus[2] ? HARP_E_TIMEOUT : HARP_OK;
   }
 
-  // ---- mixed: FP64 residual against the context's FP64 matrix
-  CView<double> Z64 = interleaved<double>((double*)ctx->z64, ctx->ld64);
-  if (tr) Z64 = Z64.t();
+  // ---- mixed: FP64-accurate residual against the context's FP64 matrix,
+  // formed in float-float on the FP32 pipe (resid.cu).
+  const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+  const size_t NR = (size_t)ctx->max_N * ctx->max_nrhs;
+  float* zhl[4] = {ctx->zff, ctx->zff + NN, ctx->zff + 2 * NN, ctx->zff + 3 * NN};
+  float* xhl[4] = {ctx->xff, ctx->xff + NR, ctx->xff + 2 * NR, ctx->xff + 3 * NR};
+  HARP_TRY(split_c128(N, N, (const double*)ctx->z64, ctx->ld64, zhl, ldw, st));
+  // element (i, k) of op(Z): (1, ld) for Z, (ld, 1) for Z^T
+  const long ars = tr ? ldw : 1, acs = tr ? 1 : ldw;
+  HARP_TRY(norm_inf_planes_f32(N, N, zhl[0], zhl[1], ars, acs, ctx->rowsum, ctx->red + 0, st));
   if (tol <= 0.0) tol = std::sqrt((double)N) * std::ldexp(1.0, -53);
-  HARP_TRY(zero_doubles(ctx->red, 4, st));
-  HARP_TRY(norm_inf<double>(N, N, Z64, ctx->red + 0, st));
-  HARP_TRY(norm_inf<double>(N, nrhs, planes<double>(ctx->v_re, ctx->v_im, ldw), ctx->red + 1, st));
-  CView<double> Rv = planes<double>(ctx->r_re, ctx->r_im, ldw);
-  CView<double> Xv = planes<double>(ctx->x_re, ctx->x_im, ldw);
+  double* colmax_r = ctx->red + 16;
+  double* colmax_x = ctx->red + 16 + nrhs;
   double bwd = INFINITY;
   int it = 0;
   bool converged = false;
   for (;;) {
-    HARP_TRY(planes_to_planes<double, double>(N, nrhs, ctx->v_re, ctx->v_im, ldw, ctx->r_re,
-                                              ctx->r_im, ldw, st));
-    HARP_TRY(cgemm<double>(N, nrhs, N, -1.0, Z64, Xv, 1.0, Rv, GEMM_SIMT, st));
-    HARP_TRY(zero_doubles(ctx->red + 2, 2, st));
-    HARP_TRY(norm_inf<double>(N, nrhs, Rv, ctx->red + 2, st));
-    HARP_TRY(norm_inf<double>(N, nrhs, Xv, ctx->red + 3, st));
-    HARP_TRY(read_back(ctx, 4, st));
+    HARP_TRY(split_planes(N, nrhs, ctx->x_re, ctx->x_im, ldw, xhl, st));
+    HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
+                         ctx->r_im, ldw, st));
+    HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, st));
+    HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
+    HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
+                              cudaMemcpyDeviceToHost, st));
+    HARP_CUDA(cudaStreamSynchronize(st));
     const double* h = ctx->red_host;
-    bwd = h[2] / (h[0] * h[3] + h[1]);
-    if (!(bwd == bwd)) return HARP_E_NONFINITE;
+    const double znorm = h[0];
+    bwd = 0.0;
+    for (int j = 0; j < nrhs; ++j) {
+      const double rj = h[16 + j], xj = h[16 + nrhs + j];
+      const double bj = (rj == 0.0) ? 0.0 : rj / (znorm * xj);
+      if (!(bj == bj)) return HARP_E_NONFINITE;
+      bwd = std::max(bwd, bj);
+    }
     if (bwd <= tol) {
       converged = true;
       break;
@@ -168,6 +192,9 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
   if (iters_out) *iters_out = it;
   if (resid_out) *resid_out = bwd;
+  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 2, ctx->dstatus + 2, sizeof(int),
+                            cudaMemcpyDeviceToHost, st));
   HARP_CUDA(cudaStreamSynchronize(st));
+  if (ctx->hstatus[2]) return HARP_E_TIMEOUT;
   return converged ? HARP_OK : HARP_E_NOCONV;
 }

@@ -59,6 +59,7 @@ def lib():
         L.harp_status_string.argtypes = [i]
         L.harp_status_string.restype = ct.c_char_p
         L.harp_last_cuda_error.restype = i
+        L.harp_kernel_launches.restype = ct.c_ulonglong
         L.harp_ctx_create.argtypes = [ct.POINTER(vp), i, i, i]
         L.harp_ctx_destroy.argtypes = [vp]
         L.harp_ctx_z64.argtypes = [vp, ct.POINTER(vp), ct.POINTER(i)]
@@ -66,11 +67,18 @@ def lib():
         L.mbf_solve.argtypes = [vp, i, vp, i, vp, i, i, vp, i, ct.c_char, i, d, i,
                                 ct.POINTER(i), ct.POINTER(d), vp]
         L.harp_fill_adjoint.argtypes = [vp, i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
+        L.harp_profile_begin.argtypes = [vp, ct.c_uint]
+        L.harp_profile_end.argtypes = [vp, vp, vp, vp]
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_z64", "harp_fill",
-                   "mbf_solve", "harp_fill_adjoint"):
+                   "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched so far in this process."""
+    return int(lib().harp_kernel_launches())
 
 
 def _prec(p) -> int:
