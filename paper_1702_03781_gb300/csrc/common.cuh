@@ -126,6 +126,10 @@ struct harp_ctx {
   int ld_lu;
   int* ipiv;
   int* perm;  // net row permutation of the cached factorisation
+  // inverses of the 64 x 64 diagonal blocks of L then U (room for doubles),
+  // real and imaginary planes, 2 * ceil(max_N / 64) * 4096 entries each
+  void* dinv_re;
+  void* dinv_im;
   int lu_N;
   int lu_prec;  // -1 = none
   int lu_valid;
@@ -148,6 +152,7 @@ struct harp_ctx {
   float* zff;
   float* xff;
   float* rowsum;
+  double* rpart;  // split-K partials: kResidMaxSplit x 2 x max_N x max_nrhs doubles
 
   // K-major hi/lo operand planes of the tensor-core GEMM (lu_tc.cu).
   float* tc_a;

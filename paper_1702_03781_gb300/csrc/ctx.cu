@@ -35,7 +35,7 @@ extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launc
 
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
-                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->gpair, c->red, c->dstatus};
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->gpair, c->red, c->dstatus};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -81,6 +81,9 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   c->ld_lu = max_N;
   alloc((void**)&c->ipiv, (size_t)max_N * sizeof(int));
   alloc((void**)&c->perm, (size_t)max_N * sizeof(int));
+  const size_t ndinv = 2 * (((size_t)max_N + 63) / 64) * 4096;
+  alloc(&c->dinv_re, ndinv * sizeof(double));
+  alloc(&c->dinv_im, ndinv * sizeof(double));
   alloc(&c->w_re, NR * sizeof(double));
   alloc(&c->w_im, NR * sizeof(double));
   alloc((void**)&c->x_re, NR * sizeof(double));
@@ -94,6 +97,7 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   alloc((void**)&c->zff, 4 * NN * sizeof(float));
   alloc((void**)&c->xff, 4 * NR * sizeof(float));
   alloc((void**)&c->rowsum, (size_t)max_N * sizeof(float));
+  alloc((void**)&c->rpart, 2 * 8 * NR * sizeof(double));
   const size_t kp = ((size_t)max_N + 31) / 32 * 32;
   c->tc_a_floats = 4 * (size_t)max_N * kp;
   c->tc_b_floats = 4 * (size_t)std::max(max_N, max_nrhs) * kp;

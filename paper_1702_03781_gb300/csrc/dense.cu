@@ -28,6 +28,7 @@ namespace harp {
 constexpr int kNB = 64;            // outer panel width
 constexpr int kLeafMax = 8;        // widest in-panel leaf
 constexpr int kLeafThreads = 512;  // threads of the leaf kernel
+constexpr int kLeafSmem = 200 * 1024;  // shared-memory budget of the leaf
 constexpr int kTrsmLeaf = 64;      // largest triangle solved by one kernel
 constexpr int kTrsmCols = 8;       // right-hand sides per CTA in the leaf
 
@@ -147,51 +148,56 @@ int residual_fp64(int N, int nrhs, CView<double> Z, CView<double> X, CView<doubl
 }
 
 // ---------------------------------------------------------------------------
-// In-panel LU leaf: columns j0 .. j0+w-1, rows j0 .. j0+M-1, one CTA. The
-// slab is copied to shared memory when it fits (use_smem), else worked on
-// in place. Per column: block-wide search for the entry of largest modulus
-// (compared as |z|^2, first index on ties), row swap inside the slab,
-// scaling of the column below the pivot and rank-1 update of the slab's
-// remaining columns.
-template <typename R>
+// In-panel LU leaf: columns j0 .. j0+w-1, rows j0 .. j0+M-1, one CTA. With
+// SMEM the slab is copied to shared memory (loads batched into registers
+// first so they overlap), else it is worked on in place. Per column: a
+// block-wide search for the entry of largest modulus (|z|^2 in the working
+// precision, first index on ties; every thread reduces the per-warp
+// candidates itself, so one barrier suffices), the row swap inside the
+// slab, then scaling of the column below the pivot and the rank-1 update
+// of the slab's remaining columns.
+template <typename R, bool SMEM>
 __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, long lda, int j0,
                                                                int M, int w, int* ipiv,
-                                                               int* zero_col, int use_smem) {
+                                                               int* zero_col) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // Pivot magnitudes |z|^2 in the working precision: FP64 runs at 1/64 of
-  // the FP32 rate on this GPU, and FP32 squares order the candidates
-  // correctly except on near-ties, where either choice is a valid pivot.
   __shared__ R red_v[kLeafThreads / 32];
   __shared__ int red_i[kLeafThreads / 32];
-  __shared__ int s_piv;
-  __shared__ R s_best;
   R* gre = Are + (size_t)j0 + (size_t)j0 * lda;
   R* gim = Aim + (size_t)j0 + (size_t)j0 * lda;
-  R *sre, *sim;
-  long cs;
-  if (use_smem) {
-    sre = reinterpret_cast<R*>(smem_raw);
-    sim = sre + (size_t)w * M;
-    cs = M;
+  R* sre = SMEM ? reinterpret_cast<R*>(smem_raw) : gre;
+  R* sim = SMEM ? sre + (size_t)w * M : gim;
+  const long cs = SMEM ? (long)M : lda;
+  constexpr int kB = 8;  // rows per thread per batch
+  if (SMEM) {
     for (int c = 0; c < w; ++c)
-      for (int r = threadIdx.x; r < M; r += blockDim.x) {
-        sre[(size_t)c * M + r] = gre[r + (size_t)c * lda];
-        sim[(size_t)c * M + r] = gim[r + (size_t)c * lda];
+      for (int r0 = 0; r0 < M; r0 += kB * kLeafThreads) {
+        R vr[kB], vi[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const int r = r0 + threadIdx.x + u * kLeafThreads;
+          vr[u] = (r < M) ? gre[r + (size_t)c * lda] : (R)0;
+          vi[u] = (r < M) ? gim[r + (size_t)c * lda] : (R)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const int r = r0 + threadIdx.x + u * kLeafThreads;
+          if (r < M) {
+            sre[(size_t)c * M + r] = vr[u];
+            sim[(size_t)c * M + r] = vi[u];
+          }
+        }
       }
-  } else {
-    sre = gre;
-    sim = gim;
-    cs = lda;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
+  constexpr int nwarps = kLeafThreads / 32;
   for (int c = 0; c < w; ++c) {
     R* cr = sre + (size_t)c * cs;
     R* ci = sim + (size_t)c * cs;
     R best = -1;
     int bi = INT_MAX;
-    for (int r = c + threadIdx.x; r < M; r += blockDim.x) {
+    for (int r = c + threadIdx.x; r < M; r += kLeafThreads) {
       const R vr = cr[r], vi = ci[r];
       const R v = vr * vr + vi * vi;
       if (v > best) {
@@ -213,103 +219,159 @@ __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, l
       red_i[warp] = bi;
     }
     __syncthreads();
-    if (warp == 0) {
-      best = lane < nwarps ? red_v[lane] : (R)-1;
-      bi = lane < nwarps ? red_i[lane] : INT_MAX;
+    best = red_v[0];
+    bi = red_i[0];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const R ob = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        s_best = best;
-        s_piv = bi;
+    for (int q = 1; q < nwarps; ++q) {
+      const R ob = red_v[q];
+      const int oi = red_i[q];
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
       }
     }
-    __syncthreads();
-    const int piv = s_piv;
-    if (!(s_best > (R)0) || piv >= M) {  // exactly zero (or non-finite) column
+    const int piv = bi;
+    if (!(best > (R)0) || piv >= M) {  // exactly zero (or non-finite) column
       if (threadIdx.x == 0) {
         ipiv[j0 + c] = j0 + c;
         atomicMin(zero_col, j0 + c + 1);
       }
-      __syncthreads();
+      __syncthreads();  // red_v reuse
       continue;
     }
     if (threadIdx.x == 0) ipiv[j0 + c] = j0 + piv;
-    if (piv != c) {
-      for (int t = threadIdx.x; t < w; t += blockDim.x) {
-        R* xr = sre + (size_t)t * cs;
-        R* xi = sim + (size_t)t * cs;
-        const R ar = xr[c], ai = xi[c];
-        xr[c] = xr[piv];
-        xi[c] = xi[piv];
-        xr[piv] = ar;
-        xi[piv] = ai;
-      }
+    if (piv != c && threadIdx.x < w) {
+      R* xr = sre + (size_t)threadIdx.x * cs;
+      R* xi = sim + (size_t)threadIdx.x * cs;
+      const R ar = xr[c], ai = xi[c];
+      xr[c] = xr[piv];
+      xi[c] = xi[piv];
+      xr[piv] = ar;
+      xi[piv] = ai;
     }
     __syncthreads();
     const R pr = cr[c], pi = ci[c];
     const R den = pr * pr + pi * pi;
     const R ir = pr / den, ii = -pi / den;
-    for (int r = c + 1 + threadIdx.x; r < M; r += blockDim.x) {
+    R ur[kLeafMax], ui[kLeafMax];
+#pragma unroll
+    for (int cc = 0; cc < kLeafMax; ++cc) {
+      if (cc > c && cc < w) {
+        ur[cc] = sre[(size_t)cc * cs + c];
+        ui[cc] = sim[(size_t)cc * cs + c];
+      }
+    }
+    for (int r = c + 1 + threadIdx.x; r < M; r += kLeafThreads) {
       const R ar = cr[r], ai = ci[r];
       const R lr = ar * ir - ai * ii, li = ar * ii + ai * ir;
       cr[r] = lr;
       ci[r] = li;
-      for (int cc = c + 1; cc < w; ++cc) {
-        R* xr = sre + (size_t)cc * cs;
-        R* xi = sim + (size_t)cc * cs;
-        const R ur = xr[c], ui = xi[c];
-        xr[r] = fma(-lr, ur, fma(li, ui, xr[r]));
-        xi[r] = fma(-lr, ui, fma(-li, ur, xi[r]));
+#pragma unroll
+      for (int cc = 0; cc < kLeafMax; ++cc) {
+        if (cc > c && cc < w) {
+          R* xr = sre + (size_t)cc * cs;
+          R* xi = sim + (size_t)cc * cs;
+          xr[r] = fma(-lr, ur[cc], fma(li, ui[cc], xr[r]));
+          xi[r] = fma(-lr, ui[cc], fma(-li, ur[cc], xi[r]));
+        }
       }
     }
     __syncthreads();
   }
-  if (use_smem) {
+  if (SMEM) {
     for (int c = 0; c < w; ++c)
-      for (int r = threadIdx.x; r < M; r += blockDim.x) {
+      for (int r = threadIdx.x; r < M; r += kLeafThreads) {
         gre[r + (size_t)c * lda] = sre[(size_t)c * M + r];
         gim[r + (size_t)c * lda] = sim[(size_t)c * M + r];
       }
   }
 }
 
-// Apply the row swaps ipiv[k1..k2) (in order) to the columns [a0, a1) and
-// [b0, b1), one thread per column, and to perm (as one more column) when
-// perm != nullptr.
-template <typename R>
-__global__ void laswp_kernel(R* Are, R* Aim, long lda, const int* ipiv, int k1, int k2, int a0,
-                             int a1, int b0, int b1, int* perm) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// Apply the row swaps ipiv[k1..k2) (in order, k2 - k1 <= kNB) to the columns
+// [a0, a1) and [b0, b1), one thread per column, and to perm (as one more
+// column) when perm != nullptr. The rows touched (the contiguous range
+// k1..k2 and the distinct pivot rows below it) are loaded into shared
+// memory first, all loads independent; the swaps then run in shared memory
+// and the rows are written back. A pivot row met several times shares one
+// slot (its first occurrence).
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) laswp_kernel(R* Are, R* Aim, long lda, const int* ipiv,
+                                                   int k1, int k2, int a0, int a1, int b0, int b1,
+                                                   int* perm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int piv[kNB], slot[kNB], segp[kNB], tgtp[kNB];
+  const int nsw = k2 - k1;
+  R* seg_r = reinterpret_cast<R*>(smem_raw);  // [nsw][NT]
+  R* seg_i = seg_r + (size_t)nsw * NT;
+  R* tgt_r = seg_i + (size_t)nsw * NT;        // [nsw][NT], slot t for first occurrences
+  R* tgt_i = tgt_r + (size_t)nsw * NT;
+  const int tid = threadIdx.x;
+  if (tid < nsw) piv[tid] = ipiv[k1 + tid];
+  __syncthreads();
+  if (tid < nsw) {
+    const int p = piv[tid];
+    int sl = -1;
+    if (p >= k2) {
+      sl = tid;
+      for (int u = 0; u < tid; ++u)
+        if (piv[u] == p) {
+          sl = u;
+          break;
+        }
+    }
+    slot[tid] = sl;
+  }
+  __syncthreads();
   const int na = a1 - a0, nb = b1 - b0;
+  const int t = blockIdx.x * NT + tid;
   if (t < na + nb) {
     const int col = (t < na) ? a0 + t : b0 + (t - na);
     R* cr = Are + (size_t)col * lda;
     R* ci = Aim + (size_t)col * lda;
-    for (int k = k1; k < k2; ++k) {
-      const int p = ipiv[k];
-      if (p != k) {
-        const R xr = cr[k], xi = ci[k];
-        cr[k] = cr[p];
-        ci[k] = ci[p];
-        cr[p] = xr;
-        ci[p] = xi;
+#pragma unroll 8
+    for (int u = 0; u < nsw; ++u) {
+      seg_r[u * NT + tid] = cr[k1 + u];
+      seg_i[u * NT + tid] = ci[k1 + u];
+      if (slot[u] == u) {
+        tgt_r[u * NT + tid] = cr[piv[u]];
+        tgt_i[u * NT + tid] = ci[piv[u]];
+      }
+    }
+    for (int u = 0; u < nsw; ++u) {
+      const int p = piv[u];
+      if (p == k1 + u) continue;
+      R* xr = (p < k2) ? &seg_r[(p - k1) * NT + tid] : &tgt_r[slot[u] * NT + tid];
+      R* xi = (p < k2) ? &seg_i[(p - k1) * NT + tid] : &tgt_i[slot[u] * NT + tid];
+      const R sr = seg_r[u * NT + tid], si = seg_i[u * NT + tid];
+      seg_r[u * NT + tid] = *xr;
+      seg_i[u * NT + tid] = *xi;
+      *xr = sr;
+      *xi = si;
+    }
+    for (int u = 0; u < nsw; ++u) {
+      cr[k1 + u] = seg_r[u * NT + tid];
+      ci[k1 + u] = seg_i[u * NT + tid];
+      if (slot[u] == u) {
+        cr[piv[u]] = tgt_r[u * NT + tid];
+        ci[piv[u]] = tgt_i[u * NT + tid];
       }
     }
   } else if (t == na + nb && perm) {
-    for (int k = k1; k < k2; ++k) {
-      const int p = ipiv[k];
-      if (p != k) {
-        const int x = perm[k];
-        perm[k] = perm[p];
-        perm[p] = x;
-      }
+    for (int u = 0; u < nsw; ++u) {
+      segp[u] = perm[k1 + u];
+      if (slot[u] == u) tgtp[u] = perm[piv[u]];
+    }
+    for (int u = 0; u < nsw; ++u) {
+      const int p = piv[u];
+      if (p == k1 + u) continue;
+      int* x = (p < k2) ? &segp[p - k1] : &tgtp[slot[u]];
+      const int sv = segp[u];
+      segp[u] = *x;
+      *x = sv;
+    }
+    for (int u = 0; u < nsw; ++u) {
+      perm[k1 + u] = segp[u];
+      if (slot[u] == u) perm[piv[u]] = tgtp[u];
     }
   }
 }
@@ -319,9 +381,17 @@ static int laswp(R* re, R* im, long ld, const int* ipiv, int k1, int k2, int a0,
                  int b1, int* perm, cudaStream_t st) {
   const int n = std::max(0, a1 - a0) + std::max(0, b1 - b0) + (perm ? 1 : 0);
   if (n == 0 || k2 <= k1) return HARP_OK;
-  const int threads = 128;
+  if (k2 - k1 > kNB) return HARP_E_UNSUPPORTED;
+  constexpr int NT = (sizeof(R) == 4) ? 128 : 64;
+  const size_t smem = (size_t)4 * (k2 - k1) * NT * sizeof(R);
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    HARP_CUDA(cudaFuncSetAttribute(laswp_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)4 * kNB * NT * sizeof(R))));
+    attr_set = true;
+  }
   ProfScope ps(HARP_K_SWAP, 0.0, st);
-  laswp_kernel<R><<<(n + threads - 1) / threads, threads, 0, st>>>(
+  laswp_kernel<R, NT><<<(n + NT - 1) / NT, NT, smem, st>>>(
       re, im, ld, ipiv, k1, k2, a0, std::max(a0, a1), b0, std::max(b0, b1), perm);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -338,7 +408,18 @@ __global__ void iota_kernel(int* p, int n) {
 // kTrsmCols right-hand sides per CTA. One barrier per eliminated row.
 template <typename R, bool LOWER, bool UNIT>
 __global__ void __launch_bounds__(kTrsmLeaf* kTrsmCols) trsm_leaf_kernel(int n, int ncols,
-                                                                          CView<R> T, CView<R> B) {
+                                                                          CView<R> T, CView<R> B,
+                                                                          int batch_n, long t_step,
+                                                                          long b_step) {
+  // blockIdx.y selects a problem of a batch: the triangle and the right-hand
+  // sides move by t_step / b_step elements, the last one may be smaller.
+  if (blockIdx.y > 0) {
+    T.re += t_step * blockIdx.y;
+    T.im += t_step * blockIdx.y;
+    B.re += b_step * blockIdx.y;
+    B.im += b_step * blockIdx.y;
+  }
+  n = min(n, batch_n - (int)blockIdx.y * n);
   // Dynamic shared memory (the FP64 tiles exceed the static 48 KB limit).
   extern __shared__ __align__(16) unsigned char smem_raw[];
   typedef R TRow[kTrsmLeaf + 1];
@@ -401,12 +482,12 @@ static int trsm_leaf(bool lower, bool unit, int n, int ncols, CView<R> T, CView<
   dim3 block(kTrsmLeaf, kTrsmCols);
   dim3 grid((ncols + kTrsmCols - 1) / kTrsmCols);
   const size_t smem = sizeof(R) * (2 * kTrsmLeaf * (kTrsmLeaf + 1) + 4 * kTrsmLeaf * kTrsmCols);
-  void (*kern)(int, int, CView<R>, CView<R>) =
+  void (*kern)(int, int, CView<R>, CView<R>, int, long, long) =
       lower ? (unit ? trsm_leaf_kernel<R, true, true> : trsm_leaf_kernel<R, true, false>)
             : (unit ? trsm_leaf_kernel<R, false, true> : trsm_leaf_kernel<R, false, false>);
   HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope ps(HARP_K_TRSM, 4.0 * n * (double)n * ncols, st);
-  kern<<<grid, block, smem, st>>>(n, ncols, T, B);
+  kern<<<grid, block, smem, st>>>(n, ncols, T, B, n, 0, 0);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -434,10 +515,134 @@ static int trsm(bool lower, bool unit, int n, int ncols, CView<R> T, CView<R> B,
 }
 
 // ---------------------------------------------------------------------------
+// Inverses of the 64 x 64 diagonal blocks of the factors, for the solves of
+// the refinement (the factors are reused by every solve of a call, so a
+// triangular leaf becomes one small parallel product). Block b of a triangle
+// is inverted by solving T_bb X = I with the leaf kernel (batched over
+// blocks); the last block may be smaller. The inverse of a leading
+// principal block of a triangular matrix is the leading block of its
+// inverse, which is what the 64-aligned recursion below uses.
+template <typename R>
+__global__ void identity_blocks_kernel(R* re, R* im, int nblk) {
+  const int b = blockIdx.y;
+  for (int e = threadIdx.x; e < kTrsmLeaf * kTrsmLeaf; e += blockDim.x) {
+    const int i = e % kTrsmLeaf, j = e / kTrsmLeaf;
+    re[(size_t)b * kTrsmLeaf * kTrsmLeaf + e] = (i == j) ? (R)1 : (R)0;
+    im[(size_t)b * kTrsmLeaf * kTrsmLeaf + e] = (R)0;
+  }
+}
+
+template <typename R>
+int diag_inverses(int N, CView<R> A, R* lre, R* lim, R* ure, R* uim, cudaStream_t st) {
+  const int nblk = (N + kTrsmLeaf - 1) / kTrsmLeaf;
+  const long bs = (long)kTrsmLeaf * kTrsmLeaf;
+  {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    identity_blocks_kernel<R><<<dim3(1, nblk), 256, 0, st>>>(lre, lim, nblk);
+    HARP_LAUNCHED();
+    identity_blocks_kernel<R><<<dim3(1, nblk), 256, 0, st>>>(ure, uim, nblk);
+    HARP_LAUNCHED();
+  }
+  dim3 block(kTrsmLeaf, kTrsmCols);
+  dim3 grid(kTrsmLeaf / kTrsmCols, nblk);
+  const size_t smem = sizeof(R) * (2 * kTrsmLeaf * (kTrsmLeaf + 1) + 4 * kTrsmLeaf * kTrsmCols);
+  const long tstep = (long)kTrsmLeaf * (A.rs + A.cs);
+  HARP_CUDA(cudaFuncSetAttribute(trsm_leaf_kernel<R, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HARP_CUDA(cudaFuncSetAttribute(trsm_leaf_kernel<R, false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope ps(HARP_K_TRSM, 8.0 * kTrsmLeaf * (double)kTrsmLeaf * kTrsmLeaf * nblk, st);
+  trsm_leaf_kernel<R, true, true><<<grid, block, smem, st>>>(
+      kTrsmLeaf, kTrsmLeaf, A, planes<R>(lre, lim, kTrsmLeaf), N, tstep, bs);
+  HARP_LAUNCHED();
+  trsm_leaf_kernel<R, false, false><<<grid, block, smem, st>>>(
+      kTrsmLeaf, kTrsmLeaf, A, planes<R>(ure, uim, kTrsmLeaf), N, tstep, bs);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// B <- D B for an n x n (n <= 64) block D (any view) and B n x ncols, in
+// place: the block and kTrsmCols columns of B are staged in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(kTrsmLeaf* kTrsmCols) leaf_inv_kernel(int n, int ncols,
+                                                                         CView<R> D, CView<R> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typedef R TRow[kTrsmLeaf + 1];
+  typedef R BRow[kTrsmCols];
+  TRow* Dr = reinterpret_cast<TRow*>(smem_raw);
+  TRow* Di = Dr + kTrsmLeaf;
+  BRow* Br = reinterpret_cast<BRow*>(Di + kTrsmLeaf);
+  BRow* Bi = Br + kTrsmLeaf;
+  const int i = threadIdx.x, c = threadIdx.y;
+  const int col = blockIdx.x * kTrsmCols + c;
+  const int tid = threadIdx.y * kTrsmLeaf + threadIdx.x;
+  for (int e = tid; e < n * n; e += kTrsmLeaf * kTrsmCols) {
+    const int r = e % n, k = e / n;
+    Dr[r][k] = D.r(r, k);
+    Di[r][k] = D.m(r, k);
+  }
+  const bool act = (i < n) && (col < ncols);
+  Br[i][c] = act ? B.r(i, col) : (R)0;
+  Bi[i][c] = act ? B.m(i, col) : (R)0;
+  __syncthreads();
+  R xr = 0, xi = 0;
+  for (int k = 0; k < n; ++k) {
+    const R dr = Dr[i][k], di = Di[i][k], br = Br[k][c], bi = Bi[k][c];
+    xr = fma(dr, br, fma(-di, bi, xr));
+    xi = fma(dr, bi, fma(di, br, xi));
+  }
+  if (act) {
+    B.r(i, col) = xr;
+    B.m(i, col) = xi;
+  }
+}
+
+// T X = B for the effective triangle T of a solve (rows row0.. of the whole
+// system), with the inverses of its 64-blocks (block b at dre/dim + b*4096,
+// column-major 64 x 64; transposed when dtrans). Splits at multiples of 64
+// so every leaf is a leading part of one block.
+template <typename R>
+static int trsm_inv(bool lower, int n, int ncols, CView<R> T, CView<R> B, int row0,
+                    const R* dre, const R* dim, bool dtrans, int mode, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return HARP_OK;
+  if (n <= kTrsmLeaf) {
+    const long off = (long)(row0 / kTrsmLeaf) * kTrsmLeaf * kTrsmLeaf;
+    CView<R> D = planes<R>(const_cast<R*>(dre) + off, const_cast<R*>(dim) + off, kTrsmLeaf);
+    if (dtrans) D = D.t();
+    dim3 block(kTrsmLeaf, kTrsmCols);
+    dim3 grid((ncols + kTrsmCols - 1) / kTrsmCols);
+    const size_t smem = sizeof(R) * (2 * kTrsmLeaf * (kTrsmLeaf + 1) + 2 * kTrsmLeaf * kTrsmCols);
+    static bool attr_set = false;
+    if (!attr_set) {
+      HARP_CUDA(cudaFuncSetAttribute(leaf_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+      attr_set = true;
+    }
+    ProfScope ps(HARP_K_TRSM, 8.0 * n * (double)n * ncols, st);
+    leaf_inv_kernel<R><<<grid, block, smem, st>>>(n, ncols, D, B);
+    HARP_LAUNCHED();
+    return HARP_OK;
+  }
+  const int n1 = ((n / 2) + kTrsmLeaf - 1) / kTrsmLeaf * kTrsmLeaf;
+  const int n2 = n - n1;
+  CView<R> B1 = B, B2 = B.sub(n1, 0);
+  if (lower) {
+    HARP_TRY(trsm_inv<R>(true, n1, ncols, T, B1, row0, dre, dim, dtrans, mode, st));
+    HARP_TRY(cgemm<R>(n2, ncols, n1, (R)-1, T.sub(n1, 0), B1, (R)1, B2, mode, st));
+    HARP_TRY(trsm_inv<R>(true, n2, ncols, T.sub(n1, n1), B2, row0 + n1, dre, dim, dtrans, mode, st));
+  } else {
+    HARP_TRY(trsm_inv<R>(false, n2, ncols, T.sub(n1, n1), B2, row0 + n1, dre, dim, dtrans, mode, st));
+    HARP_TRY(cgemm<R>(n1, ncols, n2, (R)-1, T.sub(0, n1), B2, (R)1, B1, mode, st));
+    HARP_TRY(trsm_inv<R>(false, n1, ncols, T, B1, row0, dre, dim, dtrans, mode, st));
+  }
+  return HARP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // LU driver.
 template <typename R>
 static int leaf_width(const harp_ctx* ctx, int M, int want, int* use_smem) {
-  const size_t budget = std::min<size_t>(ctx->smem_optin, 200 * 1024);
+  const size_t budget = std::min<size_t>(ctx->smem_optin, kLeafSmem);
   for (int w = std::min(want, kLeafMax); w >= 1; w >>= 1)
     if ((size_t)2 * M * w * sizeof(R) <= budget) {
       *use_smem = 1;
@@ -454,12 +659,19 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
   int use_smem = 0;
   const int lw = leaf_width<R>(ctx, M, w, &use_smem);
   if (w <= lw) {
-    const size_t smem = use_smem ? (size_t)2 * M * w * sizeof(R) : 0;
-    HARP_CUDA(cudaFuncSetAttribute(lu_leaf_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)std::max<size_t>(smem, 0)));
     ProfScope ps(HARP_K_PANEL, 4.0 * M * w * (double)(w - 1) + 6.0 * M * w, st);
-    lu_leaf_kernel<R><<<1, kLeafThreads, smem, st>>>(re, im, ld, j0, M, w, ipiv, zero_col,
-                                                     use_smem);
+    if (use_smem) {
+      static bool attr_set = false;  // per instantiation
+      if (!attr_set) {
+        HARP_CUDA(cudaFuncSetAttribute(lu_leaf_kernel<R, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kLeafSmem));
+        attr_set = true;
+      }
+      const size_t smem = (size_t)2 * M * w * sizeof(R);
+      lu_leaf_kernel<R, true><<<1, kLeafThreads, smem, st>>>(re, im, ld, j0, M, w, ipiv, zero_col);
+    } else {
+      lu_leaf_kernel<R, false><<<1, kLeafThreads, 0, st>>>(re, im, ld, j0, M, w, ipiv, zero_col);
+    }
     HARP_LAUNCHED();
     return HARP_OK;
   }
@@ -516,28 +728,35 @@ __global__ void permute_rows_kernel(int N, int nrhs, const int* perm, const R* s
 
 template <typename R>
 int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, R* bim, long ldb,
-             R* tre, R* tim, char trans, int mode, cudaStream_t st) {
+             R* tre, R* tim, char trans, const R* dinv_re, const R* dinv_im, int mode,
+             cudaStream_t st) {
   CView<R> L = planes<R>(lre, lim, ld);
+  const long nblk = (N + kTrsmLeaf - 1) / kTrsmLeaf;
+  const R* linv_r = dinv_re;
+  const R* linv_i = dinv_im;
+  const R* uinv_r = dinv_re + nblk * kTrsmLeaf * kTrsmLeaf;
+  const R* uinv_i = dinv_im + nblk * kTrsmLeaf * kTrsmLeaf;
   dim3 grid((N + 255) / 256, nrhs);
   if (trans == 'N' || trans == 'n') {
     {
       ProfScope ps(HARP_K_OTHER, 0.0, st);
       permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 0);
+      HARP_LAUNCHED();
     }
-    HARP_LAUNCHED();
     CView<R> Tm = planes<R>(tre, tim, ldb);
-    HARP_TRY(trsm<R>(true, true, N, nrhs, L, Tm, mode, st));
-    HARP_TRY(trsm<R>(false, false, N, nrhs, L, Tm, mode, st));
+    HARP_TRY(trsm_inv<R>(true, N, nrhs, L, Tm, 0, linv_r, linv_i, false, mode, st));
+    HARP_TRY(trsm_inv<R>(false, N, nrhs, L, Tm, 0, uinv_r, uinv_i, false, mode, st));
     HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));
   } else {
     CView<R> Bm = planes<R>(bre, bim, ldb);
-    HARP_TRY(trsm<R>(true, false, N, nrhs, L.t(), Bm, mode, st));  // U^T y = b
-    HARP_TRY(trsm<R>(false, true, N, nrhs, L.t(), Bm, mode, st));  // L^T z = y
+    // U^T y = b (lower), then L^T z = y (upper): inverses are the transposes
+    HARP_TRY(trsm_inv<R>(true, N, nrhs, L.t(), Bm, 0, uinv_r, uinv_i, true, mode, st));
+    HARP_TRY(trsm_inv<R>(false, N, nrhs, L.t(), Bm, 0, linv_r, linv_i, true, mode, st));
     {
       ProfScope ps(HARP_K_OTHER, 0.0, st);
       permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 1);
+      HARP_LAUNCHED();
     }
-    HARP_LAUNCHED();
     HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));
   }
   return HARP_OK;
@@ -675,9 +894,13 @@ template int lu_factor<float>(harp_ctx*, int, float*, float*, long, int*, int*, 
 template int lu_factor<double>(harp_ctx*, int, double*, double*, long, int*, int*, int*, int,
                                cudaStream_t);
 template int lu_solve<float>(int, int, float*, float*, long, const int*, float*, float*, long,
-                             float*, float*, char, int, cudaStream_t);
+                             float*, float*, char, const float*, const float*, int, cudaStream_t);
 template int lu_solve<double>(int, int, double*, double*, long, const int*, double*, double*, long,
-                              double*, double*, char, int, cudaStream_t);
+                              double*, double*, char, const double*, const double*, int,
+                              cudaStream_t);
+template int diag_inverses<float>(int, CView<float>, float*, float*, float*, float*, cudaStream_t);
+template int diag_inverses<double>(int, CView<double>, double*, double*, double*, double*,
+                                   cudaStream_t);
 template int interleaved_to_planes<float, float>(int, int, const float*, long, float*, float*, long,
                                                  cudaStream_t);
 template int interleaved_to_planes<double, double>(int, int, const double*, long, double*, double*,

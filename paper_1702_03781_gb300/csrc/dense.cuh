@@ -37,9 +37,11 @@ int split_c128(int M, int N, const double* Z, long ldz, float* const hl[4], long
                cudaStream_t st);
 int split_planes(int M, int N, const double* xr, const double* xi, long ld, float* const hl[4],
                  cudaStream_t st);
+// pr/pi: scratch for up to max_split FP64 partials of ldr * nrhs entries.
 int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
                 const float* const B[4], long ldb, const double* vr, const double* vi, double* rr,
-                double* ri, long ldr, cudaStream_t st);
+                double* ri, long ldr, double* pr, double* pi, int max_split, int num_sms,
+                cudaStream_t st);
 int colmax_cabs1(int M, int N, const double* xr, const double* xi, long ld, double* colmax,
                  cudaStream_t st);
 int norm_inf_planes_f32(int M, int N, const float* re, const float* im, long rs, long cs,
@@ -54,12 +56,20 @@ template <typename R>
 int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm, int* zero_col,
               int mode, cudaStream_t st);
 
-// Solve op(A) X = B with the factors of lu_factor; B (N x nrhs split
+// Inverses of the 64 x 64 diagonal blocks of L (unit lower) and U (upper)
+// of a factorisation held in A (N x N): block b of each at b*4096 elements
+// (column-major 64 x 64) of the given planes.
+template <typename R>
+int diag_inverses(int N, CView<R> A, R* lre, R* lim, R* ure, R* uim, cudaStream_t st);
+
+// Solve op(A) X = B with the factors of lu_factor and their diagonal-block
+// inverses (dinv planes: the L blocks, then the U blocks); B (N x nrhs split
 // planes, leading dimension ldb) is overwritten. tmp has room for N x nrhs
 // (leading dimension ldb) of each plane.
 template <typename R>
 int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, R* bim, long ldb,
-             R* tre, R* tim, char trans, int mode, cudaStream_t st);
+             R* tre, R* tim, char trans, const R* dinv_re, const R* dinv_im, int mode,
+             cudaStream_t st);
 
 // Elementwise conversions between interleaved complex storage and planes.
 template <typename Rin, typename Rout>

@@ -18,6 +18,7 @@
 // (LAPACK zcgesv style: per column max |r|, max |x| with |z| = |re| + |im|,
 // and the matrix infinity norm of Z from its hi part).
 #include <algorithm>
+#include <cmath>
 
 #include "dense.cuh"
 #include "prof.cuh"
@@ -58,12 +59,15 @@ __device__ __forceinline__ void fff_mac(float& S, float& s1, float& s2, float ah
 
 // R[i, c] = V[i, c] - sum_k A[i, k] X[k, c]; A as 4 float planes (hi/lo of
 // re/im, element (i,k) at i*ars + k*acs), X as 4 float planes (ld ldx).
+// With split-K (gridDim.z > 1) each z-slice sums its own K range and writes
+// its FP64 partial to P[z] (no V); resid_combine_kernel then forms V - sum.
 __global__ void __launch_bounds__(256) resid_ff_kernel(
     int N, int nrhs, const float* __restrict__ Ahr, const float* __restrict__ Ahi,
     const float* __restrict__ Alr, const float* __restrict__ Ali, long ars, long acs,
     const float* __restrict__ Bhr, const float* __restrict__ Bhi, const float* __restrict__ Blr,
     const float* __restrict__ Bli, long ldb, const double* __restrict__ Vr,
-    const double* __restrict__ Vi, double* __restrict__ Rr, double* __restrict__ Ri, long ldr) {
+    const double* __restrict__ Vi, double* __restrict__ Rr, double* __restrict__ Ri, long ldr,
+    int kchunk, double* __restrict__ Pr, double* __restrict__ Pi, long pstride) {
   __shared__ __align__(16) float As[4][kRBK][kRBM];
   __shared__ __align__(16) float Bs[4][kRBK][kRBN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -77,7 +81,8 @@ __global__ void __launch_bounds__(256) resid_ff_kernel(
     for (int b = 0; b < 2; ++b) Sr[a][b] = s1r[a][b] = s2r[a][b] = Si[a][b] = s1i[a][b] = s2i[a][b] = 0.f;
   const float* Ap[4] = {Ahr, Ahi, Alr, Ali};
   const float* Bp[4] = {Bhr, Bhi, Blr, Bli};
-  for (int k0 = 0; k0 < N; k0 += kRBK) {
+  const int kbeg = blockIdx.z * kchunk, kend = min(N, kbeg + kchunk);
+  for (int k0 = kbeg; k0 < kend; k0 += kRBK) {
     // A tile: kRBM x kRBK per plane (1024 elements, 4 per thread per plane)
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(256) resid_ff_kernel(
       // a transposed view)
       const int i = (acs == 1) ? e / kRBK : e % kRBM;
       const int kk = (acs == 1) ? e % kRBK : e / kRBM;
-      const bool in = (i0 + i < N) && (k0 + kk < N);
+      const bool in = (i0 + i < N) && (k0 + kk < kend);
       const long off = (long)(i0 + i) * ars + (long)(k0 + kk) * acs;
 #pragma unroll
       for (int q = 0; q < 4; ++q) As[q][kk][i] = in ? Ap[q][off] : 0.f;
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(256) resid_ff_kernel(
     for (int l = 0; l < 2; ++l) {
       const int e = threadIdx.x + 256 * l;
       const int kk = e % kRBK, j = e / kRBK;
-      const bool in = (k0 + kk < N) && (j0 + j < nrhs);
+      const bool in = (k0 + kk < kend) && (j0 + j < nrhs);
       const long off = (long)(k0 + kk) + (long)(j0 + j) * ldb;
 #pragma unroll
       for (int q = 0; q < 4; ++q) Bs[q][kk][j] = in ? Bp[q][off] : 0.f;
@@ -140,8 +145,13 @@ __global__ void __launch_bounds__(256) resid_ff_kernel(
       const long o = (long)i + (long)j * ldr;
       const double dr = (double)Sr[a][b] + ((double)s1r[a][b] + (double)s2r[a][b]);
       const double di = (double)Si[a][b] + ((double)s1i[a][b] + (double)s2i[a][b]);
-      Rr[o] = Vr[o] - dr;
-      Ri[o] = Vi[o] - di;
+      if (gridDim.z == 1) {
+        Rr[o] = Vr[o] - dr;
+        Ri[o] = Vi[o] - di;
+      } else {
+        Pr[blockIdx.z * pstride + o] = dr;
+        Pi[blockIdx.z * pstride + o] = di;
+      }
     }
   }
 }
@@ -248,14 +258,60 @@ int split_planes(int M, int N, const double* xr, const double* xi, long ld, floa
   return HARP_OK;
 }
 
+// R = V - sum_z P[z], the slices added in a fixed order in FP64.
+__global__ void resid_combine_kernel(int N, int nrhs, int nz, const double* __restrict__ Pr,
+                                     const double* __restrict__ Pi, long pstride,
+                                     const double* __restrict__ Vr, const double* __restrict__ Vi,
+                                     double* __restrict__ Rr, double* __restrict__ Ri, long ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= N) return;
+  const long o = (long)i + (long)j * ld;
+  double sr = 0.0, si = 0.0;
+  for (int z = 0; z < nz; ++z) {
+    sr += Pr[z * pstride + o];
+    si += Pi[z * pstride + o];
+  }
+  Rr[o] = Vr[o] - sr;
+  Ri[o] = Vi[o] - si;
+}
+
 int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
                 const float* const B[4], long ldb, const double* vr, const double* vi, double* rr,
-                double* ri, long ldr, cudaStream_t st) {
-  dim3 grid((nrhs + kRBN - 1) / kRBN, (N + kRBM - 1) / kRBM);
-  ProfScope ps(HARP_K_RESIDUAL, 8.0 * N * (double)N * nrhs, st);
-  resid_ff_kernel<<<grid, 256, 0, st>>>(N, nrhs, A[0], A[1], A[2], A[3], ars, acs, B[0], B[1],
-                                        B[2], B[3], ldb, vr, vi, rr, ri, ldr);
-  HARP_LAUNCHED();
+                double* ri, long ldr, double* pr, double* pi, int max_split, int num_sms,
+                cudaStream_t st) {
+  const int tiles = ((nrhs + kRBN - 1) / kRBN) * ((N + kRBM - 1) / kRBM);
+  // split K so that the CTAs (two resident per SM) fill whole waves
+  const double slots = 2.0 * num_sms;
+  int ks = 1;
+  double best = 0.0;
+  for (int k = 1; k <= max_split; ++k) {
+    if ((long)k * kRBK > N) break;
+    const double waves = tiles * k / slots;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best + 0.02) {
+      best = eff;
+      ks = k;
+    }
+  }
+  int kchunk = (N + ks - 1) / ks;
+  kchunk = (kchunk + kRBK - 1) / kRBK * kRBK;
+  ks = (N + kchunk - 1) / kchunk;
+  dim3 grid((nrhs + kRBN - 1) / kRBN, (N + kRBM - 1) / kRBM, ks);
+  const long pstride = (long)ldr * nrhs;
+  {
+    ProfScope ps(HARP_K_RESIDUAL, 8.0 * N * (double)N * nrhs, st);
+    resid_ff_kernel<<<grid, 256, 0, st>>>(N, nrhs, A[0], A[1], A[2], A[3], ars, acs, B[0], B[1],
+                                          B[2], B[3], ldb, vr, vi, rr, ri, ldr, kchunk, pr, pi,
+                                          pstride);
+    HARP_LAUNCHED();
+  }
+  if (ks > 1) {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    resid_combine_kernel<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(N, nrhs, ks, pr, pi, pstride,
+                                                                      vr, vi, rr, ri, ldr);
+    HARP_LAUNCHED();
+  }
   return HARP_OK;
 }
 

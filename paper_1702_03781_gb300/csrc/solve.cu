@@ -91,6 +91,11 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
                                                      ctx->ld_lu, st));
       HARP_TRY(lu_factor<double>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                  ctx->dstatus + 1, mode, st));
+      const size_t nb = (size_t)((N + 63) / 64) * 4096;
+      double* dr = (double*)ctx->dinv_re;
+      double* di = (double*)ctx->dinv_im;
+      HARP_TRY(diag_inverses<double>(N, planes<double>(re, im, ctx->ld_lu), dr, di, dr + nb,
+                                     di + nb, st));
     } else {
       float* re = (float*)ctx->lu_re;
       float* im = (float*)ctx->lu_im;
@@ -98,6 +103,11 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
                                                    st));
       HARP_TRY(lu_factor<float>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                 ctx->dstatus + 1, mode, st));
+      const size_t nb = (size_t)((N + 63) / 64) * 4096;
+      float* dr = (float*)ctx->dinv_re;
+      float* di = (float*)ctx->dinv_im;
+      HARP_TRY(diag_inverses<float>(N, planes<float>(re, im, ctx->ld_lu), dr, di, dr + nb, di + nb,
+                                    st));
     }
     HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, 2 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));
@@ -118,7 +128,8 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     HARP_TRY(load_rhs(ctx, N, nrhs, V, ldv, wre, wim, st));
     HARP_TRY(lu_solve<double>(N, nrhs, (double*)ctx->lu_re, (double*)ctx->lu_im, ctx->ld_lu,
                               ctx->perm, wre, wim, ldw, (double*)ctx->t_re, (double*)ctx->t_im,
-                              tr ? 'T' : 'N', mode, st));
+                              tr ? 'T' : 'N', (const double*)ctx->dinv_re,
+                              (const double*)ctx->dinv_im, mode, st));
     HARP_TRY(planes_to_interleaved(N, nrhs, wre, wim, ldw, X, ldx, st));
     return HARP_OK;
   }
@@ -129,10 +140,12 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   float* wim = (float*)ctx->w_im;
   float* tre = (float*)ctx->t_re;
   float* tim = (float*)ctx->t_im;
+  const float* dinv_r = (const float*)ctx->dinv_re;
+  const float* dinv_i = (const float*)ctx->dinv_im;
   HARP_TRY(load_rhs(ctx, N, nrhs, V, ldv, ctx->v_re, ctx->v_im, st));
   HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->v_re, ctx->v_im, ldw, wre, wim, ldw, st));
   HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
-                           tr ? 'T' : 'N', mode, st));
+                           tr ? 'T' : 'N', dinv_r, dinv_i, mode, st));
   HARP_TRY(planes_to_planes<float, double>(N, nrhs, wre, wim, ldw, ctx->x_re, ctx->x_im, ldw, st));
 
   // ---- FP32: no refinement
@@ -163,7 +176,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   for (;;) {
     HARP_TRY(split_planes(N, nrhs, ctx->x_re, ctx->x_im, ldw, xhl, st));
     HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
-                         ctx->r_im, ldw, st));
+                         ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st));
     HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, st));
     HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
     HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
@@ -185,7 +198,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     if (it >= max_iter) break;
     HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->r_re, ctx->r_im, ldw, wre, wim, ldw, st));
     HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
-                             tr ? 'T' : 'N', mode, st));
+                             tr ? 'T' : 'N', dinv_r, dinv_i, mode, st));
     HARP_TRY(add_planes<float>(N, nrhs, ctx->x_re, ctx->x_im, ldw, wre, wim, ldw, st));
     ++it;
   }
