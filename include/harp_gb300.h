@@ -172,6 +172,26 @@ int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double*
                       double freq_hz, const double* coef, const double* Lambda, const double* X,
                       int ld, int nrhs, double* grad_pos, int prec, void* stream);
 
+/* Allocation-free variant of harp_fill_adjoint (no counterpart in the paper:
+ * it exists for callers that cannot allocate device memory, for instance an
+ * application whose allocator owns all device memory or that runs under a
+ * fixed memory budget). It takes no context and calls no allocating routine:
+ * its per-pair scratch is a fixed device array inside this library, sized
+ * for at most HARP_NOALLOC_MAX_NA antennas (HARP_NOALLOC_MAX_NA^2 * 2
+ * doubles, 4 MiB, held on every GPU that loads the library until the
+ * process exits). Arguments 1..13 are those of harp_fill_adjoint without the
+ * context; it works on the current CUDA device. Returns HARP_E_UNSUPPORTED
+ * when Na > HARP_NOALLOC_MAX_NA.
+ * The first call on a device looks up that device's address of the array
+ * (a runtime query, with the device current); make that first call before
+ * any stream capture. All calls share the one array: each call clears what
+ * it uses, and calls whose work overlaps on the GPU (different streams)
+ * race on it, so serialise them. */
+#define HARP_NOALLOC_MAX_NA 512
+int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
+                              const double* coef, const double* Lambda, const double* X, int ld,
+                              int nrhs, double* grad_pos, int prec, void* stream);
+
 /* ---- Instrumentation: device time per kernel class -------------------------
  * Not part of the method; used to report each kernel's share of the time and
  * its achieved fraction of the hardware's peak. While recording, each launch

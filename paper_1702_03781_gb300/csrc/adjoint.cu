@@ -17,6 +17,7 @@
 // antenna n staged in shared memory in chunks), then H (contraction over
 // (T, S) with the coefficient table), then the per-pair derivative sums.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -281,6 +282,129 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
   else
     HARP_TRY(launch_adjoint<float>(ctx, a, st));
   adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, ctx->gpair, grad_pos);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of harp_fill_adjoint.
+//
+// Some callers cannot call cudaMalloc at all: an application whose device
+// memory is owned by its own allocator (or was reserved in full at start-up)
+// or code with a fixed memory budget that must not grow. For them the
+// per-pair gradient buffer of the adjoint lives in a fixed device array
+// declared here, so the call allocates nothing; the caller still passes
+// every input and the output.
+//
+// The array is file-scope device memory: every GPU that loads this library
+// holds it (HARP_NOALLOC_MAX_NA^2 * 2 doubles = 4 MiB) until the process
+// exits. Host code cannot use the array's name as a device address, so on
+// the first call on each device the library asks the runtime for that
+// device's address of the array (with the device current) and keeps it.
+// All calls share the one array and it keeps the last call's contents: each
+// call clears the part it uses first, and calls whose work overlaps on the
+// GPU (for example on two streams) race on it.
+static __device__ __align__(256) double g_adjoint_scratch[(size_t)HARP_NOALLOC_MAX_NA *
+                                                          HARP_NOALLOC_MAX_NA * 2];
+
+namespace harp {
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return HARP_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_adjoint_scratch);
+    if (e != cudaSuccess) return cuda_status(e);
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return HARP_OK;
+}
+
+template <typename R>
+int launch_adjoint_noalloc(int device, AdjArgs a, cudaStream_t st) {
+  using C = cplx_t<R>;
+  int optin = 0, sms = 0;
+  HARP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  HARP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  const int Nm2 = a.Nm * a.Nm;
+  int BA = 32;
+  size_t smem = 0;
+  for (; BA >= 1; BA /= 2) {
+    smem = ((size_t)BA * Nm2 + (size_t)BA * a.K + (size_t)kRChunk * a.Nm) * sizeof(C) +
+           (size_t)BA * 4 * sizeof(double);
+    if (smem <= std::min<size_t>((size_t)optin, 200 * 1024) && BA * Nm2 <= 24 * kAdjThreads)
+      break;
+  }
+  if (BA < 1) return HARP_E_UNSUPPORTED;
+  a.BA = BA;
+  a.n_mtiles = (a.Na + BA - 1) / BA;
+  a.n_items = a.Na * a.n_mtiles;
+  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  HARP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R>,
+                                                          kAdjThreads, smem));
+  const int grid = std::min(a.n_items, sms * std::max(1, per_sm));
+  adjoint_pairs_kernel<R><<<grid, kAdjThreads, smem, st>>>(a);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+}  // namespace
+}  // namespace harp
+
+extern "C" int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos,
+                                         double freq_hz, const double* coef, const double* Lambda,
+                                         const double* X, int ld, int nrhs, double* grad_pos,
+                                         int prec, void* stream) {
+  if (Na < 1) return -1;
+  if (Nm < 1) return -2;
+  if (P < 0 || P > 64) return -3;
+  if (Q < 0 || Q > 64) return -4;
+  if (!pos) return -5;
+  if (!(freq_hz > 0.0) || freq_hz > 1e15) return -6;
+  if (!coef) return -7;
+  if (!Lambda) return -8;
+  if (!X) return -9;
+  if (ld < (long)Na * Nm) return -10;
+  if (nrhs < 1) return -11;
+  if (!grad_pos) return -12;
+  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32 && prec != HARP_FP32)
+    return -13;
+  if (Na > HARP_NOALLOC_MAX_NA) return HARP_E_UNSUPPORTED;  // beyond the fixed scratch array
+  int device = -1;
+  HARP_CUDA(cudaGetDevice(&device));
+  double* scratch = nullptr;
+  HARP_TRY(noalloc_scratch(device, &scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t used = (size_t)Na * Na * 2 * sizeof(double);
+  HARP_CUDA(cudaMemsetAsync(scratch, 0, used, st));  // pairs m == n are never written
+  AdjArgs a;
+  a.Na = Na;
+  a.Nm = Nm;
+  a.P = P;
+  a.Q = Q;
+  a.nq = Q + 1;
+  a.K = (2 * P + 1) * (Q + 1);
+  a.nrhs = nrhs;
+  a.pos = pos;
+  a.k = 2.0 * kPia * freq_hz / kC0a;
+  a.coef = reinterpret_cast<const double2*>(coef);
+  a.Lam = reinterpret_cast<const double2*>(Lambda);
+  a.X = reinterpret_cast<const double2*>(X);
+  a.ld = ld;
+  a.gpair = scratch;
+  if (prec == HARP_FP64)
+    HARP_TRY(launch_adjoint_noalloc<double>(device, a, st));
+  else
+    HARP_TRY(launch_adjoint_noalloc<float>(device, a, st));
+  adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, scratch, grad_pos);
   HARP_LAUNCHED();
   return HARP_OK;
 }

@@ -67,6 +67,8 @@ def lib():
         L.mbf_solve.argtypes = [vp, i, vp, i, vp, i, i, vp, i, ct.c_char, i, d, i,
                                 ct.POINTER(i), ct.POINTER(d), vp]
         L.harp_fill_adjoint.argtypes = [vp, i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
+        L.harp_fill_adjoint_noalloc.argtypes = [i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
+        L.harp_fill_adjoint_noalloc.restype = i
         L.harp_profile_begin.argtypes = [vp, ct.c_uint]
         L.harp_profile_end.argtypes = [vp, vp, vp, vp]
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_z64", "harp_fill",
@@ -251,3 +253,31 @@ def _alias_storage(ptr: int, nbytes: int, device: int):
                                     "version": 3, "strides": None}
     t = torch.as_tensor(_A(), device=f"cuda:{device}")
     return t.untyped_storage()
+
+
+NOALLOC_MAX_NA = 512
+
+
+def fill_adjoint_noalloc(pos: torch.Tensor, freq_hz: float, coef: torch.Tensor, Lam: torch.Tensor,
+                         X: torch.Tensor, prec="fp64", out: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """The adjoint gradient through the allocation-free entry point (no
+    context; per-pair scratch in a fixed device array of the library, at
+    most NOALLOC_MAX_NA antennas). `out` (Na, 2) float64 may be given so the
+    call itself allocates nothing either."""
+    pr = _prec(prec)
+    pos = pos.to(torch.float64).contiguous()
+    coef = coef.to(torch.complex128).contiguous()
+    Nm = coef.shape[0]
+    P = (coef.shape[2] - 1) // 2
+    Q = coef.shape[3] - 1
+    Na = pos.shape[0]
+    Lam = as_colmajor(Lam.to(torch.complex128))
+    X = as_colmajor(X.to(torch.complex128))
+    if _ld(Lam) != _ld(X):
+        Lam, X = Lam.T.contiguous().T, X.T.contiguous().T
+    grad = torch.empty((Na, 2), dtype=torch.float64, device=pos.device) if out is None else out
+    _check("harp_fill_adjoint_noalloc", lib().harp_fill_adjoint_noalloc(
+        Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(Lam), _ptr(X), _ld(X),
+        X.shape[1], _ptr(grad), pr, _stream(stream)))
+    return grad
