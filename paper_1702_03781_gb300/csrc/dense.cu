@@ -19,6 +19,7 @@
 // solve phase applies the net permutation once, as a gather.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "dense.cuh"
 #include "prof.cuh"
@@ -686,16 +687,44 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
   return HARP_OK;
 }
 
+// Cluster panel (panel_cluster.cu), FP32 only.
+int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb);
+int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
+                  int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st);
+bool panel_cluster_ok(int C, size_t smem);
+
+// Factor the panel at column k (rows k..N); returns the width used in *nb.
+template <typename R>
+static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int k,
+                        int want, int* ipiv, int* zero_col, int mode, cudaStream_t st, int* nb) {
+  if constexpr (std::is_same<R, float>::value) {
+    static int ok_cache[17] = {0};  // 0 unknown, 1 resident, -1 not
+    int C = 0, Mb = 0;
+    const int w = panel_cluster_plan(ctx, N - k, want, &C, &Mb);
+    if (w > 0) {
+      if (ok_cache[C] == 0) ok_cache[C] = panel_cluster_ok(C, (size_t)218 * 1024) ? 1 : -1;
+      if (ok_cache[C] > 0) {
+        *nb = w;
+        return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st);
+      }
+    }
+  }
+  *nb = want;
+  return panel<R>(ctx, N, A, re, im, ld, k, want, ipiv, zero_col, mode, st);
+}
+
 template <typename R>
 int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm, int* zero_col,
               int mode, cudaStream_t st) {
-  ProfScope ps_o(HARP_K_OTHER, 0.0, st);
-  iota_kernel<<<(N + 255) / 256, 256, 0, st>>>(perm, N);
-  HARP_LAUNCHED();
+  {
+    ProfScope ps_o(HARP_K_OTHER, 0.0, st);
+    iota_kernel<<<(N + 255) / 256, 256, 0, st>>>(perm, N);
+    HARP_LAUNCHED();
+  }
   CView<R> A = planes<R>(re, im, ld);
-  for (int k = 0; k < N; k += kNB) {
-    const int nb = std::min(kNB, N - k);
-    HARP_TRY(panel<R>(ctx, N, A, re, im, ld, k, nb, ipiv, zero_col, mode, st));
+  for (int k = 0, nb = 0; k < N; k += nb) {
+    HARP_TRY(factor_panel<R>(ctx, N, A, re, im, ld, k, std::min(kNB, N - k), ipiv, zero_col, mode,
+                             st, &nb));
     HARP_TRY(laswp<R>(re, im, ld, ipiv, k, k + nb, 0, k, k + nb, N, perm, st));
     if (k + nb < N) {
       HARP_TRY(trsm<R>(true, true, nb, N - k - nb, A.sub(k, k), A.sub(k, k + nb), mode, st));

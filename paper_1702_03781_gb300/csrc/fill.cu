@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "ff.cuh"
 #include "prof.cuh"
 
 namespace harp {
@@ -157,6 +158,149 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_kernel(FillArgs a) {
   }
 }
 
+// FP64-accurate fill on the FP32 pipe (mixed modes). Same work split as
+// fill_kernel; coefficients and basis carried as hi/lo float pairs
+// (float4 = re_hi, im_hi, re_lo, im_lo), each entry summed in the
+// three-float accumulator of ff.cuh. Writes the FP64 matrix (Z, c128) and
+// its rounded c64 copy (Z32).
+template <int TN>
+__global__ void __launch_bounds__(kFillThreads, 1) fill_ff_kernel(FillArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, Nm = a.Nm, nq = a.nq, P = a.P, Q = a.Q;
+  const int s0 = blockIdx.y * a.s_chunk;
+  const int sc = min(a.s_chunk, Nm - s0);
+  const int W = sc * Nm;
+  const int Wp = a.Wp;
+  float4* Cs = reinterpret_cast<float4*>(smem_raw);  // [K][Wp]
+  float4* Phi = Cs + (size_t)K * Wp;                 // [K][32]
+
+  for (int idx = threadIdx.x; idx < K * Wp; idx += blockDim.x) {
+    const int kk = idx / Wp, e = idx - kk * Wp;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < W) {
+      const int sl = e / Nm, T = e - sl * Nm;
+      const double2 c = a.coef[((size_t)T * Nm + (s0 + sl)) * K + kk];
+      ff_split(c.x, v.x, v.z);
+      ff_split(c.y, v.y, v.w);
+    }
+    Cs[idx] = v;
+  }
+
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int n = item / a.n_mtiles;
+    const int m0 = (item - n * a.n_mtiles) * kPairsPerTile;
+    __syncthreads();
+    if (threadIdx.x < kPairsPerTile) {
+      const int t = threadIdx.x;
+      const int m = m0 + t;
+      bool valid = (m < a.Na) && (m != n);
+      double dx = 0.0, dy = 0.0, r = 0.0;
+      if (valid) {
+        dx = a.pos[2 * m] - a.pos[2 * n];
+        dy = a.pos[2 * m + 1] - a.pos[2 * n + 1];
+        r = hypot(dx, dy);
+        if (r == 0.0) {
+          atomicOr(a.status, ST_COINCIDENT);
+          valid = false;
+        }
+      }
+      if (!valid) {
+        for (int kk = 0; kk < K; ++kk) Phi[kk * kPairsPerTile + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        // basis in FP64 (Eq. 3, 4), then split into hi/lo pairs
+        const double d = 1.0 / r;
+        double sn, cs;
+        sincos(a.k * r, &sn, &cs);
+        const double2 ph = make_double2(cs, -sn);
+        const double2 z = make_double2(dx * d, dy * d);
+        double2 zp = make_double2(1.0, 0.0);
+        for (int p = 0; p <= P; ++p) {
+          const double2 bp = cmul(ph, zp), bn = cmul(ph, cconj(zp));
+          double dq = 1.0;
+          for (int q = 0; q <= Q; ++q) {
+            float4 v;
+            ff_split(bp.x * dq, v.x, v.z);
+            ff_split(bp.y * dq, v.y, v.w);
+            Phi[((P + p) * nq + q) * kPairsPerTile + t] = v;
+            if (p > 0) {
+              ff_split(bn.x * dq, v.x, v.z);
+              ff_split(bn.y * dq, v.y, v.w);
+              Phi[((P - p) * nq + q) * kPairsPerTile + t] = v;
+            }
+            dq *= d;
+          }
+          zp = cmul(zp, z);
+        }
+      }
+    }
+    __syncthreads();
+
+    float Sr[4][TN], s1r[4][TN], s2r[4][TN], Si[4][TN], s1i[4][TN], s2i[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j)
+        Sr[i][j] = s1r[i][j] = s2r[i][j] = Si[i][j] = s1i[i][j] = s2i[i][j] = 0.f;
+    const float4* phrow = Phi + ty * 4;
+    for (int kk = 0; kk < K; ++kk) {
+      float4 f[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f[i] = phrow[kk * kPairsPerTile + i];
+      const float4* crow = Cs + (size_t)kk * Wp + tx;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const float4 c = crow[32 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          // re += fr*cr - fi*ci ; im += fr*ci + fi*cr
+          fff_mac(Sr[i][j], s1r[i][j], s2r[i][j], f[i].x, f[i].z, c.x, c.z);
+          fff_mac(Sr[i][j], s1r[i][j], s2r[i][j], -f[i].y, -f[i].w, c.y, c.w);
+          fff_mac(Si[i][j], s1i[i][j], s2i[i][j], f[i].x, f[i].z, c.y, c.w);
+          fff_mac(Si[i][j], s1i[i][j], s2i[i][j], f[i].y, f[i].w, c.x, c.z);
+        }
+      }
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty * 4 + i;
+      if (m >= a.Na) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int e = tx + 32 * j;
+        if (e >= W) continue;
+        const int sl = e / Nm, T = e - sl * Nm, S = s0 + sl;
+        const size_t row = (size_t)m * Nm + T, col = (size_t)n * Nm + S;
+        double2 dv = make_double2((double)Sr[i][j] + ((double)s1r[i][j] + (double)s2r[i][j]),
+                                  (double)Si[i][j] + ((double)s1i[i][j] + (double)s2i[i][j]));
+        if (m == n) dv = a.self[(size_t)m * a.self_stride + T + (size_t)S * Nm];
+        reinterpret_cast<double2*>(a.Z)[row + col * a.ldz] = dv;
+        a.Z32[row + col * a.ld32] = make_float2((float)dv.x, (float)dv.y);
+      }
+    }
+  }
+}
+
+static int launch_fill_ff(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int nchunks,
+                          cudaStream_t st) {
+  void (*kern)(FillArgs) = nullptr;
+  switch (TN) {
+    case 1: kern = fill_ff_kernel<1>; break;
+    case 2: kern = fill_ff_kernel<2>; break;
+    case 3: kern = fill_ff_kernel<3>; break;
+    case 4: kern = fill_ff_kernel<4>; break;
+    default: return HARP_E_UNSUPPORTED;
+  }
+  HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int per_chunk = std::max(1, (ctx->num_sms + nchunks - 1) / nchunks);
+  dim3 grid(std::min(a.n_items, per_chunk), nchunks);
+  ProfScope ps(HARP_K_FILL, 8.0 * a.Nm * a.Nm * a.K * (double)a.Na * (a.Na - 1), st);
+  kern<<<grid, kFillThreads, smem, st>>>(a);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
 template <typename R, bool DUAL>
 static int launch_fill(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int nchunks,
                        cudaStream_t st) {
@@ -183,11 +327,11 @@ static int launch_fill(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int
 
 // Largest source-MBF chunk whose staged coefficients fit in shared memory.
 static bool plan_fill(const harp_ctx* ctx, int Nm, int K, size_t csz, int* s_chunk, int* TN,
-                      size_t* smem) {
+                      size_t* smem, int max_tn = 8) {
   for (int sc = Nm; sc >= 1; --sc) {
     const int W = sc * Nm;
     const int tn = (W + 31) / 32;
-    if (tn > 8) continue;
+    if (tn > max_tn) continue;
     const size_t bytes = ((size_t)K * 32 * tn + (size_t)K * kPairsPerTile) * csz;
     if (bytes <= ctx->smem_optin) {
       *s_chunk = sc;
@@ -222,15 +366,17 @@ int fill_dispatch(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos
   a.status = ctx->dstatus;
   a.n_mtiles = (Na + kPairsPerTile - 1) / kPairsPerTile;
   a.n_items = Na * a.n_mtiles;
+  // prec_kind 1 (mixed): float-float kernel, 16-byte staged entries
   const size_t csz = (prec_kind == 2) ? sizeof(float2) : sizeof(double2);
   int sc, TN;
   size_t smem;
-  if (!plan_fill(ctx, Nm, a.K, csz, &sc, &TN, &smem)) return HARP_E_UNSUPPORTED;
+  if (!plan_fill(ctx, Nm, a.K, csz, &sc, &TN, &smem, prec_kind == 1 ? 4 : 8))
+    return HARP_E_UNSUPPORTED;
   a.s_chunk = sc;
   a.Wp = 32 * TN;
   const int nchunks = (Nm + sc - 1) / sc;
   if (prec_kind == 2) return launch_fill<float, false>(ctx, a, TN, smem, nchunks, st);
-  if (prec_kind == 1) return launch_fill<double, true>(ctx, a, TN, smem, nchunks, st);
+  if (prec_kind == 1) return launch_fill_ff(ctx, a, TN, smem, nchunks, st);
   return launch_fill<double, false>(ctx, a, TN, smem, nchunks, st);
 }
 

@@ -1,0 +1,274 @@
+// panel_cluster.cu -- one-launch LU panel factorisation with partial pivoting
+// on a thread-block cluster.
+//
+// The panel A[k0 : k0+M, k0 : k0+nb] is split into row blocks of Mb rows,
+// one per CTA of a cluster (Mb >= nb, so the panel's own top rows all live
+// in CTA 0). Each CTA keeps its block in shared memory, column-major, for
+// the whole factorisation. Column j:
+//   1. each CTA finds its local candidate (largest |z|^2 among its rows
+//      >= j, first index on ties) and writes it into every CTA's candidate
+//      table through distributed shared memory; cluster barrier;
+//   2. every CTA reduces the table (same data, same order, same pivot p),
+//      reads the pivot row from its owner over DSMEM (and the owner of p
+//      also reads row j from CTA 0); cluster barrier;
+//   3. CTA 0 writes the pivot row into row j, the owner of p writes old
+//      row j into row p, and every CTA scales its rows below j and applies
+//      the rank-1 update to the panel's remaining columns, locally.
+// Every CTA executes the same sequence of cluster barriers (all branches
+// depend only on the shared candidate table), so the barriers cannot
+// deadlock. The row interchanges of the rest of the matrix, the triangular
+// solve for U12 and the trailing update stay with the caller.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "dense.cuh"
+#include "prof.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace harp {
+
+constexpr int kPcThreads = 256;
+constexpr int kPcMaxNb = 64;
+constexpr int kPcMaxCluster = 16;
+
+__global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, float* Aim, long lda,
+                                                                   int k0, int M, int nb, int Mb,
+                                                                   int* ipiv, int* zero_col) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int csize = (int)cluster.num_blocks();
+  extern __shared__ __align__(16) float pc_smem[];
+  float* sre = pc_smem;                   // [nb][Mb]
+  float* sim = pc_smem + (size_t)nb * Mb;
+  __shared__ float cand_v[kPcMaxCluster];
+  __shared__ int cand_i[kPcMaxCluster];
+  __shared__ float prow_r[kPcMaxNb], prow_i[kPcMaxNb], jrow_r[kPcMaxNb], jrow_i[kPcMaxNb];
+  __shared__ float red_v[kPcThreads / 32];
+  __shared__ int red_i[kPcThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = crank * Mb;  // first panel row of this CTA
+  const int rows = max(0, min(Mb, M - r0));
+  float* gre = Are + (size_t)(k0 + r0) + (size_t)k0 * lda;
+  float* gim = Aim + (size_t)(k0 + r0) + (size_t)k0 * lda;
+
+  // load the row block (independent loads batched before the stores)
+  for (int c = 0; c < nb; ++c)
+    for (int rb = 0; rb < rows; rb += 4 * kPcThreads) {
+      float vr[4], vi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = rb + tid + u * kPcThreads;
+        vr[u] = (r < rows) ? gre[r + (size_t)c * lda] : 0.f;
+        vi[u] = (r < rows) ? gim[r + (size_t)c * lda] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = rb + tid + u * kPcThreads;
+        if (r < rows) {
+          sre[(size_t)c * Mb + r] = vr[u];
+          sim[(size_t)c * Mb + r] = vi[u];
+        }
+      }
+    }
+  __syncthreads();
+
+  for (int j = 0; j < nb; ++j) {
+    // 1. local candidate
+    float best = -1.f;
+    int bi = INT_MAX;
+    for (int r = tid; r < rows; r += kPcThreads) {
+      const int g = r0 + r;
+      if (g < j) continue;
+      const float xr = sre[(size_t)j * Mb + r], xi = sim[(size_t)j * Mb + r];
+      const float v = xr * xr + xi * xi;
+      if (v > best) {
+        best = v;
+        bi = g;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = best;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid < csize) {
+      float b = red_v[0];
+      int i = red_i[0];
+      for (int q = 1; q < kPcThreads / 32; ++q)
+        if (red_v[q] > b || (red_v[q] == b && red_i[q] < i)) {
+          b = red_v[q];
+          i = red_i[q];
+        }
+      float* rv = cluster.map_shared_rank(cand_v, tid);
+      int* ri = cluster.map_shared_rank(cand_i, tid);
+      rv[crank] = b;
+      ri[crank] = i;
+    }
+    cluster.sync();
+
+    // 2. the pivot (same in every CTA) and the rows to exchange
+    best = cand_v[0];
+    bi = cand_i[0];
+    for (int q = 1; q < csize; ++q)
+      if (cand_v[q] > best || (cand_v[q] == best && cand_i[q] < bi)) {
+        best = cand_v[q];
+        bi = cand_i[q];
+      }
+    const int p = bi;
+    const bool zero = !(best > 0.f) || p >= M;
+    const int op = zero ? 0 : p / Mb;
+    if (!zero && tid < nb) {
+      const float* ore = cluster.map_shared_rank(sre, op);
+      const float* oim = cluster.map_shared_rank(sim, op);
+      prow_r[tid] = ore[(size_t)tid * Mb + (p - op * Mb)];
+      prow_i[tid] = oim[(size_t)tid * Mb + (p - op * Mb)];
+      if (crank == op) {
+        const float* zre = cluster.map_shared_rank(sre, 0);
+        const float* zim = cluster.map_shared_rank(sim, 0);
+        jrow_r[tid] = zre[(size_t)tid * Mb + j];
+        jrow_i[tid] = zim[(size_t)tid * Mb + j];
+      }
+    }
+    if (crank == 0 && tid == 0) {
+      if (zero) {
+        ipiv[k0 + j] = k0 + j;
+        atomicMin(zero_col, k0 + j + 1);
+      } else {
+        ipiv[k0 + j] = k0 + p;
+      }
+    }
+    cluster.sync();  // every remote read of this column is done
+    if (zero) continue;
+
+    // 3. swap, scale, rank-1 update (local)
+    if (tid < nb) {
+      if (crank == 0) {
+        sre[(size_t)tid * Mb + j] = prow_r[tid];
+        sim[(size_t)tid * Mb + j] = prow_i[tid];
+      }
+      if (crank == op && p != j) {
+        sre[(size_t)tid * Mb + (p - r0)] = jrow_r[tid];
+        sim[(size_t)tid * Mb + (p - r0)] = jrow_i[tid];
+      }
+    }
+    __syncthreads();
+    const float pr = prow_r[j], pi = prow_i[j];
+    const float den = pr * pr + pi * pi;
+    const float ir = pr / den, ii = -pi / den;
+    for (int r = tid; r < rows; r += kPcThreads) {
+      const int g = r0 + r;
+      if (g <= j) continue;
+      const float ar = sre[(size_t)j * Mb + r], ai = sim[(size_t)j * Mb + r];
+      const float lr = ar * ir - ai * ii, li = ar * ii + ai * ir;
+      sre[(size_t)j * Mb + r] = lr;
+      sim[(size_t)j * Mb + r] = li;
+      for (int cc = j + 1; cc < nb; ++cc) {
+        const float ur = prow_r[cc], ui = prow_i[cc];
+        float* xr = &sre[(size_t)cc * Mb + r];
+        float* xi = &sim[(size_t)cc * Mb + r];
+        *xr = fmaf(-lr, ur, fmaf(li, ui, *xr));
+        *xi = fmaf(-lr, ui, fmaf(-li, ur, *xi));
+      }
+    }
+    __syncthreads();
+  }
+
+  // store the row block
+  for (int c = 0; c < nb; ++c)
+    for (int r = tid; r < rows; r += kPcThreads) {
+      gre[r + (size_t)c * lda] = sre[(size_t)c * Mb + r];
+      gim[r + (size_t)c * lda] = sim[(size_t)c * Mb + r];
+    }
+  cluster.sync();  // no CTA leaves while others may still read its memory
+}
+
+// Plan a cluster panel for M rows: returns the panel width to use (0 when
+// the cluster path does not apply) and the cluster size and rows per CTA.
+int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb) {
+  const size_t budget = std::min<size_t>(ctx->smem_optin, 220 * 1024) - 2048;
+  for (int nb = std::min(want_nb, kPcMaxNb); nb >= 16; nb /= 2) {
+    for (int C : {1, 2, 4, 8, 16}) {
+      int mb = (M + C - 1) / C;
+      if (mb < nb) mb = nb;
+      if (C > 1 && (C - 1) * mb >= M) continue;  // every CTA owns rows
+      if ((size_t)2 * nb * mb * sizeof(float) <= budget) {
+        *csize = C;
+        *Mb = mb;
+        return nb;
+      }
+    }
+  }
+  return 0;
+}
+
+int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
+                  int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st) {
+  const size_t smem = (size_t)2 * nb * Mb * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    HARP_CUDA(cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   220 * 1024));
+    HARP_CUDA(cudaFuncSetAttribute(panel_cluster_kernel,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kPcThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ProfScope ps(HARP_K_PANEL, 4.0 * M * nb * (double)(nb - 1), st);
+  HARP_CUDA(cudaLaunchKernelEx(&cfg, panel_cluster_kernel, re, im, ld, k0, M, nb, Mb, ipiv,
+                               zero_col));
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// Whether a cluster of C CTAs with this much shared memory can be resident.
+bool panel_cluster_ok(int C, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kPcThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           220 * 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                           1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, panel_cluster_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+}  // namespace harp

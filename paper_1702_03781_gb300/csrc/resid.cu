@@ -21,41 +21,12 @@
 #include <cmath>
 
 #include "dense.cuh"
+#include "ff.cuh"
 #include "prof.cuh"
 
 namespace harp {
 
 constexpr int kRBM = 64, kRBN = 32, kRBK = 16;
-
-__device__ __forceinline__ void ff_split(double x, float& h, float& l) {
-  h = (float)x;
-  l = (float)(x - (double)h);
-}
-
-// Knuth's TwoSum: returns fl(x + y) and sets err = x + y - fl(x + y) exactly.
-__device__ __forceinline__ float two_sum(float x, float y, float& err) {
-  const float s = __fadd_rn(x, y);
-  const float v = __fsub_rn(s, x);
-  err = __fadd_rn(__fsub_rn(x, __fsub_rn(s, v)), __fsub_rn(y, v));
-  return s;
-}
-
-// (S, s1, s2) += a * b, a = ah + al, b = bh + bl.
-__device__ __forceinline__ void fff_mac(float& S, float& s1, float& s2, float ah, float al,
-                                        float bh, float bl) {
-  // Round-to-nearest intrinsics keep the compiler from contracting the
-  // product into the sums, which would break the error-free transformations.
-  const float p = __fmul_rn(ah, bh);
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  float t;
-  S = two_sum(S, p, t);
-  float t2, t3;
-  s1 = two_sum(s1, t, t2);
-  s1 = two_sum(s1, e, t3);
-  s2 = __fadd_rn(s2, __fadd_rn(t2, t3));
-}
 
 // R[i, c] = V[i, c] - sum_k A[i, k] X[k, c]; A as 4 float planes (hi/lo of
 // re/im, element (i,k) at i*ars + k*acs), X as 4 float planes (ld ldx).

@@ -24,6 +24,12 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = 2 * 128 * SMS * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
 FP64_PEAK_TFLOPS = 2 * 2 * SMS * SM_MAX_MHZ * 1e6 / 1e12     # 1.259
+# Float-float kernels (FP64-accurate on the FP32 pipe): one complex
+# multiply-add is 96 FP32 instructions (4 compensated real products of 24
+# instructions) for 8 algorithmic flops; the pipe issues 128 instructions per
+# clock per SM.
+FF_INSTR_PER_CMAC = 96
+FF_PEAK_TFLOPS = 128 * SMS * SM_MAX_MHZ * 1e6 * 8 / FF_INSTR_PER_CMAC / 1e12   # 3.357
 TF32_OVER_BF16 = 1.1 / 2.25
 
 _ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -71,6 +77,10 @@ def peak_for(kind: str, impl: str, peaks: dict):
         return "tensor", 1900.0 * TF32_OVER_BF16, "TFLOP/s", "fallback bf16 1.9 PF x 1.1/2.25 (TF32)"
     if impl == "fp32":
         return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 FMA pipe: 128 FMA/clk/SM x 152 SMs x 2070 MHz"
+    if impl == "ff":
+        return ("alu", FF_PEAK_TFLOPS, "TFLOP/s",
+                "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 96 instr per complex MAC "
+                "(float-float, FP64-accurate)")
     return "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "FP64 FMA pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz"
 
 
@@ -90,4 +100,5 @@ def entry(kind: str, impl: str, prof_kind: dict, peaks: dict) -> dict:
             "peak": round(peak, 3), "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": traffic, "launches": prof_kind["launches"],
             "avg_launch_ms": round(ms / n, 5), "flops_per_launch": prof_kind["flops"] / n,
-            "peak_source": note + (" (of measured)" if "measured" in note or "FMA" in note else "")}
+            "peak_source": note + (" (of measured)" if bound == "tensor" else
+                                   " (derived from unit counts and the maximum clock)")}
