@@ -57,8 +57,8 @@ def shares(prof: dict) -> dict:
 
 def source_hash(kind: str) -> str:
     """Hash of the sources a kernel class is built from (traffic validity)."""
-    files = {"fill": ["fill.cu"], "gemm": ["lu_tc.cu", "dense.cu"], "residual": ["dense.cu", "resid.cu"],
-             "panel": ["dense.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
+    files = {"fill": ["fill.cu", "ff.cuh"], "gemm": ["lu_tc.cu"], "residual": ["resid.cu", "ff.cuh"],
+             "panel": ["panel_cluster.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
              "adjoint": ["adjoint.cu"], "other": ["dense.cu"]}.get(kind, [])
     h = hashlib.sha256()
     for f in files:
