@@ -172,6 +172,21 @@ int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double*
                       double freq_hz, const double* coef, const double* Lambda, const double* X,
                       int ld, int nrhs, double* grad_pos, int prec, void* stream);
 
+/* Port objective of the synthesis workload (the array-synthesis use the
+ * paper's conclusion names; reading: the port response of the solution for
+ * the port excitations V = E):
+ *   P = E^T X   (Na x Na, c128, column-major; row m*Nm of each column of X),
+ *   J = sum_mn |P_mn|^2   (one double, device memory),
+ *   W = E conj(P)  (N x Na, c128, ld ldw; the right-hand side of the
+ *                   adjoint solve Z^T Lambda = W for dJ/dZ).
+ *   X, ldx  c128 N x Na solution of Z X = E, N = Na*Nm     [3, 4]
+ *   P       output or NULL                                  [5]
+ *   J       output (device double)                          [6]
+ *   W, ldw  output or NULL                                  [7, 8]
+ * Asynchronous on `stream`; J is reduced in a fixed order. */
+int harp_port_objective(int Na, int Nm, const double* X, int ldx, double* P, double* J,
+                        double* W, int ldw, void* stream);
+
 /* Allocation-free variant of harp_fill_adjoint (no counterpart in the paper:
  * it exists for callers that cannot allocate device memory, for instance an
  * application whose allocator owns all device memory or that runs under a

@@ -67,6 +67,8 @@ def lib():
         L.mbf_solve.argtypes = [vp, i, vp, i, vp, i, i, vp, i, ct.c_char, i, d, i,
                                 ct.POINTER(i), ct.POINTER(d), vp]
         L.harp_fill_adjoint.argtypes = [vp, i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
+        L.harp_port_objective.argtypes = [i, i, vp, i, vp, vp, vp, i, vp]
+        L.harp_port_objective.restype = i
         L.harp_fill_adjoint_noalloc.argtypes = [i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
         L.harp_fill_adjoint_noalloc.restype = i
         L.harp_profile_begin.argtypes = [vp, ct.c_uint]
@@ -253,6 +255,23 @@ def _alias_storage(ptr: int, nbytes: int, device: int):
                                     "version": 3, "strides": None}
     t = torch.as_tensor(_A(), device=f"cuda:{device}")
     return t.untyped_storage()
+
+
+def port_objective(X: torch.Tensor, Na: int, Nm: int, want_P: bool = True, want_W: bool = True,
+                   stream=None):
+    """(P, J, W) of the port objective: P = E^T X (Na x Na), J = sum |P|^2
+    (0-d float64 tensor on the device), W = E conj(P) (N x Na, the adjoint
+    right-hand side). Computed by the library's kernels."""
+    X = as_colmajor(X.to(torch.complex128))
+    dev = X.device
+    N = Na * Nm
+    P = colmajor_empty(Na, Na, torch.complex128, dev) if want_P else None
+    W = colmajor_empty(N, Na, torch.complex128, dev) if want_W else None
+    J = torch.empty((), dtype=torch.float64, device=dev)
+    _check("harp_port_objective", lib().harp_port_objective(
+        Na, Nm, _ptr(X), _ld(X), _ptr(P), _ptr(J), _ptr(W), _ld(W) if W is not None else N,
+        _stream(stream)))
+    return P, J, W
 
 
 NOALLOC_MAX_NA = 512
