@@ -87,10 +87,11 @@ unsigned long long harp_kernel_launches(void);
 
 /* Create a context on CUDA device `device` with workspace for systems up to
  * max_N unknowns and max_nrhs right-hand sides. The context owns its device
- * workspace (about 56 max_N^2 + 80 max_N max_nrhs bytes): the FP64 copy of
+ * workspace (about 96 max_N^2 + 80 max_N max_nrhs bytes): the FP64 copy of
  * the reduced matrix used by the refinement, the LU factors and pivots of
- * the last factorisation, and solve buffers. Returns HARP_E_NOMEM when the
- * allocation fails. One context serves one stream at a time. */
+ * the last factorisation, solve buffers, and a stream and c64 matrix buffer
+ * for harp_solve_batch. Returns HARP_E_NOMEM when the allocation fails. One
+ * context serves one stream at a time. */
 int harp_ctx_create(harp_ctx** ctx, int device, int max_N, int max_nrhs);
 
 /* Release the context and its workspace (synchronises the device). */
@@ -171,6 +172,39 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
                       double freq_hz, const double* coef, const double* Lambda, const double* X,
                       int ld, int nrhs, double* grad_pos, int prec, void* stream);
+
+/* One problem of a batch: one frequency (or layout) of the fill + solve for
+ * the port excitations. Inputs as for harp_fill; X (c128 N x Na, ld ldx,
+ * device memory) receives the solution; status, iters and resid are
+ * written by harp_solve_batch (status as returned by harp_fill/mbf_solve). */
+typedef struct {
+  int Na, Nm, P, Q;
+  const double* pos;
+  double freq_hz;
+  const double* coef;
+  const double* self_blocks;
+  long self_stride;
+  double* X;
+  int ldx;
+  int status;
+  int iters;
+  double resid;
+} harp_problem;
+
+/* Fill and solve many independent problems (the wideband case of the paper's
+ * analysis over frequency, Section III: one reduced system per frequency,
+ * with an MBF count that grows with frequency). Each of the n_ctx contexts
+ * is a worker with its own host thread and stream; problems are taken in
+ * array order (put the largest first), and workers overlap on the GPU.
+ *   ctxs, n_ctx       contexts (each sized for the largest problem it may
+ *                     take; all on the same or different devices)  [1, 2]
+ *   probs, n_probs    problems (host array)                          [3, 4]
+ *   prec              HARP_FP64 or a mixed mode                      [5]
+ *   tol, max_iter     as for mbf_solve                               [6, 7]
+ * Blocks until every problem is done. Returns HARP_OK, or the first
+ * non-zero per-problem status. */
+int harp_solve_batch(harp_ctx** ctxs, int n_ctx, harp_problem* probs, int n_probs, int prec,
+                     double tol, int max_iter);
 
 /* Port objective of the synthesis workload (the array-synthesis use the
  * paper's conclusion names; reading: the port response of the solution for

@@ -1,0 +1,77 @@
+// batch.cu -- scheduler for many independent fill + solve problems (the
+// wideband case: one problem per frequency, uneven sizes).
+//
+// Each context is a worker: one host thread and the context's own stream.
+// Workers take problems from a shared atomic counter, largest first (the
+// caller's order), and run harp_fill + mbf_solve on their stream. Problems
+// on different workers overlap on the GPU: the latency-bound parts of one
+// (the pivoted panels, the host round trip of each refinement step) run
+// while the others' fills, GEMMs and residuals occupy the remaining SMs.
+// No CUDA call here allocates; the contexts own all workspace.
+#include <atomic>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace harp;
+
+namespace {
+
+void run_worker(harp_ctx* ctx, harp_problem* probs, int n, std::atomic<int>* next, int prec,
+                double tol, int max_iter) {
+  for (;;) {
+    const int i = next->fetch_add(1);
+    if (i >= n) return;
+    harp_problem& p = probs[i];
+    const int N = p.Na * p.Nm;
+    int s;
+    if (N > ctx->max_N || p.Na > ctx->max_nrhs) {
+      s = HARP_E_UNSUPPORTED;
+    } else {
+      const int fill_prec = (prec == HARP_FP64) ? HARP_FP64 : HARP_MIXED_3XTF32;
+      // FP64 fills straight into the context's FP64 matrix; the mixed modes
+      // write Z64 there and the c64 copy into the worker's buffer.
+      void* Z = (prec == HARP_FP64) ? (void*)ctx->z64 : (void*)ctx->zbuf;
+      const int ldz = (prec == HARP_FP64) ? ctx->ld64 : N;
+      s = harp_fill(ctx, p.Na, p.Nm, p.P, p.Q, p.pos, p.freq_hz, p.coef, p.self_blocks,
+                    p.self_stride, Z, ldz, fill_prec, ctx->stream);
+      if (s == HARP_OK)
+        s = mbf_solve(ctx, N, Z, ldz, nullptr, N, p.Na, p.X, p.ldx, 'N', prec, tol, max_iter,
+                      &p.iters, &p.resid, ctx->stream);
+    }
+    p.status = s;
+  }
+}
+
+}  // namespace
+
+extern "C" int harp_solve_batch(harp_ctx** ctxs, int n_ctx, harp_problem* probs, int n_probs,
+                                int prec, double tol, int max_iter) {
+  if (!ctxs || n_ctx < 1) return -1;
+  for (int c = 0; c < n_ctx; ++c)
+    if (!ctxs[c]) return -1;
+  if (n_ctx > 64) return -2;
+  if (!probs || n_probs < 0) return -3;
+  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32) return -5;
+  if (max_iter < 0) return -7;
+  for (int i = 0; i < n_probs; ++i) {
+    probs[i].status = HARP_E_STATE;
+    probs[i].iters = 0;
+    probs[i].resid = -1.0;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> workers;
+  workers.reserve(n_ctx);
+  for (int c = 0; c < n_ctx; ++c)
+    workers.emplace_back(run_worker, ctxs[c], probs, n_probs, &next, prec, tol, max_iter);
+  for (auto& w : workers) w.join();
+  for (int c = 0; c < n_ctx; ++c) {
+    DeviceGuard g(ctxs[c]->device);
+    HARP_CUDA(cudaStreamSynchronize(ctxs[c]->stream));
+  }
+  int first_bad = HARP_OK;
+  for (int i = 0; i < n_probs; ++i)
+    if (probs[i].status != HARP_OK && first_bad == HARP_OK) first_bad = probs[i].status;
+  return first_bad;
+}

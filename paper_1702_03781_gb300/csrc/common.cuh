@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/harp_gb300.h"
 
 namespace harp {
@@ -67,7 +69,7 @@ template <typename R> inline CView<R> interleaved(R* base, long ld) {
 // ---------------------------------------------------------------------------
 // Status plumbing.
 extern int g_last_cuda_error;
-extern unsigned long long g_kernel_launches;  // host-side count of kernel launches
+extern std::atomic<unsigned long long> g_kernel_launches;  // host-side count of launches
 
 inline int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HARP_OK;
@@ -163,6 +165,10 @@ struct harp_ctx {
   // Adjoint per-pair partial gradients, Na x Na x 2 doubles (lazily sized).
   double* gpair;
   size_t gpair_bytes;
+
+  // Stream and c64 matrix buffer used by the batch scheduler (batch.cu).
+  cudaStream_t stream;
+  float2* zbuf;
 
   // Reductions and status.
   double* red;      // device scratch, 16 + 2*max_nrhs doubles

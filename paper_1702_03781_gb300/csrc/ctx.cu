@@ -8,7 +8,7 @@
 
 namespace harp {
 int g_last_cuda_error = 0;
-unsigned long long g_kernel_launches = 0;
+std::atomic<unsigned long long> g_kernel_launches{0};
 }
 
 using namespace harp;
@@ -31,13 +31,15 @@ extern "C" const char* harp_status_string(int s) {
 
 extern "C" int harp_last_cuda_error(void) { return g_last_cuda_error; }
 
-extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launches; }
+extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launches.load(); }
 
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
                   c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->gpair, c->red, c->dstatus};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->zbuf) cudaFree(c->zbuf);
+  if (c->stream) cudaStreamDestroy(c->stream);
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->hstatus) cudaFreeHost(c->hstatus);
 }
@@ -106,6 +108,8 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   const size_t nred = 16 + 2 * (size_t)max_nrhs;
   alloc((void**)&c->red, nred * sizeof(double));
   alloc((void**)&c->dstatus, 4 * sizeof(int));
+  alloc((void**)&c->zbuf, NN * sizeof(float2));
+  if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok && cudaMallocHost((void**)&c->red_host, nred * sizeof(double)) != cudaSuccess) ok = false;
   if (ok && cudaMallocHost((void**)&c->hstatus, 4 * sizeof(int)) != cudaSuccess) ok = false;
   if (!ok) {

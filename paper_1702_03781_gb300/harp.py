@@ -37,6 +37,15 @@ HARP_E_NONFINITE = 0x40000008
 _lib = None
 
 
+class HarpProblem(ct.Structure):
+    """Mirror of the C struct harp_problem (one problem of a batch)."""
+    _fields_ = [("Na", ct.c_int), ("Nm", ct.c_int), ("P", ct.c_int), ("Q", ct.c_int),
+                ("pos", ct.c_void_p), ("freq_hz", ct.c_double), ("coef", ct.c_void_p),
+                ("self_blocks", ct.c_void_p), ("self_stride", ct.c_long), ("X", ct.c_void_p),
+                ("ldx", ct.c_int), ("status", ct.c_int), ("iters", ct.c_int),
+                ("resid", ct.c_double)]
+
+
 class HarpError(RuntimeError):
     def __init__(self, fn: str, status: int):
         self.status = status
@@ -67,6 +76,8 @@ def lib():
         L.mbf_solve.argtypes = [vp, i, vp, i, vp, i, i, vp, i, ct.c_char, i, d, i,
                                 ct.POINTER(i), ct.POINTER(d), vp]
         L.harp_fill_adjoint.argtypes = [vp, i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
+        L.harp_solve_batch.argtypes = [ct.POINTER(vp), i, ct.POINTER(HarpProblem), i, i, d, i]
+        L.harp_solve_batch.restype = i
         L.harp_port_objective.argtypes = [i, i, vp, i, vp, vp, vp, i, vp]
         L.harp_port_objective.restype = i
         L.harp_fill_adjoint_noalloc.argtypes = [i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
@@ -255,6 +266,49 @@ def _alias_storage(ptr: int, nbytes: int, device: int):
                                     "version": 3, "strides": None}
     t = torch.as_tensor(_A(), device=f"cuda:{device}")
     return t.untyped_storage()
+
+
+class BatchItem:
+    """One problem of solve_batch, with its device inputs in ABI layout and
+    its output X (column-major N x Na complex128)."""
+
+    def __init__(self, pos, freq_hz, coef, self_blocks):
+        self.pos = pos.to(torch.float64).contiguous()
+        self.coef = coef.to(torch.complex128).contiguous()
+        self.freq_hz = float(freq_hz)
+        self.Nm = self.coef.shape[0]
+        self.P = (self.coef.shape[2] - 1) // 2
+        self.Q = self.coef.shape[3] - 1
+        self.Na = self.pos.shape[0]
+        if self_blocks.dim() == 2:
+            self.sb, self.stride = self_blocks.to(torch.complex128).T.contiguous(), 0
+        else:
+            self.sb = self_blocks.to(torch.complex128).transpose(1, 2).contiguous()
+            self.stride = self.Nm * self.Nm
+        self.N = self.Na * self.Nm
+        self.X = colmajor_empty(self.N, self.Na, torch.complex128, self.pos.device)
+        self.status = self.iters = 0
+        self.resid = 0.0
+
+
+def solve_batch(contexts, items, prec="mixed", tol: float = 0.0, max_iter: int = 10,
+                check: bool = True):
+    """Fill and solve every item (each for its port excitations) with the
+    library's batch scheduler: one worker thread and stream per context."""
+    arr = (HarpProblem * len(items))()
+    for k, it in enumerate(items):
+        arr[k] = HarpProblem(it.Na, it.Nm, it.P, it.Q, it.pos.data_ptr(), it.freq_hz,
+                             it.coef.data_ptr(), it.sb.data_ptr(), it.stride, it.X.data_ptr(),
+                             _ld(it.X), 0, 0, 0.0)
+    hs = (ct.c_void_p * len(contexts))(*[c.handle.value for c in contexts])
+    torch.cuda.synchronize()  # inputs prepared on torch's stream are ready
+    st = lib().harp_solve_batch(hs, len(contexts), arr, len(items), _prec(prec), float(tol),
+                                int(max_iter))
+    for k, it in enumerate(items):
+        it.status, it.iters, it.resid = arr[k].status, arr[k].iters, arr[k].resid
+    if check:
+        _check("harp_solve_batch", st)
+    return st
 
 
 def port_objective(X: torch.Tensor, Na: int, Nm: int, want_P: bool = True, want_W: bool = True,
