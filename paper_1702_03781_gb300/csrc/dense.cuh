@@ -38,10 +38,15 @@ int split_c128(int M, int N, const double* Z, long ldz, float* const hl[4], long
 int split_planes(int M, int N, const double* xr, const double* xi, long ld, float* const hl[4],
                  cudaStream_t st);
 // pr/pi: scratch for up to max_split FP64 partials of ldr * nrhs entries.
+// fff: three-float accumulator (FP64-accurate) or double-float (updates).
 int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
                 const float* const B[4], long ldb, const double* vr, const double* vi, double* rr,
                 double* ri, long ldr, double* pr, double* pi, int max_split, int num_sms,
-                cudaStream_t st);
+                cudaStream_t st, bool fff);
+int split_f32_planes(int M, int N, const float* xr, const float* xi, long ld, float* const hl[4],
+                     cudaStream_t st);
+int colmax_cabs1_f32(int M, int N, const float* xr, const float* xi, long ld, double* colmax,
+                     cudaStream_t st);
 int colmax_cabs1(int M, int N, const double* xr, const double* xi, long ld, double* colmax,
                  cudaStream_t st);
 int norm_inf_planes_f32(int M, int N, const float* re, const float* im, long rs, long cs,

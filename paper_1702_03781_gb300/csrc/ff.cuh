@@ -45,4 +45,19 @@ __device__ __forceinline__ void fff_mac(float& S, float& s1, float& s2, float ah
   s2 = __fadd_rn(s2, __fadd_rn(t2, t3));
 }
 
+// (S, s) += a * b with a double-float accumulator (Ogita-Rump-Oishi Dot2:
+// exact product error and TwoSum error gathered in one float). Half the
+// instructions of fff_mac; its error grows with the running sum (~1e-14 of
+// sum |a||b| over 3072 terms), enough for updates that are small against
+// the quantity being corrected.
+__device__ __forceinline__ void ff2_mac(float& S, float& s, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  float t;
+  S = two_sum(S, p, t);
+  s = __fadd_rn(s, __fadd_rn(t, e));
+}
+
 }  // namespace harp

@@ -32,6 +32,9 @@ constexpr int kRBM = 64, kRBN = 32, kRBK = 16;
 // re/im, element (i,k) at i*ars + k*acs), X as 4 float planes (ld ldx).
 // With split-K (gridDim.z > 1) each z-slice sums its own K range and writes
 // its FP64 partial to P[z] (no V); resid_combine_kernel then forms V - sum.
+// FFF selects the three-float accumulator (FP64-accurate); otherwise the
+// double-float one (for updates R - Z D with a small correction D).
+template <bool FFF>
 __global__ void __launch_bounds__(256) resid_ff_kernel(
     int N, int nrhs, const float* __restrict__ Ahr, const float* __restrict__ Ahi,
     const float* __restrict__ Alr, const float* __restrict__ Ali, long ars, long acs,
@@ -97,10 +100,17 @@ __global__ void __launch_bounds__(256) resid_ff_kernel(
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           // re += ar*br - ai*bi ; im += ar*bi + ai*br
-          fff_mac(Sr[a][b], s1r[a][b], s2r[a][b], ar_h[a], ar_l[a], br_h[b], br_l[b]);
-          fff_mac(Sr[a][b], s1r[a][b], s2r[a][b], -ai_h[a], -ai_l[a], bi_h[b], bi_l[b]);
-          fff_mac(Si[a][b], s1i[a][b], s2i[a][b], ar_h[a], ar_l[a], bi_h[b], bi_l[b]);
-          fff_mac(Si[a][b], s1i[a][b], s2i[a][b], ai_h[a], ai_l[a], br_h[b], br_l[b]);
+          if (FFF) {
+            fff_mac(Sr[a][b], s1r[a][b], s2r[a][b], ar_h[a], ar_l[a], br_h[b], br_l[b]);
+            fff_mac(Sr[a][b], s1r[a][b], s2r[a][b], -ai_h[a], -ai_l[a], bi_h[b], bi_l[b]);
+            fff_mac(Si[a][b], s1i[a][b], s2i[a][b], ar_h[a], ar_l[a], bi_h[b], bi_l[b]);
+            fff_mac(Si[a][b], s1i[a][b], s2i[a][b], ai_h[a], ai_l[a], br_h[b], br_l[b]);
+          } else {
+            ff2_mac(Sr[a][b], s1r[a][b], ar_h[a], ar_l[a], br_h[b], br_l[b]);
+            ff2_mac(Sr[a][b], s1r[a][b], -ai_h[a], -ai_l[a], bi_h[b], bi_l[b]);
+            ff2_mac(Si[a][b], s1i[a][b], ar_h[a], ar_l[a], bi_h[b], bi_l[b]);
+            ff2_mac(Si[a][b], s1i[a][b], ai_h[a], ai_l[a], br_h[b], br_l[b]);
+          }
         }
     }
     __syncthreads();
@@ -159,6 +169,37 @@ __global__ void split_planes_kernel(int M, int N, const double* __restrict__ xr,
   ff_split(xi[o], a, b);
   hi[o] = a;
   li[o] = b;
+}
+
+// FP32 planes (M x N, ld) -> hi/lo float planes: hi = value, lo = 0.
+__global__ void split_f32_planes_kernel(int M, int N, const float* __restrict__ xr,
+                                        const float* __restrict__ xi, long ld, float* hr,
+                                        float* hi, float* lr, float* li) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= M) return;
+  const size_t o = (size_t)i + (size_t)j * ld;
+  hr[o] = xr[o];
+  hi[o] = xi[o];
+  lr[o] = 0.f;
+  li[o] = 0.f;
+}
+
+// Per-column max of |re| + |im| of FP32 planes -> colmax[j] (zeroed before).
+__global__ void colmax_cabs1_f32_kernel(int M, int N, const float* __restrict__ xr,
+                                        const float* __restrict__ xi, long ld, double* colmax) {
+  const int j = blockIdx.y;
+  float m = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)i + (size_t)j * ld;
+    const float v = fabsf(xr[o]) + fabsf(xi[o]);
+    m = (v == v) ? fmaxf(m, v) : __int_as_float(0x7f800000);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(colmax + j),
+              (unsigned long long)__double_as_longlong((double)m));
 }
 
 // Per-column max of |re| + |im| over FP64 planes -> colmax[j] (zeroed before).
@@ -250,7 +291,7 @@ __global__ void resid_combine_kernel(int N, int nrhs, int nz, const double* __re
 int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
                 const float* const B[4], long ldb, const double* vr, const double* vi, double* rr,
                 double* ri, long ldr, double* pr, double* pi, int max_split, int num_sms,
-                cudaStream_t st) {
+                cudaStream_t st, bool fff) {
   const int tiles = ((nrhs + kRBN - 1) / kRBN) * ((N + kRBM - 1) / kRBM);
   // split K so that the CTAs (two resident per SM) fill whole waves
   const double slots = 2.0 * num_sms;
@@ -272,9 +313,9 @@ int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
   const long pstride = (long)ldr * nrhs;
   {
     ProfScope ps(HARP_K_RESIDUAL, 8.0 * N * (double)N * nrhs, st);
-    resid_ff_kernel<<<grid, 256, 0, st>>>(N, nrhs, A[0], A[1], A[2], A[3], ars, acs, B[0], B[1],
-                                          B[2], B[3], ldb, vr, vi, rr, ri, ldr, kchunk, pr, pi,
-                                          pstride);
+    auto kern = fff ? resid_ff_kernel<true> : resid_ff_kernel<false>;
+    kern<<<grid, 256, 0, st>>>(N, nrhs, A[0], A[1], A[2], A[3], ars, acs, B[0], B[1], B[2], B[3],
+                               ldb, vr, vi, rr, ri, ldr, kchunk, pr, pi, pstride);
     HARP_LAUNCHED();
   }
   if (ks > 1) {
@@ -292,6 +333,25 @@ int colmax_cabs1(int M, int N, const double* xr, const double* xi, long ld, doub
   dim3 grid(std::min(16, (M + 255) / 256), N);
   ProfScope ps(HARP_K_OTHER, 0.0, st);
   colmax_cabs1_kernel<<<grid, 256, 0, st>>>(M, N, xr, xi, ld, colmax);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+int split_f32_planes(int M, int N, const float* xr, const float* xi, long ld, float* const hl[4],
+                     cudaStream_t st) {
+  dim3 grid((M + 255) / 256, N);
+  ProfScope ps(HARP_K_OTHER, 0.0, st);
+  split_f32_planes_kernel<<<grid, 256, 0, st>>>(M, N, xr, xi, ld, hl[0], hl[1], hl[2], hl[3]);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+int colmax_cabs1_f32(int M, int N, const float* xr, const float* xi, long ld, double* colmax,
+                     cudaStream_t st) {
+  HARP_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * N, st));
+  dim3 grid(std::min(16, (M + 255) / 256), N);
+  ProfScope ps(HARP_K_OTHER, 0.0, st);
+  colmax_cabs1_f32_kernel<<<grid, 256, 0, st>>>(M, N, xr, xi, ld, colmax);
   HARP_LAUNCHED();
   return HARP_OK;
 }

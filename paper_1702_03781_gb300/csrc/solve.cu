@@ -4,10 +4,10 @@
 //
 // Mixed refinement (classical iterative refinement, Wilkinson/Moler; the
 // stopping rule follows LAPACK's zcgesv):
-//   X0 = (LU32)^{-1} V
-//   repeat: R = V - Z64 X (FP64-accurate, float-float on the FP32 pipe);
-//           stop when, for every column j, max_i |R_ij| <= tol ||Z64||_inf
-//           max_i |X_ij| (|z| = |re| + |im|); D = (LU32)^{-1} R; X += D.
+//   X0 = (LU32)^{-1} V, R0 = V - Z64 X0 (FP64-accurate, float-float)
+//   repeat: stop when, for every column j, max_i |R_ij| <= tol ||Z64||_inf
+//           max_i |X_ij| (|z| = |re| + |im|); D = (LU32)^{-1} R; X += D;
+//           R -= Z64 D (an update accurate relative to |Z64||D|).
 // The LU factors live in the context so that an adjoint solve (trans 'T')
 // reuses them.
 #include <cmath>
@@ -170,13 +170,21 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   if (tol <= 0.0) tol = std::sqrt((double)N) * std::ldexp(1.0, -53);
   double* colmax_r = ctx->red + 16;
   double* colmax_x = ctx->red + 16 + nrhs;
+  // R_0 = V - Z X_0 with the three-float accumulator (X_0 is the FP32
+  // solution, exact as hi with lo = 0). Later residuals are updated,
+  // R_{k+1} = R_k - Z D_k, whose error only has to be small against
+  // |Z||D_k|: with rho = max_j max|D_kj| / max|X_j| <= kDot2Rho the
+  // double-float accumulator (~1e-14 of sum |z||d|) keeps the update error
+  // below 2^-53 |Z||X|, otherwise the three-float one is used.
+  constexpr double kDot2Rho = 1e-2;
+  HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
+  HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
+                       ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
+                       true));
   double bwd = INFINITY;
   int it = 0;
   bool converged = false;
   for (;;) {
-    HARP_TRY(split_planes(N, nrhs, ctx->x_re, ctx->x_im, ldw, xhl, st));
-    HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
-                         ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st));
     HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, st));
     HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
     HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
@@ -196,10 +204,27 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       break;
     }
     if (it >= max_iter) break;
+    // D = (LU32)^{-1} R; X += D
     HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->r_re, ctx->r_im, ldw, wre, wim, ldw, st));
     HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
                              tr ? 'T' : 'N', dinv_r, dinv_i, mode, st));
     HARP_TRY(add_planes<float>(N, nrhs, ctx->x_re, ctx->x_im, ldw, wre, wim, ldw, st));
+    // size of the correction against the iterate (host needs it to choose
+    // the accumulator of the update)
+    HARP_TRY(colmax_cabs1_f32(N, nrhs, wre, wim, ldw, colmax_r, st));
+    HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
+    HARP_CUDA(cudaMemcpyAsync(ctx->red_host + 16, colmax_r, sizeof(double) * 2 * (size_t)nrhs,
+                              cudaMemcpyDeviceToHost, st));
+    HARP_CUDA(cudaStreamSynchronize(st));
+    double rho = 0.0;
+    for (int j = 0; j < nrhs; ++j) {
+      const double dj = h[16 + j], xj = h[16 + nrhs + j];
+      rho = std::max(rho, (dj == 0.0) ? 0.0 : dj / xj);
+    }
+    HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
+    HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
+                         ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
+                         !(rho <= kDot2Rho)));
     ++it;
   }
   HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
