@@ -4,20 +4,24 @@
 // The panel A[k0 : k0+M, k0 : k0+nb] is split into row blocks of Mb rows,
 // one per CTA of a cluster (Mb >= nb, so the panel's own top rows all live
 // in CTA 0). Each CTA keeps its block in shared memory, column-major, for
-// the whole factorisation. Column j:
+// the whole factorisation. Column j (one cluster barrier per column):
 //   1. each CTA finds its local candidate (largest |z|^2 among its rows
-//      >= j, first index on ties) and writes it into every CTA's candidate
-//      table through distributed shared memory; cluster barrier;
-//   2. every CTA reduces the table (same data, same order, same pivot p),
-//      reads the pivot row from its owner over DSMEM (and the owner of p
-//      also reads row j from CTA 0); cluster barrier;
-//   3. CTA 0 writes the pivot row into row j, the owner of p writes old
-//      row j into row p, and every CTA scales its rows below j and applies
-//      the rank-1 update to the panel's remaining columns, locally.
-// Every CTA executes the same sequence of cluster barriers (all branches
-// depend only on the shared candidate table), so the barriers cannot
-// deadlock. The row interchanges of the rest of the matrix, the triangular
-// solve for U12 and the trailing update stay with the caller.
+//      >= j, first index on ties) and writes it -- value, row index and the
+//      row's nb entries -- into every CTA's candidate table through
+//      distributed shared memory; CTA 0 also writes its current row j;
+//   2. cluster barrier;
+//   3. every CTA reduces its copy of the table (same data, same order, same
+//      pivot p) and has the pivot row and row j locally: CTA 0 writes the
+//      pivot row into row j, the owner of p writes old row j into row p,
+//      and every CTA scales its rows below j and applies the rank-1 update
+//      to the panel's remaining columns.
+// The tables are double-buffered by column parity: a CTA can only publish
+// for column j+2 after every CTA has passed barrier j+1, that is after
+// every CTA has finished reading the tables of column j. Every CTA executes
+// the same sequence of barriers (all branches depend only on the shared
+// tables), so they cannot deadlock. The row interchanges of the rest of the
+// matrix, the triangular solve for U12 and the trailing update stay with
+// the caller.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -34,18 +38,31 @@ constexpr int kPcThreads = 256;
 constexpr int kPcMaxNb = 64;
 constexpr int kPcMaxCluster = 16;
 
+// Bytes of dynamic shared memory for a panel of nb columns, Mb rows per CTA
+// and a cluster of C CTAs.
+__host__ __device__ inline size_t panel_smem_bytes(int nb, int Mb, int C) {
+  return sizeof(float) * ((size_t)2 * nb * Mb      // panel block (re, im)
+                          + (size_t)4 * C * nb     // candidate rows, 2 parities
+                          + (size_t)4 * nb         // row j, 2 parities
+                          + (size_t)2 * C)         // candidate values
+         + sizeof(int) * (size_t)2 * C;            // candidate row indices
+}
+
 __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, float* Aim, long lda,
                                                                    int k0, int M, int nb, int Mb,
                                                                    int* ipiv, int* zero_col) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
-  const int csize = (int)cluster.num_blocks();
+  const int C = (int)cluster.num_blocks();
   extern __shared__ __align__(16) float pc_smem[];
-  float* sre = pc_smem;                   // [nb][Mb]
-  float* sim = pc_smem + (size_t)nb * Mb;
-  __shared__ float cand_v[kPcMaxCluster];
-  __shared__ int cand_i[kPcMaxCluster];
-  __shared__ float prow_r[kPcMaxNb], prow_i[kPcMaxNb], jrow_r[kPcMaxNb], jrow_i[kPcMaxNb];
+  float* sre = pc_smem;                        // [nb][Mb]
+  float* sim = sre + (size_t)nb * Mb;
+  float* tab_r = sim + (size_t)nb * Mb;        // [2][C][nb]
+  float* tab_i = tab_r + (size_t)2 * C * nb;
+  float* jrow_r = tab_i + (size_t)2 * C * nb;  // [2][nb]
+  float* jrow_i = jrow_r + 2 * nb;
+  float* cand_v = jrow_i + 2 * nb;             // [2][C]
+  int* cand_i = reinterpret_cast<int*>(cand_v + 2 * C);
   __shared__ float red_v[kPcThreads / 32];
   __shared__ int red_i[kPcThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -76,6 +93,7 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
   __syncthreads();
 
   for (int j = 0; j < nb; ++j) {
+    const int par = j & 1;
     // 1. local candidate
     float best = -1.f;
     int bi = INT_MAX;
@@ -103,44 +121,58 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
       red_i[warp] = bi;
     }
     __syncthreads();
-    if (tid < csize) {
-      float b = red_v[0];
-      int i = red_i[0];
-      for (int q = 1; q < kPcThreads / 32; ++q)
-        if (red_v[q] > b || (red_v[q] == b && red_i[q] < i)) {
-          b = red_v[q];
-          i = red_i[q];
+    best = red_v[0];
+    bi = red_i[0];
+#pragma unroll
+    for (int q = 1; q < kPcThreads / 32; ++q)
+      if (red_v[q] > best || (red_v[q] == best && red_i[q] < bi)) {
+        best = red_v[q];
+        bi = red_i[q];
+      }
+    // publish: value and index, the candidate row, and (CTA 0) row j
+    if (tid < nb) {
+      float vr = 0.f, vi = 0.f;
+      if (best >= 0.f) {
+        vr = sre[(size_t)tid * Mb + (bi - r0)];
+        vi = sim[(size_t)tid * Mb + (bi - r0)];
+      }
+      float wr = 0.f, wi = 0.f;
+      if (crank == 0) {
+        wr = sre[(size_t)tid * Mb + j];
+        wi = sim[(size_t)tid * Mb + j];
+      }
+      for (int q = 0; q < C; ++q) {
+        float* tr = cluster.map_shared_rank(tab_r, q);
+        float* ti = cluster.map_shared_rank(tab_i, q);
+        tr[((size_t)par * C + crank) * nb + tid] = vr;
+        ti[((size_t)par * C + crank) * nb + tid] = vi;
+        if (crank == 0) {
+          cluster.map_shared_rank(jrow_r, q)[par * nb + tid] = wr;
+          cluster.map_shared_rank(jrow_i, q)[par * nb + tid] = wi;
         }
-      float* rv = cluster.map_shared_rank(cand_v, tid);
-      int* ri = cluster.map_shared_rank(cand_i, tid);
-      rv[crank] = b;
-      ri[crank] = i;
+      }
+    }
+    if (tid < C) {
+      cluster.map_shared_rank(cand_v, tid)[par * C + crank] = best;
+      cluster.map_shared_rank(cand_i, tid)[par * C + crank] = bi;
     }
     cluster.sync();
 
-    // 2. the pivot (same in every CTA) and the rows to exchange
-    best = cand_v[0];
-    bi = cand_i[0];
-    for (int q = 1; q < csize; ++q)
-      if (cand_v[q] > best || (cand_v[q] == best && cand_i[q] < bi)) {
-        best = cand_v[q];
-        bi = cand_i[q];
-      }
-    const int p = bi;
-    const bool zero = !(best > 0.f) || p >= M;
-    const int op = zero ? 0 : p / Mb;
-    if (!zero && tid < nb) {
-      const float* ore = cluster.map_shared_rank(sre, op);
-      const float* oim = cluster.map_shared_rank(sim, op);
-      prow_r[tid] = ore[(size_t)tid * Mb + (p - op * Mb)];
-      prow_i[tid] = oim[(size_t)tid * Mb + (p - op * Mb)];
-      if (crank == op) {
-        const float* zre = cluster.map_shared_rank(sre, 0);
-        const float* zim = cluster.map_shared_rank(sim, 0);
-        jrow_r[tid] = zre[(size_t)tid * Mb + j];
-        jrow_i[tid] = zim[(size_t)tid * Mb + j];
+    // 2. the pivot (same in every CTA), pivot row and row j from the tables
+    int win = 0;
+    best = cand_v[par * C];
+    bi = cand_i[par * C];
+    for (int q = 1; q < C; ++q) {
+      const float ob = cand_v[par * C + q];
+      const int oi = cand_i[par * C + q];
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+        win = q;
       }
     }
+    const int p = bi;
+    const bool zero = !(best > 0.f) || p >= M;
     if (crank == 0 && tid == 0) {
       if (zero) {
         ipiv[k0 + j] = k0 + j;
@@ -149,8 +181,9 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
         ipiv[k0 + j] = k0 + p;
       }
     }
-    cluster.sync();  // every remote read of this column is done
-    if (zero) continue;
+    if (zero) continue;  // uniform across the cluster
+    const float* prow_r = tab_r + ((size_t)par * C + win) * nb;
+    const float* prow_i = tab_i + ((size_t)par * C + win) * nb;
 
     // 3. swap, scale, rank-1 update (local)
     if (tid < nb) {
@@ -158,9 +191,9 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
         sre[(size_t)tid * Mb + j] = prow_r[tid];
         sim[(size_t)tid * Mb + j] = prow_i[tid];
       }
-      if (crank == op && p != j) {
-        sre[(size_t)tid * Mb + (p - r0)] = jrow_r[tid];
-        sim[(size_t)tid * Mb + (p - r0)] = jrow_i[tid];
+      if (crank == win && p != j) {
+        sre[(size_t)tid * Mb + (p - r0)] = jrow_r[par * nb + tid];
+        sim[(size_t)tid * Mb + (p - r0)] = jrow_i[par * nb + tid];
       }
     }
     __syncthreads();
@@ -191,7 +224,7 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
       gre[r + (size_t)c * lda] = sre[(size_t)c * Mb + r];
       gim[r + (size_t)c * lda] = sim[(size_t)c * Mb + r];
     }
-  cluster.sync();  // no CTA leaves while others may still read its memory
+  cluster.sync();  // no CTA leaves while a peer may still write its tables
 }
 
 // Plan a cluster panel for M rows: returns the panel width to use (0 when
@@ -203,7 +236,7 @@ int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int*
       int mb = (M + C - 1) / C;
       if (mb < nb) mb = nb;
       if (C > 1 && (C - 1) * mb >= M) continue;  // every CTA owns rows
-      if ((size_t)2 * nb * mb * sizeof(float) <= budget) {
+      if (panel_smem_bytes(nb, mb, C) <= budget) {
         *csize = C;
         *Mb = mb;
         return nb;
@@ -215,7 +248,7 @@ int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int*
 
 int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
                   int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st) {
-  const size_t smem = (size_t)2 * nb * Mb * sizeof(float);
+  const size_t smem = panel_smem_bytes(nb, Mb, C);
   static bool attr_set = false;
   if (!attr_set) {
     HARP_CUDA(cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
