@@ -170,6 +170,13 @@ struct harp_ctx {
   cudaStream_t stream;
   float2* zbuf;
 
+  // Look-ahead LU: side stream for the trailing updates and event pools
+  // (panel factored / trailing update done), n_events each.
+  cudaStream_t side;
+  cudaEvent_t* ev_fac;
+  cudaEvent_t* ev_big;
+  int n_events;
+
   // Reductions and status.
   double* red;      // device scratch, 16 + 2*max_nrhs doubles
   double* red_host; // pinned host mirror, same size

@@ -39,6 +39,13 @@ static void free_all(harp_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->zbuf) cudaFree(c->zbuf);
+  if (c->side) cudaStreamDestroy(c->side);
+  for (int e = 0; e < c->n_events; ++e) {
+    if (c->ev_fac && c->ev_fac[e]) cudaEventDestroy(c->ev_fac[e]);
+    if (c->ev_big && c->ev_big[e]) cudaEventDestroy(c->ev_big[e]);
+  }
+  free(c->ev_fac);
+  free(c->ev_big);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->hstatus) cudaFreeHost(c->hstatus);
@@ -110,6 +117,17 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   alloc((void**)&c->dstatus, 4 * sizeof(int));
   alloc((void**)&c->zbuf, NN * sizeof(float2));
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+  if (ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+  if (ok) {
+    c->n_events = max_N / 16 + 2;
+    c->ev_fac = (cudaEvent_t*)calloc(c->n_events, sizeof(cudaEvent_t));
+    c->ev_big = (cudaEvent_t*)calloc(c->n_events, sizeof(cudaEvent_t));
+    if (!c->ev_fac || !c->ev_big) ok = false;
+    for (int e = 0; ok && e < c->n_events; ++e)
+      if (cudaEventCreateWithFlags(&c->ev_fac[e], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_big[e], cudaEventDisableTiming) != cudaSuccess)
+        ok = false;
+  }
   if (ok && cudaMallocHost((void**)&c->red_host, nred * sizeof(double)) != cudaSuccess) ok = false;
   if (ok && cudaMallocHost((void**)&c->hstatus, 4 * sizeof(int)) != cudaSuccess) ok = false;
   if (!ok) {

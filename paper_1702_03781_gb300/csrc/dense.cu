@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <climits>
 #include <type_traits>
+#include <vector>
 
 #include "dense.cuh"
 #include "prof.cuh"
@@ -713,6 +714,67 @@ static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld,
   return panel<R>(ctx, N, A, re, im, ld, k, want, ipiv, zero_col, mode, st);
 }
 
+// FP32 LU with a look-ahead of one panel. Main stream: the update of the
+// next panel's columns by the current panel (row swaps, U12, CUDA-core
+// GEMM), then the next panel's factorisation -- the critical path. Side
+// stream: the rest of the current panel's update (row swaps of the other
+// columns and of the permutation, U12 and the tensor-core GEMM of the far
+// trailing matrix), which overlaps the next panel. Events order the two:
+// the side stream starts a panel's update once that panel is factored, and
+// the main stream touches columns of panel i+2 only after panel i's far
+// update (which covers them) is done. Only the side stream uses the
+// tensor-core GEMM workspace.
+static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long ld, int* ipiv,
+                               int* perm, int* zero_col, int mode, cudaStream_t st) {
+  CView<float> A = planes<float>(re, im, ld);
+  cudaStream_t s2 = ctx->side;
+  std::vector<int> ks, nbs;
+  int k = 0, nb = 0;
+  HARP_TRY(factor_panel<float>(ctx, N, A, re, im, ld, 0, std::min(kNB, N), ipiv, zero_col, mode,
+                               st, &nb));
+  ks.push_back(0);
+  nbs.push_back(nb);
+  for (int i = 0;; ++i) {
+    if (i + 1 >= ctx->n_events) return HARP_E_UNSUPPORTED;
+    k = ks[i];
+    nb = nbs[i];
+    const int k1 = k + nb;  // first column after panel i
+    HARP_CUDA(cudaEventRecord(ctx->ev_fac[i], st));
+    // main stream: update and factor panel i+1
+    int nb1 = 0;
+    if (k1 < N) {
+      const int want = std::min(kNB, N - k1);
+      // the width of panel i+1 is only known after planning; plan it now
+      int C = 0, Mb = 0;
+      nb1 = panel_cluster_plan(ctx, N - k1, want, &C, &Mb);
+      if (nb1 <= 0) nb1 = want;
+      HARP_TRY(laswp<float>(re, im, ld, ipiv, k, k1, k1, k1 + nb1, 0, 0, nullptr, st));
+      HARP_TRY(trsm<float>(true, true, nb, nb1, A.sub(k, k), A.sub(k, k1), GEMM_SIMT, st));
+      HARP_TRY(cgemm<float>(N - k1, nb1, nb, -1.f, A.sub(k1, k), A.sub(k, k1), 1.f,
+                            A.sub(k1, k1), GEMM_SIMT, st));
+      int used = 0;
+      HARP_TRY(factor_panel<float>(ctx, N, A, re, im, ld, k1, nb1, ipiv, zero_col, mode, st,
+                                   &used));
+      nb1 = used;
+      ks.push_back(k1);
+      nbs.push_back(nb1);
+    }
+    // side stream: the rest of panel i's update
+    const int k2 = k1 + nb1;  // first column past panel i+1
+    HARP_CUDA(cudaStreamWaitEvent(s2, ctx->ev_fac[i], 0));
+    HARP_TRY(laswp<float>(re, im, ld, ipiv, k, k1, 0, k, k2, N, perm, s2));
+    if (k2 < N) {
+      HARP_TRY(trsm<float>(true, true, nb, N - k2, A.sub(k, k), A.sub(k, k2), mode, s2));
+      HARP_TRY(cgemm<float>(N - k1, N - k2, nb, -1.f, A.sub(k1, k), A.sub(k, k2), 1.f,
+                            A.sub(k1, k2), mode, s2));
+    }
+    HARP_CUDA(cudaEventRecord(ctx->ev_big[i], s2));
+    HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_big[i], 0));
+    if (k1 >= N) break;
+  }
+  return HARP_OK;
+}
+
 template <typename R>
 int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm, int* zero_col,
               int mode, cudaStream_t st) {
@@ -720,6 +782,10 @@ int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm,
     ProfScope ps_o(HARP_K_OTHER, 0.0, st);
     iota_kernel<<<(N + 255) / 256, 256, 0, st>>>(perm, N);
     HARP_LAUNCHED();
+  }
+  if constexpr (std::is_same<R, float>::value) {
+    if (ctx->side && mode != GEMM_SIMT)
+      return lu_factor_lookahead(ctx, N, re, im, ld, ipiv, perm, zero_col, mode, st);
   }
   CView<R> A = planes<R>(re, im, ld);
   for (int k = 0, nb = 0; k < N; k += nb) {

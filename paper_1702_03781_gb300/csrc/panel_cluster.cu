@@ -34,7 +34,7 @@ namespace cg = cooperative_groups;
 
 namespace harp {
 
-constexpr int kPcThreads = 256;
+constexpr int kPcThreads = 512;
 constexpr int kPcMaxNb = 64;
 constexpr int kPcMaxCluster = 16;
 
