@@ -170,6 +170,12 @@ struct harp_ctx {
   cudaStream_t stream;
   float2* zbuf;
 
+  // Captured graphs of the FP32 triangular solves of the refinement, keyed
+  // by (N, nrhs, mode) for trans 'N' [0] and 'T' [1]; replayed on the
+  // caller's stream.
+  cudaGraphExec_t solve_graph[2];
+  int solve_key[2][3];
+
   // Look-ahead LU: side stream for the trailing updates and event pools
   // (panel factored / trailing update done), n_events each.
   cudaStream_t side;

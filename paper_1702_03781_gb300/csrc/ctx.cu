@@ -38,6 +38,8 @@ static void free_all(harp_ctx* c) {
                   c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->gpair, c->red, c->dstatus};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int g = 0; g < 2; ++g)
+    if (c->solve_graph[g]) cudaGraphExecDestroy(c->solve_graph[g]);
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->side) cudaStreamDestroy(c->side);
   for (int e = 0; e < c->n_events; ++e) {

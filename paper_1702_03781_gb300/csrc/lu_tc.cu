@@ -414,7 +414,13 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   const size_t smem = (size_t)TC_STAGES * stage + 1024;
   void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
       three ? tc_cgemm_kernel<true> : tc_cgemm_kernel<false>;
-  HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  static bool attr_set[2] = {false, false};  // per instantiation, set once (also keeps
+                                             // the call out of captured graphs)
+  if (!attr_set[three ? 1 : 0]) {
+    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
+    attr_set[three ? 1 : 0] = true;
+  }
   dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
   ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K, st);
   kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);

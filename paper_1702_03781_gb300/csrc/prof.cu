@@ -53,6 +53,12 @@ ProfScope::~ProfScope() {
   }
 }
 
+// Whether any kernel class used by the triangular solves is being recorded
+// (their captured graph would hide the launches from the recorder).
+bool profiling_active() {
+  return (g_prof.mask & ((1u << HARP_K_GEMM) | (1u << HARP_K_TRSM) | (1u << HARP_K_OTHER))) != 0;
+}
+
 }  // namespace harp
 
 using namespace harp;

@@ -42,6 +42,56 @@ static int read_back(harp_ctx* c, int nd, cudaStream_t st) {
   return HARP_OK;
 }
 
+bool profiling_active();
+
+// The FP32 triangular solves of one refinement call: the first runs
+// directly; later ones replay a CUDA graph of the same sequence (captured
+// once per context and (N, nrhs, mode, trans), on the context's own stream,
+// and launched on the caller's stream). The graph reads the context's
+// buffers, which never move, so it stays valid across factorisations.
+static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool first,
+                   cudaStream_t st) {
+  const long ldw = ctx->max_N;
+  float* lre = (float*)ctx->lu_re;
+  float* lim = (float*)ctx->lu_im;
+  float* wre = (float*)ctx->w_re;
+  float* wim = (float*)ctx->w_im;
+  float* tre = (float*)ctx->t_re;
+  float* tim = (float*)ctx->t_im;
+  const float* dr = (const float*)ctx->dinv_re;
+  const float* di = (const float*)ctx->dinv_im;
+  const int g = (trans == 'T') ? 1 : 0;
+  const bool keyed = ctx->solve_graph[g] && ctx->solve_key[g][0] == N &&
+                     ctx->solve_key[g][1] == nrhs && ctx->solve_key[g][2] == mode;
+  if (profiling_active() || (first && !keyed))
+    return lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
+                           trans, dr, di, mode, st);
+  if (!keyed) {
+    if (ctx->solve_graph[g]) {
+      cudaGraphExecDestroy(ctx->solve_graph[g]);
+      ctx->solve_graph[g] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    HARP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int s = lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre,
+                                  tim, trans, dr, di, mode, ctx->stream);
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (s != HARP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    HARP_CUDA(e);
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->solve_graph[g], graph, 0);
+    cudaGraphDestroy(graph);
+    HARP_CUDA(ei);
+    ctx->solve_key[g][0] = N;
+    ctx->solve_key[g][1] = nrhs;
+    ctx->solve_key[g][2] = mode;
+  }
+  HARP_CUDA(cudaGraphLaunch(ctx->solve_graph[g], st));
+  return HARP_OK;
+}
+
 }  // namespace harp
 
 using namespace harp;
@@ -144,8 +194,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   const float* dinv_i = (const float*)ctx->dinv_im;
   HARP_TRY(load_rhs(ctx, N, nrhs, V, ldv, ctx->v_re, ctx->v_im, st));
   HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->v_re, ctx->v_im, ldw, wre, wim, ldw, st));
-  HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
-                           tr ? 'T' : 'N', dinv_r, dinv_i, mode, st));
+  HARP_TRY(solve32(ctx, N, nrhs, tr ? 'T' : 'N', mode, true, st));
   HARP_TRY(planes_to_planes<float, double>(N, nrhs, wre, wim, ldw, ctx->x_re, ctx->x_im, ldw, st));
 
   // ---- FP32: no refinement
@@ -206,8 +255,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     if (it >= max_iter) break;
     // D = (LU32)^{-1} R; X += D
     HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->r_re, ctx->r_im, ldw, wre, wim, ldw, st));
-    HARP_TRY(lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
-                             tr ? 'T' : 'N', dinv_r, dinv_i, mode, st));
+    HARP_TRY(solve32(ctx, N, nrhs, tr ? 'T' : 'N', mode, false, st));
     HARP_TRY(add_planes<float>(N, nrhs, ctx->x_re, ctx->x_im, ldw, wre, wim, ldw, st));
     // size of the correction against the iterate (host needs it to choose
     // the accumulator of the update)
