@@ -170,6 +170,12 @@ struct harp_ctx {
   cudaStream_t stream;
   float2* zbuf;
 
+  // Explicit inverses of the FP32 factors (L^-1, U^-1 planes, ld max_N) and
+  // scratch for building them; valid for the cached factorisation.
+  float* finv;  // 4 planes: Linv re, im, Uinv re, im
+  float* finv_tmp;  // 2 planes
+  int finv_valid;
+
   // Captured graphs of the FP32 triangular solves of the refinement, keyed
   // by (N, nrhs, mode) for trans 'N' [0] and 'T' [1]; replayed on the
   // caller's stream.

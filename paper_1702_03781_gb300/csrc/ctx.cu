@@ -35,7 +35,7 @@ extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launc
 
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
-                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->gpair, c->red, c->dstatus};
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->gpair, c->red, c->dstatus};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int g = 0; g < 2; ++g)
@@ -118,6 +118,8 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   alloc((void**)&c->red, nred * sizeof(double));
   alloc((void**)&c->dstatus, 4 * sizeof(int));
   alloc((void**)&c->zbuf, NN * sizeof(float2));
+  alloc((void**)&c->finv, 4 * NN * sizeof(float));
+  alloc((void**)&c->finv_tmp, 2 * NN * sizeof(float));
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok) {

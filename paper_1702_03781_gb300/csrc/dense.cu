@@ -821,6 +821,101 @@ __global__ void permute_rows_kernel(int N, int nrhs, const int* perm, const R* s
   }
 }
 
+// ---------------------------------------------------------------------------
+// Explicit inverses of the triangular factors (FP32 path), so that every
+// solve of the refinement is two dense products. Recursive on 64-aligned
+// halves: for lower T = [T11 0; T21 T22],
+//   inv(T) = [inv(T11) 0; -inv(T22) T21 inv(T11)  inv(T22)],
+// for upper T = [T11 T12; 0 T22],
+//   inv(T) = [inv(T11)  -inv(T11) T12 inv(T22); 0 inv(T22)],
+// the leaves being leading parts of the 64 x 64 block inverses.
+template <typename R>
+__global__ void copy_block_kernel(int n, const R* sre, const R* sim, long lds, R* dre, R* dim,
+                                  long ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n || j >= n) return;
+  dre[i + (size_t)j * ldd] = sre[i + (size_t)j * lds];
+  dim[i + (size_t)j * ldd] = sim[i + (size_t)j * lds];
+}
+
+template <typename R>
+static int tri_inv(bool lower, int n, CView<R> T, CView<R> Ti, CView<R> tmp, int row0,
+                   const R* dre, const R* dim, int mode, cudaStream_t st) {
+  if (n <= 0) return HARP_OK;
+  if (n <= kTrsmLeaf) {
+    const long off = (long)(row0 / kTrsmLeaf) * kTrsmLeaf * kTrsmLeaf;
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    copy_block_kernel<R><<<dim3(1, n), 64, 0, st>>>(n, dre + off, dim + off, kTrsmLeaf, Ti.re,
+                                                    Ti.im, Ti.cs);
+    HARP_LAUNCHED();
+    return HARP_OK;
+  }
+  const int n1 = ((n / 2) + kTrsmLeaf - 1) / kTrsmLeaf * kTrsmLeaf;
+  const int n2 = n - n1;
+  HARP_TRY(tri_inv<R>(lower, n1, T, Ti, tmp, row0, dre, dim, mode, st));
+  HARP_TRY(tri_inv<R>(lower, n2, T.sub(n1, n1), Ti.sub(n1, n1), tmp, row0 + n1, dre, dim, mode, st));
+  if (lower) {
+    // tmp (n2 x n1) = T21 inv(T11); inv21 = -inv(T22) tmp
+    HARP_TRY(cgemm<R>(n2, n1, n1, (R)1, T.sub(n1, 0), Ti, (R)0, tmp, mode, st));
+    HARP_TRY(cgemm<R>(n2, n1, n2, (R)-1, Ti.sub(n1, n1), tmp, (R)0, Ti.sub(n1, 0), mode, st));
+  } else {
+    // tmp (n1 x n2) = T12 inv(T22); inv12 = -inv(T11) tmp
+    HARP_TRY(cgemm<R>(n1, n2, n2, (R)1, T.sub(0, n1), Ti.sub(n1, n1), (R)0, tmp, mode, st));
+    HARP_TRY(cgemm<R>(n1, n2, n1, (R)-1, Ti, tmp, (R)0, Ti.sub(0, n1), mode, st));
+  }
+  return HARP_OK;
+}
+
+template <typename R>
+int factor_inverses(int N, CView<R> A, const R* dinv_re, const R* dinv_im, R* linv_re,
+                    R* linv_im, R* uinv_re, R* uinv_im, long ldi, R* tre, R* tim, int mode,
+                    cudaStream_t st) {
+  const long nblk = (N + kTrsmLeaf - 1) / kTrsmLeaf;
+  const long bs = (long)kTrsmLeaf * kTrsmLeaf;
+  for (R* p : {linv_re, linv_im, uinv_re, uinv_im})
+    HARP_CUDA(cudaMemsetAsync(p, 0, sizeof(R) * (size_t)ldi * N, st));
+  CView<R> tmp = planes<R>(tre, tim, ldi);
+  HARP_TRY(tri_inv<R>(true, N, A, planes<R>(linv_re, linv_im, ldi), tmp, 0, dinv_re, dinv_im,
+                      mode, st));
+  HARP_TRY(tri_inv<R>(false, N, A, planes<R>(uinv_re, uinv_im, ldi), tmp, 0, dinv_re + nblk * bs,
+                      dinv_im + nblk * bs, mode, st));
+  return HARP_OK;
+}
+
+// Solve op(A) X = B with the explicit factor inverses: two dense products
+// and the row permutation. B (N x nrhs planes, ld ldb) is overwritten; tmp
+// has room for N x nrhs.
+template <typename R>
+int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,
+                 const R* uinv_im, long ldi, const int* perm, R* bre, R* bim, long ldb, R* tre,
+                 R* tim, char trans, int mode, cudaStream_t st) {
+  CView<R> Li = planes<R>(const_cast<R*>(linv_re), const_cast<R*>(linv_im), ldi);
+  CView<R> Ui = planes<R>(const_cast<R*>(uinv_re), const_cast<R*>(uinv_im), ldi);
+  CView<R> Bm = planes<R>(bre, bim, ldb), Tm = planes<R>(tre, tim, ldb);
+  dim3 grid((N + 255) / 256, nrhs);
+  if (trans == 'N' || trans == 'n') {
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 0);
+      HARP_LAUNCHED();
+    }
+    HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Li, Tm, (R)0, Bm, mode, st));  // B = L^-1 P b
+    HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Ui, Bm, (R)0, Tm, mode, st));  // T = U^-1 B
+    HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));
+  } else {
+    HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Ui.t(), Bm, (R)0, Tm, mode, st));  // T = U^-T b
+    HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Li.t(), Tm, (R)0, Bm, mode, st));  // B = L^-T T
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 1);
+      HARP_LAUNCHED();
+    }
+    HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));
+  }
+  return HARP_OK;
+}
+
 template <typename R>
 int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, R* bim, long ldb,
              R* tre, R* tim, char trans, const R* dinv_re, const R* dinv_im, int mode,
@@ -994,6 +1089,11 @@ template int lu_solve<double>(int, int, double*, double*, long, const int*, doub
                               double*, double*, char, const double*, const double*, int,
                               cudaStream_t);
 template int diag_inverses<float>(int, CView<float>, float*, float*, float*, float*, cudaStream_t);
+template int factor_inverses<float>(int, CView<float>, const float*, const float*, float*, float*,
+                                    float*, float*, long, float*, float*, int, cudaStream_t);
+template int lu_solve_inv<float>(int, int, const float*, const float*, const float*, const float*,
+                                 long, const int*, float*, float*, long, float*, float*, char, int,
+                                 cudaStream_t);
 template int diag_inverses<double>(int, CView<double>, double*, double*, double*, double*,
                                    cudaStream_t);
 template int interleaved_to_planes<float, float>(int, int, const float*, long, float*, float*, long,

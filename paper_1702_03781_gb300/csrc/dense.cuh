@@ -67,6 +67,19 @@ int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm,
 template <typename R>
 int diag_inverses(int N, CView<R> A, R* lre, R* lim, R* ure, R* uim, cudaStream_t st);
 
+// Explicit inverses of the factors held in A (FP32 path): L^-1 and U^-1 as
+// planes (ld ldi), built from the diagonal-block inverses; t planes are
+// scratch of ldi x N.
+template <typename R>
+int factor_inverses(int N, CView<R> A, const R* dinv_re, const R* dinv_im, R* linv_re,
+                    R* linv_im, R* uinv_re, R* uinv_im, long ldi, R* tre, R* tim, int mode,
+                    cudaStream_t st);
+// Solve op(A) X = B with the explicit factor inverses (two products).
+template <typename R>
+int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,
+                 const R* uinv_im, long ldi, const int* perm, R* bre, R* bim, long ldb, R* tre,
+                 R* tim, char trans, int mode, cudaStream_t st);
+
 // Solve op(A) X = B with the factors of lu_factor and their diagonal-block
 // inverses (dinv planes: the L blocks, then the U blocks); B (N x nrhs split
 // planes, leading dimension ldb) is overwritten. tmp has room for N x nrhs

@@ -63,9 +63,17 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
   const int g = (trans == 'T') ? 1 : 0;
   const bool keyed = ctx->solve_graph[g] && ctx->solve_key[g][0] == N &&
                      ctx->solve_key[g][1] == nrhs && ctx->solve_key[g][2] == mode;
-  if (profiling_active() || (first && !keyed))
-    return lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre, tim,
-                           trans, dr, di, mode, st);
+  const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+  const float* fi = ctx->finv;
+  auto run = [&](cudaStream_t s) {
+    return lu_solve_inv<float>(N, nrhs, fi, fi + NN, fi + 2 * NN, fi + 3 * NN, ctx->max_N,
+                               ctx->perm, wre, wim, ldw, tre, tim, trans, mode, s);
+  };
+  (void)lre;
+  (void)lim;
+  (void)dr;
+  (void)di;
+  if (profiling_active() || (first && !keyed)) return run(st);
   if (!keyed) {
     if (ctx->solve_graph[g]) {
       cudaGraphExecDestroy(ctx->solve_graph[g]);
@@ -73,8 +81,7 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
     }
     cudaGraph_t graph = nullptr;
     HARP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    const int s = lu_solve<float>(N, nrhs, lre, lim, ctx->ld_lu, ctx->perm, wre, wim, ldw, tre,
-                                  tim, trans, dr, di, mode, ctx->stream);
+    const int s = run(ctx->stream);
     const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
     if (s != HARP_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -158,6 +165,11 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       float* di = (float*)ctx->dinv_im;
       HARP_TRY(diag_inverses<float>(N, planes<float>(re, im, ctx->ld_lu), dr, di, dr + nb, di + nb,
                                     st));
+      const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+      float* fi = ctx->finv;
+      HARP_TRY(factor_inverses<float>(N, planes<float>(re, im, ctx->ld_lu), dr, di, fi, fi + NN,
+                                      fi + 2 * NN, fi + 3 * NN, ctx->max_N, ctx->finv_tmp,
+                                      ctx->finv_tmp + NN, mode, st));
     }
     HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, 2 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));
