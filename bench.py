@@ -32,10 +32,10 @@ WORKLOAD = "SKA-like station: 256 antennas in a 38 m disc (min sep 1.5 m), 12 MB
 
 # Arithmetic each kernel class runs on in the mixed step (roofline bound).
 IMPL = {"fill": "ff", "gemm": "tensor_tf32", "residual": "ff", "panel": "fp32", "trsm": "fp32",
-        "swap": "fp32", "adjoint": "fp32", "other": "fp32"}
+        "swap": "fp32", "adjoint": "fp32", "other": "fp32", "resid_update": "ff2"}
 # Kernel classes that do the step's arithmetic (the others are latency-bound
 # glue: pivot search, row swaps, conversions).
-COMPUTE_KINDS = ("fill", "gemm", "residual")
+COMPUTE_KINDS = ("fill", "gemm", "residual", "resid_update")
 
 
 def _dist():

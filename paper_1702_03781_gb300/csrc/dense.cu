@@ -290,111 +290,121 @@ __global__ void __launch_bounds__(kLeafThreads) lu_leaf_kernel(R* Are, R* Aim, l
 }
 
 // Apply the row swaps ipiv[k1..k2) (in order, k2 - k1 <= kNB) to the columns
-// [a0, a1) and [b0, b1), one thread per column, and to perm (as one more
-// column) when perm != nullptr. The rows touched (the contiguous range
-// k1..k2 and the distinct pivot rows below it) are loaded into shared
-// memory first, all loads independent; the swaps then run in shared memory
-// and the rows are written back. A pivot row met several times shares one
-// slot (its first occurrence).
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) laswp_kernel(R* Are, R* Aim, long lda, const int* ipiv,
-                                                   int k1, int k2, int a0, int a1, int b0, int b1,
-                                                   int* perm) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int piv[kNB], slot[kNB], segp[kNB], tgtp[kNB];
+// [a0, a1) and [b0, b1), and to perm (as one more column of ints) when perm
+// != nullptr. Each CTA first composes the swaps into the net permutation of
+// the touched rows (rows k1..k2 and the distinct pivot rows below them, at
+// most 2*kNB): warp 0 runs the swaps on row labels in shared memory. A pivot
+// outside [k1 + u, nrows) (left unset by a panel that gave up) is taken as
+// no swap, so every access stays inside the nrows x lda matrix.
+// Every column is then a gather by one warp -- all loads of the touched rows
+// (from their source rows) before all stores -- with no dependency chain.
+constexpr int kSwapWarps = 8;
+template <typename R>
+__global__ void __launch_bounds__(kSwapWarps * 32) laswp_kernel(R* Are, R* Aim, long lda,
+                                                                int nrows, const int* ipiv, int k1,
+                                                                int k2, int a0, int a1, int b0,
+                                                                int b1, int* perm) {
+  __shared__ int piv[kNB], row[2 * kNB], src[2 * kNB], nt_s;
   const int nsw = k2 - k1;
-  R* seg_r = reinterpret_cast<R*>(smem_raw);  // [nsw][NT]
-  R* seg_i = seg_r + (size_t)nsw * NT;
-  R* tgt_r = seg_i + (size_t)nsw * NT;        // [nsw][NT], slot t for first occurrences
-  R* tgt_i = tgt_r + (size_t)nsw * NT;
-  const int tid = threadIdx.x;
-  if (tid < nsw) piv[tid] = ipiv[k1 + tid];
-  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < nsw) {
-    const int p = piv[tid];
-    int sl = -1;
-    if (p >= k2) {
-      sl = tid;
-      for (int u = 0; u < tid; ++u)
-        if (piv[u] == p) {
-          sl = u;
-          break;
-        }
-    }
-    slot[tid] = sl;
+    const int p = ipiv[k1 + tid];
+    piv[tid] = (p >= k1 + tid && p < nrows) ? p : k1 + tid;
   }
   __syncthreads();
+  if (warp == 0) {
+    // slots 0..nsw-1: rows k1..k2-1; then one slot per distinct pivot row >= k2
+    for (int u = lane; u < nsw; u += 32) {
+      row[u] = k1 + u;
+      src[u] = k1 + u;
+    }
+    __syncwarp();
+    int nt = nsw;
+    for (int u = 0; u < nsw; ++u) {
+      const int p = piv[u];
+      int sl = -1;
+      if (p < k2) {
+        sl = p - k1;
+      } else {
+        for (int v0 = nsw; v0 < nt && sl < 0; v0 += 32) {
+          const int v = v0 + lane;
+          const unsigned hit = __ballot_sync(0xffffffffu, v < nt && row[v] == p);
+          if (hit) sl = v0 + __ffs(hit) - 1;
+        }
+        if (sl < 0) {
+          sl = nt++;
+          if (lane == 0) {
+            row[sl] = p;
+            src[sl] = p;
+          }
+        }
+      }
+      // run swap u on the labels: afterwards slot v holds original row src[v]
+      if (lane == 0 && sl != u) {
+        const int t = src[u];
+        src[u] = src[sl];
+        src[sl] = t;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) nt_s = nt;
+  }
+  __syncthreads();
+  const int nt = nt_s;
   const int na = a1 - a0, nb = b1 - b0;
-  const int t = blockIdx.x * NT + tid;
-  if (t < na + nb) {
-    const int col = (t < na) ? a0 + t : b0 + (t - na);
-    R* cr = Are + (size_t)col * lda;
-    R* ci = Aim + (size_t)col * lda;
-#pragma unroll 8
-    for (int u = 0; u < nsw; ++u) {
-      seg_r[u * NT + tid] = cr[k1 + u];
-      seg_i[u * NT + tid] = ci[k1 + u];
-      if (slot[u] == u) {
-        tgt_r[u * NT + tid] = cr[piv[u]];
-        tgt_i[u * NT + tid] = ci[piv[u]];
+  const int ncols = na + nb + (perm ? 1 : 0);
+  for (int c = blockIdx.x * kSwapWarps + warp; c < ncols; c += gridDim.x * kSwapWarps) {
+    constexpr int kPer = (2 * kNB + 31) / 32;
+    if (c < na + nb) {
+      const int col = (c < na) ? a0 + c : b0 + (c - na);
+      R* cr = Are + (size_t)col * lda;
+      R* ci = Aim + (size_t)col * lda;
+      R vr[kPer], vi[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) {
+          vr[q] = cr[src[t]];
+          vi[q] = ci[src[t]];
+        }
       }
-    }
-    for (int u = 0; u < nsw; ++u) {
-      const int p = piv[u];
-      if (p == k1 + u) continue;
-      R* xr = (p < k2) ? &seg_r[(p - k1) * NT + tid] : &tgt_r[slot[u] * NT + tid];
-      R* xi = (p < k2) ? &seg_i[(p - k1) * NT + tid] : &tgt_i[slot[u] * NT + tid];
-      const R sr = seg_r[u * NT + tid], si = seg_i[u * NT + tid];
-      seg_r[u * NT + tid] = *xr;
-      seg_i[u * NT + tid] = *xi;
-      *xr = sr;
-      *xi = si;
-    }
-    for (int u = 0; u < nsw; ++u) {
-      cr[k1 + u] = seg_r[u * NT + tid];
-      ci[k1 + u] = seg_i[u * NT + tid];
-      if (slot[u] == u) {
-        cr[piv[u]] = tgt_r[u * NT + tid];
-        ci[piv[u]] = tgt_i[u * NT + tid];
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) {
+          cr[row[t]] = vr[q];
+          ci[row[t]] = vi[q];
+        }
       }
-    }
-  } else if (t == na + nb && perm) {
-    for (int u = 0; u < nsw; ++u) {
-      segp[u] = perm[k1 + u];
-      if (slot[u] == u) tgtp[u] = perm[piv[u]];
-    }
-    for (int u = 0; u < nsw; ++u) {
-      const int p = piv[u];
-      if (p == k1 + u) continue;
-      int* x = (p < k2) ? &segp[p - k1] : &tgtp[slot[u]];
-      const int sv = segp[u];
-      segp[u] = *x;
-      *x = sv;
-    }
-    for (int u = 0; u < nsw; ++u) {
-      perm[k1 + u] = segp[u];
-      if (slot[u] == u) perm[piv[u]] = tgtp[u];
+    } else {
+      int v[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) v[q] = perm[src[t]];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) perm[row[t]] = v[q];
+      }
     }
   }
 }
 
 template <typename R>
-static int laswp(R* re, R* im, long ld, const int* ipiv, int k1, int k2, int a0, int a1, int b0,
-                 int b1, int* perm, cudaStream_t st) {
+static int laswp(R* re, R* im, long ld, int nrows, const int* ipiv, int k1, int k2, int a0, int a1,
+                 int b0, int b1, int* perm, cudaStream_t st) {
   const int n = std::max(0, a1 - a0) + std::max(0, b1 - b0) + (perm ? 1 : 0);
   if (n == 0 || k2 <= k1) return HARP_OK;
-  if (k2 - k1 > kNB) return HARP_E_UNSUPPORTED;
-  constexpr int NT = (sizeof(R) == 4) ? 128 : 64;
-  const size_t smem = (size_t)4 * (k2 - k1) * NT * sizeof(R);
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    HARP_CUDA(cudaFuncSetAttribute(laswp_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)((size_t)4 * kNB * NT * sizeof(R))));
-    attr_set = true;
-  }
+  if (k2 - k1 > kNB || k2 > nrows || k1 < 0) return HARP_E_UNSUPPORTED;
+  const int blocks = std::min((n + kSwapWarps - 1) / kSwapWarps, 4 * 152);
   ProfScope ps(HARP_K_SWAP, 0.0, st);
-  laswp_kernel<R, NT><<<(n + NT - 1) / NT, NT, smem, st>>>(
-      re, im, ld, ipiv, k1, k2, a0, std::max(a0, a1), b0, std::max(b0, b1), perm);
+  laswp_kernel<R><<<blocks, kSwapWarps * 32, 0, st>>>(re, im, ld, nrows, ipiv, k1, k2, a0,
+                                                      std::max(a0, a1), b0, std::max(b0, b1),
+                                                      perm);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -679,12 +689,12 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
   }
   const int w1 = w / 2, w2 = w - w1;
   HARP_TRY(panel<R>(ctx, N, A, re, im, ld, j0, w1, ipiv, zero_col, mode, st));
-  HARP_TRY(laswp<R>(re, im, ld, ipiv, j0, j0 + w1, j0 + w1, j0 + w, 0, 0, nullptr, st));
+  HARP_TRY(laswp<R>(re, im, ld, N, ipiv, j0, j0 + w1, j0 + w1, j0 + w, 0, 0, nullptr, st));
   HARP_TRY(trsm<R>(true, true, w1, w2, A.sub(j0, j0), A.sub(j0, j0 + w1), mode, st));
   HARP_TRY(cgemm<R>(M - w1, w2, w1, (R)-1, A.sub(j0 + w1, j0), A.sub(j0, j0 + w1), (R)1,
                     A.sub(j0 + w1, j0 + w1), mode, st));
   HARP_TRY(panel<R>(ctx, N, A, re, im, ld, j0 + w1, w2, ipiv, zero_col, mode, st));
-  HARP_TRY(laswp<R>(re, im, ld, ipiv, j0 + w1, j0 + w, j0, j0 + w1, 0, 0, nullptr, st));
+  HARP_TRY(laswp<R>(re, im, ld, N, ipiv, j0 + w1, j0 + w, j0, j0 + w1, 0, 0, nullptr, st));
   return HARP_OK;
 }
 
@@ -748,7 +758,7 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
       int C = 0, Mb = 0;
       nb1 = panel_cluster_plan(ctx, N - k1, want, &C, &Mb);
       if (nb1 <= 0) nb1 = want;
-      HARP_TRY(laswp<float>(re, im, ld, ipiv, k, k1, k1, k1 + nb1, 0, 0, nullptr, st));
+      HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, k1, k1 + nb1, 0, 0, nullptr, st));
       HARP_TRY(trsm<float>(true, true, nb, nb1, A.sub(k, k), A.sub(k, k1), GEMM_SIMT, st));
       HARP_TRY(cgemm<float>(N - k1, nb1, nb, -1.f, A.sub(k1, k), A.sub(k, k1), 1.f,
                             A.sub(k1, k1), GEMM_SIMT, st));
@@ -762,7 +772,7 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
     // side stream: the rest of panel i's update
     const int k2 = k1 + nb1;  // first column past panel i+1
     HARP_CUDA(cudaStreamWaitEvent(s2, ctx->ev_fac[i], 0));
-    HARP_TRY(laswp<float>(re, im, ld, ipiv, k, k1, 0, k, k2, N, perm, s2));
+    HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, 0, k, k2, N, perm, s2));
     if (k2 < N) {
       HARP_TRY(trsm<float>(true, true, nb, N - k2, A.sub(k, k), A.sub(k, k2), mode, s2));
       HARP_TRY(cgemm<float>(N - k1, N - k2, nb, -1.f, A.sub(k1, k), A.sub(k, k2), 1.f,
@@ -791,7 +801,7 @@ int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm,
   for (int k = 0, nb = 0; k < N; k += nb) {
     HARP_TRY(factor_panel<R>(ctx, N, A, re, im, ld, k, std::min(kNB, N - k), ipiv, zero_col, mode,
                              st, &nb));
-    HARP_TRY(laswp<R>(re, im, ld, ipiv, k, k + nb, 0, k, k + nb, N, perm, st));
+    HARP_TRY(laswp<R>(re, im, ld, N, ipiv, k, k + nb, 0, k, k + nb, N, perm, st));
     if (k + nb < N) {
       HARP_TRY(trsm<R>(true, true, nb, N - k - nb, A.sub(k, k), A.sub(k, k + nb), mode, st));
       HARP_TRY(cgemm<R>(N - k - nb, N - k - nb, nb, (R)-1, A.sub(k + nb, k), A.sub(k, k + nb), (R)1,

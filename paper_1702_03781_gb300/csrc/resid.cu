@@ -312,7 +312,7 @@ int residual_ff(int N, int nrhs, const float* const A[4], long ars, long acs,
   dim3 grid((nrhs + kRBN - 1) / kRBN, (N + kRBM - 1) / kRBM, ks);
   const long pstride = (long)ldr * nrhs;
   {
-    ProfScope ps(HARP_K_RESIDUAL, 8.0 * N * (double)N * nrhs, st);
+    ProfScope ps(fff ? HARP_K_RESIDUAL : HARP_K_RESID_UPDATE, 8.0 * N * (double)N * nrhs, st);
     auto kern = fff ? resid_ff_kernel<true> : resid_ff_kernel<false>;
     kern<<<grid, 256, 0, st>>>(N, nrhs, A[0], A[1], A[2], A[3], ars, acs, B[0], B[1], B[2], B[3],
                                ldb, vr, vi, rr, ri, ldr, kchunk, pr, pi, pstride);

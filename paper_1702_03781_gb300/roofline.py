@@ -18,8 +18,8 @@ import hashlib
 import json
 import os
 
-KINDS = ["fill", "gemm", "residual", "panel", "trsm", "swap", "adjoint", "other"]
-N_KINDS = 8
+KINDS = ["fill", "gemm", "residual", "panel", "trsm", "swap", "adjoint", "other", "resid_update"]
+N_KINDS = 9
 SMS = 152
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = 2 * 128 * SMS * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
@@ -30,6 +30,10 @@ FP64_PEAK_TFLOPS = 2 * 2 * SMS * SM_MAX_MHZ * 1e6 / 1e12     # 1.259
 # clock per SM.
 FF_INSTR_PER_CMAC = 96
 FF_PEAK_TFLOPS = 128 * SMS * SM_MAX_MHZ * 1e6 * 8 / FF_INSTR_PER_CMAC / 1e12   # 3.357
+# Double-float (Dot2) residual updates: 4 compensated real products of 12
+# instructions, 48 per complex multiply-add.
+FF2_INSTR_PER_CMAC = 48
+FF2_PEAK_TFLOPS = 128 * SMS * SM_MAX_MHZ * 1e6 * 8 / FF2_INSTR_PER_CMAC / 1e12  # 6.714
 TF32_OVER_BF16 = 1.1 / 2.25
 
 _ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -59,7 +63,8 @@ def source_hash(kind: str) -> str:
     """Hash of the sources a kernel class is built from (traffic validity)."""
     files = {"fill": ["fill.cu", "ff.cuh"], "gemm": ["lu_tc.cu"], "residual": ["resid.cu", "ff.cuh"],
              "panel": ["panel_cluster.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
-             "adjoint": ["adjoint.cu"], "other": ["dense.cu"]}.get(kind, [])
+             "adjoint": ["adjoint.cu"], "other": ["dense.cu"],
+             "resid_update": ["resid.cu", "ff.cuh"]}.get(kind, [])
     h = hashlib.sha256()
     for f in files:
         p = os.path.join(_ROOT, "paper_1702_03781_gb300", "csrc", f)
@@ -77,6 +82,10 @@ def peak_for(kind: str, impl: str, peaks: dict):
         return "tensor", 1900.0 * TF32_OVER_BF16, "TFLOP/s", "fallback bf16 1.9 PF x 1.1/2.25 (TF32)"
     if impl == "fp32":
         return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 FMA pipe: 128 FMA/clk/SM x 152 SMs x 2070 MHz"
+    if impl == "ff2":
+        return ("alu", FF2_PEAK_TFLOPS, "TFLOP/s",
+                "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 48 instr per complex MAC "
+                "(double-float Dot2)")
     if impl == "ff":
         return ("alu", FF_PEAK_TFLOPS, "TFLOP/s",
                 "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 96 instr per complex MAC "
