@@ -157,6 +157,40 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
               double* X, int ldx, char trans, int prec, double tol, int max_iter, int* iters_out,
               double* resid_out, void* stream);
 
+/* ---- Refinement residual ---------------------------------------------------
+ * A building block of the mixed solve, exported so that it can be checked on
+ * its own (the paper has no counterpart: it solves in one precision).
+ *
+ * How the mixed modes form R = V - Z64 X (option HARP_OPT_RESIDUAL):
+ *   HARP_RESIDUAL_SLICES  tensor cores: Z64 and the FP32 right-hand side are
+ *                         cut into exact bf16 integer digits after a
+ *                         power-of-two scaling per row (column); every
+ *                         digit product is exact in the FP32 accumulator and
+ *                         the products are combined in FP64 (the default
+ *                         where the context could allocate its buffers)
+ *   HARP_RESIDUAL_FF      FP32 pipe: float-float products with a three-float
+ *                         accumulator (FP64-accurate)
+ * harp_ctx_set_option returns HARP_E_UNSUPPORTED for SLICES when the context
+ * has no buffers for it; harp_ctx_get_option reports the method in use. */
+#define HARP_OPT_RESIDUAL 1
+#define HARP_RESIDUAL_SLICES 0
+#define HARP_RESIDUAL_FF 1
+int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
+int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
+
+/* R = V - op(Z) X with the context's residual method.
+ *   Z, ldz       c128 N x N (device, column-major), N <= max_N   [2, 3, 4]
+ *   X, ldx       c64 N x nrhs: the FP32 right-hand side           [5, 6]
+ *   V, ldv       c128 N x nrhs                                    [7, 8]
+ *   nrhs         <= max_nrhs                                      [9]
+ *   R, ldr       c128 N x nrhs output (may not alias Z, X, V)     [10, 11]
+ *   trans        'N' (op(Z) = Z) or 'T' (op(Z) = Z^T)             [12]
+ * Device pointers; work runs on `stream` and uses the context's solve
+ * buffers (not concurrently with a solve on the same context). */
+int harp_residual(harp_ctx* ctx, int N, const double* Z, int ldz, const float* X, int ldx,
+                  const double* V, int ldv, int nrhs, double* R, int ldr, char trans,
+                  void* stream);
+
 /* Position gradient of a real objective J(X) of the solution of Z X = V:
  *   grad[m] = -2 Re sum over pairs (m, n) and (n, m) of
  *             sum_TS G_TS dZ_TS/dx_m,       G = Lambda X^T,

@@ -189,6 +189,25 @@ struct harp_ctx {
   cudaEvent_t* ev_big;
   int n_events;
 
+  // Tensor-core refinement residual (ozaki.cu), allocated when memory
+  // allows (oz_a == nullptr: the float-float residual is used): bf16 digit
+  // planes of op(Z) (2 * oz_max_slices planes of Np x Kp) and of the FP32
+  // right-hand side (2 * oz_max_slices planes of roundup(max_nrhs, 64) x Kp),
+  // integer pair results (oz_slot_pairs x 2 x max_N x max_nrhs), FP64 Horner
+  // accumulators (2 x max_N x max_nrhs), row / column exponents, row-sum
+  // partials; then the state of the last oz_prepare.
+  void* oz_a;
+  void* oz_y;
+  int* oz_slots;
+  int oz_slot_pairs;
+  int oz_max_slices;
+  double* oz_acc;
+  int* oz_rexp;
+  int* oz_cexp;
+  double* oz_part;
+  int oz_N, oz_bits, oz_slices, oz_Kp, oz_Np;
+  int residual_mode;  // HARP_RESIDUAL_*
+
   // Reductions and status.
   double* red;      // device scratch, 16 + 2*max_nrhs doubles
   double* red_host; // pinned host mirror, same size

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace harp {
 int g_last_cuda_error = 0;
@@ -35,7 +36,8 @@ extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launc
 
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
-                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->gpair, c->red, c->dstatus};
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->gpair, c->red, c->dstatus,
+                  c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int g = 0; g < 2; ++g)
@@ -120,6 +122,43 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   alloc((void**)&c->zbuf, NN * sizeof(float2));
   alloc((void**)&c->finv, 4 * NN * sizeof(float));
   alloc((void**)&c->finv_tmp, 2 * NN * sizeof(float));
+  if (ok) {
+    // Tensor-core residual buffers: optional (the float-float residual
+    // serves when they do not fit).
+    const int S = oz_groups(max_N, oz_digit_bits(max_N), 1.0) - 1;
+    const size_t kp = ((size_t)max_N + 63) / 64 * 64, np = ((size_t)max_N + 127) / 128 * 128;
+    const size_t rp = ((size_t)max_nrhs + 63) / 64 * 64;
+    const size_t per_pair = 2 * NR * sizeof(int);
+    int slots = (int)std::min<size_t>(oz_pairs(S + 1), std::max<size_t>(S, (1536u << 20) / per_pair));
+    bool oz_ok = true;
+    auto oalloc = [&](void** p, size_t bytes) {
+      if (!oz_ok) return;
+      if (cudaMalloc(p, bytes) != cudaSuccess) {
+        oz_ok = false;
+        cudaGetLastError();
+      }
+    };
+    oalloc(&c->oz_a, 2 * (size_t)S * np * kp * 2);
+    oalloc(&c->oz_y, 2 * (size_t)S * rp * kp * 2);
+    oalloc((void**)&c->oz_slots, (size_t)slots * per_pair);
+    oalloc((void**)&c->oz_acc, 2 * NR * sizeof(double));
+    oalloc((void**)&c->oz_rexp, (size_t)max_N * sizeof(int));
+    oalloc((void**)&c->oz_cexp, (size_t)max_nrhs * sizeof(int));
+    oalloc((void**)&c->oz_part, 32 * (size_t)max_N * sizeof(double));
+    if (oz_ok) {
+      c->oz_max_slices = S;
+      c->oz_slot_pairs = slots;
+    } else {
+      void* op[] = {c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part};
+      for (void* p : op)
+        if (p) cudaFree(p);
+      c->oz_a = c->oz_y = nullptr;
+      c->oz_slots = c->oz_rexp = c->oz_cexp = nullptr;
+      c->oz_acc = c->oz_part = nullptr;
+    }
+    c->oz_N = -1;
+    c->residual_mode = HARP_RESIDUAL_SLICES;
+  }
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok) {

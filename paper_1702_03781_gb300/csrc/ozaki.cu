@@ -1,0 +1,687 @@
+// ozaki.cu -- FP64-accurate refinement residual on the tensor cores by exact
+// integer slices (Ozaki's error-free splitting of a matrix product):
+//
+//   R = S - op(Z) Y,   Z: N x N FP64 (the context's matrix), Y: N x nrhs FP32
+//   (the FP32 solution X_0 or a correction D_k), S = V or the previous R.
+//
+// Scaling and slices. Each row i of A = op(Z) is scaled by 2^-sig_i so that
+// its largest real or imaginary part is below 1/2, each column j of Y by
+// 2^-tau_j likewise, and the scaled values are cut into signed base-2^b
+// digits by repeated round-to-nearest (all steps exact in FP64):
+//   a_ik = 2^sig_i sum_t d_t[i,k] 2^-bt,   y_kj = 2^tau_j sum_u e_u[k,j] 2^-bu,
+// with |d|, |e| <= 2^(b-1), so every digit is an integer exact in bf16.
+//
+// Exact products. For one slice pair (t, u) the four real products
+// Re(d_t) Re(e_u), Re(d_t) Im(e_u), Im(d_t) Re(e_u), Im(d_t) Im(e_u) are
+// sums over K of integer products of magnitude <= 2^(2b-2); b is the
+// largest width with K 2^(2b-2) <= 2^24, so every partial sum is an integer
+// an FP32 accumulator holds exactly, and the bf16 tcgen05 product with FP32
+// accumulation (kind::f16) is exact. Two MMAs per 16-deep K step produce all
+// four: A_re x [Y_re | Y_im] and A_im x [Y_re | Y_im] (N = 2 x 64 columns).
+//
+// Combination. The pair results of one group g = t + u share the weight
+// 2^-bg; they are added exactly in integers (re = rr - ii, im = ri + ir),
+// and the groups are combined in FP64 by Horner's rule from the smallest
+// weight up, then scaled back by 2^(sig_i + tau_j). Only the pairs with
+// t + u <= G are formed; oz_groups picks G from the accuracy the caller
+// needs (the dropped groups are below the FP64 rounding of the result).
+//
+// Kernels: oz_rowexp (row exponents and row sums of |re| + |im| for the
+// stopping test, one pass over Z), oz_slice_a (digits of op(Z), K-major),
+// oz_colexp_y / oz_slice_y (digits of Y), oz_mma (one CTA per 128 x 64
+// output tile and slice pair; TMA into a two-stage ring, tcgen05.mma by one
+// thread, integer pair results written out), oz_combine (groups -> FP64).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "dense.cuh"
+#include "ozaki.cuh"
+#include "prof.cuh"
+
+namespace harp {
+
+constexpr int OZ_BM = 128;  // output rows per CTA (TMEM lanes)
+constexpr int OZ_BN = 64;   // output columns per CTA
+constexpr int OZ_BK = 64;   // K per stage: one 128-byte swizzle atom of bf16
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_A_PLANE = OZ_BM * OZ_BK * 2;  // 16 KB
+constexpr int OZ_B_PLANE = OZ_BN * OZ_BK * 2;  //  8 KB
+constexpr int OZ_STAGE = 2 * OZ_A_PLANE + 2 * OZ_B_PLANE;
+constexpr int OZ_KCH = 32;  // K chunks of the row-exponent pass
+constexpr long long OZ_WAIT_CYCLES = 1LL << 30;  // ~0.5 s at 2 GHz
+// Exponent of an all-zero row or column: any value below kOzNone (real
+// exponents are above -1100); the row pass starts from a byte-filled
+// 0x80808080.
+constexpr int OZ_NOEXP = INT_MIN;
+constexpr int kOzNone = -4000;
+__host__ __device__ __forceinline__ bool oz_none(int e) { return e < kOzNone; }
+
+// Exponent e with |v| < 2^e (v != 0), from the bits (no libm).
+__device__ __forceinline__ int exp_above(double v) {
+  const int eb = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+  return (eb == 0 ? 1 : eb) - 1022;
+}
+__device__ __forceinline__ int exp_above_f(float v) {
+  const int eb = (int)((__float_as_uint(v) >> 23) & 0xff);
+  return (eb == 0 ? 1 : eb) - 126;
+}
+
+// ---------------------------------------------------------------------------
+// Row exponents of op(Z) (max over the row of the exponents of |re|, |im|,
+// atomically max-ed into emax[i], which starts at OZ_NOEXP) and partial row
+// sums of |re| + |im| per K chunk (part[chunk * N + i]). Element (i, k) of
+// op(Z) is z[i * ars + k * acs] (c128 units); lanes run along whichever of
+// i and k is contiguous.
+__global__ void __launch_bounds__(256) oz_rowexp_kernel(int N, const double2* __restrict__ z,
+                                                        long ars, long acs, int kchunk,
+                                                        int* emax, double* part) {
+  __shared__ double ssum[8][33];
+  __shared__ int sexp[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32;
+  const int kc0 = blockIdx.y * kchunk, kc1 = min(N, kc0 + kchunk);
+  if (ars == 1) {
+    // rows contiguous: lane = row, warps step along k
+    const int i = i0 + tx;
+    double s = 0.0;
+    int e = OZ_NOEXP;
+    if (i < N)
+      for (int k = kc0 + ty; k < kc1; k += 8) {
+        const double2 v = z[(long)i + (long)k * acs];
+        s += fabs(v.x) + fabs(v.y);
+        if (v.x != 0.0) e = max(e, exp_above(v.x));
+        if (v.y != 0.0) e = max(e, exp_above(v.y));
+      }
+    ssum[ty][tx] = s;
+    sexp[ty][tx] = e;
+    __syncthreads();
+    if (ty == 0 && i < N) {
+      double t = 0.0;
+      int m = OZ_NOEXP;
+      for (int w = 0; w < 8; ++w) {
+        t += ssum[w][tx];
+        m = max(m, sexp[w][tx]);
+      }
+      part[(long)blockIdx.y * N + i] = t;
+      if (!oz_none(m)) atomicMax(&emax[i], m);
+    }
+  } else {
+    // k contiguous: a warp walks one row at a time, lanes along k
+    for (int l = ty; l < 32; l += 8) {
+      const int i = i0 + l;
+      if (i >= N) break;
+      double s = 0.0;
+      int e = OZ_NOEXP;
+      for (int k = kc0 + tx; k < kc1; k += 32) {
+        const double2 v = z[(long)i * ars + k];
+        s += fabs(v.x) + fabs(v.y);
+        if (v.x != 0.0) e = max(e, exp_above(v.x));
+        if (v.y != 0.0) e = max(e, exp_above(v.y));
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+      }
+      if (tx == 0) {
+        part[(long)blockIdx.y * N + i] = s;
+        if (!oz_none(e)) atomicMax(&emax[i], e);
+      }
+    }
+  }
+}
+
+// ||op(Z)||_inf with |z| = |re| + |im|: the K-chunk partials of each row
+// summed in chunk order, then the largest row (out must be zeroed first).
+__global__ void oz_rownorm_kernel(int N, int nch, const double* __restrict__ part, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (i < N)
+    for (int c = 0; c < nch; ++c) s += part[(long)c * N + i];
+  if (!(s == s)) s = __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, off));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(s));
+}
+
+// Digits of one value of a row (column) whose largest exponent is e
+// (|v| < 2^e): v is scaled by 2^-(e+1) (|w| < 1/2) and out[t * pstride],
+// t < s, is the round-to-nearest integer of the remainder x 2^b.
+__device__ __forceinline__ void oz_digits(double v, int e, int b, int s, __nv_bfloat16* out,
+                                          size_t pstride) {
+  double w = oz_none(e) ? 0.0 : ldexp(v, -(e + 1));
+  const double radix = (double)(1 << b);
+  for (int t = 0; t < s; ++t) {
+    w *= radix;
+    const double d = rint(w);
+    w -= d;
+    out[(size_t)t * pstride] = __float2bfloat16_rn((float)d);
+  }
+}
+
+// Digits of op(Z): out[(2t + p) * plane + i * Kp + k] (p = 0 re, 1 im) for
+// rows i < Np, zero for rows N <= i < Np and columns N <= k < Kp. A 32 x 32
+// tile goes through shared memory so that both the reads of Z and the
+// K-major writes are coalesced.
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(int N, int Np, int Kp,
+                                                         const double2* __restrict__ z,
+                                                         long ars, long acs,
+                                                         const int* __restrict__ emax, int b,
+                                                         int s, __nv_bfloat16* out, size_t plane) {
+  __shared__ double tr[32][33], ti[32][33];  // [i_local][k_local]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  for (int l = ty; l < 32; l += 8) {
+    const int il = (ars == 1) ? tx : l, kl = (ars == 1) ? l : tx;
+    const int i = i0 + il, k = k0 + kl;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < N && k < N) v = z[(long)i * ars + (long)k * acs];
+    tr[il][kl] = v.x;
+    ti[il][kl] = v.y;
+  }
+  __syncthreads();
+  const int k = k0 + tx;
+  if (k >= Kp) return;
+  for (int l = ty; l < 32; l += 8) {
+    const int i = i0 + l;
+    if (i >= Np) break;
+    const int e = (i < N) ? emax[i] : OZ_NOEXP;
+    __nv_bfloat16* o = out + (size_t)i * Kp + k;
+    oz_digits(tr[l][tx], e, b, s, o, 2 * plane);
+    oz_digits(ti[l][tx], e, b, s, o + plane, 2 * plane);
+  }
+}
+
+// Column exponents of Y (FP32 planes, column j at j * ldy).
+__global__ void oz_colexp_y_kernel(int N, const float* __restrict__ yr, const float* __restrict__ yi,
+                                   long ldy, int* emax) {
+  __shared__ int sm[32];
+  const int j = blockIdx.x;
+  int e = OZ_NOEXP;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const float a = yr[(long)j * ldy + k], c = yi[(long)j * ldy + k];
+    if (a != 0.f) e = max(e, exp_above_f(a));
+    if (c != 0.f) e = max(e, exp_above_f(c));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = OZ_NOEXP;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, sm[w]);
+    emax[j] = m;
+  }
+}
+
+// Digits of Y: out[(2u + p) * plane + j * Kp + k] for columns j < gridDim.y,
+// zero for columns j >= nrhs and rows N <= k < Kp.
+__global__ void oz_slice_y_kernel(int N, int nrhs, int Kp, const float* __restrict__ yr,
+                                  const float* __restrict__ yi, long ldy,
+                                  const int* __restrict__ emax, int b, int s, __nv_bfloat16* out,
+                                  size_t plane) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (k >= Kp) return;
+  const bool in = (j < nrhs) && (k < N);
+  const int e = (j < nrhs) ? emax[j] : OZ_NOEXP;
+  const double a = in ? (double)yr[(long)j * ldy + k] : 0.0;
+  const double c = in ? (double)yi[(long)j * ldy + k] : 0.0;
+  __nv_bfloat16* o = out + (size_t)j * Kp + k;
+  oz_digits(a, e, b, s, o, 2 * plane);
+  oz_digits(c, e, b, s, o + plane, 2 * plane);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core pair products.
+__device__ __forceinline__ uint32_t oz_su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void oz_mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void oz_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool oz_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the error flag set) when the clock budget runs out.
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, int* err) {
+  const long long t0 = clock64();
+  while (!oz_try_wait(bar, parity)) {
+    if (clock64() - t0 > OZ_WAIT_CYCLES) {
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void oz_tma_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                          int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+// K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor: kind::f16 with bf16 A and B, FP32 accumulate,
+// K-major operands.
+__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void oz_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+#define OZ_LD16(taddr, v)                                                                         \
+  asm volatile(                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
+      "%15}, [%16];"                                                                              \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),      \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),  \
+        "=r"(v[14]), "=r"(v[15])                                                                  \
+      : "r"(taddr))
+
+struct OzArgs {
+  int N, nrhs, nk, tiles_m;
+  int* err;
+  int* slots;        // [slot][plane][j][i], i contiguous (N), j < nrhs
+  long slot_stride;  // 2 * nrhs * N
+  unsigned char pt[kOzMaxPairs], pu[kOzMaxPairs], ps[kOzMaxPairs];  // slice t, u; slot
+};
+
+// grid (tiles_m * tiles_n, npairs): blockIdx.y picks the slice pair, so the
+// CTAs of one pair (same A slice) run together and share it in L2.
+__global__ void __launch_bounds__(OZ_THREADS, 2)
+    oz_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const __grid_constant__ OzArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_done;
+  __shared__ uint32_t tmem_slot;
+  if (*reinterpret_cast<volatile int*>(a.err)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (oz_su32(smem_raw) + 1023u) & ~1023u;
+  const int tm = blockIdx.x % a.tiles_m, tn = blockIdx.x / a.tiles_m;
+  const int i0 = tm * OZ_BM, j0 = tn * OZ_BN;
+  const int q = blockIdx.y;
+  const int t = a.pt[q], u = a.pu[q];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      oz_mbar_init(oz_su32(&bar_full[s]), 1);
+      oz_mbar_init(oz_su32(&bar_empty[s]), 1);
+    }
+    oz_mbar_init(oz_su32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     oz_su32(&tmem_slot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // d0: A_re x [Y_re | Y_im] -> columns 0..63 rr, 64..127 ri
+  // d1: A_im x [Y_re | Y_im] -> columns 0..63 ir, 64..127 ii
+  const uint32_t d0 = tmem, d1 = tmem + 128;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int issued = 0;
+      for (int kt = 0; kt < a.nk; ++kt) {
+        const int s = kt % OZ_STAGES, use = kt / OZ_STAGES;
+        if (use > 0 && !oz_wait(oz_su32(&bar_empty[s]), (use - 1) & 1, a.err)) break;
+        const uint32_t st = base + s * OZ_STAGE;
+        const uint32_t fb = oz_su32(&bar_full[s]);
+        oz_expect_tx(fb, OZ_STAGE);
+        oz_tma_3d(st, &tmA, fb, kt * OZ_BK, i0, 2 * t);
+        oz_tma_3d(st + OZ_A_PLANE, &tmA, fb, kt * OZ_BK, i0, 2 * t + 1);
+        oz_tma_3d(st + 2 * OZ_A_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u);
+        oz_tma_3d(st + 2 * OZ_A_PLANE + OZ_B_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u + 1);
+        issued = kt + 1;
+      }
+      for (int kt = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); kt < issued; ++kt)
+        oz_wait(oz_su32(&bar_full[kt % OZ_STAGES]), (kt / OZ_STAGES) & 1, a.err);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer (single thread)
+      constexpr uint32_t ID = bf16_idesc(OZ_BM, 2 * OZ_BN);
+      for (int kt = 0; kt < a.nk; ++kt) {
+        const int s = kt % OZ_STAGES, use = kt / OZ_STAGES;
+        if (!oz_wait(oz_su32(&bar_full[s]), use & 1, a.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * OZ_STAGE;
+#pragma unroll
+        for (int j = 0; j < OZ_BK / 16; ++j) {
+          const uint32_t ko = 32u * j;  // 16 bf16 = 32 bytes along K inside the atom
+          const uint64_t are = oz_desc(st + ko);
+          const uint64_t aim = oz_desc(st + OZ_A_PLANE + ko);
+          const uint64_t by = oz_desc(st + 2 * OZ_A_PLANE + ko);  // 128 rows: Y_re then Y_im
+          const uint32_t acc = (kt == 0 && j == 0) ? 0u : 1u;
+          oz_mma(d0, are, by, ID, acc);
+          oz_mma(d1, aim, by, ID, acc);
+        }
+        oz_commit(oz_su32(&bar_empty[s]));
+      }
+      oz_commit(oz_su32(&bar_done));
+    }
+    __syncwarp();
+  }
+
+  // ---- epilogue: exact integer pair results -> slots
+  const bool ok = oz_wait(oz_su32(&bar_done), 0, a.err);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int gi = i0 + warp * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  int* sre = a.slots + (long)a.ps[q] * a.slot_stride;
+  int* sim = sre + (long)a.nrhs * a.N;
+#pragma unroll 1
+  for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+    uint32_t rr[16], ri[16], ir[16], ii[16];
+    OZ_LD16(d0 + lane_off + c0, rr);
+    OZ_LD16(d0 + lane_off + OZ_BN + c0, ri);
+    OZ_LD16(d1 + lane_off + c0, ir);
+    OZ_LD16(d1 + lane_off + OZ_BN + c0, ii);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (ok && gi < a.N) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = j0 + c0 + c;
+        if (j < a.nrhs) {
+          const long o = (long)j * a.N + gi;
+          sre[o] = __float2int_rn(__uint_as_float(rr[c])) - __float2int_rn(__uint_as_float(ii[c]));
+          sim[o] = __float2int_rn(__uint_as_float(ri[c])) + __float2int_rn(__uint_as_float(ir[c]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Groups -> FP64. For each group g of the chunk (descending g), the integer
+// pair results are summed exactly (int64) and folded in by Horner's rule,
+// acc = acc 2^-b + S_g. The last chunk scales acc by 2^(sig_i + tau_j - 2b)
+// and writes R = S - acc.
+struct OzCombine {
+  int ng;                       // groups in this chunk
+  int gstart[kOzMaxG + 1];      // pair slots of group c: [gstart[c], gstart[c+1])
+  unsigned char slot[kOzMaxPairs];
+};
+
+__global__ void oz_combine_kernel(int N, int nrhs, const int* __restrict__ slots, long slot_stride,
+                                  const __grid_constant__ OzCombine c, int b, int first, int last,
+                                  double* __restrict__ acc_re, double* __restrict__ acc_im,
+                                  const int* __restrict__ rexp, const int* __restrict__ cexp,
+                                  const double* sr, const double* si, double* rr, double* ri,
+                                  long ldr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= N) return;
+  const long o = (long)j * N + i;
+  double ar = first ? 0.0 : acc_re[o];
+  double ai = first ? 0.0 : acc_im[o];
+  const double w = ldexp(1.0, -b);
+  for (int g = 0; g < c.ng; ++g) {
+    long long s_re = 0, s_im = 0;
+    for (int p = c.gstart[g]; p < c.gstart[g + 1]; ++p) {
+      const int* sl = slots + (long)c.slot[p] * slot_stride;
+      s_re += sl[o];
+      s_im += sl[(long)nrhs * N + o];
+    }
+    ar = fma(ar, w, (double)s_re);
+    ai = fma(ai, w, (double)s_im);
+  }
+  if (!last) {
+    acc_re[o] = ar;
+    acc_im[o] = ai;
+    return;
+  }
+  const int er = rexp[i], ec = cexp[j];
+  double vr = 0.0, vi = 0.0;
+  if (!oz_none(er) && !oz_none(ec)) {
+    const int e = (er + 1) + (ec + 1) - 2 * b;
+    vr = ldexp(ar, e);
+    vi = ldexp(ai, e);
+  }
+  const long r = (long)j * ldr + i;
+  rr[r] = sr[r] - vr;
+  ri[r] = si[r] - vi;
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+static PFN_cuTensorMapEncodeTiled_v12000 oz_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D map over bf16 planes [np][rows][Kp], box (64, box_rows, 1), 128B swizzle.
+static bool oz_map(CUtensorMap* m, void* base, int rows, int Kp, int np, int box_rows) {
+  auto enc = oz_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)np};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * (cuuint64_t)rows};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int ceil_log2(long v) {
+  int c = 0;
+  while ((1L << c) < v) ++c;
+  return c;
+}
+
+int oz_digit_bits(int K) {
+  // K 2^(2b-2) <= 2^24, and |digit| <= 2^(b-1) <= 128 exact in bf16
+  const int b = (24 - ceil_log2(std::max(K, 1))) / 2 + 1;
+  return std::min(8, b);
+}
+
+int oz_groups(int K, int b, double rho) {
+  // Smallest G with b (G - 1) >= 55 + log2(sqrt K) + log2 G + log2 rho: the
+  // first dropped group, of G pair sums with digits below 2^(b-1) and
+  // weight 2^-b(G+1), summed over K terms of random sign, stays below 2^-55
+  // of ||op(Z)||_inf max|X_j| (the scalings lose at most a factor 16).
+  const double lr = (rho > 0.0) ? std::log2(std::min(rho, 1.0)) : -1100.0;
+  for (int G = 2; G <= kOzMaxG; ++G)
+    if (b * (G - 1) >= 55.0 + 0.5 * std::log2((double)std::max(K, 1)) + std::log2((double)G) + lr)
+      return G;
+  return kOzMaxG;
+}
+
+int oz_pairs(int G) { return G * (G - 1) / 2; }
+
+int oz_prepare(harp_ctx* ctx, int N, const double2* z, long ld, bool trans, double* znorm,
+               cudaStream_t st) {
+  if (!ctx->oz_a) return HARP_E_UNSUPPORTED;
+  const int b = oz_digit_bits(N);
+  const int s = oz_groups(N, b, 1.0) - 1;
+  if (s > ctx->oz_max_slices) return HARP_E_UNSUPPORTED;
+  const int Kp = (N + OZ_BK - 1) / OZ_BK * OZ_BK;
+  const int Np = (N + OZ_BM - 1) / OZ_BM * OZ_BM;
+  const long ars = trans ? ld : 1, acs = trans ? 1 : ld;
+  const int kchunk = (N + OZ_KCH - 1) / OZ_KCH;
+  const int nch = (N + kchunk - 1) / kchunk;
+  ProfScope ps(HARP_K_OTHER, 0.0, st);
+  HARP_CUDA(cudaMemsetAsync(ctx->oz_rexp, 0x80, sizeof(int) * N, st));  // "no entry"
+  oz_rowexp_kernel<<<dim3((N + 31) / 32, nch), 256, 0, st>>>(N, z, ars, acs, kchunk, ctx->oz_rexp,
+                                                            ctx->oz_part);
+  HARP_LAUNCHED();
+  HARP_CUDA(cudaMemsetAsync(znorm, 0, sizeof(double), st));
+  oz_rownorm_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, nch, ctx->oz_part, znorm);
+  HARP_LAUNCHED();
+  const size_t plane = (size_t)Np * Kp;
+  oz_slice_a_kernel<<<dim3(Kp / 32, Np / 32), 256, 0, st>>>(
+      N, Np, Kp, z, ars, acs, ctx->oz_rexp, b, s, (__nv_bfloat16*)ctx->oz_a, plane);
+  HARP_LAUNCHED();
+  ctx->oz_N = N;
+  ctx->oz_bits = b;
+  ctx->oz_slices = s;
+  ctx->oz_Kp = Kp;
+  ctx->oz_Np = Np;
+  return HARP_OK;
+}
+
+int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi, long ldy,
+                const double* sr, const double* si, double* rr, double* ri, long ldr, double rho,
+                int prof_kind, cudaStream_t st) {
+  if (!ctx->oz_a || ctx->oz_N != N) return HARP_E_STATE;
+  if (nrhs < 1 || nrhs > ctx->max_nrhs) return HARP_E_UNSUPPORTED;
+  const int b = ctx->oz_bits, Kp = ctx->oz_Kp, Np = ctx->oz_Np;
+  const int G = std::min(oz_groups(N, b, rho), ctx->oz_slices + 1);
+  const int sy = G - 1;
+  const int nrhs_p = (nrhs + OZ_BN - 1) / OZ_BN * OZ_BN;
+  const size_t plane_y = (size_t)nrhs_p * Kp;
+  {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    oz_colexp_y_kernel<<<nrhs, 256, 0, st>>>(N, yr, yi, ldy, ctx->oz_cexp);
+    HARP_LAUNCHED();
+    oz_slice_y_kernel<<<dim3((Kp + 255) / 256, nrhs_p), 256, 0, st>>>(
+        N, nrhs, Kp, yr, yi, ldy, ctx->oz_cexp, b, sy, (__nv_bfloat16*)ctx->oz_y, plane_y);
+    HARP_LAUNCHED();
+  }
+  // the operands are zero padded to whole tiles, so no box leaves its tensor
+  CUtensorMap ma, mb;
+  if (!oz_map(&ma, ctx->oz_a, Np, Kp, 2 * ctx->oz_slices, OZ_BM) ||
+      !oz_map(&mb, ctx->oz_y, nrhs_p, Kp, 2 * sy, OZ_BN))
+    return HARP_E_UNSUPPORTED;
+  static bool attr_set = false;
+  if (!attr_set) {
+    HARP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   OZ_STAGES * OZ_STAGE + 1024));
+    attr_set = true;
+  }
+  const int tiles_m = Np / OZ_BM, tiles_n = nrhs_p / OZ_BN;
+  const long slot_stride = 2L * nrhs * N;
+  // Groups in descending g, cut into chunks of at most oz_slot_pairs pairs.
+  int g = G;
+  bool first = true;
+  while (g >= 2) {
+    OzArgs a;
+    OzCombine c;
+    a.N = N;
+    a.nrhs = nrhs;
+    a.nk = Kp / OZ_BK;
+    a.tiles_m = tiles_m;
+    a.err = ctx->dstatus + 2;
+    a.slots = ctx->oz_slots;
+    a.slot_stride = slot_stride;
+    int np = 0;
+    c.ng = 0;
+    c.gstart[0] = 0;
+    while (g >= 2) {
+      const int tlo = std::max(1, g - sy), thi = std::min(g - 1, ctx->oz_slices);
+      const int cnt = std::max(0, thi - tlo + 1);
+      if (np > 0 && np + cnt > ctx->oz_slot_pairs) break;
+      if (cnt > ctx->oz_slot_pairs) return HARP_E_UNSUPPORTED;
+      for (int t = tlo; t <= thi; ++t) {
+        c.slot[np] = (unsigned char)np;
+        a.pt[np] = (unsigned char)(t - 1);
+        a.pu[np] = (unsigned char)(g - t - 1);
+        a.ps[np] = (unsigned char)np;
+        ++np;
+      }
+      c.gstart[++c.ng] = np;
+      --g;
+    }
+    const bool last = (g < 2);
+    if (np > 0) {
+      // order the products by A slice so that one slice is live in L2 at a time
+      std::vector<int> ord(np);
+      for (int k = 0; k < np; ++k) ord[k] = k;
+      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return a.pt[x] < a.pt[y]; });
+      unsigned char pt[kOzMaxPairs], pu[kOzMaxPairs], psl[kOzMaxPairs];
+      for (int k = 0; k < np; ++k) {
+        pt[k] = a.pt[ord[k]];
+        pu[k] = a.pu[ord[k]];
+        psl[k] = a.ps[ord[k]];
+      }
+      for (int k = 0; k < np; ++k) {
+        a.pt[k] = pt[k];
+        a.pu[k] = pu[k];
+        a.ps[k] = psl[k];
+      }
+      ProfScope ps(prof_kind, 8.0 * np * (double)N * N * nrhs, st);
+      oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024, st>>>(
+          ma, mb, a);
+      HARP_LAUNCHED();
+    }
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      oz_combine_kernel<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(
+          N, nrhs, ctx->oz_slots, slot_stride, c, b, first ? 1 : 0, last ? 1 : 0, ctx->oz_acc,
+          ctx->oz_acc + (size_t)N * nrhs, ctx->oz_rexp, ctx->oz_cexp, sr, si, rr, ri, ldr);
+      HARP_LAUNCHED();
+    }
+    first = false;
+  }
+  return HARP_OK;
+}
+
+}  // namespace harp

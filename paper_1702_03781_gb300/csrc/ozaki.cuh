@@ -1,0 +1,29 @@
+// ozaki.cuh -- internal interface of the tensor-core refinement residual
+// (exact integer slices, ozaki.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace harp {
+
+constexpr int kOzMaxG = 13;  // largest slice-group index t + u formed
+constexpr int kOzMaxPairs = kOzMaxG * (kOzMaxG - 1) / 2;
+
+// Digit width for a K-long product (exact FP32 accumulation, bf16 digits).
+int oz_digit_bits(int K);
+// Groups G needed for a residual whose correction is rho times the iterate.
+int oz_groups(int K, int b, double rho);
+int oz_pairs(int G);
+
+// Row exponents, ||op(Z)||_inf (|re| + |im|, into *znorm on the device) and
+// the digits of op(Z), Z the N x N c128 matrix (ld) -- once per solve.
+int oz_prepare(harp_ctx* ctx, int N, const double2* z, long ld, bool trans, double* znorm,
+               cudaStream_t st);
+// R = S - op(Z) Y for FP32 planes Y (ldy); S, R FP64 planes (ldr, may alias).
+// rho: max_j max|Y_j| / max|X_j| of the iterate X the residual belongs to
+// (1 for a full residual).
+int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi, long ldy,
+                const double* sr, const double* si, double* rr, double* ri, long ldr, double rho,
+                int prof_kind, cudaStream_t st);
+
+}  // namespace harp

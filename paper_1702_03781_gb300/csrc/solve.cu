@@ -4,7 +4,8 @@
 //
 // Mixed refinement (classical iterative refinement, Wilkinson/Moler; the
 // stopping rule follows LAPACK's zcgesv):
-//   X0 = (LU32)^{-1} V, R0 = V - Z64 X0 (FP64-accurate, float-float)
+//   X0 = (LU32)^{-1} V, R0 = V - Z64 X0 (FP64-accurate: exact integer
+//   slices on the tensor cores, ozaki.cu, or float-float, resid.cu)
 //   repeat: stop when, for every column j, max_i |R_ij| <= tol ||Z64||_inf
 //           max_i |X_ij| (|z| = |re| + |im|); D = (LU32)^{-1} R; X += D;
 //           R -= Z64 D (an update accurate relative to |Z64||D|).
@@ -15,6 +16,7 @@
 #include <climits>
 
 #include "dense.cuh"
+#include "ozaki.cuh"
 
 namespace harp {
 
@@ -28,6 +30,10 @@ static int gemm_mode(int prec) {
 }
 // Factorisations are shared between the modes that store the same type.
 static int lu_class(int prec) { return prec == HARP_FP64 ? 0 : 1; }
+
+static bool use_slices(const harp_ctx* c) {
+  return c->oz_a && c->residual_mode == HARP_RESIDUAL_SLICES;
+}
 
 // Copy the right-hand sides (or the port excitations) into FP64 planes.
 static int load_rhs(harp_ctx* c, int N, int nrhs, const double* V, int ldv, double* re, double* im,
@@ -219,15 +225,21 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   }
 
   // ---- mixed: FP64-accurate residual against the context's FP64 matrix,
-  // formed in float-float on the FP32 pipe (resid.cu).
+  // by exact integer slices on the tensor cores (ozaki.cu) or in
+  // float-float on the FP32 pipe (resid.cu).
   const size_t NN = (size_t)ctx->max_N * ctx->max_N;
   const size_t NR = (size_t)ctx->max_N * ctx->max_nrhs;
   float* zhl[4] = {ctx->zff, ctx->zff + NN, ctx->zff + 2 * NN, ctx->zff + 3 * NN};
   float* xhl[4] = {ctx->xff, ctx->xff + NR, ctx->xff + 2 * NR, ctx->xff + 3 * NR};
-  HARP_TRY(split_c128(N, N, (const double*)ctx->z64, ctx->ld64, zhl, ldw, st));
   // element (i, k) of op(Z): (1, ld) for Z, (ld, 1) for Z^T
   const long ars = tr ? ldw : 1, acs = tr ? 1 : ldw;
-  HARP_TRY(norm_inf_planes_f32(N, N, zhl[0], zhl[1], ars, acs, ctx->rowsum, ctx->red + 0, st));
+  const bool slices = use_slices(ctx);
+  if (slices) {
+    HARP_TRY(oz_prepare(ctx, N, ctx->z64, ctx->ld64, tr, ctx->red + 0, st));
+  } else {
+    HARP_TRY(split_c128(N, N, (const double*)ctx->z64, ctx->ld64, zhl, ldw, st));
+    HARP_TRY(norm_inf_planes_f32(N, N, zhl[0], zhl[1], ars, acs, ctx->rowsum, ctx->red + 0, st));
+  }
   if (tol <= 0.0) tol = std::sqrt((double)N) * std::ldexp(1.0, -53);
   double* colmax_r = ctx->red + 16;
   double* colmax_x = ctx->red + 16 + nrhs;
@@ -237,11 +249,18 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   // |Z||D_k|: with rho = max_j max|D_kj| / max|X_j| <= kDot2Rho the
   // double-float accumulator (~1e-14 of sum |z||d|) keeps the update error
   // below 2^-53 |Z||X|, otherwise the three-float one is used.
+  // With slices the update forms only the digit groups that the size of D
+  // against X leaves above the FP64 rounding of the residual.
   constexpr double kDot2Rho = 1e-2;
-  HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
-  HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
-                       ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
-                       true));
+  if (slices) {
+    HARP_TRY(oz_residual(ctx, N, nrhs, wre, wim, ldw, ctx->v_re, ctx->v_im, ctx->r_re, ctx->r_im,
+                         ldw, 1.0, HARP_K_RESIDUAL, st));
+  } else {
+    HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
+    HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
+                         ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
+                         true));
+  }
   double bwd = INFINITY;
   int it = 0;
   bool converged = false;
@@ -281,10 +300,15 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       const double dj = h[16 + j], xj = h[16 + nrhs + j];
       rho = std::max(rho, (dj == 0.0) ? 0.0 : dj / xj);
     }
-    HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
-    HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
-                         ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
-                         !(rho <= kDot2Rho)));
+    if (slices) {
+      HARP_TRY(oz_residual(ctx, N, nrhs, wre, wim, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
+                           ctx->r_im, ldw, rho, HARP_K_RESID_UPDATE, st));
+    } else {
+      HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
+      HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
+                           ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
+                           !(rho <= kDot2Rho)));
+    }
     ++it;
   }
   HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
@@ -295,4 +319,69 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   HARP_CUDA(cudaStreamSynchronize(st));
   if (ctx->hstatus[2]) return HARP_E_TIMEOUT;
   return converged ? HARP_OK : HARP_E_NOCONV;
+}
+
+extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
+  if (!ctx) return -1;
+  if (option != HARP_OPT_RESIDUAL) return -2;
+  if (value != HARP_RESIDUAL_SLICES && value != HARP_RESIDUAL_FF) return -3;
+  if (value == HARP_RESIDUAL_SLICES && !ctx->oz_a) return HARP_E_UNSUPPORTED;
+  ctx->residual_mode = value;
+  return HARP_OK;
+}
+
+extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
+  if (!ctx) return -1;
+  if (option != HARP_OPT_RESIDUAL) return -2;
+  if (!value) return -3;
+  *value = use_slices(ctx) ? HARP_RESIDUAL_SLICES : HARP_RESIDUAL_FF;
+  return HARP_OK;
+}
+
+extern "C" int harp_residual(harp_ctx* ctx, int N, const double* Z, int ldz, const float* X,
+                             int ldx, const double* V, int ldv, int nrhs, double* R, int ldr,
+                             char trans, void* stream) {
+  if (!ctx) return -1;
+  if (N < 1 || N > ctx->max_N) return -2;
+  if (!Z) return -3;
+  if (ldz < N) return -4;
+  if (!X) return -5;
+  if (ldx < N) return -6;
+  if (!V) return -7;
+  if (ldv < N) return -8;
+  if (nrhs < 1 || nrhs > ctx->max_nrhs || nrhs > 65535) return -9;
+  if (!R) return -10;
+  if (ldr < N) return -11;
+  const bool tr = (trans == 'T' || trans == 't');
+  if (!tr && trans != 'N' && trans != 'n') return -12;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  const long ldw = ctx->max_N;
+  const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+  const size_t NR = (size_t)ctx->max_N * ctx->max_nrhs;
+  float* wre = (float*)ctx->w_re;
+  float* wim = (float*)ctx->w_im;
+  HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
+  HARP_TRY(interleaved_to_planes<float, float>(N, nrhs, X, ldx, wre, wim, ldw, st));
+  HARP_TRY(interleaved_to_planes<double, double>(N, nrhs, V, ldv, ctx->v_re, ctx->v_im, ldw, st));
+  if (use_slices(ctx)) {
+    HARP_TRY(oz_prepare(ctx, N, (const double2*)Z, ldz, tr, ctx->red + 0, st));
+    HARP_TRY(oz_residual(ctx, N, nrhs, wre, wim, ldw, ctx->v_re, ctx->v_im, ctx->r_re, ctx->r_im,
+                         ldw, 1.0, HARP_K_RESIDUAL, st));
+  } else {
+    float* zhl[4] = {ctx->zff, ctx->zff + NN, ctx->zff + 2 * NN, ctx->zff + 3 * NN};
+    float* xhl[4] = {ctx->xff, ctx->xff + NR, ctx->xff + 2 * NR, ctx->xff + 3 * NR};
+    HARP_TRY(split_c128(N, N, Z, ldz, zhl, ldw, st));
+    HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
+    const long ars = tr ? ldw : 1, acs = tr ? 1 : ldw;
+    HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->v_re, ctx->v_im, ctx->r_re,
+                         ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
+                         true));
+  }
+  HARP_TRY(planes_to_interleaved(N, nrhs, ctx->r_re, ctx->r_im, ldw, R, ldr, st));
+  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 2, ctx->dstatus + 2, sizeof(int),
+                            cudaMemcpyDeviceToHost, st));
+  HARP_CUDA(cudaStreamSynchronize(st));
+  return ctx->hstatus[2] ? HARP_E_TIMEOUT : HARP_OK;
 }

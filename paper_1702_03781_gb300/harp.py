@@ -34,6 +34,10 @@ HARP_E_UNSUPPORTED = 0x40000006
 HARP_E_STATE = 0x40000007
 HARP_E_NONFINITE = 0x40000008
 
+# harp_ctx_set_option: how the mixed refinement forms its FP64 residual
+HARP_OPT_RESIDUAL = 1
+RESIDUAL = {"slices": 0, "ff": 1}
+
 _lib = None
 
 
@@ -84,8 +88,12 @@ def lib():
         L.harp_fill_adjoint_noalloc.restype = i
         L.harp_profile_begin.argtypes = [vp, ct.c_uint]
         L.harp_profile_end.argtypes = [vp, vp, vp, vp]
+        L.harp_ctx_set_option.argtypes = [vp, i, i]
+        L.harp_ctx_get_option.argtypes = [vp, i, ct.POINTER(i)]
+        L.harp_residual.argtypes = [vp, i, vp, i, vp, i, vp, i, i, vp, i, ct.c_char, vp]
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_z64", "harp_fill",
-                   "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end"):
+                   "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
+                   "harp_ctx_set_option", "harp_ctx_get_option", "harp_residual"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -234,6 +242,31 @@ class Harp:
         ok = (HARP_OK, HARP_E_NOCONV) if allow_noconv else (HARP_OK,)
         _check("mbf_solve", st, ok)
         return X, {"iters": it.value, "resid": res.value, "status": st}
+
+    # -- refinement residual -------------------------------------------------
+    def set_residual(self, method: str):
+        """'slices' (tensor cores, exact integer digits) or 'ff' (float-float)."""
+        _check("harp_ctx_set_option",
+               lib().harp_ctx_set_option(self._h, HARP_OPT_RESIDUAL, RESIDUAL[method]))
+
+    def residual_method(self) -> str:
+        v = ct.c_int(-1)
+        _check("harp_ctx_get_option", lib().harp_ctx_get_option(self._h, HARP_OPT_RESIDUAL,
+                                                                ct.byref(v)))
+        return {k: m for m, k in RESIDUAL.items()}[v.value]
+
+    def residual(self, Z: torch.Tensor, X: torch.Tensor, V: torch.Tensor, trans: str = "N",
+                 stream=None) -> torch.Tensor:
+        """R = V - op(Z) X (complex128) for FP64 Z, FP32 X (complex64), FP64 V."""
+        Z = as_colmajor(Z.to(torch.complex128))
+        X = as_colmajor(X.to(torch.complex64))
+        V = as_colmajor(V.to(torch.complex128))
+        N, nrhs = X.shape
+        R = colmajor_empty(N, nrhs, torch.complex128, X.device)
+        _check("harp_residual", lib().harp_residual(
+            self._h, N, _ptr(Z), _ld(Z), _ptr(X), _ld(X), _ptr(V), _ld(V), nrhs, _ptr(R), _ld(R),
+            trans.encode(), _stream(stream)))
+        return R
 
     # -- adjoint ------------------------------------------------------------
     def fill_adjoint(self, pos: torch.Tensor, freq_hz: float, coef: torch.Tensor,

@@ -58,3 +58,10 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
                        None) == -1
     L.harp_ctx_create.argtypes = [ct.POINTER(vp), ct.c_int, ct.c_int, ct.c_int]
     assert L.harp_ctx_create(None, 0, 16, 4) == -1
+    L.harp_residual.argtypes = [vp, ct.c_int, vp, ct.c_int, vp, ct.c_int, vp, ct.c_int, ct.c_int,
+                                vp, ct.c_int, ct.c_char, vp]
+    assert L.harp_residual(None, 4, None, 4, None, 4, None, 4, 1, None, 4, b"N", None) == -1
+    L.harp_ctx_set_option.argtypes = [vp, ct.c_int, ct.c_int]
+    assert L.harp_ctx_set_option(None, 1, 0) == -1
+    L.harp_ctx_get_option.argtypes = [vp, ct.c_int, vp]
+    assert L.harp_ctx_get_option(None, 1, None) == -1
