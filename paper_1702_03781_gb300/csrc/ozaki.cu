@@ -7,7 +7,7 @@
 // Scaling and slices. Each row i of A = op(Z) is scaled by 2^-sig_i so that
 // its largest real or imaginary part is below 1/2, each column j of Y by
 // 2^-tau_j likewise, and the scaled values are cut into signed base-2^b
-// digits by repeated round-to-nearest (all steps exact in FP64):
+// digits by repeated round-to-nearest on a 64-bit fixed point:
 //   a_ik = 2^sig_i sum_t d_t[i,k] 2^-bt,   y_kj = 2^tau_j sum_u e_u[k,j] 2^-bu,
 // with |d|, |e| <= 2^(b-1), so every digit is an integer exact in bf16.
 //
@@ -153,16 +153,26 @@ __global__ void oz_rownorm_kernel(int N, int nch, const double* __restrict__ par
 }
 
 // Digits of one value of a row (column) whose largest exponent is e
-// (|v| < 2^e): v is scaled by 2^-(e+1) (|w| < 1/2) and out[t * pstride],
-// t < s, is the round-to-nearest integer of the remainder x 2^b.
+// (|v| < 2^e). The scaled value w = v 2^-(e+1) (|w| < 1/2) is taken to the
+// 64-bit fixed point X = round(w 2^63) (|X| < 2^62; bits below 2^-63 of the
+// scale are dropped, ~2^-61 of the row's largest entry), and out[t * pstride],
+// t < s, gets the signed base-2^b digits from the top, each the
+// round-to-nearest quotient of the remainder by 2^(63 - b(t+1)), so
+// |digit| <= 2^(b-1). Integer arithmetic: the FP64 pipe runs at 1/64 rate.
 __device__ __forceinline__ void oz_digits(double v, int e, int b, int s, __nv_bfloat16* out,
                                           size_t pstride) {
-  double w = oz_none(e) ? 0.0 : ldexp(v, -(e + 1));
-  const double radix = (double)(1 << b);
+  long long X = oz_none(e) ? 0LL : __double2ll_rn(ldexp(v, 62 - e));
+  int shift = 63;
   for (int t = 0; t < s; ++t) {
-    w *= radix;
-    const double d = rint(w);
-    w -= d;
+    shift -= b;
+    long long d;
+    if (shift > 0) {
+      d = (X + (1LL << (shift - 1))) >> shift;
+      X -= d << shift;
+    } else {
+      d = X << (-shift);
+      X = 0;
+    }
     out[(size_t)t * pstride] = __float2bfloat16_rn((float)d);
   }
 }
