@@ -709,15 +709,12 @@ template <typename R>
 static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int k,
                         int want, int* ipiv, int* zero_col, int mode, cudaStream_t st, int* nb) {
   if constexpr (std::is_same<R, float>::value) {
-    static int ok_cache[17] = {0};  // 0 unknown, 1 resident, -1 not
+    // the plan only offers clusters that can be resident
     int C = 0, Mb = 0;
     const int w = panel_cluster_plan(ctx, N - k, want, &C, &Mb);
     if (w > 0) {
-      if (ok_cache[C] == 0) ok_cache[C] = panel_cluster_ok(C, (size_t)218 * 1024) ? 1 : -1;
-      if (ok_cache[C] > 0) {
-        *nb = w;
-        return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st);
-      }
+      *nb = w;
+      return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st);
     }
   }
   *nb = want;

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "dense.cuh"
 #include "prof.cuh"
@@ -41,7 +42,8 @@ constexpr int kPcMaxCluster = 16;
 // Bytes of dynamic shared memory for a panel of nb columns, Mb rows per CTA
 // and a cluster of C CTAs.
 __host__ __device__ inline size_t panel_smem_bytes(int nb, int Mb, int C) {
-  return sizeof(float) * ((size_t)2 * nb * Mb      // panel block (re, im)
+  return sizeof(float) * ((size_t)2 * nb * (Mb + 1)  // panel block (re, im), column stride Mb + 1
+
                           + (size_t)4 * C * nb     // candidate rows, 2 parities
                           + (size_t)4 * nb         // row j, 2 parities
                           + (size_t)2 * C)         // candidate values
@@ -55,9 +57,12 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
   const int crank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
   extern __shared__ __align__(16) float pc_smem[];
-  float* sre = pc_smem;                        // [nb][Mb]
-  float* sim = sre + (size_t)nb * Mb;
-  float* tab_r = sim + (size_t)nb * Mb;        // [2][C][nb]
+  // Column stride Mb + 1: the row-wise accesses (a row's nb entries) then
+  // fall in distinct banks.
+  const int ldS = Mb + 1;
+  float* sre = pc_smem;                        // [nb][ldS]
+  float* sim = sre + (size_t)nb * ldS;
+  float* tab_r = sim + (size_t)nb * ldS;       // [2][C][nb]
   float* tab_i = tab_r + (size_t)2 * C * nb;
   float* jrow_r = tab_i + (size_t)2 * C * nb;  // [2][nb]
   float* jrow_i = jrow_r + 2 * nb;
@@ -85,22 +90,37 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
       for (int u = 0; u < 4; ++u) {
         const int r = rb + tid + u * kPcThreads;
         if (r < rows) {
-          sre[(size_t)c * Mb + r] = vr[u];
-          sim[(size_t)c * Mb + r] = vi[u];
+          sre[(size_t)c * ldS + r] = vr[u];
+          sim[(size_t)c * ldS + r] = vi[u];
         }
       }
     }
   __syncthreads();
 
+  float inv_r = 0.f, inv_i = 0.f;  // 1 / pivot of the previous column
+  bool scale_prev = false;
   for (int j = 0; j < nb; ++j) {
     const int par = j & 1;
+    // 0. deferred scaling of column j-1 below its diagonal (L multipliers);
+    // the update of step j-1 read it unscaled
+    if (scale_prev) {
+      for (int r = tid; r < rows; r += kPcThreads) {
+        if (r0 + r <= j - 1) continue;
+        float* xr = &sre[(size_t)(j - 1) * ldS + r];
+        float* xi = &sim[(size_t)(j - 1) * ldS + r];
+        const float ar = *xr, ai = *xi;
+        *xr = ar * inv_r - ai * inv_i;
+        *xi = ar * inv_i + ai * inv_r;
+      }
+      scale_prev = false;
+    }
     // 1. local candidate
     float best = -1.f;
     int bi = INT_MAX;
     for (int r = tid; r < rows; r += kPcThreads) {
       const int g = r0 + r;
       if (g < j) continue;
-      const float xr = sre[(size_t)j * Mb + r], xi = sim[(size_t)j * Mb + r];
+      const float xr = sre[(size_t)j * ldS + r], xi = sim[(size_t)j * ldS + r];
       const float v = xr * xr + xi * xi;
       if (v > best) {
         best = v;
@@ -121,25 +141,30 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
       red_i[warp] = bi;
     }
     __syncthreads();
-    best = red_v[0];
-    bi = red_i[0];
+    // every warp reduces the kPcThreads/32 warp candidates with shuffles
+    // (largest value, then smallest row), so all threads hold the result
+    best = (lane < kPcThreads / 32) ? red_v[lane] : -2.f;
+    bi = (lane < kPcThreads / 32) ? red_i[lane] : INT_MAX;
 #pragma unroll
-    for (int q = 1; q < kPcThreads / 32; ++q)
-      if (red_v[q] > best || (red_v[q] == best && red_i[q] < bi)) {
-        best = red_v[q];
-        bi = red_i[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
       }
+    }
     // publish: value and index, the candidate row, and (CTA 0) row j
     if (tid < nb) {
       float vr = 0.f, vi = 0.f;
       if (best >= 0.f) {
-        vr = sre[(size_t)tid * Mb + (bi - r0)];
-        vi = sim[(size_t)tid * Mb + (bi - r0)];
+        vr = sre[(size_t)tid * ldS + (bi - r0)];
+        vi = sim[(size_t)tid * ldS + (bi - r0)];
       }
       float wr = 0.f, wi = 0.f;
       if (crank == 0) {
-        wr = sre[(size_t)tid * Mb + j];
-        wi = sim[(size_t)tid * Mb + j];
+        wr = sre[(size_t)tid * ldS + j];
+        wi = sim[(size_t)tid * ldS + j];
       }
       for (int q = 0; q < C; ++q) {
         float* tr = cluster.map_shared_rank(tab_r, q);
@@ -159,16 +184,20 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
     cluster.sync();
 
     // 2. the pivot (same in every CTA), pivot row and row j from the tables
-    int win = 0;
-    best = cand_v[par * C];
-    bi = cand_i[par * C];
-    for (int q = 1; q < C; ++q) {
-      const float ob = cand_v[par * C + q];
-      const int oi = cand_i[par * C + q];
-      if (ob > best || (ob == best && oi < bi)) {
+    // the C candidates reduced with shuffles in every warp (same order:
+    // largest value, then smallest row; win = the owning CTA)
+    int win = lane;
+    best = (lane < C) ? cand_v[par * C + lane] : -2.f;
+    bi = (lane < C) ? cand_i[par * C + lane] : INT_MAX;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      const int ow = __shfl_xor_sync(0xffffffffu, win, off);
+      if (ob > best || (ob == best && oi < bi) || (ob == best && oi == bi && ow < win)) {
         best = ob;
         bi = oi;
-        win = q;
+        win = ow;
       }
     }
     const int p = bi;
@@ -188,59 +217,117 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
     // 3. swap, scale, rank-1 update (local)
     if (tid < nb) {
       if (crank == 0) {
-        sre[(size_t)tid * Mb + j] = prow_r[tid];
-        sim[(size_t)tid * Mb + j] = prow_i[tid];
+        sre[(size_t)tid * ldS + j] = prow_r[tid];
+        sim[(size_t)tid * ldS + j] = prow_i[tid];
       }
       if (crank == win && p != j) {
-        sre[(size_t)tid * Mb + (p - r0)] = jrow_r[par * nb + tid];
-        sim[(size_t)tid * Mb + (p - r0)] = jrow_i[par * nb + tid];
+        sre[(size_t)tid * ldS + (p - r0)] = jrow_r[par * nb + tid];
+        sim[(size_t)tid * ldS + (p - r0)] = jrow_i[par * nb + tid];
       }
     }
     __syncthreads();
     const float pr = prow_r[j], pi = prow_i[j];
     const float den = pr * pr + pi * pi;
-    const float ir = pr / den, ii = -pi / den;
-    for (int r = tid; r < rows; r += kPcThreads) {
-      const int g = r0 + r;
-      if (g <= j) continue;
-      const float ar = sre[(size_t)j * Mb + r], ai = sim[(size_t)j * Mb + r];
-      const float lr = ar * ir - ai * ii, li = ar * ii + ai * ir;
-      sre[(size_t)j * Mb + r] = lr;
-      sim[(size_t)j * Mb + r] = li;
-      for (int cc = j + 1; cc < nb; ++cc) {
-        const float ur = prow_r[cc], ui = prow_i[cc];
-        float* xr = &sre[(size_t)cc * Mb + r];
-        float* xi = &sim[(size_t)cc * Mb + r];
-        *xr = fmaf(-lr, ur, fmaf(li, ui, *xr));
-        *xi = fmaf(-lr, ui, fmaf(-li, ur, *xi));
+    inv_r = pr / den;
+    inv_i = -pi / den;
+    scale_prev = true;
+    // rank-1 update of columns j+1.. below row j: warp w takes columns
+    // j+1+w, j+1+w+16, ..., lanes take rows (conflict-free); the multiplier
+    // of a row is formed from the unscaled column j in registers
+    constexpr int kW = kPcThreads / 32;
+    constexpr int kCpw = (kPcMaxNb + kW - 1) / kW;
+    float ur[kCpw], ui[kCpw];
+#pragma unroll
+    for (int m = 0; m < kCpw; ++m) {
+      const int cc = j + 1 + warp + kW * m;
+      ur[m] = (cc < nb) ? prow_r[cc] : 0.f;
+      ui[m] = (cc < nb) ? prow_i[cc] : 0.f;
+    }
+    if (j + 1 + warp < nb) {
+      for (int r = lane; r < rows; r += 32) {
+        if (r0 + r <= j) continue;
+        const float ar = sre[(size_t)j * ldS + r], ai = sim[(size_t)j * ldS + r];
+        const float lr = ar * inv_r - ai * inv_i, li = ar * inv_i + ai * inv_r;
+#pragma unroll
+        for (int m = 0; m < kCpw; ++m) {
+          const int cc = j + 1 + warp + kW * m;
+          if (cc < nb) {
+            float* xr = &sre[(size_t)cc * ldS + r];
+            float* xi = &sim[(size_t)cc * ldS + r];
+            const float vr = *xr, vi = *xi;
+            *xr = fmaf(-lr, ur[m], fmaf(li, ui[m], vr));
+            *xi = fmaf(-lr, ui[m], fmaf(-li, ur[m], vi));
+          }
+        }
       }
     }
     __syncthreads();
   }
+  // scaling of the last column
+  if (scale_prev) {
+    for (int r = tid; r < rows; r += kPcThreads) {
+      if (r0 + r <= nb - 1) continue;
+      float* xr = &sre[(size_t)(nb - 1) * ldS + r];
+      float* xi = &sim[(size_t)(nb - 1) * ldS + r];
+      const float ar = *xr, ai = *xi;
+      *xr = ar * inv_r - ai * inv_i;
+      *xi = ar * inv_i + ai * inv_r;
+    }
+  }
+  __syncthreads();
 
   // store the row block
   for (int c = 0; c < nb; ++c)
     for (int r = tid; r < rows; r += kPcThreads) {
-      gre[r + (size_t)c * lda] = sre[(size_t)c * Mb + r];
-      gim[r + (size_t)c * lda] = sim[(size_t)c * Mb + r];
+      gre[r + (size_t)c * lda] = sre[(size_t)c * ldS + r];
+      gim[r + (size_t)c * lda] = sim[(size_t)c * ldS + r];
     }
   cluster.sync();  // no CTA leaves while a peer may still write its tables
 }
 
 // Plan a cluster panel for M rows: returns the panel width to use (0 when
 // the cluster path does not apply) and the cluster size and rows per CTA.
+bool panel_cluster_ok(int C, size_t smem);
+
+// Residency of a cluster of C CTAs with this much shared memory, cached per
+// C as the largest size known to fit and the smallest known not to.
+static bool cluster_resident(int C, size_t smem) {
+  static std::mutex mu;
+  static size_t ok_max[kPcMaxCluster + 1] = {0};
+  static size_t bad_min[kPcMaxCluster + 1] = {0};
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= ok_max[C]) return true;
+  if (bad_min[C] && smem >= bad_min[C]) return false;
+  const bool ok = panel_cluster_ok(C, smem);
+  if (ok) ok_max[C] = std::max(ok_max[C], smem);
+  else bad_min[C] = bad_min[C] ? std::min(bad_min[C], smem) : smem;
+  return ok;
+}
+
 int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb) {
+  // The per-column update is a pass over the CTA's rows, so more CTAs are
+  // faster until a CTA holds ~192 rows (measured on the 3072 x 64 panel:
+  // 5.2 us per column with 384 rows per CTA, 4.6 with 192); take the
+  // smallest cluster that fits in shared memory and reaches that, else the
+  // largest that fits.
   const size_t budget = std::min<size_t>(ctx->smem_optin, 220 * 1024) - 2048;
+  constexpr int kRowsTarget = 192;
   for (int nb = std::min(want_nb, kPcMaxNb); nb >= 16; nb /= 2) {
+    int best_c = 0, best_mb = 0;
     for (int C : {1, 2, 4, 8, 16}) {
       int mb = (M + C - 1) / C;
       if (mb < nb) mb = nb;
       if (C > 1 && (C - 1) * mb >= M) continue;  // every CTA owns rows
-      if (panel_smem_bytes(nb, mb, C) <= budget) {
-        *csize = C;
-        *Mb = mb;
-        return nb;
-      }
+      if (panel_smem_bytes(nb, mb, C) > budget) continue;
+      if (!cluster_resident(C, panel_smem_bytes(nb, mb, C))) continue;
+      best_c = C;
+      best_mb = mb;
+      if (mb <= kRowsTarget) break;
+    }
+    if (best_c) {
+      *csize = best_c;
+      *Mb = best_mb;
+      return nb;
     }
   }
   return 0;
