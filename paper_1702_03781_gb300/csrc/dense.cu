@@ -18,6 +18,7 @@
 // column-parallel swap kernel never runs a long dependency chain; the
 // solve phase applies the net permutation once, as a gather.
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <type_traits>
 #include <vector>
@@ -39,8 +40,16 @@ constexpr int kTrsmCols = 8;       // right-hand sides per CTA in the leaf
 // 16 x 16 threads, 4 x 4 complex register tile per thread.
 template <typename R>
 __global__ void __launch_bounds__(256) cgemm_simt_kernel(int M, int N, int K, R alpha, CView<R> A,
-                                                         CView<R> B, R beta, CView<R> C) {
+                                                         CView<R> B, R beta, CView<R> C, long sA,
+                                                         long sB, long sC) {
   __shared__ R As_r[8][64], As_i[8][64], Bs_r[8][64], Bs_i[8][64];
+  // batch z: every operand moved by its element stride
+  A.re += blockIdx.z * sA;
+  A.im += blockIdx.z * sA;
+  B.re += blockIdx.z * sB;
+  B.im += blockIdx.z * sB;
+  C.re += blockIdx.z * sC;
+  C.im += blockIdx.z * sC;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   R cr[4][4], ci[4][4];
@@ -115,11 +124,13 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int M, int N, int K, R 
 
 template <typename R>
 int cgemm_simt(int M, int N, int K, R alpha, CView<R> A, CView<R> B, R beta, CView<R> C,
-               cudaStream_t st, int kind = HARP_K_GEMM) {
-  if (M <= 0 || N <= 0) return HARP_OK;
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  ProfScope ps(kind, 8.0 * M * N * (double)K, st);
-  cgemm_simt_kernel<R><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C);
+               cudaStream_t st, int kind = HARP_K_GEMM, long sA = 0, long sB = 0, long sC = 0,
+               int batch = 1) {
+  if (M <= 0 || N <= 0 || batch <= 0) return HARP_OK;
+  if (batch > 65535) return HARP_E_UNSUPPORTED;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  ProfScope ps(kind, 8.0 * M * N * (double)K * batch, st);
+  cgemm_simt_kernel<R><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C, sA, sB, sC);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -127,16 +138,22 @@ int cgemm_simt(int M, int N, int K, R alpha, CView<R> A, CView<R> B, R beta, CVi
 // Tensor-core path (lu_tc.cu). Returns HARP_E_UNSUPPORTED when the shapes
 // or strides do not suit it; the caller then uses the CUDA-core kernel.
 int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> B, float beta,
-                 CView<float> C, int mode, cudaStream_t st);
+                 CView<float> C, int mode, cudaStream_t st, long sA, long sB, long sC, int batch);
 
 template <>
 int cgemm<float>(int M, int N, int K, float alpha, CView<float> A, CView<float> B, float beta,
                  CView<float> C, int mode, cudaStream_t st) {
+  return cgemm_batched(M, N, K, alpha, A, 0, B, 0, beta, C, 0, 1, mode, st);
+}
+
+int cgemm_batched(int M, int N, int K, float alpha, CView<float> A, long sA, CView<float> B,
+                  long sB, float beta, CView<float> C, long sC, int batch, int mode,
+                  cudaStream_t st) {
   if (mode != GEMM_SIMT && K > 0) {
-    int s = cgemm_tc_f32(M, N, K, alpha, A, B, beta, C, mode, st);
+    int s = cgemm_tc_f32(M, N, K, alpha, A, B, beta, C, mode, st, sA, sB, sC, batch);
     if (s != HARP_E_UNSUPPORTED) return s;
   }
-  return cgemm_simt<float>(M, N, K, alpha, A, B, beta, C, st);
+  return cgemm_simt<float>(M, N, K, alpha, A, B, beta, C, st, HARP_K_GEMM, sA, sB, sC, batch);
 }
 template <>
 int cgemm<double>(int M, int N, int K, double alpha, CView<double> A, CView<double> B, double beta,
@@ -846,48 +863,124 @@ __global__ void copy_block_kernel(int n, const R* sre, const R* sim, long lds, R
   dim[i + (size_t)j * ldd] = sim[i + (size_t)j * lds];
 }
 
+// The diagonal-block inverses (64 x 64 at dre + b * 4096, the last block
+// possibly smaller) copied onto the diagonal of Ti: block b, column c.
 template <typename R>
-static int tri_inv(bool lower, int n, CView<R> T, CView<R> Ti, CView<R> tmp, int row0,
-                   const R* dre, const R* dim, int mode, cudaStream_t st) {
-  if (n <= 0) return HARP_OK;
-  if (n <= kTrsmLeaf) {
-    const long off = (long)(row0 / kTrsmLeaf) * kTrsmLeaf * kTrsmLeaf;
-    ProfScope ps(HARP_K_OTHER, 0.0, st);
-    copy_block_kernel<R><<<dim3(1, n), 64, 0, st>>>(n, dre + off, dim + off, kTrsmLeaf, Ti.re,
-                                                    Ti.im, Ti.cs);
-    HARP_LAUNCHED();
-    return HARP_OK;
-  }
+__global__ void copy_diag_blocks_kernel(int N, const R* __restrict__ dre,
+                                        const R* __restrict__ dim, R* tre, R* tim, long ld) {
+  const int b = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
+  const int nb = min(kTrsmLeaf, N - b * kTrsmLeaf);
+  if (c >= nb || r >= nb) return;
+  const size_t s = (size_t)b * kTrsmLeaf * kTrsmLeaf + r + (size_t)c * kTrsmLeaf;
+  const size_t d = (size_t)b * kTrsmLeaf + r + ((size_t)b * kTrsmLeaf + c) * ld;
+  tre[d] = dre[s];
+  tim[d] = dim[s];
+}
+
+// Nodes of the halving recursion over a triangle of n rows at off: each
+// splits into n1 (a multiple of the 64-row leaf) + n2; listed per depth in
+// increasing offset.
+static void inv_nodes(int off, int n, int depth, std::vector<std::vector<std::array<int, 3>>>& lv) {
+  if (n <= kTrsmLeaf) return;
   const int n1 = ((n / 2) + kTrsmLeaf - 1) / kTrsmLeaf * kTrsmLeaf;
   const int n2 = n - n1;
-  HARP_TRY(tri_inv<R>(lower, n1, T, Ti, tmp, row0, dre, dim, mode, st));
-  HARP_TRY(tri_inv<R>(lower, n2, T.sub(n1, n1), Ti.sub(n1, n1), tmp, row0 + n1, dre, dim, mode, st));
-  if (lower) {
-    // tmp (n2 x n1) = T21 inv(T11); inv21 = -inv(T22) tmp
-    HARP_TRY(cgemm<R>(n2, n1, n1, (R)1, T.sub(n1, 0), Ti, (R)0, tmp, mode, st));
-    HARP_TRY(cgemm<R>(n2, n1, n2, (R)-1, Ti.sub(n1, n1), tmp, (R)0, Ti.sub(n1, 0), mode, st));
-  } else {
-    // tmp (n1 x n2) = T12 inv(T22); inv12 = -inv(T11) tmp
-    HARP_TRY(cgemm<R>(n1, n2, n2, (R)1, T.sub(0, n1), Ti.sub(n1, n1), (R)0, tmp, mode, st));
-    HARP_TRY(cgemm<R>(n1, n2, n1, (R)-1, Ti, tmp, (R)0, Ti.sub(0, n1), mode, st));
+  if ((int)lv.size() <= depth) lv.resize(depth + 1);
+  lv[depth].push_back({off, n1, n2});
+  inv_nodes(off, n1, depth + 1, lv);
+  inv_nodes(off + n1, n2, depth + 1, lv);
+}
+
+// Ti = T^-1 for the unit-lower (lower) or upper triangle of T, bottom-up by
+// depth: for a node [T11 0; T21 T22], inv21 = -inv(T22) (T21 inv(T11)); for
+// [T11 T12; 0 T22], inv12 = -inv(T11) (T12 inv(T22)). The nodes of one depth
+// with the same split and a constant offset step are one batched product
+// (their blocks lie at a constant stride along the diagonal). tmp holds the
+// intermediate product at the block's own position (strictly lower blocks
+// for L, strictly upper for U, so both triangles can share it).
+static int tri_inv(bool lower, int N, CView<float> T, CView<float> Ti, CView<float> tmp,
+                   const float* dre, const float* dim, int mode, cudaStream_t st) {
+  if (N <= 0) return HARP_OK;
+  {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    const int nblk = (N + kTrsmLeaf - 1) / kTrsmLeaf;
+    copy_diag_blocks_kernel<float><<<dim3(nblk, kTrsmLeaf), kTrsmLeaf, 0, st>>>(N, dre, dim, Ti.re,
+                                                                                Ti.im, Ti.cs);
+    HARP_LAUNCHED();
+  }
+  std::vector<std::vector<std::array<int, 3>>> lv;
+  inv_nodes(0, N, 0, lv);
+  for (int d = (int)lv.size() - 1; d >= 0; --d) {
+    const auto& nodes = lv[d];
+    size_t i = 0;
+    while (i < nodes.size()) {
+      const int off = nodes[i][0], n1 = nodes[i][1], n2 = nodes[i][2];
+      size_t j = i + 1;
+      long step = 0;
+      if (j < nodes.size() && nodes[j][1] == n1 && nodes[j][2] == n2) {
+        step = nodes[j][0] - off;
+        ++j;
+        while (j < nodes.size() && nodes[j][1] == n1 && nodes[j][2] == n2 &&
+               nodes[j][0] - nodes[j - 1][0] == step)
+          ++j;
+      }
+      const int cnt = (int)(j - i);
+      auto so = [&](const CView<float>& v) { return step * (v.rs + v.cs); };
+      if (lower) {
+        HARP_TRY(cgemm_batched(n2, n1, n1, 1.f, T.sub(off + n1, off), so(T), Ti.sub(off, off),
+                               so(Ti), 0.f, tmp.sub(off + n1, off), so(tmp), cnt, mode, st));
+        HARP_TRY(cgemm_batched(n2, n1, n2, -1.f, Ti.sub(off + n1, off + n1), so(Ti),
+                               tmp.sub(off + n1, off), so(tmp), 0.f, Ti.sub(off + n1, off), so(Ti),
+                               cnt, mode, st));
+      } else {
+        HARP_TRY(cgemm_batched(n1, n2, n2, 1.f, T.sub(off, off + n1), so(T),
+                               Ti.sub(off + n1, off + n1), so(Ti), 0.f, tmp.sub(off, off + n1),
+                               so(tmp), cnt, mode, st));
+        HARP_TRY(cgemm_batched(n1, n2, n1, -1.f, Ti.sub(off, off), so(Ti), tmp.sub(off, off + n1),
+                               so(tmp), 0.f, Ti.sub(off, off + n1), so(Ti), cnt, mode, st));
+      }
+      i = j;
+    }
   }
   return HARP_OK;
 }
 
-template <typename R>
-int factor_inverses(int N, CView<R> A, const R* dinv_re, const R* dinv_im, R* linv_re,
-                    R* linv_im, R* uinv_re, R* uinv_im, long ldi, R* tre, R* tim, int mode,
-                    cudaStream_t st) {
+int factor_inverses(int N, CView<float> A, const float* dinv_re, const float* dinv_im,
+                    float* linv_re, float* linv_im, float* uinv_re, float* uinv_im, long ldi,
+                    float* tre, float* tim, int mode, cudaStream_t st, cudaStream_t side,
+                    cudaEvent_t fork, cudaEvent_t join) {
   const long nblk = (N + kTrsmLeaf - 1) / kTrsmLeaf;
   const long bs = (long)kTrsmLeaf * kTrsmLeaf;
-  for (R* p : {linv_re, linv_im, uinv_re, uinv_im})
-    HARP_CUDA(cudaMemsetAsync(p, 0, sizeof(R) * (size_t)ldi * N, st));
-  CView<R> tmp = planes<R>(tre, tim, ldi);
-  HARP_TRY(tri_inv<R>(true, N, A, planes<R>(linv_re, linv_im, ldi), tmp, 0, dinv_re, dinv_im,
-                      mode, st));
-  HARP_TRY(tri_inv<R>(false, N, A, planes<R>(uinv_re, uinv_im, ldi), tmp, 0, dinv_re + nblk * bs,
-                      dinv_im + nblk * bs, mode, st));
-  return HARP_OK;
+  for (float* p : {linv_re, linv_im, uinv_re, uinv_im})
+    HARP_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * (size_t)ldi * N, st));
+  CView<float> tmp = planes<float>(tre, tim, ldi);
+  if (!side) {
+    HARP_TRY(tri_inv(true, N, A, planes<float>(linv_re, linv_im, ldi), tmp, dinv_re, dinv_im,
+                     mode, st));
+    return tri_inv(false, N, A, planes<float>(uinv_re, uinv_im, ldi), tmp, dinv_re + nblk * bs,
+                   dinv_im + nblk * bs, mode, st);
+  }
+  // L^-1 on st and U^-1 on the side stream, each with half of the
+  // tensor-core operand workspace (the largest product, a half-size block,
+  // needs a quarter of it).
+  float *wa, *wb;
+  size_t na, nb;
+  int* err;
+  tc_get_workspace(&wa, &na, &wb, &nb, &err);
+  HARP_CUDA(cudaEventRecord(fork, st));
+  HARP_CUDA(cudaStreamWaitEvent(side, fork, 0));
+  tc_set_workspace(wa, na / 2, wb, nb / 2, err);
+  int s1 = tri_inv(true, N, A, planes<float>(linv_re, linv_im, ldi), tmp, dinv_re, dinv_im, mode,
+                   st);
+  tc_set_workspace(wa ? wa + na / 2 : nullptr, na / 2, wb ? wb + nb / 2 : nullptr, nb / 2, err);
+  int s2 = (s1 == HARP_OK)
+               ? tri_inv(false, N, A, planes<float>(uinv_re, uinv_im, ldi), tmp,
+                         dinv_re + nblk * bs, dinv_im + nblk * bs, mode, side)
+               : HARP_OK;
+  tc_set_workspace(wa, na, wb, nb, err);
+  // join even after an error, so that st never runs ahead of queued side work
+  HARP_CUDA(cudaEventRecord(join, side));
+  HARP_CUDA(cudaStreamWaitEvent(st, join, 0));
+  return s1 != HARP_OK ? s1 : s2;
 }
 
 // Solve op(A) X = B with the explicit factor inverses: two dense products
@@ -1096,8 +1189,6 @@ template int lu_solve<double>(int, int, double*, double*, long, const int*, doub
                               double*, double*, char, const double*, const double*, int,
                               cudaStream_t);
 template int diag_inverses<float>(int, CView<float>, float*, float*, float*, float*, cudaStream_t);
-template int factor_inverses<float>(int, CView<float>, const float*, const float*, float*, float*,
-                                    float*, float*, long, float*, float*, int, cudaStream_t);
 template int lu_solve_inv<float>(int, int, const float*, const float*, const float*, const float*,
                                  long, const int*, float*, float*, long, float*, float*, char, int,
                                  cudaStream_t);

@@ -24,6 +24,13 @@ template <>
 int cgemm<double>(int M, int N, int K, double alpha, CView<double> A, CView<double> B, double beta,
                   CView<double> C, int mode, cudaStream_t st);
 
+// batch products C_z = beta*C_z + alpha*A_z*B_z, z < batch, operand z at
+// element offset z*sA (z*sB, z*sC) from the given views (same offset for the
+// real and imaginary planes).
+int cgemm_batched(int M, int N, int K, float alpha, CView<float> A, long sA, CView<float> B,
+                  long sB, float beta, CView<float> C, long sC, int batch, int mode,
+                  cudaStream_t st);
+
 // R = R - Z X in FP64 (the refinement residual; R holds V on entry).
 int residual_fp64(int N, int nrhs, CView<double> Z, CView<double> X, CView<double> R,
                   cudaStream_t st);
@@ -31,6 +38,7 @@ int residual_fp64(int N, int nrhs, CView<double> Z, CView<double> X, CView<doubl
 // Scratch and timeout flag used by the tensor-core GEMM of this thread's
 // current solve (lu_tc.cu); a null workspace selects the CUDA-core GEMM.
 void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int* err);
+void tc_get_workspace(float** a, size_t* a_floats, float** b, size_t* b_floats, int** err);
 
 // Float-float refinement pieces (resid.cu).
 int split_c128(int M, int N, const double* Z, long ldz, float* const hl[4], long ldp,
@@ -69,11 +77,12 @@ int diag_inverses(int N, CView<R> A, R* lre, R* lim, R* ure, R* uim, cudaStream_
 
 // Explicit inverses of the factors held in A (FP32 path): L^-1 and U^-1 as
 // planes (ld ldi), built from the diagonal-block inverses; t planes are
-// scratch of ldi x N.
-template <typename R>
-int factor_inverses(int N, CView<R> A, const R* dinv_re, const R* dinv_im, R* linv_re,
-                    R* linv_im, R* uinv_re, R* uinv_im, long ldi, R* tre, R* tim, int mode,
-                    cudaStream_t st);
+// scratch of ldi x N. With a side stream (and two events to fork and join)
+// U^-1 is built there while L^-1 is built on st.
+int factor_inverses(int N, CView<float> A, const float* dinv_re, const float* dinv_im,
+                    float* linv_re, float* linv_im, float* uinv_re, float* uinv_im, long ldi,
+                    float* tre, float* tim, int mode, cudaStream_t st, cudaStream_t side,
+                    cudaEvent_t fork, cudaEvent_t join);
 // Solve op(A) X = B with the explicit factor inverses (two products).
 template <typename R>
 int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,

@@ -127,6 +127,7 @@ struct TcArgs {
   float* cre;
   float* cim;
   long crs, ccs;
+  long cstride;  // element offset of product z's C (grid z)
   int* err;
 };
 
@@ -146,6 +147,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;  // 1024-byte aligned tiles
   const int i0 = blockIdx.y * TC_BM, j0 = blockIdx.x * TC_BN;
+  const int pz = blockIdx.z * NP;  // first plane of product z in the split operands
+  float* cre = a.cre + blockIdx.z * a.cstride;
+  float* cim = a.cim + blockIdx.z * a.cstride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -181,8 +185,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t fb = su32(&bar_full[s]);
         mbar_expect_tx(fb, STAGE);
         for (int q = 0; q < NP; ++q) {
-          tma_load_3d(st + q * TC_A_PLANE, &tmA, fb, kt * TC_BK, i0, q);
-          tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, kt * TC_BK, j0, q);
+          tma_load_3d(st + q * TC_A_PLANE, &tmA, fb, kt * TC_BK, i0, pz + q);
+          tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, kt * TC_BK, j0, pz + q);
         }
         issued = kt + 1;
       }
@@ -259,8 +263,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (a.beta != 0.f) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          cr[j] = (j < nj) ? a.cre[o0 + (long)j * a.ccs] : 0.f;
-          ci[j] = (j < nj) ? a.cim[o0 + (long)j * a.ccs] : 0.f;
+          cr[j] = (j < nj) ? cre[o0 + (long)j * a.ccs] : 0.f;
+          ci[j] = (j < nj) ? cim[o0 + (long)j * a.ccs] : 0.f;
         }
       }
 #pragma unroll
@@ -277,8 +281,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         if (j < nj) {
-          a.cre[o0 + (long)j * a.ccs] = cr[j];
-          a.cim[o0 + (long)j * a.ccs] = ci[j];
+          cre[o0 + (long)j * a.ccs] = cr[j];
+          cim[o0 + (long)j * a.ccs] = ci[j];
         }
       }
     }
@@ -299,8 +303,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // tile goes through shared memory so both the view reads and the plane
 // writes are coalesced whichever of the view's strides is contiguous.
 __global__ void split_kmajor_kernel(int R, int Kc, int Kp, CView<float> V, float* out,
-                                    size_t plane, int three) {
+                                    size_t plane, int three, long sV) {
   __shared__ float tr[32][33], ti[32][33];  // [k_local][r_local]
+  // product z: view moved by z*sV, planes of product z after those of z-1
+  V.re += blockIdx.z * sV;
+  V.im += blockIdx.z * sV;
+  out += (size_t)blockIdx.z * (three ? 4 : 2) * plane;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   const bool rows_contig = (V.rs == 1);
@@ -377,27 +385,39 @@ void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int*
   g_tc.err = err;
 }
 
+void tc_get_workspace(float** a, size_t* a_floats, float** b, size_t* b_floats, int** err) {
+  *a = g_tc.a;
+  *a_floats = g_tc.a_floats;
+  *b = g_tc.b;
+  *b_floats = g_tc.b_floats;
+  *err = g_tc.err;
+}
+
 int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> B, float beta,
-                 CView<float> C, int mode, cudaStream_t st) {
+                 CView<float> C, int mode, cudaStream_t st, long sA, long sB, long sC,
+                 int batch) {
   // Narrow products (the in-panel updates) stay on the CUDA cores.
   if (M < 64 || N < 64 || K < 32 || !g_tc.a || !g_tc.b) return HARP_E_UNSUPPORTED;
+  if (batch < 1 || batch > 65535) return HARP_E_UNSUPPORTED;
   const bool three = (mode == GEMM_TC_3XTF32);
   const int NP = three ? 4 : 2;
   const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
   const size_t pa = (size_t)M * Kp, pb = (size_t)N * Kp;
-  if ((size_t)NP * pa > g_tc.a_floats || (size_t)NP * pb > g_tc.b_floats) return HARP_E_UNSUPPORTED;
+  if ((size_t)batch * NP * pa > g_tc.a_floats || (size_t)batch * NP * pb > g_tc.b_floats)
+    return HARP_E_UNSUPPORTED;
   {
     ProfScope ps(HARP_K_OTHER, 0.0, st);
     dim3 blk(32, 8);
-    split_kmajor_kernel<<<dim3(Kp / 32, (M + 31) / 32), blk, 0, st>>>(M, K, Kp, A, g_tc.a, pa,
-                                                                       three);
+    split_kmajor_kernel<<<dim3(Kp / 32, (M + 31) / 32, batch), blk, 0, st>>>(M, K, Kp, A, g_tc.a,
+                                                                              pa, three, sA);
     HARP_LAUNCHED();
-    split_kmajor_kernel<<<dim3(Kp / 32, (N + 31) / 32), blk, 0, st>>>(N, K, Kp, B.t(), g_tc.b,
-                                                                       pb, three);
+    split_kmajor_kernel<<<dim3(Kp / 32, (N + 31) / 32, batch), blk, 0, st>>>(N, K, Kp, B.t(),
+                                                                              g_tc.b, pb, three, sB);
     HARP_LAUNCHED();
   }
   CUtensorMap ma, mb;
-  if (!make_map(&ma, g_tc.a, M, Kp, NP, TC_BM) || !make_map(&mb, g_tc.b, N, Kp, NP, TC_BN))
+  if (!make_map(&ma, g_tc.a, M, Kp, NP * batch, TC_BM) ||
+      !make_map(&mb, g_tc.b, N, Kp, NP * batch, TC_BN))
     return HARP_E_UNSUPPORTED;
   TcArgs args;
   args.M = M;
@@ -409,6 +429,7 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   args.cim = C.im;
   args.crs = C.rs;
   args.ccs = C.cs;
+  args.cstride = sC;
   args.err = g_tc.err;
   const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
   const size_t smem = (size_t)TC_STAGES * stage + 1024;
@@ -421,8 +442,8 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
                                    (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
     attr_set[three ? 1 : 0] = true;
   }
-  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
-  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K, st);
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
+  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K * batch, st);
   kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
   HARP_LAUNCHED();
   return HARP_OK;

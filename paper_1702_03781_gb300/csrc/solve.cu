@@ -173,9 +173,10 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
                                     st));
       const size_t NN = (size_t)ctx->max_N * ctx->max_N;
       float* fi = ctx->finv;
-      HARP_TRY(factor_inverses<float>(N, planes<float>(re, im, ctx->ld_lu), dr, di, fi, fi + NN,
-                                      fi + 2 * NN, fi + 3 * NN, ctx->max_N, ctx->finv_tmp,
-                                      ctx->finv_tmp + NN, mode, st));
+      HARP_TRY(factor_inverses(N, planes<float>(re, im, ctx->ld_lu), dr, di, fi, fi + NN,
+                               fi + 2 * NN, fi + 3 * NN, ctx->max_N, ctx->finv_tmp,
+                               ctx->finv_tmp + NN, mode, st, ctx->side, ctx->ev_fac[0],
+                               ctx->ev_big[0]));
     }
     HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, 2 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));

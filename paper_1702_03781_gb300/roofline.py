@@ -3,9 +3,11 @@ the library's instrumentation (CUDA events around each launch, on the
 launching stream) and the peak each class is bounded by.
 
 Peaks:
-  * HBM and dense BF16 tensor throughput: MEASURED_PEAKS.json (driver-written,
-    measured on the GB300s). TF32 tensor peak = measured BF16 peak x
-    the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s).
+  * HBM and dense BF16 tensor throughput: MEASURED_PEAKS.json (measured on
+    the GB300s this runs on). TF32 tensor peak = measured BF16 peak x the
+    nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s). The exact-slice residual
+    counts the bf16 digit products it executes (8 flops per complex
+    multiply-add per digit pair) against the BF16 peak.
   * FP32 and FP64 FMA pipes ("alu"): unit count x SMs x maximum SM clock,
     with the per-SM FMA rates measured by an FMA-loop probe on a GB300
     (FP32 74.9 TFLOP/s, FP64 1.20 TFLOP/s at 1995 MHz): 128 FP32 and 2 FP64
@@ -75,13 +77,21 @@ def source_hash(kind: str) -> str:
 
 def peak_for(kind: str, impl: str, peaks: dict):
     """(bound, peak, unit, note) for a kernel class."""
+    if impl == "tensor_bf16":
+        bf16 = peaks.get("bf16_tflops")
+        if bf16:
+            return "tensor", bf16, "TFLOP/s", "measured bf16 burst (exact-slice digit products)"
+        return "tensor", 1900.0, "TFLOP/s", "fallback bf16 1.9 PF (exact-slice digit products)"
     if impl == "tensor_tf32":
         bf16 = peaks.get("bf16_tflops")
         if bf16:
             return "tensor", bf16 * TF32_OVER_BF16, "TFLOP/s", "measured bf16 burst x 1.1/2.25 (TF32)"
         return "tensor", 1900.0 * TF32_OVER_BF16, "TFLOP/s", "fallback bf16 1.9 PF x 1.1/2.25 (TF32)"
     if impl == "fp32":
-        return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 FMA pipe: 128 FMA/clk/SM x 152 SMs x 2070 MHz"
+        note = "FP32 FMA pipe: 128 FMA/clk/SM x 152 SMs x 2070 MHz"
+        if kind == "panel":
+            note += "; the pivoted panel is latency-bound (one cluster barrier per column)"
+        return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", note
     if impl == "ff2":
         return ("alu", FF2_PEAK_TFLOPS, "TFLOP/s",
                 "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 48 instr per complex MAC "
