@@ -719,7 +719,6 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
 int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb);
 int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
                   int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st);
-bool panel_cluster_ok(int C, size_t smem);
 
 // Factor the panel at column k (rows k..N); returns the width used in *nb.
 template <typename R>

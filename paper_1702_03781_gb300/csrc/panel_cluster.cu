@@ -1,27 +1,34 @@
 // panel_cluster.cu -- one-launch LU panel factorisation with partial pivoting
-// on a thread-block cluster.
+// on a thread-block cluster, rows held in place.
 //
-// The panel A[k0 : k0+M, k0 : k0+nb] is split into row blocks of Mb rows,
-// one per CTA of a cluster (Mb >= nb, so the panel's own top rows all live
-// in CTA 0). Each CTA keeps its block in shared memory, column-major, for
-// the whole factorisation. Column j (one cluster barrier per column):
-//   1. each CTA finds its local candidate (largest |z|^2 among its rows
-//      >= j, first index on ties) and writes it -- value, row index and the
-//      row's nb entries -- into every CTA's candidate table through
-//      distributed shared memory; CTA 0 also writes its current row j;
+// The panel A[k0 : k0+M, k0 : k0+nb] (nb <= 64, a multiple of 16, M >= nb)
+// is split into row blocks of Mb rows, one per CTA of a cluster; each CTA
+// keeps its block in shared memory for the whole factorisation. Rows never
+// move: a pivot row is only marked as chosen, and the row interchanges
+// (LAPACK's ipiv) are composed once at the end and applied when the block is
+// written back. Columns are taken in sub-blocks of 16; warp w of every CTA
+// owns column 16 s + w of sub-block s. Step t:
+//   1. every warp applies the rank-1 term of pivot t-1 to its column of the
+//      sub-block (rows not yet chosen; multiplier a[r][t-1] / pivot), and the
+//      warp owning column t also finds the CTA's candidate (largest |a|^2,
+//      smallest row on ties: two warp reductions) and writes it -- |a|^2,
+//      row, entry -- into every CTA's table through distributed shared
+//      memory;
 //   2. cluster barrier;
-//   3. every CTA reduces its copy of the table (same data, same order, same
-//      pivot p) and has the pivot row and row j locally: CTA 0 writes the
-//      pivot row into row j, the owner of p writes old row j into row p,
-//      and every CTA scales its rows below j and applies the rank-1 update
-//      to the panel's remaining columns.
-// The tables are double-buffered by column parity: a CTA can only publish
-// for column j+2 after every CTA has passed barrier j+1, that is after
-// every CTA has finished reading the tables of column j. Every CTA executes
-// the same sequence of barriers (all branches depend only on the shared
-// tables), so they cannot deadlock. The row interchanges of the rest of the
-// matrix, the triangular solve for U12 and the trailing update stay with
-// the caller.
+//   3. every warp reduces the table (same data, same order: the same pivot in
+//      every CTA), marks the pivot row as chosen and reads the pivot row's
+//      entry in its own column from the owning CTA; chosen rows are never
+//      written again, so that read needs no further barrier.
+// At the end of a sub-block with columns to its right, U12 = L11^-1 A12 is
+// formed from its 16 pivot rows (read from their owners) and every row not
+// yet chosen gets -L21 U12; the owners write U12 into their pivot rows after
+// the next cluster barrier, when no CTA reads the old values any more.
+// Multipliers stay unscaled until the write-back (l = a / pivot). The tables
+// are double-buffered by step parity: a CTA writes the tables of step t+2
+// only after every CTA passed barrier t+1, that is after every CTA finished
+// reading those of step t. Every CTA executes the same barriers. A zero
+// pivot (all remaining |a| = 0) still chooses a row (the smallest), with a
+// zero inverse, and reports its column through *zero_col.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -36,40 +43,55 @@ namespace cg = cooperative_groups;
 namespace harp {
 
 constexpr int kPcThreads = 512;
+constexpr int kPcW = kPcThreads / 32;  // sub-block width: one column per warp
 constexpr int kPcMaxNb = 64;
 constexpr int kPcMaxCluster = 16;
+constexpr int kPcMaxRpl = 12;                 // rows per lane (register arrays)
+constexpr int kPcMaxRows = 32 * kPcMaxRpl;  // rows per CTA
 
 // Bytes of dynamic shared memory for a panel of nb columns, Mb rows per CTA
-// and a cluster of C CTAs.
+// and a cluster of C CTAs (the layout of panel_cluster_kernel).
 __host__ __device__ inline size_t panel_smem_bytes(int nb, int Mb, int C) {
-  return sizeof(float) * ((size_t)2 * nb * (Mb + 1)  // panel block (re, im), column stride Mb + 1
-
-                          + (size_t)4 * C * nb     // candidate rows, 2 parities
-                          + (size_t)4 * nb         // row j, 2 parities
-                          + (size_t)2 * C)         // candidate values
-         + sizeof(int) * (size_t)2 * C;            // candidate row indices
+  return sizeof(float) * ((size_t)2 * nb * (Mb + 1)     // panel block, column stride Mb + 1
+                          + (size_t)2 * nb               // 1 / pivot per step
+                          + (size_t)2 * kPcW * kPcW      // L11 of a sub-block
+                          + (size_t)2 * kPcW * kPcMaxNb  // U12 of a sub-block
+                          + (size_t)3 * 2 * C)           // tables: |a|^2, re, im
+         + sizeof(int) * ((size_t)2 * C                  // table: row
+                          + (size_t)nb                   // pivot row of each step
+                          + (size_t)2 * Mb               // step a row was chosen, its output row
+                          + (size_t)4 * kPcMaxNb);       // interchange composition slots
 }
 
-__global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, float* Aim, long lda,
+// RPL: rows per lane (ceil(Mb / 32)), so that a lane's rows of a column are
+// loaded into registers together and the step's arithmetic is unrolled.
+template <int RPL>
+__global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are, float* Aim, long lda,
                                                                    int k0, int M, int nb, int Mb,
                                                                    int* ipiv, int* zero_col) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
   extern __shared__ __align__(16) float pc_smem[];
-  // Column stride Mb + 1: the row-wise accesses (a row's nb entries) then
-  // fall in distinct banks.
+  // Column stride Mb + 1: a row's entries fall in distinct banks.
   const int ldS = Mb + 1;
-  float* sre = pc_smem;                        // [nb][ldS]
+  float* sre = pc_smem;                              // [nb][ldS]
   float* sim = sre + (size_t)nb * ldS;
-  float* tab_r = sim + (size_t)nb * ldS;       // [2][C][nb]
-  float* tab_i = tab_r + (size_t)2 * C * nb;
-  float* jrow_r = tab_i + (size_t)2 * C * nb;  // [2][nb]
-  float* jrow_i = jrow_r + 2 * nb;
-  float* cand_v = jrow_i + 2 * nb;             // [2][C]
-  int* cand_i = reinterpret_cast<int*>(cand_v + 2 * C);
-  __shared__ float red_v[kPcThreads / 32];
-  __shared__ int red_i[kPcThreads / 32];
+  float* s_inv_r = sim + (size_t)nb * ldS;           // [nb]
+  float* s_inv_i = s_inv_r + nb;
+  float* l11_r = s_inv_i + nb;                       // [kPcW][kPcW]
+  float* l11_i = l11_r + kPcW * kPcW;
+  float* u12_r = l11_i + kPcW * kPcW;                // [kPcW][kPcMaxNb]
+  float* u12_i = u12_r + kPcW * kPcMaxNb;
+  float* t_mag = u12_i + kPcW * kPcMaxNb;            // [2][C]
+  float* t_re = t_mag + 2 * C;
+  float* t_im = t_re + 2 * C;
+  int* t_row = reinterpret_cast<int*>(t_im + 2 * C);  // [2][C]
+  int* piv_row = t_row + 2 * C;                       // [nb] panel row chosen at each step
+  int* step_of = piv_row + nb;                        // [Mb] step a local row was chosen (nb: not)
+  int* dest = step_of + Mb;                           // [Mb] output panel row of a local row
+  int* sl_log = dest + Mb;                            // [2 kPcMaxNb] composition slots
+  int* sl_phys = sl_log + 2 * kPcMaxNb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = crank * Mb;  // first panel row of this CTA
   const int rows = max(0, min(Mb, M - r0));
@@ -95,212 +117,309 @@ __global__ void __launch_bounds__(kPcThreads) panel_cluster_kernel(float* Are, f
         }
       }
     }
+  for (int r = tid; r < Mb; r += kPcThreads) {
+    step_of[r] = nb;
+    dest[r] = r0 + r;
+  }
   __syncthreads();
 
-  float inv_r = 0.f, inv_i = 0.f;  // 1 / pivot of the previous column
-  bool scale_prev = false;
-  for (int j = 0; j < nb; ++j) {
-    const int par = j & 1;
-    // 0. deferred scaling of column j-1 below its diagonal (L multipliers);
-    // the update of step j-1 read it unscaled
-    if (scale_prev) {
-      for (int r = tid; r < rows; r += kPcThreads) {
-        if (r0 + r <= j - 1) continue;
-        float* xr = &sre[(size_t)(j - 1) * ldS + r];
-        float* xi = &sim[(size_t)(j - 1) * ldS + r];
-        const float ar = *xr, ai = *xi;
-        *xr = ar * inv_r - ai * inv_i;
-        *xi = ar * inv_i + ai * inv_r;
-      }
-      scale_prev = false;
-    }
-    // 1. local candidate
-    float best = -1.f;
-    int bi = INT_MAX;
-    for (int r = tid; r < rows; r += kPcThreads) {
-      const int g = r0 + r;
-      if (g < j) continue;
-      const float xr = sre[(size_t)j * ldS + r], xi = sim[(size_t)j * ldS + r];
-      const float v = xr * xr + xi * xi;
-      if (v > best) {
-        best = v;
-        bi = g;
-      }
-    }
+  unsigned chosen = 0;             // bit k: local row lane + 32 k is chosen
+  float u_r = 0.f, u_i = 0.f;      // pivot row's entry in this warp's column
+  float inv_r = 0.f, inv_i = 0.f;  // 1 / pivot of the last step
+  for (int t = 0; t < nb; ++t) {
+    const int par = t & 1;
+    const int sb = t / kPcW;
+    const int c = sb * kPcW + warp;  // this warp's column
+    const bool first = (t == sb * kPcW);
+    // 1. rank-1 term of pivot t-1; the owner of column t finds the candidate
+    if (c >= t) {
+      const bool own = (c == t);
+      float xr[RPL], xi[RPL], ar[RPL], ai[RPL];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_down_sync(0xffffffffu, best, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
+      for (int k = 0; k < RPL; ++k) {  // all loads first
+        const int r = lane + 32 * k;
+        const bool in = r < rows;
+        xr[k] = in ? sre[(size_t)c * ldS + r] : 0.f;
+        xi[k] = in ? sim[(size_t)c * ldS + r] : 0.f;
+        ar[k] = (in && !first) ? sre[(size_t)(t - 1) * ldS + r] : 0.f;
+        ai[k] = (in && !first) ? sim[(size_t)(t - 1) * ldS + r] : 0.f;
       }
-    }
-    if (lane == 0) {
-      red_v[warp] = best;
-      red_i[warp] = bi;
-    }
-    __syncthreads();
-    // every warp reduces the kPcThreads/32 warp candidates with shuffles
-    // (largest value, then smallest row), so all threads hold the result
-    best = (lane < kPcThreads / 32) ? red_v[lane] : -2.f;
-    bi = (lane < kPcThreads / 32) ? red_i[lane] : INT_MAX;
+      float best = -1.f, bre = 0.f, bim = 0.f;
+      int bi = INT_MAX;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    // publish: value and index, the candidate row, and (CTA 0) row j
-    if (tid < nb) {
-      float vr = 0.f, vi = 0.f;
-      if (best >= 0.f) {
-        vr = sre[(size_t)tid * ldS + (bi - r0)];
-        vi = sim[(size_t)tid * ldS + (bi - r0)];
-      }
-      float wr = 0.f, wi = 0.f;
-      if (crank == 0) {
-        wr = sre[(size_t)tid * ldS + j];
-        wi = sim[(size_t)tid * ldS + j];
-      }
-      for (int q = 0; q < C; ++q) {
-        float* tr = cluster.map_shared_rank(tab_r, q);
-        float* ti = cluster.map_shared_rank(tab_i, q);
-        tr[((size_t)par * C + crank) * nb + tid] = vr;
-        ti[((size_t)par * C + crank) * nb + tid] = vi;
-        if (crank == 0) {
-          cluster.map_shared_rank(jrow_r, q)[par * nb + tid] = wr;
-          cluster.map_shared_rank(jrow_i, q)[par * nb + tid] = wi;
+      for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        if (r >= rows || (chosen & (1u << k))) continue;
+        if (!first) {
+          const float lr = ar[k] * inv_r - ai[k] * inv_i, li = ar[k] * inv_i + ai[k] * inv_r;
+          xr[k] = fmaf(-lr, u_r, fmaf(li, u_i, xr[k]));
+          xi[k] = fmaf(-lr, u_i, fmaf(-li, u_r, xi[k]));
+          sre[(size_t)c * ldS + r] = xr[k];
+          sim[(size_t)c * ldS + r] = xi[k];
         }
-      }
-    }
-    if (tid < C) {
-      cluster.map_shared_rank(cand_v, tid)[par * C + crank] = best;
-      cluster.map_shared_rank(cand_i, tid)[par * C + crank] = bi;
-    }
-    cluster.sync();
-
-    // 2. the pivot (same in every CTA), pivot row and row j from the tables
-    // the C candidates reduced with shuffles in every warp (same order:
-    // largest value, then smallest row; win = the owning CTA)
-    int win = lane;
-    best = (lane < C) ? cand_v[par * C + lane] : -2.f;
-    bi = (lane < C) ? cand_i[par * C + lane] : INT_MAX;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      const int ow = __shfl_xor_sync(0xffffffffu, win, off);
-      if (ob > best || (ob == best && oi < bi) || (ob == best && oi == bi && ow < win)) {
-        best = ob;
-        bi = oi;
-        win = ow;
-      }
-    }
-    const int p = bi;
-    const bool zero = !(best > 0.f) || p >= M;
-    if (crank == 0 && tid == 0) {
-      if (zero) {
-        ipiv[k0 + j] = k0 + j;
-        atomicMin(zero_col, k0 + j + 1);
-      } else {
-        ipiv[k0 + j] = k0 + p;
-      }
-    }
-    if (zero) continue;  // uniform across the cluster
-    const float* prow_r = tab_r + ((size_t)par * C + win) * nb;
-    const float* prow_i = tab_i + ((size_t)par * C + win) * nb;
-
-    // 3. swap, scale, rank-1 update (local)
-    if (tid < nb) {
-      if (crank == 0) {
-        sre[(size_t)tid * ldS + j] = prow_r[tid];
-        sim[(size_t)tid * ldS + j] = prow_i[tid];
-      }
-      if (crank == win && p != j) {
-        sre[(size_t)tid * ldS + (p - r0)] = jrow_r[par * nb + tid];
-        sim[(size_t)tid * ldS + (p - r0)] = jrow_i[par * nb + tid];
-      }
-    }
-    __syncthreads();
-    const float pr = prow_r[j], pi = prow_i[j];
-    const float den = pr * pr + pi * pi;
-    inv_r = pr / den;
-    inv_i = -pi / den;
-    scale_prev = true;
-    // rank-1 update of columns j+1.. below row j: warp w takes columns
-    // j+1+w, j+1+w+16, ..., lanes take rows (conflict-free); the multiplier
-    // of a row is formed from the unscaled column j in registers
-    constexpr int kW = kPcThreads / 32;
-    constexpr int kCpw = (kPcMaxNb + kW - 1) / kW;
-    float ur[kCpw], ui[kCpw];
-#pragma unroll
-    for (int m = 0; m < kCpw; ++m) {
-      const int cc = j + 1 + warp + kW * m;
-      ur[m] = (cc < nb) ? prow_r[cc] : 0.f;
-      ui[m] = (cc < nb) ? prow_i[cc] : 0.f;
-    }
-    if (j + 1 + warp < nb) {
-      for (int r = lane; r < rows; r += 32) {
-        if (r0 + r <= j) continue;
-        const float ar = sre[(size_t)j * ldS + r], ai = sim[(size_t)j * ldS + r];
-        const float lr = ar * inv_r - ai * inv_i, li = ar * inv_i + ai * inv_r;
-#pragma unroll
-        for (int m = 0; m < kCpw; ++m) {
-          const int cc = j + 1 + warp + kW * m;
-          if (cc < nb) {
-            float* xr = &sre[(size_t)cc * ldS + r];
-            float* xi = &sim[(size_t)cc * ldS + r];
-            const float vr = *xr, vi = *xi;
-            *xr = fmaf(-lr, ur[m], fmaf(li, ui[m], vr));
-            *xi = fmaf(-lr, ui[m], fmaf(-li, ur[m], vi));
+        if (own) {
+          const float v = xr[k] * xr[k] + xi[k] * xi[k];
+          if (v > best) {
+            best = v;
+            bi = r0 + r;
+            bre = xr[k];
+            bim = xi[k];
           }
         }
       }
+      if (own) {
+        // warp argmax in two reductions: the largest |a|^2 (bit patterns of
+        // non-negative floats order like their values), then the smallest
+        // row among the lanes holding it; a lane without rows offers 0 and
+        // row INT_MAX, which loses every tie
+        const unsigned key = (best >= 0.f) ? __float_as_uint(best) : 0u;
+        const unsigned row = (best >= 0.f) ? (unsigned)bi : (unsigned)INT_MAX;
+        const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+        const unsigned rmin = __reduce_min_sync(0xffffffffu, key == kmax ? row : 0xffffffffu);
+        const int src = __ffs(__ballot_sync(0xffffffffu, key == kmax && row == rmin)) - 1;
+        bre = __shfl_sync(0xffffffffu, bre, src);
+        bim = __shfl_sync(0xffffffffu, bim, src);
+        if (lane < C) {
+          cluster.map_shared_rank(t_mag, lane)[par * C + crank] = __uint_as_float(kmax);
+          cluster.map_shared_rank(t_row, lane)[par * C + crank] = (int)rmin;
+          cluster.map_shared_rank(t_re, lane)[par * C + crank] = bre;
+          cluster.map_shared_rank(t_im, lane)[par * C + crank] = bim;
+        }
+      }
     }
-    __syncthreads();
+    cluster.sync();
+
+    // 3. the pivot (same in every CTA): the same two reductions over the
+    // C table entries (lane q reads entry q; rows are distinct, so the
+    // winner is unique unless no CTA had rows)
+    const unsigned tkey = (lane < C) ? __float_as_uint(t_mag[par * C + lane]) : 0u;
+    const unsigned trow = (lane < C) ? (unsigned)t_row[par * C + lane] : 0xffffffffu;
+    const unsigned tk = __reduce_max_sync(0xffffffffu, tkey);
+    const unsigned tr = __reduce_min_sync(0xffffffffu, tkey == tk ? trow : 0xffffffffu);
+    const int pw = __ffs(__ballot_sync(0xffffffffu, tkey == tk && trow == tr)) - 1;
+    const float pm = __uint_as_float(tk);
+    const int pr = (int)tr;
+    const bool none = (tr >= (unsigned)M);  // no row left anywhere (M >= nb rules it out)
+    const bool zero = !(pm > 0.f);
+    // the pivot row's entry in this warp's column, read early (chosen rows
+    // are not written again)
+    u_r = u_i = 0.f;
+    if (!none && c > t) {
+      const size_t o = (size_t)c * ldS + (pr - pw * Mb);
+      u_r = cluster.map_shared_rank(sre, pw)[o];
+      u_i = cluster.map_shared_rank(sim, pw)[o];
+    }
+    if (zero || none) {
+      inv_r = inv_i = 0.f;
+    } else {
+      const float pvr = t_re[par * C + pw], pvi = t_im[par * C + pw];
+      const float rd = __frcp_rn(pvr * pvr + pvi * pvi);
+      inv_r = pvr * rd;
+      inv_i = -pvi * rd;
+    }
+    if (tid == 0) {
+      piv_row[t] = none ? -1 : pr;
+      s_inv_r[t] = inv_r;
+      s_inv_i[t] = inv_i;
+      if (crank == 0 && zero) atomicMin(zero_col, k0 + t + 1);
+    }
+    if (!none && pw == crank && ((pr - r0) & 31) == lane) {
+      chosen |= 1u << ((pr - r0) >> 5);
+      if (warp == 0) step_of[pr - r0] = t;
+    }
+    // U12 of the previous sub-block into its pivot rows (their old values
+    // were last read before the barrier above)
+    if (first && sb > 0) {
+      const int s0 = (sb - 1) * kPcW, c1 = sb * kPcW, nr = nb - c1;
+      for (int e = tid; e < kPcW * nr; e += kPcThreads) {
+        const int s = e / nr, cc = c1 + e % nr;
+        const int row = piv_row[s0 + s];
+        if (row >= r0 && row < r0 + rows) {
+          sre[(size_t)cc * ldS + (row - r0)] = u12_r[s * kPcMaxNb + cc];
+          sim[(size_t)cc * ldS + (row - r0)] = u12_i[s * kPcMaxNb + cc];
+        }
+      }
+    }
+
+    // end of a sub-block with columns to its right: U12 = L11^-1 A12 and
+    // A22 -= L21 U12 on the rows not yet chosen
+    if (t == (sb + 1) * kPcW - 1 && t + 1 < nb) {
+      __syncthreads();  // this sub-block's pivot rows and inverses are in shared memory
+      const int s0 = sb * kPcW, c1 = s0 + kPcW, nr = nb - c1;
+      for (int e = tid; e < kPcW * (kPcW + nr); e += kPcThreads) {
+        const int s = e / (kPcW + nr), j = e % (kPcW + nr);
+        const int cc = (j < kPcW) ? s0 + j : c1 + (j - kPcW);
+        if (j < kPcW && j >= s) continue;  // L11: strictly lower part only
+        const int row = piv_row[s0 + s];
+        float vr = 0.f, vi = 0.f;
+        if (row >= 0) {
+          const int own = row / Mb;
+          const size_t o = (size_t)cc * ldS + (row - own * Mb);
+          vr = cluster.map_shared_rank(sre, own)[o];
+          vi = cluster.map_shared_rank(sim, own)[o];
+        }
+        if (j < kPcW) {
+          const float ir = s_inv_r[cc], ii = s_inv_i[cc];
+          l11_r[s * kPcW + j] = vr * ir - vi * ii;
+          l11_i[s * kPcW + j] = vr * ii + vi * ir;
+        } else {
+          u12_r[s * kPcMaxNb + cc] = vr;
+          u12_i[s * kPcMaxNb + cc] = vi;
+        }
+      }
+      __syncthreads();
+      // U12 = L11^-1 A12 by forward substitution: warp w takes columns
+      // c1 + w + 16 m together, lane s holds row s; row q is final after
+      // step q and reaches the other lanes by shuffle
+      {
+        constexpr int kCpw = (kPcMaxNb - kPcW + kPcW - 1) / kPcW;  // columns per warp
+        float lr_row[kPcW], li_row[kPcW];
+#pragma unroll
+        for (int q = 0; q < kPcW; ++q) {
+          lr_row[q] = (lane < kPcW && q < lane) ? l11_r[lane * kPcW + q] : 0.f;
+          li_row[q] = (lane < kPcW && q < lane) ? l11_i[lane * kPcW + q] : 0.f;
+        }
+        float ur[kCpw], ui[kCpw];
+#pragma unroll
+        for (int m = 0; m < kCpw; ++m) {
+          const int cc = c1 + warp + kPcW * m;
+          ur[m] = (lane < kPcW && cc < nb) ? u12_r[lane * kPcMaxNb + cc] : 0.f;
+          ui[m] = (lane < kPcW && cc < nb) ? u12_i[lane * kPcMaxNb + cc] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kPcW - 1; ++q) {
+#pragma unroll
+          for (int m = 0; m < kCpw; ++m) {
+            const float vr = __shfl_sync(0xffffffffu, ur[m], q);
+            const float vi = __shfl_sync(0xffffffffu, ui[m], q);
+            ur[m] = fmaf(-lr_row[q], vr, fmaf(li_row[q], vi, ur[m]));
+            ui[m] = fmaf(-lr_row[q], vi, fmaf(-li_row[q], vr, ui[m]));
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < kCpw; ++m) {
+          const int cc = c1 + warp + kPcW * m;
+          if (lane < kPcW && cc < nb) {
+            u12_r[lane * kPcMaxNb + cc] = ur[m];
+            u12_i[lane * kPcMaxNb + cc] = ui[m];
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        if (r >= rows || (chosen & (1u << k))) continue;
+        float lr[kPcW], li[kPcW];
+#pragma unroll
+        for (int s = 0; s < kPcW; ++s) {
+          const float ar = sre[(size_t)(s0 + s) * ldS + r], ai = sim[(size_t)(s0 + s) * ldS + r];
+          const float ir = s_inv_r[s0 + s], ii = s_inv_i[s0 + s];
+          lr[s] = ar * ir - ai * ii;
+          li[s] = ar * ii + ai * ir;
+        }
+        for (int cc = c1 + warp; cc < nb; cc += kPcW) {
+          float xr = sre[(size_t)cc * ldS + r], xi = sim[(size_t)cc * ldS + r];
+#pragma unroll
+          for (int s = 0; s < kPcW; ++s) {
+            const float ur = u12_r[s * kPcMaxNb + cc], ui = u12_i[s * kPcMaxNb + cc];
+            xr = fmaf(-lr[s], ur, fmaf(li[s], ui, xr));
+            xi = fmaf(-lr[s], ui, fmaf(-li[s], ur, xi));
+          }
+          sre[(size_t)cc * ldS + r] = xr;
+          sim[(size_t)cc * ldS + r] = xi;
+        }
+      }
+      __syncthreads();
+    }
   }
-  // scaling of the last column
-  if (scale_prev) {
-    for (int r = tid; r < rows; r += kPcThreads) {
-      if (r0 + r <= nb - 1) continue;
-      float* xr = &sre[(size_t)(nb - 1) * ldS + r];
-      float* xi = &sim[(size_t)(nb - 1) * ldS + r];
-      const float ar = *xr, ai = *xi;
-      *xr = ar * inv_r - ai * inv_i;
-      *xi = ar * inv_i + ai * inv_r;
+
+  // Compose the interchanges: slots map logical positions to panel rows;
+  // step t moves its pivot row to position t (ipiv: the position it came
+  // from) and the row at t to that position.
+  __syncthreads();
+  if (warp == 0) {
+    for (int v = lane; v < nb; v += 32) {
+      sl_log[v] = v;
+      sl_phys[v] = v;
+    }
+    __syncwarp();
+    int ns = nb;
+    for (int t = 0; t < nb; ++t) {
+      const int p = piv_row[t];
+      if (p < 0) {
+        if (crank == 0 && lane == 0) ipiv[k0 + t] = k0 + t;
+        continue;
+      }
+      int q = -1;
+      for (int v0 = 0; v0 < ns && q < 0; v0 += 32) {
+        const int v = v0 + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, v < ns && sl_phys[v] == p);
+        if (hit) q = v0 + __ffs(hit) - 1;
+      }
+      if (q < 0) {
+        q = ns++;
+        if (lane == 0) {
+          sl_log[q] = p;
+          sl_phys[q] = p;
+        }
+      }
+      __syncwarp();
+      if (crank == 0 && lane == 0) ipiv[k0 + t] = k0 + sl_log[q];
+      if (lane == 0 && q != t) {
+        const int x = sl_phys[t];
+        sl_phys[t] = sl_phys[q];
+        sl_phys[q] = x;
+      }
+      __syncwarp();
+    }
+    for (int v = lane; v < ns; v += 32) {
+      const int ph = sl_phys[v];
+      if (ph >= r0 && ph < r0 + rows) dest[ph - r0] = sl_log[v];
     }
   }
   __syncthreads();
 
-  // store the row block
-  for (int c = 0; c < nb; ++c)
+  // write back: below a row's own step the scaled multipliers, from it on
+  // the U entries
+  float* ore = Are + (size_t)k0 + (size_t)k0 * lda;
+  float* oim = Aim + (size_t)k0 + (size_t)k0 * lda;
+  for (int cc = 0; cc < nb; ++cc) {
+    const float ir = s_inv_r[cc], ii = s_inv_i[cc];
     for (int r = tid; r < rows; r += kPcThreads) {
-      gre[r + (size_t)c * lda] = sre[(size_t)c * ldS + r];
-      gim[r + (size_t)c * lda] = sim[(size_t)c * ldS + r];
+      const float ar = sre[(size_t)cc * ldS + r], ai = sim[(size_t)cc * ldS + r];
+      float vr = ar, vi = ai;
+      if (cc < step_of[r]) {
+        vr = ar * ir - ai * ii;
+        vi = ar * ii + ai * ir;
+      }
+      const size_t o = (size_t)dest[r] + (size_t)cc * lda;
+      ore[o] = vr;
+      oim[o] = vi;
     }
-  cluster.sync();  // no CTA leaves while a peer may still write its tables
+  }
+  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
 // Plan a cluster panel for M rows: returns the panel width to use (0 when
 // the cluster path does not apply) and the cluster size and rows per CTA.
-bool panel_cluster_ok(int C, size_t smem);
+bool panel_cluster_ok(int C, size_t smem, int Mb);
 
-// Residency of a cluster of C CTAs with this much shared memory, cached per
-// C as the largest size known to fit and the smallest known not to.
-static bool cluster_resident(int C, size_t smem) {
+// Residency of a cluster of C CTAs (instantiation for Mb rows) with this
+// much shared memory, cached per (C, instantiation) as the largest size
+// known to fit and the smallest known not to.
+static bool cluster_resident(int C, size_t smem, int Mb) {
   static std::mutex mu;
-  static size_t ok_max[kPcMaxCluster + 1] = {0};
-  static size_t bad_min[kPcMaxCluster + 1] = {0};
+  static size_t ok_max[kPcMaxCluster + 1][5] = {};
+  static size_t bad_min[kPcMaxCluster + 1][5] = {};
+  const int rpl = (Mb + 31) / 32;
+  const int i = rpl <= 2 ? 0 : rpl <= 4 ? 1 : rpl <= 6 ? 2 : rpl <= 8 ? 3 : 4;
   std::lock_guard<std::mutex> lock(mu);
-  if (smem <= ok_max[C]) return true;
-  if (bad_min[C] && smem >= bad_min[C]) return false;
-  const bool ok = panel_cluster_ok(C, smem);
-  if (ok) ok_max[C] = std::max(ok_max[C], smem);
-  else bad_min[C] = bad_min[C] ? std::min(bad_min[C], smem) : smem;
+  if (smem <= ok_max[C][i]) return true;
+  if (bad_min[C][i] && smem >= bad_min[C][i]) return false;
+  const bool ok = panel_cluster_ok(C, smem, Mb);
+  if (ok) ok_max[C][i] = std::max(ok_max[C][i], smem);
+  else bad_min[C][i] = bad_min[C][i] ? std::min(bad_min[C][i], smem) : smem;
   return ok;
 }
 
@@ -312,14 +431,16 @@ int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int*
   // largest that fits.
   const size_t budget = std::min<size_t>(ctx->smem_optin, 220 * 1024) - 2048;
   constexpr int kRowsTarget = 192;
-  for (int nb = std::min(want_nb, kPcMaxNb); nb >= 16; nb /= 2) {
+  for (int nb : {64, 32, 16}) {  // multiples of the sub-block width
+    if (nb > want_nb || nb > kPcMaxNb) continue;
     int best_c = 0, best_mb = 0;
     for (int C : {1, 2, 4, 8, 16}) {
       int mb = (M + C - 1) / C;
       if (mb < nb) mb = nb;
+      if (M < nb || mb > kPcMaxRows) continue;
       if (C > 1 && (C - 1) * mb >= M) continue;  // every CTA owns rows
       if (panel_smem_bytes(nb, mb, C) > budget) continue;
-      if (!cluster_resident(C, panel_smem_bytes(nb, mb, C))) continue;
+      if (!cluster_resident(C, panel_smem_bytes(nb, mb, C), mb)) continue;
       best_c = C;
       best_mb = mb;
       if (mb <= kRowsTarget) break;
@@ -333,17 +454,41 @@ int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int*
   return 0;
 }
 
+using PanelKernel = void (*)(float*, float*, long, int, int, int, int, int*, int*);
+
+// The instantiation for Mb rows per CTA (rows per lane rounded up) and its
+// index among them.
+static PanelKernel panel_kernel_for(int Mb, int* idx) {
+  const int rpl = (Mb + 31) / 32;
+  static const PanelKernel ks[] = {panel_cluster_kernel<2>, panel_cluster_kernel<4>,
+                                   panel_cluster_kernel<6>, panel_cluster_kernel<8>,
+                                   panel_cluster_kernel<12>};
+  const int i = rpl <= 2 ? 0 : rpl <= 4 ? 1 : rpl <= 6 ? 2 : rpl <= 8 ? 3 : 4;
+  *idx = i;
+  return ks[i];
+}
+
+static int panel_attrs(PanelKernel k, int idx) {
+  static bool done[5] = {false, false, false, false, false};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[idx]) return HARP_OK;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return cuda_status(cudaGetLastError());
+  done[idx] = true;
+  return HARP_OK;
+}
+
 int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
                   int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st) {
+  if (Mb > kPcMaxRows || nb % kPcW != 0 || nb > kPcMaxNb || M < nb || C > kPcMaxCluster)
+    return HARP_E_UNSUPPORTED;
   const size_t smem = panel_smem_bytes(nb, Mb, C);
-  static bool attr_set = false;
-  if (!attr_set) {
-    HARP_CUDA(cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   220 * 1024));
-    HARP_CUDA(cudaFuncSetAttribute(panel_cluster_kernel,
-                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    attr_set = true;
-  }
+  int idx = 0;
+  PanelKernel kern = panel_kernel_for(Mb, &idx);
+  HARP_TRY(panel_attrs(kern, idx));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(kPcThreads);
@@ -357,14 +502,20 @@ int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ProfScope ps(HARP_K_PANEL, 4.0 * M * nb * (double)(nb - 1), st);
-  HARP_CUDA(cudaLaunchKernelEx(&cfg, panel_cluster_kernel, re, im, ld, k0, M, nb, Mb, ipiv,
-                               zero_col));
+  HARP_CUDA(cudaLaunchKernelEx(&cfg, kern, re, im, ld, k0, M, nb, Mb, ipiv, zero_col));
   HARP_LAUNCHED();
   return HARP_OK;
 }
 
-// Whether a cluster of C CTAs with this much shared memory can be resident.
-bool panel_cluster_ok(int C, size_t smem) {
+// Whether a cluster of C CTAs of the instantiation for Mb rows, with this
+// much shared memory, can be resident.
+bool panel_cluster_ok(int C, size_t smem, int Mb) {
+  int idx = 0;
+  PanelKernel kern = panel_kernel_for(Mb, &idx);
+  if (panel_attrs(kern, idx) != HARP_OK) {
+    cudaGetLastError();
+    return false;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(kPcThreads);
@@ -376,15 +527,8 @@ bool panel_cluster_ok(int C, size_t smem) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           220 * 1024) != cudaSuccess ||
-      cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                           1) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, panel_cluster_kernel, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
