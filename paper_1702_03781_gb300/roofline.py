@@ -63,10 +63,11 @@ def shares(prof: dict) -> dict:
 
 def source_hash(kind: str) -> str:
     """Hash of the sources a kernel class is built from (traffic validity)."""
-    files = {"fill": ["fill.cu", "ff.cuh"], "gemm": ["lu_tc.cu"], "residual": ["resid.cu", "ff.cuh"],
+    files = {"fill": ["fill.cu", "ff.cuh"], "gemm": ["lu_tc.cu"],
+             "residual": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"],
              "panel": ["panel_cluster.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
              "adjoint": ["adjoint.cu"], "other": ["dense.cu"],
-             "resid_update": ["resid.cu", "ff.cuh"]}.get(kind, [])
+             "resid_update": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"]}.get(kind, [])
     h = hashlib.sha256()
     for f in files:
         p = os.path.join(_ROOT, "paper_1702_03781_gb300", "csrc", f)
