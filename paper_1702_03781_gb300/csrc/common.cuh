@@ -175,6 +175,12 @@ struct harp_ctx {
   float* finv;  // 4 planes: Linv re, im, Uinv re, im
   float* finv_tmp;  // 2 planes
   int finv_valid;
+  // L^-1 and U^-1 as tensor-core operand planes (K-major hi/lo TF32, split
+  // once per factorisation for the forward solves), finv_split_floats each;
+  // finv_split_mode: the GEMM mode they were split for, -1 when not valid.
+  float* finv_split;
+  size_t finv_split_floats;
+  int finv_split_mode;
 
   // Captured graphs of the FP32 triangular solves of the refinement, keyed
   // by (N, nrhs, mode) for trans 'N' [0] and 'T' [1]; replayed on the

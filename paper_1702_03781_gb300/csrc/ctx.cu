@@ -36,7 +36,7 @@ extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launc
 
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
-                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->gpair, c->red, c->dstatus,
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->finv_split, c->gpair, c->red, c->dstatus,
                   c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -122,6 +122,9 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   alloc((void**)&c->zbuf, NN * sizeof(float2));
   alloc((void**)&c->finv, 4 * NN * sizeof(float));
   alloc((void**)&c->finv_tmp, 2 * NN * sizeof(float));
+  c->finv_split_floats = 4 * (size_t)max_N * kp;
+  alloc((void**)&c->finv_split, 2 * c->finv_split_floats * sizeof(float));
+  c->finv_split_mode = -1;
   if (ok) {
     // Tensor-core residual buffers: optional (the float-float residual
     // serves when they do not fit).

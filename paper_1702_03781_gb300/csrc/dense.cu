@@ -988,7 +988,8 @@ int factor_inverses(int N, CView<float> A, const float* dinv_re, const float* di
 template <typename R>
 int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,
                  const R* uinv_im, long ldi, const int* perm, R* bre, R* bim, long ldb, R* tre,
-                 R* tim, char trans, int mode, cudaStream_t st) {
+                 R* tim, char trans, int mode, cudaStream_t st, const float* li_split,
+                 const float* ui_split) {
   CView<R> Li = planes<R>(const_cast<R*>(linv_re), const_cast<R*>(linv_im), ldi);
   CView<R> Ui = planes<R>(const_cast<R*>(uinv_re), const_cast<R*>(uinv_im), ldi);
   CView<R> Bm = planes<R>(bre, bim, ldb), Tm = planes<R>(tre, tim, ldb);
@@ -999,8 +1000,16 @@ int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* u
       permute_rows_kernel<R><<<grid, 256, 0, st>>>(N, nrhs, perm, bre, bim, tre, tim, ldb, 0);
       HARP_LAUNCHED();
     }
-    HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Li, Tm, (R)0, Bm, mode, st));  // B = L^-1 P b
-    HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Ui, Bm, (R)0, Tm, mode, st));  // T = U^-1 B
+    // B = L^-1 P b, T = U^-1 B (the inverses pre-split when given)
+    int s1 = HARP_E_UNSUPPORTED, s2 = HARP_E_UNSUPPORTED;
+    if constexpr (std::is_same<R, float>::value)
+      if (li_split) s1 = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, li_split, Tm, 0.f, Bm, mode, st);
+    if (s1 == HARP_E_UNSUPPORTED) s1 = cgemm<R>(N, nrhs, N, (R)1, Li, Tm, (R)0, Bm, mode, st);
+    HARP_TRY(s1);
+    if constexpr (std::is_same<R, float>::value)
+      if (ui_split) s2 = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, ui_split, Bm, 0.f, Tm, mode, st);
+    if (s2 == HARP_E_UNSUPPORTED) s2 = cgemm<R>(N, nrhs, N, (R)1, Ui, Bm, (R)0, Tm, mode, st);
+    HARP_TRY(s2);
     HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));
   } else {
     HARP_TRY(cgemm<R>(N, nrhs, N, (R)1, Ui.t(), Bm, (R)0, Tm, mode, st));  // T = U^-T b
@@ -1190,7 +1199,7 @@ template int lu_solve<double>(int, int, double*, double*, long, const int*, doub
 template int diag_inverses<float>(int, CView<float>, float*, float*, float*, float*, cudaStream_t);
 template int lu_solve_inv<float>(int, int, const float*, const float*, const float*, const float*,
                                  long, const int*, float*, float*, long, float*, float*, char, int,
-                                 cudaStream_t);
+                                 cudaStream_t, const float*, const float*);
 template int diag_inverses<double>(int, CView<double>, double*, double*, double*, double*,
                                    cudaStream_t);
 template int interleaved_to_planes<float, float>(int, int, const float*, long, float*, float*, long,

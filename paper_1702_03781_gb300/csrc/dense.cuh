@@ -84,10 +84,21 @@ int factor_inverses(int N, CView<float> A, const float* dinv_re, const float* di
                     float* tre, float* tim, int mode, cudaStream_t st, cudaStream_t side,
                     cudaEvent_t fork, cudaEvent_t join);
 // Solve op(A) X = B with the explicit factor inverses (two products).
+// li_split / ui_split (optional): L^-1 and U^-1 already split into
+// tensor-core operand planes (tc_split_operand, same mode), used by the
+// 'N' products.
 template <typename R>
 int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,
                  const R* uinv_im, long ldi, const int* perm, R* bre, R* bim, long ldb, R* tre,
-                 R* tim, char trans, int mode, cudaStream_t st);
+                 R* tim, char trans, int mode, cudaStream_t st, const float* li_split = nullptr,
+                 const float* ui_split = nullptr);
+
+// K-major tensor-core operand planes of V (R x K) for repeated use, and the
+// product that takes them as its A operand (lu_tc.cu).
+int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats, int mode,
+                     cudaStream_t st);
+int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
+                        float beta, CView<float> C, int mode, cudaStream_t st);
 
 // Solve op(A) X = B with the factors of lu_factor and their diagonal-block
 // inverses (dinv planes: the L blocks, then the U blocks); B (N x nrhs split

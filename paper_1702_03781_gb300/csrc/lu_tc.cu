@@ -449,4 +449,68 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   return HARP_OK;
 }
 
+// K-major TF32 planes of an operand V (R x K) into out, as the GEMM's own
+// split makes them (NP planes of R x Kp), for an operand used by many products.
+int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats, int mode,
+                     cudaStream_t st) {
+  const bool three = (mode == GEMM_TC_3XTF32);
+  const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
+  const size_t pl = (size_t)R * Kp;
+  if ((size_t)(three ? 4 : 2) * pl > out_floats) return HARP_E_UNSUPPORTED;
+  ProfScope ps(HARP_K_OTHER, 0.0, st);
+  split_kmajor_kernel<<<dim3(Kp / 32, (R + 31) / 32, 1), dim3(32, 8), 0, st>>>(R, K, Kp, V, out, pl,
+                                                                              three, 0);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// C = beta*C + alpha * A B with A given as planes from tc_split_operand
+// (M x K, same mode): only B is split here.
+int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
+                        float beta, CView<float> C, int mode, cudaStream_t st) {
+  if (M < 64 || N < 64 || K < 32 || !g_tc.b || !a_split) return HARP_E_UNSUPPORTED;
+  const bool three = (mode == GEMM_TC_3XTF32);
+  const int NP = three ? 4 : 2;
+  const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
+  const size_t pb = (size_t)N * Kp;
+  if ((size_t)NP * pb > g_tc.b_floats) return HARP_E_UNSUPPORTED;
+  {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    split_kmajor_kernel<<<dim3(Kp / 32, (N + 31) / 32, 1), dim3(32, 8), 0, st>>>(N, K, Kp, B.t(),
+                                                                                g_tc.b, pb, three, 0);
+    HARP_LAUNCHED();
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, const_cast<float*>(a_split), M, Kp, NP, TC_BM) ||
+      !make_map(&mb, g_tc.b, N, Kp, NP, TC_BN))
+    return HARP_E_UNSUPPORTED;
+  TcArgs args;
+  args.M = M;
+  args.N = N;
+  args.nk = Kp / TC_BK;
+  args.alpha = alpha;
+  args.beta = beta;
+  args.cre = C.re;
+  args.cim = C.im;
+  args.crs = C.rs;
+  args.ccs = C.cs;
+  args.cstride = 0;
+  args.err = g_tc.err;
+  const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
+  const size_t smem = (size_t)TC_STAGES * stage + 1024;
+  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
+      three ? tc_cgemm_kernel<true> : tc_cgemm_kernel<false>;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[three ? 1 : 0]) {
+    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
+    attr_set[three ? 1 : 0] = true;
+  }
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
+  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K, st);
+  kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
 }  // namespace harp

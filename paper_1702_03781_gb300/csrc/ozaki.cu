@@ -554,13 +554,16 @@ int oz_digit_bits(int K) {
 }
 
 int oz_groups(int K, int b, double rho) {
-  // Smallest G with b (G - 1) >= 55 + log2(sqrt K) + log2 G + log2 rho: the
-  // first dropped group, of G pair sums with digits below 2^(b-1) and
-  // weight 2^-b(G+1), summed over K terms of random sign, stays below 2^-55
-  // of ||op(Z)||_inf max|X_j| (the scalings lose at most a factor 16).
+  // Smallest G with b (G - 1) >= 53 + log2(sqrt K) + log2 G + log2 rho. The
+  // first dropped group (G pair sums of digits below 2^(b-1), weight
+  // 2^-b(G+1)) is below G 2^(-b(G-1)-2) of 2^(sig+tau) per term; over K terms
+  // of random sign, sqrt(K) times that, i.e. below 2^-55 of 2^(sig+tau) <=
+  // 16 ||op(Z)||_inf max|X_j|: under 2^-51 of the stopping test's scale,
+  // about the FP64 rounding of one residual entry. rho scales the
+  // correction's columns against the iterate's.
   const double lr = (rho > 0.0) ? std::log2(std::min(rho, 1.0)) : -1100.0;
   for (int G = 2; G <= kOzMaxG; ++G)
-    if (b * (G - 1) >= 55.0 + 0.5 * std::log2((double)std::max(K, 1)) + std::log2((double)G) + lr)
+    if (b * (G - 1) >= 53.0 + 0.5 * std::log2((double)std::max(K, 1)) + std::log2((double)G) + lr)
       return G;
   return kOzMaxG;
 }

@@ -71,9 +71,12 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
                      ctx->solve_key[g][1] == nrhs && ctx->solve_key[g][2] == mode;
   const size_t NN = (size_t)ctx->max_N * ctx->max_N;
   const float* fi = ctx->finv;
+  const bool pre = (ctx->finv_split_mode == mode);
+  const float* lsp = pre ? ctx->finv_split : nullptr;
+  const float* usp = pre ? ctx->finv_split + ctx->finv_split_floats : nullptr;
   auto run = [&](cudaStream_t s) {
     return lu_solve_inv<float>(N, nrhs, fi, fi + NN, fi + 2 * NN, fi + 3 * NN, ctx->max_N,
-                               ctx->perm, wre, wim, ldw, tre, tim, trans, mode, s);
+                               ctx->perm, wre, wim, ldw, tre, tim, trans, mode, s, lsp, usp);
   };
   (void)lre;
   (void)lim;
@@ -177,6 +180,17 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
                                fi + 2 * NN, fi + 3 * NN, ctx->max_N, ctx->finv_tmp,
                                ctx->finv_tmp + NN, mode, st, ctx->side, ctx->ev_fac[0],
                                ctx->ev_big[0]));
+      // the inverses as tensor-core operands, once for all forward solves
+      ctx->finv_split_mode = -1;
+      if (mode != GEMM_SIMT) {
+        const size_t fs = ctx->finv_split_floats;
+        const long ldi = ctx->max_N;
+        if (tc_split_operand(N, N, planes<float>(fi, fi + NN, ldi), ctx->finv_split, fs, mode,
+                             st) == HARP_OK &&
+            tc_split_operand(N, N, planes<float>(fi + 2 * NN, fi + 3 * NN, ldi),
+                             ctx->finv_split + fs, fs, mode, st) == HARP_OK)
+          ctx->finv_split_mode = mode;
+      }
     }
     HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, 2 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));
