@@ -98,8 +98,9 @@ int harp_ctx_create(harp_ctx** ctx, int device, int max_N, int max_nrhs);
 int harp_ctx_destroy(harp_ctx* ctx);
 
 /* Device pointer and leading dimension of the context's FP64 reduced
- * matrix (c128, max_N x max_N). harp_fill writes it in the mixed modes; a
- * caller may also write its own FP64 matrix there before a mixed solve. */
+ * matrix (c128, max_N x max_N). harp_fill writes it in the mixed modes (this
+ * call first waits, on the host, until that write is complete); a caller may
+ * also write its own FP64 matrix there before a mixed solve. */
 int harp_ctx_z64(harp_ctx* ctx, void** z64, int* ld);
 
 /* Fill the reduced MBF matrix (Eq. 3 and 4 for every ordered pair m != n,
@@ -115,10 +116,14 @@ int harp_ctx_z64(harp_ctx* ctx, void** z64, int* ld);
  *   self_stride  complex elements between antennas; 0 = one block
  *                shared by all antennas                           [10]
  *   Z            output, N x N column-major: c128 for HARP_FP64, c64 for
- *                the mixed modes (then the context's FP64 matrix is
- *                written too)                                      [11]
+ *                HARP_FP32 and the mixed modes (FP32 evaluation)   [11]
  *   ldz          leading dimension of Z (>= N)                    [12]
  *   prec         harp_prec                                        [13]
+ * In the mixed modes the call also starts the FP64-accurate evaluation of the
+ * context's matrix Z64 on the context's own fill stream, after the work
+ * already queued on `stream`; it runs beside whatever follows (the
+ * factorisation needs only Z). mbf_solve waits for it before its first use
+ * of Z64, and harp_ctx_z64 waits for it on the host.
  * Coincident antennas (r == 0) are detected on the device: the entries of
  * that pair are written as zero and HARP_E_COINCIDENT is returned (the call
  * synchronises the stream to read the flag). */

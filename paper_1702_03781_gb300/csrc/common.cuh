@@ -191,6 +191,11 @@ struct harp_ctx {
   // Look-ahead LU: side stream for the trailing updates and event pools
   // (panel factored / trailing update done), n_events each.
   cudaStream_t side;
+  // Stream of the FP64-accurate fill of Z64 in the mixed modes, which runs
+  // beside the factorisation (it needs only the FP32 matrix); ev_fill_fork
+  // orders it after the caller's earlier work, ev_z64 marks Z64 complete.
+  cudaStream_t fill_stream;
+  cudaEvent_t ev_fill_fork, ev_z64;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;
@@ -217,6 +222,7 @@ struct harp_ctx {
   // Reductions and status.
   double* red;      // device scratch, 16 + 2*max_nrhs doubles
   double* red_host; // pinned host mirror, same size
-  int* dstatus;     // device status words [0] bits, [1] zero-pivot column, [2] timeout
+  int* dstatus;     // device status words [0] bits, [1] zero-pivot column, [2] timeout,
+                    // [3] bits of the background Z64 fill (not read)
   int* hstatus;     // pinned host mirror
 };

@@ -44,6 +44,9 @@ static void free_all(harp_ctx* c) {
     if (c->solve_graph[g]) cudaGraphExecDestroy(c->solve_graph[g]);
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
+  if (c->ev_fill_fork) cudaEventDestroy(c->ev_fill_fork);
+  if (c->ev_z64) cudaEventDestroy(c->ev_z64);
   for (int e = 0; e < c->n_events; ++e) {
     if (c->ev_fac && c->ev_fac[e]) cudaEventDestroy(c->ev_fac[e]);
     if (c->ev_big && c->ev_big[e]) cudaEventDestroy(c->ev_big[e]);
@@ -164,6 +167,11 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   }
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+  if (ok && cudaStreamCreateWithFlags(&c->fill_stream, cudaStreamNonBlocking) != cudaSuccess)
+    ok = false;
+  if (ok && (cudaEventCreateWithFlags(&c->ev_fill_fork, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&c->ev_z64, cudaEventDisableTiming) != cudaSuccess))
+    ok = false;
   if (ok) {
     c->n_events = max_N / 16 + 2;
     c->ev_fac = (cudaEvent_t*)calloc(c->n_events, sizeof(cudaEvent_t));
@@ -208,6 +216,11 @@ extern "C" int harp_ctx_z64(harp_ctx* c, void** z64, int* ld) {
   if (!c) return -1;
   if (!z64) return -2;
   if (!ld) return -3;
+  // a mixed fill may still be writing Z64 on the context's fill stream
+  {
+    DeviceGuard g(c->device);
+    if (c->ev_z64) HARP_CUDA(cudaEventSynchronize(c->ev_z64));
+  }
   *z64 = c->z64;
   *ld = c->ld64;
   return HARP_OK;

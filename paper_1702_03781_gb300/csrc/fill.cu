@@ -16,6 +16,9 @@
 // with a 4-pair x TN-entry register tile per thread. Lanes run along (S,T)
 // with T fastest, so stores are runs of Nm consecutive rows of a column.
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "ff.cuh"
@@ -276,14 +279,47 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_ff_kernel(FillArgs a) {
                                   (double)Si[i][j] + ((double)s1i[i][j] + (double)s2i[i][j]));
         if (m == n) dv = a.self[(size_t)m * a.self_stride + T + (size_t)S * Nm];
         reinterpret_cast<double2*>(a.Z)[row + col * a.ldz] = dv;
-        a.Z32[row + col * a.ld32] = make_float2((float)dv.x, (float)dv.y);
+        if (a.Z32) a.Z32[row + col * a.ld32] = make_float2((float)dv.x, (float)dv.y);
       }
     }
   }
 }
 
+// How many 16-CTA clusters of this kernel and shared-memory size can be
+// resident at once (one per GPC with 16 free SMs), cached; 0 when none.
+static int fill_cluster_slots(void (*kern)(FillArgs), size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<void*, size_t>, int>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : cache)
+    if (e.first.first == (void*)kern && e.first.second == smem) return e.second;
+  int n = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(kFillThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cache.push_back({{(void*)kern, smem}, n});
+  return n;
+}
+
+// background: the fill runs beside the factorisation. It is then launched as
+// 16-CTA clusters (each occupies one GPC) on half of the GPCs, so that whole
+// GPCs stay free for the factorisation's 16-CTA panel clusters; a plain grid
+// over all SMs would leave no GPC with 16 free SMs until the fill ends.
 static int launch_fill_ff(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int nchunks,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool background) {
   void (*kern)(FillArgs) = nullptr;
   switch (TN) {
     case 1: kern = fill_ff_kernel<1>; break;
@@ -293,10 +329,30 @@ static int launch_fill_ff(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, 
     default: return HARP_E_UNSUPPORTED;
   }
   HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int per_chunk = std::max(1, (ctx->num_sms + nchunks - 1) / nchunks);
-  dim3 grid(std::min(a.n_items, per_chunk), nchunks);
   ProfScope ps(HARP_K_FILL, 8.0 * a.Nm * a.Nm * a.K * (double)a.Na * (a.Na - 1), st);
-  kern<<<grid, kFillThreads, smem, st>>>(a);
+  const int slots = background ? fill_cluster_slots(kern, smem) : 0;
+  if (slots >= 2) {
+    // about half of the cluster slots (4 of the 7 a GB300 holds), split over
+    // the source chunks
+    const int q = std::max(1, ((slots + 1) / 2) / nchunks);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16 * q, nchunks);
+    cfg.blockDim = dim3(kFillThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HARP_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+  } else {
+    const int per_chunk = std::max(1, (ctx->num_sms + nchunks - 1) / nchunks);
+    dim3 grid(std::min(a.n_items, per_chunk), nchunks);
+    kern<<<grid, kFillThreads, smem, st>>>(a);
+  }
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -345,7 +401,8 @@ static bool plan_fill(const harp_ctx* ctx, int Nm, int K, size_t csz, int* s_chu
 
 int fill_dispatch(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
                   const double* coef, const double* self_blocks, long self_stride, void* Z,
-                  long ldz, float2* Z32, long ld32, int prec_kind, cudaStream_t st) {
+                  long ldz, float2* Z32, long ld32, int prec_kind, cudaStream_t st,
+                  int* status = nullptr, bool background = false) {
   // prec_kind: 0 = FP64 only, 1 = FP64 with rounded c64 copy, 2 = FP32 only
   FillArgs a;
   a.Na = Na;
@@ -363,7 +420,7 @@ int fill_dispatch(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos
   a.ldz = ldz;
   a.Z32 = Z32;
   a.ld32 = ld32;
-  a.status = ctx->dstatus;
+  a.status = status ? status : ctx->dstatus;
   a.n_mtiles = (Na + kPairsPerTile - 1) / kPairsPerTile;
   a.n_items = Na * a.n_mtiles;
   // prec_kind 1 (mixed): float-float kernel, 16-byte staged entries
@@ -376,7 +433,7 @@ int fill_dispatch(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos
   a.Wp = 32 * TN;
   const int nchunks = (Nm + sc - 1) / sc;
   if (prec_kind == 2) return launch_fill<float, false>(ctx, a, TN, smem, nchunks, st);
-  if (prec_kind == 1) return launch_fill_ff(ctx, a, TN, smem, nchunks, st);
+  if (prec_kind == 1) return launch_fill_ff(ctx, a, TN, smem, nchunks, st, background);
   return launch_fill<double, false>(ctx, a, TN, smem, nchunks, st);
 }
 
@@ -416,12 +473,23 @@ extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const doub
   else if (prec == HARP_FP32)
     s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, Z, ldz,
                       nullptr, 0, 2, st);
-  else
-    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, ctx->z64,
-                      ctx->ld64, reinterpret_cast<float2*>(Z), ldz, 1, st);
+  else  // mixed: the FP32 matrix for the factorisation, here
+    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, Z, ldz,
+                      nullptr, 0, 2, st);
   if (s != HARP_OK) return s;
   HARP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
   HARP_CUDA(cudaStreamSynchronize(st));
   if (ctx->hstatus[0] & ST_COINCIDENT) return HARP_E_COINCIDENT;
+  if (mixed) {
+    // The FP64-accurate Z64, which only the refinement reads, on the
+    // context's fill stream beside the factorisation that follows, after the
+    // caller's earlier work (a previous solve may still read Z64).
+    HARP_CUDA(cudaEventRecord(ctx->ev_fill_fork, st));
+    HARP_CUDA(cudaStreamWaitEvent(ctx->fill_stream, ctx->ev_fill_fork, 0));
+    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, ctx->z64,
+                      ctx->ld64, nullptr, 0, 1, ctx->fill_stream, ctx->dstatus + 3, true);
+    if (s != HARP_OK) return s;
+    HARP_CUDA(cudaEventRecord(ctx->ev_z64, ctx->fill_stream));
+  }
   return HARP_OK;
 }

@@ -249,6 +249,8 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   // element (i, k) of op(Z): (1, ld) for Z, (ld, 1) for Z^T
   const long ars = tr ? ldw : 1, acs = tr ? 1 : ldw;
   const bool slices = use_slices(ctx);
+  // Z64 may still be filling on the context's fill stream (mixed harp_fill)
+  HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_z64, 0));
   if (slices) {
     HARP_TRY(oz_prepare(ctx, N, ctx->z64, ctx->ld64, tr, ctx->red + 0, st));
   } else {

@@ -65,16 +65,20 @@ def test_fill_fp32_matches_oracle(harp):
     assert _rel(Z, Zo) <= 1e-5
 
 
-def test_fill_mixed_writes_fp64_and_rounded_copy(harp):
+def test_fill_mixed_writes_fp32_matrix_and_fp64_accurate_z64(harp):
+    """The mixed fill returns the FP32 evaluation (the factorisation's input)
+    and fills the context's Z64 on its own stream; harp_ctx_z64 (harp.z64)
+    waits for that fill, which must then be FP64-accurate."""
     p = synth.station()
     pos, coef, sb = _dev(p)
     Z32 = harp.fill(pos, p.freq_hz, coef, sb, prec="mixed")
-    torch.cuda.synchronize()
+    Zf = harp.fill(pos, p.freq_hz, coef, sb, prec="fp32")
     Z64 = harp.z64(p.N)
     Zo = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
     z64 = _np(Z64)
     assert np.max(np.abs(z64 - Zo)) <= 1e-13 * np.max(np.abs(Zo))
-    assert torch.equal(Z32, Z64.to(torch.complex64))
+    assert torch.equal(Z32, Zf)
+    assert _rel(_np(Z32).astype(np.complex128), Zo) <= 1e-5
 
 
 def test_fill_shared_self_block(harp):
