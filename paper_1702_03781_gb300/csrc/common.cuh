@@ -112,6 +112,8 @@ struct DeviceGuard {
 
 // ---------------------------------------------------------------------------
 // The context: device workspace sized at creation.
+constexpr int kPmapInts = 1 + 2 * 128;  // count, then up to 128 row pairs
+
 struct harp_ctx {
   int device;
   int max_N, max_nrhs;
@@ -199,6 +201,9 @@ struct harp_ctx {
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;
+  // Row maps of the cluster-factored panels (n_events x kPmapInts ints): the
+  // net interchange of panel i as (destination, source) row pairs.
+  int* pmap;
 
   // Tensor-core refinement residual (ozaki.cu), allocated when memory
   // allows (oz_a == nullptr: the float-float residual is used): bf16 digit

@@ -36,7 +36,7 @@ extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launc
 
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
-                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->finv_split, c->gpair, c->red, c->dstatus,
+                  c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->finv_split, c->pmap, c->gpair, c->red, c->dstatus,
                   c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -174,6 +174,8 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
     ok = false;
   if (ok) {
     c->n_events = max_N / 16 + 2;
+    if (cudaMalloc((void**)&c->pmap, (size_t)c->n_events * kPmapInts * sizeof(int)) != cudaSuccess)
+      ok = false;
     c->ev_fac = (cudaEvent_t*)calloc(c->n_events, sizeof(cudaEvent_t));
     c->ev_big = (cudaEvent_t*)calloc(c->n_events, sizeof(cudaEvent_t));
     if (!c->ev_fac || !c->ev_big) ok = false;

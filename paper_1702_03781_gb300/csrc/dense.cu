@@ -426,6 +426,82 @@ static int laswp(R* re, R* im, long ld, int nrows, const int* ipiv, int k1, int 
   return HARP_OK;
 }
 
+// The row interchanges of a cluster-factored panel on the columns [a0, a1)
+// and [b0, b1) (and perm, as one more column, when given), from the panel's
+// exported row map: rmap[0] = n entries, then pairs (destination row, source
+// row), every destination taking the old content of its source. One warp
+// per column: all loads, then all stores.
+template <typename R>
+__global__ void __launch_bounds__(kSwapWarps * 32) laswp_map_kernel(R* Are, R* Aim, long lda,
+                                                                    const int* rmap, int a0, int a1,
+                                                                    int b0, int b1, int* perm) {
+  __shared__ int dst[2 * kNB], src[2 * kNB];
+  __shared__ int nt_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) nt_s = min(rmap[0], 2 * kNB);
+  __syncthreads();
+  const int nt = nt_s;
+  for (int t = tid; t < nt; t += blockDim.x) {
+    dst[t] = rmap[1 + 2 * t];
+    src[t] = rmap[2 + 2 * t];
+  }
+  __syncthreads();
+  const int na = a1 - a0, nb = b1 - b0;
+  const int ncols = na + nb + (perm ? 1 : 0);
+  constexpr int kPer = (2 * kNB + 31) / 32;
+  for (int c = blockIdx.x * kSwapWarps + warp; c < ncols; c += gridDim.x * kSwapWarps) {
+    if (c < na + nb) {
+      const int col = (c < na) ? a0 + c : b0 + (c - na);
+      R* cr = Are + (size_t)col * lda;
+      R* ci = Aim + (size_t)col * lda;
+      R vr[kPer], vi[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) {
+          vr[q] = cr[src[t]];
+          vi[q] = ci[src[t]];
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) {
+          cr[dst[t]] = vr[q];
+          ci[dst[t]] = vi[q];
+        }
+      }
+    } else {
+      int v[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) v[q] = perm[src[t]];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int t = lane + 32 * q;
+        if (t < nt) perm[dst[t]] = v[q];
+      }
+    }
+  }
+}
+
+template <typename R>
+static int laswp_map(R* re, R* im, long ld, const int* rmap, int a0, int a1, int b0, int b1,
+                     int* perm, cudaStream_t st) {
+  const int n = std::max(0, a1 - a0) + std::max(0, b1 - b0) + (perm ? 1 : 0);
+  if (n == 0) return HARP_OK;
+  const int blocks = std::min((n + kSwapWarps - 1) / kSwapWarps, 4 * 152);
+  ProfScope ps(HARP_K_SWAP, 0.0, st);
+  laswp_map_kernel<R><<<blocks, kSwapWarps * 32, 0, st>>>(re, im, ld, rmap, a0, std::max(a0, a1),
+                                                          b0, std::max(b0, b1), perm);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
 __global__ void iota_kernel(int* p, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = i;
@@ -718,19 +794,24 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
 // Cluster panel (panel_cluster.cu), FP32 only.
 int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb);
 int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
-                  int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st);
+                  int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
 
 // Factor the panel at column k (rows k..N); returns the width used in *nb.
+// rmap (optional): where a cluster panel exports its row map; *mapped
+// tells whether it did.
 template <typename R>
 static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int k,
-                        int want, int* ipiv, int* zero_col, int mode, cudaStream_t st, int* nb) {
+                        int want, int* ipiv, int* zero_col, int mode, cudaStream_t st, int* nb,
+                        int* rmap = nullptr, bool* mapped = nullptr) {
+  if (mapped) *mapped = false;
   if constexpr (std::is_same<R, float>::value) {
     // the plan only offers clusters that can be resident
     int C = 0, Mb = 0;
     const int w = panel_cluster_plan(ctx, N - k, want, &C, &Mb);
     if (w > 0) {
       *nb = w;
-      return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st);
+      if (mapped) *mapped = (rmap != nullptr);
+      return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st, rmap);
     }
   }
   *nb = want;
@@ -752,11 +833,15 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
   CView<float> A = planes<float>(re, im, ld);
   cudaStream_t s2 = ctx->side;
   std::vector<int> ks, nbs;
+  std::vector<char> maps;  // panel i exported its row map to pmap(i)
+  auto pmap = [&](int i) { return ctx->pmap + (size_t)i * kPmapInts; };
   int k = 0, nb = 0;
+  bool mp = false;
   HARP_TRY(factor_panel<float>(ctx, N, A, re, im, ld, 0, std::min(kNB, N), ipiv, zero_col, mode,
-                               st, &nb));
+                               st, &nb, pmap(0), &mp));
   ks.push_back(0);
   nbs.push_back(nb);
+  maps.push_back(mp);
   for (int i = 0;; ++i) {
     if (i + 1 >= ctx->n_events) return HARP_E_UNSUPPORTED;
     k = ks[i];
@@ -771,21 +856,28 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
       int C = 0, Mb = 0;
       nb1 = panel_cluster_plan(ctx, N - k1, want, &C, &Mb);
       if (nb1 <= 0) nb1 = want;
-      HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, k1, k1 + nb1, 0, 0, nullptr, st));
+      if (maps[i])
+        HARP_TRY(laswp_map<float>(re, im, ld, pmap(i), k1, k1 + nb1, 0, 0, nullptr, st));
+      else
+        HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, k1, k1 + nb1, 0, 0, nullptr, st));
       HARP_TRY(trsm<float>(true, true, nb, nb1, A.sub(k, k), A.sub(k, k1), GEMM_SIMT, st));
       HARP_TRY(cgemm<float>(N - k1, nb1, nb, -1.f, A.sub(k1, k), A.sub(k, k1), 1.f,
                             A.sub(k1, k1), GEMM_SIMT, st));
       int used = 0;
       HARP_TRY(factor_panel<float>(ctx, N, A, re, im, ld, k1, nb1, ipiv, zero_col, mode, st,
-                                   &used));
+                                   &used, pmap(i + 1), &mp));
       nb1 = used;
       ks.push_back(k1);
       nbs.push_back(nb1);
+      maps.push_back(mp);
     }
     // side stream: the rest of panel i's update
     const int k2 = k1 + nb1;  // first column past panel i+1
     HARP_CUDA(cudaStreamWaitEvent(s2, ctx->ev_fac[i], 0));
-    HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, 0, k, k2, N, perm, s2));
+    if (maps[i])
+      HARP_TRY(laswp_map<float>(re, im, ld, pmap(i), 0, k, k2, N, perm, s2));
+    else
+      HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, 0, k, k2, N, perm, s2));
     if (k2 < N) {
       HARP_TRY(trsm<float>(true, true, nb, N - k2, A.sub(k, k), A.sub(k, k2), mode, s2));
       HARP_TRY(cgemm<float>(N - k1, N - k2, nb, -1.f, A.sub(k1, k), A.sub(k, k2), 1.f,

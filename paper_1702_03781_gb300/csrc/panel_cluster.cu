@@ -6,7 +6,8 @@
 // keeps its block in shared memory for the whole factorisation. Rows never
 // move: a pivot row is only marked as chosen, and the row interchanges
 // (LAPACK's ipiv) are composed once at the end and applied when the block is
-// written back. Columns are taken in sub-blocks of 16; warp w of every CTA
+// written back (and, when asked, exported as a row map for the other
+// columns' interchanges). Columns are taken in sub-blocks of 16; warp w of every CTA
 // owns column 16 s + w of sub-block s. Step t:
 //   1. every warp applies the rank-1 term of pivot t-1 to its column of the
 //      sub-block (rows not yet chosen; multiplier a[r][t-1] / pivot), and the
@@ -68,7 +69,8 @@ __host__ __device__ inline size_t panel_smem_bytes(int nb, int Mb, int C) {
 template <int RPL>
 __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are, float* Aim, long lda,
                                                                    int k0, int M, int nb, int Mb,
-                                                                   int* ipiv, int* zero_col) {
+                                                                   int* ipiv, int* zero_col,
+                                                                   int* rmap) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
@@ -373,6 +375,15 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
       }
       __syncwarp();
     }
+    // the net row move of the panel for the other columns (rmap, when
+    // given): row k0 + sl_log[v] takes old row k0 + sl_phys[v]
+    if (rmap && crank == 0) {
+      if (lane == 0) rmap[0] = ns;
+      for (int v = lane; v < ns; v += 32) {
+        rmap[1 + 2 * v] = k0 + sl_log[v];
+        rmap[2 + 2 * v] = k0 + sl_phys[v];
+      }
+    }
     for (int v = lane; v < ns; v += 32) {
       const int ph = sl_phys[v];
       if (ph >= r0 && ph < r0 + rows) dest[ph - r0] = sl_log[v];
@@ -454,7 +465,7 @@ int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int*
   return 0;
 }
 
-using PanelKernel = void (*)(float*, float*, long, int, int, int, int, int*, int*);
+using PanelKernel = void (*)(float*, float*, long, int, int, int, int, int*, int*, int*);
 
 // The instantiation for Mb rows per CTA (rows per lane rounded up) and its
 // index among them.
@@ -482,7 +493,7 @@ static int panel_attrs(PanelKernel k, int idx) {
 }
 
 int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
-                  int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st) {
+                  int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap) {
   if (Mb > kPcMaxRows || nb % kPcW != 0 || nb > kPcMaxNb || M < nb || C > kPcMaxCluster)
     return HARP_E_UNSUPPORTED;
   const size_t smem = panel_smem_bytes(nb, Mb, C);
@@ -502,7 +513,7 @@ int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ProfScope ps(HARP_K_PANEL, 4.0 * M * nb * (double)(nb - 1), st);
-  HARP_CUDA(cudaLaunchKernelEx(&cfg, kern, re, im, ld, k0, M, nb, Mb, ipiv, zero_col));
+  HARP_CUDA(cudaLaunchKernelEx(&cfg, kern, re, im, ld, k0, M, nb, Mb, ipiv, zero_col, rmap));
   HARP_LAUNCHED();
   return HARP_OK;
 }
