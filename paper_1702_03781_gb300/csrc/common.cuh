@@ -222,6 +222,11 @@ struct harp_ctx {
   int* oz_cexp;
   double* oz_part;
   int oz_N, oz_bits, oz_slices, oz_Kp, oz_Np;
+  // Ticket of the mixed fill whose Z64 the current slices (trans 'N') were
+  // made from, on the fill stream with ||Z64||_inf in oz_znorm; -1 after any
+  // other preparation or after harp_ctx_z64 handed Z64 out for writing.
+  long long z64_ticket, oz_ticket;
+  double* oz_znorm;
   int residual_mode;  // HARP_RESIDUAL_*
 
   // Reductions and status.

@@ -37,7 +37,8 @@ extern "C" unsigned long long harp_kernel_launches(void) { return g_kernel_launc
 static void free_all(harp_ctx* c) {
   void* ptrs[] = {c->z64, c->lu_re, c->lu_im, c->ipiv, c->w_re, c->w_im, c->x_re, c->x_im,
                   c->r_re, c->r_im, c->v_re, c->v_im, c->t_re, c->t_im, c->perm, c->zff, c->xff, c->rowsum, c->tc_a, c->tc_b, c->dinv_re, c->dinv_im, c->rpart, c->finv, c->finv_tmp, c->finv_split, c->pmap, c->gpair, c->red, c->dstatus,
-                  c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part};
+                  c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part,
+                  c->oz_znorm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int g = 0; g < 2; ++g)
@@ -151,18 +152,22 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
     oalloc((void**)&c->oz_rexp, (size_t)max_N * sizeof(int));
     oalloc((void**)&c->oz_cexp, (size_t)max_nrhs * sizeof(int));
     oalloc((void**)&c->oz_part, 32 * (size_t)max_N * sizeof(double));
+    oalloc((void**)&c->oz_znorm, sizeof(double));
     if (oz_ok) {
       c->oz_max_slices = S;
       c->oz_slot_pairs = slots;
     } else {
-      void* op[] = {c->oz_a, c->oz_y, c->oz_slots, c->oz_acc, c->oz_rexp, c->oz_cexp, c->oz_part};
+      void* op[] = {c->oz_a,    c->oz_y,    c->oz_slots, c->oz_acc,
+                    c->oz_rexp, c->oz_cexp, c->oz_part,  c->oz_znorm};
       for (void* p : op)
         if (p) cudaFree(p);
       c->oz_a = c->oz_y = nullptr;
       c->oz_slots = c->oz_rexp = c->oz_cexp = nullptr;
-      c->oz_acc = c->oz_part = nullptr;
+      c->oz_acc = c->oz_part = c->oz_znorm = nullptr;
     }
     c->oz_N = -1;
+    c->z64_ticket = 0;
+    c->oz_ticket = -1;
     c->residual_mode = HARP_RESIDUAL_SLICES;
   }
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
@@ -218,7 +223,9 @@ extern "C" int harp_ctx_z64(harp_ctx* c, void** z64, int* ld) {
   if (!c) return -1;
   if (!z64) return -2;
   if (!ld) return -3;
-  // a mixed fill may still be writing Z64 on the context's fill stream
+  // the caller may write Z64 now: slices made from a fill's Z64 no longer
+  // stand for it; a mixed fill may still be writing it on the fill stream
+  c->oz_ticket = -1;
   {
     DeviceGuard g(c->device);
     if (c->ev_z64) HARP_CUDA(cudaEventSynchronize(c->ev_z64));

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "ff.cuh"
+#include "ozaki.cuh"
 #include "prof.cuh"
 
 namespace harp {
@@ -489,6 +490,13 @@ extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const doub
     s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, ctx->z64,
                       ctx->ld64, nullptr, 0, 1, ctx->fill_stream, ctx->dstatus + 3, true);
     if (s != HARP_OK) return s;
+    // and, when the refinement uses the tensor-core residual, the digit
+    // slices of Z64 for trans 'N' solves, on the same stream
+    const long long ticket = ++ctx->z64_ticket;
+    if (ctx->oz_a && ctx->residual_mode == HARP_RESIDUAL_SLICES &&
+        oz_prepare(ctx, (int)N, ctx->z64, ctx->ld64, false, ctx->oz_znorm, ctx->fill_stream) ==
+            HARP_OK)
+      ctx->oz_ticket = ticket;
     HARP_CUDA(cudaEventRecord(ctx->ev_z64, ctx->fill_stream));
   }
   return HARP_OK;

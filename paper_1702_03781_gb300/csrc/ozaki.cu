@@ -573,6 +573,7 @@ int oz_pairs(int G) { return G * (G - 1) / 2; }
 int oz_prepare(harp_ctx* ctx, int N, const double2* z, long ld, bool trans, double* znorm,
                cudaStream_t st) {
   if (!ctx->oz_a) return HARP_E_UNSUPPORTED;
+  ctx->oz_ticket = -1;  // the caller marks slices made from a fill's Z64
   const int b = oz_digit_bits(N);
   const int s = oz_groups(N, b, 1.0) - 1;
   if (s > ctx->oz_max_slices) return HARP_E_UNSUPPORTED;

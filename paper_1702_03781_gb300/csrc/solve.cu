@@ -252,7 +252,13 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   // Z64 may still be filling on the context's fill stream (mixed harp_fill)
   HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_z64, 0));
   if (slices) {
-    HARP_TRY(oz_prepare(ctx, N, ctx->z64, ctx->ld64, tr, ctx->red + 0, st));
+    // the slices of the last mixed fill's Z64, when it made them for trans
+    // 'N' (the wait above covers them), else made here
+    if (!tr && ctx->oz_ticket == ctx->z64_ticket && ctx->oz_ticket > 0 && ctx->oz_N == N)
+      HARP_CUDA(cudaMemcpyAsync(ctx->red + 0, ctx->oz_znorm, sizeof(double),
+                                cudaMemcpyDeviceToDevice, st));
+    else
+      HARP_TRY(oz_prepare(ctx, N, ctx->z64, ctx->ld64, tr, ctx->red + 0, st));
   } else {
     HARP_TRY(split_c128(N, N, (const double*)ctx->z64, ctx->ld64, zhl, ldw, st));
     HARP_TRY(norm_inf_planes_f32(N, N, zhl[0], zhl[1], ars, acs, ctx->rowsum, ctx->red + 0, st));
