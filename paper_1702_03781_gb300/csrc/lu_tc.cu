@@ -6,8 +6,9 @@
 // accumulators, Dr = Ar Br - Ai Bi and Di = Ar Bi + Ai Br (the minus sign is
 // the instruction descriptor's negate-A bit). In the three-term TF32 mode
 // each FP32 operand x is split as x = hi + lo with hi = x rounded to TF32 and
-// lo = x - hi (exact), and a*b ~ ah bh + ah bl + al bh (12 MMAs per k8 step),
-// which keeps the product accurate to about 2^-22 relative; the one-term
+// lo = x - hi rounded to TF32 (both to nearest), and a*b ~ ah bh + ah bl +
+// al bh (12 MMAs per k8 step), which keeps the product accurate to about
+// 3 x 2^-24 relative; the one-term
 // mode uses ah bh only (4 MMAs per k8 step).
 //
 // Operands are first copied into "K-major" hi/lo planes (row r of the MMA
@@ -330,8 +331,11 @@ __global__ void split_kmajor_kernel(int R, int Kc, int Kp, CView<float> V, float
     out[o] = hr;
     out[plane + o] = hi;
     if (three) {
-      out[2 * plane + o] = xr - hr;
-      out[3 * plane + o] = xi - hi;
+      // lo = x - hi (exact), itself rounded to nearest TF32: the MMA would
+      // otherwise drop its low mantissa bits by truncation
+      const float lr = xr - hr, li = xi - hi;
+      out[2 * plane + o] = __uint_as_float((__float_as_uint(lr) + 0x1000u) & 0xffffe000u);
+      out[3 * plane + o] = __uint_as_float((__float_as_uint(li) + 0x1000u) & 0xffffe000u);
     }
   }
 }
