@@ -98,6 +98,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def wideband_throughput(device: int, n_ctx: int = 4, n_freq: int = 64) -> dict:
+    """Config 3: the station layout at n_freq frequencies over 50-350 MHz
+    (Nm 6..20, N 1536..5120, 256 ports each), filled and solved (mixed, to
+    the LAPACK tolerance) by the library's batch scheduler on n_ctx
+    contexts. One warm-up batch of n_ctx frequencies, then one timed batch
+    of all of them (host wall clock around the synchronous batch call)."""
+    import torch
+    from paper_1702_03781_gb300 import harp as H
+    from paper_1702_03781_gb300 import synth
+    d = f"cuda:{device}"
+    probs = synth.wideband(n_freq)
+    items = [H.BatchItem(torch.from_numpy(q.pos).to(d), q.freq_hz, torch.from_numpy(q.coef).to(d),
+                         torch.from_numpy(q.self_blocks).to(d)) for q in probs]
+    max_N = max(it.N for it in items)
+    ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n_ctx)]
+    H.solve_batch(ctxs, items[-n_ctx:], prec="mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H.solve_batch(ctxs, items, prec="mixed", check=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ok = all(it.status == 0 for it in items)
+    iters = [it.iters for it in items]
+    for c in ctxs:
+        c.close()
+    return {"frequencies": n_freq, "contexts": n_ctx, "N_range": [min(it.N for it in items), max_N],
+            "ms_per_frequency": round(1e3 * wall / n_freq, 3), "wall_ms": round(1e3 * wall, 2),
+            "all_converged": ok, "corrections": [min(iters), max(iters)],
+            "timing": "host wall clock around one synchronous batch call"}
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -149,6 +180,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-wideband", action="store_true")
     ap.add_argument("--nvtx-step", default="",
                     help="run the warm-up, then one step of this path ('mixed' or 'fp64') inside "
                          "an NVTX range named harp_step, and exit (for an ncu launch list)")
@@ -317,6 +349,8 @@ def main():
             "roofline_kernels": roof_all,
             "kernel_shares": shares,
         }
+        if not args.no_wideband:
+            line["wideband"] = wideband_throughput(local)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(1)
         print(json.dumps(line))
