@@ -60,8 +60,7 @@ __host__ __device__ inline size_t panel_smem_bytes(int nb, int Mb, int C) {
                           + (size_t)3 * 2 * C)           // tables: |a|^2, re, im
          + sizeof(int) * ((size_t)2 * C                  // table: row
                           + (size_t)nb                   // pivot row of each step
-                          + (size_t)2 * Mb               // step a row was chosen, its output row
-                          + (size_t)4 * kPcMaxNb);       // interchange composition slots
+                          + (size_t)2 * Mb);             // step a row was chosen, its output row
 }
 
 // RPL: rows per lane (ceil(Mb / 32)), so that a lane's rows of a column are
@@ -92,33 +91,24 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
   int* piv_row = t_row + 2 * C;                       // [nb] panel row chosen at each step
   int* step_of = piv_row + nb;                        // [Mb] step a local row was chosen (nb: not)
   int* dest = step_of + Mb;                           // [Mb] output panel row of a local row
-  int* sl_log = dest + Mb;                            // [2 kPcMaxNb] composition slots
-  int* sl_phys = sl_log + 2 * kPcMaxNb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = crank * Mb;  // first panel row of this CTA
   const int rows = max(0, min(Mb, M - r0));
   float* gre = Are + (size_t)(k0 + r0) + (size_t)k0 * lda;
   float* gim = Aim + (size_t)(k0 + r0) + (size_t)k0 * lda;
 
-  // load the row block (independent loads batched before the stores)
-  for (int c = 0; c < nb; ++c)
-    for (int rb = 0; rb < rows; rb += 4 * kPcThreads) {
-      float vr[4], vi[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = rb + tid + u * kPcThreads;
-        vr[u] = (r < rows) ? gre[r + (size_t)c * lda] : 0.f;
-        vi[u] = (r < rows) ? gim[r + (size_t)c * lda] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = rb + tid + u * kPcThreads;
-        if (r < rows) {
-          sre[(size_t)c * ldS + r] = vr[u];
-          sim[(size_t)c * ldS + r] = vi[u];
-        }
-      }
-    }
+  // load the row block: every element's asynchronous copy is issued before
+  // any is waited for, so the block costs one memory round trip
+  for (int e = tid; e < rows * nb; e += kPcThreads) {
+    const int c = e / rows, r = e - c * rows;
+    const unsigned dr = (unsigned)__cvta_generic_to_shared(sre + (size_t)c * ldS + r);
+    const unsigned di = (unsigned)__cvta_generic_to_shared(sim + (size_t)c * ldS + r);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr),
+                 "l"(gre + r + (size_t)c * lda));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(di),
+                 "l"(gim + r + (size_t)c * lda));
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   for (int r = tid; r < Mb; r += kPcThreads) {
     step_of[r] = nb;
     dest[r] = r0 + r;
@@ -336,58 +326,68 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
     }
   }
 
-  // Compose the interchanges: slots map logical positions to panel rows;
-  // step t moves its pivot row to position t (ipiv: the position it came
-  // from) and the row at t to that position.
+  // Compose the interchanges (every CTA, the same data): step t swaps
+  // position t with the position of its pivot row (ipiv: that position).
+  // Only the first nb positions and the pivot rows' positions are touched.
+  // A row below nb moves only when it is chosen, and the row displaced from
+  // position t is always one of the first nb rows, so warp 0 tracks two
+  // tables in registers, lane l holding entries l and l + 32: prow (the row
+  // at position v < nb) and rpos (the position of row v < nb).
   __syncthreads();
   if (warp == 0) {
-    for (int v = lane; v < nb; v += 32) {
-      sl_log[v] = v;
-      sl_phys[v] = v;
-    }
-    __syncwarp();
-    int ns = nb;
+    int prow0 = lane, prow1 = lane + 32, rpos0 = lane, rpos1 = lane + 32;
+    const int pv0 = (lane < nb) ? piv_row[lane] : -1;
+    const int pv1 = (lane + 32 < nb) ? piv_row[lane + 32] : -1;
     for (int t = 0; t < nb; ++t) {
-      const int p = piv_row[t];
-      if (p < 0) {
+      const int hi_t = t >> 5, ln_t = t & 31;
+      const int p = __shfl_sync(0xffffffffu, hi_t ? pv1 : pv0, ln_t);
+      if (p < 0) {  // no row left: the position keeps its row
         if (crank == 0 && lane == 0) ipiv[k0 + t] = k0 + t;
         continue;
       }
-      int q = -1;
-      for (int v0 = 0; v0 < ns && q < 0; v0 += 32) {
-        const int v = v0 + lane;
-        const unsigned hit = __ballot_sync(0xffffffffu, v < ns && sl_phys[v] == p);
-        if (hit) q = v0 + __ffs(hit) - 1;
+      const int jq = __shfl_sync(0xffffffffu, (p & 32) ? rpos1 : rpos0, p & 31);
+      const int rt = __shfl_sync(0xffffffffu, hi_t ? prow1 : prow0, ln_t);
+      const int j = (p < nb) ? jq : p;  // the pivot row's current position
+      if (crank == 0 && lane == 0) ipiv[k0 + t] = k0 + j;
+      if (lane == ln_t) (hi_t ? prow1 : prow0) = p;
+      if (p < nb && lane == (p & 31)) ((p & 32) ? rpos1 : rpos0) = t;
+      if (j != t) {  // row rt (below nb) moves to position j
+        if (j < nb && lane == (j & 31)) ((j & 32) ? prow1 : prow0) = rt;
+        if (lane == (rt & 31)) ((rt & 32) ? rpos1 : rpos0) = j;
       }
-      if (q < 0) {
-        q = ns++;
-        if (lane == 0) {
-          sl_log[q] = p;
-          sl_phys[q] = p;
-        }
-      }
-      __syncwarp();
-      if (crank == 0 && lane == 0) ipiv[k0 + t] = k0 + sl_log[q];
-      if (lane == 0 && q != t) {
-        const int x = sl_phys[t];
-        sl_phys[t] = sl_phys[q];
-        sl_phys[q] = x;
-      }
-      __syncwarp();
     }
     // the net row move of the panel for the other columns (rmap, when
-    // given): row k0 + sl_log[v] takes old row k0 + sl_phys[v]
+    // given): position v < nb takes row prow[v]; a row v < nb that ended
+    // at or beyond nb is listed after them
+    const bool d0 = lane < nb && rpos0 >= nb, d1 = lane + 32 < nb && rpos1 >= nb;
+    const unsigned b0 = __ballot_sync(0xffffffffu, d0), b1 = __ballot_sync(0xffffffffu, d1);
+    const unsigned below = (1u << lane) - 1u;
     if (rmap && crank == 0) {
-      if (lane == 0) rmap[0] = ns;
-      for (int v = lane; v < ns; v += 32) {
-        rmap[1 + 2 * v] = k0 + sl_log[v];
-        rmap[2 + 2 * v] = k0 + sl_phys[v];
+      if (lane == 0) rmap[0] = nb + __popc(b0) + __popc(b1);
+      if (lane < nb) {
+        rmap[1 + 2 * lane] = k0 + lane;
+        rmap[2 + 2 * lane] = k0 + prow0;
+      }
+      if (lane + 32 < nb) {
+        rmap[1 + 2 * (lane + 32)] = k0 + lane + 32;
+        rmap[2 + 2 * (lane + 32)] = k0 + prow1;
+      }
+      if (d0) {
+        const int q = nb + __popc(b0 & below);
+        rmap[1 + 2 * q] = k0 + rpos0;
+        rmap[2 + 2 * q] = k0 + lane;
+      }
+      if (d1) {
+        const int q = nb + __popc(b0) + __popc(b1 & below);
+        rmap[1 + 2 * q] = k0 + rpos1;
+        rmap[2 + 2 * q] = k0 + lane + 32;
       }
     }
-    for (int v = lane; v < ns; v += 32) {
-      const int ph = sl_phys[v];
-      if (ph >= r0 && ph < r0 + rows) dest[ph - r0] = sl_log[v];
-    }
+    // output positions of this CTA's rows that move
+    if (lane < nb && prow0 >= r0 && prow0 < r0 + rows) dest[prow0 - r0] = lane;
+    if (lane + 32 < nb && prow1 >= r0 && prow1 < r0 + rows) dest[prow1 - r0] = lane + 32;
+    if (d0 && lane >= r0 && lane < r0 + rows) dest[lane - r0] = rpos0;
+    if (d1 && lane + 32 >= r0 && lane + 32 < r0 + rows) dest[lane + 32 - r0] = rpos1;
   }
   __syncthreads();
 
@@ -395,19 +395,19 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
   // the U entries
   float* ore = Are + (size_t)k0 + (size_t)k0 * lda;
   float* oim = Aim + (size_t)k0 + (size_t)k0 * lda;
-  for (int cc = 0; cc < nb; ++cc) {
+#pragma unroll 4
+  for (int e = tid; e < rows * nb; e += kPcThreads) {
+    const int cc = e / rows, r = e - cc * rows;
     const float ir = s_inv_r[cc], ii = s_inv_i[cc];
-    for (int r = tid; r < rows; r += kPcThreads) {
-      const float ar = sre[(size_t)cc * ldS + r], ai = sim[(size_t)cc * ldS + r];
-      float vr = ar, vi = ai;
-      if (cc < step_of[r]) {
-        vr = ar * ir - ai * ii;
-        vi = ar * ii + ai * ir;
-      }
-      const size_t o = (size_t)dest[r] + (size_t)cc * lda;
-      ore[o] = vr;
-      oim[o] = vi;
+    const float ar = sre[(size_t)cc * ldS + r], ai = sim[(size_t)cc * ldS + r];
+    float vr = ar, vi = ai;
+    if (cc < step_of[r]) {
+      vr = ar * ir - ai * ii;
+      vi = ar * ii + ai * ir;
     }
+    const size_t o = (size_t)dest[r] + (size_t)cc * lda;
+    ore[o] = vr;
+    oim[o] = vi;
   }
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
 }
