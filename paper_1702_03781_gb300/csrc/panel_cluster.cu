@@ -8,22 +8,25 @@
 // (LAPACK's ipiv) are composed once at the end and applied when the block is
 // written back (and, when asked, exported as a row map for the other
 // columns' interchanges). Columns are taken in sub-blocks of 16; warp w of every CTA
-// owns column 16 s + w of sub-block s. Step t:
-//   1. every warp applies the rank-1 term of pivot t-1 to its column of the
-//      sub-block (rows not yet chosen; multiplier a[r][t-1] / pivot), and the
-//      warp owning column t also finds the CTA's candidate (largest |a|^2,
-//      smallest row on ties: two warp reductions) and writes it -- |a|^2,
-//      row, entry -- into every CTA's table through distributed shared
-//      memory;
+// owns column 16 s + w of sub-block s and holds its rows of that column in
+// registers while the sub-block is factored. Step t:
+//   1. every warp applies the rank-1 term of pivot t-1 to its column (rows
+//      not yet chosen; multiplier a[r][t-1] / pivot) in registers and stores
+//      it to shared memory, and the warp owning column t also finds the
+//      CTA's candidate (largest |a|^2, smallest row on ties: two warp
+//      reductions) and writes it -- |a|^2, row, entry, one 16-byte entry --
+//      into every CTA's table through distributed shared memory;
 //   2. cluster barrier;
-//   3. every warp reduces the table (same data, same order: the same pivot in
-//      every CTA), marks the pivot row as chosen and reads the pivot row's
-//      entry in its own column from the owning CTA; chosen rows are never
-//      written again, so that read needs no further barrier.
+//   3. every warp loads column t (the next step's multipliers), reduces the
+//      table (same data, same order: the same pivot in every CTA), marks the
+//      pivot row as chosen and reads the pivot row's entry in its own column
+//      from the owning CTA; chosen rows are never written again, so that
+//      read needs no further barrier.
 // At the end of a sub-block with columns to its right, U12 = L11^-1 A12 is
 // formed from its 16 pivot rows (read from their owners) and every row not
-// yet chosen gets -L21 U12; the owners write U12 into their pivot rows after
-// the next cluster barrier, when no CTA reads the old values any more.
+// yet chosen gets -L21 U12 (a register-tiled rank-16 product); the owners
+// write U12 into their pivot rows after the next cluster barrier, when no
+// CTA reads the old values any more.
 // Multipliers stay unscaled until the write-back (l = a / pivot). The tables
 // are double-buffered by step parity: a CTA writes the tables of step t+2
 // only after every CTA passed barrier t+1, that is after every CTA finished
@@ -57,10 +60,70 @@ __host__ __device__ inline size_t panel_smem_bytes(int nb, int Mb, int C) {
                           + (size_t)2 * nb               // 1 / pivot per step
                           + (size_t)2 * kPcW * kPcW      // L11 of a sub-block
                           + (size_t)2 * kPcW * kPcMaxNb  // U12 of a sub-block
-                          + (size_t)3 * 2 * C)           // tables: |a|^2, re, im
-         + sizeof(int) * ((size_t)2 * C                  // table: row
-                          + (size_t)nb                   // pivot row of each step
+                          + (size_t)4 * 2 * C)           // candidate tables
+         + sizeof(int) * ((size_t)nb                     // pivot row of each step
                           + (size_t)2 * Mb);             // step a row was chosen, its output row
+}
+
+// A22 -= L21 U12 for one sub-block on this CTA's rows not yet chosen. The
+// multipliers stay unscaled in shared memory; each term forms l = a / pivot
+// exactly as the write-back stores it, so that the update uses the L that
+// is kept. Warp w takes columns c1 + w + 16 m (m < NM), lane l rows l + 32 k
+// in chunks of kCh; the accumulators live in registers across the 16 terms,
+// each term reading one multiplier per row and NM entries of U12 (the same
+// for the whole warp).
+template <int RPL, int NM>
+__device__ __forceinline__ void panel_rank16(float* sre, float* sim, int ldS,
+                                             const float* s_inv_r, const float* s_inv_i,
+                                             const float* u12_r, const float* u12_i, int s0,
+                                             int c1, int lane, int warp, unsigned inrows,
+                                             unsigned live) {
+  constexpr int kCh = RPL <= 6 ? RPL : (RPL % 6 == 0 ? 6 : 4);
+  static_assert(RPL % kCh == 0, "row chunks");
+#pragma unroll
+  for (int k0 = 0; k0 < RPL; k0 += kCh) {
+    float cr[kCh][NM], ci[kCh][NM];
+#pragma unroll
+    for (int kk = 0; kk < kCh; ++kk)
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const bool in = (inrows >> (k0 + kk)) & 1u;
+        const size_t o = (size_t)(c1 + warp + kPcW * m) * ldS + lane + 32 * (k0 + kk);
+        cr[kk][m] = in ? sre[o] : 0.f;
+        ci[kk][m] = in ? sim[o] : 0.f;
+      }
+#pragma unroll 4
+    for (int s = 0; s < kPcW; ++s) {
+      const float ir = s_inv_r[s0 + s], ii = s_inv_i[s0 + s];
+      float ur[NM], ui[NM];
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        ur[m] = u12_r[s * kPcMaxNb + c1 + warp + kPcW * m];
+        ui[m] = u12_i[s * kPcMaxNb + c1 + warp + kPcW * m];
+      }
+#pragma unroll
+      for (int kk = 0; kk < kCh; ++kk) {
+        const bool in = (inrows >> (k0 + kk)) & 1u;
+        const size_t o = (size_t)(s0 + s) * ldS + lane + 32 * (k0 + kk);
+        const float a_r = in ? sre[o] : 0.f, a_i = in ? sim[o] : 0.f;
+        const float lr = a_r * ir - a_i * ii, li = a_r * ii + a_i * ir;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          cr[kk][m] = fmaf(-lr, ur[m], fmaf(li, ui[m], cr[kk][m]));
+          ci[kk][m] = fmaf(-lr, ui[m], fmaf(-li, ur[m], ci[kk][m]));
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < kCh; ++kk)
+      if ((live >> (k0 + kk)) & 1u)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const size_t o = (size_t)(c1 + warp + kPcW * m) * ldS + lane + 32 * (k0 + kk);
+          sre[o] = cr[kk][m];
+          sim[o] = ci[kk][m];
+        }
+  }
 }
 
 // RPL: rows per lane (ceil(Mb / 32)), so that a lane's rows of a column are
@@ -76,7 +139,9 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
   extern __shared__ __align__(16) float pc_smem[];
   // Column stride Mb + 1: a row's entries fall in distinct banks.
   const int ldS = Mb + 1;
-  float* sre = pc_smem;                              // [nb][ldS]
+  // candidate tables by step parity: |a|^2 bits, row, re, im
+  float4* tab = reinterpret_cast<float4*>(pc_smem);  // [2][C]
+  float* sre = pc_smem + 8 * C;                      // [nb][ldS]
   float* sim = sre + (size_t)nb * ldS;
   float* s_inv_r = sim + (size_t)nb * ldS;           // [nb]
   float* s_inv_i = s_inv_r + nb;
@@ -84,11 +149,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
   float* l11_i = l11_r + kPcW * kPcW;
   float* u12_r = l11_i + kPcW * kPcW;                // [kPcW][kPcMaxNb]
   float* u12_i = u12_r + kPcW * kPcMaxNb;
-  float* t_mag = u12_i + kPcW * kPcMaxNb;            // [2][C]
-  float* t_re = t_mag + 2 * C;
-  float* t_im = t_re + 2 * C;
-  int* t_row = reinterpret_cast<int*>(t_im + 2 * C);  // [2][C]
-  int* piv_row = t_row + 2 * C;                       // [nb] panel row chosen at each step
+  int* piv_row = reinterpret_cast<int*>(u12_i + kPcW * kPcMaxNb);  // [nb] row chosen at each step
   int* step_of = piv_row + nb;                        // [Mb] step a local row was chosen (nb: not)
   int* dest = step_of + Mb;                           // [Mb] output panel row of a local row
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -115,51 +176,62 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
   }
   __syncthreads();
 
-  unsigned chosen = 0;             // bit k: local row lane + 32 k is chosen
+  unsigned chosen = 0;  // bit k: local row lane + 32 k is chosen
+  unsigned inrows = 0;  // bit k: local row lane + 32 k exists
+#pragma unroll
+  for (int k = 0; k < RPL; ++k)
+    if (lane + 32 * k < rows) inrows |= 1u << k;
+  float xr[RPL], xi[RPL];          // this warp's column of the current sub-block
+  float ar[RPL], ai[RPL];          // the last pivot column (unscaled multipliers)
   float u_r = 0.f, u_i = 0.f;      // pivot row's entry in this warp's column
   float inv_r = 0.f, inv_i = 0.f;  // 1 / pivot of the last step
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) xr[k] = xi[k] = ar[k] = ai[k] = 0.f;
   for (int t = 0; t < nb; ++t) {
     const int par = t & 1;
     const int sb = t / kPcW;
     const int c = sb * kPcW + warp;  // this warp's column
     const bool first = (t == sb * kPcW);
-    // 1. rank-1 term of pivot t-1; the owner of column t finds the candidate
-    if (c >= t) {
-      const bool own = (c == t);
-      float xr[RPL], xi[RPL], ar[RPL], ai[RPL];
-#pragma unroll
-      for (int k = 0; k < RPL; ++k) {  // all loads first
-        const int r = lane + 32 * k;
-        const bool in = r < rows;
-        xr[k] = in ? sre[(size_t)c * ldS + r] : 0.f;
-        xi[k] = in ? sim[(size_t)c * ldS + r] : 0.f;
-        ar[k] = (in && !first) ? sre[(size_t)(t - 1) * ldS + r] : 0.f;
-        ai[k] = (in && !first) ? sim[(size_t)(t - 1) * ldS + r] : 0.f;
-      }
-      float best = -1.f, bre = 0.f, bim = 0.f;
-      int bi = INT_MAX;
+    if (first) {  // the sub-block's columns into registers
 #pragma unroll
       for (int k = 0; k < RPL; ++k) {
-        const int r = lane + 32 * k;
-        if (r >= rows || (chosen & (1u << k))) continue;
-        if (!first) {
+        const bool in = (inrows >> k) & 1u;
+        xr[k] = in ? sre[(size_t)c * ldS + lane + 32 * k] : 0.f;
+        xi[k] = in ? sim[(size_t)c * ldS + lane + 32 * k] : 0.f;
+      }
+    }
+    // 1. rank-1 term of pivot t-1 on the rows not yet chosen (registers,
+    // then shared memory for the other warps and CTAs); the owner of column
+    // t finds the candidate
+    if (c >= t) {
+      const unsigned live = inrows & ~chosen;
+      if (!first) {
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
           const float lr = ar[k] * inv_r - ai[k] * inv_i, li = ar[k] * inv_i + ai[k] * inv_r;
-          xr[k] = fmaf(-lr, u_r, fmaf(li, u_i, xr[k]));
-          xi[k] = fmaf(-lr, u_i, fmaf(-li, u_r, xi[k]));
-          sre[(size_t)c * ldS + r] = xr[k];
-          sim[(size_t)c * ldS + r] = xi[k];
+          const float yr = fmaf(-lr, u_r, fmaf(li, u_i, xr[k]));
+          const float yi = fmaf(-lr, u_i, fmaf(-li, u_r, xi[k]));
+          if ((live >> k) & 1u) {
+            xr[k] = yr;
+            xi[k] = yi;
+            sre[(size_t)c * ldS + lane + 32 * k] = yr;
+            sim[(size_t)c * ldS + lane + 32 * k] = yi;
+          }
         }
-        if (own) {
+      }
+      if (c == t) {
+        float best = -1.f, bre = 0.f, bim = 0.f;
+        int bi = INT_MAX;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
           const float v = xr[k] * xr[k] + xi[k] * xi[k];
-          if (v > best) {
+          if (((live >> k) & 1u) && v > best) {
             best = v;
-            bi = r0 + r;
+            bi = r0 + lane + 32 * k;
             bre = xr[k];
             bim = xi[k];
           }
         }
-      }
-      if (own) {
         // warp argmax in two reductions: the largest |a|^2 (bit patterns of
         // non-negative floats order like their values), then the smallest
         // row among the lanes holding it; a lane without rows offers 0 and
@@ -171,30 +243,39 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
         const int src = __ffs(__ballot_sync(0xffffffffu, key == kmax && row == rmin)) - 1;
         bre = __shfl_sync(0xffffffffu, bre, src);
         bim = __shfl_sync(0xffffffffu, bim, src);
-        if (lane < C) {
-          cluster.map_shared_rank(t_mag, lane)[par * C + crank] = __uint_as_float(kmax);
-          cluster.map_shared_rank(t_row, lane)[par * C + crank] = (int)rmin;
-          cluster.map_shared_rank(t_re, lane)[par * C + crank] = bre;
-          cluster.map_shared_rank(t_im, lane)[par * C + crank] = bim;
-        }
+        if (lane < C)  // one 16-byte entry into every CTA's table
+          cluster.map_shared_rank(tab, lane)[par * C + crank] =
+              make_float4(__uint_as_float(kmax), __int_as_float((int)rmin), bre, bim);
       }
     }
     cluster.sync();
 
-    // 3. the pivot (same in every CTA): the same two reductions over the
-    // C table entries (lane q reads entry q; rows are distinct, so the
-    // winner is unique unless no CTA had rows)
-    const unsigned tkey = (lane < C) ? __float_as_uint(t_mag[par * C + lane]) : 0u;
-    const unsigned trow = (lane < C) ? (unsigned)t_row[par * C + lane] : 0xffffffffu;
+    // 3. the next step's multipliers (column t, complete since the barrier),
+    // then the pivot (same in every CTA): the same two reductions over the C
+    // table entries (lane q reads entry q; rows are distinct, so the winner
+    // is unique unless no CTA had rows)
+    if (c > t) {
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const bool in = (inrows >> k) & 1u;
+        ar[k] = in ? sre[(size_t)t * ldS + lane + 32 * k] : 0.f;
+        ai[k] = in ? sim[(size_t)t * ldS + lane + 32 * k] : 0.f;
+      }
+    }
+    const float4 te = (lane < C) ? tab[par * C + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const unsigned tkey = (lane < C) ? __float_as_uint(te.x) : 0u;
+    const unsigned trow = (lane < C) ? (unsigned)__float_as_int(te.y) : 0xffffffffu;
     const unsigned tk = __reduce_max_sync(0xffffffffu, tkey);
     const unsigned tr = __reduce_min_sync(0xffffffffu, tkey == tk ? trow : 0xffffffffu);
     const int pw = __ffs(__ballot_sync(0xffffffffu, tkey == tk && trow == tr)) - 1;
+    const float pvr = __shfl_sync(0xffffffffu, te.z, pw);
+    const float pvi = __shfl_sync(0xffffffffu, te.w, pw);
     const float pm = __uint_as_float(tk);
     const int pr = (int)tr;
     const bool none = (tr >= (unsigned)M);  // no row left anywhere (M >= nb rules it out)
     const bool zero = !(pm > 0.f);
-    // the pivot row's entry in this warp's column, read early (chosen rows
-    // are not written again)
+    // the pivot row's entry in this warp's column (chosen rows are not
+    // written again)
     u_r = u_i = 0.f;
     if (!none && c > t) {
       const size_t o = (size_t)c * ldS + (pr - pw * Mb);
@@ -204,7 +285,6 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
     if (zero || none) {
       inv_r = inv_i = 0.f;
     } else {
-      const float pvr = t_re[par * C + pw], pvi = t_im[par * C + pw];
       const float rd = __frcp_rn(pvr * pvr + pvi * pvi);
       inv_r = pvr * rd;
       inv_i = -pvi * rd;
@@ -298,29 +378,18 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
         }
       }
       __syncthreads();
-#pragma unroll 1
-      for (int k = 0; k < RPL; ++k) {
-        const int r = lane + 32 * k;
-        if (r >= rows || (chosen & (1u << k))) continue;
-        float lr[kPcW], li[kPcW];
-#pragma unroll
-        for (int s = 0; s < kPcW; ++s) {
-          const float ar = sre[(size_t)(s0 + s) * ldS + r], ai = sim[(size_t)(s0 + s) * ldS + r];
-          const float ir = s_inv_r[s0 + s], ii = s_inv_i[s0 + s];
-          lr[s] = ar * ir - ai * ii;
-          li[s] = ar * ii + ai * ir;
-        }
-        for (int cc = c1 + warp; cc < nb; cc += kPcW) {
-          float xr = sre[(size_t)cc * ldS + r], xi = sim[(size_t)cc * ldS + r];
-#pragma unroll
-          for (int s = 0; s < kPcW; ++s) {
-            const float ur = u12_r[s * kPcMaxNb + cc], ui = u12_i[s * kPcMaxNb + cc];
-            xr = fmaf(-lr[s], ur, fmaf(li[s], ui, xr));
-            xi = fmaf(-lr[s], ui, fmaf(-li[s], ur, xi));
-          }
-          sre[(size_t)cc * ldS + r] = xr;
-          sim[(size_t)cc * ldS + r] = xi;
-        }
+      {
+        const unsigned live = inrows & ~chosen;
+        const int nm = (nb - c1) / kPcW;  // columns per warp: 1, 2 or 3
+        if (nm == 3)
+          panel_rank16<RPL, 3>(sre, sim, ldS, s_inv_r, s_inv_i, u12_r, u12_i, s0, c1, lane, warp,
+                               inrows, live);
+        else if (nm == 2)
+          panel_rank16<RPL, 2>(sre, sim, ldS, s_inv_r, s_inv_i, u12_r, u12_i, s0, c1, lane, warp,
+                               inrows, live);
+        else
+          panel_rank16<RPL, 1>(sre, sim, ldS, s_inv_r, s_inv_i, u12_r, u12_i, s0, c1, lane, warp,
+                               inrows, live);
       }
       __syncthreads();
     }
