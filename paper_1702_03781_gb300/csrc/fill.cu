@@ -163,20 +163,28 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_kernel(FillArgs a) {
 }
 
 // FP64-accurate fill on the FP32 pipe (mixed modes). Same work split as
-// fill_kernel; coefficients and basis carried as hi/lo float pairs
-// (float4 = re_hi, im_hi, re_lo, im_lo), each entry summed in the
-// three-float accumulator of ff.cuh. Writes the FP64 matrix (Z, c128) and
-// its rounded c64 copy (Z32).
+// fill_kernel, with the sum of Eq. 4 factored by the order of the basis:
+//   Z^{mn}_TS = sum_p E_p W_p,  E_p = e^{-jkr} e^{jp alpha},
+//   W_p = sum_q c_pq(T, S) d^q   (d = 1/r real),
+// so that the inner sums are complex x real. Coefficients and basis are
+// carried as hi/lo float pairs (coefficients as float4 = re_hi, im_hi,
+// re_lo, im_lo; E_p likewise; d^q as float2 = hi, lo). Each W_p, Q + 1
+// terms of decreasing size, is summed in a double-float accumulator, then
+// renormalised to a hi/lo pair; the 2P + 1 products E_p W_p go into the
+// three-float accumulator of ff.cuh. Writes the FP64 matrix (Z, c128) and,
+// when asked, its rounded c64 copy (Z32).
 template <int TN>
 __global__ void __launch_bounds__(kFillThreads, 1) fill_ff_kernel(FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = a.K, Nm = a.Nm, nq = a.nq, P = a.P, Q = a.Q;
+  const int K = a.K, Nm = a.Nm, nq = a.nq, P = a.P;
+  const int np = 2 * P + 1;
   const int s0 = blockIdx.y * a.s_chunk;
   const int sc = min(a.s_chunk, Nm - s0);
   const int W = sc * Nm;
   const int Wp = a.Wp;
   float4* Cs = reinterpret_cast<float4*>(smem_raw);  // [K][Wp]
-  float4* Phi = Cs + (size_t)K * Wp;                 // [K][32]
+  float4* Es = Cs + (size_t)K * Wp;                  // [np][32]
+  float2* Ds = reinterpret_cast<float2*>(Es + (size_t)np * kPairsPerTile);  // [nq][32]
 
   for (int idx = threadIdx.x; idx < K * Wp; idx += blockDim.x) {
     const int kk = idx / Wp, e = idx - kk * Wp;
@@ -210,9 +218,10 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_ff_kernel(FillArgs a) {
         }
       }
       if (!valid) {
-        for (int kk = 0; kk < K; ++kk) Phi[kk * kPairsPerTile + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int pi = 0; pi < np; ++pi) Es[pi * kPairsPerTile + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < nq; ++q) Ds[q * kPairsPerTile + t] = make_float2(0.f, 0.f);
       } else {
-        // basis in FP64 (Eq. 3, 4), then split into hi/lo pairs
+        // basis factors in FP64 (Eq. 3, 4), then split into hi/lo pairs
         const double d = 1.0 / r;
         double sn, cs;
         sincos(a.k * r, &sn, &cs);
@@ -221,20 +230,23 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_ff_kernel(FillArgs a) {
         double2 zp = make_double2(1.0, 0.0);
         for (int p = 0; p <= P; ++p) {
           const double2 bp = cmul(ph, zp), bn = cmul(ph, cconj(zp));
-          double dq = 1.0;
-          for (int q = 0; q <= Q; ++q) {
-            float4 v;
-            ff_split(bp.x * dq, v.x, v.z);
-            ff_split(bp.y * dq, v.y, v.w);
-            Phi[((P + p) * nq + q) * kPairsPerTile + t] = v;
-            if (p > 0) {
-              ff_split(bn.x * dq, v.x, v.z);
-              ff_split(bn.y * dq, v.y, v.w);
-              Phi[((P - p) * nq + q) * kPairsPerTile + t] = v;
-            }
-            dq *= d;
+          float4 v;
+          ff_split(bp.x, v.x, v.z);
+          ff_split(bp.y, v.y, v.w);
+          Es[(P + p) * kPairsPerTile + t] = v;
+          if (p > 0) {
+            ff_split(bn.x, v.x, v.z);
+            ff_split(bn.y, v.y, v.w);
+            Es[(P - p) * kPairsPerTile + t] = v;
           }
           zp = cmul(zp, z);
+        }
+        double dq = 1.0;
+        for (int q = 0; q < nq; ++q) {
+          float2 v;
+          ff_split(dq, v.x, v.y);
+          Ds[q * kPairsPerTile + t] = v;
+          dq *= d;
         }
       }
     }
@@ -246,22 +258,36 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_ff_kernel(FillArgs a) {
 #pragma unroll
       for (int j = 0; j < TN; ++j)
         Sr[i][j] = s1r[i][j] = s2r[i][j] = Si[i][j] = s1i[i][j] = s2i[i][j] = 0.f;
-    const float4* phrow = Phi + ty * 4;
-    for (int kk = 0; kk < K; ++kk) {
-      float4 f[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) f[i] = phrow[kk * kPairsPerTile + i];
-      const float4* crow = Cs + (size_t)kk * Wp + tx;
+    for (int pi = 0; pi < np; ++pi) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const float4 c = crow[32 * j];
+        // W_p for this thread's 4 pairs and column j: sum over q of c * d^q
+        float wr[4], er[4], wi[4], ei[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wr[i] = er[i] = wi[i] = ei[i] = 0.f;
+        const float4* crow = Cs + (size_t)pi * nq * Wp + tx + 32 * j;
+        for (int q = 0; q < nq; ++q) {
+          const float4 c = crow[(size_t)q * Wp];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 dq = Ds[q * kPairsPerTile + ty * 4 + i];
+            ff2_mac(wr[i], er[i], c.x, c.z, dq.x, dq.y);
+            ff2_mac(wi[i], ei[i], c.y, c.w, dq.x, dq.y);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          // re += fr*cr - fi*ci ; im += fr*ci + fi*cr
-          fff_mac(Sr[i][j], s1r[i][j], s2r[i][j], f[i].x, f[i].z, c.x, c.z);
-          fff_mac(Sr[i][j], s1r[i][j], s2r[i][j], -f[i].y, -f[i].w, c.y, c.w);
-          fff_mac(Si[i][j], s1i[i][j], s2i[i][j], f[i].x, f[i].z, c.y, c.w);
-          fff_mac(Si[i][j], s1i[i][j], s2i[i][j], f[i].y, f[i].w, c.x, c.z);
+          // renormalise (|e| is far below |w|): hi + lo = w + e
+          const float whr = __fadd_rn(wr[i], er[i]);
+          const float wlr = __fsub_rn(er[i], __fsub_rn(whr, wr[i]));
+          const float whi = __fadd_rn(wi[i], ei[i]);
+          const float wli = __fsub_rn(ei[i], __fsub_rn(whi, wi[i]));
+          const float4 f = Es[pi * kPairsPerTile + ty * 4 + i];
+          // re += fr*wr - fi*wi ; im += fr*wi + fi*wr
+          fff_mac(Sr[i][j], s1r[i][j], s2r[i][j], f.x, f.z, whr, wlr);
+          fff_mac(Sr[i][j], s1r[i][j], s2r[i][j], -f.y, -f.w, whi, wli);
+          fff_mac(Si[i][j], s1i[i][j], s2i[i][j], f.x, f.z, whi, wli);
+          fff_mac(Si[i][j], s1i[i][j], s2i[i][j], f.y, f.w, whr, wlr);
         }
       }
     }
@@ -389,7 +415,11 @@ static bool plan_fill(const harp_ctx* ctx, int Nm, int K, size_t csz, int* s_chu
     const int W = sc * Nm;
     const int tn = (W + 31) / 32;
     if (tn > max_tn) continue;
-    const size_t bytes = ((size_t)K * 32 * tn + (size_t)K * kPairsPerTile) * csz;
+    // staged coefficients, then the per-item basis (the float-float kernel's
+    // factors E_p and d^q take at most K + 1 of its 16-byte entries per pair)
+    const size_t bytes =
+        ((size_t)K * 32 * tn + (size_t)(K + (csz == sizeof(double2) ? 1 : 0)) * kPairsPerTile) *
+        csz;
     if (bytes <= ctx->smem_optin) {
       *s_chunk = sc;
       *TN = tn;
