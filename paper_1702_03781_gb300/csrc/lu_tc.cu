@@ -130,6 +130,7 @@ struct TcArgs {
   long crs, ccs;
   long cstride;  // element offset of product z's C (grid z)
   int* err;
+  int ksplit;    // grid z splits K (one product, nk k-tiles each) instead of batching
 };
 
 template <bool THREE>
@@ -148,7 +149,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;  // 1024-byte aligned tiles
   const int i0 = blockIdx.y * TC_BM, j0 = blockIdx.x * TC_BN;
-  const int pz = blockIdx.z * NP;  // first plane of product z in the split operands
+  // batched: grid z is the product (its planes in the split operands);
+  // split K: grid z is the K range, all of one product
+  const int pz = a.ksplit ? 0 : blockIdx.z * NP;
+  const int kt0 = a.ksplit ? blockIdx.z * a.nk : 0;
   float* cre = a.cre + blockIdx.z * a.cstride;
   float* cim = a.cim + blockIdx.z * a.cstride;
 
@@ -186,8 +190,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t fb = su32(&bar_full[s]);
         mbar_expect_tx(fb, STAGE);
         for (int q = 0; q < NP; ++q) {
-          tma_load_3d(st + q * TC_A_PLANE, &tmA, fb, kt * TC_BK, i0, pz + q);
-          tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, kt * TC_BK, j0, pz + q);
+          tma_load_3d(st + q * TC_A_PLANE, &tmA, fb, (kt0 + kt) * TC_BK, i0, pz + q);
+          tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, (kt0 + kt) * TC_BK, j0,
+                      pz + q);
         }
         issued = kt + 1;
       }
@@ -435,6 +440,7 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   args.ccs = C.cs;
   args.cstride = sC;
   args.err = g_tc.err;
+  args.ksplit = 0;
   const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
   const size_t smem = (size_t)TC_STAGES * stage + 1024;
   void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
@@ -453,6 +459,52 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   return HARP_OK;
 }
 
+// C = alpha * (sum of the S split-K partials) + beta * C; the partials are
+// column-major M x N planes, re at ws + z M N, im at ws + (S + z) M N.
+__global__ void splitk_reduce_kernel(int M, int N, int S, const float* __restrict__ ws,
+                                     float alpha, float beta, CView<float> C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= M) return;
+  const size_t mn = (size_t)M * N, o = i + (size_t)j * M;
+  float sr = 0.f, si = 0.f;
+  for (int z = 0; z < S; ++z) {
+    sr += ws[o + z * mn];
+    si += ws[o + (S + z) * mn];
+  }
+  const size_t c = (size_t)i * C.rs + (size_t)j * C.cs;
+  float cr = alpha * sr, ci = alpha * si;
+  if (beta != 0.f) {
+    cr = fmaf(beta, C.re[c], cr);
+    ci = fmaf(beta, C.im[c], ci);
+  }
+  C.re[c] = cr;
+  C.im[c] = ci;
+}
+
+// K splits for a product of `tiles` output tiles and nk k-tiles: the count
+// (at most 8, at least 8 k-tiles each) that minimises the waves of one-CTA-
+// per-SM work, ceil(tiles S / SMs) / S.
+static int splitk_count(int tiles, int nk) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  int best = 1;
+  double best_t = 1.0;
+  for (int S = 2; S <= 8 && nk / S >= 8; ++S) {
+    if (nk % S) continue;
+    const double t = (double)((tiles * S + sms - 1) / sms) / S;
+    if (t < best_t - 1e-9) {
+      best_t = t;
+      best = S;
+    }
+  }
+  return best;
+}
+
 // K-major TF32 planes of an operand V (R x K) into out, as the GEMM's own
 // split makes them (NP planes of R x Kp), for an operand used by many products.
 int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats, int mode,
@@ -469,7 +521,9 @@ int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats
 }
 
 // C = beta*C + alpha * A B with A given as planes from tc_split_operand
-// (M x K, same mode): only B is split here.
+// (M x K, same mode): only B is split here. A grid that would leave SMs
+// idle splits K, the partials going to the (here unused) A workspace and a
+// reduction forming C.
 int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
                         float beta, CView<float> C, int mode, cudaStream_t st) {
   if (M < 64 || N < 64 || K < 32 || !g_tc.b || !a_split) return HARP_E_UNSUPPORTED;
@@ -500,6 +554,21 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   args.ccs = C.cs;
   args.cstride = 0;
   args.err = g_tc.err;
+  args.ksplit = 0;
+  const int gx = (N + TC_BN - 1) / TC_BN, gy = (M + TC_BM - 1) / TC_BM;
+  int S = splitk_count(gx * gy, args.nk);
+  if ((size_t)2 * S * M * N > g_tc.a_floats || !g_tc.a) S = 1;
+  if (S > 1) {
+    args.nk /= S;
+    args.ksplit = 1;
+    args.alpha = 1.f;
+    args.beta = 0.f;
+    args.cre = g_tc.a;
+    args.cim = g_tc.a + (size_t)S * M * N;
+    args.crs = 1;
+    args.ccs = M;
+    args.cstride = (long)M * N;
+  }
   const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
   const size_t smem = (size_t)TC_STAGES * stage + 1024;
   void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
@@ -510,10 +579,14 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
                                    (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
     attr_set[three ? 1 : 0] = true;
   }
-  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
+  dim3 grid(gx, gy, S);
   ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K, st);
   kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
   HARP_LAUNCHED();
+  if (S > 1) {
+    splitk_reduce_kernel<<<dim3((M + 255) / 256, N), 256, 0, st>>>(M, N, S, g_tc.a, alpha, beta, C);
+    HARP_LAUNCHED();
+  }
   return HARP_OK;
 }
 
