@@ -818,6 +818,152 @@ static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld,
   return panel<R>(ctx, N, A, re, im, ld, k, want, ipiv, zero_col, mode, st);
 }
 
+// ---------------------------------------------------------------------------
+// The look-ahead update of the next panel's columns (at most 64 of them) by
+// the current panel (width n <= 64): U12 = L11^-1 A12 in place, then
+// A22 -= L21 U12. Both are latency-bound at these sizes, so each is one
+// launch that stages everything it reads at once.
+
+// U12 = L11^-1 A12, L11 unit lower: warp w of CTA b solves column 8 b + w,
+// lane l holding rows l and l + 32; row p is final after step p and reaches
+// the other lanes by shuffle. L11 by columns in shared memory (zeros on and
+// above the diagonal).
+__global__ void __launch_bounds__(256) la_trsm_kernel(int n, int ncols, const float* __restrict__ lre,
+                                                      const float* __restrict__ lim, float* bre,
+                                                      float* bim, long ld) {
+  __shared__ float Lr[64 * 65], Li[64 * 65];  // [p][row], row stride 1, column stride 65
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int p = e >> 6, row = e & 63;
+    const bool in = row < n && p < n && row > p;
+    Lr[p * 65 + row] = in ? lre[row + (size_t)p * ld] : 0.f;
+    Li[p * 65 + row] = in ? lim[row + (size_t)p * ld] : 0.f;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= ncols) return;
+  float* br = bre + (size_t)c * ld;
+  float* bi = bim + (size_t)c * ld;
+  float x0r = (lane < n) ? br[lane] : 0.f, x0i = (lane < n) ? bi[lane] : 0.f;
+  float x1r = (lane + 32 < n) ? br[lane + 32] : 0.f, x1i = (lane + 32 < n) ? bi[lane + 32] : 0.f;
+  for (int p = 0; p + 1 < n; ++p) {
+    const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
+    const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
+    const float l0r = Lr[p * 65 + lane], l0i = Li[p * 65 + lane];
+    const float l1r = Lr[p * 65 + lane + 32], l1i = Li[p * 65 + lane + 32];
+    x0r = fmaf(-l0r, pr, fmaf(l0i, pi, x0r));
+    x0i = fmaf(-l0r, pi, fmaf(-l0i, pr, x0i));
+    x1r = fmaf(-l1r, pr, fmaf(l1i, pi, x1r));
+    x1i = fmaf(-l1r, pi, fmaf(-l1i, pr, x1i));
+  }
+  if (lane < n) {
+    br[lane] = x0r;
+    bi[lane] = x0i;
+  }
+  if (lane + 32 < n) {
+    br[lane + 32] = x1r;
+    bi[lane + 32] = x1i;
+  }
+}
+
+// C -= A B for C M x ncols, A M x n, B n x ncols (n, ncols <= 64), all
+// column-major planes with leading dimension ld: 32 rows of C per CTA, lane
+// l row l, warp w columns 8 w .. 8 w + 7; the CTA's rows of A and all of B
+// are staged in shared memory by one round of loads.
+__global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
+                                                      const float* __restrict__ are,
+                                                      const float* __restrict__ aim,
+                                                      const float* __restrict__ bre,
+                                                      const float* __restrict__ bim, float* cre,
+                                                      float* cim, long ld) {
+  __shared__ __align__(16) float Ar[64 * 32], Ai[64 * 32];  // [k][row]
+  __shared__ __align__(16) float Br[64 * 64], Bi[64 * 64];  // [k][col]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i0 = blockIdx.x * 32;
+  {
+    float vr[8], vi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q, r = e & 31, k = e >> 5;
+      const bool in = (i0 + r < M) && (k < n);
+      vr[q] = in ? are[(i0 + r) + (size_t)k * ld] : 0.f;
+      vi[q] = in ? aim[(i0 + r) + (size_t)k * ld] : 0.f;
+    }
+    float wr[16], wi[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, c = e & 63, k = e >> 6;
+      const bool in = (k < n) && (c < ncols);
+      wr[q] = in ? bre[k + (size_t)c * ld] : 0.f;
+      wi[q] = in ? bim[k + (size_t)c * ld] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q;
+      Ar[e] = vr[q];
+      Ai[e] = vi[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q;
+      Br[e] = wr[q];
+      Bi[e] = wi[q];
+    }
+  }
+  const int row = i0 + lane, c0 = warp * 8;
+  float accr[8], acci[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool in = (row < M) && (c0 + j < ncols);
+    accr[j] = in ? cre[row + (size_t)(c0 + j) * ld] : 0.f;
+    acci[j] = in ? cim[row + (size_t)(c0 + j) * ld] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    const float ar = Ar[k * 32 + lane], ai = Ai[k * 32 + lane];
+    const float4 b0r = *reinterpret_cast<const float4*>(&Br[k * 64 + c0]);
+    const float4 b1r = *reinterpret_cast<const float4*>(&Br[k * 64 + c0 + 4]);
+    const float4 b0i = *reinterpret_cast<const float4*>(&Bi[k * 64 + c0]);
+    const float4 b1i = *reinterpret_cast<const float4*>(&Bi[k * 64 + c0 + 4]);
+    const float bR[8] = {b0r.x, b0r.y, b0r.z, b0r.w, b1r.x, b1r.y, b1r.z, b1r.w};
+    const float bI[8] = {b0i.x, b0i.y, b0i.z, b0i.w, b1i.x, b1i.y, b1i.z, b1i.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      accr[j] = fmaf(-ar, bR[j], fmaf(ai, bI[j], accr[j]));
+      acci[j] = fmaf(-ar, bI[j], fmaf(-ai, bR[j], acci[j]));
+    }
+  }
+  if (row < M) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (c0 + j < ncols) {
+        cre[row + (size_t)(c0 + j) * ld] = accr[j];
+        cim[row + (size_t)(c0 + j) * ld] = acci[j];
+      }
+  }
+}
+
+// The look-ahead update of columns [k1, k1 + nb1) by the panel at k (width
+// nb): U12 = L11^-1 A12, A22 -= L21 U12 (planes, leading dimension ld).
+static int lookahead_update(float* re, float* im, long ld, int N, int k, int nb, int k1, int nb1,
+                            cudaStream_t st) {
+  const size_t d = (size_t)k + (size_t)k * ld, u = (size_t)k + (size_t)k1 * ld;
+  {
+    ProfScope ps(HARP_K_TRSM, 4.0 * nb * (double)nb * nb1, st);
+    la_trsm_kernel<<<(nb1 + 7) / 8, 256, 0, st>>>(nb, nb1, re + d, im + d, re + u, im + u, ld);
+    HARP_LAUNCHED();
+  }
+  const int M = N - k1;
+  if (M <= 0) return HARP_OK;
+  const size_t l = (size_t)k1 + (size_t)k * ld, c = (size_t)k1 + (size_t)k1 * ld;
+  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)nb1 * nb, st);
+  la_gemm_kernel<<<(M + 31) / 32, 256, 0, st>>>(M, nb, nb1, re + l, im + l, re + u, im + u, re + c,
+                                               im + c, ld);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
 // FP32 LU with a look-ahead of one panel. Main stream: the update of the
 // next panel's columns by the current panel (row swaps, U12, CUDA-core
 // GEMM), then the next panel's factorisation -- the critical path. Side
@@ -860,9 +1006,13 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
         HARP_TRY(laswp_map<float>(re, im, ld, pmap(i), k1, k1 + nb1, 0, 0, nullptr, st));
       else
         HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, k1, k1 + nb1, 0, 0, nullptr, st));
-      HARP_TRY(trsm<float>(true, true, nb, nb1, A.sub(k, k), A.sub(k, k1), GEMM_SIMT, st));
-      HARP_TRY(cgemm<float>(N - k1, nb1, nb, -1.f, A.sub(k1, k), A.sub(k, k1), 1.f,
-                            A.sub(k1, k1), GEMM_SIMT, st));
+      if (nb <= 64 && nb1 <= 64) {
+        HARP_TRY(lookahead_update(re, im, ld, N, k, nb, k1, nb1, st));
+      } else {
+        HARP_TRY(trsm<float>(true, true, nb, nb1, A.sub(k, k), A.sub(k, k1), GEMM_SIMT, st));
+        HARP_TRY(cgemm<float>(N - k1, nb1, nb, -1.f, A.sub(k1, k), A.sub(k, k1), 1.f,
+                              A.sub(k1, k1), GEMM_SIMT, st));
+      }
       int used = 0;
       HARP_TRY(factor_panel<float>(ctx, N, A, re, im, ld, k1, nb1, ipiv, zero_col, mode, st,
                                    &used, pmap(i + 1), &mp));

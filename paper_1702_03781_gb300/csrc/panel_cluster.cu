@@ -92,7 +92,7 @@ __device__ __forceinline__ void panel_rank16(float* sre, float* sim, int ldS,
         cr[kk][m] = in ? sre[o] : 0.f;
         ci[kk][m] = in ? sim[o] : 0.f;
       }
-#pragma unroll 4
+#pragma unroll 1
     for (int s = 0; s < kPcW; ++s) {
       const float ir = s_inv_r[s0 + s], ii = s_inv_i[s0 + s];
       float ur[NM], ui[NM];
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
   float* sim = sre + (size_t)nb * ldS;
   float* s_inv_r = sim + (size_t)nb * ldS;           // [nb]
   float* s_inv_i = s_inv_r + nb;
-  float* l11_r = s_inv_i + nb;                       // [kPcW][kPcW]
+  float* l11_r = s_inv_i + nb;                       // [kPcW][kPcW], by columns
   float* l11_i = l11_r + kPcW * kPcW;
   float* u12_r = l11_i + kPcW * kPcW;                // [kPcW][kPcMaxNb]
   float* u12_i = u12_r + kPcW * kPcMaxNb;
@@ -318,39 +318,49 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
     if (t == (sb + 1) * kPcW - 1 && t + 1 < nb) {
       __syncthreads();  // this sub-block's pivot rows and inverses are in shared memory
       const int s0 = sb * kPcW, c1 = s0 + kPcW, nr = nb - c1;
-      for (int e = tid; e < kPcW * (kPcW + nr); e += kPcThreads) {
-        const int s = e / (kPcW + nr), j = e % (kPcW + nr);
-        const int cc = (j < kPcW) ? s0 + j : c1 + (j - kPcW);
-        if (j < kPcW && j >= s) continue;  // L11: strictly lower part only
-        const int row = piv_row[s0 + s];
-        float vr = 0.f, vi = 0.f;
-        if (row >= 0) {
-          const int own = row / Mb;
-          const size_t o = (size_t)cc * ldS + (row - own * Mb);
-          vr = cluster.map_shared_rank(sre, own)[o];
-          vi = cluster.map_shared_rank(sim, own)[o];
+      // the 16 x (16 + nr) <= 2 x 512 entries: both remote reads of a thread
+      // issued before either is used
+      {
+        const int ne = kPcW * (kPcW + nr);
+        float vr[2], vi[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = tid + h * kPcThreads;
+          const int s = e / (kPcW + nr), j = e % (kPcW + nr);
+          const int cc = (j < kPcW) ? s0 + j : c1 + (j - kPcW);
+          const int row = (e < ne) ? piv_row[s0 + s] : -1;
+          vr[h] = vi[h] = 0.f;
+          if (row >= 0 && !(j < kPcW && j >= s)) {  // L11: strictly lower part only
+            const int own = row / Mb;
+            const size_t o = (size_t)cc * ldS + (row - own * Mb);
+            vr[h] = cluster.map_shared_rank(sre, own)[o];
+            vi[h] = cluster.map_shared_rank(sim, own)[o];
+          }
         }
-        if (j < kPcW) {
-          const float ir = s_inv_r[cc], ii = s_inv_i[cc];
-          l11_r[s * kPcW + j] = vr * ir - vi * ii;
-          l11_i[s * kPcW + j] = vr * ii + vi * ir;
-        } else {
-          u12_r[s * kPcMaxNb + cc] = vr;
-          u12_i[s * kPcMaxNb + cc] = vi;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = tid + h * kPcThreads;
+          if (e >= ne) continue;
+          const int s = e / (kPcW + nr), j = e % (kPcW + nr);
+          const int cc = (j < kPcW) ? s0 + j : c1 + (j - kPcW);
+          if (j < kPcW) {  // L11 by columns: entry (s, j) at j * 16 + s
+            const float ir = s_inv_r[cc], ii = s_inv_i[cc];
+            l11_r[j * kPcW + s] = vr[h] * ir - vi[h] * ii;
+            l11_i[j * kPcW + s] = vr[h] * ii + vi[h] * ir;
+          } else {
+            u12_r[s * kPcMaxNb + cc] = vr[h];
+            u12_i[s * kPcMaxNb + cc] = vi[h];
+          }
         }
       }
       __syncthreads();
       // U12 = L11^-1 A12 by forward substitution: warp w takes columns
       // c1 + w + 16 m together, lane s holds row s; row q is final after
-      // step q and reaches the other lanes by shuffle
+      // step q and reaches the other lanes by shuffle. This code and the
+      // sub-block update run once per 16 columns; their loops stay rolled,
+      // which keeps the kernel's code small.
       {
         constexpr int kCpw = (kPcMaxNb - kPcW + kPcW - 1) / kPcW;  // columns per warp
-        float lr_row[kPcW], li_row[kPcW];
-#pragma unroll
-        for (int q = 0; q < kPcW; ++q) {
-          lr_row[q] = (lane < kPcW && q < lane) ? l11_r[lane * kPcW + q] : 0.f;
-          li_row[q] = (lane < kPcW && q < lane) ? l11_i[lane * kPcW + q] : 0.f;
-        }
         float ur[kCpw], ui[kCpw];
 #pragma unroll
         for (int m = 0; m < kCpw; ++m) {
@@ -358,14 +368,16 @@ __global__ void __launch_bounds__(kPcThreads, 1) panel_cluster_kernel(float* Are
           ur[m] = (lane < kPcW && cc < nb) ? u12_r[lane * kPcMaxNb + cc] : 0.f;
           ui[m] = (lane < kPcW && cc < nb) ? u12_i[lane * kPcMaxNb + cc] : 0.f;
         }
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < kPcW - 1; ++q) {
+          const float lr = (lane < kPcW && q < lane) ? l11_r[q * kPcW + lane] : 0.f;
+          const float li = (lane < kPcW && q < lane) ? l11_i[q * kPcW + lane] : 0.f;
 #pragma unroll
           for (int m = 0; m < kCpw; ++m) {
             const float vr = __shfl_sync(0xffffffffu, ur[m], q);
             const float vi = __shfl_sync(0xffffffffu, ui[m], q);
-            ur[m] = fmaf(-lr_row[q], vr, fmaf(li_row[q], vi, ur[m]));
-            ui[m] = fmaf(-lr_row[q], vi, fmaf(-li_row[q], vr, ui[m]));
+            ur[m] = fmaf(-lr, vr, fmaf(li, vi, ur[m]));
+            ui[m] = fmaf(-lr, vi, fmaf(-li, vr, ui[m]));
           }
         }
 #pragma unroll
