@@ -833,19 +833,32 @@ __global__ void __launch_bounds__(256) la_trsm_kernel(int n, int ncols, const fl
                                                       float* bim, long ld) {
   __shared__ float Lr[64 * 65], Li[64 * 65];  // [p][row], row stride 1, column stride 65
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int p = e >> 6, row = e & 63;
-    const bool in = row < n && p < n && row > p;
-    Lr[p * 65 + row] = in ? lre[row + (size_t)p * ld] : 0.f;
-    Li[p * 65 + row] = in ? lim[row + (size_t)p * ld] : 0.f;
+  const int c = blockIdx.x * 8 + warp;
+  const bool col = c < ncols;
+  float* br = bre + (size_t)(col ? c : 0) * ld;
+  float* bi = bim + (size_t)(col ? c : 0) * ld;
+  // every load (the triangle and this warp's column) issued before any use
+  float x0r = (col && lane < n) ? br[lane] : 0.f, x0i = (col && lane < n) ? bi[lane] : 0.f;
+  float x1r = (col && lane + 32 < n) ? br[lane + 32] : 0.f;
+  float x1i = (col && lane + 32 < n) ? bi[lane + 32] : 0.f;
+  {
+    float vr[16], vi[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, p = e >> 6, row = e & 63;
+      const bool in = row < n && p < n && row > p;
+      vr[q] = in ? lre[row + (size_t)p * ld] : 0.f;
+      vi[q] = in ? lim[row + (size_t)p * ld] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, p = e >> 6, row = e & 63;
+      Lr[p * 65 + row] = vr[q];
+      Li[p * 65 + row] = vi[q];
+    }
   }
   __syncthreads();
-  const int c = blockIdx.x * 8 + warp;
-  if (c >= ncols) return;
-  float* br = bre + (size_t)c * ld;
-  float* bi = bim + (size_t)c * ld;
-  float x0r = (lane < n) ? br[lane] : 0.f, x0i = (lane < n) ? bi[lane] : 0.f;
-  float x1r = (lane + 32 < n) ? br[lane + 32] : 0.f, x1i = (lane + 32 < n) ? bi[lane + 32] : 0.f;
+  if (!col) return;
   for (int p = 0; p + 1 < n; ++p) {
     const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
     const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
@@ -880,6 +893,14 @@ __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
   __shared__ __align__(16) float Br[64 * 64], Bi[64 * 64];  // [k][col]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * 32;
+  const int row = i0 + lane, c0 = warp * 8;
+  float accr[8], acci[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool in = (row < M) && (c0 + j < ncols);
+    accr[j] = in ? cre[row + (size_t)(c0 + j) * ld] : 0.f;
+    acci[j] = in ? cim[row + (size_t)(c0 + j) * ld] : 0.f;
+  }
   {
     float vr[8], vi[8];
 #pragma unroll
@@ -909,14 +930,6 @@ __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
       Br[e] = wr[q];
       Bi[e] = wi[q];
     }
-  }
-  const int row = i0 + lane, c0 = warp * 8;
-  float accr[8], acci[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const bool in = (row < M) && (c0 + j < ncols);
-    accr[j] = in ? cre[row + (size_t)(c0 + j) * ld] : 0.f;
-    acci[j] = in ? cim[row + (size_t)(c0 + j) * ld] : 0.f;
   }
   __syncthreads();
 #pragma unroll 4
@@ -1029,7 +1042,15 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
     else
       HARP_TRY(laswp<float>(re, im, ld, N, ipiv, k, k1, 0, k, k2, N, perm, s2));
     if (k2 < N) {
-      HARP_TRY(trsm<float>(true, true, nb, N - k2, A.sub(k, k), A.sub(k, k2), mode, s2));
+      if (nb <= 64) {
+        const size_t d = (size_t)k + (size_t)k * ld, u = (size_t)k + (size_t)k2 * ld;
+        ProfScope ps(HARP_K_TRSM, 4.0 * nb * (double)nb * (N - k2), s2);
+        la_trsm_kernel<<<(N - k2 + 7) / 8, 256, 0, s2>>>(nb, N - k2, re + d, im + d, re + u, im + u,
+                                                         ld);
+        HARP_LAUNCHED();
+      } else {
+        HARP_TRY(trsm<float>(true, true, nb, N - k2, A.sub(k, k), A.sub(k, k2), mode, s2));
+      }
       HARP_TRY(cgemm<float>(N - k1, N - k2, nb, -1.f, A.sub(k1, k), A.sub(k, k2), 1.f,
                             A.sub(k1, k2), mode, s2));
     }
