@@ -31,12 +31,13 @@ WORKLOAD = "SKA-like station: 256 antennas in a 38 m disc (min sep 1.5 m), 12 MB
 
 
 # Arithmetic each kernel class runs on in the mixed step (roofline bound).
-IMPL = {"fill": "ff", "gemm": "tensor_tf32", "residual": "ff", "panel": "fp32", "trsm": "fp32",
-        "swap": "fp32", "adjoint": "fp32", "other": "fp32", "resid_update": "ff2"}
+IMPL = {"fill": "fp32", "gemm": "tensor_tf32", "residual": "ff", "panel": "fp32",
+        "trsm": "fp32", "swap": "fp32", "adjoint": "fp32", "other": "fp32", "resid_update": "ff2",
+        "fill_ff": "ff_fill"}
 # Kernel classes that do the step's arithmetic (the others are glue: row
 # swaps, triangular leaves, conversions); the residual classes run on the
 # bf16 tensor cores when the context uses the exact-slice residual.
-COMPUTE_KINDS = ("fill", "gemm", "residual", "resid_update")
+COMPUTE_KINDS = ("fill", "fill_ff", "gemm", "residual", "resid_update")
 
 
 def _dist():

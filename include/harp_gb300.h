@@ -286,8 +286,8 @@ int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos, d
  * of a selected class is bracketed by a CUDA event pair on its own stream,
  * and the class accumulates the launch's algorithmic flop count
  * (8 real flops per complex multiply-add). */
-#define HARP_PROF_KINDS 9
-#define HARP_K_FILL 0     /* harp_fill kernels                                  */
+#define HARP_PROF_KINDS 10
+#define HARP_K_FILL 0     /* harp_fill kernels (FP64 and FP32 evaluation)        */
 #define HARP_K_GEMM 1     /* LU trailing updates and triangular-solve updates   */
 #define HARP_K_RESIDUAL 2 /* FP64-accurate residual R = V - Z X of the refinement */
 #define HARP_K_PANEL 3    /* in-panel LU leaves (pivot search)                  */
@@ -296,6 +296,7 @@ int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos, d
 #define HARP_K_ADJOINT 6  /* harp_fill_adjoint kernels                          */
 #define HARP_K_OTHER 7    /* conversions, norms, permutations                   */
 #define HARP_K_RESID_UPDATE 8 /* residual updates R - Z D (double-float, small D) */
+#define HARP_K_FILL_FF 9  /* the mixed fill's FP64-accurate Z64 (float-float)    */
 
 /* Start recording the classes whose bit (1 << HARP_K_*) is set in mask.
  * Process-wide; discards earlier records. */

@@ -356,7 +356,7 @@ static int launch_fill_ff(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, 
     default: return HARP_E_UNSUPPORTED;
   }
   HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ProfScope ps(HARP_K_FILL, 8.0 * a.Nm * a.Nm * a.K * (double)a.Na * (a.Na - 1), st);
+  ProfScope ps(HARP_K_FILL_FF, 8.0 * a.Nm * a.Nm * a.K * (double)a.Na * (a.Na - 1), st);
   const int slots = background ? fill_cluster_slots(kern, smem) : 0;
   if (slots >= 2) {
     // about half of the cluster slots (4 of the 7 a GB300 holds), split over

@@ -20,8 +20,9 @@ import hashlib
 import json
 import os
 
-KINDS = ["fill", "gemm", "residual", "panel", "trsm", "swap", "adjoint", "other", "resid_update"]
-N_KINDS = 9
+KINDS = ["fill", "gemm", "residual", "panel", "trsm", "swap", "adjoint", "other", "resid_update",
+         "fill_ff"]
+N_KINDS = 10
 SMS = 152
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = 2 * 128 * SMS * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
@@ -32,6 +33,15 @@ FP64_PEAK_TFLOPS = 2 * 2 * SMS * SM_MAX_MHZ * 1e6 / 1e12     # 1.259
 # clock per SM.
 FF_INSTR_PER_CMAC = 96
 FF_PEAK_TFLOPS = 128 * SMS * SM_MAX_MHZ * 1e6 * 8 / FF_INSTR_PER_CMAC / 1e12   # 3.357
+# The FP64-accurate fill factors Eq. 4 by the order of the basis: per
+# antenna-pair entry and per p, Q + 1 complex x real products into a
+# double-float accumulator (2 x 12 instructions each), a renormalisation (6)
+# and one complex product into the three-float accumulator (4 x 24); that is
+# 24 + 102 / (Q + 1) instructions per complex multiply-add of the flat sum
+# (8 algorithmic flops), 41 at Q = 5.
+FILL_FF_Q = 5
+FILL_FF_INSTR_PER_CMAC = 24 + 102 / (FILL_FF_Q + 1)
+FILL_FF_PEAK_TFLOPS = 128 * SMS * SM_MAX_MHZ * 1e6 * 8 / FILL_FF_INSTR_PER_CMAC / 1e12  # 7.86
 # Double-float (Dot2) residual updates: 4 compensated real products of 12
 # instructions, 48 per complex multiply-add.
 FF2_INSTR_PER_CMAC = 48
@@ -67,7 +77,8 @@ def source_hash(kind: str) -> str:
              "residual": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"],
              "panel": ["panel_cluster.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
              "adjoint": ["adjoint.cu"], "other": ["dense.cu"],
-             "resid_update": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"]}.get(kind, [])
+             "resid_update": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"],
+             "fill_ff": ["fill.cu", "ff.cuh"]}.get(kind, [])
     h = hashlib.sha256()
     for f in files:
         p = os.path.join(_ROOT, "paper_1702_03781_gb300", "csrc", f)
@@ -97,6 +108,11 @@ def peak_for(kind: str, impl: str, peaks: dict):
         return ("alu", FF2_PEAK_TFLOPS, "TFLOP/s",
                 "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 48 instr per complex MAC "
                 "(double-float Dot2)")
+    if impl == "ff_fill":
+        return ("alu", FILL_FF_PEAK_TFLOPS, "TFLOP/s",
+                "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 41 instr per complex MAC of "
+                "the flat sum at Q = 5 (factored float-float fill, FP64-accurate); the background "
+                "launch holds 4 GPC-sized clusters, 64 of the 152 SMs")
     if impl == "ff":
         return ("alu", FF_PEAK_TFLOPS, "TFLOP/s",
                 "FP32 pipe at 128 instr/clk/SM x 152 SMs x 2070 MHz, 96 instr per complex MAC "
