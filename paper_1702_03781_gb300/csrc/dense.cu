@@ -637,10 +637,99 @@ __global__ void identity_blocks_kernel(R* re, R* im, int nblk) {
   }
 }
 
+// FP32 inverses of the 64 x 64 diagonal blocks of the unit-lower L (z = 0)
+// and the upper U (z = 1) of an LU: block b = blockIdx.x, its columns
+// 8 blockIdx.y .. + 7, one warp per column (lane l rows l and l + 32), solving
+// T x = e_c by substitution with shuffles; a last block of n < 64 rows is
+// embedded in the identity. Output by blocks of 64 x 64, column-major.
+__global__ void __launch_bounds__(256) diag_inv_f32_kernel(int N, CView<float> A, float* lre,
+                                                           float* lim, float* ure, float* uim) {
+  __shared__ float Tr[64 * 65], Ti[64 * 65];  // [p][row]: column p of the block
+  const int b = blockIdx.x, upper = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = min(64, N - 64 * b);
+  const CView<float> T = A.sub(64L * b, 64L * b);
+  {
+    float vr[16], vi[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, p = e >> 6, row = e & 63;
+      const bool in = row < n && p < n && (upper ? row <= p : row > p);
+      vr[q] = in ? T.r(row, p) : 0.f;
+      vi[q] = in ? T.m(row, p) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q;
+      Tr[(e >> 6) * 65 + (e & 63)] = vr[q];
+      Ti[(e >> 6) * 65 + (e & 63)] = vi[q];
+    }
+  }
+  __syncthreads();
+  const int c = blockIdx.y * 8 + warp;
+  float x0r = (lane == c) ? 1.f : 0.f, x1r = (lane + 32 == c) ? 1.f : 0.f;
+  float x0i = 0.f, x1i = 0.f;
+  if (c < n) {
+    if (!upper) {
+      for (int p = c; p + 1 < n; ++p) {  // rows above c stay zero
+        const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
+        const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
+        const float l0r = Tr[p * 65 + lane], l0i = Ti[p * 65 + lane];
+        const float l1r = Tr[p * 65 + lane + 32], l1i = Ti[p * 65 + lane + 32];
+        x0r = fmaf(-l0r, pr, fmaf(l0i, pi, x0r));
+        x0i = fmaf(-l0r, pi, fmaf(-l0i, pr, x0i));
+        x1r = fmaf(-l1r, pr, fmaf(l1i, pi, x1r));
+        x1i = fmaf(-l1r, pi, fmaf(-l1i, pr, x1i));
+      }
+    } else {
+      for (int p = c; p >= 0; --p) {  // rows below c stay zero
+        // the owner of row p divides by the diagonal, then everyone subtracts
+        const bool own0 = (lane == p), own1 = (lane + 32 == p);
+        if (own0 || own1) {
+          const float dr = Tr[p * 65 + p], di = Ti[p * 65 + p];
+          const float den = dr * dr + di * di;
+          const float xr = own0 ? x0r : x1r, xi = own0 ? x0i : x1i;
+          const float qr = (xr * dr + xi * di) / den, qi = (xi * dr - xr * di) / den;
+          if (own0) {
+            x0r = qr;
+            x0i = qi;
+          } else {
+            x1r = qr;
+            x1i = qi;
+          }
+        }
+        const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
+        const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
+        const float u0r = (lane < p) ? Tr[p * 65 + lane] : 0.f;
+        const float u0i = (lane < p) ? Ti[p * 65 + lane] : 0.f;
+        const float u1r = (lane + 32 < p) ? Tr[p * 65 + lane + 32] : 0.f;
+        const float u1i = (lane + 32 < p) ? Ti[p * 65 + lane + 32] : 0.f;
+        x0r = fmaf(-u0r, pr, fmaf(u0i, pi, x0r));
+        x0i = fmaf(-u0r, pi, fmaf(-u0i, pr, x0i));
+        x1r = fmaf(-u1r, pr, fmaf(u1i, pi, x1r));
+        x1i = fmaf(-u1r, pi, fmaf(-u1i, pr, x1i));
+      }
+    }
+  }
+  float* ore = (upper ? ure : lre) + (size_t)b * 4096 + (size_t)c * 64;
+  float* oim = (upper ? uim : lim) + (size_t)b * 4096 + (size_t)c * 64;
+  ore[lane] = x0r;
+  oim[lane] = x0i;
+  ore[lane + 32] = x1r;
+  oim[lane + 32] = x1i;
+}
+
 template <typename R>
 int diag_inverses(int N, CView<R> A, R* lre, R* lim, R* ure, R* uim, cudaStream_t st) {
   const int nblk = (N + kTrsmLeaf - 1) / kTrsmLeaf;
   const long bs = (long)kTrsmLeaf * kTrsmLeaf;
+  if constexpr (std::is_same<R, float>::value) {
+    static_assert(kTrsmLeaf == 64, "diagonal blocks of 64");
+    ProfScope ps(HARP_K_TRSM, 8.0 * kTrsmLeaf * (double)kTrsmLeaf * kTrsmLeaf * nblk, st);
+    diag_inv_f32_kernel<<<dim3(nblk, 8, 2), 256, 0, st>>>(N, A, lre, lim, ure, uim);
+    HARP_LAUNCHED();
+    return HARP_OK;
+  }
   {
     ProfScope ps(HARP_K_OTHER, 0.0, st);
     identity_blocks_kernel<R><<<dim3(1, nblk), 256, 0, st>>>(lre, lim, nblk);
