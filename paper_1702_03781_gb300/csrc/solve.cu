@@ -16,13 +16,13 @@
 #include <climits>
 
 #include "dense.cuh"
+#include "prof.cuh"
 #include "ozaki.cuh"
 
 namespace harp {
 
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
-static bool is_mixed(int prec) { return prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32; }
 static int gemm_mode(int prec) {
   if (prec == HARP_MIXED_TF32) return GEMM_TC_TF32;
   if (prec == HARP_MIXED_3XTF32 || prec == HARP_FP32) return GEMM_TC_3XTF32;
@@ -42,13 +42,29 @@ static int load_rhs(harp_ctx* c, int N, int nrhs, const double* V, int ldv, doub
   return port_rhs_planes<double>(N, nrhs, N / nrhs, re, im, c->max_N, st);
 }
 
-static int read_back(harp_ctx* c, int nd, cudaStream_t st) {
-  HARP_CUDA(cudaMemcpyAsync(c->red_host, c->red, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
-  HARP_CUDA(cudaStreamSynchronize(st));
-  return HARP_OK;
-}
-
 bool profiling_active();
+
+// The first FP32 solve with the port right-hand sides V = E (column m has
+// its unit entry in row m s): L^-1 P V is column c_m of L^-1, where
+// perm[c_m] = m s, so that product is a gather (CTA m: find c_m, copy the
+// column).
+__global__ void port_linv_gather_kernel(int N, int s, const int* __restrict__ perm,
+                                        const float* __restrict__ lre,
+                                        const float* __restrict__ lim, long ldi, float* wre,
+                                        float* wim, long ldw) {
+  __shared__ int col;
+  const int m = blockIdx.x;
+  if (threadIdx.x == 0) col = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    if (perm[i] == m * s) col = i;
+  __syncthreads();
+  const int c = col;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    wre[r + (size_t)m * ldw] = (c >= 0) ? lre[r + (size_t)c * ldi] : 0.f;
+    wim[r + (size_t)m * ldw] = (c >= 0) ? lim[r + (size_t)c * ldi] : 0.f;
+  }
+}
 
 // The FP32 triangular solves of one refinement call: the first runs
 // directly; later ones replay a CUDA graph of the same sequence (captured
@@ -58,14 +74,10 @@ bool profiling_active();
 static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool first,
                    cudaStream_t st) {
   const long ldw = ctx->max_N;
-  float* lre = (float*)ctx->lu_re;
-  float* lim = (float*)ctx->lu_im;
   float* wre = (float*)ctx->w_re;
   float* wim = (float*)ctx->w_im;
   float* tre = (float*)ctx->t_re;
   float* tim = (float*)ctx->t_im;
-  const float* dr = (const float*)ctx->dinv_re;
-  const float* di = (const float*)ctx->dinv_im;
   const int g = (trans == 'T') ? 1 : 0;
   const bool keyed = ctx->solve_graph[g] && ctx->solve_key[g][0] == N &&
                      ctx->solve_key[g][1] == nrhs && ctx->solve_key[g][2] == mode;
@@ -78,10 +90,6 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
     return lu_solve_inv<float>(N, nrhs, fi, fi + NN, fi + 2 * NN, fi + 3 * NN, ctx->max_N,
                                ctx->perm, wre, wim, ldw, tre, tim, trans, mode, s, lsp, usp);
   };
-  (void)lre;
-  (void)lim;
-  (void)dr;
-  (void)di;
   if (profiling_active() || (first && !keyed)) return run(st);
   if (!keyed) {
     if (ctx->solve_graph[g]) {
@@ -217,17 +225,33 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     return HARP_OK;
   }
 
-  float* lre = (float*)ctx->lu_re;
-  float* lim = (float*)ctx->lu_im;
   float* wre = (float*)ctx->w_re;
   float* wim = (float*)ctx->w_im;
   float* tre = (float*)ctx->t_re;
   float* tim = (float*)ctx->t_im;
-  const float* dinv_r = (const float*)ctx->dinv_re;
-  const float* dinv_i = (const float*)ctx->dinv_im;
   HARP_TRY(load_rhs(ctx, N, nrhs, V, ldv, ctx->v_re, ctx->v_im, st));
-  HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->v_re, ctx->v_im, ldw, wre, wim, ldw, st));
-  HARP_TRY(solve32(ctx, N, nrhs, tr ? 'T' : 'N', mode, true, st));
+  const size_t NNi = (size_t)ctx->max_N * ctx->max_N;
+  if (!V && !tr && N % nrhs == 0 && ctx->finv_split_mode == mode) {
+    // port right-hand sides: the L^-1 product is a column gather, then U^-1
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      port_linv_gather_kernel<<<nrhs, 256, 0, st>>>(N, N / nrhs, ctx->perm, ctx->finv,
+                                                    ctx->finv + NNi, ctx->max_N, wre, wim, ldw);
+      HARP_LAUNCHED();
+    }
+    int su = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, ctx->finv_split + ctx->finv_split_floats,
+                                 planes<float>(wre, wim, ldw), 0.f, planes<float>(tre, tim, ldw),
+                                 mode, st);
+    if (su == HARP_E_UNSUPPORTED)  // shapes the tensor-core product does not take
+      su = cgemm<float>(N, nrhs, N, 1.f,
+                        planes<float>(ctx->finv + 2 * NNi, ctx->finv + 3 * NNi, ctx->max_N),
+                        planes<float>(wre, wim, ldw), 0.f, planes<float>(tre, tim, ldw), mode, st);
+    HARP_TRY(su);
+    HARP_TRY(planes_to_planes<float, float>(N, nrhs, tre, tim, ldw, wre, wim, ldw, st));
+  } else {
+    HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->v_re, ctx->v_im, ldw, wre, wim, ldw, st));
+    HARP_TRY(solve32(ctx, N, nrhs, tr ? 'T' : 'N', mode, true, st));
+  }
   HARP_TRY(planes_to_planes<float, double>(N, nrhs, wre, wim, ldw, ctx->x_re, ctx->x_im, ldw, st));
 
   // ---- FP32: no refinement
@@ -289,7 +313,9 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   bool converged = false;
   for (;;) {
     HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, st));
-    HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
+    // after a correction, colmax_x already holds X's column maxima (formed
+    // for the size of the correction; X has not changed since)
+    if (it == 0) HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
     HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
                               cudaMemcpyDeviceToHost, st));
     HARP_CUDA(cudaStreamSynchronize(st));
