@@ -185,10 +185,10 @@ struct harp_ctx {
   int finv_split_mode;
 
   // Captured graphs of the FP32 triangular solves of the refinement, keyed
-  // by (N, nrhs, mode) for trans 'N' [0] and 'T' [1]; replayed on the
-  // caller's stream.
+  // by (N, nrhs, mode, finv_incremental) for trans 'N' [0] and 'T' [1];
+  // replayed on the caller's stream.
   cudaGraphExec_t solve_graph[2];
-  int solve_key[2][3];
+  int solve_key[2][4];
 
   // Look-ahead LU: side stream for the trailing updates and event pools
   // (panel factored / trailing update done), n_events each.
@@ -198,6 +198,15 @@ struct harp_ctx {
   // orders it after the caller's earlier work, ev_z64 marks Z64 complete.
   cudaStream_t fill_stream;
   cudaEvent_t ev_fill_fork, ev_z64;
+  // Streams on which the FP32 look-ahead LU builds the factor inverses
+  // panel by panel beside the factorisation ([0] (L^-1)^T, [1] U^-1);
+  // ev_inv marks them complete. finv_incremental: the last FP32
+  // factorisation left U^-1 in the U slot of finv with its tensor-core
+  // split, and (L^-1)^T = (L^T)^-1 in the L slot (its split still to be
+  // made, transposed, by the solve).
+  cudaStream_t inv_stream[2];
+  cudaEvent_t ev_inv[2];
+  int finv_incremental;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;

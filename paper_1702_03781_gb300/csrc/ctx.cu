@@ -46,6 +46,10 @@ static void free_all(harp_ctx* c) {
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
+  for (int q = 0; q < 2; ++q) {
+    if (c->inv_stream[q]) cudaStreamDestroy(c->inv_stream[q]);
+    if (c->ev_inv[q]) cudaEventDestroy(c->ev_inv[q]);
+  }
   if (c->ev_fill_fork) cudaEventDestroy(c->ev_fill_fork);
   if (c->ev_z64) cudaEventDestroy(c->ev_z64);
   for (int e = 0; e < c->n_events; ++e) {
@@ -177,6 +181,11 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   if (ok && (cudaEventCreateWithFlags(&c->ev_fill_fork, cudaEventDisableTiming) != cudaSuccess ||
              cudaEventCreateWithFlags(&c->ev_z64, cudaEventDisableTiming) != cudaSuccess))
     ok = false;
+  for (int q = 0; ok && q < 2; ++q)
+    if (cudaStreamCreateWithFlags(&c->inv_stream[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_inv[q], cudaEventDisableTiming) != cudaSuccess)
+      ok = false;
+  c->finv_incremental = 0;
   if (ok) {
     c->n_events = max_N / 16 + 2;
     if (cudaMalloc((void**)&c->pmap, (size_t)c->n_events * kPmapInts * sizeof(int)) != cudaSuccess)

@@ -637,86 +637,124 @@ __global__ void identity_blocks_kernel(R* re, R* im, int nblk) {
   }
 }
 
+// Triangle blocks of at most 64 rows, inverted by one warp per column with
+// shuffles. The block is held by columns in shared memory (Tr/Ti[p * 65 +
+// row], zeros outside the triangle); column c of the inverse solves
+// T x = e_c by substitution, lane l holding rows l and l + 32.
+__device__ __forceinline__ void tri64_load(int n, const CView<float>& T, bool upper, float* Tr,
+                                           float* Ti, int tid) {
+  float vr[16], vi[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + 256 * q, p = e >> 6, row = e & 63;
+    const bool in = row < n && p < n && (upper ? row <= p : row > p);
+    vr[q] = in ? T.r(row, p) : 0.f;
+    vi[q] = in ? T.m(row, p) : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + 256 * q;
+    Tr[(e >> 6) * 65 + (e & 63)] = vr[q];
+    Ti[(e >> 6) * 65 + (e & 63)] = vi[q];
+  }
+}
+
+// Unit lower (upper = false) or upper triangle; for c >= n the column of the
+// identity (a block of n < 64 rows embedded in the identity).
+__device__ __forceinline__ void tri64_inv_column(int n, const float* Tr, const float* Ti, bool upper,
+                                                 int c, int lane, float& x0r, float& x0i,
+                                                 float& x1r, float& x1i) {
+  x0r = (lane == c) ? 1.f : 0.f;
+  x1r = (lane + 32 == c) ? 1.f : 0.f;
+  x0i = x1i = 0.f;
+  if (c >= n) return;
+  if (!upper) {
+    for (int p = c; p + 1 < n; ++p) {  // rows above c stay zero
+      const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
+      const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
+      const float l0r = Tr[p * 65 + lane], l0i = Ti[p * 65 + lane];
+      const float l1r = Tr[p * 65 + lane + 32], l1i = Ti[p * 65 + lane + 32];
+      x0r = fmaf(-l0r, pr, fmaf(l0i, pi, x0r));
+      x0i = fmaf(-l0r, pi, fmaf(-l0i, pr, x0i));
+      x1r = fmaf(-l1r, pr, fmaf(l1i, pi, x1r));
+      x1i = fmaf(-l1r, pi, fmaf(-l1i, pr, x1i));
+    }
+    return;
+  }
+  for (int p = c; p >= 0; --p) {  // rows below c stay zero
+    // the owner of row p divides by the diagonal, then everyone subtracts
+    const bool own0 = (lane == p), own1 = (lane + 32 == p);
+    if (own0 || own1) {
+      const float dr = Tr[p * 65 + p], di = Ti[p * 65 + p];
+      const float den = dr * dr + di * di;
+      const float xr = own0 ? x0r : x1r, xi = own0 ? x0i : x1i;
+      const float qr = (xr * dr + xi * di) / den, qi = (xi * dr - xr * di) / den;
+      if (own0) {
+        x0r = qr;
+        x0i = qi;
+      } else {
+        x1r = qr;
+        x1i = qi;
+      }
+    }
+    const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
+    const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
+    const float u0r = (lane < p) ? Tr[p * 65 + lane] : 0.f;
+    const float u0i = (lane < p) ? Ti[p * 65 + lane] : 0.f;
+    const float u1r = (lane + 32 < p) ? Tr[p * 65 + lane + 32] : 0.f;
+    const float u1i = (lane + 32 < p) ? Ti[p * 65 + lane + 32] : 0.f;
+    x0r = fmaf(-u0r, pr, fmaf(u0i, pi, x0r));
+    x0i = fmaf(-u0r, pi, fmaf(-u0i, pr, x0i));
+    x1r = fmaf(-u1r, pr, fmaf(u1i, pi, x1r));
+    x1i = fmaf(-u1r, pi, fmaf(-u1i, pr, x1i));
+  }
+}
+
 // FP32 inverses of the 64 x 64 diagonal blocks of the unit-lower L (z = 0)
 // and the upper U (z = 1) of an LU: block b = blockIdx.x, its columns
-// 8 blockIdx.y .. + 7, one warp per column (lane l rows l and l + 32), solving
-// T x = e_c by substitution with shuffles; a last block of n < 64 rows is
-// embedded in the identity. Output by blocks of 64 x 64, column-major.
+// 8 blockIdx.y .. + 7 (a warp each); a last block of n < 64 rows is embedded
+// in the identity. Output by blocks of 64 x 64, column-major.
 __global__ void __launch_bounds__(256) diag_inv_f32_kernel(int N, CView<float> A, float* lre,
                                                            float* lim, float* ure, float* uim) {
-  __shared__ float Tr[64 * 65], Ti[64 * 65];  // [p][row]: column p of the block
+  __shared__ float Tr[64 * 65], Ti[64 * 65];
   const int b = blockIdx.x, upper = blockIdx.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = min(64, N - 64 * b);
-  const CView<float> T = A.sub(64L * b, 64L * b);
-  {
-    float vr[16], vi[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int e = tid + 256 * q, p = e >> 6, row = e & 63;
-      const bool in = row < n && p < n && (upper ? row <= p : row > p);
-      vr[q] = in ? T.r(row, p) : 0.f;
-      vi[q] = in ? T.m(row, p) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int e = tid + 256 * q;
-      Tr[(e >> 6) * 65 + (e & 63)] = vr[q];
-      Ti[(e >> 6) * 65 + (e & 63)] = vi[q];
-    }
-  }
+  tri64_load(n, A.sub(64L * b, 64L * b), upper, Tr, Ti, tid);
   __syncthreads();
   const int c = blockIdx.y * 8 + warp;
-  float x0r = (lane == c) ? 1.f : 0.f, x1r = (lane + 32 == c) ? 1.f : 0.f;
-  float x0i = 0.f, x1i = 0.f;
-  if (c < n) {
-    if (!upper) {
-      for (int p = c; p + 1 < n; ++p) {  // rows above c stay zero
-        const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
-        const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
-        const float l0r = Tr[p * 65 + lane], l0i = Ti[p * 65 + lane];
-        const float l1r = Tr[p * 65 + lane + 32], l1i = Ti[p * 65 + lane + 32];
-        x0r = fmaf(-l0r, pr, fmaf(l0i, pi, x0r));
-        x0i = fmaf(-l0r, pi, fmaf(-l0i, pr, x0i));
-        x1r = fmaf(-l1r, pr, fmaf(l1i, pi, x1r));
-        x1i = fmaf(-l1r, pi, fmaf(-l1i, pr, x1i));
-      }
-    } else {
-      for (int p = c; p >= 0; --p) {  // rows below c stay zero
-        // the owner of row p divides by the diagonal, then everyone subtracts
-        const bool own0 = (lane == p), own1 = (lane + 32 == p);
-        if (own0 || own1) {
-          const float dr = Tr[p * 65 + p], di = Ti[p * 65 + p];
-          const float den = dr * dr + di * di;
-          const float xr = own0 ? x0r : x1r, xi = own0 ? x0i : x1i;
-          const float qr = (xr * dr + xi * di) / den, qi = (xi * dr - xr * di) / den;
-          if (own0) {
-            x0r = qr;
-            x0i = qi;
-          } else {
-            x1r = qr;
-            x1i = qi;
-          }
-        }
-        const float pr = __shfl_sync(0xffffffffu, p < 32 ? x0r : x1r, p & 31);
-        const float pi = __shfl_sync(0xffffffffu, p < 32 ? x0i : x1i, p & 31);
-        const float u0r = (lane < p) ? Tr[p * 65 + lane] : 0.f;
-        const float u0i = (lane < p) ? Ti[p * 65 + lane] : 0.f;
-        const float u1r = (lane + 32 < p) ? Tr[p * 65 + lane + 32] : 0.f;
-        const float u1i = (lane + 32 < p) ? Ti[p * 65 + lane + 32] : 0.f;
-        x0r = fmaf(-u0r, pr, fmaf(u0i, pi, x0r));
-        x0i = fmaf(-u0r, pi, fmaf(-u0i, pr, x0i));
-        x1r = fmaf(-u1r, pr, fmaf(u1i, pi, x1r));
-        x1i = fmaf(-u1r, pi, fmaf(-u1i, pr, x1i));
-      }
-    }
-  }
+  float x0r, x0i, x1r, x1i;
+  tri64_inv_column(n, Tr, Ti, upper, c, lane, x0r, x0i, x1r, x1i);
   float* ore = (upper ? ure : lre) + (size_t)b * 4096 + (size_t)c * 64;
   float* oim = (upper ? uim : lim) + (size_t)b * 4096 + (size_t)c * 64;
   ore[lane] = x0r;
   oim[lane] = x0i;
   ore[lane + 32] = x1r;
   oim[lane + 32] = x1i;
+}
+
+// The inverse of one triangle block T (n <= 64 rows; unit lower or upper)
+// into the n x n block O, transposed when trans_out; 8 CTAs of 8 warps.
+__global__ void __launch_bounds__(256) tri64_inv_kernel(int n, CView<float> T, int upper,
+                                                        CView<float> O, int trans_out) {
+  __shared__ float Tr[64 * 65], Ti[64 * 65];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  tri64_load(n, T, upper, Tr, Ti, tid);
+  __syncthreads();
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= n) return;
+  float x0r, x0i, x1r, x1i;
+  tri64_inv_column(n, Tr, Ti, upper, c, lane, x0r, x0i, x1r, x1i);
+  if (lane < n) {
+    const long o = trans_out ? c * O.rs + lane * O.cs : lane * O.rs + c * O.cs;
+    O.re[o] = x0r;
+    O.im[o] = x0i;
+  }
+  if (lane + 32 < n) {
+    const long o = trans_out ? c * O.rs + (lane + 32) * O.cs : (lane + 32) * O.rs + c * O.cs;
+    O.re[o] = x1r;
+    O.im[o] = x1i;
+  }
 }
 
 template <typename R>
@@ -968,16 +1006,19 @@ __global__ void __launch_bounds__(256) la_trsm_kernel(int n, int ncols, const fl
   }
 }
 
-// C -= A B for C M x ncols, A M x n, B n x ncols (n, ncols <= 64), all
-// column-major planes with leading dimension ld: 32 rows of C per CTA, lane
-// l row l, warp w columns 8 w .. 8 w + 7; the CTA's rows of A and all of B
-// are staged in shared memory by one round of loads.
+// C -= A B for C M x ncols, A M x n, B n x ncols (n, ncols <= 64), column-
+// major planes with leading dimensions lda, ldb, ldc (TA: A given by its
+// transpose, element (r, k) at a[k + r lda]; ZC: C starts from zero instead
+// of being read): 32 rows of C per CTA, lane l row l, warp w columns
+// 8 w .. 8 w + 7; the CTA's rows of A and all of B are staged in shared
+// memory by one round of loads.
+template <bool TA, bool ZC>
 __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
                                                       const float* __restrict__ are,
-                                                      const float* __restrict__ aim,
+                                                      const float* __restrict__ aim, long lda,
                                                       const float* __restrict__ bre,
-                                                      const float* __restrict__ bim, float* cre,
-                                                      float* cim, long ld) {
+                                                      const float* __restrict__ bim, long ldb,
+                                                      float* cre, float* cim, long ldc) {
   __shared__ __align__(16) float Ar[64 * 32], Ai[64 * 32];  // [k][row]
   __shared__ __align__(16) float Br[64 * 64], Bi[64 * 64];  // [k][col]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -986,9 +1027,9 @@ __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
   float accr[8], acci[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const bool in = (row < M) && (c0 + j < ncols);
-    accr[j] = in ? cre[row + (size_t)(c0 + j) * ld] : 0.f;
-    acci[j] = in ? cim[row + (size_t)(c0 + j) * ld] : 0.f;
+    const bool in = !ZC && (row < M) && (c0 + j < ncols);
+    accr[j] = in ? cre[row + (size_t)(c0 + j) * ldc] : 0.f;
+    acci[j] = in ? cim[row + (size_t)(c0 + j) * ldc] : 0.f;
   }
   {
     float vr[8], vi[8];
@@ -996,16 +1037,17 @@ __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
     for (int q = 0; q < 8; ++q) {
       const int e = tid + 256 * q, r = e & 31, k = e >> 5;
       const bool in = (i0 + r < M) && (k < n);
-      vr[q] = in ? are[(i0 + r) + (size_t)k * ld] : 0.f;
-      vi[q] = in ? aim[(i0 + r) + (size_t)k * ld] : 0.f;
+      const size_t o = TA ? (size_t)k + (size_t)(i0 + r) * lda : (size_t)(i0 + r) + (size_t)k * lda;
+      vr[q] = in ? are[o] : 0.f;
+      vi[q] = in ? aim[o] : 0.f;
     }
     float wr[16], wi[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int e = tid + 256 * q, c = e & 63, k = e >> 6;
       const bool in = (k < n) && (c < ncols);
-      wr[q] = in ? bre[k + (size_t)c * ld] : 0.f;
-      wi[q] = in ? bim[k + (size_t)c * ld] : 0.f;
+      wr[q] = in ? bre[k + (size_t)c * ldb] : 0.f;
+      wi[q] = in ? bim[k + (size_t)c * ldb] : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -1040,8 +1082,8 @@ __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       if (c0 + j < ncols) {
-        cre[row + (size_t)(c0 + j) * ld] = accr[j];
-        cim[row + (size_t)(c0 + j) * ld] = acci[j];
+        cre[row + (size_t)(c0 + j) * ldc] = accr[j];
+        cim[row + (size_t)(c0 + j) * ldc] = acci[j];
       }
   }
 }
@@ -1060,10 +1102,67 @@ static int lookahead_update(float* re, float* im, long ld, int N, int k, int nb,
   if (M <= 0) return HARP_OK;
   const size_t l = (size_t)k1 + (size_t)k * ld, c = (size_t)k1 + (size_t)k1 * ld;
   ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)nb1 * nb, st);
-  la_gemm_kernel<<<(M + 31) / 32, 256, 0, st>>>(M, nb, nb1, re + l, im + l, re + u, im + u, re + c,
-                                               im + c, ld);
+  la_gemm_kernel<false, false><<<(M + 31) / 32, 256, 0, st>>>(
+      M, nb, nb1, re + l, im + l, ld, re + u, im + u, ld, re + c, im + c, ld);
   HARP_LAUNCHED();
   return HARP_OK;
+}
+
+// The factor inverses built beside the look-ahead LU, one panel at a time,
+// on ctx->inv_stream. X = U^-1 and V = (L^-1)^T = (L^T)^-1 are upper
+// triangular; after the panel at k (width nb):
+//   X[k:k+nb, k:k+nb] = U_kk^-1,
+//   X[0:k, k:k+nb] = X[0:k, 0:k] (-U[0:k, k:k+nb] U_kk^-1),
+// and V likewise from L^T, whose block column is row block k of L. Block
+// column k of U is final once the panel is factored, and row block k of L
+// once the panel's interchanges reached the L columns (later panels swap only
+// rows below it). Each product takes X[0:k, 0:k] (V[0:k, 0:k]) from
+// persistent TF32 split planes, to which every new block column is appended.
+struct IncInverse {
+  CView<float> T;  // planes of U^-1 (upper) or of (L^-1)^T
+  CView<float> W;  // a k x 64 scratch (column-major, leading dimension ldw)
+  float* sp;       // split planes of T (N rows, row stride Kp, plane stride N Kp)
+  long Kp;
+  size_t plane;
+  bool lower;      // T is (L^-1)^T, built from the row blocks of L
+  float* wa;       // tensor-core workspace of this chain
+  size_t na;
+  float* wb;
+  size_t nbf;
+};
+
+static int inc_inverse_step(const IncInverse& I, CView<float> A, int k, int nb, int mode, int* err,
+                            cudaStream_t s) {
+  const CView<float> T = I.T;
+  {
+    ProfScope ps(HARP_K_TRSM, 8.0 * nb * (double)nb * nb, s);
+    tri64_inv_kernel<<<(nb + 7) / 8, 256, 0, s>>>(nb, A.sub(k, k), I.lower ? 0 : 1, T.sub(k, k),
+                                                   I.lower ? 1 : 0);
+    HARP_LAUNCHED();
+  }
+  if (k > 0) {
+    // W = -(U[0:k, k:k+nb] or L[k:k+nb, 0:k]^T) T[k:k+nb, k:k+nb]
+    {
+      ProfScope ps(HARP_K_GEMM, 8.0 * k * (double)nb * nb, s);
+      const CView<float> D = T.sub(k, k);
+      if (I.lower) {
+        const CView<float> Lr = A.sub(k, 0);  // its transpose is the k x nb operand
+        la_gemm_kernel<true, true><<<(k + 31) / 32, 256, 0, s>>>(
+            k, nb, nb, Lr.re, Lr.im, Lr.cs, D.re, D.im, D.cs, I.W.re, I.W.im, I.W.cs);
+      } else {
+        const CView<float> Uc = A.sub(0, k);
+        la_gemm_kernel<false, true><<<(k + 31) / 32, 256, 0, s>>>(
+            k, nb, nb, Uc.re, Uc.im, Uc.cs, D.re, D.im, D.cs, I.W.re, I.W.im, I.W.cs);
+      }
+      HARP_LAUNCHED();
+    }
+    tc_set_workspace(I.wa, I.na, I.wb, I.nbf, err);
+    int r = cgemm_tc_f32_asplit(k, nb, k, 1.f, I.sp, I.W, 0.f, T.sub(0, k), mode, s, I.Kp,
+                                I.plane);
+    if (r == HARP_E_UNSUPPORTED) r = cgemm<float>(k, nb, k, 1.f, T, I.W, 0.f, T.sub(0, k), mode, s);
+    HARP_TRY(r);
+  }
+  return tc_split_block(k + nb, nb, T.sub(0, k), I.sp + k, I.Kp, I.plane, mode, s);
 }
 
 // FP32 LU with a look-ahead of one panel. Main stream: the update of the
@@ -1074,12 +1173,62 @@ static int lookahead_update(float* re, float* im, long ld, int N, int k, int nb,
 // trailing matrix), which overlaps the next panel. Events order the two:
 // the side stream starts a panel's update once that panel is factored, and
 // the main stream touches columns of panel i+2 only after panel i's far
-// update (which covers them) is done. Only the side stream uses the
-// tensor-core GEMM workspace.
+// update (which covers them) is done. The side stream and the inverse
+// stream (the factor inverses, panel by panel, once a panel's far update is
+// done) use separate halves of the tensor-core GEMM workspace.
 static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long ld, int* ipiv,
                                int* perm, int* zero_col, int mode, cudaStream_t st) {
   CView<float> A = planes<float>(re, im, ld);
   cudaStream_t s2 = ctx->side;
+  float *wa = nullptr, *wb = nullptr;
+  size_t na = 0, nbf = 0;
+  int* werr = nullptr;
+  tc_get_workspace(&wa, &na, &wb, &nbf, &werr);
+  struct Restore {
+    float *a, *b;
+    size_t na, nb;
+    int* e;
+    ~Restore() { tc_set_workspace(a, na, b, nb, e); }
+  } restore{wa, wb, na, nbf, werr};
+  // the factor inverses beside the factorisation (L^-1 on one inverse
+  // stream, U^-1 on the other), when the workspaces and streams are there;
+  // the tensor-core workspace is split in three (side stream, two chains)
+  ctx->finv_incremental = 0;
+  cudaStream_t si[2] = {ctx->inv_stream[0], ctx->inv_stream[1]};
+  bool inc = si[0] && si[1] && wa && wb && ctx->finv && ctx->finv_split && ctx->finv_tmp;
+  IncInverse I[2];
+  const size_t wa3 = na / 3, wb3 = nbf / 3;
+  if (inc) {
+    const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+    const long ldi = ctx->max_N;
+    for (int c = 0; c < 2; ++c) {
+      I[c].lower = (c == 0);
+      I[c].T = planes<float>(ctx->finv + 2 * c * NN, ctx->finv + (2 * c + 1) * NN, ldi);
+      // the scratch: 64 columns each, side by side
+      I[c].W = planes<float>(ctx->finv_tmp + (size_t)c * 64 * ldi,
+                             ctx->finv_tmp + NN + (size_t)c * 64 * ldi, ldi);
+      I[c].Kp = (N + 31) / 32 * 32;
+      I[c].plane = (size_t)N * I[c].Kp;
+      I[c].sp = ctx->finv_split + c * ctx->finv_split_floats;
+      I[c].wa = wa + (1 + c) * wa3;
+      I[c].na = wa3;
+      I[c].wb = wb + (1 + c) * wb3;
+      I[c].nbf = wb3;
+    }
+    inc = (mode == GEMM_TC_3XTF32 ? 4 : 2) * I[0].plane <= ctx->finv_split_floats &&
+          (size_t)128 * ldi <= NN;
+  }
+  if (inc) {
+    // after the caller's earlier work: zero each inverse and its split
+    const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+    const size_t np = (mode == GEMM_TC_3XTF32 ? 4 : 2) * I[0].plane;
+    HARP_CUDA(cudaEventRecord(ctx->ev_inv[0], st));
+    for (int c = 0; c < 2; ++c) {
+      HARP_CUDA(cudaStreamWaitEvent(si[c], ctx->ev_inv[0], 0));
+      HARP_CUDA(cudaMemsetAsync(ctx->finv + 2 * c * NN, 0, 2 * NN * sizeof(float), si[c]));
+      HARP_CUDA(cudaMemsetAsync(I[c].sp, 0, np * sizeof(float), si[c]));
+    }
+  }
   std::vector<int> ks, nbs;
   std::vector<char> maps;  // panel i exported its row map to pmap(i)
   auto pmap = [&](int i) { return ctx->pmap + (size_t)i * kPmapInts; };
@@ -1140,13 +1289,32 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
       } else {
         HARP_TRY(trsm<float>(true, true, nb, N - k2, A.sub(k, k), A.sub(k, k2), mode, s2));
       }
+      if (inc) tc_set_workspace(wa, wa3, wb, wb3, werr);
       HARP_TRY(cgemm<float>(N - k1, N - k2, nb, -1.f, A.sub(k1, k), A.sub(k, k2), 1.f,
                             A.sub(k1, k2), mode, s2));
     }
     HARP_CUDA(cudaEventRecord(ctx->ev_big[i], s2));
     HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_big[i], 0));
+    // inverse stream: panel i's block columns of the factor inverses (every
+    // panel but the last must be kNB wide, so that the block columns stay
+    // on the tensor cores' 32-wide K tiles)
+    if (inc && (nb != kNB && k1 < N)) inc = false;
+    if (inc) {
+      for (int c = 0; c < 2; ++c) {
+        HARP_CUDA(cudaStreamWaitEvent(si[c], ctx->ev_big[i], 0));
+        HARP_TRY(inc_inverse_step(I[c], A, k, nb, mode, werr, si[c]));
+      }
+    }
     if (k1 >= N) break;
   }
+  if (si[0] && si[1] && ctx->finv) {
+    // the caller's stream continues once both inverse streams are done
+    for (int c = 0; c < 2; ++c) {
+      HARP_CUDA(cudaEventRecord(ctx->ev_inv[c], si[c]));
+      HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_inv[c], 0));
+    }
+  }
+  ctx->finv_incremental = inc ? 1 : 0;
   return HARP_OK;
 }
 
@@ -1338,12 +1506,9 @@ int factor_inverses(int N, CView<float> A, const float* dinv_re, const float* di
 // and the row permutation. B (N x nrhs planes, ld ldb) is overwritten; tmp
 // has room for N x nrhs.
 template <typename R>
-int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,
-                 const R* uinv_im, long ldi, const int* perm, R* bre, R* bim, long ldb, R* tre,
-                 R* tim, char trans, int mode, cudaStream_t st, const float* li_split,
-                 const float* ui_split) {
-  CView<R> Li = planes<R>(const_cast<R*>(linv_re), const_cast<R*>(linv_im), ldi);
-  CView<R> Ui = planes<R>(const_cast<R*>(uinv_re), const_cast<R*>(uinv_im), ldi);
+int lu_solve_inv(int N, int nrhs, CView<R> Li, CView<R> Ui, const int* perm, R* bre, R* bim,
+                 long ldb, R* tre, R* tim, char trans, int mode, cudaStream_t st,
+                 const float* li_split, const float* ui_split) {
   CView<R> Bm = planes<R>(bre, bim, ldb), Tm = planes<R>(tre, tim, ldb);
   dim3 grid((N + 255) / 256, nrhs);
   if (trans == 'N' || trans == 'n') {
@@ -1549,9 +1714,9 @@ template int lu_solve<double>(int, int, double*, double*, long, const int*, doub
                               double*, double*, char, const double*, const double*, int,
                               cudaStream_t);
 template int diag_inverses<float>(int, CView<float>, float*, float*, float*, float*, cudaStream_t);
-template int lu_solve_inv<float>(int, int, const float*, const float*, const float*, const float*,
-                                 long, const int*, float*, float*, long, float*, float*, char, int,
-                                 cudaStream_t, const float*, const float*);
+template int lu_solve_inv<float>(int, int, CView<float>, CView<float>, const int*, float*, float*,
+                                 long, float*, float*, char, int, cudaStream_t, const float*,
+                                 const float*);
 template int diag_inverses<double>(int, CView<double>, double*, double*, double*, double*,
                                    cudaStream_t);
 template int interleaved_to_planes<float, float>(int, int, const float*, long, float*, float*, long,

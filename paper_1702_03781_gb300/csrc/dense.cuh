@@ -88,17 +88,24 @@ int factor_inverses(int N, CView<float> A, const float* dinv_re, const float* di
 // tensor-core operand planes (tc_split_operand, same mode), used by the
 // 'N' products.
 template <typename R>
-int lu_solve_inv(int N, int nrhs, const R* linv_re, const R* linv_im, const R* uinv_re,
-                 const R* uinv_im, long ldi, const int* perm, R* bre, R* bim, long ldb, R* tre,
-                 R* tim, char trans, int mode, cudaStream_t st, const float* li_split = nullptr,
-                 const float* ui_split = nullptr);
+int lu_solve_inv(int N, int nrhs, CView<R> Li, CView<R> Ui, const int* perm, R* bre, R* bim,
+                 long ldb, R* tre, R* tim, char trans, int mode, cudaStream_t st,
+                 const float* li_split = nullptr, const float* ui_split = nullptr);
 
 // K-major tensor-core operand planes of V (R x K) for repeated use, and the
 // product that takes them as its A operand (lu_tc.cu).
 int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats, int mode,
                      cudaStream_t st);
+// a_ld > 0: A is a block of larger split planes, row stride a_ld, plane
+// stride a_plane (K then a multiple of 32). split_k: K may be split to fill
+// the SMs (off for products that run beside other work).
 int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
-                        float beta, CView<float> C, int mode, cudaStream_t st);
+                        float beta, CView<float> C, int mode, cudaStream_t st, long a_ld = 0,
+                        size_t a_plane = 0, bool split_k = true);
+// The TF32 planes of V (R x Kc) into a block of larger split planes
+// (element (r, k) at out[p * plane + r * ldo + k]).
+int tc_split_block(int R, int Kc, CView<float> V, float* out, long ldo, size_t plane, int mode,
+                   cudaStream_t st);
 
 // Solve op(A) X = B with the factors of lu_factor and their diagonal-block
 // inverses (dinv planes: the L blocks, then the U blocks); B (N x nrhs split

@@ -363,17 +363,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 3-D map over planes [NP][rows][Kp] fp32, box (32, box_rows, 1), 128B swizzle.
-static bool make_map(CUtensorMap* m, float* base, int rows, int Kp, int NP, int box_rows) {
+static bool make_map_ld(CUtensorMap* m, float* base, int rows, int Kp, long ld, size_t plane,
+                        int NP, int box_rows) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NP};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)Kp * 4 * (cuuint64_t)rows};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)plane * 4};
   cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+static bool make_map(CUtensorMap* m, float* base, int rows, int Kp, int NP, int box_rows) {
+  return make_map_ld(m, base, rows, Kp, Kp, (size_t)Kp * rows, NP, box_rows);
 }
 
 // Workspace for the split operands and the timeout flag (set per solve).
@@ -505,6 +510,50 @@ static int splitk_count(int tiles, int nk) {
   return best;
 }
 
+// The TF32 planes of V (R x Kc) written into a sub-block of larger split
+// planes: element (r, k) at out[p * plane + r * ldo + k]; nothing outside
+// the R x Kc block is touched.
+__global__ void split_block_kernel(int R, int Kc, CView<float> V, float* out, long ldo,
+                                   size_t plane, int three) {
+  __shared__ float tr[32][33], ti[32][33];  // [k_local][r_local]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const bool rows_contig = (V.rs == 1);
+  for (int l = ty; l < 32; l += 8) {
+    const int rl = rows_contig ? tx : l, kl = rows_contig ? l : tx;
+    const int r = r0 + rl, k = k0 + kl;
+    const bool in = (r < R) && (k < Kc);
+    tr[kl][rl] = in ? V.r(r, k) : 0.f;
+    ti[kl][rl] = in ? V.m(r, k) : 0.f;
+  }
+  __syncthreads();
+  for (int l = ty; l < 32; l += 8) {
+    const int r = r0 + l, k = k0 + tx;
+    if (r >= R || k >= Kc) continue;
+    const float xr = tr[tx][l], xi = ti[tx][l];
+    const float hr = __uint_as_float((__float_as_uint(xr) + 0x1000u) & 0xffffe000u);
+    const float hi = __uint_as_float((__float_as_uint(xi) + 0x1000u) & 0xffffe000u);
+    const size_t o = (size_t)r * ldo + k;
+    out[o] = hr;
+    out[plane + o] = hi;
+    if (three) {
+      const float lr = xr - hr, li = xi - hi;
+      out[2 * plane + o] = __uint_as_float((__float_as_uint(lr) + 0x1000u) & 0xffffe000u);
+      out[3 * plane + o] = __uint_as_float((__float_as_uint(li) + 0x1000u) & 0xffffe000u);
+    }
+  }
+}
+
+int tc_split_block(int R, int Kc, CView<float> V, float* out, long ldo, size_t plane, int mode,
+                   cudaStream_t st) {
+  if (R <= 0 || Kc <= 0) return HARP_OK;
+  ProfScope ps(HARP_K_OTHER, 0.0, st);
+  split_block_kernel<<<dim3((Kc + 31) / 32, (R + 31) / 32), dim3(32, 8), 0, st>>>(
+      R, Kc, V, out, ldo, plane, mode == GEMM_TC_3XTF32 ? 1 : 0);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
 // K-major TF32 planes of an operand V (R x K) into out, as the GEMM's own
 // split makes them (NP planes of R x Kp), for an operand used by many products.
 int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats, int mode,
@@ -525,7 +574,8 @@ int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats
 // idle splits K, the partials going to the (here unused) A workspace and a
 // reduction forming C.
 int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
-                        float beta, CView<float> C, int mode, cudaStream_t st) {
+                        float beta, CView<float> C, int mode, cudaStream_t st, long a_ld,
+                        size_t a_plane, bool split_k) {
   if (M < 64 || N < 64 || K < 32 || !g_tc.b || !a_split) return HARP_E_UNSUPPORTED;
   const bool three = (mode == GEMM_TC_3XTF32);
   const int NP = three ? 4 : 2;
@@ -538,8 +588,12 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
                                                                                 g_tc.b, pb, three, 0);
     HARP_LAUNCHED();
   }
+  // A's planes: row stride a_ld and plane stride a_plane when it is a block
+  // of larger split planes (K extent Kp, a multiple of the k-tile)
+  if (a_ld > 0 && (K % TC_BK != 0 || a_ld < Kp || a_ld % 4 != 0)) return HARP_E_UNSUPPORTED;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, const_cast<float*>(a_split), M, Kp, NP, TC_BM) ||
+  if (!make_map_ld(&ma, const_cast<float*>(a_split), M, Kp, a_ld > 0 ? a_ld : Kp,
+                   a_ld > 0 ? a_plane : (size_t)M * Kp, NP, TC_BM) ||
       !make_map(&mb, g_tc.b, N, Kp, NP, TC_BN))
     return HARP_E_UNSUPPORTED;
   TcArgs args;
@@ -556,7 +610,7 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   args.err = g_tc.err;
   args.ksplit = 0;
   const int gx = (N + TC_BN - 1) / TC_BN, gy = (M + TC_BM - 1) / TC_BM;
-  int S = splitk_count(gx * gy, args.nk);
+  int S = split_k ? splitk_count(gx * gy, args.nk) : 1;
   if ((size_t)2 * S * M * N > g_tc.a_floats || !g_tc.a) S = 1;
   if (S > 1) {
     args.nk /= S;

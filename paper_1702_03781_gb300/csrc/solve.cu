@@ -31,6 +31,14 @@ static int gemm_mode(int prec) {
 // Factorisations are shared between the modes that store the same type.
 static int lu_class(int prec) { return prec == HARP_FP64 ? 0 : 1; }
 
+// L^-1 as a view of the L slot of finv, which holds (L^-1)^T when the
+// inverses were built beside the factorisation.
+static CView<float> linv_view(const harp_ctx* c) {
+  const size_t NN = (size_t)c->max_N * c->max_N;
+  const CView<float> v = planes<float>(c->finv, c->finv + NN, c->max_N);
+  return c->finv_incremental ? v.t() : v;
+}
+
 static bool use_slices(const harp_ctx* c) {
   return c->oz_a && c->residual_mode == HARP_RESIDUAL_SLICES;
 }
@@ -49,9 +57,7 @@ bool profiling_active();
 // perm[c_m] = m s, so that product is a gather (CTA m: find c_m, copy the
 // column).
 __global__ void port_linv_gather_kernel(int N, int s, const int* __restrict__ perm,
-                                        const float* __restrict__ lre,
-                                        const float* __restrict__ lim, long ldi, float* wre,
-                                        float* wim, long ldw) {
+                                        CView<float> Li, float* wre, float* wim, long ldw) {
   __shared__ int col;
   const int m = blockIdx.x;
   if (threadIdx.x == 0) col = -1;
@@ -61,8 +67,8 @@ __global__ void port_linv_gather_kernel(int N, int s, const int* __restrict__ pe
   __syncthreads();
   const int c = col;
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
-    wre[r + (size_t)m * ldw] = (c >= 0) ? lre[r + (size_t)c * ldi] : 0.f;
-    wim[r + (size_t)m * ldw] = (c >= 0) ? lim[r + (size_t)c * ldi] : 0.f;
+    wre[r + (size_t)m * ldw] = (c >= 0) ? Li.r(r, c) : 0.f;
+    wim[r + (size_t)m * ldw] = (c >= 0) ? Li.m(r, c) : 0.f;
   }
 }
 
@@ -80,15 +86,19 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
   float* tim = (float*)ctx->t_im;
   const int g = (trans == 'T') ? 1 : 0;
   const bool keyed = ctx->solve_graph[g] && ctx->solve_key[g][0] == N &&
-                     ctx->solve_key[g][1] == nrhs && ctx->solve_key[g][2] == mode;
+                     ctx->solve_key[g][1] == nrhs && ctx->solve_key[g][2] == mode &&
+                     ctx->solve_key[g][3] == ctx->finv_incremental;
   const size_t NN = (size_t)ctx->max_N * ctx->max_N;
   const float* fi = ctx->finv;
   const bool pre = (ctx->finv_split_mode == mode);
   const float* lsp = pre ? ctx->finv_split : nullptr;
   const float* usp = pre ? ctx->finv_split + ctx->finv_split_floats : nullptr;
+  const CView<float> Li = linv_view(ctx), Ui = planes<float>(const_cast<float*>(fi) + 2 * NN,
+                                                             const_cast<float*>(fi) + 3 * NN,
+                                                             ctx->max_N);
   auto run = [&](cudaStream_t s) {
-    return lu_solve_inv<float>(N, nrhs, fi, fi + NN, fi + 2 * NN, fi + 3 * NN, ctx->max_N,
-                               ctx->perm, wre, wim, ldw, tre, tim, trans, mode, s, lsp, usp);
+    return lu_solve_inv<float>(N, nrhs, Li, Ui, ctx->perm, wre, wim, ldw, tre, tim, trans, mode,
+                               s, lsp, usp);
   };
   if (profiling_active() || (first && !keyed)) return run(st);
   if (!keyed) {
@@ -111,6 +121,7 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
     ctx->solve_key[g][0] = N;
     ctx->solve_key[g][1] = nrhs;
     ctx->solve_key[g][2] = mode;
+    ctx->solve_key[g][3] = ctx->finv_incremental;
   }
   HARP_CUDA(cudaGraphLaunch(ctx->solve_graph[g], st));
   return HARP_OK;
@@ -175,6 +186,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       float* im = (float*)ctx->lu_im;
       HARP_TRY(interleaved_to_planes<float, float>(N, N, (const float*)Z, ldz, re, im, ctx->ld_lu,
                                                    st));
+      ctx->finv_incremental = 0;
       HARP_TRY(lu_factor<float>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                 ctx->dstatus + 1, mode, st));
       const size_t nb = (size_t)((N + 63) / 64) * 4096;
@@ -184,13 +196,21 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
                                     st));
       const size_t NN = (size_t)ctx->max_N * ctx->max_N;
       float* fi = ctx->finv;
-      HARP_TRY(factor_inverses(N, planes<float>(re, im, ctx->ld_lu), dr, di, fi, fi + NN,
-                               fi + 2 * NN, fi + 3 * NN, ctx->max_N, ctx->finv_tmp,
-                               ctx->finv_tmp + NN, mode, st, ctx->side, ctx->ev_fac[0],
-                               ctx->ev_big[0]));
-      // the inverses as tensor-core operands, once for all forward solves
       ctx->finv_split_mode = -1;
-      if (mode != GEMM_SIMT) {
+      if (ctx->finv_incremental) {
+        // built beside the factorisation: U^-1 with its split, and (L^-1)^T,
+        // whose transpose is split here
+        if (tc_split_operand(N, N, planes<float>(fi, fi + NN, ctx->max_N).t(), ctx->finv_split,
+                             ctx->finv_split_floats, mode, st) == HARP_OK)
+          ctx->finv_split_mode = mode;
+      } else {
+        HARP_TRY(factor_inverses(N, planes<float>(re, im, ctx->ld_lu), dr, di, fi, fi + NN,
+                                 fi + 2 * NN, fi + 3 * NN, ctx->max_N, ctx->finv_tmp,
+                                 ctx->finv_tmp + NN, mode, st, ctx->side, ctx->ev_fac[0],
+                                 ctx->ev_big[0]));
+      }
+      // the inverses as tensor-core operands, once for all forward solves
+      if (mode != GEMM_SIMT && !ctx->finv_incremental) {
         const size_t fs = ctx->finv_split_floats;
         const long ldi = ctx->max_N;
         if (tc_split_operand(N, N, planes<float>(fi, fi + NN, ldi), ctx->finv_split, fs, mode,
@@ -235,8 +255,8 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     // port right-hand sides: the L^-1 product is a column gather, then U^-1
     {
       ProfScope ps(HARP_K_OTHER, 0.0, st);
-      port_linv_gather_kernel<<<nrhs, 256, 0, st>>>(N, N / nrhs, ctx->perm, ctx->finv,
-                                                    ctx->finv + NNi, ctx->max_N, wre, wim, ldw);
+      port_linv_gather_kernel<<<nrhs, 256, 0, st>>>(N, N / nrhs, ctx->perm, linv_view(ctx), wre,
+                                                    wim, ldw);
       HARP_LAUNCHED();
     }
     int su = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, ctx->finv_split + ctx->finv_split_floats,
