@@ -1158,7 +1158,7 @@ static int inc_inverse_step(const IncInverse& I, CView<float> A, int k, int nb, 
     }
     tc_set_workspace(I.wa, I.na, I.wb, I.nbf, err);
     int r = cgemm_tc_f32_asplit(k, nb, k, 1.f, I.sp, I.W, 0.f, T.sub(0, k), mode, s, I.Kp,
-                                I.plane);
+                                I.plane, true, 1);  // T[0:k, 0:k] upper triangular
     if (r == HARP_E_UNSUPPORTED) r = cgemm<float>(k, nb, k, 1.f, T, I.W, 0.f, T.sub(0, k), mode, s);
     HARP_TRY(r);
   }
@@ -1520,11 +1520,13 @@ int lu_solve_inv(int N, int nrhs, CView<R> Li, CView<R> Ui, const int* perm, R* 
     // B = L^-1 P b, T = U^-1 B (the inverses pre-split when given)
     int s1 = HARP_E_UNSUPPORTED, s2 = HARP_E_UNSUPPORTED;
     if constexpr (std::is_same<R, float>::value)
-      if (li_split) s1 = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, li_split, Tm, 0.f, Bm, mode, st);
+      if (li_split)  // L^-1 is lower triangular: each row tile skips its zero k-tiles
+        s1 = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, li_split, Tm, 0.f, Bm, mode, st, 0, 0, true, 2);
     if (s1 == HARP_E_UNSUPPORTED) s1 = cgemm<R>(N, nrhs, N, (R)1, Li, Tm, (R)0, Bm, mode, st);
     HARP_TRY(s1);
     if constexpr (std::is_same<R, float>::value)
-      if (ui_split) s2 = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, ui_split, Bm, 0.f, Tm, mode, st);
+      if (ui_split)  // and U^-1 upper triangular
+        s2 = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, ui_split, Bm, 0.f, Tm, mode, st, 0, 0, true, 1);
     if (s2 == HARP_E_UNSUPPORTED) s2 = cgemm<R>(N, nrhs, N, (R)1, Ui, Bm, (R)0, Tm, mode, st);
     HARP_TRY(s2);
     HARP_TRY(planes_to_planes<R, R>(N, nrhs, tre, tim, ldb, bre, bim, ldb, st));

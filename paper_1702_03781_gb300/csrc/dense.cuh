@@ -98,10 +98,11 @@ int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats
                      cudaStream_t st);
 // a_ld > 0: A is a block of larger split planes, row stride a_ld, plane
 // stride a_plane (K then a multiple of 32). split_k: K may be split to fill
-// the SMs (off for products that run beside other work).
+// the SMs. a_tri: A is upper (1: row i zero for k < i) or lower (2: zero for
+// k > i) triangular, and the zero k-tiles of each row tile are skipped.
 int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
                         float beta, CView<float> C, int mode, cudaStream_t st, long a_ld = 0,
-                        size_t a_plane = 0, bool split_k = true);
+                        size_t a_plane = 0, bool split_k = true, int a_tri = 0);
 // The TF32 planes of V (R x Kc) into a block of larger split planes
 // (element (r, k) at out[p * plane + r * ldo + k]).
 int tc_split_block(int R, int Kc, CView<float> V, float* out, long ldo, size_t plane, int mode,

@@ -131,6 +131,7 @@ struct TcArgs {
   long cstride;  // element offset of product z's C (grid z)
   int* err;
   int ksplit;    // grid z splits K (one product, nk k-tiles each) instead of batching
+  int tri;       // A triangular: 1 upper (row i zero below k = i), 2 lower (zero above)
 };
 
 template <bool THREE>
@@ -153,6 +154,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // split K: grid z is the K range, all of one product
   const int pz = a.ksplit ? 0 : blockIdx.z * NP;
   const int kt0 = a.ksplit ? blockIdx.z * a.nk : 0;
+  // k-tiles [kb, ke) of this CTA's range (relative to kt0): with a
+  // triangular A the tiles that are zero for all of its rows are skipped
+  int kb = 0, ke = a.nk;
+  if (a.tri == 1) kb = max(0, i0 / TC_BK - kt0);
+  if (a.tri == 2) ke = min(a.nk, (i0 + TC_BM + TC_BK - 1) / TC_BK - kt0);
+  const bool empty = (kb >= ke);
   float* cre = a.cre + blockIdx.z * a.cstride;
   float* cim = a.cim + blockIdx.z * a.cstride;
 
@@ -183,8 +190,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       // ---- TMA producer
       int issued = 0;
-      for (int kt = 0; kt < a.nk; ++kt) {
-        const int s = kt % TC_STAGES, use = kt / TC_STAGES;
+      for (int kt = kb; kt < ke; ++kt) {
+        const int j = kt - kb;  // ring iteration
+        const int s = j % TC_STAGES, use = j / TC_STAGES;
         if (use > 0 && !mbar_wait(su32(&bar_empty[s]), (use - 1) & 1, a.err)) break;
         const uint32_t st = base + s * STAGE;
         const uint32_t fb = su32(&bar_full[s]);
@@ -194,11 +202,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, (kt0 + kt) * TC_BK, j0,
                       pz + q);
         }
-        issued = kt + 1;
+        issued = j + 1;
       }
       // make sure every issued copy has landed before the CTA can exit
-      for (int kt = (issued > TC_STAGES ? issued - TC_STAGES : 0); kt < issued; ++kt)
-        mbar_wait(su32(&bar_full[kt % TC_STAGES]), (kt / TC_STAGES) & 1, a.err);
+      for (int q = (issued > TC_STAGES ? issued - TC_STAGES : 0); q < issued; ++q)
+        mbar_wait(su32(&bar_full[q % TC_STAGES]), (q / TC_STAGES) & 1, a.err);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -207,8 +215,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       constexpr uint32_t ID = tf32_idesc(TC_BM, TC_BN, false);
       constexpr uint32_t IDN = tf32_idesc(TC_BM, TC_BN, true);
       bool first = true;
-      for (int kt = 0; kt < a.nk; ++kt) {
-        const int s = kt % TC_STAGES, use = kt / TC_STAGES;
+      for (int kt = kb; kt < ke; ++kt) {
+        const int it = kt - kb;  // ring iteration, as the producer counts them
+        const int s = it % TC_STAGES, use = it / TC_STAGES;
         if (!mbar_wait(su32(&bar_full[s]), use & 1, a.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE;
@@ -275,8 +284,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        float xr = a.alpha * __uint_as_float(vr[j]);
-        float xi = a.alpha * __uint_as_float(vi[j]);
+        // no k-tile in range: the accumulator was never written, the product is 0
+        float xr = empty ? 0.f : a.alpha * __uint_as_float(vr[j]);
+        float xi = empty ? 0.f : a.alpha * __uint_as_float(vi[j]);
         if (a.beta != 0.f) {
           xr = fmaf(a.beta, cr[j], xr);
           xi = fmaf(a.beta, ci[j], xi);
@@ -446,6 +456,7 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   args.cstride = sC;
   args.err = g_tc.err;
   args.ksplit = 0;
+  args.tri = 0;
   const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
   const size_t smem = (size_t)TC_STAGES * stage + 1024;
   void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
@@ -575,7 +586,7 @@ int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats
 // reduction forming C.
 int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, CView<float> B,
                         float beta, CView<float> C, int mode, cudaStream_t st, long a_ld,
-                        size_t a_plane, bool split_k) {
+                        size_t a_plane, bool split_k, int a_tri) {
   if (M < 64 || N < 64 || K < 32 || !g_tc.b || !a_split) return HARP_E_UNSUPPORTED;
   const bool three = (mode == GEMM_TC_3XTF32);
   const int NP = three ? 4 : 2;
@@ -609,6 +620,7 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   args.cstride = 0;
   args.err = g_tc.err;
   args.ksplit = 0;
+  args.tri = a_tri;
   const int gx = (N + TC_BN - 1) / TC_BN, gy = (M + TC_BM - 1) / TC_BM;
   int S = split_k ? splitk_count(gx * gy, args.nk) : 1;
   if ((size_t)2 * S * M * N > g_tc.a_floats || !g_tc.a) S = 1;

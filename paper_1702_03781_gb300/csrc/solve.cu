@@ -261,7 +261,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     }
     int su = cgemm_tc_f32_asplit(N, nrhs, N, 1.f, ctx->finv_split + ctx->finv_split_floats,
                                  planes<float>(wre, wim, ldw), 0.f, planes<float>(tre, tim, ldw),
-                                 mode, st);
+                                 mode, st, 0, 0, true, 1);  // U^-1 upper triangular
     if (su == HARP_E_UNSUPPORTED)  // shapes the tensor-core product does not take
       su = cgemm<float>(N, nrhs, N, 1.f,
                         planes<float>(ctx->finv + 2 * NNi, ctx->finv + 3 * NNi, ctx->max_N),
