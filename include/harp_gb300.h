@@ -155,7 +155,10 @@ int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, do
  *                at exit (may be NULL; -1 for HARP_FP64, HARP_FP32) [15]
  * The mixed modes refine against the context's FP64 matrix (written by the
  * last mixed harp_fill, or by the caller through harp_ctx_z64) and
- * synchronise the stream once per step. Returns +i on an exactly zero pivot
+ * synchronise the stream once per step. The FP32 factorisation also runs
+ * work on streams of the context (the trailing updates, and the factor
+ * inverses built panel by panel beside it); that work is ordered before
+ * anything the call later enqueues on `stream`. Returns +i on an exactly zero pivot
  * in column i, HARP_E_NOCONV when tol was not met (X then holds the best
  * iterate). */
 int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int ldv, int nrhs,
