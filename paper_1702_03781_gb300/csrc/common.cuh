@@ -207,6 +207,10 @@ struct harp_ctx {
   cudaStream_t inv_stream[2];
   cudaEvent_t ev_inv[2];
   int finv_incremental;
+  // Whether the FP32 factorisation may build the inverses beside itself (1),
+  // or builds them after it (0: the batch scheduler, whose concurrent
+  // factorisations leave no idle SMs for them).
+  int inv_beside;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;

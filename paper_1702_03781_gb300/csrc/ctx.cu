@@ -186,6 +186,7 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
         cudaEventCreateWithFlags(&c->ev_inv[q], cudaEventDisableTiming) != cudaSuccess)
       ok = false;
   c->finv_incremental = 0;
+  c->inv_beside = 1;
   if (ok) {
     c->n_events = max_N / 16 + 2;
     if (cudaMalloc((void**)&c->pmap, (size_t)c->n_events * kPmapInts * sizeof(int)) != cudaSuccess)

@@ -1195,7 +1195,8 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
   // the tensor-core workspace is split in three (side stream, two chains)
   ctx->finv_incremental = 0;
   cudaStream_t si[2] = {ctx->inv_stream[0], ctx->inv_stream[1]};
-  bool inc = si[0] && si[1] && wa && wb && ctx->finv && ctx->finv_split && ctx->finv_tmp;
+  bool inc = ctx->inv_beside && si[0] && si[1] && wa && wb && ctx->finv && ctx->finv_split &&
+             ctx->finv_tmp;
   IncInverse I[2];
   const size_t wa3 = na / 3, wb3 = nbf / 3;
   if (inc) {
