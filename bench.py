@@ -345,7 +345,9 @@ def main():
             "gpu_launches": int(L1 - L0),
             "clocks": clk.summary(),
             "e2e": {"value": round(e2e_max / ws, 4), "unit": "ms", "h2d_bytes_per_step": int(bi),
-                    "d2h_bytes_per_step": int(bo)},
+                    "d2h_bytes_per_step": int(bo),
+                    "median_ms": round(statistics.median(ms_e2e) / ws, 4),
+                    "steps_ms": [round(m, 3) for m in ms_e2e]},
             "roofline": roof,
             "roofline_kernels": roof_all,
             "kernel_shares": shares,

@@ -291,10 +291,12 @@ int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos, d
  * (8 real flops per complex multiply-add). */
 #define HARP_PROF_KINDS 10
 #define HARP_K_FILL 0     /* harp_fill kernels (FP64 and FP32 evaluation)        */
-#define HARP_K_GEMM 1     /* LU trailing updates and triangular-solve updates   */
+#define HARP_K_GEMM 1     /* tensor-core products: LU trailing updates, the
+                             factor inverses' products, the solves' products    */
 #define HARP_K_RESIDUAL 2 /* FP64-accurate residual R = V - Z X of the refinement */
 #define HARP_K_PANEL 3    /* in-panel LU leaves (pivot search)                  */
-#define HARP_K_TRSM 4     /* triangular-solve leaves                            */
+#define HARP_K_TRSM 4     /* triangular-solve leaves, triangle-block inverses and
+                             the narrow look-ahead products (64 wide)          */
 #define HARP_K_SWAP 5     /* row interchanges                                   */
 #define HARP_K_ADJOINT 6  /* harp_fill_adjoint kernels                          */
 #define HARP_K_OTHER 7    /* conversions, norms, permutations                   */

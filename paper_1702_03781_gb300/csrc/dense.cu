@@ -1101,7 +1101,7 @@ static int lookahead_update(float* re, float* im, long ld, int N, int k, int nb,
   const int M = N - k1;
   if (M <= 0) return HARP_OK;
   const size_t l = (size_t)k1 + (size_t)k * ld, c = (size_t)k1 + (size_t)k1 * ld;
-  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)nb1 * nb, st);
+  ProfScope ps(HARP_K_TRSM, 8.0 * M * (double)nb1 * nb, st);
   la_gemm_kernel<false, false><<<(M + 31) / 32, 256, 0, st>>>(
       M, nb, nb1, re + l, im + l, ld, re + u, im + u, ld, re + c, im + c, ld);
   HARP_LAUNCHED();
@@ -1143,7 +1143,7 @@ static int inc_inverse_step(const IncInverse& I, CView<float> A, int k, int nb, 
   if (k > 0) {
     // W = -(U[0:k, k:k+nb] or L[k:k+nb, 0:k]^T) T[k:k+nb, k:k+nb]
     {
-      ProfScope ps(HARP_K_GEMM, 8.0 * k * (double)nb * nb, s);
+      ProfScope ps(HARP_K_TRSM, 8.0 * k * (double)nb * nb, s);
       const CView<float> D = T.sub(k, k);
       if (I.lower) {
         const CView<float> Lr = A.sub(k, 0);  // its transpose is the k x nb operand

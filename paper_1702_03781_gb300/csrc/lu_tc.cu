@@ -646,7 +646,8 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
     attr_set[three ? 1 : 0] = true;
   }
   dim3 grid(gx, gy, S);
-  ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K, st);
+  // a triangular A: the algorithmic work is half the full product's
+  ProfScope ps(HARP_K_GEMM, (a_tri ? 4.0 : 8.0) * M * (double)N * K, st);
   kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
   HARP_LAUNCHED();
   if (S > 1) {
