@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -56,12 +57,13 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = None
+        self._summary = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"harp_clocks{self.index}_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -70,6 +72,7 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
+        lines = []
         if self.proc:
             self.proc.terminate()
             try:
@@ -77,13 +80,17 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.f.close()
+            with open(self.path) as f:
+                lines = f.readlines()
+        if self.path:
+            os.unlink(self.path)
+        self._summary = self._parse(lines) if self.proc else None
 
-    def summary(self):
-        if not self.proc or not os.path.exists(self.path):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    @staticmethod
+    def _parse(lines):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -97,6 +104,9 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+    def summary(self):
+        return self._summary or {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
 
 
 def wideband_throughput(device: int, n_ctx: int = 4, n_freq: int = 64) -> dict:
@@ -278,30 +288,6 @@ def main():
     # the kernel class with the most device time, whatever bounds it
     dominant = max((k for k in roofline.KINDS if prof_all[k]["launches"]),
                    key=lambda k: prof_all[k]["ms"])
-    barrier()
-    L0 = H.kernel_launches()
-    roofline.begin(h, 1 << roofline.KINDS.index(dominant))
-    with ClockSampler(local) as clk:
-        barrier()
-        ms_mixed = timed(step_mixed, args.steps)
-        barrier()
-    prof_dom = roofline.end(h)[dominant]
-    L1 = H.kernel_launches()
-    ms_fp64 = timed(step_fp64, max(2, min(args.steps, 5)))
-    barrier()
-
-    # agreement of the two GPU paths on the last step
-    rel = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
-
-    # per-kernel timing of the dominant kernel (see DESIGN: roofline)
-    t_mixed = statistics.mean(ms_mixed)
-    t_max = t_mixed
-    if ws > 1:
-        tt = torch.tensor([t_mixed], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = t_max / ws  # whole-job ms per frequency (ws frequencies per step)
-
     # ---- end to end through the public API with host buffers
     pos_h = torch.from_numpy(p.pos).pin_memory()
     coef_h = torch.from_numpy(p.coef).pin_memory()
@@ -317,7 +303,35 @@ def main():
         h.fill(pd, p.freq_hz, cd, sd, prec="mixed", out=Z32)
         h.solve(Z32, None, nrhs=Na, prec="mixed", max_iter=10, out=X)
         X_h.copy_(X.T, non_blocking=True)
-    ms_e2e = timed(step_e2e, args.steps)
+    for _ in range(args.warmup):
+        step_e2e()
+
+    barrier()
+    L0 = H.kernel_launches()
+    roofline.begin(h, 1 << roofline.KINDS.index(dominant))
+    # one clock record over the three timed regions (mixed, FP64, end to end)
+    with ClockSampler(local) as clk:
+        barrier()
+        ms_mixed = timed(step_mixed, args.steps)
+        barrier()
+        prof_dom = roofline.end(h)[dominant]
+        L1 = H.kernel_launches()
+        ms_fp64 = timed(step_fp64, max(2, min(args.steps, 5)))
+        barrier()
+        # agreement of the two GPU paths (last mixed step against last FP64 step)
+        rel = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
+        barrier()
+        ms_e2e = timed(step_e2e, args.steps)
+        barrier()
+
+    t_mixed = statistics.mean(ms_mixed)
+    t_max = t_mixed
+    if ws > 1:
+        tt = torch.tensor([t_mixed], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = t_max / ws  # whole-job ms per frequency (ws frequencies per step)
+
     e2e_max = statistics.mean(ms_e2e)
     if ws > 1:
         tt = torch.tensor([e2e_max], device=dev, dtype=torch.float64)
