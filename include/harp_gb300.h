@@ -199,6 +199,18 @@ int harp_residual(harp_ctx* ctx, int N, const double* Z, int ldz, const float* X
                   const double* V, int ldv, int nrhs, double* R, int ldr, char trans,
                   void* stream);
 
+/* Check of the bounded device wait that every mbarrier wait of the
+ * tensor-core kernels uses (a budget of 2^30 SM clock cycles, about 0.5 s at
+ * 2 GHz). One thread waits on a fresh mbarrier of arrival count 1:
+ *   release != 0  the thread arrives first; the wait ends at once -> HARP_OK
+ *   release == 0  nothing arrives; the wait runs out its budget, sets the
+ *                 context's timeout word and the call returns HARP_E_TIMEOUT
+ * The status is read back exactly as mbf_solve reads it, and the word is
+ * cleared afterwards, so the context stays usable. Synchronises `stream`;
+ * not concurrently with a solve on the same context (they share the word).
+ * Errors: -1 null ctx; HARP_E_CUDA. */
+int harp_wait_check(harp_ctx* ctx, int release, void* stream);
+
 /* Position gradient of a real objective J(X) of the solution of Z X = V:
  *   grad[m] = -2 Re sum over pairs (m, n) and (n, m) of
  *             sum_TS G_TS dZ_TS/dx_m,       G = Lambda X^T,

@@ -657,4 +657,34 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   return HARP_OK;
 }
 
+// One thread waits, with the tensor-core kernels' bounded wait, on a fresh
+// mbarrier of arrival count 1. With release != 0 the thread arrives first and
+// the wait ends at once; with release == 0 nothing arrives, the wait runs out
+// its clock budget and sets *err.
+__global__ void wait_check_kernel(int release, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = su32(&bar);
+  mbar_init(b, 1);
+  if (release) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+  mbar_wait(b, 0, err);
+}
+
 }  // namespace harp
+
+extern "C" int harp_wait_check(harp_ctx* ctx, int release, void* stream) {
+  using namespace harp;
+  if (!ctx) return -1;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
+  wait_check_kernel<<<1, 32, 0, st>>>(release, ctx->dstatus + 2);
+  HARP_LAUNCHED();
+  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 2, ctx->dstatus + 2, sizeof(int),
+                            cudaMemcpyDeviceToHost, st));
+  HARP_CUDA(cudaStreamSynchronize(st));
+  const int timed_out = ctx->hstatus[2];
+  HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
+  return timed_out ? HARP_E_TIMEOUT : HARP_OK;
+}

@@ -91,9 +91,11 @@ def lib():
         L.harp_ctx_set_option.argtypes = [vp, i, i]
         L.harp_ctx_get_option.argtypes = [vp, i, ct.POINTER(i)]
         L.harp_residual.argtypes = [vp, i, vp, i, vp, i, vp, i, i, vp, i, ct.c_char, vp]
+        L.harp_wait_check.argtypes = [vp, i, vp]
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_z64", "harp_fill",
                    "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
-                   "harp_ctx_set_option", "harp_ctx_get_option", "harp_residual"):
+                   "harp_ctx_set_option", "harp_ctx_get_option", "harp_residual",
+                   "harp_wait_check"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -267,6 +269,11 @@ class Harp:
             self._h, N, _ptr(Z), _ld(Z), _ptr(X), _ld(X), _ptr(V), _ld(V), nrhs, _ptr(R), _ld(R),
             trans.encode(), _stream(stream)))
         return R
+
+    def wait_check(self, release: bool, stream=None) -> int:
+        """Status of one bounded device wait on an mbarrier that is released
+        (HARP_OK) or never arrived at (HARP_E_TIMEOUT after ~0.5 s)."""
+        return lib().harp_wait_check(self._h, 1 if release else 0, _stream(stream))
 
     # -- adjoint ------------------------------------------------------------
     def fill_adjoint(self, pos: torch.Tensor, freq_hz: float, coef: torch.Tensor,

@@ -65,3 +65,5 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     assert L.harp_ctx_set_option(None, 1, 0) == -1
     L.harp_ctx_get_option.argtypes = [vp, ct.c_int, vp]
     assert L.harp_ctx_get_option(None, 1, None) == -1
+    L.harp_wait_check.argtypes = [vp, ct.c_int, vp]
+    assert L.harp_wait_check(None, 0, None) == -1
