@@ -206,6 +206,7 @@ def main():
 
     from paper_1702_03781_gb300 import synth
     from paper_1702_03781_gb300 import harp as H
+    from paper_1702_03781_gb300 import replicas
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -239,8 +240,7 @@ def main():
 
     def barrier():
         torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     def timed(fn, steps):
@@ -324,19 +324,13 @@ def main():
         ms_e2e = timed(step_e2e, args.steps)
         barrier()
 
+    # one frequency per rank and step: the whole job's time per frequency is
+    # the slowest rank's step time over the ranks' frequencies
     t_mixed = statistics.mean(ms_mixed)
-    t_max = t_mixed
-    if ws > 1:
-        tt = torch.tensor([t_mixed], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = t_max / ws  # whole-job ms per frequency (ws frequencies per step)
-
-    e2e_max = statistics.mean(ms_e2e)
-    if ws > 1:
-        tt = torch.tensor([e2e_max], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_max = float(tt.item())
+    t_max = replicas.max_over_ranks(t_mixed, dev)
+    value = replicas.ms_per_unit(t_max, ws)
+    e2e_max = replicas.max_over_ranks(statistics.mean(ms_e2e), dev)
+    e2e_med = replicas.max_over_ranks(statistics.median(ms_e2e), dev)
 
     if rank == 0:
         peaks = _peaks()
@@ -358,9 +352,9 @@ def main():
             "refinement": {"iters": info.get("iters"), "backward_error": info.get("resid")},
             "gpu_launches": int(L1 - L0),
             "clocks": clk.summary(),
-            "e2e": {"value": round(e2e_max / ws, 4), "unit": "ms", "h2d_bytes_per_step": int(bi),
-                    "d2h_bytes_per_step": int(bo),
-                    "median_ms": round(statistics.median(ms_e2e) / ws, 4),
+            "e2e": {"value": round(replicas.ms_per_unit(e2e_max, ws), 4), "unit": "ms",
+                    "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+                    "median_ms": round(replicas.ms_per_unit(e2e_med, ws), 4),
                     "steps_ms": [round(m, 3) for m in ms_e2e]},
             "roofline": roof,
             "roofline_kernels": roof_all,
