@@ -34,6 +34,16 @@ MUTATIONS = {
     "grad_alpha_sign": ("const cplx zx = a * (dx / r) + b * (-dy / (r * r));",
                         "const cplx zx = a * (dx / r) + b * (dy / (r * r));"),
     "grad_dr_power": ("(double)q * pow(d, (double)(q - 1)) * dd_dr", "(double)q * pow(d, (double)q) * dd_dr"),
+    "self_block_transposed": ("Zblk[T + (size_t)S * ldz] = sb[T + (size_t)S * Nm];",
+                              "Zblk[T + (size_t)S * ldz] = sb[S + (size_t)T * Nm];"),
+    "grad_partner_sign": ("      grad[2 * n] -= gx;\n      grad[2 * n + 1] -= gy;",
+                          "      grad[2 * n] += gx;\n      grad[2 * n + 1] += gy;"),
+    "objective_not_modulus": ("J += creal(v) * creal(v) + cimag(v) * cimag(v);",
+                              "J += creal(v) * creal(v) - cimag(v) * cimag(v);"),
+    "transpose_solve_conjugated": ("for (int i = 0; i < k; ++i) s -= A[i + (size_t)k * lda] * b[i];",
+                                   "for (int i = 0; i < k; ++i) s -= conj(A[i + (size_t)k * lda]) * b[i];"),
+    "adjoint_contraction_transposed": ("G += Lam[i + (size_t)c * ld] * X[j + (size_t)c * ld];",
+                                       "G += Lam[j + (size_t)c * ld] * X[i + (size_t)c * ld];"),
 }
 
 
