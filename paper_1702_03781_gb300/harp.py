@@ -116,7 +116,14 @@ def _stream(stream) -> ct.c_void_p:
 
 
 def _ptr(t: torch.Tensor | None) -> ct.c_void_p:
-    return ct.c_void_p(t.data_ptr() if t is not None else 0)
+    """Device address of a CUDA tensor (NULL for None). Every tensor argument
+    of the ABI is device memory; a host tensor is refused here, never handed
+    to a kernel."""
+    if t is None:
+        return ct.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError(f"expected a CUDA tensor (device memory), got one on {t.device}")
+    return ct.c_void_p(t.data_ptr())
 
 
 def colmajor_empty(rows: int, cols: int, dtype, device) -> torch.Tensor:
@@ -337,9 +344,9 @@ def solve_batch(contexts, items, prec="mixed", tol: float = 0.0, max_iter: int =
     library's batch scheduler: one worker thread and stream per context."""
     arr = (HarpProblem * len(items))()
     for k, it in enumerate(items):
-        arr[k] = HarpProblem(it.Na, it.Nm, it.P, it.Q, it.pos.data_ptr(), it.freq_hz,
-                             it.coef.data_ptr(), it.sb.data_ptr(), it.stride, it.X.data_ptr(),
-                             _ld(it.X), 0, 0, 0.0)
+        arr[k] = HarpProblem(it.Na, it.Nm, it.P, it.Q, _ptr(it.pos).value, it.freq_hz,
+                             _ptr(it.coef).value, _ptr(it.sb).value, it.stride,
+                             _ptr(it.X).value, _ld(it.X), 0, 0, 0.0)
     hs = (ct.c_void_p * len(contexts))(*[c.handle.value for c in contexts])
     torch.cuda.synchronize()  # inputs prepared on torch's stream are ready
     st = lib().harp_solve_batch(hs, len(contexts), arr, len(items), _prec(prec), float(tol),

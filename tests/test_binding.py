@@ -1,0 +1,89 @@
+"""The Python binding is marshalling only: no CPU fallback, no host pointers
+handed to kernels, no dependence on the oracle, and the column-major layout
+the C ABI expects. Runs without a GPU."""
+import ctypes as ct
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1702_03781_gb300 import harp as H
+from paper_1702_03781_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_1702_03781_gb300")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1702_03781_gb300 import build
+    return build.build()
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    monkeypatch.setattr(H, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(H, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        H.lib()
+
+
+def test_host_tensors_are_refused():
+    assert H._ptr(None).value is None
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        H._ptr(torch.zeros(4, dtype=torch.float64))
+
+
+def test_fill_and_solve_refuse_host_tensors_before_any_library_call(built):
+    # a context object that never reached the library: the refusal must come
+    # from the binding, before a pointer crosses the ABI
+    h = object.__new__(H.Harp)
+    h._h, h.device, h.max_N, h.max_nrhs = ct.c_void_p(0), 0, 64, 16
+    p = synth.tiny()
+    pos, coef, sb = (torch.from_numpy(p.pos), torch.from_numpy(p.coef),
+                     torch.from_numpy(p.self_blocks))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        h.fill(pos, p.freq_hz, coef, sb, prec="fp64")
+    Z = torch.zeros((p.N, p.N), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        h.solve(Z, None, nrhs=p.Na, prec="fp64", out=H.colmajor_empty(p.N, p.Na,
+                                                                        torch.complex128, "cpu"))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        H.port_objective(torch.zeros((p.N, p.Na), dtype=torch.complex128), p.Na, p.Nm)
+
+
+def test_colmajor_layout():
+    Z = H.colmajor_empty(5, 3, torch.complex64, "cpu")
+    assert Z.shape == (5, 3) and Z.stride() == (1, 5)
+    assert H._ld(Z) == 5
+    assert H.as_colmajor(Z) is Z
+    R = torch.arange(15, dtype=torch.float64).reshape(5, 3)  # row-major
+    C = H.as_colmajor(R)
+    assert C.stride() == (1, 5)
+    assert torch.equal(C, R)
+    # a column-major view with padding keeps its leading dimension
+    big = H.colmajor_empty(8, 3, torch.float64, "cpu")
+    view = big[:5, :]
+    assert H.as_colmajor(view) is view and H._ld(view) == 8
+
+
+def test_package_never_imports_the_oracle():
+    for dirpath, _, files in os.walk(PKG):
+        for f in files:
+            if f.endswith(".py"):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+    code = ("import sys; import paper_1702_03781_gb300.harp, paper_1702_03781_gb300.synthesis, "
+            "paper_1702_03781_gb300.replicas, paper_1702_03781_gb300.roofline; "
+            "assert 'oracle' not in sys.modules, 'oracle imported'")
+    subprocess.check_call([sys.executable, "-c", code], cwd=ROOT)
+
+
+def test_library_sources_do_not_reference_the_oracle():
+    csrc = os.path.join(PKG, "csrc")
+    for f in os.listdir(csrc):
+        src = open(os.path.join(csrc, f), errors="replace").read()
+        assert "oracle" not in src.lower(), f
