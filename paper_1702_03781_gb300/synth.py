@@ -204,6 +204,17 @@ def large(layout: int = 0) -> Problem:
     return make_problem("large-1024x16", 1024, 38.0, 1.5, F110, 16, 8, 5, cfg=5, layout=layout)
 
 
+def physical(p: Problem) -> Problem:
+    """The same problem with c_{p0} = 0 for every harmonic p and MBF pair:
+    without the distance-independent q = 0 part of Eq. 3, every coupling
+    block decays at least as d = 1/r."""
+    coef = p.coef.copy()
+    coef[..., 0] = 0.0
+    return Problem(p.name + "-physical", p.pos, p.freq_hz, p.Nm, p.P, p.Q,
+                   np.ascontiguousarray(coef), p.self_blocks, p.V,
+                   meta=dict(p.meta, physical=True))
+
+
 def small(Na: int, Nm: int, P: int = 3, Q: int = 2, seed_cfg: int = 9,
           layout: int = 0, freq_hz: float = F110, min_sep: float = 1.5) -> Problem:
     """A small random problem of any shape, in a disc sized for ~40% cover."""

@@ -44,7 +44,8 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("mk", [lambda: synth.tiny(), lambda: synth.small(37, 5, P=3, Q=2),
-                                lambda: synth.small(70, 3, P=2, Q=4, seed_cfg=21)])
+                                lambda: synth.small(70, 3, P=2, Q=4, seed_cfg=21),
+                                lambda: synth.physical(synth.small(37, 5, P=3, Q=2))])
 def test_fill_fp64_matches_oracle(harp, mk):
     p = mk()
     pos, coef, sb = _dev(p)
@@ -114,7 +115,8 @@ def test_solve_fp64_matches_oracle(harp, mk):
     assert _rel(_np(X), Xo) <= 1e-10
 
 
-@pytest.mark.parametrize("mk", [lambda: synth.tiny(), lambda: synth.small(37, 5, P=3, Q=2)])
+@pytest.mark.parametrize("mk", [lambda: synth.tiny(), lambda: synth.small(37, 5, P=3, Q=2),
+                                lambda: synth.physical(synth.small(37, 5, P=3, Q=2))])
 def test_solve_mixed_refined_matches_oracle(harp, mk):
     p = mk()
     pos, coef, sb = _dev(p)

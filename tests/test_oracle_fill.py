@@ -236,3 +236,27 @@ def test_layout_generator_respects_disc_and_separation():
     d[np.arange(256), np.arange(256)] = np.inf
     assert d.min() >= 1.5
     assert np.array_equal(pos, synth.disc_layout(256, 19.0, 1.5, 2000))
+
+
+def test_physical_set_removes_exactly_the_q0_part():
+    """The fill is linear in c, so Z(c) - Z(c with c_p0 = 0) is the q = 0
+    part alone: e^{-jkr} sum_p c_p0 e^{j p alpha} (Eq. 3, 4) in every mutual
+    block, zero in the self blocks. Without it each mutual entry is bounded
+    by sum_{p, q >= 1} |c_pq| d^q, which decays with distance."""
+    p = synth.small(12, 3, P=2, Q=3)
+    ph = synth.physical(p)
+    assert np.all(ph.coef[..., 0] == 0) and np.array_equal(ph.coef[..., 1:], p.coef[..., 1:])
+    assert ph.pos is p.pos and ph.self_blocks is p.self_blocks
+    Z = _blocks(oracle.fill(p.pos, F, p.coef, p.self_blocks), p.Na, p.Nm)
+    Zp = _blocks(oracle.fill(ph.pos, F, ph.coef, ph.self_blocks), p.Na, p.Nm)
+    harm = np.arange(-p.P, p.P + 1)
+    for m, n in _pairs(p.Na):
+        dx, dy = p.pos[m] - p.pos[n]
+        r, alpha = math.hypot(dx, dy), math.atan2(dy, dx)
+        q0 = np.exp(-1j * K * r) * np.einsum("tsp,p->ts", p.coef[..., 0],
+                                              np.exp(1j * harm * alpha))
+        np.testing.assert_allclose(Z[m, n] - Zp[m, n], q0, rtol=0, atol=1e-13 * np.abs(q0).max())
+        bound = np.einsum("tspq,q->ts", np.abs(p.coef[..., 1:]), r ** -np.arange(1.0, p.Q + 1))
+        assert np.all(np.abs(Zp[m, n]) <= bound * (1 + 1e-12))
+    for a in range(p.Na):
+        assert np.array_equal(Zp[a, a], p.self_blocks[a])
