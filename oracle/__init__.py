@@ -153,6 +153,38 @@ def port_objective_grad(pos, freq_hz, coef, self_blocks, dvar: int = 1, want_gra
     return J.value, g
 
 
+def port_impedance_objective_grad(pos, freq_hz, coef, self_blocks, dvar: int = 1,
+                                  want_grad: bool = True):
+    """(J, grad (Na, 2) or None) for the impedance reading of the synthesis
+    objective (Section V): J = sum_mn |(P^{-1})_mn|^2, where P = E^T Z^{-1} E
+    is the port response and E selects MBF 0 of every antenna.
+
+    Forward, step by step: X = Z^{-1} E and Y = P^{-1}, both with this
+    oracle's LU.
+
+    Adjoint: dY = -Y dP Y gives dJ = 2 Re tr(G^H dP) with G = -Y^H Y Y^H.
+    Since dP = -E^T Z^{-1} dZ X, the adjoint is Lambda = Z^{-T} E conj(G), and
+    the gradient is the same contraction as for the admittance reading, with
+    E conj(G) in place of E conj(P)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    Na, Nm = pos.shape[0], np.shape(coef)[0]
+    Z = fill(pos, freq_hz, coef, self_blocks, dvar=dvar)
+    A, ipiv, info = lu(Z)
+    if info:
+        raise np.linalg.LinAlgError(f"oracle_lu: zero pivot at column {info - 1}")
+    E = np.zeros((Na * Nm, Na), dtype=np.complex128)
+    E[np.arange(Na) * Nm, np.arange(Na)] = 1.0
+    X = lu_solve(A, ipiv, E)
+    P = E.T @ X
+    Y = solve(P, np.eye(Na, dtype=np.complex128))
+    J = float(np.sum(np.abs(Y) ** 2))
+    if not want_grad:
+        return J, None
+    G = -(Y.conj().T @ Y @ Y.conj().T)
+    Lam = lu_solve(A, ipiv, E @ np.conj(G), trans="T")
+    return J, grad_from_adjoint(pos, freq_hz, coef, Lam, X, dvar=dvar)
+
+
 def relerr(a, b) -> float:
     """Frobenius relative error ||a - b|| / ||b||."""
     a = np.asarray(a)

@@ -106,3 +106,43 @@ def test_adjoint_pieces_agree_with_direct_formula():
                   - oracle.fill(q2, p.freq_hz, p.coef, p.self_blocks)) / (2 * h)
             expect = -2 * np.real(np.sum(G * dZ))
             assert g[i, c] == pytest.approx(expect, rel=1e-6, abs=1e-8)
+
+
+def _Jimp(p, pos=None):
+    J, _ = oracle.port_impedance_objective_grad(p.pos if pos is None else pos, p.freq_hz,
+                                                p.coef, p.self_blocks, want_grad=False)
+    return J
+
+
+def test_impedance_objective_matches_library_inverse():
+    """The impedance reading J = sum |(E^T Z^{-1} E)^{-1}|^2, against numpy's
+    LAPACK solve and inverse on the oracle's Z."""
+    p = _problem()
+    J, _ = oracle.port_impedance_objective_grad(p.pos, p.freq_hz, p.coef, p.self_blocks,
+                                                want_grad=False)
+    Z = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
+    Zp = np.linalg.inv(p.V.T @ np.linalg.solve(Z, p.V))
+    assert J == pytest.approx(np.sum(np.abs(Zp) ** 2), rel=1e-11)
+
+
+def test_impedance_gradient_matches_richardson_finite_differences():
+    p = _problem()
+    _, g = oracle.port_impedance_objective_grad(p.pos, p.freq_hz, p.coef, p.self_blocks)
+    h = 1e-4
+    gfd = np.zeros_like(g)
+    for i in range(p.Na):
+        for c in range(2):
+            def jd(s):
+                q = p.pos.copy()
+                q[i, c] += s
+                return _Jimp(p, pos=q)
+            d1 = (jd(h) - jd(-h)) / (2 * h)
+            d2 = (jd(h / 2) - jd(-h / 2)) / h
+            gfd[i, c] = (4 * d2 - d1) / 3
+    assert np.linalg.norm(g - gfd) / np.linalg.norm(gfd) < 1e-7
+
+
+def test_impedance_gradient_translation_invariance():
+    p = synth.small(12, 2, P=3, Q=2, seed_cfg=13)
+    _, g = oracle.port_impedance_objective_grad(p.pos, p.freq_hz, p.coef, p.self_blocks)
+    assert np.all(np.abs(g.sum(axis=0)) < 1e-11 * np.abs(g).sum())
