@@ -91,7 +91,10 @@ unsigned long long harp_kernel_launches(void);
  * the reduced matrix used by the refinement, the LU factors and pivots of
  * the last factorisation, solve buffers, and a stream and c64 matrix buffer
  * for harp_solve_batch. Returns HARP_E_NOMEM when the allocation fails. One
- * context serves one stream at a time. */
+ * context serves one stream at a time. A process may hold several contexts,
+ * all on one device: the library's one-time setup (kernel shared-memory
+ * attributes, the SM count behind its split-K choice) is made for the first
+ * device it runs on. Use one process per GPU. */
 int harp_ctx_create(harp_ctx** ctx, int device, int max_N, int max_nrhs);
 
 /* Release the context and its workspace (synchronises the device). */
