@@ -87,3 +87,41 @@ def test_library_sources_do_not_reference_the_oracle():
     for f in os.listdir(csrc):
         src = open(os.path.join(csrc, f), errors="replace").read()
         assert "oracle" not in src.lower(), f
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor: only the two members the marshalling reads."""
+    is_cuda = True
+
+    def __init__(self, addr):
+        self.addr = addr
+
+    def data_ptr(self):
+        return self.addr
+
+
+def test_batch_descriptor_carries_the_device_addresses():
+    addrs = [0x7F0000001000, 0x7F0000002000, 0x7F0000003000, 0x7F0000004000]
+    pos, coef, sb, X = (_FakeCudaTensor(a) for a in addrs)
+    pr = H.HarpProblem(4, 2, 1, 1, H._ptr(pos).value, 1e8, H._ptr(coef).value,
+                       H._ptr(sb).value, 4, H._ptr(X).value, 8, 0, 0, 0.0)
+    assert (pr.pos, pr.coef, pr.self_blocks, pr.X) == tuple(addrs)
+    assert (pr.Na, pr.Nm, pr.P, pr.Q, pr.self_stride, pr.ldx) == (4, 2, 1, 1, 4, 8)
+
+
+def test_batch_descriptor_matches_the_c_layout(tmp_path):
+    """The ctypes mirror of harp_problem has the C compiler's field offsets
+    and size (gcc on the header itself)."""
+    names = [n for n, _ in H.HarpProblem._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "harp_gb300.h"\n'
+        "int main(void) {\n"
+        + "".join(f'  printf("%zu\\n", offsetof(harp_problem, {n}));\n' for n in names)
+        + '  printf("%zu\\n", sizeof(harp_problem));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(prog),
+                           "-o", str(exe)])
+    c = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
+    py = [getattr(H.HarpProblem, n).offset for n in names] + [ct.sizeof(H.HarpProblem)]
+    assert py == c, dict(zip(names + ["sizeof"], zip(py, c)))
