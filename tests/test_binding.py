@@ -125,3 +125,55 @@ def test_batch_descriptor_matches_the_c_layout(tmp_path):
     c = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
     py = [getattr(H.HarpProblem, n).offset for n in names] + [ct.sizeof(H.HarpProblem)]
     assert py == c, dict(zip(names + ["sizeof"], zip(py, c)))
+
+
+def _header_prototypes():
+    src = open(os.path.join(ROOT, "include", "harp_gb300.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(\w+)\s*\(([^;{}]*?)\)\s*;", src, flags=re.S):
+        ret, name, params = " ".join(m.group(1).split()), m.group(2), " ".join(m.group(3).split())
+        if name in ("if", "while") or ret.startswith("typedef"):
+            continue
+        args = [] if params in ("", "void") else [a.strip() for a in params.split(",")]
+        protos[name] = (ret, args)
+    return protos
+
+
+def _kind_of_c(decl: str) -> str:
+    if "*" in decl:
+        return "ptr"
+    toks = decl.replace("const", "").split()
+    base = " ".join(toks[:-1]) if len(toks) > 1 else toks[0]
+    return {"int": "int", "long": "long", "double": "double", "char": "char",
+            "unsigned": "uint", "size_t": "size_t", "harp_prec": "int"}[base]
+
+
+def _kind_of_ctype(t) -> str:
+    if t in (ct.c_void_p, ct.c_char_p) or (isinstance(t, type) and issubclass(t, ct._Pointer)):
+        return "ptr"
+    for k, v in (("int", ct.c_int), ("long", ct.c_long), ("double", ct.c_double),
+                 ("char", ct.c_char), ("uint", ct.c_uint), ("size_t", ct.c_size_t)):
+        if t is v:
+            return k
+    raise AssertionError(f"unmapped ctypes type {t}")
+
+
+def test_binding_signatures_match_the_header(built):
+    protos = _header_prototypes()
+    L = H.lib()
+    checked = 0
+    for name, (ret, args) in protos.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            assert not args, f"{name}: the binding sets no argtypes for {len(args)} arguments"
+            continue
+        want = [_kind_of_c(a) for a in args]
+        got = [_kind_of_ctype(t) for t in fn.argtypes]
+        assert got == want, f"{name}: binding {got} vs header {want}"
+        checked += 1
+    assert checked >= 15
+    # non-int results
+    assert L.harp_status_string.restype is ct.c_char_p
+    assert L.harp_kernel_launches.restype is ct.c_ulonglong
