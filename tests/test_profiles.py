@@ -40,3 +40,16 @@ def test_profile_commands_run_committed_files_and_keep_clocks():
                     n_ncu += 1
                     assert "--clock-control none" in line, (f, line)
     assert n_ncu >= 4
+
+
+def test_no_committed_code_uses_scratch_files():
+    """Scratch work (probes, sweeps, notes) lives in an ignored folder that no
+    committed file imports, reads or runs."""
+    scratch = "_" + "work"
+    for f in _tracked():
+        if f.endswith(".md") or f == ".gitignore" or not os.path.isfile(os.path.join(ROOT, f)):
+            continue
+        if f == "tests/test_profiles.py":
+            continue
+        text = open(os.path.join(ROOT, f), errors="replace").read()
+        assert scratch not in text, f
