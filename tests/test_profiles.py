@@ -45,11 +45,12 @@ def test_profile_commands_run_committed_files_and_keep_clocks():
 def test_no_committed_code_uses_scratch_files():
     """Scratch work (probes, sweeps, notes) lives in an ignored folder that no
     committed file imports, reads or runs."""
-    scratch = "_" + "work"
+    # the folder name on its own (not inside identifiers such as a workspace)
+    scratch = re.compile(r"(?<![\w])_" + r"work\b")
     for f in _tracked():
         if f.endswith(".md") or f == ".gitignore" or not os.path.isfile(os.path.join(ROOT, f)):
             continue
         if f == "tests/test_profiles.py":
             continue
         text = open(os.path.join(ROOT, f), errors="replace").read()
-        assert scratch not in text, f
+        assert not scratch.search(text), f
