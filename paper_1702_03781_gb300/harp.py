@@ -138,6 +138,17 @@ def as_colmajor(x: torch.Tensor) -> torch.Tensor:
     return x.T.contiguous().T
 
 
+def _check_out(out: torch.Tensor, rows: int, cols: int, dtype) -> torch.Tensor:
+    """A caller-given output: rows x cols of `dtype`, column-major with a
+    leading dimension >= rows (the layout the library writes)."""
+    if tuple(out.shape) != (rows, cols) or out.dtype != dtype:
+        raise ValueError(f"out must be {rows} x {cols} {dtype}, got {tuple(out.shape)} {out.dtype}")
+    if out.stride(0) != 1 or out.stride(1) < max(1, rows):
+        raise ValueError(f"out must be column-major (strides (1, ld >= {rows})), "
+                         f"got strides {tuple(out.stride())}")
+    return out
+
+
 def _ld(x: torch.Tensor) -> int:
     return max(int(x.stride(1)), int(x.shape[0]), 1)
 
@@ -216,7 +227,7 @@ class Harp:
             sb = self_blocks.to(torch.complex128).transpose(1, 2).contiguous()
             stride = Nm * Nm
         dt = torch.complex128 if pr == FP64 else torch.complex64
-        Z = colmajor_empty(N, N, dt, pos.device) if out is None else out
+        Z = colmajor_empty(N, N, dt, pos.device) if out is None else _check_out(out, N, N, dt)
         _check("harp_fill", lib().harp_fill(self._h, Na, Nm, P, Q, _ptr(pos), float(freq_hz),
                                             _ptr(coef), _ptr(sb), stride, _ptr(Z), _ld(Z), pr,
                                             _stream(stream)))
@@ -242,7 +253,8 @@ class Harp:
         if nrhs is None:
             raise ValueError("nrhs is required when V is None")
         dev = Z.device if Z is not None else V.device
-        X = colmajor_empty(N, nrhs, torch.complex128, dev) if out is None else out
+        X = (colmajor_empty(N, nrhs, torch.complex128, dev) if out is None
+             else _check_out(out, N, nrhs, torch.complex128))
         it, res = ct.c_int(0), ct.c_double(0.0)
         st = lib().mbf_solve(self._h, N, _ptr(Z), _ld(Z) if Z is not None else N, _ptr(V),
                              _ld(V) if V is not None else N, nrhs, _ptr(X), _ld(X),

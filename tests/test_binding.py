@@ -177,3 +177,25 @@ def test_binding_signatures_match_the_header(built):
     # non-int results
     assert L.harp_status_string.restype is ct.c_char_p
     assert L.harp_kernel_launches.restype is ct.c_ulonglong
+
+
+def test_outputs_must_have_the_layout_the_library_writes():
+    h = object.__new__(H.Harp)
+    h._h, h.device, h.max_N, h.max_nrhs = ct.c_void_p(0), 0, 64, 16
+    p = synth.tiny()
+    pos, coef, sb = (torch.from_numpy(p.pos), torch.from_numpy(p.coef),
+                     torch.from_numpy(p.self_blocks))
+    # row-major, wrong dtype, wrong shape: refused before anything else
+    for bad in (torch.empty((p.N, p.N), dtype=torch.complex64),
+                H.colmajor_empty(p.N, p.N, torch.complex128, "cpu"),
+                H.colmajor_empty(p.N, p.N - 1, torch.complex64, "cpu")):
+        with pytest.raises(ValueError, match="out must be"):
+            h.fill(pos, p.freq_hz, coef, sb, prec="mixed", out=bad)
+    Z = H.colmajor_empty(p.N, p.N, torch.complex128, "cpu")
+    with pytest.raises(ValueError, match="out must be"):
+        h.solve(Z, None, nrhs=p.Na, prec="fp64", out=torch.empty((p.N, p.Na), dtype=torch.complex128))
+    # a padded column-major view is accepted (the host-tensor refusal comes next)
+    big = H.colmajor_empty(p.N + 8, p.Na, torch.complex128, "cpu")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        h.solve(Z, None, nrhs=p.Na, prec="fp64", out=big[:p.N, :])
+    assert H._check_out(big[:p.N, :], p.N, p.Na, torch.complex128) is not None
