@@ -241,6 +241,10 @@ class Harp:
         V = None solves for the port excitations (nrhs ports)."""
         pr = _prec(prec)
         if Z is not None:
+            # the library reads c128 for FP64 and c64 for the other modes
+            want = torch.complex128 if pr == FP64 else torch.complex64
+            if Z.dtype != want:
+                raise ValueError(f"Z must be {want} for prec={prec!r}, got {Z.dtype}")
             Z = as_colmajor(Z)
             N = Z.shape[0]
         elif V is not None:

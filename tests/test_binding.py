@@ -199,3 +199,17 @@ def test_outputs_must_have_the_layout_the_library_writes():
     with pytest.raises(ValueError, match="CUDA tensor"):
         h.solve(Z, None, nrhs=p.Na, prec="fp64", out=big[:p.N, :])
     assert H._check_out(big[:p.N, :], p.N, p.Na, torch.complex128) is not None
+
+
+def test_solve_refuses_a_matrix_of_the_wrong_precision():
+    h = object.__new__(H.Harp)
+    h._h, h.device, h.max_N, h.max_nrhs = ct.c_void_p(0), 0, 64, 16
+    Z128 = H.colmajor_empty(8, 8, torch.complex128, "cpu")
+    Z64 = H.colmajor_empty(8, 8, torch.complex64, "cpu")
+    with pytest.raises(ValueError, match="complex64"):
+        h.solve(Z128, None, nrhs=2, prec="mixed")
+    with pytest.raises(ValueError, match="complex128"):
+        h.solve(Z64, None, nrhs=2, prec="fp64")
+    # the matching precision reaches the pointer marshalling (host tensors refused there)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        h.solve(Z64, None, nrhs=2, prec="mixed")
