@@ -138,6 +138,34 @@ def as_colmajor(x: torch.Tensor) -> torch.Tensor:
     return x.T.contiguous().T
 
 
+def _model_shape(pos: torch.Tensor, coef: torch.Tensor) -> tuple[int, int, int, int]:
+    """(Na, Nm, P, Q) of positions (Na, 2) and a coefficient table
+    (Nm, Nm, 2P+1, Q+1); anything else is refused before the library reads
+    past a buffer."""
+    if pos.dim() != 2 or pos.shape[1] != 2 or pos.shape[0] < 1:
+        raise ValueError(f"pos must be (Na, 2) with Na >= 1, got {tuple(pos.shape)}")
+    if coef.dim() != 4 or coef.shape[0] != coef.shape[1] or coef.shape[0] < 1 \
+            or coef.shape[2] % 2 != 1 or coef.shape[3] < 1:
+        raise ValueError(f"coef must be (Nm, Nm, 2P+1, Q+1), got {tuple(coef.shape)}")
+    return pos.shape[0], coef.shape[0], (coef.shape[2] - 1) // 2, coef.shape[3] - 1
+
+
+def _self_layout(self_blocks: torch.Tensor, Na: int, Nm: int) -> tuple[torch.Tensor, int]:
+    """Self blocks in ABI layout (column-major per antenna) and their stride:
+    (Na, Nm, Nm) [antenna, T, S], or one shared (Nm, Nm) block (stride 0)."""
+    if tuple(self_blocks.shape) == (Nm, Nm):
+        return self_blocks.to(torch.complex128).T.contiguous(), 0
+    if tuple(self_blocks.shape) == (Na, Nm, Nm):
+        return self_blocks.to(torch.complex128).transpose(1, 2).contiguous(), Nm * Nm
+    raise ValueError(f"self_blocks must be ({Na}, {Nm}, {Nm}) or ({Nm}, {Nm}), "
+                     f"got {tuple(self_blocks.shape)}")
+
+
+def _expect_shape(name: str, t: torch.Tensor, shape: tuple) -> None:
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be {tuple(shape)}, got {tuple(t.shape)}")
+
+
 def _check_out(out: torch.Tensor, rows: int, cols: int, dtype) -> torch.Tensor:
     """A caller-given output: rows x cols of `dtype`, column-major with a
     leading dimension >= rows (the layout the library writes)."""
@@ -213,19 +241,11 @@ class Harp:
         column-major N x N. self_blocks: (Na, Nm, Nm) [antenna, T, S] or one
         shared (Nm, Nm) block."""
         pr = _prec(prec)
+        Na, Nm, P, Q = _model_shape(pos, coef)
         pos = pos.to(torch.float64).contiguous()
         coef = coef.to(torch.complex128).contiguous()
-        Nm = coef.shape[0]
-        P = (coef.shape[2] - 1) // 2
-        Q = coef.shape[3] - 1
-        Na = pos.shape[0]
         N = Na * Nm
-        if self_blocks.dim() == 2:
-            sb = self_blocks.to(torch.complex128).T.contiguous()
-            stride = 0
-        else:
-            sb = self_blocks.to(torch.complex128).transpose(1, 2).contiguous()
-            stride = Nm * Nm
+        sb, stride = _self_layout(self_blocks, Na, Nm)
         dt = torch.complex128 if pr == FP64 else torch.complex64
         Z = colmajor_empty(N, N, dt, pos.device) if out is None else _check_out(out, N, N, dt)
         _check("harp_fill", lib().harp_fill(self._h, Na, Nm, P, Q, _ptr(pos), float(freq_hz),
@@ -245,6 +265,8 @@ class Harp:
             want = torch.complex128 if pr == FP64 else torch.complex64
             if Z.dtype != want:
                 raise ValueError(f"Z must be {want} for prec={prec!r}, got {Z.dtype}")
+            if Z.dim() != 2 or Z.shape[0] != Z.shape[1]:
+                raise ValueError(f"Z must be square, got {tuple(Z.shape)}")
             Z = as_colmajor(Z)
             N = Z.shape[0]
         elif V is not None:
@@ -252,6 +274,8 @@ class Harp:
         else:
             raise ValueError("need Z or V to know N")
         if V is not None:
+            if V.dim() != 2 or V.shape[0] != N:
+                raise ValueError(f"V must be ({N}, nrhs), got {tuple(V.shape)}")
             V = as_colmajor(V.to(torch.complex128))
             nrhs = V.shape[1]
         if nrhs is None:
@@ -283,10 +307,14 @@ class Harp:
     def residual(self, Z: torch.Tensor, X: torch.Tensor, V: torch.Tensor, trans: str = "N",
                  stream=None) -> torch.Tensor:
         """R = V - op(Z) X (complex128) for FP64 Z, FP32 X (complex64), FP64 V."""
+        if X.dim() != 2:
+            raise ValueError(f"X must be (N, nrhs), got {tuple(X.shape)}")
+        N, nrhs = X.shape
+        _expect_shape("Z", Z, (N, N))
+        _expect_shape("V", V, (N, nrhs))
         Z = as_colmajor(Z.to(torch.complex128))
         X = as_colmajor(X.to(torch.complex64))
         V = as_colmajor(V.to(torch.complex128))
-        N, nrhs = X.shape
         R = colmajor_empty(N, nrhs, torch.complex128, X.device)
         _check("harp_residual", lib().harp_residual(
             self._h, N, _ptr(Z), _ld(Z), _ptr(X), _ld(X), _ptr(V), _ld(V), nrhs, _ptr(R), _ld(R),
@@ -303,12 +331,12 @@ class Harp:
                      Lam: torch.Tensor, X: torch.Tensor, prec="fp64", stream=None) -> torch.Tensor:
         """grad (Na, 2) float64 of J from the adjoint Lambda and solution X."""
         pr = _prec(prec)
+        Na, Nm, P, Q = _model_shape(pos, coef)
+        if X.dim() != 2 or X.shape[0] != Na * Nm:
+            raise ValueError(f"X must be ({Na * Nm}, nrhs), got {tuple(X.shape)}")
+        _expect_shape("Lam", Lam, tuple(X.shape))
         pos = pos.to(torch.float64).contiguous()
         coef = coef.to(torch.complex128).contiguous()
-        Nm = coef.shape[0]
-        P = (coef.shape[2] - 1) // 2
-        Q = coef.shape[3] - 1
-        Na = pos.shape[0]
         Lam = as_colmajor(Lam.to(torch.complex128))
         X = as_colmajor(X.to(torch.complex128))
         if _ld(Lam) != _ld(X):
@@ -336,18 +364,11 @@ class BatchItem:
     its output X (column-major N x Na complex128)."""
 
     def __init__(self, pos, freq_hz, coef, self_blocks):
+        self.Na, self.Nm, self.P, self.Q = _model_shape(pos, coef)
         self.pos = pos.to(torch.float64).contiguous()
         self.coef = coef.to(torch.complex128).contiguous()
         self.freq_hz = float(freq_hz)
-        self.Nm = self.coef.shape[0]
-        self.P = (self.coef.shape[2] - 1) // 2
-        self.Q = self.coef.shape[3] - 1
-        self.Na = self.pos.shape[0]
-        if self_blocks.dim() == 2:
-            self.sb, self.stride = self_blocks.to(torch.complex128).T.contiguous(), 0
-        else:
-            self.sb = self_blocks.to(torch.complex128).transpose(1, 2).contiguous()
-            self.stride = self.Nm * self.Nm
+        self.sb, self.stride = _self_layout(self_blocks, self.Na, self.Nm)
         self.N = self.Na * self.Nm
         self.X = colmajor_empty(self.N, self.Na, torch.complex128, self.pos.device)
         self.status = self.iters = 0
@@ -379,6 +400,7 @@ def port_objective(X: torch.Tensor, Na: int, Nm: int, want_P: bool = True, want_
     """(P, J, W) of the port objective: P = E^T X (Na x Na), J = sum |P|^2
     (0-d float64 tensor on the device), W = E conj(P) (N x Na, the adjoint
     right-hand side). Computed by the library's kernels."""
+    _expect_shape("X", X, (Na * Nm, Na))
     X = as_colmajor(X.to(torch.complex128))
     dev = X.device
     N = Na * Nm
@@ -402,12 +424,15 @@ def fill_adjoint_noalloc(pos: torch.Tensor, freq_hz: float, coef: torch.Tensor, 
     most NOALLOC_MAX_NA antennas). `out` (Na, 2) float64 may be given so the
     call itself allocates nothing either."""
     pr = _prec(prec)
+    Na, Nm, P, Q = _model_shape(pos, coef)
+    if X.dim() != 2 or X.shape[0] != Na * Nm:
+        raise ValueError(f"X must be ({Na * Nm}, nrhs), got {tuple(X.shape)}")
+    _expect_shape("Lam", Lam, tuple(X.shape))
+    if out is not None and (tuple(out.shape) != (Na, 2) or out.dtype != torch.float64
+                            or not out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous ({Na}, 2) float64 tensor")
     pos = pos.to(torch.float64).contiguous()
     coef = coef.to(torch.complex128).contiguous()
-    Nm = coef.shape[0]
-    P = (coef.shape[2] - 1) // 2
-    Q = coef.shape[3] - 1
-    Na = pos.shape[0]
     Lam = as_colmajor(Lam.to(torch.complex128))
     X = as_colmajor(X.to(torch.complex128))
     if _ld(Lam) != _ld(X):

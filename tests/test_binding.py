@@ -213,3 +213,83 @@ def test_solve_refuses_a_matrix_of_the_wrong_precision():
     # the matching precision reaches the pointer marshalling (host tensors refused there)
     with pytest.raises(ValueError, match="CUDA tensor"):
         h.solve(Z64, None, nrhs=2, prec="mixed")
+
+
+def test_malformed_shapes_are_refused_before_the_library_reads_them():
+    """A self-block table for fewer antennas, a coefficient table of another
+    Nm, or vectors of the wrong length would make a kernel read past a
+    device buffer: the binding refuses them first."""
+    h = object.__new__(H.Harp)
+    h._h, h.device, h.max_N, h.max_nrhs = ct.c_void_p(0), 0, 64, 16
+    p = synth.tiny()
+    pos, coef, sb = (torch.from_numpy(p.pos), torch.from_numpy(p.coef),
+                     torch.from_numpy(p.self_blocks))
+    cases = [
+        (dict(self_blocks=sb[:-1]), "self_blocks must be"),
+        (dict(self_blocks=sb[:, :-1, :]), "self_blocks must be"),
+        (dict(coef=coef[:, :-1]), "coef must be"),
+        (dict(coef=coef[:, :, :-1]), "coef must be"),
+        (dict(pos=pos[:, :1]), "pos must be"),
+        (dict(pos=pos[:0]), "pos must be"),
+    ]
+    for kw, msg in cases:
+        a = dict(pos=pos, coef=coef, self_blocks=sb)
+        a.update(kw)
+        with pytest.raises(ValueError, match=msg):
+            h.fill(a["pos"], p.freq_hz, a["coef"], a["self_blocks"], prec="fp64")
+        with pytest.raises(ValueError, match=msg):
+            H.BatchItem(a["pos"], p.freq_hz, a["coef"], a["self_blocks"])
+    # one shared block and one block per antenna are both accepted
+    assert H._self_layout(sb[0], p.Na, p.Nm)[1] == 0
+    assert H._self_layout(sb, p.Na, p.Nm)[1] == p.Nm * p.Nm
+
+    X = torch.zeros((p.N, p.Na), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="X must be"):
+        H.port_objective(X[:-1], p.Na, p.Nm)
+    with pytest.raises(ValueError, match="X must be"):
+        h.fill_adjoint(pos, p.freq_hz, coef, X, X[:-1])
+    with pytest.raises(ValueError, match="Lam must be"):
+        h.fill_adjoint(pos, p.freq_hz, coef, X[:, :-1], X)
+    with pytest.raises(ValueError, match="Lam must be"):
+        H.fill_adjoint_noalloc(pos, p.freq_hz, coef, X[:, :-1], X)
+    with pytest.raises(ValueError, match="out must be"):
+        H.fill_adjoint_noalloc(pos, p.freq_hz, coef, X, X,
+                               out=torch.empty((p.Na, 3), dtype=torch.float64))
+    Z = H.colmajor_empty(p.N, p.N, torch.complex128, "cpu")
+    with pytest.raises(ValueError, match="square"):
+        h.solve(Z[:, :-1], None, nrhs=p.Na, prec="fp64")
+    with pytest.raises(ValueError, match="V must be"):
+        h.solve(Z, X[:-1], prec="fp64")
+    with pytest.raises(ValueError, match="V must be"):
+        h.residual(Z, X.to(torch.complex64), X[:, :-1])
+
+
+def test_valid_calls_pass_every_check_up_to_the_device_pointers():
+    """The shapes the tests and the bench use pass validation: with host
+    tensors the only refusal left is the device-memory one."""
+    h = object.__new__(H.Harp)
+    h._h, h.device, h.max_N, h.max_nrhs = ct.c_void_p(0), 0, 64, 16
+    p = synth.tiny()
+    pos, coef, sb = (torch.from_numpy(p.pos), torch.from_numpy(p.coef),
+                     torch.from_numpy(p.self_blocks))
+    X = H.colmajor_empty(p.N, p.Na, torch.complex128, "cpu")
+    Z64 = H.colmajor_empty(p.N, p.N, torch.complex128, "cpu")
+    Z32 = H.colmajor_empty(p.N, p.N, torch.complex64, "cpu")
+    calls = [
+        lambda: h.fill(pos, p.freq_hz, coef, sb, prec="fp64"),
+        lambda: h.fill(pos, p.freq_hz, coef, sb[0], prec="mixed"),
+        lambda: h.fill(pos, p.freq_hz, coef, sb, prec="mixed", out=Z32),
+        lambda: h.solve(Z64, None, nrhs=p.Na, prec="fp64", out=X),
+        lambda: h.solve(Z32, None, nrhs=p.Na, prec="mixed", max_iter=10),
+        lambda: h.solve(Z32, torch.zeros((p.N, 9), dtype=torch.complex128), prec="mixed"),
+        lambda: h.solve(None, torch.zeros((p.N, 9), dtype=torch.complex128), prec="fp64",
+                        trans="T"),
+        lambda: h.residual(Z64, X.to(torch.complex64), X),
+        lambda: h.fill_adjoint(pos, p.freq_hz, coef, X, X),
+        lambda: H.fill_adjoint_noalloc(pos, p.freq_hz, coef, X, X),
+        lambda: H.port_objective(X, p.Na, p.Nm),
+        lambda: H.solve_batch([], [H.BatchItem(pos, p.freq_hz, coef, sb)]),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            call()
