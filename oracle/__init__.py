@@ -63,6 +63,7 @@ def num_threads() -> int:
 
 
 def wavenumber(freq_hz: float) -> float:
+    """k = 2 pi f / c0 of the phase factor e^{-jkr} (Eq. 1, 4)."""
     return float(lib().oracle_wavenumber(freq_hz))
 
 
@@ -94,7 +95,8 @@ def fill(pos, freq_hz, coef, self_blocks, ff=None, dvar: int = 1) -> np.ndarray:
 
 
 def lu(Z: np.ndarray):
-    """(LU, ipiv, info): partial-pivot LU of a copy of Z."""
+    """(LU, ipiv, info): partial-pivot LU of a copy of Z, the direct solve of
+    the reduced system (Section II-B); textbook right-looking elimination."""
     A = np.array(Z, dtype=np.complex128, order="F", copy=True)
     N = A.shape[0]
     ipiv = np.zeros(N, dtype=np.int32)
@@ -103,6 +105,8 @@ def lu(Z: np.ndarray):
 
 
 def lu_solve(LU, ipiv, B, trans: str = "N") -> np.ndarray:
+    """X with op(Z) X = B from the factors of `lu` (forward and back
+    substitution; trans 'T' solves with Z^T for the adjoint)."""
     X = np.array(B, dtype=np.complex128, order="F", copy=True)
     if X.ndim == 1:
         X = X.reshape(-1, 1, order="F")
@@ -112,6 +116,8 @@ def lu_solve(LU, ipiv, B, trans: str = "N") -> np.ndarray:
 
 
 def solve(Z, V, trans: str = "N") -> np.ndarray:
+    """Z X = V (or Z^T X = V) for every right-hand side: the MBF coefficients
+    for each port excitation (Section II-B, II-C)."""
     A, ipiv, info = lu(Z)
     if info:
         raise np.linalg.LinAlgError(f"oracle_lu: zero pivot at column {info - 1}")
@@ -119,6 +125,8 @@ def solve(Z, V, trans: str = "N") -> np.ndarray:
 
 
 def port_objective(X, Na: int, Nm: int):
+    """(J, P): the port response P = E^T X (row m*Nm of column n, MBF 0 of
+    each antenna) and J = sum |P_mn|^2, the synthesis objective (Section V)."""
     X = np.asarray(X, dtype=np.complex128, order="F")
     Pm = np.zeros((Na, Na), dtype=np.complex128, order="F")
     J = lib().oracle_port_objective(Na, Nm, _p(X), X.shape[0], _p(Pm))
@@ -126,6 +134,9 @@ def port_objective(X, Na: int, Nm: int):
 
 
 def grad_from_adjoint(pos, freq_hz, coef, Lam, X, dvar: int = 1) -> np.ndarray:
+    """dJ/d(positions) (Na, 2) from the adjoint Lambda and the solution X:
+    -2 Re sum over pair blocks of (Lambda X^T) . dZ/dDelta, with dZ from Eq. 3, 4
+    differentiated in r and alpha."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     coef = np.ascontiguousarray(coef, dtype=np.complex128)
     Nm, _, np_, nq = coef.shape
