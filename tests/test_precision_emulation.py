@@ -1,4 +1,5 @@
-"""Why the mixed path uses three-term TF32 products: an emulation on the CPU.
+"""Why the mixed path uses three-term TF32 products, and what tournament
+pivoting would change: an emulation on the CPU.
 
 A blocked complex LU in FP32 whose trailing updates use either plain TF32
 products (both operands rounded to a 10-bit mantissa, FP32 accumulation) or
@@ -10,8 +11,10 @@ On a station-shaped system with cond(Z) * 2^-11 > 1 (N = 768, cond 1.3e4):
   1.6e-8 over 10 corrections) and miss the tolerance;
 - the three-term products behave like FP32 and converge in 3 corrections
   (3.6e-7, 1.6e-10, 4.9e-14, 2.8e-17).
-This documents the precision choice; the GPU path itself is checked against
-the oracle in the GPU tests.
+Tournament pivoting (one row block per cluster CTA, a binary tree of
+eliminations) refines in the same number of corrections as partial pivoting.
+These document design choices; the GPU path itself is checked against the
+oracle in the GPU tests.
 """
 import numpy as np
 import pytest
@@ -43,20 +46,63 @@ def _mm_3xtf32(a, b):
     return ah @ bh + (ah @ bl + al @ bh)
 
 
-def _lu(Z, mm, nb=64):
-    """Right-looking blocked LU with partial pivoting in complex64; the
+def _gepp_order(B):
+    """Pivot rows (indices into B), in order, of partial-pivot elimination on
+    a complex64 copy of B."""
+    B = np.array(B, dtype=np.complex64)
+    rows = np.arange(B.shape[0])
+    for j in range(min(B.shape)):
+        a = B[j:, j]
+        p = j + int(np.argmax(a.real * a.real + a.imag * a.imag))
+        if p != j:
+            B[[j, p]] = B[[p, j]]
+            rows[[j, p]] = rows[[p, j]]
+        if B[j, j] != 0:
+            B[j + 1:, j] /= B[j, j]
+            B[j + 1:, j + 1:] -= np.outer(B[j + 1:, j], B[j, j + 1:])
+    return rows[:min(B.shape)]
+
+
+def _tournament(panel, nblk):
+    """Tournament pivoting (TSLU): partial-pivot elimination on each of nblk
+    row blocks picks candidate rows; a binary tree of eliminations on stacked
+    candidate pairs picks the panel's pivot rows, in pivot order."""
+    blocks = [b for b in np.array_split(np.arange(panel.shape[0]), nblk) if len(b)]
+    cands = [b[_gepp_order(panel[b])] for b in blocks]
+    while len(cands) > 1:
+        nxt = []
+        for i in range(0, len(cands), 2):
+            if i + 1 == len(cands):
+                nxt.append(cands[i])
+                continue
+            idx = np.concatenate([cands[i], cands[i + 1]])
+            nxt.append(idx[_gepp_order(panel[idx])])
+        cands = nxt
+    return cands[0][:panel.shape[1]]
+
+
+def _lu(Z, mm, nb=64, tournament_blocks=0):
+    """Right-looking blocked LU in complex64 with partial pivoting, or with
+    tournament pivoting over `tournament_blocks` row blocks per panel; the
     trailing update A22 -= L21 U12 uses the product `mm`."""
     A = np.array(Z, dtype=np.complex64, order="F")
     N = A.shape[0]
     perm = np.arange(N)
     for k in range(0, N, nb):
         kb = min(nb, N - k)
+        if tournament_blocks:
+            win = _tournament(A[k:, k:k + kb], tournament_blocks)
+            rest = np.setdiff1d(np.arange(N - k), win, assume_unique=True)
+            order = np.concatenate([win, rest]) + k
+            A[k:] = A[order]
+            perm[k:] = perm[order]
         for j in range(k, k + kb):
-            a = A[j:, j]
-            p = j + int(np.argmax(a.real * a.real + a.imag * a.imag))
-            if p != j:
-                A[[j, p]] = A[[p, j]]
-                perm[[j, p]] = perm[[p, j]]
+            if not tournament_blocks:
+                a = A[j:, j]
+                p = j + int(np.argmax(a.real * a.real + a.imag * a.imag))
+                if p != j:
+                    A[[j, p]] = A[[p, j]]
+                    perm[[j, p]] = perm[[p, j]]
             A[j + 1:, j] /= A[j, j]
             A[j + 1:, j + 1:k + kb] -= np.outer(A[j + 1:, j], A[j, j + 1:k + kb])
         if k + kb < N:
@@ -122,3 +168,22 @@ def test_three_term_tf32_factors_converge(ill_conditioned):
     A, perm = _lu(Z, _mm_3xtf32)
     its, hist = _refine(Z, V, A, perm)
     assert its is not None and its <= 6, hist
+
+
+def test_tournament_pivoting_refines_like_partial_pivoting(ill_conditioned):
+    """The cluster panel's per-column barrier would go with tournament
+    pivoting (16 row blocks, one per cluster CTA). Its factors must refine as
+    well as partial pivoting's: same correction count within one, growth
+    within a small factor."""
+    Z, V = ill_conditioned
+    A_pp, p_pp = _lu(Z, _mm_3xtf32)
+    A_t, p_t = _lu(Z, _mm_3xtf32, tournament_blocks=16)
+    assert sorted(p_t) == list(range(Z.shape[0]))
+    its_pp, h_pp = _refine(Z, V, A_pp, p_pp)
+    its_t, h_t = _refine(Z, V, A_t, p_t)
+    assert its_pp is not None and its_t is not None, (h_pp, h_t)
+    assert abs(its_t - its_pp) <= 1, (h_pp, h_t)
+    amax = np.max(np.abs(Z))
+    g_pp, g_t = np.max(np.abs(np.triu(A_pp))) / amax, np.max(np.abs(np.triu(A_t))) / amax
+    assert g_t < 4 * g_pp, (g_pp, g_t)
+    assert np.max(np.abs(np.tril(A_t, -1))) < 16  # |L| stays bounded
