@@ -59,6 +59,11 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                            "-ffp-contract=off", str(mutated), "-o", str(lib), "-lm"])
     env = dict(os.environ, ORACLE_LIB=str(lib))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+    # the pin file most likely to catch this mistake first (-x stops there)
+    first = ("tests/test_oracle_grad.py" if name.startswith(("grad_", "adjoint_", "objective_"))
+             else "tests/test_oracle_solve.py" if name.startswith(("lu_", "pivot_", "transpose_"))
+             else "tests/test_oracle_fill.py")
+    pins = [first] + [f for f in PINS if f != first]
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"
