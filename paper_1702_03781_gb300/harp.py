@@ -12,7 +12,6 @@ here index naturally (Z[i, j] is row i, column j) with strides (1, ld).
 from __future__ import annotations
 
 import ctypes as ct
-import math
 import os
 
 import torch

@@ -7,7 +7,6 @@ import re
 import subprocess
 import sys
 
-import numpy as np
 import pytest
 import torch
 

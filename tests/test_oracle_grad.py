@@ -2,7 +2,6 @@
 J = sum_mn |(E^T Z^{-1} E)_mn|^2: central finite differences with
 Richardson extrapolation, translation invariance, and the rotation identity
 (rotating the layout equals rephasing the harmonics, Eq. 3)."""
-import math
 
 import numpy as np
 import pytest
