@@ -254,7 +254,7 @@ typedef struct {
  * is a worker with its own host thread and stream; problems are taken in
  * array order (put the largest first), and workers overlap on the GPU.
  *   ctxs, n_ctx       contexts (each sized for the largest problem it may
- *                     take; all on the same or different devices)  [1, 2]
+ *                     take; all on one device, see harp_ctx_create) [1, 2]
  *   probs, n_probs    problems (host array)                          [3, 4]
  *   prec              HARP_FP64 or a mixed mode                      [5]
  *   tol, max_iter     as for mbf_solve                               [6, 7]
