@@ -99,7 +99,8 @@ def harp_coefficients(Nm: int, P: int, Q: int, seed: int) -> np.ndarray:
 
 
 def self_blocks(Na: int, Nm: int, seed: int) -> np.ndarray:
-    """(Na, Nm, Nm) row-diagonally-dominant blocks [antenna, T, S]."""
+    """(Na, Nm, Nm) blocks [antenna, T, S]: CN(0, 1) entries with the real margin
+    sum_{S != T} |A_TS| + 1 added to each diagonal entry."""
     rng = np.random.default_rng(seed)
     A = complex_normal(rng, (Na, Nm, Nm))
     absrow = np.abs(A).sum(axis=2) - np.abs(np.diagonal(A, axis1=1, axis2=2))

@@ -18,3 +18,52 @@ def test_problem_shapes():
     assert p.V.shape == (3072, 256)
     t = synth.tiny()
     assert (t.Na, t.Nm, t.N, t.K) == (16, 4, 64, 36)
+
+
+def test_self_blocks_follow_the_recipe():
+    """Reading 10: A ~ CN(0, 1) from the block seed, then the real margin
+    sum_{S != T} |A_TS| + 1 added to each diagonal entry. That boosts the
+    diagonal well above its row (|A_TT| >= off-diagonal sum + 1 - |a_TT|)
+    without making every row strictly dominant."""
+    import numpy as np
+    raw = synth.complex_normal(np.random.default_rng(7), (32, 5, 5))
+    off = np.abs(raw).sum(axis=2) - np.abs(np.diagonal(raw, axis1=1, axis2=2))
+    expect = raw.copy()
+    expect[:, np.arange(5), np.arange(5)] += off + 1.0
+    sb = synth.self_blocks(32, 5, seed=7)
+    assert np.array_equal(sb, expect)
+    diag = np.abs(np.diagonal(sb, axis1=1, axis2=2))
+    rows = np.abs(sb).sum(axis=2) - diag
+    raw_diag = np.abs(np.diagonal(raw, axis1=1, axis2=2))
+    assert np.all(diag >= rows + 1.0 - raw_diag - 1e-12)
+
+
+def test_coefficients_scale_as_two_to_minus_q():
+    """c_pq ~ CN(0, 1) 2^-q (reading 3): E|c_pq|^2 = 4^-q for every power q."""
+    import numpy as np
+    c = synth.harp_coefficients(12, 8, 5, seed=3)
+    m2 = (np.abs(c) ** 2).mean(axis=(0, 1, 2))  # 12 * 12 * 17 = 2448 samples per q
+    np.testing.assert_allclose(m2 * 4.0 ** np.arange(6), 1.0, rtol=0.1)
+
+
+def test_seed_plan_is_deterministic_and_distinct():
+    """Seeds 1000 c + layout, 1000 c + 100 + i (coefficients), 1000 c + 200 + i
+    (self blocks): the same problem twice is identical; different
+    frequencies draw different coefficients on the same layout."""
+    import numpy as np
+    a, b = synth.station(), synth.station()
+    assert np.array_equal(a.pos, b.pos) and np.array_equal(a.coef, b.coef)
+    assert np.array_equal(a.self_blocks, b.self_blocks)
+    w = synth.wideband(3)
+    assert all(np.array_equal(w[0].pos, q.pos) for q in w)
+    assert not np.array_equal(w[0].self_blocks[:, :6, :6], w[1].self_blocks[:, :6, :6])
+    assert np.array_equal(w[0].pos, synth.station().pos)  # the station layout
+
+
+def test_port_rhs_selects_mbf0_of_each_antenna():
+    import numpy as np
+    V = synth.port_rhs(5, 3)
+    assert V.shape == (15, 5) and V.dtype == np.complex128
+    assert np.array_equal(np.argwhere(V == 1.0), np.array([[0, 0], [3, 1], [6, 2], [9, 3],
+                                                          [12, 4]]))
+    assert np.count_nonzero(V) == 5
