@@ -15,7 +15,7 @@ available):
 * HARP coefficients c_pq^{TS} of Eq. 3: complex normal CN(0, 1) scaled by
   2^-q (q the polynomial power), harmonic p in [-P, P], q in [0, Q];
 * self blocks (diagonal blocks of the reduced matrix): CN(0, 1) with the
-  diagonal raised to the absolute row sum plus one;
+  off-diagonal absolute row sum plus one added to each diagonal entry;
 * right-hand sides: unit voltage on MBF 0 of each antenna port (one column
   per port), the "excitation at each port" of Section II-C.
 
