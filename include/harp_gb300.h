@@ -87,10 +87,12 @@ unsigned long long harp_kernel_launches(void);
 
 /* Create a context on CUDA device `device` with workspace for systems up to
  * max_N unknowns and max_nrhs right-hand sides. The context owns its device
- * workspace (about 96 max_N^2 + 80 max_N max_nrhs bytes): the FP64 copy of
- * the reduced matrix used by the refinement, the LU factors and pivots of
- * the last factorisation, solve buffers, and a stream and c64 matrix buffer
- * for harp_solve_batch. Returns HARP_E_NOMEM when the allocation fails. One
+ * workspace, about 144 max_N^2 + 224 max_N max_nrhs bytes: the FP64 copy of
+ * the reduced matrix used by the refinement, the LU factors, pivots and
+ * factor inverses of the last factorisation, tensor-core operand planes,
+ * solve buffers, and a stream and c64 matrix buffer for harp_solve_batch.
+ * The exact-slice residual's buffers come on top when they fit (0.66 GB at
+ * max_N = 3072, max_nrhs = 256, 2.2 GB in all at that size). Returns HARP_E_NOMEM when the allocation fails. One
  * context serves one stream at a time. A process may hold several contexts,
  * all on one device: the library's one-time setup (kernel shared-memory
  * attributes, the SM count behind its split-K choice) is made for the first
