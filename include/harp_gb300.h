@@ -81,8 +81,9 @@ const char* harp_status_string(int status);
 /* Last CUDA error code seen by the library in this process (0 if none). */
 int harp_last_cuda_error(void);
 
-/* Number of CUDA kernels this library has launched in this process (host
- * counter, for instrumentation; not synchronised across threads). */
+/* Number of CUDA kernels this library has launched in this process (an
+ * atomic host counter, for instrumentation; launches from every thread and
+ * context are counted). */
 unsigned long long harp_kernel_launches(void);
 
 /* Create a context on CUDA device `device` with workspace for systems up to
