@@ -288,9 +288,14 @@ int harp_port_objective(int Na, int Nm, const double* X, int ldx, double* P, dou
  * its per-pair scratch is a fixed device array inside this library, sized
  * for at most HARP_NOALLOC_MAX_NA antennas (HARP_NOALLOC_MAX_NA^2 * 2
  * doubles, 4 MiB, held on every GPU that loads the library until the
- * process exits). Arguments 1..13 are those of harp_fill_adjoint without the
- * context; it works on the current CUDA device. Returns HARP_E_UNSUPPORTED
- * when Na > HARP_NOALLOC_MAX_NA.
+ * process exits). Its 14 arguments are arguments 2..15 of harp_fill_adjoint
+ * (everything but the context, stream included); it works on the current
+ * CUDA device, which must hold every pointer and the stream. A negative
+ * status -i names the 1-based position i of the bad argument in THIS call
+ * (one less than the same argument's position in harp_fill_adjoint, e.g.
+ * Na < 1 gives -1). Returns HARP_E_UNSUPPORTED when Na > HARP_NOALLOC_MAX_NA.
+ * While profiling is on, its pair kernel is recorded in HARP_K_ADJOINT like
+ * harp_fill_adjoint's.
  * The first call on a device looks up that device's address of the array
  * (a runtime query, with the device current); make that first call before
  * any stream capture. All calls share the one array: each call clears what

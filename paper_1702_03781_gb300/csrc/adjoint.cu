@@ -352,6 +352,8 @@ int launch_adjoint_noalloc(int device, AdjArgs a, cudaStream_t st) {
   HARP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R>,
                                                           kAdjThreads, smem));
   const int grid = std::min(a.n_items, sms * std::max(1, per_sm));
+  ProfScope ps(HARP_K_ADJOINT,
+               8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
   adjoint_pairs_kernel<R><<<grid, kAdjThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -384,7 +386,10 @@ extern "C" int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const dou
   HARP_TRY(noalloc_scratch(device, &scratch));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t used = (size_t)Na * Na * 2 * sizeof(double);
-  HARP_CUDA(cudaMemsetAsync(scratch, 0, used, st));  // pairs m == n are never written
+  // a safeguard only: the pair kernel writes every entry (m, n) with m != n
+  // and the reduction never reads m == n, so no leftover of an earlier call
+  // is read even without it
+  HARP_CUDA(cudaMemsetAsync(scratch, 0, used, st));
   AdjArgs a;
   a.Na = Na;
   a.Nm = Nm;

@@ -430,14 +430,31 @@ def fill_adjoint_noalloc(pos: torch.Tensor, freq_hz: float, coef: torch.Tensor, 
     if out is not None and (tuple(out.shape) != (Na, 2) or out.dtype != torch.float64
                             or not out.is_contiguous()):
         raise ValueError(f"out must be a contiguous ({Na}, 2) float64 tensor")
-    pos = pos.to(torch.float64).contiguous()
-    coef = coef.to(torch.complex128).contiguous()
-    Lam = as_colmajor(Lam.to(torch.complex128))
-    X = as_colmajor(X.to(torch.complex128))
-    if _ld(Lam) != _ld(X):
-        Lam, X = Lam.T.contiguous().T, X.T.contiguous().T
-    grad = torch.empty((Na, 2), dtype=torch.float64, device=pos.device) if out is None else out
-    _check("harp_fill_adjoint_noalloc", lib().harp_fill_adjoint_noalloc(
-        Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(Lam), _ptr(X), _ld(X),
-        X.shape[1], _ptr(grad), pr, _stream(stream)))
+    # The entry point has no context: it runs on the current CUDA device and
+    # takes that device's scratch array, so every tensor (and the stream) must
+    # live on one device, which is made current for the call.
+    named = {"pos": pos, "coef": coef, "Lam": Lam, "X": X}
+    if out is not None:
+        named["out"] = out
+    for name, t in named.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor (device memory), got one on {t.device}")
+    devs = {t.device for t in named.values()}
+    if len(devs) != 1:
+        raise ValueError("pos, coef, Lam, X and out must be on one CUDA device, got "
+                         + ", ".join(f"{n}: {t.device}" for n, t in named.items()))
+    dev = pos.device
+    if stream is not None and stream.device != dev:
+        raise ValueError(f"stream is on {stream.device}, the tensors on {dev}")
+    with torch.cuda.device(dev):
+        pos = pos.to(torch.float64).contiguous()
+        coef = coef.to(torch.complex128).contiguous()
+        Lam = as_colmajor(Lam.to(torch.complex128))
+        X = as_colmajor(X.to(torch.complex128))
+        if _ld(Lam) != _ld(X):
+            Lam, X = Lam.T.contiguous().T, X.T.contiguous().T
+        grad = torch.empty((Na, 2), dtype=torch.float64, device=dev) if out is None else out
+        _check("harp_fill_adjoint_noalloc", lib().harp_fill_adjoint_noalloc(
+            Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(Lam), _ptr(X), _ld(X),
+            X.shape[1], _ptr(grad), pr, _stream(stream)))
     return grad

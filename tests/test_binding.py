@@ -54,6 +54,20 @@ def test_fill_and_solve_refuse_host_tensors_before_any_library_call(built):
         H.port_objective(torch.zeros((p.N, p.Na), dtype=torch.complex128), p.Na, p.Nm)
 
 
+def test_noalloc_refuses_host_tensors_before_any_library_call(monkeypatch):
+    """The context-free adjoint runs on the current device: every tensor must
+    be device memory, checked in the binding before the library is even
+    loaded."""
+    def no_library():
+        raise AssertionError("the library was reached")
+    monkeypatch.setattr(H, "lib", no_library)
+    p = synth.tiny()
+    pos, coef = torch.from_numpy(p.pos), torch.from_numpy(p.coef)
+    X = torch.zeros((p.N, p.Na), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="pos must be a CUDA tensor"):
+        H.fill_adjoint_noalloc(pos, p.freq_hz, coef, X, X)
+
+
 def test_colmajor_layout():
     Z = H.colmajor_empty(5, 3, torch.complex64, "cpu")
     assert Z.shape == (5, 3) and Z.stride() == (1, 5)

@@ -52,9 +52,12 @@ def test_noalloc_matches_regular_entry_point_twice(prec):
     h.close()
 
 
-def test_noalloc_after_a_larger_call_clears_its_scratch():
-    """A smaller problem after a larger one must not see the larger call's
-    leftovers in the shared array."""
+def test_noalloc_after_a_larger_call_gives_the_same_result():
+    """A smaller problem after a larger one still gives the regular entry
+    point's gradient. (The pair kernel writes every entry it later reads, so
+    the larger call's leftovers in the shared array are never read; the
+    clearing at the start of each call is a safeguard this test cannot
+    observe.)"""
     from paper_1702_03781_gb300 import harp as H
     h, p, pos, coef, Lam, X = _setup("fp64")
     big = synth.small(40, 2, P=1, Q=1, seed_cfg=32)
@@ -69,6 +72,21 @@ def test_noalloc_after_a_larger_call_clears_its_scratch():
     r, o = ref.cpu().numpy(), out.cpu().numpy()
     assert np.linalg.norm(o - r) / np.linalg.norm(r) <= 1e-12
     h.close()
+
+
+def test_noalloc_refuses_tensors_on_two_devices():
+    """pos on the GPU and the output on the host: refused in the binding,
+    before a pointer reaches the device-agnostic entry point."""
+    from paper_1702_03781_gb300 import harp as H
+    p = synth.small(8, 2, P=1, Q=1, seed_cfg=33)
+    d = "cuda:0"
+    pos, coef = torch.from_numpy(p.pos).to(d), torch.from_numpy(p.coef).to(d)
+    X = torch.zeros((p.N, p.Na), dtype=torch.complex128, device=d)
+    with pytest.raises(ValueError, match="out must be a CUDA tensor"):
+        H.fill_adjoint_noalloc(pos, p.freq_hz, coef, X, X,
+                               out=torch.empty((p.Na, 2), dtype=torch.float64))
+    with pytest.raises(ValueError, match="X must be a CUDA tensor"):
+        H.fill_adjoint_noalloc(pos, p.freq_hz, coef, X, X.cpu())
 
 
 def test_noalloc_rejects_too_many_antennas():
