@@ -29,8 +29,14 @@
  *    j = n*Nm + S carries source MBF S of antenna n. alpha is the direction
  *    from source antenna n to testing antenna m, anticlockwise from +x.
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
- *    stream). Calls that must read a device result (mixed-precision
- *    refinement, status checks) synchronise that stream before returning.
+ *    stream). Calls that must read a device result (the zero-pivot check of
+ *    a factorisation, the stopping test of the mixed-precision refinement)
+ *    synchronise that stream before returning; harp_fill does not.
+ *  - Statuses found on the device by a call that does not synchronise
+ *    (coincident antennas or non-finite entries in harp_fill, non-finite
+ *    right-hand sides of an FP64 solve) stay pending in the context and
+ *    are returned by the next call that synchronises (mbf_solve) or by
+ *    harp_ctx_sync, which then clears them.
  *  - Return value: HARP_OK (0) on success; -i when argument i (1-based) is
  *    invalid (LAPACK convention); +i (1 <= i <= N) when the LU met an
  *    exactly zero pivot in column i (X is not written); or one of the
@@ -103,6 +109,16 @@ int harp_ctx_create(harp_ctx** ctx, int device, int max_N, int max_nrhs);
 /* Release the context and its workspace (synchronises the device). */
 int harp_ctx_destroy(harp_ctx* ctx);
 
+/* Wait until the work enqueued on `stream` (and the context's background
+ * Z64 fill) is done, then return the context's pending device status and
+ * clear it: HARP_E_TIMEOUT (a bounded device wait gave up), else
+ * HARP_E_COINCIDENT or HARP_E_NONFINITE left by harp_fill or by an FP64
+ * solve's right-hand-side check, else HARP_OK. This is how the statuses of
+ * calls that do not synchronise are collected (Section II's fill has no
+ * such check; the status words are this library's). Errors: -1 null ctx,
+ * HARP_E_CUDA. */
+int harp_ctx_sync(harp_ctx* ctx, void* stream);
+
 /* Device pointer and leading dimension of the context's FP64 reduced
  * matrix (c128, max_N x max_N). harp_fill writes it in the mixed modes (this
  * call first waits, on the host, until that write is complete); a caller may
@@ -131,8 +147,11 @@ int harp_ctx_z64(harp_ctx* ctx, void** z64, int* ld);
  * factorisation needs only Z). mbf_solve waits for it before its first use
  * of Z64, and harp_ctx_z64 waits for it on the host.
  * Coincident antennas (r == 0) are detected on the device: the entries of
- * that pair are written as zero and HARP_E_COINCIDENT is returned (the call
- * synchronises the stream to read the flag). */
+ * that pair are written as zero and HARP_E_COINCIDENT becomes the context's
+ * pending status. An entry that comes out NaN or infinite (non-finite
+ * positions, coefficients or self blocks) makes HARP_E_NONFINITE pending.
+ * The call does not synchronise: the next mbf_solve on this context (or
+ * harp_ctx_sync) returns the pending status, coincidence first. */
 int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
               const double* coef, const double* self_blocks, long self_stride, void* Z, int ldz,
               int prec, void* stream);
@@ -161,12 +180,17 @@ int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, do
  *                at exit (may be NULL; -1 for HARP_FP64, HARP_FP32) [15]
  * The mixed modes refine against the context's FP64 matrix (written by the
  * last mixed harp_fill, or by the caller through harp_ctx_z64) and
- * synchronise the stream once per step. The FP32 factorisation also runs
+ * synchronise the stream once per step. For trans 'N' the call reads the
+ * pending status after the factorisation: HARP_E_COINCIDENT or
+ * HARP_E_NONFINITE left by the fill, or HARP_E_NONFINITE when Z or V holds a
+ * NaN or an infinity (checked as they are copied in); X is then not
+ * written. The FP32 factorisation also runs
  * work on streams of the context (the trailing updates, and the factor
  * inverses built panel by panel beside it); that work is ordered before
  * anything the call later enqueues on `stream`. Returns +i on an exactly zero pivot
- * in column i, HARP_E_NOCONV when tol was not met (X then holds the best
- * iterate). */
+ * in column i, HARP_E_NOCONV when tol was not met within max_iter steps: X
+ * then holds the iterate with the smallest backward error seen and
+ * resid_out that error. */
 int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int ldv, int nrhs,
               double* X, int ldx, char trans, int prec, double tol, int max_iter, int* iters_out,
               double* resid_out, void* stream);

@@ -244,3 +244,21 @@ extern "C" int harp_ctx_z64(harp_ctx* c, void** z64, int* ld) {
   *ld = c->ld64;
   return HARP_OK;
 }
+
+namespace harp {
+int take_pending_status(harp_ctx* c, const int* h, cudaStream_t st);
+}
+
+extern "C" int harp_ctx_sync(harp_ctx* c, void* stream) {
+  if (!c) return -1;
+  DeviceGuard g(c->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  // the background Z64 fill of a mixed harp_fill runs on the fill stream
+  if (c->ev_z64) HARP_CUDA(cudaStreamWaitEvent(st, c->ev_z64, 0));
+  HARP_CUDA(cudaMemcpyAsync(c->hstatus, c->dstatus, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HARP_CUDA(cudaStreamSynchronize(st));
+  const int s = take_pending_status(c, c->hstatus, st);
+  HARP_CUDA(cudaStreamSynchronize(st));
+  return s;
+}

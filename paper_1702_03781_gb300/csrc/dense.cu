@@ -1583,21 +1583,24 @@ int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, 
 // ---------------------------------------------------------------------------
 // Conversions, RHS, norms.
 template <typename Rin, typename Rout>
-__global__ void i2p_kernel(int M, int N, const Rin* src, long lds, Rout* re, Rout* im, long ldd) {
+__global__ void i2p_kernel(int M, int N, const Rin* src, long lds, Rout* re, Rout* im, long ldd,
+                           int* flag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= M) return;
   const Rin* s = src + 2 * ((size_t)i + (size_t)j * lds);
-  re[i + (size_t)j * ldd] = (Rout)s[0];
-  im[i + (size_t)j * ldd] = (Rout)s[1];
+  const Rin a = s[0], b = s[1];
+  re[i + (size_t)j * ldd] = (Rout)a;
+  im[i + (size_t)j * ldd] = (Rout)b;
+  if (flag && !(isfinite(a) && isfinite(b))) atomicOr(flag, ST_NONFINITE);
 }
 template <typename Rin, typename Rout>
 int interleaved_to_planes(int M, int N, const Rin* src, long lds, Rout* re, Rout* im, long ldd,
-                          cudaStream_t st) {
+                          cudaStream_t st, int* nonfinite_flag) {
   if (M <= 0 || N <= 0) return HARP_OK;
   dim3 grid((M + 255) / 256, N);
   ProfScope ps_o(HARP_K_OTHER, 0.0, st);
-  i2p_kernel<Rin, Rout><<<grid, 256, 0, st>>>(M, N, src, lds, re, im, ldd);
+  i2p_kernel<Rin, Rout><<<grid, 256, 0, st>>>(M, N, src, lds, re, im, ldd, nonfinite_flag);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -1723,11 +1726,11 @@ template int lu_solve_inv<float>(int, int, CView<float>, CView<float>, const int
 template int diag_inverses<double>(int, CView<double>, double*, double*, double*, double*,
                                    cudaStream_t);
 template int interleaved_to_planes<float, float>(int, int, const float*, long, float*, float*, long,
-                                                 cudaStream_t);
+                                                 cudaStream_t, int*);
 template int interleaved_to_planes<double, double>(int, int, const double*, long, double*, double*,
-                                                   long, cudaStream_t);
+                                                   long, cudaStream_t, int*);
 template int interleaved_to_planes<double, float>(int, int, const double*, long, float*, float*,
-                                                  long, cudaStream_t);
+                                                  long, cudaStream_t, int*);
 template int planes_to_planes<double, float>(int, int, const double*, const double*, long, float*,
                                              float*, long, cudaStream_t);
 template int planes_to_planes<double, double>(int, int, const double*, const double*, long, double*,

@@ -118,9 +118,11 @@ int lu_solve(int N, int nrhs, R* lre, R* lim, long ld, const int* perm, R* bre, 
              cudaStream_t st);
 
 // Elementwise conversions between interleaved complex storage and planes.
+// nonfinite_flag (optional, device): ST_NONFINITE is or-ed into it when an
+// entry read is NaN or infinite.
 template <typename Rin, typename Rout>
 int interleaved_to_planes(int M, int N, const Rin* src, long lds, Rout* re, Rout* im, long ldd,
-                          cudaStream_t st);
+                          cudaStream_t st, int* nonfinite_flag = nullptr);
 template <typename Rin, typename Rout>
 int planes_to_planes(int M, int N, const Rin* sre, const Rin* sim, long lds, Rout* dre, Rout* dim,
                      long ldd, cudaStream_t st);

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_kernel(FillArgs a) {
   }
 
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  bool nonfinite = false;  // a stored entry is NaN or infinite
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int n = item / a.n_mtiles;
     const int m0 = (item - n * a.n_mtiles) * kPairsPerTile;
@@ -155,11 +156,13 @@ __global__ void __launch_bounds__(kFillThreads, 1) fill_kernel(FillArgs a) {
           dv = a.self[(size_t)m * a.self_stride + T + (size_t)S * Nm];
           v = mk<R>((R)dv.x, (R)dv.y);
         }
+        nonfinite |= !(isfinite(v.x) && isfinite(v.y));
         reinterpret_cast<C*>(a.Z)[row + col * a.ldz] = v;
         if (DUAL) a.Z32[row + col * a.ld32] = make_float2((float)dv.x, (float)dv.y);
       }
     }
   }
+  if (nonfinite) atomicOr(a.status, ST_NONFINITE);
 }
 
 // FP64-accurate fill on the FP32 pipe (mixed modes). Same work split as
@@ -496,6 +499,10 @@ extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const doub
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
   cudaStream_t st = (cudaStream_t)stream;
+  // the context's pending status describes the latest fill: coincident
+  // antennas and non-finite entries are flagged by the kernels below and
+  // reported, without a host synchronisation here, by the next mbf_solve or
+  // harp_ctx_sync
   HARP_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), st));
   int s;
   if (prec == HARP_FP64)
@@ -508,9 +515,6 @@ extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const doub
     s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, Z, ldz,
                       nullptr, 0, 2, st);
   if (s != HARP_OK) return s;
-  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
-  HARP_CUDA(cudaStreamSynchronize(st));
-  if (ctx->hstatus[0] & ST_COINCIDENT) return HARP_E_COINCIDENT;
   if (mixed) {
     // The FP64-accurate Z64, which only the refinement reads, on the
     // context's fill stream beside the factorisation that follows, after the

@@ -46,11 +46,29 @@ static bool use_slices(const harp_ctx* c) {
 // Copy the right-hand sides (or the port excitations) into FP64 planes.
 static int load_rhs(harp_ctx* c, int N, int nrhs, const double* V, int ldv, double* re, double* im,
                     cudaStream_t st) {
-  if (V) return interleaved_to_planes<double, double>(N, nrhs, V, ldv, re, im, c->max_N, st);
+  if (V)
+    return interleaved_to_planes<double, double>(N, nrhs, V, ldv, re, im, c->max_N, st,
+                                                 c->dstatus);
   return port_rhs_planes<double>(N, nrhs, N / nrhs, re, im, c->max_N, st);
 }
 
 bool profiling_active();
+
+// The status a caller must see from the context's device words (host
+// mirror h, read after a synchronisation): a bounded wait that gave up, then
+// the pending flags of the last fill or of this solve's input check
+// (coincident antennas, non-finite entries). Clears what it reports.
+int take_pending_status(harp_ctx* c, const int* h, cudaStream_t st) {
+  if (h[2]) {
+    HARP_CUDA(cudaMemsetAsync(c->dstatus + 2, 0, sizeof(int), st));
+    return HARP_E_TIMEOUT;
+  }
+  if (h[0] & (ST_COINCIDENT | ST_NONFINITE)) {
+    HARP_CUDA(cudaMemsetAsync(c->dstatus, 0, sizeof(int), st));
+    return (h[0] & ST_COINCIDENT) ? HARP_E_COINCIDENT : HARP_E_NONFINITE;
+  }
+  return HARP_OK;
+}
 
 // The first FP32 solve with the port right-hand sides V = E (column m has
 // its unit entry in row m s): L^-1 P V is column c_m of L^-1, where
@@ -173,7 +191,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       double* re = (double*)ctx->lu_re;
       double* im = (double*)ctx->lu_im;
       HARP_TRY(interleaved_to_planes<double, double>(N, N, (const double*)Z, ldz, re, im,
-                                                     ctx->ld_lu, st));
+                                                     ctx->ld_lu, st, ctx->dstatus));
       HARP_TRY(lu_factor<double>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                  ctx->dstatus + 1, mode, st));
       const size_t nb = (size_t)((N + 63) / 64) * 4096;
@@ -185,7 +203,7 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       float* re = (float*)ctx->lu_re;
       float* im = (float*)ctx->lu_im;
       HARP_TRY(interleaved_to_planes<float, float>(N, N, (const float*)Z, ldz, re, im, ctx->ld_lu,
-                                                   st));
+                                                   st, ctx->dstatus));
       ctx->finv_incremental = 0;
       HARP_TRY(lu_factor<float>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                 ctx->dstatus + 1, mode, st));
@@ -220,10 +238,10 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
           ctx->finv_split_mode = mode;
       }
     }
-    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 1, ctx->dstatus + 1, 2 * sizeof(int),
+    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, 3 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));
     HARP_CUDA(cudaStreamSynchronize(st));
-    if (ctx->hstatus[2]) return HARP_E_TIMEOUT;
+    HARP_TRY(take_pending_status(ctx, ctx->hstatus, st));
     if (ctx->hstatus[1] != INT_MAX) return ctx->hstatus[1];
     ctx->lu_N = N;
     ctx->lu_prec = lu_class(prec);
@@ -277,10 +295,10 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   // ---- FP32: no refinement
   if (prec == HARP_FP32) {
     HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
-    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 2, ctx->dstatus + 2, sizeof(int),
+    HARP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, 3 * sizeof(int),
                               cudaMemcpyDeviceToHost, st));
     HARP_CUDA(cudaStreamSynchronize(st));
-    return ctx->hstatus[2] ? HARP_E_TIMEOUT : HARP_OK;
+    return take_pending_status(ctx, ctx->hstatus, st);
   }
 
   // ---- mixed: FP64-accurate residual against the context's FP64 matrix,
@@ -328,7 +346,10 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
                          ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
                          true));
   }
-  double bwd = INFINITY;
+  // X (the caller's buffer) receives every iterate that improves on the
+  // best backward error so far, so that it holds the best iterate when the
+  // tolerance is not met; a converged iterate is written after the loop.
+  double bwd = INFINITY, best = INFINITY;
   int it = 0;
   bool converged = false;
   for (;;) {
@@ -351,6 +372,10 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     if (bwd <= tol) {
       converged = true;
       break;
+    }
+    if (bwd < best || it == 0) {
+      best = bwd;
+      HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
     }
     if (it >= max_iter) break;
     // D = (LU32)^{-1} R; X += D
@@ -380,13 +405,13 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     }
     ++it;
   }
-  HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
+  if (converged) HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
   if (iters_out) *iters_out = it;
-  if (resid_out) *resid_out = bwd;
-  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus + 2, ctx->dstatus + 2, sizeof(int),
+  if (resid_out) *resid_out = converged ? bwd : best;
+  HARP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, 3 * sizeof(int),
                             cudaMemcpyDeviceToHost, st));
   HARP_CUDA(cudaStreamSynchronize(st));
-  if (ctx->hstatus[2]) return HARP_E_TIMEOUT;
+  HARP_TRY(take_pending_status(ctx, ctx->hstatus, st));
   return converged ? HARP_OK : HARP_E_NOCONV;
 }
 

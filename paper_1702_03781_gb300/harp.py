@@ -91,7 +91,9 @@ def lib():
         L.harp_ctx_get_option.argtypes = [vp, i, ct.POINTER(i)]
         L.harp_residual.argtypes = [vp, i, vp, i, vp, i, vp, i, i, vp, i, ct.c_char, vp]
         L.harp_wait_check.argtypes = [vp, i, vp]
-        for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_z64", "harp_fill",
+        L.harp_ctx_sync.argtypes = [vp, vp]
+        for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_sync", "harp_ctx_z64",
+                   "harp_fill",
                    "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
                    "harp_ctx_set_option", "harp_ctx_get_option", "harp_residual",
                    "harp_wait_check"):
@@ -222,6 +224,12 @@ class Harp:
     def handle(self) -> ct.c_void_p:
         return self._h
 
+    def sync(self, stream=None) -> None:
+        """Wait for the work enqueued on `stream` and raise HarpError on the
+        context's pending device status (coincident antennas or non-finite
+        entries found by fill(), a bounded wait that gave up), clearing it."""
+        _check("harp_ctx_sync", lib().harp_ctx_sync(self._h, _stream(stream)))
+
     def z64(self, N: int) -> torch.Tensor:
         """The context's FP64 reduced matrix as a column-major (N x N) view."""
         p, ld = ct.c_void_p(), ct.c_int()
@@ -238,7 +246,8 @@ class Harp:
              stream=None) -> torch.Tensor:
         """Reduced MBF matrix: complex128 (fp64) or complex64 (other modes),
         column-major N x N. self_blocks: (Na, Nm, Nm) [antenna, T, S] or one
-        shared (Nm, Nm) block."""
+        shared (Nm, Nm) block. Asynchronous: coincident antennas or
+        non-finite entries are raised by the next solve() or by sync()."""
         pr = _prec(prec)
         Na, Nm, P, Q = _model_shape(pos, coef)
         pos = pos.to(torch.float64).contiguous()

@@ -93,14 +93,25 @@ def test_fill_shared_self_block(harp):
 
 
 def test_fill_coincident_antennas_reported(harp):
+    """The fill does not synchronise: coincident antennas are the context's
+    pending status, returned by the next solve or by harp_ctx_sync."""
     from paper_1702_03781_gb300.harp import HarpError, HARP_E_COINCIDENT
     p = synth.small(6, 2)
     pos = p.pos.copy()
     pos[4] = pos[1]
+    args = (torch.from_numpy(pos).cuda(), p.freq_hz, torch.from_numpy(p.coef).cuda(),
+            torch.from_numpy(p.self_blocks).cuda())
+    harp.fill(*args, prec="fp64")
     with pytest.raises(HarpError) as e:
-        harp.fill(torch.from_numpy(pos).cuda(), p.freq_hz, torch.from_numpy(p.coef).cuda(),
-                  torch.from_numpy(p.self_blocks).cuda(), prec="fp64")
+        harp.sync()
     assert e.value.status == HARP_E_COINCIDENT
+    harp.sync()  # reported once, then cleared
+    for prec in ("fp64", "mixed"):
+        Z = harp.fill(*args, prec=prec)
+        with pytest.raises(HarpError) as e:
+            harp.solve(Z, None, nrhs=p.Na, prec=prec)
+        assert e.value.status == HARP_E_COINCIDENT
+    harp.sync()
 
 
 @pytest.mark.parametrize("mk", [lambda: synth.tiny(), lambda: synth.small(37, 5, P=3, Q=2),

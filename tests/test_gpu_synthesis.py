@@ -94,3 +94,36 @@ def test_station_gradient_mixed_vs_oracle_and_finite_differences(harp):
     gu = np.sum(g * u)
     assert abs(gu - richardson) / abs(richardson) <= 1e-6
     assert abs(gu - d1) / abs(d1) <= 1e-5
+
+
+def test_station_gradient_32_coordinates_vs_richardson_differences(harp):
+    """The synthesis workload's gradient checked coordinate by coordinate:
+    32 seeded-random coordinates of the 256 x 2 positions, each against the
+    Richardson combination of central differences of the oracle's J
+    (h = 1e-4 m and h/2), in relative 2-norm over the 32 coordinates."""
+    from paper_1702_03781_gb300.synthesis import port_objective
+    p = synth.station()
+    pos, coef, sb = _dev(p)
+    x = pos.clone().requires_grad_(True)
+    J = port_objective(x, harp, p.freq_hz, coef, sb, prec="mixed")
+    J.backward()
+    g = x.grad.cpu().numpy()
+    rng = np.random.default_rng(4004)
+    picks = rng.choice(p.pos.size, size=32, replace=False)
+
+    def J_at(flat_idx, h):
+        q = p.pos.copy()
+        q.reshape(-1)[flat_idx] += h
+        Jq, _ = oracle.port_objective_grad(q, p.freq_hz, p.coef, p.self_blocks,
+                                           want_grad=False)
+        return Jq
+
+    h = 1e-4
+    fd, ga = [], []
+    for idx in picks:
+        d1 = (J_at(idx, h) - J_at(idx, -h)) / (2 * h)
+        d2 = (J_at(idx, h / 2) - J_at(idx, -h / 2)) / h
+        fd.append((4 * d2 - d1) / 3)
+        ga.append(g.reshape(-1)[idx])
+    fd, ga = np.array(fd), np.array(ga)
+    assert np.linalg.norm(ga - fd) / np.linalg.norm(fd) <= 1e-6
