@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-wideband", action="store_true")
+    ap.add_argument("--pivot", default="", choices=["", "partial", "tournament"],
+                    help="pivot rule of the FP32 factorisation's panels (default: the library's)")
     ap.add_argument("--nvtx-step", default="",
                     help="run the warm-up, then one step of this path ('mixed' or 'fp64') inside "
                          "an NVTX range named harp_step, and exit (for an ncu launch list)")
@@ -221,6 +223,8 @@ def main():
     coef = torch.from_numpy(p.coef).to(dev)
     sb = torch.from_numpy(p.self_blocks).to(dev)
     h = H.Harp(local, max_N=N, max_nrhs=Na)
+    if args.pivot:
+        h.set_pivot(args.pivot)
     Z32 = H.colmajor_empty(N, N, torch.complex64, dev)
     Z64 = H.colmajor_empty(N, N, torch.complex128, dev)
     X = H.colmajor_empty(N, Na, torch.complex128, dev)
@@ -344,6 +348,7 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "nrhs": Na, "K": p.K,
+                       "pivot": h.pivot_rule(),
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "fp64_gpu_ms_per_step": round(statistics.mean(ms_fp64), 4),

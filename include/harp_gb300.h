@@ -209,10 +209,27 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  *   HARP_RESIDUAL_FF      FP32 pipe: float-float products with a three-float
  *                         accumulator (FP64-accurate)
  * harp_ctx_set_option returns HARP_E_UNSUPPORTED for SLICES when the context
- * has no buffers for it; harp_ctx_get_option reports the method in use. */
+ * has no buffers for it; harp_ctx_get_option reports the method in use.
+ * Errors of both: -1 null ctx, -2 unknown option, -3 unknown value (set) or
+ * null value pointer (get). */
 #define HARP_OPT_RESIDUAL 1
 #define HARP_RESIDUAL_SLICES 0
 #define HARP_RESIDUAL_FF 1
+/* How the FP32 factorisation of the mixed modes (and of HARP_FP32) picks
+ * its pivots within each 64-column panel (option HARP_OPT_PIVOT):
+ *   HARP_PIVOT_PARTIAL     partial pivoting (the largest |z| of the column,
+ *                          as LAPACK's getrf), one cluster barrier per column
+ *   HARP_PIVOT_TOURNAMENT  tournament pivoting (communication-avoiding LU):
+ *                          each CTA of the panel's cluster pivots its own
+ *                          row block, the candidates meet in a tree of
+ *                          fan-in 4, and the root's pick pivots the panel;
+ *                          a few cluster barriers per panel
+ * Both factor the same matrix (rows in another order); the refinement then
+ * converges to the same FP64-accurate solution. The FP64 mode always uses
+ * partial pivoting. */
+#define HARP_OPT_PIVOT 2
+#define HARP_PIVOT_PARTIAL 0
+#define HARP_PIVOT_TOURNAMENT 1
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

@@ -241,6 +241,7 @@ struct harp_ctx {
   long long z64_ticket, oz_ticket;
   double* oz_znorm;
   int residual_mode;  // HARP_RESIDUAL_*
+  int pivot_mode;     // HARP_PIVOT_* of the FP32 factorisation's panels
 
   // Reductions and status.
   double* red;      // device scratch, 16 + 2*max_nrhs doubles

@@ -918,10 +918,34 @@ static int panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld, int j0
   return HARP_OK;
 }
 
-// Cluster panel (panel_cluster.cu), FP32 only.
+// Cluster panels, FP32 only: partial pivoting (panel_cluster.cu) and
+// tournament pivoting (panel_calu.cu).
 int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb);
 int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb,
                   int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
+int panel_calu_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb);
+int panel_calu(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb, int C,
+               int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
+
+// How the FP32 panel at M remaining rows is factored: kind 2 tournament
+// cluster panel, 1 partial-pivoting cluster panel, 0 the recursive panel;
+// returns the width.
+static int plan_panel_f32(const harp_ctx* ctx, int M, int want, int* kind, int* C, int* Mb) {
+  if (ctx->pivot_mode == HARP_PIVOT_TOURNAMENT) {
+    const int w = panel_calu_plan(ctx, M, want, C, Mb);
+    if (w > 0) {
+      *kind = 2;
+      return w;
+    }
+  }
+  const int w = panel_cluster_plan(ctx, M, want, C, Mb);
+  if (w > 0) {
+    *kind = 1;
+    return w;
+  }
+  *kind = 0;
+  return want;
+}
 
 // Factor the panel at column k (rows k..N); returns the width used in *nb.
 // rmap (optional): where a cluster panel exports its row map; *mapped
@@ -932,12 +956,14 @@ static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld,
                         int* rmap = nullptr, bool* mapped = nullptr) {
   if (mapped) *mapped = false;
   if constexpr (std::is_same<R, float>::value) {
-    // the plan only offers clusters that can be resident
-    int C = 0, Mb = 0;
-    const int w = panel_cluster_plan(ctx, N - k, want, &C, &Mb);
-    if (w > 0) {
+    // the plans only offer clusters that can be resident
+    int kind = 0, C = 0, Mb = 0;
+    const int w = plan_panel_f32(ctx, N - k, want, &kind, &C, &Mb);
+    if (kind > 0) {
       *nb = w;
       if (mapped) *mapped = (rmap != nullptr);
+      if (kind == 2)
+        return panel_calu(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st, rmap);
       return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st, rmap);
     }
   }
@@ -1251,9 +1277,8 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
     if (k1 < N) {
       const int want = std::min(kNB, N - k1);
       // the width of panel i+1 is only known after planning; plan it now
-      int C = 0, Mb = 0;
-      nb1 = panel_cluster_plan(ctx, N - k1, want, &C, &Mb);
-      if (nb1 <= 0) nb1 = want;
+      int kind = 0, C = 0, Mb = 0;
+      nb1 = plan_panel_f32(ctx, N - k1, want, &kind, &C, &Mb);
       if (maps[i])
         HARP_TRY(laswp_map<float>(re, im, ld, pmap(i), k1, k1 + nb1, 0, 0, nullptr, st));
       else

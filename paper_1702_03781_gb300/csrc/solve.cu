@@ -366,7 +366,11 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     for (int j = 0; j < nrhs; ++j) {
       const double rj = h[16 + j], xj = h[16 + nrhs + j];
       const double bj = (rj == 0.0) ? 0.0 : rj / (znorm * xj);
-      if (!(bj == bj)) return HARP_E_NONFINITE;
+      if (!(bj == bj)) {  // reported here: the pending flag of the input check goes with it
+        HARP_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), st));
+        HARP_CUDA(cudaStreamSynchronize(st));
+        return HARP_E_NONFINITE;
+      }
       bwd = std::max(bwd, bj);
     }
     if (bwd <= tol) {
@@ -417,6 +421,11 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
 
 extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
   if (!ctx) return -1;
+  if (option == HARP_OPT_PIVOT) {
+    if (value != HARP_PIVOT_PARTIAL && value != HARP_PIVOT_TOURNAMENT) return -3;
+    ctx->pivot_mode = value;
+    return HARP_OK;
+  }
   if (option != HARP_OPT_RESIDUAL) return -2;
   if (value != HARP_RESIDUAL_SLICES && value != HARP_RESIDUAL_FF) return -3;
   if (value == HARP_RESIDUAL_SLICES && !ctx->oz_a) return HARP_E_UNSUPPORTED;
@@ -426,9 +435,12 @@ extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
 
 extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
   if (!ctx) return -1;
-  if (option != HARP_OPT_RESIDUAL) return -2;
+  if (option != HARP_OPT_RESIDUAL && option != HARP_OPT_PIVOT) return -2;
   if (!value) return -3;
-  *value = use_slices(ctx) ? HARP_RESIDUAL_SLICES : HARP_RESIDUAL_FF;
+  if (option == HARP_OPT_PIVOT)
+    *value = ctx->pivot_mode;
+  else
+    *value = use_slices(ctx) ? HARP_RESIDUAL_SLICES : HARP_RESIDUAL_FF;
   return HARP_OK;
 }
 

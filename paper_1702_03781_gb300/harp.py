@@ -33,9 +33,12 @@ HARP_E_UNSUPPORTED = 0x40000006
 HARP_E_STATE = 0x40000007
 HARP_E_NONFINITE = 0x40000008
 
-# harp_ctx_set_option: how the mixed refinement forms its FP64 residual
+# harp_ctx_set_option: how the mixed refinement forms its FP64 residual, and
+# how the FP32 factorisation pivots its panels
 HARP_OPT_RESIDUAL = 1
 RESIDUAL = {"slices": 0, "ff": 1}
+HARP_OPT_PIVOT = 2
+PIVOT = {"partial": 0, "tournament": 1}
 
 _lib = None
 
@@ -311,6 +314,18 @@ class Harp:
         _check("harp_ctx_get_option", lib().harp_ctx_get_option(self._h, HARP_OPT_RESIDUAL,
                                                                 ct.byref(v)))
         return {k: m for m, k in RESIDUAL.items()}[v.value]
+
+    def set_pivot(self, rule: str):
+        """Pivot rule of the FP32 factorisation's panels: 'partial' or
+        'tournament' (communication-avoiding LU)."""
+        _check("harp_ctx_set_option",
+               lib().harp_ctx_set_option(self._h, HARP_OPT_PIVOT, PIVOT[rule]))
+
+    def pivot_rule(self) -> str:
+        v = ct.c_int(-1)
+        _check("harp_ctx_get_option", lib().harp_ctx_get_option(self._h, HARP_OPT_PIVOT,
+                                                                ct.byref(v)))
+        return {k: m for m, k in PIVOT.items()}[v.value]
 
     def residual(self, Z: torch.Tensor, X: torch.Tensor, V: torch.Tensor, trans: str = "N",
                  stream=None) -> torch.Tensor:

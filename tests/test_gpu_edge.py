@@ -18,8 +18,9 @@ Tolerances (stated here, derived from the arithmetic):
     resid_out must equal the zcgesv column test of the returned X evaluated
     against the oracle's matrix, to 1e-3 relative (the two differ only by the
     FP64 rounding of the residual, far below the stalled error).
-  * the P = Q = 0 fill: every mutual entry equals c_00 e^{-jkr} to 1e-15
-    relative (FP64 sincos on both sides).
+  * the P = Q = 0 fill: every mutual entry equals c_00 e^{-jkr} within
+    1e-13 of max |c_00| (FP64 on both sides; the phase kr, up to ~50 rad
+    here, carries a few ulp of argument reduction, ~1e-14).
 """
 import math
 
@@ -96,7 +97,9 @@ def test_mixed_tf32_converges_on_a_well_conditioned_case(harp):
     p = synth.tiny()
     pos, coef, sb = _dev(p)
     Zo = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
-    assert np.linalg.cond(Zo) * 2.0 ** -11 < 0.1  # the regime where TF32 refinement contracts
+    # the regime where TF32 refinement contracts: the error shrinks by about
+    # cond * 2^-11 per correction (0.19 here)
+    assert np.linalg.cond(Zo) * 2.0 ** -11 < 0.5
     Z = harp.fill(pos, p.freq_hz, coef, sb, prec="mixed_tf32")
     X, info = harp.solve(Z, None, nrhs=p.Na, prec="mixed_tf32", max_iter=30)
     assert info["status"] == 0
@@ -104,8 +107,11 @@ def test_mixed_tf32_converges_on_a_well_conditioned_case(harp):
 
 
 def test_mixed_tf32_station_reports_noconv_with_best_iterate(harp):
-    """At the station cond_2 ~ 7.5e4, so cond * 2^-11 > 1: single-term TF32
-    refinement stalls. The call must say so and return its best iterate."""
+    """At the station cond_2 ~ 7.5e4, so cond * 2^-11 >> 1: single-term TF32
+    factors do not make refinement contract (the forward error of the first
+    solution is already of the order of the solution itself). The call must
+    say so and return the iterate of smallest backward error, whose error it
+    reports."""
     from paper_1702_03781_gb300.harp import HARP_E_NOCONV
     p = synth.station()
     pos, coef, sb = _dev(p)
@@ -116,10 +122,11 @@ def test_mixed_tf32_station_reports_noconv_with_best_iterate(harp):
     assert info["status"] == HARP_E_NOCONV
     assert info["iters"] == 10 and info["resid"] > tol
     Zo = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
-    got = _zcgesv_test(Zo, _np(X), p.V)
+    Xg = _np(X)
+    assert np.all(np.isfinite(Xg))
+    got = _zcgesv_test(Zo, Xg, p.V)
     assert got == pytest.approx(info["resid"], rel=1e-3)
-    # the best iterate is still a useful FP32-level solution
-    assert _rel(_np(X), oracle.solve(Zo, p.V)) <= 1e-2
+    assert info["resid"] < 1.0
 
 
 def test_max_iter_zero_returns_the_first_solution_and_noconv(harp):
@@ -174,7 +181,7 @@ def test_p_q_zero_fill_is_the_closed_form(harp):
                 continue
             r = math.hypot(*(p.pos[m] - p.pos[n]))
             ref = c00 * np.exp(-1j * k * r)
-            assert np.max(np.abs(blk - ref)) <= 1e-15 * 4 * np.max(np.abs(c00))
+            assert np.max(np.abs(blk - ref)) <= 1e-13 * np.max(np.abs(c00))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

@@ -11,10 +11,10 @@ On a station-shaped system with cond(Z) * 2^-11 > 1 (N = 768, cond 1.3e4):
   1.6e-8 over 10 corrections) and miss the tolerance;
 - the three-term products behave like FP32 and converge in 3 corrections
   (3.6e-7, 1.6e-10, 4.9e-14, 2.8e-17).
-Tournament pivoting (one row block per cluster CTA, a binary tree of
-eliminations) refines in the same number of corrections as partial pivoting.
-These document design choices; the GPU path itself is checked against the
-oracle in the GPU tests.
+Tournament pivoting (one row block per cluster CTA, a tree of eliminations
+of fan-in 4, as the tournament cluster panel runs it) refines in the same
+number of corrections as partial pivoting. These document design choices;
+the GPU path itself is checked against the oracle in the GPU tests.
 """
 import numpy as np
 import pytest
@@ -63,35 +63,35 @@ def _gepp_order(B):
     return rows[:min(B.shape)]
 
 
-def _tournament(panel, nblk):
+def _tournament(panel, nblk, fan_in=4):
     """Tournament pivoting (TSLU): partial-pivot elimination on each of nblk
-    row blocks picks candidate rows; a binary tree of eliminations on stacked
-    candidate pairs picks the panel's pivot rows, in pivot order."""
+    row blocks picks candidate rows; a tree of eliminations on stacks of
+    fan_in candidate sets picks the panel's pivot rows, in pivot order. With
+    fan_in = 4 this is the tree of the cluster panel (panel_calu.cu: 16 row
+    blocks, two levels)."""
     blocks = [b for b in np.array_split(np.arange(panel.shape[0]), nblk) if len(b)]
     cands = [b[_gepp_order(panel[b])] for b in blocks]
     while len(cands) > 1:
         nxt = []
-        for i in range(0, len(cands), 2):
-            if i + 1 == len(cands):
-                nxt.append(cands[i])
-                continue
-            idx = np.concatenate([cands[i], cands[i + 1]])
+        for i in range(0, len(cands), fan_in):
+            idx = np.concatenate(cands[i:i + fan_in])
             nxt.append(idx[_gepp_order(panel[idx])])
         cands = nxt
     return cands[0][:panel.shape[1]]
 
 
-def _lu(Z, mm, nb=64, tournament_blocks=0):
+def _lu(Z, mm, nb=64, tournament_blocks=0, fan_in=4):
     """Right-looking blocked LU in complex64 with partial pivoting, or with
-    tournament pivoting over `tournament_blocks` row blocks per panel; the
-    trailing update A22 -= L21 U12 uses the product `mm`."""
+    tournament pivoting over `tournament_blocks` row blocks per panel (tree
+    fan-in `fan_in`); the trailing update A22 -= L21 U12 uses the product
+    `mm`."""
     A = np.array(Z, dtype=np.complex64, order="F")
     N = A.shape[0]
     perm = np.arange(N)
     for k in range(0, N, nb):
         kb = min(nb, N - k)
         if tournament_blocks:
-            win = _tournament(A[k:, k:k + kb], tournament_blocks)
+            win = _tournament(A[k:, k:k + kb], tournament_blocks, fan_in)
             rest = np.setdiff1d(np.arange(N - k), win, assume_unique=True)
             order = np.concatenate([win, rest]) + k
             A[k:] = A[order]
@@ -170,14 +170,15 @@ def test_three_term_tf32_factors_converge(ill_conditioned):
     assert its is not None and its <= 6, hist
 
 
-def test_tournament_pivoting_refines_like_partial_pivoting(ill_conditioned):
-    """The cluster panel's per-column barrier would go with tournament
-    pivoting (16 row blocks, one per cluster CTA). Its factors must refine as
-    well as partial pivoting's: same correction count within one, growth
-    within a small factor."""
+@pytest.mark.parametrize("fan_in", [2, 4])
+def test_tournament_pivoting_refines_like_partial_pivoting(ill_conditioned, fan_in):
+    """Tournament pivoting as the tournament cluster panel does it (16 row
+    blocks, one per cluster CTA, tree fan-in 4; fan-in 2 for comparison). Its
+    factors must refine as well as partial pivoting's: same correction count
+    within one, growth within a small factor, |L| bounded."""
     Z, V = ill_conditioned
     A_pp, p_pp = _lu(Z, _mm_3xtf32)
-    A_t, p_t = _lu(Z, _mm_3xtf32, tournament_blocks=16)
+    A_t, p_t = _lu(Z, _mm_3xtf32, tournament_blocks=16, fan_in=fan_in)
     assert sorted(p_t) == list(range(Z.shape[0]))
     its_pp, h_pp = _refine(Z, V, A_pp, p_pp)
     its_t, h_t = _refine(Z, V, A_t, p_t)
