@@ -126,7 +126,11 @@ int harp_ctx_sync(harp_ctx* ctx, void* stream);
 int harp_ctx_z64(harp_ctx* ctx, void** z64, int* ld);
 
 /* Fill the reduced MBF matrix (Eq. 3 and 4 for every ordered pair m != n,
- * self blocks on the diagonal).
+ * self blocks on the diagonal). The inputs are read in the order of
+ * `stream`: in the mixed modes the call copies pos, coef and the self blocks
+ * into the context (the first mixed fill of a larger model may allocate
+ * room for them), so the background fill never reads the caller's buffers
+ * after work queued later on `stream`.
  *   ctx          context (workspace for the mixed modes)          [1]
  *   Na, Nm       antennas, MBFs per antenna; N = Na*Nm <= max_N   [2, 3]
  *   P, Q         harmonic order and polynomial degree (>= 0)      [4, 5]

@@ -198,6 +198,10 @@ struct harp_ctx {
   // orders it after the caller's earlier work, ev_z64 marks Z64 complete.
   cudaStream_t fill_stream;
   cudaEvent_t ev_fill_fork, ev_z64;
+  // Copies of the last mixed fill's inputs (positions, coefficients, self
+  // blocks) that the background fill reads, fin_bytes long (grown on demand).
+  void* fin;
+  size_t fin_bytes;
   // Streams on which the FP32 look-ahead LU builds the factor inverses
   // panel by panel beside the factorisation ([0] (L^-1)^T, [1] U^-1);
   // ev_inv marks them complete. finv_incremental: the last FP32

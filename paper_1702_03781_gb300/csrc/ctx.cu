@@ -44,6 +44,7 @@ static void free_all(harp_ctx* c) {
   for (int g = 0; g < 2; ++g)
     if (c->solve_graph[g]) cudaGraphExecDestroy(c->solve_graph[g]);
   if (c->zbuf) cudaFree(c->zbuf);
+  if (c->fin) cudaFree(c->fin);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
   for (int q = 0; q < 2; ++q) {

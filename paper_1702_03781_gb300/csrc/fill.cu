@@ -516,12 +516,42 @@ extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const doub
                       nullptr, 0, 2, st);
   if (s != HARP_OK) return s;
   if (mixed) {
+    // The background fill below runs after this call returns, so it reads
+    // context-owned copies of the model inputs, made here on `stream`: the
+    // caller may release or reuse its buffers in the order of its stream.
+    // The copies wait for the previous background fill, which read the last
+    // ones (the refinement waits for it anyway).
+    const size_t pos_b = (size_t)Na * 2 * sizeof(double);
+    const size_t coef_b = (size_t)Nm * Nm * (2 * P + 1) * (Q + 1) * sizeof(double2);
+    const size_t self_b =
+        ((size_t)(Na - 1) * (size_t)self_stride + (size_t)Nm * Nm) * sizeof(double2);
+    const size_t a16 = 255;
+    const size_t o_coef = (pos_b + a16) & ~a16, o_self = (o_coef + coef_b + a16) & ~a16;
+    const size_t need = o_self + self_b;
+    if (ctx->fin_bytes < need) {
+      HARP_CUDA(cudaStreamSynchronize(ctx->fill_stream));
+      if (ctx->fin) cudaFree(ctx->fin);
+      ctx->fin = nullptr;
+      ctx->fin_bytes = 0;
+      if (cudaMalloc(&ctx->fin, need) != cudaSuccess) {
+        cudaGetLastError();
+        return HARP_E_NOMEM;
+      }
+      ctx->fin_bytes = need;
+    }
+    char* fb = static_cast<char*>(ctx->fin);
+    HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_z64, 0));
+    HARP_CUDA(cudaMemcpyAsync(fb, pos, pos_b, cudaMemcpyDeviceToDevice, st));
+    HARP_CUDA(cudaMemcpyAsync(fb + o_coef, coef, coef_b, cudaMemcpyDeviceToDevice, st));
+    HARP_CUDA(cudaMemcpyAsync(fb + o_self, self_blocks, self_b, cudaMemcpyDeviceToDevice, st));
     // The FP64-accurate Z64, which only the refinement reads, on the
     // context's fill stream beside the factorisation that follows, after the
     // caller's earlier work (a previous solve may still read Z64).
     HARP_CUDA(cudaEventRecord(ctx->ev_fill_fork, st));
     HARP_CUDA(cudaStreamWaitEvent(ctx->fill_stream, ctx->ev_fill_fork, 0));
-    s = fill_dispatch(ctx, Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride, ctx->z64,
+    s = fill_dispatch(ctx, Na, Nm, P, Q, reinterpret_cast<const double*>(fb), freq_hz,
+                      reinterpret_cast<const double*>(fb + o_coef),
+                      reinterpret_cast<const double*>(fb + o_self), self_stride, ctx->z64,
                       ctx->ld64, nullptr, 0, 1, ctx->fill_stream, ctx->dstatus + 3, true);
     if (s != HARP_OK) return s;
     // and, when the refinement uses the tensor-core residual, the digit

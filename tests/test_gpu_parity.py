@@ -193,3 +193,24 @@ def test_adjoint_fp64_matches_oracle_gradient(harp):
     g = _np(harp.fill_adjoint(pos, p.freq_hz, coef, Lam, X, prec="fp64"))
     _, go = oracle.port_objective_grad(p.pos, p.freq_hz, p.coef, p.self_blocks)
     assert _rel(g, go) <= 1e-10
+
+
+def test_background_fill_reads_its_own_copy_of_the_inputs(harp):
+    """The mixed fill's FP64 matrix is made on the context's own stream after
+    harp_fill returns. The binding hands it temporaries (the self blocks in
+    column-major order, a contiguous copy of a strided coefficient table)
+    that go back to the allocator when fill() returns; the allocations below
+    reuse and overwrite them on the caller's stream at once. Z64 must still be
+    the oracle's matrix: the library works from its own copies."""
+    p = synth.small(110, 7, P=2, Q=2, seed_cfg=62)
+    pos, coef, sb = _dev(p)
+    coef_strided = coef.permute(1, 0, 2, 3).contiguous().permute(1, 0, 2, 3)
+    assert not coef_strided.is_contiguous()
+    Zo = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
+    for _ in range(3):
+        harp.fill(pos, p.freq_hz, coef_strided, sb, prec="mixed")
+        junk = [torch.full(t.shape, complex(1e30, -1e30), dtype=torch.complex128, device="cuda:0")
+                for t in (sb, coef) for _ in range(4)]
+        z64 = _np(harp.z64(p.N))
+        del junk
+        assert np.max(np.abs(z64 - Zo)) <= 1e-13 * np.max(np.abs(Zo))
