@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-wideband", action="store_true")
-    ap.add_argument("--pivot", default="", choices=["", "partial", "tournament"],
+    ap.add_argument("--pivot", default="", choices=["", "partial", "tournament", "block"],
                     help="pivot rule of the FP32 factorisation's panels (default: the library's)")
     ap.add_argument("--nvtx-step", default="",
                     help="run the warm-up, then one step of this path ('mixed' or 'fp64') inside "

@@ -228,12 +228,25 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  *                          row block, the candidates meet in a tree of
  *                          fan-in 4, and the root's pick pivots the panel;
  *                          a few cluster barriers per panel
- * Both factor the same matrix (rows in another order); the refinement then
+ *   HARP_PIVOT_BLOCK       pivoting restricted to each panel's 64 x 64
+ *                          diagonal block (one CTA), the rows below solved
+ *                          against its U (no pivot search across the panel).
+ *                          Its factors are only used where the refinement
+ *                          checks them: HARP_FP32 uses partial pivoting
+ *                          instead, and a factorisation that meets a zero
+ *                          pivot, or whose refinement stops contracting (a
+ *                          correction that does not halve the backward
+ *                          error), is redone with partial pivoting and
+ *                          counted in HARP_OPT_PIVOT_FALLBACKS
+ * All factor the same matrix (rows in another order); the refinement then
  * converges to the same FP64-accurate solution. The FP64 mode always uses
- * partial pivoting. */
+ * partial pivoting. HARP_OPT_PIVOT_FALLBACKS (get only) reads the number of
+ * such redone factorisations of the context. */
 #define HARP_OPT_PIVOT 2
 #define HARP_PIVOT_PARTIAL 0
 #define HARP_PIVOT_TOURNAMENT 1
+#define HARP_PIVOT_BLOCK 2
+#define HARP_OPT_PIVOT_FALLBACKS 3
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

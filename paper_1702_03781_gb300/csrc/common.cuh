@@ -137,6 +137,7 @@ struct harp_ctx {
   int lu_N;
   int lu_prec;  // -1 = none
   int lu_valid;
+  int lu_pivot;  // HARP_PIVOT_* the cached factorisation was made with
 
   // Solve buffers (room for doubles), N x nrhs planes, ld = max_N.
   void* w_re;
@@ -202,6 +203,11 @@ struct harp_ctx {
   // blocks) that the background fill reads, fin_bytes long (grown on demand).
   void* fin;
   size_t fin_bytes;
+  // U11^-1 of the latest block-local panel (2 planes of 64 x 64 floats).
+  float* blk_uinv;
+  // Factorisations whose pivoting restricted to the diagonal blocks did not
+  // give factors the refinement could use, redone with partial pivoting.
+  long long pivot_fallbacks;
   // Streams on which the FP32 look-ahead LU builds the factor inverses
   // panel by panel beside the factorisation ([0] (L^-1)^T, [1] U^-1);
   // ev_inv marks them complete. finv_incremental: the last FP32

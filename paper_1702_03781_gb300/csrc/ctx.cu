@@ -45,6 +45,7 @@ static void free_all(harp_ctx* c) {
     if (c->solve_graph[g]) cudaGraphExecDestroy(c->solve_graph[g]);
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->fin) cudaFree(c->fin);
+  if (c->blk_uinv) cudaFree(c->blk_uinv);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
   for (int q = 0; q < 2; ++q) {
@@ -128,6 +129,7 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   const size_t nred = 16 + 2 * (size_t)max_nrhs;
   alloc((void**)&c->red, nred * sizeof(double));
   alloc((void**)&c->dstatus, 4 * sizeof(int));
+  alloc((void**)&c->blk_uinv, 2 * 64 * 64 * sizeof(float));
   alloc((void**)&c->zbuf, NN * sizeof(float2));
   alloc((void**)&c->finv, 4 * NN * sizeof(float));
   alloc((void**)&c->finv_tmp, 2 * NN * sizeof(float));

@@ -927,10 +927,17 @@ int panel_calu_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb
 int panel_calu(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb, int C,
                int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
 
-// How the FP32 panel at M remaining rows is factored: kind 2 tournament
-// cluster panel, 1 partial-pivoting cluster panel, 0 the recursive panel;
-// returns the width.
+// How the FP32 panel at M remaining rows is factored: kind 3 pivoting
+// restricted to the diagonal block, 2 tournament cluster panel, 1
+// partial-pivoting cluster panel, 0 the recursive panel; returns the width.
 static int plan_panel_f32(const harp_ctx* ctx, int M, int want, int* kind, int* C, int* Mb) {
+  if (ctx->pivot_mode == HARP_PIVOT_BLOCK && want % 16 == 0 && want <= 64 && M >= want &&
+      ctx->blk_uinv) {
+    *kind = 3;
+    *C = 1;
+    *Mb = want;
+    return want;
+  }
   if (ctx->pivot_mode == HARP_PIVOT_TOURNAMENT) {
     const int w = panel_calu_plan(ctx, M, want, C, Mb);
     if (w > 0) {
@@ -947,6 +954,11 @@ static int plan_panel_f32(const harp_ctx* ctx, int M, int want, int* kind, int* 
   return want;
 }
 
+// The panel at column k with pivoting restricted to its diagonal block
+// (defined with the look-ahead kernels below).
+static int panel_block_local(harp_ctx* ctx, int N, CView<float> A, float* re, float* im, long ld,
+                             int k, int nb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
+
 // Factor the panel at column k (rows k..N); returns the width used in *nb.
 // rmap (optional): where a cluster panel exports its row map; *mapped
 // tells whether it did.
@@ -962,6 +974,7 @@ static int factor_panel(harp_ctx* ctx, int N, CView<R> A, R* re, R* im, long ld,
     if (kind > 0) {
       *nb = w;
       if (mapped) *mapped = (rmap != nullptr);
+      if (kind == 3) return panel_block_local(ctx, N, A, re, im, ld, k, w, ipiv, zero_col, st, rmap);
       if (kind == 2)
         return panel_calu(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st, rmap);
       return panel_cluster(ctx, re, im, ld, k, N - k, w, C, Mb, ipiv, zero_col, st, rmap);
@@ -1032,13 +1045,13 @@ __global__ void __launch_bounds__(256) la_trsm_kernel(int n, int ncols, const fl
   }
 }
 
-// C -= A B for C M x ncols, A M x n, B n x ncols (n, ncols <= 64), column-
-// major planes with leading dimensions lda, ldb, ldc (TA: A given by its
-// transpose, element (r, k) at a[k + r lda]; ZC: C starts from zero instead
-// of being read): 32 rows of C per CTA, lane l row l, warp w columns
-// 8 w .. 8 w + 7; the CTA's rows of A and all of B are staged in shared
-// memory by one round of loads.
-template <bool TA, bool ZC>
+// C -= A B (NEG) or C += A B for C M x ncols, A M x n, B n x ncols (n, ncols
+// <= 64), column-major planes with leading dimensions lda, ldb, ldc (TA: A
+// given by its transpose, element (r, k) at a[k + r lda]; ZC: C starts from
+// zero instead of being read): 32 rows of C per CTA, lane l row l, warp w
+// columns 8 w .. 8 w + 7; the CTA's rows of A and all of B are staged in
+// shared memory by one round of loads, so C may be A itself (same rows).
+template <bool TA, bool ZC, bool NEG = true>
 __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
                                                       const float* __restrict__ are,
                                                       const float* __restrict__ aim, long lda,
@@ -1100,8 +1113,13 @@ __global__ void __launch_bounds__(256) la_gemm_kernel(int M, int n, int ncols,
     const float bI[8] = {b0i.x, b0i.y, b0i.z, b0i.w, b1i.x, b1i.y, b1i.z, b1i.w};
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      accr[j] = fmaf(-ar, bR[j], fmaf(ai, bI[j], accr[j]));
-      acci[j] = fmaf(-ar, bI[j], fmaf(-ai, bR[j], acci[j]));
+      if (NEG) {
+        accr[j] = fmaf(-ar, bR[j], fmaf(ai, bI[j], accr[j]));
+        acci[j] = fmaf(-ar, bI[j], fmaf(-ai, bR[j], acci[j]));
+      } else {
+        accr[j] = fmaf(ar, bR[j], fmaf(-ai, bI[j], accr[j]));
+        acci[j] = fmaf(ar, bI[j], fmaf(ai, bR[j], acci[j]));
+      }
     }
   }
   if (row < M) {
@@ -1130,6 +1148,30 @@ static int lookahead_update(float* re, float* im, long ld, int N, int k, int nb,
   ProfScope ps(HARP_K_TRSM, 8.0 * M * (double)nb1 * nb, st);
   la_gemm_kernel<false, false><<<(M + 31) / 32, 256, 0, st>>>(
       M, nb, nb1, re + l, im + l, ld, re + u, im + u, ld, re + c, im + c, ld);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// The panel at column k with pivoting restricted to its nb x nb diagonal
+// block (the refinement's factors only; see HARP_PIVOT_BLOCK): partial
+// pivoting on the block (the tournament kernel with one CTA and no other
+// rows), then L21 = A21 U11^-1 for the rows below through the explicit
+// inverse of U11 (one warp per column) and one CUDA-core product in place.
+static int panel_block_local(harp_ctx* ctx, int N, CView<float> A, float* re, float* im, long ld,
+                             int k, int nb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap) {
+  HARP_TRY(panel_calu(ctx, re, im, ld, k, nb, nb, 1, nb, ipiv, zero_col, st, rmap));
+  const int M2 = N - k - nb;
+  if (M2 <= 0) return HARP_OK;
+  const CView<float> Ui = planes<float>(ctx->blk_uinv, ctx->blk_uinv + 64 * 64, 64);
+  {
+    ProfScope ps(HARP_K_TRSM, 8.0 * nb * (double)nb * nb, st);
+    tri64_inv_kernel<<<(nb + 7) / 8, 256, 0, st>>>(nb, A.sub(k, k), 1, Ui, 0);
+    HARP_LAUNCHED();
+  }
+  const CView<float> L = A.sub(k + nb, k);
+  ProfScope ps(HARP_K_PANEL, 4.0 * M2 * (double)nb * nb, st);
+  la_gemm_kernel<false, true, false><<<(M2 + 31) / 32, 256, 0, st>>>(
+      M2, nb, nb, L.re, L.im, L.cs, Ui.re, Ui.im, 64, L.re, L.im, L.cs);
   HARP_LAUNCHED();
   return HARP_OK;
 }

@@ -149,42 +149,15 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
 
 using namespace harp;
 
-extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int ldv,
-                         int nrhs, double* X, int ldx, char trans, int prec, double tol,
-                         int max_iter, int* iters_out, double* resid_out, void* stream) {
-  if (!ctx) return -1;
-  if (N < 1 || N > ctx->max_N) return -2;
-  const bool tr = (trans == 'T' || trans == 't');
-  if (!tr && trans != 'N' && trans != 'n') return -10;
-  if (!tr && !Z) return -3;
-  if (!tr && ldz < N) return -4;
-  if (V && ldv < N) return -6;
-  if (nrhs < 1 || nrhs > ctx->max_nrhs || nrhs > 65535) return -7;
-  if (!V && (N % nrhs) != 0) return -5;
-  if (!X) return -8;
-  if (ldx < N) return -9;
-  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32 && prec != HARP_FP32)
-    return -11;
-  if (!(tol == tol)) return -12;
-  if (max_iter < 0) return -13;
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return cuda_status(cudaGetLastError());
-  cudaStream_t st = (cudaStream_t)stream;
-  const int mode = gemm_mode(prec);
-  const long ldw = ctx->max_N;
-  if (iters_out) *iters_out = 0;
-  if (resid_out) *resid_out = -1.0;
-
-  // Tensor-core GEMM scratch for this call; cleared timeout flag.
-  tc_set_workspace(ctx->tc_a, ctx->tc_a_floats, ctx->tc_b, ctx->tc_b_floats, ctx->dstatus + 2);
-  HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
-  struct Unset {
-    ~Unset() { tc_set_workspace(nullptr, 0, nullptr, 0, nullptr); }
-  } unset_on_return;
-
-  // ---- factorisation (trans 'N') or reuse of the cached one (trans 'T')
-  if (!tr) {
-    ctx->lu_valid = 0;
+// Factorise Z (c64, or c128 when z_c128; trans 'N' solves) into the
+// context: PZ = LU with the context's pivot rule (FP32 modes) or partial
+// pivoting (FP64), the diagonal-block inverses and, in the FP32 modes, the
+// explicit factor inverses. Returns +i on an exactly zero pivot in column i,
+// or the pending status (coincident antennas, non-finite entries).
+static int factorise(harp_ctx* ctx, int N, const void* Z, int ldz, bool z_c128, int prec,
+                     int mode, cudaStream_t st) {
+  ctx->lu_valid = 0;
+  {
     set_int_kernel<<<1, 1, 0, st>>>(ctx->dstatus + 1, INT_MAX);
     HARP_LAUNCHED();
     if (lu_class(prec) == 0) {
@@ -202,8 +175,12 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     } else {
       float* re = (float*)ctx->lu_re;
       float* im = (float*)ctx->lu_im;
-      HARP_TRY(interleaved_to_planes<float, float>(N, N, (const float*)Z, ldz, re, im, ctx->ld_lu,
-                                                   st, ctx->dstatus));
+      if (z_c128)  // the FP32 copy of an FP64 matrix (the context's Z64)
+        HARP_TRY(interleaved_to_planes<double, float>(N, N, (const double*)Z, ldz, re, im,
+                                                      ctx->ld_lu, st, ctx->dstatus));
+      else
+        HARP_TRY(interleaved_to_planes<float, float>(N, N, (const float*)Z, ldz, re, im,
+                                                     ctx->ld_lu, st, ctx->dstatus));
       ctx->finv_incremental = 0;
       HARP_TRY(lu_factor<float>(ctx, N, re, im, ctx->ld_lu, ctx->ipiv, ctx->perm,
                                 ctx->dstatus + 1, mode, st));
@@ -245,11 +222,26 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
     if (ctx->hstatus[1] != INT_MAX) return ctx->hstatus[1];
     ctx->lu_N = N;
     ctx->lu_prec = lu_class(prec);
+    ctx->lu_pivot = (lu_class(prec) == 0) ? HARP_PIVOT_PARTIAL : ctx->pivot_mode;
     ctx->lu_valid = 1;
-  } else if (!ctx->lu_valid || ctx->lu_N != N || ctx->lu_prec != lu_class(prec)) {
-    return HARP_E_STATE;
   }
+  return HARP_OK;
+}
 
+
+// Solve with the cached factors (FP64: substitution; FP32: the explicit
+// inverses; mixed: refinement against Z64). With stall_exit the refinement
+// stops as soon as a correction contracts the backward error by less than
+// half (the factors of restricted pivoting are then not worth refining) and
+// *stalled is set.
+static int solve_factored(harp_ctx* ctx, int N, const double* V, int ldv, int nrhs, double* X,
+                          int ldx, bool tr, int prec, int mode, double tol, int max_iter,
+                          int* iters_out, double* resid_out, cudaStream_t st, bool stall_exit,
+                          bool* stalled) {
+  const long ldw = ctx->max_N;
+  *stalled = false;
+  if (iters_out) *iters_out = 0;
+  if (resid_out) *resid_out = -1.0;
   // ---- FP64: direct solve
   if (prec == HARP_FP64) {
     double* wre = (double*)ctx->w_re;
@@ -377,9 +369,14 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
       converged = true;
       break;
     }
+    const double prev = best;
     if (bwd < best || it == 0) {
       best = bwd;
       HARP_TRY(planes_to_interleaved(N, nrhs, ctx->x_re, ctx->x_im, ldw, X, ldx, st));
+    }
+    if (stall_exit && it > 0 && !(bwd <= 0.5 * prev)) {
+      *stalled = true;
+      break;
     }
     if (it >= max_iter) break;
     // D = (LU32)^{-1} R; X += D
@@ -419,10 +416,91 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
   return converged ? HARP_OK : HARP_E_NOCONV;
 }
 
+extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int ldv,
+                         int nrhs, double* X, int ldx, char trans, int prec, double tol,
+                         int max_iter, int* iters_out, double* resid_out, void* stream) {
+  if (!ctx) return -1;
+  if (N < 1 || N > ctx->max_N) return -2;
+  const bool tr = (trans == 'T' || trans == 't');
+  if (!tr && trans != 'N' && trans != 'n') return -10;
+  if (!tr && !Z) return -3;
+  if (!tr && ldz < N) return -4;
+  if (V && ldv < N) return -6;
+  if (nrhs < 1 || nrhs > ctx->max_nrhs || nrhs > 65535) return -7;
+  if (!V && (N % nrhs) != 0) return -5;
+  if (!X) return -8;
+  if (ldx < N) return -9;
+  if (prec != HARP_FP64 && prec != HARP_MIXED_3XTF32 && prec != HARP_MIXED_TF32 && prec != HARP_FP32)
+    return -11;
+  if (!(tol == tol)) return -12;
+  if (max_iter < 0) return -13;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  const int mode = gemm_mode(prec);
+  if (iters_out) *iters_out = 0;
+  if (resid_out) *resid_out = -1.0;
+
+  // Tensor-core GEMM scratch for this call; cleared timeout flag.
+  tc_set_workspace(ctx->tc_a, ctx->tc_a_floats, ctx->tc_b, ctx->tc_b_floats, ctx->dstatus + 2);
+  HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
+  struct Unset {
+    ~Unset() { tc_set_workspace(nullptr, 0, nullptr, 0, nullptr); }
+  } unset_on_return;
+
+  // Pivoting restricted to the diagonal blocks gives factors only the
+  // refinement can vouch for: the FP32 mode (no refinement) uses partial
+  // pivoting instead, and a factorisation that meets a zero pivot or whose
+  // refinement stalls is redone with partial pivoting.
+  const int rule = ctx->pivot_mode;
+  struct Restore {
+    harp_ctx* c;
+    int rule;
+    ~Restore() { c->pivot_mode = rule; }
+  } restore{ctx, rule};
+  const bool refined = (prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32);
+  if (rule == HARP_PIVOT_BLOCK && !refined) ctx->pivot_mode = HARP_PIVOT_PARTIAL;
+  auto fall_back = [&]() {
+    ++ctx->pivot_fallbacks;
+    ctx->pivot_mode = HARP_PIVOT_PARTIAL;
+  };
+  if (!tr) {
+    int s = factorise(ctx, N, Z, ldz, false, prec, mode, st);
+    if (s >= 1 && s <= N && ctx->pivot_mode == HARP_PIVOT_BLOCK) {
+      fall_back();
+      s = factorise(ctx, N, Z, ldz, false, prec, mode, st);
+    }
+    if (s != HARP_OK) return s;
+  } else if (!ctx->lu_valid || ctx->lu_N != N || ctx->lu_prec != lu_class(prec)) {
+    return HARP_E_STATE;
+  }
+  bool stalled = false;
+  const bool check = (ctx->lu_pivot == HARP_PIVOT_BLOCK);
+  int s = solve_factored(ctx, N, V, ldv, nrhs, X, ldx, tr, prec, mode, tol, max_iter, iters_out,
+                         resid_out, st, check, &stalled);
+  if (check && stalled) {
+    // refactor with partial pivoting (for 'T' from the context's Z64, the
+    // matrix the refinement converges to) and solve again
+    fall_back();
+    if (!tr) {
+      s = factorise(ctx, N, Z, ldz, false, prec, mode, st);
+    } else {
+      HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_z64, 0));
+      s = factorise(ctx, N, ctx->z64, ctx->ld64, true, prec, mode, st);
+    }
+    if (s != HARP_OK) return s;
+    s = solve_factored(ctx, N, V, ldv, nrhs, X, ldx, tr, prec, mode, tol, max_iter, iters_out,
+                       resid_out, st, false, &stalled);
+  }
+  return s;
+}
+
 extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
   if (!ctx) return -1;
   if (option == HARP_OPT_PIVOT) {
-    if (value != HARP_PIVOT_PARTIAL && value != HARP_PIVOT_TOURNAMENT) return -3;
+    if (value != HARP_PIVOT_PARTIAL && value != HARP_PIVOT_TOURNAMENT &&
+        value != HARP_PIVOT_BLOCK)
+      return -3;
     ctx->pivot_mode = value;
     return HARP_OK;
   }
@@ -435,10 +513,14 @@ extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
 
 extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
   if (!ctx) return -1;
-  if (option != HARP_OPT_RESIDUAL && option != HARP_OPT_PIVOT) return -2;
+  if (option != HARP_OPT_RESIDUAL && option != HARP_OPT_PIVOT &&
+      option != HARP_OPT_PIVOT_FALLBACKS)
+    return -2;
   if (!value) return -3;
   if (option == HARP_OPT_PIVOT)
     *value = ctx->pivot_mode;
+  else if (option == HARP_OPT_PIVOT_FALLBACKS)
+    *value = (int)std::min<long long>(ctx->pivot_fallbacks, INT_MAX);
   else
     *value = use_slices(ctx) ? HARP_RESIDUAL_SLICES : HARP_RESIDUAL_FF;
   return HARP_OK;

@@ -38,7 +38,8 @@ HARP_E_NONFINITE = 0x40000008
 HARP_OPT_RESIDUAL = 1
 RESIDUAL = {"slices": 0, "ff": 1}
 HARP_OPT_PIVOT = 2
-PIVOT = {"partial": 0, "tournament": 1}
+PIVOT = {"partial": 0, "tournament": 1, "block": 2}
+HARP_OPT_PIVOT_FALLBACKS = 3
 
 _lib = None
 
@@ -316,8 +317,9 @@ class Harp:
         return {k: m for m, k in RESIDUAL.items()}[v.value]
 
     def set_pivot(self, rule: str):
-        """Pivot rule of the FP32 factorisation's panels: 'partial' or
-        'tournament' (communication-avoiding LU)."""
+        """Pivot rule of the FP32 factorisation's panels: 'partial',
+        'tournament' (communication-avoiding LU) or 'block' (restricted to
+        the diagonal blocks, checked by the refinement)."""
         _check("harp_ctx_set_option",
                lib().harp_ctx_set_option(self._h, HARP_OPT_PIVOT, PIVOT[rule]))
 
@@ -326,6 +328,14 @@ class Harp:
         _check("harp_ctx_get_option", lib().harp_ctx_get_option(self._h, HARP_OPT_PIVOT,
                                                                 ct.byref(v)))
         return {k: m for m, k in PIVOT.items()}[v.value]
+
+    def pivot_fallbacks(self) -> int:
+        """Factorisations of this context whose block-restricted pivots were
+        redone with partial pivoting."""
+        v = ct.c_int(-1)
+        _check("harp_ctx_get_option", lib().harp_ctx_get_option(
+            self._h, HARP_OPT_PIVOT_FALLBACKS, ct.byref(v)))
+        return v.value
 
     def residual(self, Z: torch.Tensor, X: torch.Tensor, V: torch.Tensor, trans: str = "N",
                  stream=None) -> torch.Tensor:
