@@ -925,7 +925,8 @@ int panel_cluster(const harp_ctx* ctx, float* re, float* im, long ld, int k0, in
                   int C, int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
 int panel_calu_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb);
 int panel_calu(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb, int C,
-               int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap);
+               int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap, int restricted = 0);
+bool panel_block_plan(const harp_ctx* ctx, int M, int nb, int* csize, int* Mb);
 
 // How the FP32 panel at M remaining rows is factored: kind 3 pivoting
 // restricted to the diagonal block, 2 tournament cluster panel, 1
@@ -1153,12 +1154,17 @@ static int lookahead_update(float* re, float* im, long ld, int N, int k, int nb,
 }
 
 // The panel at column k with pivoting restricted to its nb x nb diagonal
-// block (the refinement's factors only; see HARP_PIVOT_BLOCK): partial
-// pivoting on the block (the tournament kernel with one CTA and no other
-// rows), then L21 = A21 U11^-1 for the rows below through the explicit
-// inverse of U11 (one warp per column) and one CUDA-core product in place.
+// block (the refinement's factors only; see HARP_PIVOT_BLOCK). Usually one
+// cluster launch: CTA 0 pivots the block, every CTA eliminates its rows
+// below against the block's U (the tournament kernel without its
+// tournament). Panels too tall for one cluster: the block alone (one CTA),
+// then L21 = A21 U11^-1 through the explicit inverse of U11 (one warp per
+// column) and one CUDA-core product in place.
 static int panel_block_local(harp_ctx* ctx, int N, CView<float> A, float* re, float* im, long ld,
                              int k, int nb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap) {
+  int C = 0, Mb = 0;
+  if (panel_block_plan(ctx, N - k, nb, &C, &Mb))
+    return panel_calu(ctx, re, im, ld, k, N - k, nb, C, Mb, ipiv, zero_col, st, rmap, 1);
   HARP_TRY(panel_calu(ctx, re, im, ld, k, nb, nb, 1, nb, ipiv, zero_col, st, rmap));
   const int M2 = N - k - nb;
   if (M2 <= 0) return HARP_OK;

@@ -24,15 +24,14 @@
 // matrix with another row order, so the solve and its refinement are
 // unchanged.
 //
-// Work layout (512 threads, 16 warps): warp w holds columns w + 16 j
-// (j < nb / 16) of the rows it factors in registers, lane l the rows
-// l + 32 k. Step t of a factorisation: the warp owning column t finds the
-// pivot (largest |a|^2 among rows not yet chosen, smallest row on ties: two
-// warp reductions) and writes the column's multipliers to shared memory;
-// after one block barrier every warp applies the rank-1 term to its columns.
-// The warp owning column t + 1 updates that column first and searches its
-// pivot before its other columns, so the pivot searches form the critical
-// path. Multiplier buffers are double-buffered by step parity.
+// Work layout (512 threads, 16 warps): warp w holds nb / 16 consecutive
+// columns of the rows it factors in registers, lane l the rows l + 32 k. The
+// steps of a factorisation come in groups, one group per warp: warp g picks
+// the pivots of its own columns alone (largest |a|^2 among rows not yet
+// chosen, smallest row on ties: two warp reductions), updating its later
+// columns in registers, while the other warps apply the previous group's
+// rank-1 updates, read from a two-group ring of multipliers in shared
+// memory. One block barrier per group instead of one per step.
 // A zero pivot of the root (all remaining |a| = 0) still chooses a row (the
 // smallest), with a zero inverse, and reports its column through *zero_col.
 #include <cooperative_groups.h>
@@ -60,8 +59,8 @@ constexpr int kCaMaxCluster = 16;
 struct CaLayout {
   static constexpr size_t buf = 0;                                    // 2 planes [64][kCaLd]
   static constexpr size_t u11 = buf + 2 * sizeof(float) * 64 * kCaLd;  // 2 planes [64][kCaLdU]
-  static constexpr size_t mult = u11 + 2 * sizeof(float) * 64 * kCaLdU;  // 2 planes [2][kCaStack]
-  static constexpr size_t inv = mult + 2 * sizeof(float) * 2 * kCaStack;  // 2 planes [64]
+  static constexpr size_t mult = u11 + 2 * sizeof(float) * 64 * kCaLdU;  // 2 planes [8][kCaStack]
+  static constexpr size_t inv = mult + 2 * sizeof(float) * 8 * kCaStack;  // 2 planes [64]
   static constexpr size_t ints = inv + 2 * sizeof(float) * 64;
   // int arrays: sel[64], cid[64], piv_id[64], sid[256], step_of[256], dest[256], misc[16]
   static constexpr size_t bytes = ints + sizeof(int) * (3 * 64 + 3 * kCaStack + 16);
@@ -70,7 +69,7 @@ struct CaLayout {
 struct CaSmem {
   float *bre, *bim;  // row buffer: column c at c * kCaLd, rows 0..255
   float *ure, *uim;  // the root's block: element (t, c) at c * kCaLdU + t
-  float *mre, *mim;  // multipliers by step parity: [par * kCaStack + row]
+  float *mre, *mim;  // multipliers of two groups of steps: [(group parity * 4 + step) * kCaStack + row]
   float *inv_r, *inv_i;  // 1 / pivot of each step of the latest factorisation
   int* sel;      // stack row chosen at each step of the latest factorisation
   int* cid;      // panel rows of this CTA's current candidates (misc[2] of them)
@@ -78,7 +77,7 @@ struct CaSmem {
   int* sid;      // panel row of each stack row (-1: empty)
   int* step_of;  // step a stack row was chosen at (root), or a local row's pivot step
   int* dest;     // output position (panel row) of each local row
-  int* misc;     // [0..1] pivot row by parity, [2] candidate count, [3] first zero pivot
+  int* misc;     // [2] candidate count, [3] first zero pivot
 };
 
 __device__ __forceinline__ CaSmem ca_smem(unsigned char* raw) {
@@ -88,7 +87,7 @@ __device__ __forceinline__ CaSmem ca_smem(unsigned char* raw) {
   S.ure = reinterpret_cast<float*>(raw + CaLayout::u11);
   S.uim = S.ure + 64 * kCaLdU;
   S.mre = reinterpret_cast<float*>(raw + CaLayout::mult);
-  S.mim = S.mre + 2 * kCaStack;
+  S.mim = S.mre + 8 * kCaStack;
   S.inv_r = reinterpret_cast<float*>(raw + CaLayout::inv);
   S.inv_i = S.inv_r + 64;
   int* ip = reinterpret_cast<int*>(raw + CaLayout::ints);
@@ -102,7 +101,7 @@ __device__ __forceinline__ CaSmem ca_smem(unsigned char* raw) {
   return S;
 }
 
-// The rows a warp holds: slot j = column warp + 16 j, k = row lane + 32 k.
+// The rows a warp holds: slot j = column warp * (nb / 16) + j, k = row lane + 32 k.
 template <int RPL>
 struct CaX {
   float r[4][RPL];
@@ -112,24 +111,43 @@ struct CaX {
 template <int RPL>
 __device__ __forceinline__ void ca_load(CaX<RPL>& X, const CaSmem& S, unsigned valid, int nb,
                                         int warp, int lane) {
+  const int cpw = nb >> 4;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int c = warp + 16 * j;
+    const int c = warp * cpw + j;
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
-      const bool in = c < nb && ((valid >> k) & 1u);
+      const bool in = j < cpw && ((valid >> k) & 1u);
       X.r[j][k] = in ? S.bre[c * kCaLd + lane + 32 * k] : 0.f;
       X.i[j][k] = in ? S.bim[c * kCaLd + lane + 32 * k] : 0.f;
     }
   }
 }
 
-// Pivot search of column t (slot J of the calling warp, warp t & 15) among
-// the live rows, then the column's multipliers a / pivot into the buffers of
-// parity t & 1, the pivot row into misc[t & 1] and 1 / pivot into inv[t].
+// Column ownership: warp w holds the columns w * cpw + j (slot j < cpw,
+// cpw = nb / 16 consecutive columns), lane l the rows l + 32 k. A
+// factorisation runs in groups of cpw steps: the steps of group g are the
+// columns of warp g, which picks their pivots alone (no barrier between
+// them); the other warps apply the group's rank-1 updates to their columns
+// in the next group, reading the multipliers from a ring of two groups in
+// shared memory. One block barrier per group.
+__device__ __forceinline__ float* ca_lre(const CaSmem& S, int t, int cpw) {
+  const int g = t / cpw, q = t - g * cpw;
+  return S.mre + ((g & 1) * 4 + q) * kCaStack;
+}
+__device__ __forceinline__ float* ca_lim(const CaSmem& S, int t, int cpw) {
+  const int g = t / cpw, q = t - g * cpw;
+  return S.mim + ((g & 1) * 4 + q) * kCaStack;
+}
+
+// Pivot search of column t (slot J of the calling warp) among the live rows;
+// the pivot row, 1 / pivot and the multipliers a / pivot (zero for rows not
+// live, the pivot row included) go to shared memory and, for the caller's
+// own later columns, to lr / li. Returns the pivot row.
 template <int RPL>
-__device__ __forceinline__ void ca_pick(const CaX<RPL>& X, int J, unsigned live, int t,
-                                        const CaSmem& S, int lane, bool report_zero) {
+__device__ __forceinline__ int ca_pick(const CaX<RPL>& X, int J, unsigned live, int t, int cpw,
+                                       const CaSmem& S, int lane, bool report_zero,
+                                       float (&lr)[RPL], float (&li)[RPL]) {
   float best = -1.f, br = 0.f, bi = 0.f;
   int brow = INT_MAX;
 #pragma unroll
@@ -160,34 +178,26 @@ __device__ __forceinline__ void ca_pick(const CaX<RPL>& X, int J, unsigned live,
     ir = pvr * rd;
     ii = -pvi * rd;
   }
-  const int par = t & 1;
+  const int pr = (int)rmin;
+  const unsigned now = live & ~((lane == (pr & 31)) ? (1u << (pr >> 5)) : 0u);
+  float* Lr = ca_lre(S, t, cpw);
+  float* Li = ca_lim(S, t, cpw);
 #pragma unroll
   for (int k = 0; k < RPL; ++k) {
     const float xr = X.r[J][k], xi = X.i[J][k];
-    S.mre[par * kCaStack + lane + 32 * k] = xr * ir - xi * ii;
-    S.mim[par * kCaStack + lane + 32 * k] = xr * ii + xi * ir;
+    const bool on = (now >> k) & 1u;
+    lr[k] = on ? xr * ir - xi * ii : 0.f;
+    li[k] = on ? xr * ii + xi * ir : 0.f;
+    Lr[lane + 32 * k] = lr[k];
+    Li[lane + 32 * k] = li[k];
   }
   if (lane == 0) {
-    S.misc[par] = (int)rmin;
+    S.sel[t] = pr;
     S.inv_r[t] = ir;
     S.inv_i[t] = ii;
     if (report_zero && zero && S.misc[3] > t) S.misc[3] = t;
   }
-}
-
-// Column t's multipliers a * inv[t] (pivots known) into the buffers of
-// parity t & 1 (slot J of warp t & 15).
-template <int RPL>
-__device__ __forceinline__ void ca_mult(const CaX<RPL>& X, int J, int t, const CaSmem& S,
-                                        int lane) {
-  const float ir = S.inv_r[t], ii = S.inv_i[t];
-  const int par = t & 1;
-#pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    const float xr = X.r[J][k], xi = X.i[J][k];
-    S.mre[par * kCaStack + lane + 32 * k] = xr * ir - xi * ii;
-    S.mim[par * kCaStack + lane + 32 * k] = xr * ii + xi * ir;
-  }
+  return pr;
 }
 
 // Entry of the pivot row pr in slot J (all lanes get it).
@@ -205,17 +215,26 @@ __device__ __forceinline__ void ca_rowval(const CaX<RPL>& X, int J, int pr, floa
   ui = __shfl_sync(0xffffffffu, vi, pr & 31);
 }
 
-// x -= l u on the live rows of slot J.
+// x -= l u on slot J (the multipliers of rows that must not change are 0).
 template <int RPL>
-__device__ __forceinline__ void ca_axpy(CaX<RPL>& X, int J, unsigned live, const float (&lr)[RPL],
+__device__ __forceinline__ void ca_axpy(CaX<RPL>& X, int J, const float (&lr)[RPL],
                                         const float (&li)[RPL], float ur, float ui) {
 #pragma unroll
   for (int k = 0; k < RPL; ++k) {
-    const float yr = fmaf(-lr[k], ur, fmaf(li[k], ui, X.r[J][k]));
-    const float yi = fmaf(-lr[k], ui, fmaf(-li[k], ur, X.i[J][k]));
-    const bool on = (live >> k) & 1u;
-    X.r[J][k] = on ? yr : X.r[J][k];
-    X.i[J][k] = on ? yi : X.i[J][k];
+    X.r[J][k] = fmaf(-lr[k], ur, fmaf(li[k], ui, X.r[J][k]));
+    X.i[J][k] = fmaf(-lr[k], ui, fmaf(-li[k], ur, X.i[J][k]));
+  }
+}
+
+template <int RPL>
+__device__ __forceinline__ void ca_load_mult(const CaSmem& S, int t, int cpw, int lane,
+                                             float (&lr)[RPL], float (&li)[RPL]) {
+  const float* Lr = ca_lre(S, t, cpw);
+  const float* Li = ca_lim(S, t, cpw);
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    lr[k] = Lr[lane + 32 * k];
+    li[k] = Li[lane + 32 * k];
   }
 }
 
@@ -223,105 +242,116 @@ __device__ __forceinline__ void ca_axpy(CaX<RPL>& X, int J, unsigned live, const
 // exist), nsel = min(rows, nb) steps. Leaves the stack row chosen at each
 // step in S.sel[] and 1 / pivot in S.inv; with `root`, also the step of
 // every chosen row in S.step_of[] and the first zero pivot in S.misc[3].
-// Returns this lane's mask of chosen rows. Chosen rows are not updated
-// after their step, so a chosen row keeps U in the columns from its step
-// on and its unscaled multipliers before it.
+// Returns this lane's mask of chosen rows. A chosen row takes no update
+// after its step, so it keeps U in the columns from its step on and its
+// unscaled multipliers before it.
 template <int RPL>
 __device__ unsigned ca_gepp(CaX<RPL>& X, unsigned valid, int nb, int nsel, const CaSmem& S,
                             int warp, int lane, bool root) {
+  const int cpw = nb >> 4;
+  const int ngroups = (nsel + cpw - 1) / cpw;
   unsigned chosen = 0;
-  if (warp == 0 && nsel > 0) ca_pick<RPL>(X, 0, valid, 0, S, lane, root);
-#pragma unroll
-  for (int JT = 0; JT < 4; ++JT) {
-    const int tb = 16 * JT, te = min(nsel, tb + 16);
 #pragma unroll 1
-    for (int t = tb; t < te; ++t) {
-      __syncthreads();  // step t's pivot and multipliers are in shared memory
-      const int par = t & 1;
-      const int pr = S.misc[par];
-      if (warp == 0 && lane == 0) {
-        S.sel[t] = pr;
-        if (root) S.step_of[pr] = t;
-      }
-      if (lane == (pr & 31)) chosen |= 1u << (pr >> 5);
-      const unsigned live = valid & ~chosen;
-      float lr[RPL], li[RPL];
+  for (int g = 0; g <= ngroups; ++g) {
+    // the previous group's pivots, then its updates on the columns of the
+    // warps still to pick (their columns all lie to its right)
+    if (g > 0) {
+      const int p0 = (g - 1) * cpw, p1 = min(nsel, p0 + cpw);
+      for (int t = p0; t < p1; ++t) {
+        const int pr = S.sel[t];
+        if (lane == (pr & 31)) chosen |= 1u << (pr >> 5);
+        if (root && warp == 0 && lane == 0) S.step_of[pr] = t;
+        if (warp >= g) {
+          float lr[RPL], li[RPL];
+          ca_load_mult<RPL>(S, t, cpw, lane, lr, li);
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) {
-        lr[k] = S.mre[par * kCaStack + lane + 32 * k];
-        li[k] = S.mim[par * kCaStack + lane + 32 * k];
-      }
-      const int t1 = t + 1;
-      const bool next = (t1 < nsel) && (warp == (t1 & 15));
-      if (next) {  // column t + 1 first, then its pivot search
-        float ur, ui;
-        if ((t1 >> 4) == JT) {
-          ca_rowval<RPL>(X, JT, pr, ur, ui);
-          ca_axpy<RPL>(X, JT, live, lr, li, ur, ui);
-          ca_pick<RPL>(X, JT, live, t1, S, lane, root);
-        } else if (JT + 1 < 4) {
-          const int J1 = (JT + 1 < 4) ? JT + 1 : 3;
-          ca_rowval<RPL>(X, J1, pr, ur, ui);
-          ca_axpy<RPL>(X, J1, live, lr, li, ur, ui);
-          ca_pick<RPL>(X, J1, live, t1, S, lane, root);
+          for (int j = 0; j < 4; ++j) {
+            if (j >= cpw) continue;
+            float ur, ui;
+            ca_rowval<RPL>(X, j, pr, ur, ui);
+            ca_axpy<RPL>(X, j, lr, li, ur, ui);
+          }
         }
       }
+    }
+    if (g < ngroups && warp == g) {
+      // the owner: pick its columns in order, each step applied at once to
+      // its later columns (registers only)
+      const int t0 = g * cpw, t1 = min(nsel, t0 + cpw);
+      unsigned mine = chosen;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int c = warp + 16 * j;
-        if (c <= t || c >= nb || (next && c == t1)) continue;
-        float ur, ui;
-        ca_rowval<RPL>(X, j, pr, ur, ui);
-        ca_axpy<RPL>(X, j, live, lr, li, ur, ui);
+        const int t = t0 + j;
+        if (j >= cpw || t >= t1) continue;
+        float lr[RPL], li[RPL];
+        const int pr = ca_pick<RPL>(X, j, valid & ~mine, t, cpw, S, lane, root, lr, li);
+        if (lane == (pr & 31)) mine |= 1u << (pr >> 5);
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) {
+          if (j2 <= j || j2 >= cpw) continue;
+          float ur, ui;
+          ca_rowval<RPL>(X, j2, pr, ur, ui);
+          ca_axpy<RPL>(X, j2, lr, li, ur, ui);
+        }
       }
     }
+    __syncthreads();  // group g's pivots and multipliers are in shared memory
   }
-  __syncthreads();  // the last step's shared data has been read
   return chosen;
 }
 
 // Elimination with the pivots known (phase 3): the live rows in X against
 // the root's block (U in S.ure/uim on and above the diagonal, 1 / pivot in
-// S.inv). Afterwards x * inv[c] is the L entry of column c of every live
-// row.
+// S.inv), in the groups of ca_gepp. Afterwards x * inv[c] is the L entry of
+// column c of every live row.
 template <int RPL>
 __device__ void ca_elim(CaX<RPL>& X, unsigned live, int nb, const CaSmem& S, int warp, int lane) {
-  if (warp == 0) ca_mult<RPL>(X, 0, 0, S, lane);
-#pragma unroll
-  for (int JT = 0; JT < 4; ++JT) {
-    const int tb = 16 * JT, te = min(nb, tb + 16);
+  const int cpw = nb >> 4;
+  const int ngroups = nb / cpw;
 #pragma unroll 1
-    for (int t = tb; t < te; ++t) {
-      __syncthreads();
-      const int par = t & 1;
-      float lr[RPL], li[RPL];
+  for (int g = 0; g <= ngroups; ++g) {
+    if (g > 0 && warp >= g) {
+      const int p0 = (g - 1) * cpw;
+      for (int t = p0; t < p0 + cpw; ++t) {
+        float lr[RPL], li[RPL];
+        ca_load_mult<RPL>(S, t, cpw, lane, lr, li);
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) {
-        lr[k] = S.mre[par * kCaStack + lane + 32 * k];
-        li[k] = S.mim[par * kCaStack + lane + 32 * k];
-      }
-      const int t1 = t + 1;
-      const bool next = (t1 < nb) && (warp == (t1 & 15));
-      if (next) {
-        const float ur = S.ure[t1 * kCaLdU + t], ui = S.uim[t1 * kCaLdU + t];
-        if ((t1 >> 4) == JT) {
-          ca_axpy<RPL>(X, JT, live, lr, li, ur, ui);
-          ca_mult<RPL>(X, JT, t1, S, lane);
-        } else if (JT + 1 < 4) {
-          const int J1 = (JT + 1 < 4) ? JT + 1 : 3;
-          ca_axpy<RPL>(X, J1, live, lr, li, ur, ui);
-          ca_mult<RPL>(X, J1, t1, S, lane);
+        for (int j = 0; j < 4; ++j) {
+          if (j >= cpw) continue;
+          const int c = warp * cpw + j;
+          ca_axpy<RPL>(X, j, lr, li, S.ure[c * kCaLdU + t], S.uim[c * kCaLdU + t]);
         }
       }
+    }
+    if (g < ngroups && warp == g) {
+      const int t0 = g * cpw;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int c = warp + 16 * j;
-        if (c <= t || c >= nb || (next && c == t1)) continue;
-        ca_axpy<RPL>(X, j, live, lr, li, S.ure[c * kCaLdU + t], S.uim[c * kCaLdU + t]);
+        if (j >= cpw) continue;
+        const int t = t0 + j;
+        const float ir = S.inv_r[t], ii = S.inv_i[t];
+        float lr[RPL], li[RPL];
+        float* Lr = ca_lre(S, t, cpw);
+        float* Li = ca_lim(S, t, cpw);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const float xr = X.r[j][k], xi = X.i[j][k];
+          const bool on = (live >> k) & 1u;
+          lr[k] = on ? xr * ir - xi * ii : 0.f;
+          li[k] = on ? xr * ii + xi * ir : 0.f;
+          Lr[lane + 32 * k] = lr[k];
+          Li[lane + 32 * k] = li[k];
+        }
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) {
+          if (j2 <= j || j2 >= cpw) continue;
+          const int c = t0 + j2;
+          ca_axpy<RPL>(X, j2, lr, li, S.ure[c * kCaLdU + t], S.uim[c * kCaLdU + t]);
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // The root keeps the final factorisation of its chosen rows: row t (its
@@ -330,10 +360,11 @@ __device__ void ca_elim(CaX<RPL>& X, unsigned live, int nb, const CaSmem& S, int
 template <int RPL>
 __device__ __forceinline__ void ca_keep(const CaX<RPL>& X, unsigned chosen, int nb,
                                         const CaSmem& S, int warp, int lane) {
+  const int cpw = nb >> 4;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int c = warp + 16 * j;
-    if (c >= nb) continue;
+    const int c = warp * cpw + j;
+    if (j >= cpw) continue;
 #pragma unroll
     for (int k = 0; k < RPL; ++k)
       if ((chosen >> k) & 1u) {
@@ -380,7 +411,7 @@ template <int RPL>
 __global__ void __launch_bounds__(kCaThreads, 1) panel_calu_kernel(float* Are, float* Aim, long lda,
                                                                    int k0, int M, int nb, int Mb,
                                                                    int* ipiv, int* zero_col,
-                                                                   int* rmap) {
+                                                                   int* rmap, int restricted) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
@@ -393,9 +424,12 @@ __global__ void __launch_bounds__(kCaThreads, 1) panel_calu_kernel(float* Are, f
   const float* gim = Aim + (size_t)(k0 + r0) + (size_t)k0 * lda;
 
   // ---- 1. the CTA's block: originals into the buffer (one round of
-  // asynchronous copies), partial pivoting on it in registers
-  for (int e = tid; e < rows * nb; e += kCaThreads) {
-    const int c = e / rows, r = e - c * rows;
+  // asynchronous copies), partial pivoting on it in registers. With
+  // `restricted` only CTA 0 pivots, on the panel's first nb rows (the
+  // diagonal block), and there is no tournament.
+  const int lrows = restricted ? (crank == 0 ? min(rows, nb) : 0) : rows;
+  for (int e = tid; e < lrows * nb; e += kCaThreads) {
+    const int c = e / lrows, r = e - c * lrows;
     const unsigned dr = (unsigned)__cvta_generic_to_shared(S.bre + c * kCaLd + r);
     const unsigned di = (unsigned)__cvta_generic_to_shared(S.bim + c * kCaLd + r);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr),
@@ -407,22 +441,24 @@ __global__ void __launch_bounds__(kCaThreads, 1) panel_calu_kernel(float* Are, f
   if (tid == 0) S.misc[3] = INT_MAX;
   for (int r = tid; r < kCaStack; r += kCaThreads) S.dest[r] = r0 + r;
   __syncthreads();
-  unsigned valid = 0;
+  unsigned valid = 0, lvalid = 0;
 #pragma unroll
-  for (int k = 0; k < RPL; ++k)
+  for (int k = 0; k < RPL; ++k) {
     if (lane + 32 * k < rows) valid |= 1u << k;
-  const bool single = (C == 1);  // the CTA's own pick is the panel's
-  {
+    if (lane + 32 * k < lrows) lvalid |= 1u << k;
+  }
+  const bool single = (C == 1) || restricted;  // CTA 0's own pick is the panel's
+  if (lrows > 0) {
     CaX<RPL> X;
-    ca_load<RPL>(X, S, valid, nb, warp, lane);
-    const unsigned chosen = ca_gepp<RPL>(X, valid, nb, min(rows, nb), S, warp, lane, single);
+    ca_load<RPL>(X, S, lvalid, nb, warp, lane);
+    const unsigned chosen = ca_gepp<RPL>(X, lvalid, nb, min(lrows, nb), S, warp, lane, single);
     if (single) ca_keep<RPL>(X, chosen, nb, S, warp, lane);
   }
 
   // ---- 2. the tournament: levels of stride s = 1, 4, 16
   int ncand = min(rows, nb);
   bool local = true;  // S.sel indexes the CTA's own block (else the stack)
-  for (int s = 1; s < C; s *= 4) {
+  for (int s = 1; !restricted && s < C; s *= 4) {
     const bool active = (crank % s) == 0;
     if (active) ca_gather(S, ncand, nb, tid, local, r0);
     cluster.sync();  // every active CTA's candidates are in rows 0..63
@@ -506,12 +542,13 @@ __global__ void __launch_bounds__(kCaThreads, 1) panel_calu_kernel(float* Are, f
     if (((valid >> k) & 1u) && S.step_of[lane + 32 * k] < nb) piv |= 1u << k;
   const unsigned live = valid & ~piv;
   CaX<RPL> X;  // the originals, again from the panel (untouched until the write-back)
+  const int cpw = nb >> 4;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int c = warp + 16 * j;
+    const int c = warp * cpw + j;
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
-      const bool in = c < nb && ((live >> k) & 1u);
+      const bool in = j < cpw && ((live >> k) & 1u);
       X.r[j][k] = in ? gre[lane + 32 * k + (size_t)c * lda] : 0.f;
       X.i[j][k] = in ? gim[lane + 32 * k + (size_t)c * lda] : 0.f;
     }
@@ -526,8 +563,8 @@ __global__ void __launch_bounds__(kCaThreads, 1) panel_calu_kernel(float* Are, f
   float* oim = Aim + (size_t)k0 + (size_t)k0 * lda;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int c = warp + 16 * j;
-    if (c >= nb) continue;
+    const int c = warp * cpw + j;
+    if (j >= cpw) continue;
     const float ir = S.inv_r[c], ii = S.inv_i[c];
 #pragma unroll
     for (int k = 0; k < RPL; ++k)
@@ -554,7 +591,7 @@ __global__ void __launch_bounds__(kCaThreads, 1) panel_calu_kernel(float* Are, f
   }
 }
 
-using CaluKernel = void (*)(float*, float*, long, int, int, int, int, int*, int*, int*);
+using CaluKernel = void (*)(float*, float*, long, int, int, int, int, int*, int*, int*, int);
 
 static CaluKernel calu_kernel_for(int Mb, int* idx) {
   const int rpl = (Mb + 31) / 32;
@@ -650,8 +687,30 @@ int panel_calu_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int* Mb
   return 0;
 }
 
+// Cluster size and rows per CTA for a panel pivoted within its diagonal
+// block: only the elimination of the rows below is spread over the CTAs,
+// so take the smallest cluster that brings a CTA to <= 192 rows (else the
+// largest that fits). Returns false when no resident cluster holds the
+// panel (at most 16 CTAs of 256 rows).
+bool panel_block_plan(const harp_ctx* ctx, int M, int nb, int* csize, int* Mb) {
+  if (ctx->smem_optin < CaLayout::bytes || M < nb || nb % 16 != 0 || nb > kCaMaxNb) return false;
+  int best = 0;
+  for (int C : {1, 2, 4, 8, 16}) {
+    const int mb = (M + C - 1) / C;
+    if (mb > kCaStack || mb < nb) continue;
+    if (C > 1 && (C - 1) * mb >= M) continue;
+    if (!calu_resident(C, mb)) continue;
+    best = C;
+    if (mb <= 192) break;
+  }
+  if (!best) return false;
+  *csize = best;
+  *Mb = (M + best - 1) / best;
+  return true;
+}
+
 int panel_calu(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M, int nb, int C,
-               int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap) {
+               int Mb, int* ipiv, int* zero_col, cudaStream_t st, int* rmap, int restricted) {
   (void)ctx;
   if (Mb > kCaStack || nb % 16 != 0 || nb > kCaMaxNb || M < nb || C > kCaMaxCluster || C < 1 ||
       (long)C * Mb < M)
@@ -672,7 +731,8 @@ int panel_calu(const harp_ctx* ctx, float* re, float* im, long ld, int k0, int M
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ProfScope ps(HARP_K_PANEL, 4.0 * M * nb * (double)(nb - 1), st);
-  HARP_CUDA(cudaLaunchKernelEx(&cfg, kern, re, im, ld, k0, M, nb, Mb, ipiv, zero_col, rmap));
+  HARP_CUDA(cudaLaunchKernelEx(&cfg, kern, re, im, ld, k0, M, nb, Mb, ipiv, zero_col, rmap,
+                               restricted));
   HARP_LAUNCHED();
   return HARP_OK;
 }
