@@ -42,6 +42,11 @@ def lib():
         L.oracle_port_objective_grad.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, vp,
                                                  ct.c_double, vp, ct.c_int, vp, ct.c_long, vp, vp]
         L.oracle_port_objective_grad.restype = ct.c_int
+        L.oracle_eep.argtypes = [ct.c_int, ct.c_int, vp, ct.c_double, vp, ct.c_long, ct.c_int,
+                                 ct.c_int, vp, vp, vp, vp]
+        L.oracle_eep.restype = None
+        L.oracle_pattern_error.argtypes = [ct.c_int, vp, vp, ct.c_double, vp]
+        L.oracle_pattern_error.restype = None
         L.oracle_wavenumber.argtypes = [ct.c_double]
         L.oracle_wavenumber.restype = ct.c_double
         L.oracle_num_threads.restype = ct.c_int
@@ -202,3 +207,33 @@ def relerr(a, b) -> float:
     b = np.asarray(b)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def eep(pos, freq_hz, X, Nm: int, ux, uy, F) -> np.ndarray:
+    """Embedded element patterns of every column (port) of X, Eq. 5 term by
+    term (Section II-C): E[comp, m, d] for comp 0 = theta, 1 = phi.
+    X: (Na*Nm, nports); ux, uy: (D,) direction cosines; F: (2, D, Nm) MBF
+    patterns."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    X = np.asfortranarray(X, dtype=np.complex128)
+    ux = np.ascontiguousarray(ux, dtype=np.float64)
+    uy = np.ascontiguousarray(uy, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    Na, nports, D = pos.shape[0], X.shape[1], ux.shape[0]
+    assert X.shape[0] == Na * Nm and F.shape == (2, D, Nm) and uy.shape == (D,)
+    E = np.zeros((2, nports, D), dtype=np.complex128)
+    lib().oracle_eep(Na, Nm, _p(pos), float(freq_hz), _p(X), X.shape[0], nports, D, _p(ux),
+                     _p(uy), _p(F), _p(E))
+    return E
+
+
+def pattern_error(E, Eref, norm: float) -> np.ndarray:
+    """Eq. 8 (Section III-A): sqrt(|dE_theta|^2 + |dE_phi|^2) / norm per
+    direction; E, Eref: (2, ...) theta and phi components."""
+    E = np.ascontiguousarray(E, dtype=np.complex128)
+    Eref = np.ascontiguousarray(Eref, dtype=np.complex128)
+    assert E.shape == Eref.shape and E.shape[0] == 2
+    n = E[0].size
+    eps = np.zeros(n)
+    lib().oracle_pattern_error(n, _p(E), _p(Eref), float(norm), _p(eps))
+    return eps.reshape(E.shape[1:])

@@ -374,3 +374,43 @@ int oracle_port_objective_grad(int Na, int Nm, int P, int Q, const double* pos, 
   free(ipiv);
   return rc;
 }
+
+/* ---- Section II-C, Eq. 5 and 6: embedded element patterns -----------------
+ * The pattern of the array for the MBF coefficients c_ij (MBF j on antenna
+ * i) is the double sum of Eq. 5,
+ *   F(u) = sum_i sum_j c_ij F_j(u) e^{jk (u_x x_i + u_y y_i)},
+ * evaluated here term by term as written (no factoring by the array
+ * factor of Eq. 6). The embedded element pattern of port m is the pattern
+ * of the currents for excitation at port m: c_ij = X[i*Nm + j, m].
+ *   ux, uy   direction cosines of the D directions
+ *   F        MBF patterns, index [comp][d][j] (comp 0: theta, 1: phi)
+ *   E        output, index [comp][m][d] */
+void oracle_eep(int Na, int Nm, const double* pos, double freq_hz, const cplx* X, long ldx,
+                int nports, int D, const double* ux, const double* uy, const cplx* F, cplx* E) {
+  const double k = oracle_wavenumber(freq_hz);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int m = 0; m < nports; ++m)
+    for (int d = 0; d < D; ++d)
+      for (int comp = 0; comp < 2; ++comp) {
+        cplx s = 0.0;
+        for (int i = 0; i < Na; ++i)
+          for (int j = 0; j < Nm; ++j) {
+            const cplx c = X[(size_t)i * Nm + j + (size_t)m * ldx];
+            const cplx Fj = F[((size_t)comp * D + d) * Nm + j];
+            const double ph = k * (ux[d] * pos[2 * i] + uy[d] * pos[2 * i + 1]);
+            s += c * Fj * cexp(I * ph);
+          }
+        E[((size_t)comp * nports + m) * D + d] = s;
+      }
+}
+
+/* Eq. 8: the error between two patterns in each direction,
+ *   eps = sqrt(|E_theta - Eref_theta|^2 + |E_phi - Eref_phi|^2) / norm,
+ * with the fields normalised by `norm` (the maximum of the isolated
+ * antenna's pattern). E, Eref: [comp][n]; eps: [n]. */
+void oracle_pattern_error(int n, const cplx* E, const cplx* Eref, double norm, double* eps) {
+  for (int q = 0; q < n; ++q) {
+    const double a = cabs(E[q] - Eref[q]), b = cabs(E[n + q] - Eref[n + q]);
+    eps[q] = sqrt(a * a + b * b) / norm;
+  }
+}

@@ -222,3 +222,32 @@ def small(Na: int, Nm: int, P: int = 3, Q: int = 2, seed_cfg: int = 9,
     radius = max(2.0 * min_sep, min_sep * math.sqrt(Na / 0.4) / 2.0 * 1.05)
     return make_problem(f"small-{Na}x{Nm}", Na, radius, min_sep, freq_hz, Nm, P, Q,
                         cfg=seed_cfg, layout=layout)
+
+
+# ---- Pattern inputs (Section II-C): directions and synthetic MBF patterns.
+# The SKALA MBF patterns are not available; smooth seeded stand-ins take
+# their place.
+
+def direction_grid(d_theta_deg: float = 1.0, d_phi_deg: float = 1.0):
+    """Upper-hemisphere grid theta in [0, 90] deg, phi in [0, 360) deg:
+    (theta, phi) in radians and the direction cosines (ux, uy), each (D,),
+    theta major."""
+    th = np.deg2rad(np.arange(0.0, 90.0 + 1e-9, d_theta_deg))
+    ph = np.deg2rad(np.arange(0.0, 360.0 - 1e-9, d_phi_deg))
+    T, Ph = np.meshgrid(th, ph, indexing="ij")
+    T, Ph = T.ravel(), Ph.ravel()
+    return T, Ph, np.sin(T) * np.cos(Ph), np.sin(T) * np.sin(Ph)
+
+
+def mbf_patterns(Nm: int, theta: np.ndarray, phi: np.ndarray, seed: int) -> np.ndarray:
+    """(2, D, Nm) complex128 patterns [comp][d][j] (comp 0 = theta, 1 = phi):
+    F_j = sum_{l=0..2} a_jl cos(theta)^l e^{i m_j phi}, with seeded
+    a_jl ~ CN(0,1) per component and m_j = j mod 3, smooth in both angles
+    like the patterns of small antennas."""
+    rng = np.random.default_rng(seed)
+    a = complex_normal(rng, (2, Nm, 3))
+    m = np.arange(Nm) % 3
+    ct = np.cos(theta)
+    powers = np.stack([np.ones_like(ct), ct, ct * ct], axis=1)  # (D, 3)
+    F = np.einsum("dl,cjl->cdj", powers, a) * np.exp(1j * np.outer(phi, m))[None]
+    return np.ascontiguousarray(F)

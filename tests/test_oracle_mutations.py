@@ -12,7 +12,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "harp_oracle.c")
-PINS = ["tests/test_oracle_fill.py", "tests/test_oracle_solve.py", "tests/test_oracle_grad.py"]
+PINS = ["tests/test_oracle_fill.py", "tests/test_oracle_solve.py", "tests/test_oracle_grad.py",
+        "tests/test_oracle_eep.py"]
 
 MUTATIONS = {
     "phase_sign": ("const cplx phase = cexp(-I * k * r); /* e^{-jkr}",
@@ -44,6 +45,14 @@ MUTATIONS = {
                                    "for (int i = 0; i < k; ++i) s -= conj(A[i + (size_t)k * lda]) * b[i];"),
     "adjoint_contraction_transposed": ("G += Lam[i + (size_t)c * ld] * X[j + (size_t)c * ld];",
                                        "G += Lam[j + (size_t)c * ld] * X[i + (size_t)c * ld];"),
+    "eep_phase_sign": ("s += c * Fj * cexp(I * ph);", "s += c * Fj * cexp(-I * ph);"),
+    "eep_current_index_transposed": ("const cplx c = X[(size_t)i * Nm + j + (size_t)m * ldx];",
+                                     "const cplx c = X[(size_t)j * Na + i + (size_t)m * ldx];"),
+    "eep_pattern_conjugated": ("const cplx Fj = F[((size_t)comp * D + d) * Nm + j];",
+                               "const cplx Fj = conj(F[((size_t)comp * D + d) * Nm + j]);"),
+    "eep_uy_dropped": ("const double ph = k * (ux[d] * pos[2 * i] + uy[d] * pos[2 * i + 1]);",
+                       "const double ph = k * (ux[d] * pos[2 * i]);"),
+    "pattern_error_phi_dropped": ("eps[q] = sqrt(a * a + b * b) / norm;", "eps[q] = a / norm;"),
 }
 
 
@@ -62,6 +71,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     # the pin file most likely to catch this mistake first (-x stops there)
     first = ("tests/test_oracle_grad.py" if name.startswith(("grad_", "adjoint_", "objective_"))
              else "tests/test_oracle_solve.py" if name.startswith(("lu_", "pivot_", "transpose_"))
+             else "tests/test_oracle_eep.py" if name.startswith(("eep_", "pattern_"))
              else "tests/test_oracle_fill.py")
     pins = [first] + [f for f in PINS if f != first]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
