@@ -140,6 +140,42 @@ def wideband_throughput(device: int, n_ctx: int = 4, n_freq: int = 64) -> dict:
             "timing": "host wall clock around one synchronous batch call"}
 
 
+def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:
+    """The embedded element patterns of all 256 ports of the station on the
+    1-degree hemisphere grid (91 x 360 directions) from the step's solution
+    (Section II-C): device time of harp_eep with CUDA events, its
+    algorithmic flops (the array-factor product, 8 D Na Nm nports) against
+    the TF32 tensor peak."""
+    import torch
+    from paper_1702_03781_gb300 import roofline
+    from paper_1702_03781_gb300 import synth
+    th, ph, ux, uy = synth.direction_grid(1.0, 1.0)
+    F = torch.from_numpy(synth.mbf_patterns(p.Nm, th, ph, 73)).to(dev)
+    pos = torch.from_numpy(p.pos).to(dev)
+    uxt, uyt = torch.from_numpy(ux).to(dev), torch.from_numpy(uy).to(dev)
+    E = torch.empty((2, p.Na, th.size), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        h.eep(pos, p.freq_hz, X, p.Nm, uxt, uyt, F, out=E)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.eep(pos, p.freq_hz, X, p.Nm, uxt, uyt, F, out=E)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    h.sync()
+    t = statistics.median(ms)
+    flops = 8.0 * th.size * p.Na * p.Nm * p.Na
+    _, peak, unit, note = roofline.peak_for("gemm", "tensor_tf32", peaks)
+    achieved = flops / (t * 1e-3) / 1e12
+    return {"directions": int(th.size), "ports": p.Na, "ms": round(t, 4),
+            "flops": flops, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": unit,
+            "frac": round(achieved / peak, 4), "peak_source": note + " (of measured)",
+            "timing": "CUDA events around harp_eep, median of 5 after 2 warm-ups"}
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -365,6 +401,7 @@ def main():
             "roofline_kernels": roof_all,
             "kernel_shares": shares,
         }
+        line["eep"] = eep_throughput(h, p, X, dev, peaks)
         if not args.no_wideband:
             line["wideband"] = wideband_throughput(local)
         if not args.no_cpu_baseline:

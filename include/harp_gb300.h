@@ -339,6 +339,52 @@ int harp_solve_batch(harp_ctx** ctxs, int n_ctx, harp_problem* probs, int n_prob
 int harp_port_objective(int Na, int Nm, const double* X, int ldx, double* P, double* J,
                         double* W, int ldw, void* stream);
 
+/* ---- Patterns (Section II-C) ---------------------------------------------
+ * Embedded element patterns of the ports from the solution of the port
+ * excitations: Eq. 5 with the sums swapped as in Eq. 6,
+ *   E_m(u) = sum_j F_j(u) sum_i X[i*Nm + j, m] e^{jk (u_x x_i + u_y y_i)},
+ * for the D directions u of the caller's grid (direction cosines ux, uy)
+ * and both field components. The array factors of all MBFs and ports are
+ * one product of the phase matrix e^{jk u.x_i} (made on the device, a
+ * chunk of directions at a time) and the currents, on the tensor cores
+ * with three-term TF32 products and FP32 accumulation; the result carries
+ * FP32-level error (relative ~1e-6 of the pattern's scale).
+ *   ctx          context (its tensor-core workspace; the call grows the
+ *                context's pattern workspace on first use)        [1]
+ *   Na, Nm       antennas, MBFs per antenna                       [2, 3]
+ *   pos          double [Na][2], metres                           [4]
+ *   freq_hz      frequency (> 0); k = 2 pi f / c0                 [5]
+ *   X, ldx       c128 (Na Nm) x nports, column-major: the MBF
+ *                coefficients for excitation at each port (the
+ *                solution of mbf_solve)                           [6, 7]
+ *   nports       ports (columns of X)                             [8]
+ *   D            directions                                       [9]
+ *   ux, uy       double [D]: direction cosines sin(theta) cos(phi),
+ *                sin(theta) sin(phi)                              [10, 11]
+ *   F            c128 [2][D][Nm]: the MBF patterns, theta then phi
+ *                component, per direction and MBF                 [12]
+ *   E            output c64 [2][nports][D]: the patterns, theta then
+ *                phi component, per port and direction            [13]
+ * Device pointers; asynchronous on `stream` (a bounded wait that gives up
+ * is reported by harp_ctx_sync). The array pattern of an excitation law w
+ * over the ports is the call with X w as its single column. Errors: -i
+ * argument i; HARP_E_UNSUPPORTED when Na, Nm * nports or nports exceed
+ * 65535; HARP_E_NOMEM; HARP_E_CUDA. */
+int harp_eep(harp_ctx* ctx, int Na, int Nm, const double* pos, double freq_hz, const double* X,
+             int ldx, int nports, int D, const double* ux, const double* uy, const double* F,
+             float* E, void* stream);
+
+/* The error between two patterns in each of n directions (Eq. 8, Section
+ * III-A): eps[q] = sqrt(|E_theta - Eref_theta|^2 + |E_phi - Eref_phi|^2)
+ * / norm, with norm the maximum of the isolated antenna's pattern.
+ *   n       directions (times ports)                    [1]
+ *   E, Eref c64 [2][n]: theta then phi components       [2, 3]
+ *   norm    > 0                                         [4]
+ *   eps     output float [n]                            [5]
+ * Device pointers; asynchronous on `stream`; no context. */
+int harp_pattern_error(long n, const float* E, const float* Eref, double norm, float* eps,
+                       void* stream);
+
 /* Allocation-free variant of harp_fill_adjoint (no counterpart in the paper:
  * it exists for callers that cannot allocate device memory, for instance an
  * application whose allocator owns all device memory or that runs under a

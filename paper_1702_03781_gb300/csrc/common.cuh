@@ -203,6 +203,10 @@ struct harp_ctx {
   // blocks) that the background fill reads, fin_bytes long (grown on demand).
   void* fin;
   size_t fin_bytes;
+  // Workspace of harp_eep (the currents by MBF, a chunk of the phase matrix
+  // and of the array factors), eep_bytes long (grown on demand).
+  void* eep_ws;
+  size_t eep_bytes;
   // U11^-1 of the latest block-local panel (2 planes of 64 x 64 floats).
   float* blk_uinv;
   // Factorisations whose pivoting restricted to the diagonal blocks did not

@@ -46,6 +46,7 @@ static void free_all(harp_ctx* c) {
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->fin) cudaFree(c->fin);
   if (c->blk_uinv) cudaFree(c->blk_uinv);
+  if (c->eep_ws) cudaFree(c->eep_ws);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
   for (int q = 0; q < 2; ++q) {

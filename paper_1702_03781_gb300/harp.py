@@ -96,6 +96,10 @@ def lib():
         L.harp_residual.argtypes = [vp, i, vp, i, vp, i, vp, i, i, vp, i, ct.c_char, vp]
         L.harp_wait_check.argtypes = [vp, i, vp]
         L.harp_ctx_sync.argtypes = [vp, vp]
+        L.harp_eep.argtypes = [vp, i, i, vp, d, vp, i, i, i, vp, vp, vp, vp, vp]
+        L.harp_eep.restype = i
+        L.harp_pattern_error.argtypes = [l, vp, vp, d, vp, vp]
+        L.harp_pattern_error.restype = i
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_sync", "harp_ctx_z64",
                    "harp_fill",
                    "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
@@ -359,6 +363,38 @@ class Harp:
         (HARP_OK) or never arrived at (HARP_E_TIMEOUT after ~0.5 s)."""
         return lib().harp_wait_check(self._h, 1 if release else 0, _stream(stream))
 
+    # -- patterns (Section II-C) --------------------------------------------
+    def eep(self, pos: torch.Tensor, freq_hz: float, X: torch.Tensor, Nm: int,
+            ux: torch.Tensor, uy: torch.Tensor, F: torch.Tensor, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+        """Embedded element patterns (2, nports, D) complex64 of the ports
+        whose MBF coefficients are the columns of X (N x nports), for the
+        directions (ux, uy) and the MBF patterns F (2, D, Nm)."""
+        if pos.dim() != 2 or pos.shape[1] != 2:
+            raise ValueError(f"pos must be (Na, 2), got {tuple(pos.shape)}")
+        Na = pos.shape[0]
+        if X.dim() != 2 or X.shape[0] != Na * Nm:
+            raise ValueError(f"X must be ({Na * Nm}, nports), got {tuple(X.shape)}")
+        if ux.dim() != 1 or tuple(uy.shape) != tuple(ux.shape):
+            raise ValueError("ux and uy must be (D,)")
+        D = ux.shape[0]
+        _expect_shape("F", F, (2, D, Nm))
+        nports = X.shape[1]
+        pos = pos.to(torch.float64).contiguous()
+        X = as_colmajor(X.to(torch.complex128))
+        ux = ux.to(torch.float64).contiguous()
+        uy = uy.to(torch.float64).contiguous()
+        F = F.to(torch.complex128).contiguous()
+        if out is None:
+            out = torch.empty((2, nports, D), dtype=torch.complex64, device=pos.device)
+        elif tuple(out.shape) != (2, nports, D) or out.dtype != torch.complex64 \
+                or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous (2, {nports}, {D}) complex64 tensor")
+        _check("harp_eep", lib().harp_eep(
+            self._h, Na, Nm, _ptr(pos), float(freq_hz), _ptr(X), _ld(X), nports, D, _ptr(ux),
+            _ptr(uy), _ptr(F), _ptr(out), _stream(stream)))
+        return out
+
     # -- adjoint ------------------------------------------------------------
     def fill_adjoint(self, pos: torch.Tensor, freq_hz: float, coef: torch.Tensor,
                      Lam: torch.Tensor, X: torch.Tensor, prec="fp64", stream=None) -> torch.Tensor:
@@ -492,3 +528,18 @@ def fill_adjoint_noalloc(pos: torch.Tensor, freq_hz: float, coef: torch.Tensor, 
             Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(Lam), _ptr(X), _ld(X),
             X.shape[1], _ptr(grad), pr, _stream(stream)))
     return grad
+
+
+def pattern_error(E: torch.Tensor, Eref: torch.Tensor, norm: float, stream=None) -> torch.Tensor:
+    """Eq. 8 per direction: sqrt(|dE_theta|^2 + |dE_phi|^2) / norm for
+    complex64 patterns (2, ...) of the same shape; float32 (...)."""
+    if E.shape != Eref.shape or E.dim() < 1 or E.shape[0] != 2:
+        raise ValueError("E and Eref must have the same shape (2, ...)")
+    if E.dtype != torch.complex64 or Eref.dtype != torch.complex64:
+        raise ValueError("E and Eref must be complex64")
+    E, Eref = E.contiguous(), Eref.contiguous()
+    eps = torch.empty(E.shape[1:], dtype=torch.float32, device=E.device)
+    n = eps.numel()
+    _check("harp_pattern_error", lib().harp_pattern_error(n, _ptr(E), _ptr(Eref), float(norm),
+                                                          _ptr(eps), _stream(stream)))
+    return eps
