@@ -385,6 +385,29 @@ int harp_eep(harp_ctx* ctx, int Na, int Nm, const double* pos, double freq_hz, c
 int harp_pattern_error(long n, const float* E, const float* Eref, double norm, float* eps,
                        void* stream);
 
+/* ---- HARP model construction (Section II-A, Eq. 2-3; Section II-B) ------
+ * The coefficients c_pq^{TS} of Eq. 3 from samples of the complementary
+ * interaction B_TS (Eq. 2) on a polar grid: angles alpha_a = 2 pi a /
+ * Nalpha (regular), radii given as d_l = 1/r_l (the paper samples them
+ * regularly in 1/r). Per MBF pair: the DFT over alpha (the improved model's
+ * DFT estimate of the harmonics), then a least-squares polynomial in d for
+ * each harmonic (thin QR of the Vandermonde matrix), all in FP64. Exact
+ * for a model band-limited to |p| <= P when Nalpha >= 2P + 1 and
+ * Nd >= Q + 1.
+ *   Nm, P, Q     model sizes (Q + 1 <= 16)                        [1, 2, 3]
+ *   Nd, Nalpha   grid sizes (Nd >= Q + 1, Nalpha >= 2P + 1)       [4, 5]
+ *   d            double [Nd]: the sampled d = 1/r                 [6]
+ *   B            c128 [Nm][Nm][Nd][Nalpha]: samples B_TS(d_l, alpha_a) [7]
+ *   coef         output c128 [Nm][Nm][2P+1][Q+1], the layout harp_fill
+ *                reads                                            [8]
+ *   rms          output double [Nm][Nm] (or NULL): root-mean-square
+ *                residual of the fitted model on the samples      [9]
+ * Device pointers; asynchronous on `stream`; no context. Errors: -i
+ * argument i; HARP_E_UNSUPPORTED when Q + 1 > 16 or one pair's samples
+ * exceed the shared memory of a CTA. */
+int harp_model_fit(int Nm, int P, int Q, int Nd, int Nalpha, const double* d, const double* B,
+                   double* coef, double* rms, void* stream);
+
 /* Allocation-free variant of harp_fill_adjoint (no counterpart in the paper:
  * it exists for callers that cannot allocate device memory, for instance an
  * application whose allocator owns all device memory or that runs under a

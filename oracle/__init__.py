@@ -237,3 +237,36 @@ def pattern_error(E, Eref, norm: float) -> np.ndarray:
     eps = np.zeros(n)
     lib().oracle_pattern_error(n, _p(E), _p(Eref), float(norm), _p(eps))
     return eps.reshape(E.shape[1:])
+
+
+def model_fit(d, B, P: int, Q: int):
+    """HARP model construction (Section II-A, Eq. 2-3; Section II-B for the
+    sampling and the DFT): from samples B[T, S, l, a] of the complementary
+    interaction on a polar grid -- d_l regular in d = 1/r, alpha_a = 2 pi a /
+    N_alpha regular in angle -- the coefficients c[T, S, p + P, q] of
+    B(d, alpha) = sum_p e^{j p alpha} sum_q c_pq d^q:
+      1. the DFT over alpha gives each harmonic's radial samples,
+         b_p(d_l) = (1 / N_alpha) sum_a B(d_l, alpha_a) e^{-j p alpha_a};
+      2. a least-squares polynomial fit in d (library QR/SVD solve of the
+         Vandermonde system V[l, q] = d_l^q) gives c_pq.
+    Returns (coef, rms) with rms[T, S] the root-mean-square residual of the
+    fitted model on the samples."""
+    d = np.asarray(d, dtype=np.float64)
+    B = np.asarray(B, dtype=np.complex128)
+    Nm, Nm2, Nd, Na_ = B.shape
+    assert Nm == Nm2 and Nd == d.size
+    alpha = 2.0 * np.pi * np.arange(Na_) / Na_
+    ps = np.arange(-P, P + 1)
+    W = np.exp(-1j * np.outer(alpha, ps)) / Na_            # (N_alpha, 2P+1)
+    V = d[:, None] ** np.arange(Q + 1)[None, :]             # (Nd, Q+1)
+    coef = np.zeros((Nm, Nm, 2 * P + 1, Q + 1), dtype=np.complex128)
+    rms = np.zeros((Nm, Nm))
+    Ea = np.exp(1j * np.outer(alpha, ps))                   # (N_alpha, 2P+1)
+    for T in range(Nm):
+        for S in range(Nm):
+            b = B[T, S] @ W                                  # (Nd, 2P+1)
+            for k in range(2 * P + 1):
+                coef[T, S, k] = np.linalg.lstsq(V, b[:, k], rcond=None)[0]
+            model = (V @ coef[T, S].T) @ Ea.T                # (Nd, N_alpha)
+            rms[T, S] = np.sqrt(np.mean(np.abs(model - B[T, S]) ** 2))
+    return coef, rms

@@ -100,6 +100,8 @@ def lib():
         L.harp_eep.restype = i
         L.harp_pattern_error.argtypes = [l, vp, vp, d, vp, vp]
         L.harp_pattern_error.restype = i
+        L.harp_model_fit.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
+        L.harp_model_fit.restype = i
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_sync", "harp_ctx_z64",
                    "harp_fill",
                    "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
@@ -543,3 +545,22 @@ def pattern_error(E: torch.Tensor, Eref: torch.Tensor, norm: float, stream=None)
     _check("harp_pattern_error", lib().harp_pattern_error(n, _ptr(E), _ptr(Eref), float(norm),
                                                           _ptr(eps), _stream(stream)))
     return eps
+
+
+def model_fit(d: torch.Tensor, B: torch.Tensor, P: int, Q: int, stream=None):
+    """HARP model construction: coefficients (Nm, Nm, 2P+1, Q+1) complex128
+    and the rms residual (Nm, Nm) from samples B (Nm, Nm, Nd, N_alpha) on
+    the grid d (Nd,) x alpha_a = 2 pi a / N_alpha."""
+    if B.dim() != 4 or B.shape[0] != B.shape[1]:
+        raise ValueError(f"B must be (Nm, Nm, Nd, N_alpha), got {tuple(B.shape)}")
+    Nm, _, Nd, Nal = B.shape
+    _expect_shape("d", d, (Nd,))
+    if not B.is_cuda or not d.is_cuda:
+        raise ValueError("expected CUDA tensors (device memory)")
+    d = d.to(torch.float64).contiguous()
+    B = B.to(torch.complex128).contiguous()
+    coef = torch.empty((Nm, Nm, 2 * P + 1, Q + 1), dtype=torch.complex128, device=B.device)
+    rms = torch.empty((Nm, Nm), dtype=torch.float64, device=B.device)
+    _check("harp_model_fit", lib().harp_model_fit(Nm, P, Q, Nd, Nal, _ptr(d), _ptr(B),
+                                                  _ptr(coef), _ptr(rms), _stream(stream)))
+    return coef, rms

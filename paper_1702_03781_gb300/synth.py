@@ -251,3 +251,12 @@ def mbf_patterns(Nm: int, theta: np.ndarray, phi: np.ndarray, seed: int) -> np.n
     powers = np.stack([np.ones_like(ct), ct, ct * ct], axis=1)  # (D, 3)
     F = np.einsum("dl,cjl->cdj", powers, a) * np.exp(1j * np.outer(phi, m))[None]
     return np.ascontiguousarray(F)
+
+
+def model_grid(r_min: float = 1.5, r_max: float = 40.0, n_d: int = 24, n_alpha: int = 32):
+    """The sampling grid of a HARP model build (Section II-B): n_d radii
+    regular in d = 1/r between 1/r_max and 1/r_min, and n_alpha angles
+    regular on [0, 2 pi). Returns d (n_d,), alpha (n_alpha,)."""
+    d = np.linspace(1.0 / r_max, 1.0 / r_min, n_d)
+    alpha = 2.0 * np.pi * np.arange(n_alpha) / n_alpha
+    return d, alpha
