@@ -324,6 +324,57 @@ typedef struct {
 int harp_solve_batch(harp_ctx** ctxs, int n_ctx, harp_problem* probs, int n_probs, int prec,
                      double tol, int max_iter);
 
+/* ---- Tessellation (Section II-D, Fig. 3; Section IV-B) -------------------
+ * Reading of the paper's hexagons: flat-topped, circumradius R. The inner
+ * hexagons of circumradius R_in tile the plane with centres x = 1.5 R_in i,
+ * y = sqrt(3) R_in (j + (i mod 2) / 2); an antenna belongs to the inner part
+ * of the tile of the nearest centre (smallest (i, j) on ties); a tile's
+ * subarray is every antenna inside the concentric hexagon of circumradius
+ * R_in + R_ext, edge included. The membership decisions are plain IEEE FP64
+ * with every product and sum rounded separately (no fused multiply-add).
+ *
+ * harp_tessellate: the tiles that hold antennas, sorted by (i, j), and per
+ * tile its inner members and its subarray, each in increasing antenna
+ * order, as CSR lists.
+ *   Na, pos          antennas, double [Na][2] metres (device)       [1, 2]
+ *   R_in, R_ext      metres (R_in > 0, R_ext >= 0)                   [3, 4]
+ *   max_tiles        room in the tile arrays                         [5]
+ *   tiles            output int [max_tiles][2]: (i, j)               [6]
+ *   inner_ptr/_idx   output int [max_tiles + 1] / [Na]               [7, 8]
+ *   outer_ptr/_idx   output int [max_tiles + 1] / [outer_cap]        [9, 10]
+ *   outer_cap        room in outer_idx                               [11]
+ *   n_tiles          host int: the number of tiles                   [12]
+ *   outer_total      host long: the total subarray membership        [13]
+ * Device outputs; synchronises `stream` (allocates stream-ordered scratch).
+ * Returns HARP_E_UNSUPPORTED, with the sizes needed in *n_tiles and
+ * *outer_total, when max_tiles or outer_cap is too small. */
+int harp_tessellate(int Na, const double* pos, double R_in, double R_ext, int max_tiles,
+                    int* tiles, int* inner_ptr, int* inner_idx, int* outer_ptr, int* outer_idx,
+                    long outer_cap, int* n_tiles, long* outer_total, void* stream);
+
+/* The currents of every port by the tessellation approach: each tile's
+ * subarray is filled (Eq. 3-4) and solved for its port excitations with the
+ * batch scheduler (the subarrays are independent problems of uneven size,
+ * largest first), and column m of X keeps the currents of port m on the
+ * subarray of m's tile, zero on the other antennas' rows (the paper keeps
+ * the EEPs of the inner elements only).
+ *   ctxs, n_ctx        contexts, each sized for the largest subarray  [1, 2]
+ *   Na, Nm, P, Q, pos, freq_hz, coef, self_blocks, self_stride
+ *                      the array, as for harp_fill                    [3..11]
+ *   n_tiles, inner_ptr, inner_idx, outer_ptr, outer_idx
+ *                      harp_tessellate's lists (device)               [12..16]
+ *   X, ldx             output c128 (Na Nm) x Na                       [17, 18]
+ *   prec, tol, max_iter   as for harp_solve_batch                     [19, 20, 21]
+ * Device pointers; blocks until done; allocates the subarrays' inputs and
+ * solutions for the call. Returns HARP_OK or the first non-zero status of
+ * a subarray's fill or solve. */
+int harp_solve_tessellated(harp_ctx** ctxs, int n_ctx, int Na, int Nm, int P, int Q,
+                           const double* pos, double freq_hz, const double* coef,
+                           const double* self_blocks, long self_stride, int n_tiles,
+                           const int* inner_ptr, const int* inner_idx, const int* outer_ptr,
+                           const int* outer_idx, double* X, int ldx, int prec, double tol,
+                           int max_iter);
+
 /* Port objective of the synthesis workload (the array-synthesis use the
  * paper's conclusion names; reading: the port response of the solution for
  * the port excitations V = E):

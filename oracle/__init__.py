@@ -10,6 +10,7 @@ out. Matrices cross the boundary column-major (Fortran order).
 from __future__ import annotations
 
 import ctypes as ct
+import math
 import os
 
 import numpy as np
@@ -270,3 +271,76 @@ def model_fit(d, B, P: int, Q: int):
             model = (V @ coef[T, S].T) @ Ea.T                # (Nd, N_alpha)
             rms[T, S] = np.sqrt(np.mean(np.abs(model - B[T, S]) ** 2))
     return coef, rms
+
+
+# ---- Tessellation (Section II-D, Fig. 3; Section IV-B) -------------------
+# Reading: hexagons are flat-topped with circumradius R (vertex distance);
+# the inner hexagons of circumradius R_in tile the plane with centres
+# x = 1.5 R_in i, y = sqrt(3) R_in (j + (i mod 2) / 2); an antenna belongs
+# to the tile of the nearest centre (smallest (i, j) on ties), and a tile's
+# subarray is every antenna inside the concentric hexagon of circumradius
+# R_in + R_ext (boundary included). The arithmetic below is plain IEEE FP64
+# without fused multiply-adds, the same sequence the library uses, so the
+# membership decisions are identical.
+SQRT3 = 1.7320508075688772
+
+
+def hex_center(i: int, j: int, R: float):
+    return 1.5 * R * i, SQRT3 * R * (j + 0.5 * (i & 1))
+
+
+def in_hexagon(dx: float, dy: float, R: float) -> bool:
+    """Inside the flat-topped hexagon of circumradius R (or on its edge)."""
+    ax, ay = abs(dx), abs(dy)
+    return ay <= 0.5 * SQRT3 * R and SQRT3 * ax + ay <= SQRT3 * R
+
+
+def hex_tile(x: float, y: float, R: float):
+    """(i, j) of the nearest centre of the R-hexagon lattice."""
+    i0 = math.floor(x / (1.5 * R))
+    best = None
+    for i in (i0 - 1, i0, i0 + 1, i0 + 2):
+        j0 = math.floor(y / (SQRT3 * R) - 0.5 * (i & 1))
+        for j in (j0 - 1, j0, j0 + 1, j0 + 2):
+            cx, cy = hex_center(i, j, R)
+            ddx, ddy = x - cx, y - cy
+            d2 = ddx * ddx + ddy * ddy
+            if best is None or d2 < best[0] or (d2 == best[0] and (i, j) < best[1]):
+                best = (d2, (i, j))
+    return best[1]
+
+
+def tessellate(pos, R_in: float, R_ext: float):
+    """Tiles (i, j) sorted, and per tile the sorted antenna indices of its
+    inner part and of its subarray (inner and extended parts)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    tij = [hex_tile(float(x), float(y), R_in) for x, y in pos]
+    tiles = sorted(set(tij))
+    inner = [[a for a in range(len(pos)) if tij[a] == t] for t in tiles]
+    outer = []
+    for t in tiles:
+        cx, cy = hex_center(t[0], t[1], R_in)
+        outer.append([a for a in range(len(pos))
+                      if in_hexagon(float(pos[a, 0]) - cx, float(pos[a, 1]) - cy, R_in + R_ext)])
+    return tiles, inner, outer
+
+
+def solve_tessellated(pos, freq_hz, coef, self_blocks, R_in: float, R_ext: float):
+    """The currents of every port by the tessellation approach: each tile's
+    subarray filled (Eq. 3-4) and solved for the excitation of each of its
+    inner antennas; column m of the result holds the currents of port m on
+    the subarray of m's tile (zero elsewhere)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    Na, Nm = pos.shape[0], coef.shape[0]
+    X = np.zeros((Na * Nm, Na), dtype=np.complex128)
+    tiles, inner, outer = tessellate(pos, R_in, R_ext)
+    for t in range(len(tiles)):
+        sub = outer[t]
+        sb = self_blocks if self_blocks.ndim == 2 else self_blocks[sub]
+        Z = fill(pos[sub], freq_hz, coef, sb)
+        rows = (np.asarray(sub)[:, None] * Nm + np.arange(Nm)[None, :]).ravel()
+        for m in inner[t]:
+            v = np.zeros(len(sub) * Nm, dtype=np.complex128)
+            v[sub.index(m) * Nm] = 1.0
+            X[rows, m] = solve(Z, v[:, None])[:, 0]
+    return X

@@ -102,6 +102,12 @@ def lib():
         L.harp_pattern_error.restype = i
         L.harp_model_fit.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
         L.harp_model_fit.restype = i
+        L.harp_tessellate.argtypes = [i, vp, d, d, i, vp, vp, vp, vp, vp, l, ct.POINTER(i),
+                                      ct.POINTER(l), vp]
+        L.harp_tessellate.restype = i
+        L.harp_solve_tessellated.argtypes = [ct.POINTER(vp), i, i, i, i, i, vp, d, vp, vp, l, i,
+                                             vp, vp, vp, vp, vp, i, i, d, i]
+        L.harp_solve_tessellated.restype = i
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_sync", "harp_ctx_z64",
                    "harp_fill",
                    "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
@@ -564,3 +570,67 @@ def model_fit(d: torch.Tensor, B: torch.Tensor, P: int, Q: int, stream=None):
     _check("harp_model_fit", lib().harp_model_fit(Nm, P, Q, Nd, Nal, _ptr(d), _ptr(B),
                                                   _ptr(coef), _ptr(rms), _stream(stream)))
     return coef, rms
+
+
+class Tessellation:
+    """Tiles (T, 2) int32 and the CSR lists of the tiles' inner members and
+    subarrays (device int32 tensors), from harp_tessellate."""
+
+    def __init__(self, tiles, inner_ptr, inner_idx, outer_ptr, outer_idx):
+        self.tiles, self.inner_ptr, self.inner_idx = tiles, inner_ptr, inner_idx
+        self.outer_ptr, self.outer_idx = outer_ptr, outer_idx
+
+    @property
+    def n_tiles(self) -> int:
+        return self.tiles.shape[0]
+
+    def sizes(self):
+        """Subarray sizes (antennas) per tile, on the host."""
+        op = self.outer_ptr.cpu()
+        return (op[1:] - op[:-1]).tolist()
+
+
+def tessellate(pos: torch.Tensor, R_in: float, R_ext: float, stream=None) -> Tessellation:
+    """Hexagonal tiles of the array (inner circumradius R_in, extension
+    R_ext) with their inner members and subarrays."""
+    if pos.dim() != 2 or pos.shape[1] != 2 or pos.shape[0] < 1:
+        raise ValueError(f"pos must be (Na, 2), got {tuple(pos.shape)}")
+    pos = pos.to(torch.float64).contiguous()
+    Na, dev = pos.shape[0], pos.device
+    max_t, cap = max(16, Na), 4 * Na
+    for _ in range(3):
+        tiles = torch.empty((max_t, 2), dtype=torch.int32, device=dev)
+        ip = torch.empty(max_t + 1, dtype=torch.int32, device=dev)
+        ii = torch.empty(Na, dtype=torch.int32, device=dev)
+        op = torch.empty(max_t + 1, dtype=torch.int32, device=dev)
+        oi = torch.empty(max(1, cap), dtype=torch.int32, device=dev)
+        nt, tot = ct.c_int(0), ct.c_long(0)
+        st = lib().harp_tessellate(Na, _ptr(pos), float(R_in), float(R_ext), max_t, _ptr(tiles),
+                                   _ptr(ip), _ptr(ii), _ptr(op), _ptr(oi), cap, ct.byref(nt),
+                                   ct.byref(tot), _stream(stream))
+        if st == HARP_E_UNSUPPORTED and (nt.value > max_t or tot.value > cap):
+            max_t, cap = max(max_t, nt.value), max(cap, tot.value)
+            continue
+        _check("harp_tessellate", st)
+        T = nt.value
+        return Tessellation(tiles[:T], ip[:T + 1], ii, op[:T + 1], oi[:tot.value])
+    raise RuntimeError("harp_tessellate: list sizes did not settle")
+
+
+def solve_tessellated(contexts, tess: Tessellation, pos: torch.Tensor, freq_hz: float,
+                      coef: torch.Tensor, self_blocks: torch.Tensor, prec="mixed",
+                      tol: float = 0.0, max_iter: int = 10) -> torch.Tensor:
+    """The (Na Nm) x Na currents of every port by the tessellation approach
+    (each column nonzero on its tile's subarray only)."""
+    Na, Nm, P, Q = _model_shape(pos, coef)
+    pos = pos.to(torch.float64).contiguous()
+    coef = coef.to(torch.complex128).contiguous()
+    sb, stride = _self_layout(self_blocks, Na, Nm)
+    X = colmajor_empty(Na * Nm, Na, torch.complex128, pos.device)
+    hs = (ct.c_void_p * len(contexts))(*[c.handle.value for c in contexts])
+    torch.cuda.synchronize()  # inputs prepared on torch's stream are ready
+    _check("harp_solve_tessellated", lib().harp_solve_tessellated(
+        hs, len(contexts), Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(sb), stride,
+        tess.n_tiles, _ptr(tess.inner_ptr), _ptr(tess.inner_idx), _ptr(tess.outer_ptr),
+        _ptr(tess.outer_idx), _ptr(X), _ld(X), _prec(prec), float(tol), int(max_iter)))
+    return X
