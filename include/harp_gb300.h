@@ -375,6 +375,41 @@ int harp_solve_tessellated(harp_ctx** ctxs, int n_ctx, int Na, int Nm, int P, in
                            const int* outer_idx, double* X, int ldx, int prec, double tol,
                            int max_iter);
 
+/* ---- Radius of influence (Section II-D, Section IV-A) ---------------------
+ * Interactions kept only between antennas closer than RI: block (m, n) of
+ * the reduced matrix is kept when m == n or r^2 < RI^2 (plain IEEE FP64,
+ * each product and sum rounded separately), and the matrix is block sparse.
+ *
+ * harp_ri_pairs: the block-CSR structure: row_ptr (long [Na + 1], device)
+ * and col_idx (int [cap], device), each block row's columns in increasing
+ * order, the diagonal included; *nnzb (host) the number of kept blocks.
+ * Synchronises `stream`. Returns HARP_E_UNSUPPORTED with *nnzb set when
+ * cap is too small. Arguments: Na [1], pos (device double [Na][2]) [2],
+ * RI (metres, >= 0) [3], cap [4], row_ptr [5], col_idx [6], nnzb [7]. */
+int harp_ri_pairs(int Na, const double* pos, double RI, long cap, long* row_ptr, int* col_idx,
+                  long* nnzb, void* stream);
+
+/* harp_ri_fill: the kept blocks' values, Eq. 3 in Eq. 4 for m != n and the
+ * self blocks on the diagonal, in the block-CSR order: block b at
+ * values[b * Nm * Nm], column-major Nm x Nm, c128 for HARP_FP64, c64 (FP32
+ * evaluation) for the other modes. Arguments 1..9 as for harp_fill (without
+ * the context), then row_ptr, col_idx, nnzb from harp_ri_pairs [10, 11, 12],
+ * values [13], prec [14], flag (device int: ST bits or-ed in, 1 coincident
+ * antennas, 2 non-finite entries) [15]. Asynchronous on `stream`. */
+int harp_ri_fill(int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
+                 const double* coef, const double* self_blocks, long self_stride,
+                 const long* row_ptr, const int* col_idx, long nnzb, void* values, int prec,
+                 int* flag, void* stream);
+
+/* harp_bsr_to_dense: the block-sparse matrix in dense column-major storage
+ * (zeros outside the kept blocks), c128 or c64 by prec as in harp_ri_fill,
+ * for the dense solve (mbf_solve; in the mixed modes the FP64 copy goes to
+ * the context's Z64 through harp_ctx_z64). N = Na Nm <= 65535. Arguments:
+ * Na, Nm [1, 2], row_ptr, col_idx, nnzb [3, 4, 5], values [6], prec [7],
+ * Z, ldz [8, 9]. Asynchronous on `stream`. */
+int harp_bsr_to_dense(int Na, int Nm, const long* row_ptr, const int* col_idx, long nnzb,
+                      const void* values, int prec, void* Z, int ldz, void* stream);
+
 /* Port objective of the synthesis workload (the array-synthesis use the
  * paper's conclusion names; reading: the port response of the solution for
  * the port excitations V = E):

@@ -344,3 +344,36 @@ def solve_tessellated(pos, freq_hz, coef, self_blocks, R_in: float, R_ext: float
             v[sub.index(m) * Nm] = 1.0
             X[rows, m] = solve(Z, v[:, None])[:, 0]
     return X
+
+
+# ---- Radius of influence (Section II-D, Section IV-A) ---------------------
+def ri_pairs(pos, RI: float):
+    """Block-sparse structure of the reduced matrix under a radius of
+    influence: block (m, n) is kept when m == n or the antennas are closer
+    than RI (r^2 < RI^2 with r^2 = dx*dx + dy*dy, each operation rounded in
+    FP64). Returns CSR (row_ptr (Na+1,), col_idx) with each row's columns
+    in increasing order."""
+    pos = np.asarray(pos, dtype=np.float64)
+    Na = pos.shape[0]
+    R2 = float(RI) * float(RI)
+    row_ptr, cols = [0], []
+    for m in range(Na):
+        for n in range(Na):
+            dx = float(pos[m, 0]) - float(pos[n, 0])
+            dy = float(pos[m, 1]) - float(pos[n, 1])
+            if m == n or dx * dx + dy * dy < R2:
+                cols.append(n)
+        row_ptr.append(len(cols))
+    return np.array(row_ptr, dtype=np.int64), np.array(cols, dtype=np.int64)
+
+
+def ri_fill(pos, freq_hz, coef, self_blocks, RI: float):
+    """The reduced matrix under the radius of influence: the full fill with
+    every block (m, n) of pairs at r >= RI set to zero."""
+    Z = fill(pos, freq_hz, coef, self_blocks)
+    Nm = coef.shape[0]
+    row_ptr, cols = ri_pairs(pos, RI)
+    keep = np.zeros((len(row_ptr) - 1,) * 2, dtype=bool)
+    for m in range(len(row_ptr) - 1):
+        keep[m, cols[row_ptr[m]:row_ptr[m + 1]]] = True
+    return Z * np.kron(keep, np.ones((Nm, Nm), dtype=bool))

@@ -108,6 +108,12 @@ def lib():
         L.harp_solve_tessellated.argtypes = [ct.POINTER(vp), i, i, i, i, i, vp, d, vp, vp, l, i,
                                              vp, vp, vp, vp, vp, i, i, d, i]
         L.harp_solve_tessellated.restype = i
+        L.harp_ri_pairs.argtypes = [i, vp, d, l, vp, vp, ct.POINTER(l), vp]
+        L.harp_ri_pairs.restype = i
+        L.harp_ri_fill.argtypes = [i, i, i, i, vp, d, vp, vp, l, vp, vp, l, vp, i, vp, vp]
+        L.harp_ri_fill.restype = i
+        L.harp_bsr_to_dense.argtypes = [i, i, vp, vp, l, vp, i, vp, i, vp]
+        L.harp_bsr_to_dense.restype = i
         for fn in ("harp_ctx_create", "harp_ctx_destroy", "harp_ctx_sync", "harp_ctx_z64",
                    "harp_fill",
                    "mbf_solve", "harp_fill_adjoint", "harp_profile_begin", "harp_profile_end",
@@ -634,3 +640,55 @@ def solve_tessellated(contexts, tess: Tessellation, pos: torch.Tensor, freq_hz: 
         tess.n_tiles, _ptr(tess.inner_ptr), _ptr(tess.inner_idx), _ptr(tess.outer_ptr),
         _ptr(tess.outer_idx), _ptr(X), _ld(X), _prec(prec), float(tol), int(max_iter)))
     return X
+
+
+def ri_pairs(pos: torch.Tensor, RI: float, stream=None):
+    """Block-CSR structure (row_ptr int64 (Na+1,), col_idx int32 (nnzb,)) of
+    the kept blocks under a radius of influence RI."""
+    if pos.dim() != 2 or pos.shape[1] != 2 or pos.shape[0] < 1:
+        raise ValueError(f"pos must be (Na, 2), got {tuple(pos.shape)}")
+    pos = pos.to(torch.float64).contiguous()
+    Na = pos.shape[0]
+    cap = Na * Na
+    row_ptr = torch.empty(Na + 1, dtype=torch.int64, device=pos.device)
+    col_idx = torch.empty(cap, dtype=torch.int32, device=pos.device)
+    nnzb = ct.c_long(0)
+    _check("harp_ri_pairs", lib().harp_ri_pairs(Na, _ptr(pos), float(RI), cap, _ptr(row_ptr),
+                                                _ptr(col_idx), ct.byref(nnzb), _stream(stream)))
+    return row_ptr, col_idx[:nnzb.value].clone()
+
+
+def ri_fill(pos, freq_hz, coef, self_blocks, row_ptr, col_idx, prec="fp64", stream=None):
+    """The kept blocks' values (nnzb, Nm, Nm) (each block column-major:
+    [b, S, T] in torch's row-major view), complex128 for fp64, complex64
+    otherwise; raises on coincident antennas or non-finite entries."""
+    Na, Nm, P, Q = _model_shape(pos, coef)
+    pos = pos.to(torch.float64).contiguous()
+    coef = coef.to(torch.complex128).contiguous()
+    sb, stride = _self_layout(self_blocks, Na, Nm)
+    pr = _prec(prec)
+    nnzb = col_idx.shape[0]
+    dt = torch.complex128 if pr == FP64 else torch.complex64
+    vals = torch.empty((nnzb, Nm, Nm), dtype=dt, device=pos.device)
+    flag = torch.zeros(1, dtype=torch.int32, device=pos.device)
+    _check("harp_ri_fill", lib().harp_ri_fill(
+        Na, Nm, P, Q, _ptr(pos), float(freq_hz), _ptr(coef), _ptr(sb), stride, _ptr(row_ptr),
+        _ptr(col_idx), nnzb, _ptr(vals), pr, _ptr(flag), _stream(stream)))
+    f = int(flag.item())
+    if f & 1:
+        raise HarpError("harp_ri_fill", HARP_E_COINCIDENT)
+    if f & 2:
+        raise HarpError("harp_ri_fill", HARP_E_NONFINITE)
+    return vals
+
+
+def bsr_to_dense(row_ptr, col_idx, vals, Na: int, out: torch.Tensor | None = None, stream=None):
+    """The block-sparse matrix in dense column-major storage (N x N)."""
+    nnzb, Nm, _ = vals.shape
+    N = Na * Nm
+    pr = FP64 if vals.dtype == torch.complex128 else FP32
+    Z = colmajor_empty(N, N, vals.dtype, vals.device) if out is None else out
+    _check("harp_bsr_to_dense", lib().harp_bsr_to_dense(
+        Na, Nm, _ptr(row_ptr), _ptr(col_idx), nnzb, _ptr(vals.contiguous()), pr, _ptr(Z), _ld(Z),
+        _stream(stream)))
+    return Z
