@@ -109,35 +109,50 @@ class ClockSampler:
         return self._summary or {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
 
 
-def wideband_throughput(device: int, n_ctx: int = 4, n_freq: int = 64) -> dict:
+def wideband_throughput(device: int, n_ctx: int | None = None, n_freq: int = 64) -> dict:
     """Config 3: the station layout at n_freq frequencies over 50-350 MHz
     (Nm 6..20, N 1536..5120, 256 ports each), filled and solved (mixed, to
-    the LAPACK tolerance) by the library's batch scheduler on n_ctx
-    contexts. One warm-up batch of n_ctx frequencies, then one timed batch
-    of all of them (host wall clock around the synchronous batch call)."""
+    the LAPACK tolerance) by the library's batch scheduler. The worker
+    count and each context's tile-shape knobs come from the autotuner's
+    cache when it holds the wideband batch (else 4 workers, default knobs).
+    One warm-up batch of n_ctx frequencies, then one timed batch of all of
+    them: device time from CUDA events on every worker's stream (first
+    start to last end) and host wall clock around the synchronous call."""
     import torch
+    from paper_1702_03781_gb300 import autotune
     from paper_1702_03781_gb300 import harp as H
     from paper_1702_03781_gb300 import synth
     d = f"cuda:{device}"
+    cache = autotune.load()
+    tuned = cache.get("wideband_batch")
+    if n_ctx is None:
+        n_ctx = int(tuned["workers"]) if tuned else 4
     probs = synth.wideband(n_freq)
     items = [H.BatchItem(torch.from_numpy(q.pos).to(d), q.freq_hz, torch.from_numpy(q.coef).to(d),
                          torch.from_numpy(q.self_blocks).to(d)) for q in probs]
     max_N = max(it.N for it in items)
+    mid = sorted(probs, key=lambda q: q.N)[len(probs) // 2]
     ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n_ctx)]
+    knobs = [autotune.apply(c, mid.N, mid.Nm, mid.K, cache) for c in ctxs][0]
     H.solve_batch(ctxs, items[-n_ctx:], prec="mixed")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     H.solve_batch(ctxs, items, prec="mixed", check=False)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    dev_ms = ctxs[0].batch_device_ms()
     ok = all(it.status == 0 for it in items)
     iters = [it.iters for it in items]
     for c in ctxs:
         c.close()
     return {"frequencies": n_freq, "contexts": n_ctx, "N_range": [min(it.N for it in items), max_N],
+            "device_ms_per_frequency": round(dev_ms / n_freq, 3),
             "ms_per_frequency": round(1e3 * wall / n_freq, 3), "wall_ms": round(1e3 * wall, 2),
-            "all_converged": ok, "corrections": [min(iters), max(iters)],
-            "timing": "host wall clock around one synchronous batch call"}
+            "device_ms": round(dev_ms, 2), "all_converged": ok,
+            "corrections": [min(iters), max(iters)], "knobs": knobs,
+            "tuned": bool(tuned) and autotune.key(mid.N, mid.Nm, mid.K) in cache,
+            "timing": "device: CUDA events on every worker stream, first start to last end; "
+                      "wall: host clock around one synchronous batch call"}
 
 
 def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:

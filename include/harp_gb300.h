@@ -247,6 +247,24 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 #define HARP_PIVOT_TOURNAMENT 1
 #define HARP_PIVOT_BLOCK 2
 #define HARP_OPT_PIVOT_FALLBACKS 3
+/* Tile-shape knobs (the autotuner's search space; results are the same up
+ * to rounding whatever their values):
+ *   HARP_OPT_PANEL_ROWS   target rows per CTA of the partial-pivoting
+ *                         cluster panel (32..384, default 192): the planner
+ *                         takes the smallest cluster that reaches it
+ *   HARP_OPT_FILL_CHUNK   the largest number of source MBFs a fill CTA
+ *                         stages at once (0: the largest that fits shared
+ *                         memory, the default)
+ *   HARP_OPT_SPLITK_MAX   the cap (1..8, default 8) on the K splits of the
+ *                         tensor-core products of mbf_solve
+ * HARP_OPT_BATCH_DEVICE_US (get only): device time of the last
+ * harp_solve_batch whose first context this is, in microseconds, from the
+ * first worker's start to the last worker's end (CUDA events on the
+ * workers' streams). */
+#define HARP_OPT_PANEL_ROWS 4
+#define HARP_OPT_FILL_CHUNK 5
+#define HARP_OPT_SPLITK_MAX 6
+#define HARP_OPT_BATCH_DEVICE_US 7
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

@@ -8,6 +8,7 @@
 // (the pivoted panels, the host round trip of each refinement step) run
 // while the others' fills, GEMMs and residuals occupy the remaining SMs.
 // No CUDA call here allocates; the contexts own all workspace.
+#include <algorithm>
 #include <atomic>
 #include <thread>
 #include <vector>
@@ -19,10 +20,22 @@ using namespace harp;
 namespace {
 
 void run_worker(harp_ctx* ctx, harp_problem* probs, int n, std::atomic<int>* next, int prec,
-                double tol, int max_iter) {
+                double tol, int max_iter, cudaEvent_t ev0, cudaEvent_t ev1, int* used) {
+  *used = 0;
   for (;;) {
     const int i = next->fetch_add(1);
-    if (i >= n) return;
+    if (i >= n) {
+      if (*used) {
+        DeviceGuard g(ctx->device);
+        cudaEventRecord(ev1, ctx->stream);
+      }
+      return;
+    }
+    if (!*used) {
+      DeviceGuard g(ctx->device);
+      cudaEventRecord(ev0, ctx->stream);
+      *used = 1;
+    }
     harp_problem& p = probs[i];
     const int N = p.Na * p.Nm;
     int s;
@@ -72,13 +85,53 @@ extern "C" int harp_solve_batch(harp_ctx** ctxs, int n_ctx, harp_problem* probs,
     beside[c] = ctxs[c]->inv_beside;
     if (n_ctx > 1) ctxs[c]->inv_beside = 0;
   }
+  // device time of the batch: an event pair on every worker's stream
+  std::vector<cudaEvent_t> ev(2 * n_ctx, nullptr);
+  std::vector<int> used(n_ctx, 0);
+  for (int c = 0; c < n_ctx; ++c) {
+    DeviceGuard g(ctxs[c]->device);
+    HARP_CUDA(cudaEventCreate(&ev[2 * c]));
+    HARP_CUDA(cudaEventCreate(&ev[2 * c + 1]));
+  }
+  struct Destroy {
+    std::vector<cudaEvent_t>* v;
+    ~Destroy() {
+      for (cudaEvent_t e : *v)
+        if (e) cudaEventDestroy(e);
+    }
+  } destroy{&ev};
   for (int c = 0; c < n_ctx; ++c)
-    workers.emplace_back(run_worker, ctxs[c], probs, n_probs, &next, prec, tol, max_iter);
+    workers.emplace_back(run_worker, ctxs[c], probs, n_probs, &next, prec, tol, max_iter,
+                         ev[2 * c], ev[2 * c + 1], &used[c]);
   for (auto& w : workers) w.join();
   for (int c = 0; c < n_ctx; ++c) ctxs[c]->inv_beside = beside[c];
   for (int c = 0; c < n_ctx; ++c) {
     DeviceGuard g(ctxs[c]->device);
     HARP_CUDA(cudaStreamSynchronize(ctxs[c]->stream));
+  }
+  {
+    // first start to last end, relative to any worker's start
+    int ref = -1;
+    for (int c = 0; c < n_ctx; ++c)
+      if (used[c]) {
+        ref = c;
+        break;
+      }
+    double lo = 0.0, hi = 0.0;
+    if (ref >= 0) {
+      for (int c = 0; c < n_ctx; ++c) {
+        if (!used[c]) continue;
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, ev[2 * ref], ev[2 * c]) != cudaSuccess ||
+            cudaEventElapsedTime(&b, ev[2 * ref], ev[2 * c + 1]) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        lo = std::min(lo, (double)a);
+        hi = std::max(hi, (double)b);
+      }
+    }
+    ctxs[0]->batch_device_us = 1e3 * (hi - lo);
   }
   int first_bad = HARP_OK;
   for (int i = 0; i < n_probs; ++i)

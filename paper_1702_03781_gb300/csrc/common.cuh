@@ -256,6 +256,16 @@ struct harp_ctx {
   double* oz_znorm;
   int residual_mode;  // HARP_RESIDUAL_*
   int pivot_mode;     // HARP_PIVOT_* of the FP32 factorisation's panels
+  // Tile-shape knobs (HARP_OPT_PANEL_ROWS, HARP_OPT_FILL_CHUNK,
+  // HARP_OPT_SPLITK_MAX): target rows per CTA of the cluster panel, the
+  // largest source-MBF chunk of the fill (0: the largest that fits), the cap
+  // on the K splits of the tensor-core products.
+  int panel_rows;
+  int fill_chunk;
+  int splitk_max;
+  // Device time of the last harp_solve_batch that used this context as its
+  // first, microseconds (first start to last end over the workers' streams).
+  double batch_device_us;
 
   // Reductions and status.
   double* red;      // device scratch, 16 + 2*max_nrhs doubles

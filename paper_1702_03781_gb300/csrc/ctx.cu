@@ -178,6 +178,9 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
     c->oz_ticket = -1;
     c->residual_mode = HARP_RESIDUAL_SLICES;
   }
+  c->panel_rows = 192;
+  c->fill_chunk = 0;
+  c->splitk_max = 8;
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) ok = false;
   if (ok && cudaStreamCreateWithFlags(&c->fill_stream, cudaStreamNonBlocking) != cudaSuccess)

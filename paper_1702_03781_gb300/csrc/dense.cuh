@@ -39,6 +39,8 @@ int residual_fp64(int N, int nrhs, CView<double> Z, CView<double> X, CView<doubl
 // current solve (lu_tc.cu); a null workspace selects the CUDA-core GEMM.
 void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int* err);
 void tc_get_workspace(float** a, size_t* a_floats, float** b, size_t* b_floats, int** err);
+// Cap (1..8) on the K splits of this thread's tensor-core products.
+void tc_set_splitk_max(int s);
 
 // Float-float refinement pieces (resid.cu).
 int split_c128(int M, int N, const double* Z, long ldz, float* const hl[4], long ldp,

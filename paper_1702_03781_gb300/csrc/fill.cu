@@ -414,7 +414,8 @@ static int launch_fill(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, int
 // Largest source-MBF chunk whose staged coefficients fit in shared memory.
 static bool plan_fill(const harp_ctx* ctx, int Nm, int K, size_t csz, int* s_chunk, int* TN,
                       size_t* smem, int max_tn = 8) {
-  for (int sc = Nm; sc >= 1; --sc) {
+  const int top = (ctx->fill_chunk > 0) ? std::min(ctx->fill_chunk, Nm) : Nm;
+  for (int sc = top; sc >= 1; --sc) {
     const int W = sc * Nm;
     const int tn = (W + 31) / 32;
     if (tn > max_tn) continue;

@@ -400,6 +400,9 @@ struct TcWorkspace {
   int* err = nullptr;
 };
 static thread_local TcWorkspace g_tc;
+static thread_local int g_splitk_max = 8;  // the calling solve's cap on K splits
+
+void tc_set_splitk_max(int s) { g_splitk_max = (s >= 1 && s <= 8) ? s : 8; }
 
 void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int* err) {
   g_tc.a = a;
@@ -498,8 +501,8 @@ __global__ void splitk_reduce_kernel(int M, int N, int S, const float* __restric
 }
 
 // K splits for a product of `tiles` output tiles and nk k-tiles: the count
-// (at most 8, at least 8 k-tiles each) that minimises the waves of one-CTA-
-// per-SM work, ceil(tiles S / SMs) / S.
+// (at most the solve's cap, 8 by default; at least 8 k-tiles each) that
+// minimises the waves of one-CTA-per-SM work, ceil(tiles S / SMs) / S.
 static int splitk_count(int tiles, int nk) {
   static int sms = 0;
   if (!sms) {
@@ -510,7 +513,7 @@ static int splitk_count(int tiles, int nk) {
   }
   int best = 1;
   double best_t = 1.0;
-  for (int S = 2; S <= 8 && nk / S >= 8; ++S) {
+  for (int S = 2; S <= g_splitk_max && nk / S >= 8; ++S) {
     if (nk % S) continue;
     const double t = (double)((tiles * S + sms - 1) / sms) / S;
     if (t < best_t - 1e-9) {

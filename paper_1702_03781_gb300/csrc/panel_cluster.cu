@@ -464,7 +464,7 @@ int panel_cluster_plan(const harp_ctx* ctx, int M, int want_nb, int* csize, int*
   // smallest cluster that fits in shared memory and reaches that, else the
   // largest that fits.
   const size_t budget = std::min<size_t>(ctx->smem_optin, 220 * 1024) - 2048;
-  constexpr int kRowsTarget = 192;
+  const int kRowsTarget = ctx->panel_rows > 0 ? ctx->panel_rows : 192;
   for (int nb : {64, 32, 16}) {  // multiples of the sub-block width
     if (nb > want_nb || nb > kPcMaxNb) continue;
     int best_c = 0, best_mb = 0;

@@ -443,9 +443,13 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
 
   // Tensor-core GEMM scratch for this call; cleared timeout flag.
   tc_set_workspace(ctx->tc_a, ctx->tc_a_floats, ctx->tc_b, ctx->tc_b_floats, ctx->dstatus + 2);
+  tc_set_splitk_max(ctx->splitk_max);
   HARP_CUDA(cudaMemsetAsync(ctx->dstatus + 2, 0, sizeof(int), st));
   struct Unset {
-    ~Unset() { tc_set_workspace(nullptr, 0, nullptr, 0, nullptr); }
+    ~Unset() {
+      tc_set_workspace(nullptr, 0, nullptr, 0, nullptr);
+      tc_set_splitk_max(8);
+    }
   } unset_on_return;
 
   // Pivoting restricted to the diagonal blocks gives factors only the
@@ -497,6 +501,21 @@ extern "C" int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const dou
 
 extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
   if (!ctx) return -1;
+  if (option == HARP_OPT_PANEL_ROWS) {
+    if (value < 32 || value > 384) return -3;
+    ctx->panel_rows = value;
+    return HARP_OK;
+  }
+  if (option == HARP_OPT_FILL_CHUNK) {
+    if (value < 0) return -3;
+    ctx->fill_chunk = value;
+    return HARP_OK;
+  }
+  if (option == HARP_OPT_SPLITK_MAX) {
+    if (value < 1 || value > 8) return -3;
+    ctx->splitk_max = value;
+    return HARP_OK;
+  }
   if (option == HARP_OPT_PIVOT) {
     if (value != HARP_PIVOT_PARTIAL && value != HARP_PIVOT_TOURNAMENT &&
         value != HARP_PIVOT_BLOCK)
@@ -513,10 +532,19 @@ extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
 
 extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
   if (!ctx) return -1;
+  if (!value) return -3;
+  switch (option) {
+    case HARP_OPT_PANEL_ROWS: *value = ctx->panel_rows; return HARP_OK;
+    case HARP_OPT_FILL_CHUNK: *value = ctx->fill_chunk; return HARP_OK;
+    case HARP_OPT_SPLITK_MAX: *value = ctx->splitk_max; return HARP_OK;
+    case HARP_OPT_BATCH_DEVICE_US:
+      *value = (int)std::min(ctx->batch_device_us + 0.5, 2147483647.0);
+      return HARP_OK;
+    default: break;
+  }
   if (option != HARP_OPT_RESIDUAL && option != HARP_OPT_PIVOT &&
       option != HARP_OPT_PIVOT_FALLBACKS)
     return -2;
-  if (!value) return -3;
   if (option == HARP_OPT_PIVOT)
     *value = ctx->pivot_mode;
   else if (option == HARP_OPT_PIVOT_FALLBACKS)

@@ -40,6 +40,14 @@ RESIDUAL = {"slices": 0, "ff": 1}
 HARP_OPT_PIVOT = 2
 PIVOT = {"partial": 0, "tournament": 1, "block": 2}
 HARP_OPT_PIVOT_FALLBACKS = 3
+# tile-shape knobs of a context (the autotuner's search space) and the
+# device time of the last batch
+HARP_OPT_PANEL_ROWS = 4
+HARP_OPT_FILL_CHUNK = 5
+HARP_OPT_SPLITK_MAX = 6
+HARP_OPT_BATCH_DEVICE_US = 7
+KNOBS = {"panel_rows": HARP_OPT_PANEL_ROWS, "fill_chunk": HARP_OPT_FILL_CHUNK,
+         "splitk_max": HARP_OPT_SPLITK_MAX}
 
 _lib = None
 
@@ -346,6 +354,24 @@ class Harp:
         _check("harp_ctx_get_option", lib().harp_ctx_get_option(self._h, HARP_OPT_PIVOT,
                                                                 ct.byref(v)))
         return {k: m for m, k in PIVOT.items()}[v.value]
+
+    def set_knob(self, name: str, value: int):
+        """A tile-shape knob: 'panel_rows', 'fill_chunk' or 'splitk_max'."""
+        _check("harp_ctx_set_option",
+               lib().harp_ctx_set_option(self._h, KNOBS[name], int(value)))
+
+    def knob(self, name: str) -> int:
+        v = ct.c_int(-1)
+        _check("harp_ctx_get_option", lib().harp_ctx_get_option(self._h, KNOBS[name],
+                                                                ct.byref(v)))
+        return v.value
+
+    def batch_device_ms(self) -> float:
+        """Device time of the last solve_batch led by this context."""
+        v = ct.c_int(-1)
+        _check("harp_ctx_get_option", lib().harp_ctx_get_option(
+            self._h, HARP_OPT_BATCH_DEVICE_US, ct.byref(v)))
+        return v.value / 1e3
 
     def pivot_fallbacks(self) -> int:
         """Factorisations of this context whose block-restricted pivots were
