@@ -155,6 +155,119 @@ def wideband_throughput(device: int, n_ctx: int | None = None, n_freq: int = 64)
                       "wall: host clock around one synchronous batch call"}
 
 
+def method_work(N: int, nrhs: int, K: int, prof: dict, info: dict, peaks: dict,
+                fp64_ms: float, mixed_ms: float) -> dict:
+    """The step's algorithmic work per part, from the per-class device times
+    of one instrumented step:
+      * residual: R = V - Z X with Z the FP64 matrix, 8 N^2 nrhs flops and
+        16 N^2 + (8 + 16 + 16) N nrhs bytes (Z64, X as FP32 planes, V and R
+        in FP64) per residual; the first residual of a solve is one call
+        (class 'residual'), each correction adds one update ('resid_update');
+      * LU: (8/3) N^3 flops (complex) over the summed device time of the
+        factorisation's classes (panel, gemm, trsm, swap; the factor
+        inverses and the correction solves run in 'gemm' too, so this
+        rate is a lower bound), against the TF32 peak and the three-term
+        TF32 effective peak (a third of it);
+      * the FP64 GPU path against its bound: fill (8 K N^2) + LU + two
+        triangular solves (8 N^2 nrhs) flops at the FP64 FMA peak."""
+    from paper_1702_03781_gb300 import roofline
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    tf32 = bf16 * roofline.TF32_OVER_BF16
+    res_flops = 8.0 * N * N * nrhs
+    res_bytes = 16.0 * N * N + 40.0 * N * nrhs
+    out = {}
+    calls = {"residual": 1, "resid_update": int(info.get("iters") or 0)}
+    for kind, n in calls.items():
+        pk = prof.get(kind, {})
+        if not pk.get("launches") or n < 1:
+            continue
+        ms = pk["ms"] / n
+        t = None
+        try:
+            tj = json.load(open(roofline.TRAFFIC_FILE)).get(kind)
+            if tj and tj.get("source_sha") == roofline.source_hash(kind):
+                t = tj["bytes_per_launch"] * pk["launches"] / n
+        except Exception:
+            pass
+        out[kind] = {"calls_per_step": n, "ms_per_call": round(ms, 4),
+                     "flops_per_call": res_flops, "bytes_per_call": res_bytes,
+                     "tflops": round(res_flops / (ms * 1e-3) / 1e12, 3),
+                     "gbs": round(res_bytes / (ms * 1e-3) / 1e9, 1),
+                     "frac_hbm": round(res_bytes / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "digit_product_tflops": round(pk["flops"] / (pk["ms"] * 1e-3) / 1e12, 2),
+                     "digit_product_frac_bf16": round(pk["flops"] / (pk["ms"] * 1e-3) / 1e12 / bf16,
+                                                      4),
+                     "traffic_per_call": t,
+                     "traffic_over_algorithmic": round(t / res_bytes, 2) if t else None}
+    lu_flops = 8.0 / 3.0 * N ** 3
+    lu_ms = sum(prof.get(k, {}).get("ms", 0.0) for k in ("panel", "gemm", "trsm", "swap"))
+    if lu_ms > 0:
+        ach = lu_flops / (lu_ms * 1e-3) / 1e12
+        out["lu"] = {"flops": lu_flops, "device_ms_sum": round(lu_ms, 3),
+                     "tflops": round(ach, 3), "frac_tf32": round(ach / tf32, 4),
+                     "frac_3xtf32_effective": round(3 * ach / tf32, 4),
+                     "peak_tf32": round(tf32, 1),
+                     "note": "classes panel+gemm+trsm+swap summed over their launches"}
+    fp64_flops = 8.0 * K * N * N + lu_flops + 8.0 * N * N * nrhs
+    bound_ms = fp64_flops / (roofline.FP64_PEAK_TFLOPS * 1e12) * 1e3
+    out["fp64_path"] = {"flops": fp64_flops, "bound_ms": round(bound_ms, 2),
+                        "measured_ms": round(fp64_ms, 2),
+                        "frac_of_bound": round(bound_ms / fp64_ms, 4),
+                        "mixed_speedup_vs_measured": round(fp64_ms / mixed_ms, 2),
+                        "mixed_speedup_vs_bound": round(bound_ms / mixed_ms, 2)}
+    return out
+
+
+def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int = 8) -> dict:
+    """Config 5's synthesis batch: J and dJ/dpos for seeded random layouts
+    1..n_layouts (seeds 5001..5008) of 1024 antennas x 16 MBFs at 110 MHz
+    (N = 16384, 1024 ports): forward fill + mixed solve, transposed solve
+    with the cached factors, FP64 adjoint kernel. The layouts are sharded
+    over the ranks (replicas.shard); each rank times its own with CUDA
+    events (one layout per event pair) after one untimed gradient of its
+    first layout; the whole job's time is the slowest rank's. The adjoint
+    kernel's roofline is taken from the library's instrumentation over the
+    timed layouts."""
+    import torch
+    from paper_1702_03781_gb300 import harp as H
+    from paper_1702_03781_gb300 import replicas, roofline, synth
+    from paper_1702_03781_gb300.synthesis import layout_gradients
+    mine = replicas.shard(n_layouts, ws, rank)
+    probs = [synth.large(1 + i) for i in mine]
+    stream = torch.cuda.current_stream()
+    ms, res = [], []
+    prof = None
+    with H.Harp(device, max_N=16384, max_nrhs=1024) as h:
+        if probs:
+            layout_gradients(h, probs[:1])
+        torch.cuda.synchronize()
+        roofline.begin(h, 1 << roofline.KINDS.index("adjoint"))
+        for p in probs:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res += layout_gradients(h, [p])
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        prof = roofline.end(h)["adjoint"]
+    total = replicas.max_over_ranks(sum(ms), torch.device("cuda", device))
+    out = {"layouts": n_layouts, "seeds": [5001 + i for i in range(n_layouts)], "N": 16384,
+           "ports": 1024, "ranks": ws,
+           "ms_per_layout": round(total / max(1, len(probs)), 2) if probs else None,
+           "job_ms": round(total, 1),
+           "rank0_layouts": [5001 + i for i in mine],
+           "rank0_ms": [round(m, 1) for m in ms],
+           "all_converged": all(i[leg]["status"] == 0 for _, _, i in res
+                                for leg in ("forward", "adjoint")),
+           "corrections": {"forward": [i["forward"]["iters"] for _, _, i in res],
+                           "adjoint": [i["adjoint"]["iters"] for _, _, i in res]},
+           "timing": "CUDA events per layout (forward + backward), after one untimed layout"}
+    if prof and prof["launches"]:
+        out["adjoint_roofline"] = roofline.entry("adjoint", "fp64", prof, peaks)
+    return out
+
+
 def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:
     """The embedded element patterns of all 256 ports of the station on the
     1-degree hemisphere grid (91 x 360 directions) from the step's solution
@@ -243,6 +356,8 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-wideband", action="store_true")
+    ap.add_argument("--no-synthesis", action="store_true",
+                    help="skip the 8-layout N = 16384 synthesis batch (about a minute)")
     ap.add_argument("--pivot", default="", choices=["", "partial", "tournament", "block"],
                     help="pivot rule of the FP32 factorisation's panels (default: the library's)")
     ap.add_argument("--nvtx-step", default="",
@@ -387,6 +502,11 @@ def main():
     e2e_max = replicas.max_over_ranks(statistics.mean(ms_e2e), dev)
     e2e_med = replicas.max_over_ranks(statistics.median(ms_e2e), dev)
 
+    synth_batch = None
+    if not args.no_synthesis:
+        barrier()
+        synth_batch = synthesis_batch(local, ws, rank, _peaks())
+
     if rank == 0:
         peaks = _peaks()
         roof = roofline.entry(dominant, impl[dominant], prof_dom, peaks)
@@ -416,7 +536,14 @@ def main():
             "roofline_kernels": roof_all,
             "kernel_shares": shares,
         }
+        # The method's own work beside the rates above (which count what the
+        # kernels execute: digit products for the exact-slice residual).
+        method = method_work(N, Na, p.K, prof_all, info, peaks, float(statistics.mean(ms_fp64)),
+                             t_mixed)
+        line["method_work"] = method
         line["eep"] = eep_throughput(h, p, X, dev, peaks)
+        if synth_batch is not None:
+            line["synthesis_batch"] = synth_batch
         if not args.no_wideband:
             line["wideband"] = wideband_throughput(local)
         if not args.no_cpu_baseline:

@@ -155,7 +155,8 @@ def main(argv=None) -> int:
     log = lambda s: print(s, file=sys.stderr, flush=True)  # noqa: E731
     cache = load(args.out)
     wb = synth.wideband()
-    classes = [synth.station()] + [wb[i] for i in (0, 21, 42, 63)]
+    mid = sorted(wb, key=lambda q: q.N)[len(wb) // 2]  # the class the batch's contexts use
+    classes = [synth.station(), mid] + [wb[i] for i in (0, 21, 42, 63)]
     for p in classes:
         log(f"tuning {p.name} (N={p.N}, Nm={p.Nm}, K={p.K})")
         cache[key(p.N, p.Nm, p.K)] = tune_problem(p, reps=args.reps, log=log)

@@ -75,7 +75,7 @@ def source_hash(kind: str) -> str:
     """Hash of the sources a kernel class is built from (traffic validity)."""
     files = {"fill": ["fill.cu", "ff.cuh"], "gemm": ["lu_tc.cu"],
              "residual": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"],
-             "panel": ["panel_cluster.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
+             "panel": ["panel_cluster.cu", "panel_common.cuh", "panel_calu.cu"], "trsm": ["dense.cu"], "swap": ["dense.cu"],
              "adjoint": ["adjoint.cu"], "other": ["dense.cu"],
              "resid_update": ["ozaki.cu", "ozaki.cuh", "resid.cu", "ff.cuh"],
              "fill_ff": ["fill.cu", "ff.cuh"]}.get(kind, [])

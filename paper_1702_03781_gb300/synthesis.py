@@ -16,7 +16,8 @@ from . import harp as H
 
 
 class PortObjective(torch.autograd.Function):
-    """J = PortObjective.apply(pos, harp, freq_hz, coef, self_blocks, prec).
+    """J = PortObjective.apply(pos, harp, freq_hz, coef, self_blocks, prec,
+    max_iter, info).
 
     `harp` is an H.Harp context; its cached factorisation is used by the
     backward pass, so no other solve may run on it between forward and
@@ -24,16 +25,18 @@ class PortObjective(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, pos, harp, freq_hz, coef, self_blocks, prec="mixed", max_iter=10):
+    def forward(ctx, pos, harp, freq_hz, coef, self_blocks, prec="mixed", max_iter=10,
+                info=None):
         Nm = coef.shape[0]
         Na = pos.shape[0]
         Z = harp.fill(pos.detach(), freq_hz, coef, self_blocks,
                       prec="fp64" if prec == "fp64" else "mixed")
-        X, info = harp.solve(Z, None, nrhs=Na, prec=prec, max_iter=max_iter)
+        X, fwd = harp.solve(Z, None, nrhs=Na, prec=prec, max_iter=max_iter)
         _, J, W = H.port_objective(X, Na, Nm, want_P=False, want_W=True)
         ctx.harp, ctx.freq_hz, ctx.prec, ctx.max_iter = harp, freq_hz, prec, max_iter
         ctx.save_for_backward(pos.detach(), coef, X, W)
-        ctx.info = info
+        ctx.info = info if info is not None else {}
+        ctx.info["forward"] = fwd
         return J
 
     @staticmethod
@@ -42,14 +45,35 @@ class PortObjective(torch.autograd.Function):
         h = ctx.harp
         # Lambda from the cached factors (FP32 LU with FP64-accurate
         # refinement in the mixed mode)
-        Lam, _ = h.solve(None, W, prec=ctx.prec, trans="T", max_iter=ctx.max_iter)
+        Lam, adj = h.solve(None, W, prec=ctx.prec, trans="T", max_iter=ctx.max_iter)
+        ctx.info["adjoint"] = adj
         # The contraction G = Lambda X^T with the recomputed derivatives runs
         # in FP64: summed over ~Na partners per antenna with cancellation, an
         # FP32 contraction leaves ~1e-6 relative error in the gradient at the
         # station size, above the synthesis tolerance.
         grad = h.fill_adjoint(pos, ctx.freq_hz, coef, Lam, X, prec="fp64")
-        return grad * gJ, None, None, None, None, None, None
+        return grad * gJ, None, None, None, None, None, None, None
 
 
-def port_objective(pos, harp, freq_hz, coef, self_blocks, prec="mixed", max_iter=10):
-    return PortObjective.apply(pos, harp, freq_hz, coef, self_blocks, prec, max_iter)
+def port_objective(pos, harp, freq_hz, coef, self_blocks, prec="mixed", max_iter=10, info=None):
+    """J (0-d float64 tensor); `info`, when given, receives the forward and
+    adjoint solves' {'iters', 'resid', 'status'} under "forward" and
+    "adjoint" (the latter once backward has run)."""
+    return PortObjective.apply(pos, harp, freq_hz, coef, self_blocks, prec, max_iter, info)
+
+
+def layout_gradients(harp, problems, prec="mixed", max_iter=60):
+    """J and dJ/dpos of every problem (one antenna layout each, all of the
+    same size), one after another on one context: the synthesis batch.
+    Returns [(J float, grad (Na, 2) float64 tensor, info dict)]."""
+    out = []
+    dev = torch.device("cuda", harp.device)
+    for p in problems:
+        x = torch.from_numpy(p.pos).to(dev).requires_grad_(True)
+        coef = torch.from_numpy(p.coef).to(dev)
+        sb = torch.from_numpy(p.self_blocks).to(dev)
+        info = {}
+        J = port_objective(x, harp, p.freq_hz, coef, sb, prec=prec, max_iter=max_iter, info=info)
+        J.backward()
+        out.append((float(J.detach()), x.grad, info))
+    return out

@@ -1,4 +1,6 @@
 """Input generator checks that need no GPU."""
+import numpy as np
+
 from paper_1702_03781_gb300 import synth
 
 
@@ -67,3 +69,13 @@ def test_port_rhs_selects_mbf0_of_each_antenna():
     assert np.array_equal(np.argwhere(V == 1.0), np.array([[0, 0], [3, 1], [6, 2], [9, 3],
                                                           [12, 4]]))
     assert np.count_nonzero(V) == 5
+
+
+def test_large_layout_seeds():
+    """The synthesis batch's 8 layouts (1..8) draw distinct seeded positions."""
+    p = synth.large(3)
+    assert p.meta["layout"] == 3 and (p.Na, p.Nm, p.N) == (1024, 16, 16384)
+    pos = [synth.large(layout).pos for layout in range(1, 9)]
+    for i in range(8):
+        for j in range(i):
+            assert not np.array_equal(pos[i], pos[j])
