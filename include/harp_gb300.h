@@ -260,11 +260,17 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  * HARP_OPT_BATCH_DEVICE_US (get only): device time of the last
  * harp_solve_batch whose first context this is, in microseconds, from the
  * first worker's start to the last worker's end (CUDA events on the
- * workers' streams). */
+ * workers' streams).
+ * HARP_OPT_TC_FALLBACKS (get only, process-wide): FP32 products in a
+ * tensor-core mode whose shapes the tensor cores take (M, N >= 64,
+ * K >= 32) but which ran on the CUDA cores because the tensor-core path
+ * refused them (workspace too small, a tensor map the driver would not
+ * encode). A health counter: it stays 0 in a well-sized context. */
 #define HARP_OPT_PANEL_ROWS 4
 #define HARP_OPT_FILL_CHUNK 5
 #define HARP_OPT_SPLITK_MAX 6
 #define HARP_OPT_BATCH_DEVICE_US 7
+#define HARP_OPT_TC_FALLBACKS 8
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

@@ -18,6 +18,7 @@
 // column-parallel swap kernel never runs a long dependency chain; the
 // solve phase applies the net permutation once, as a gather.
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <climits>
 #include <type_traits>
@@ -146,12 +147,18 @@ int cgemm<float>(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   return cgemm_batched(M, N, K, alpha, A, 0, B, 0, beta, C, 0, 1, mode, st);
 }
 
+// Tensor-core-sized FP32 products that ran on the CUDA cores instead.
+static std::atomic<long> g_tc_fallbacks{0};
+
+long tc_fallbacks() { return g_tc_fallbacks.load(); }
+
 int cgemm_batched(int M, int N, int K, float alpha, CView<float> A, long sA, CView<float> B,
                   long sB, float beta, CView<float> C, long sC, int batch, int mode,
                   cudaStream_t st) {
   if (mode != GEMM_SIMT && K > 0) {
     int s = cgemm_tc_f32(M, N, K, alpha, A, B, beta, C, mode, st, sA, sB, sC, batch);
     if (s != HARP_E_UNSUPPORTED) return s;
+    if (M >= 64 && N >= 64 && K >= 32) g_tc_fallbacks.fetch_add(1);
   }
   return cgemm_simt<float>(M, N, K, alpha, A, B, beta, C, st, HARP_K_GEMM, sA, sB, sC, batch);
 }
@@ -1272,7 +1279,9 @@ static int lu_factor_lookahead(harp_ctx* ctx, int N, float* re, float* im, long 
   bool inc = ctx->inv_beside && si[0] && si[1] && wa && wb && ctx->finv && ctx->finv_split &&
              ctx->finv_tmp;
   IncInverse I[2];
-  const size_t wa3 = na / 3, wb3 = nbf / 3;
+  // thirds rounded down to 256 bytes: each third is the base of TMA
+  // tensor maps, which must be 16-byte aligned
+  const size_t wa3 = (na / 3) & ~(size_t)63, wb3 = (nbf / 3) & ~(size_t)63;
   if (inc) {
     const size_t NN = (size_t)ctx->max_N * ctx->max_N;
     const long ldi = ctx->max_N;

@@ -41,6 +41,8 @@ void tc_set_workspace(float* a, size_t a_floats, float* b, size_t b_floats, int*
 void tc_get_workspace(float** a, size_t* a_floats, float** b, size_t* b_floats, int** err);
 // Cap (1..8) on the K splits of this thread's tensor-core products.
 void tc_set_splitk_max(int s);
+// FP32 products of tensor-core shape that fell back to the CUDA cores.
+long tc_fallbacks();
 
 // Float-float refinement pieces (resid.cu).
 int split_c128(int M, int N, const double* Z, long ldz, float* const hl[4], long ldp,

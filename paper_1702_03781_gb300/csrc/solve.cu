@@ -537,6 +537,9 @@ extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
     case HARP_OPT_PANEL_ROWS: *value = ctx->panel_rows; return HARP_OK;
     case HARP_OPT_FILL_CHUNK: *value = ctx->fill_chunk; return HARP_OK;
     case HARP_OPT_SPLITK_MAX: *value = ctx->splitk_max; return HARP_OK;
+    case HARP_OPT_TC_FALLBACKS:
+      *value = (int)std::min<long>(tc_fallbacks(), 2147483647L);
+      return HARP_OK;
     case HARP_OPT_BATCH_DEVICE_US:
       *value = (int)std::min(ctx->batch_device_us + 0.5, 2147483647.0);
       return HARP_OK;

@@ -46,6 +46,7 @@ HARP_OPT_PANEL_ROWS = 4
 HARP_OPT_FILL_CHUNK = 5
 HARP_OPT_SPLITK_MAX = 6
 HARP_OPT_BATCH_DEVICE_US = 7
+HARP_OPT_TC_FALLBACKS = 8
 KNOBS = {"panel_rows": HARP_OPT_PANEL_ROWS, "fill_chunk": HARP_OPT_FILL_CHUNK,
          "splitk_max": HARP_OPT_SPLITK_MAX}
 
@@ -372,6 +373,14 @@ class Harp:
         _check("harp_ctx_get_option", lib().harp_ctx_get_option(
             self._h, HARP_OPT_BATCH_DEVICE_US, ct.byref(v)))
         return v.value / 1e3
+
+    def tc_fallbacks(self) -> int:
+        """Process-wide count of FP32 products of tensor-core shape that ran
+        on the CUDA cores (0 when every workspace and tensor map was fine)."""
+        v = ct.c_int(-1)
+        _check("harp_ctx_get_option", lib().harp_ctx_get_option(
+            self._h, HARP_OPT_TC_FALLBACKS, ct.byref(v)))
+        return v.value
 
     def pivot_fallbacks(self) -> int:
         """Factorisations of this context whose block-restricted pivots were
