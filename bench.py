@@ -134,6 +134,10 @@ def wideband_throughput(device: int, n_ctx: int | None = None, n_freq: int = 64)
     mid = sorted(probs, key=lambda q: q.N)[len(probs) // 2]
     ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n_ctx)]
     knobs = [autotune.apply(c, mid.N, mid.Nm, mid.K, cache) for c in ctxs][0]
+    if tuned and "inverses" in tuned:
+        for c in ctxs:
+            c.set_knob("inverses", int(tuned["inverses"]))
+        knobs = dict(knobs, inverses=int(tuned["inverses"]))
     H.solve_batch(ctxs, items[-n_ctx:], prec="mixed")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -389,6 +393,8 @@ def main():
     coef = torch.from_numpy(p.coef).to(dev)
     sb = torch.from_numpy(p.self_blocks).to(dev)
     h = H.Harp(local, max_N=N, max_nrhs=Na)
+    from paper_1702_03781_gb300 import autotune
+    knobs = autotune.apply(h, N, p.Nm, p.K)  # the tuned tile shapes (defaults when untuned)
     if args.pivot:
         h.set_pivot(args.pivot)
     Z32 = H.colmajor_empty(N, N, torch.complex64, dev)
@@ -519,7 +525,7 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "nrhs": Na, "K": p.K,
-                       "pivot": h.pivot_rule(),
+                       "pivot": h.pivot_rule(), "knobs": knobs,
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "fp64_gpu_ms_per_step": round(statistics.mean(ms_fp64), 4),

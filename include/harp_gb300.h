@@ -261,6 +261,11 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  * harp_solve_batch whose first context this is, in microseconds, from the
  * first worker's start to the last worker's end (CUDA events on the
  * workers' streams).
+ * HARP_OPT_INVERSES: where the FP32 factorisation builds the explicit
+ * inverses of its triangular factors (used by every solve of the
+ * refinement): 0 after the factorisation, 1 beside it (block column by
+ * block column on two more streams, as each panel is done), 2 beside it
+ * except in a harp_solve_batch of several contexts (default).
  * HARP_OPT_TC_FALLBACKS (get only, process-wide): FP32 products in a
  * tensor-core mode whose shapes the tensor cores take (M, N >= 64,
  * K >= 32) but which ran on the CUDA cores because the tensor-core path
@@ -271,6 +276,7 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 #define HARP_OPT_SPLITK_MAX 6
 #define HARP_OPT_BATCH_DEVICE_US 7
 #define HARP_OPT_TC_FALLBACKS 8
+#define HARP_OPT_INVERSES 9
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

@@ -7,7 +7,9 @@ is cut, never what is computed:
   * fill_chunk  -- the largest number of source MBFs a fill CTA stages at
                    once (0: the largest that fits shared memory);
   * splitk_max  -- the cap on the K splits of the solve's tensor-core
-                   products.
+                   products;
+  * inverses    -- where the factor inverses are built: 0 after the
+                   factorisation, 1 beside it, 2 beside it unless batched.
 For a problem class (N, Nm, K) the tuner times one mixed fill + solve of
 the port excitations with CUDA events (median of a few repetitions, after
 a warm-up) and walks the knobs one at a time from the defaults (coordinate
@@ -30,9 +32,9 @@ from . import harp as H
 from . import synth
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
-DEFAULTS = {"panel_rows": 192, "fill_chunk": 0, "splitk_max": 8}
+DEFAULTS = {"panel_rows": 192, "fill_chunk": 0, "splitk_max": 8, "inverses": 2}
 SPACE = {"panel_rows": [96, 128, 192, 256, 384], "fill_chunk": [0, 6, 4, 3, 2],
-         "splitk_max": [8, 4, 2, 1]}
+         "splitk_max": [8, 4, 2, 1], "inverses": [2, 0]}
 MARGIN = 0.01  # a change must save more than 1 % of the step
 
 
@@ -116,9 +118,11 @@ def tune_problem(p, device: int = 0, reps: int = 3, log=None) -> dict:
 
 def tune_batch_workers(problems, device: int = 0, candidates=(2, 3, 4, 6), cache=None,
                        log=None) -> dict:
-    """The number of worker contexts for a batch of problems (device time
-    of one batch call after a warm-up batch), with each context's knobs
-    from the cache for the batch's median problem class."""
+    """The number of worker contexts and where they build their factor
+    inverses (after the factorisation, or beside it on two more streams)
+    for a batch of problems: device time of one batch call after a warm-up
+    batch, each context's other knobs from the cache for the batch's median
+    problem class."""
     cache = load() if cache is None else cache
     dev = f"cuda:{device}"
     items = [H.BatchItem(torch.from_numpy(q.pos).to(dev), q.freq_hz,
@@ -128,19 +132,21 @@ def tune_batch_workers(problems, device: int = 0, candidates=(2, 3, 4, 6), cache
     mid = sorted(problems, key=lambda q: q.N)[len(problems) // 2]
     res = {}
     for n in candidates:
-        ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n)]
-        for c in ctxs:
-            apply(c, mid.N, mid.Nm, mid.K, cache)
-        H.solve_batch(ctxs, items[-n:], prec="mixed")
-        H.solve_batch(ctxs, items, prec="mixed", check=False)
-        res[n] = ctxs[0].batch_device_ms() / len(items)
-        if log:
-            log(f"  workers={n}: {res[n]:.3f} ms per problem")
-        for c in ctxs:
-            c.close()
+        for inv in (2, 1):
+            ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n)]
+            for c in ctxs:
+                apply(c, mid.N, mid.Nm, mid.K, cache)
+                c.set_knob("inverses", inv)
+            H.solve_batch(ctxs, items[-n:], prec="mixed")
+            H.solve_batch(ctxs, items, prec="mixed", check=False)
+            res[(n, inv)] = ctxs[0].batch_device_ms() / len(items)
+            if log:
+                log(f"  workers={n} inverses={inv}: {res[(n, inv)]:.3f} ms per problem")
+            for c in ctxs:
+                c.close()
     best = min(res, key=res.get)
-    return {"workers": best, "ms_per_problem": round(res[best], 4),
-            "trials": {str(k): round(v, 4) for k, v in res.items()},
+    return {"workers": best[0], "inverses": best[1], "ms_per_problem": round(res[best], 4),
+            "trials": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in res.items()},
             "class": key(mid.N, mid.Nm, mid.K)}
 
 

@@ -76,14 +76,15 @@ extern "C" int harp_solve_batch(harp_ctx** ctxs, int n_ctx, harp_problem* probs,
   std::atomic<int> next{0};
   std::vector<std::thread> workers;
   workers.reserve(n_ctx);
-  // With several workers the factorisations overlap one another, so each
-  // builds its factor inverses after itself rather than beside itself
-  // (measured on the 64 wideband frequencies with 4 contexts: 15 ms per
-  // frequency instead of 28).
+  // Where each worker builds its factor inverses (HARP_OPT_INVERSES): by
+  // default after its factorisation when several workers run (their
+  // factorisations overlap one another and leave few idle SMs), beside it
+  // for a single worker; the autotuner measures both.
   std::vector<int> beside(n_ctx);
   for (int c = 0; c < n_ctx; ++c) {
     beside[c] = ctxs[c]->inv_beside;
-    if (n_ctx > 1) ctxs[c]->inv_beside = 0;
+    const int pol = ctxs[c]->inv_policy;
+    ctxs[c]->inv_beside = (pol == 1 || (pol == 2 && n_ctx == 1)) ? 1 : 0;
   }
   // device time of the batch: an event pair on every worker's stream
   std::vector<cudaEvent_t> ev(2 * n_ctx, nullptr);

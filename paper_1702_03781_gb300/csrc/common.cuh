@@ -225,6 +225,9 @@ struct harp_ctx {
   // or builds them after it (0: the batch scheduler, whose concurrent
   // factorisations leave no idle SMs for them).
   int inv_beside;
+  // HARP_OPT_INVERSES: 0 after, 1 beside, 2 beside unless in a batch of
+  // several contexts (default)
+  int inv_policy;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;

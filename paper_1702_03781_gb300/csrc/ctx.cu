@@ -194,6 +194,7 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
       ok = false;
   c->finv_incremental = 0;
   c->inv_beside = 1;
+  c->inv_policy = 2;
   if (ok) {
     c->n_events = max_N / 16 + 2;
     if (cudaMalloc((void**)&c->pmap, (size_t)c->n_events * kPmapInts * sizeof(int)) != cudaSuccess)

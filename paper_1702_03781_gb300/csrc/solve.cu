@@ -511,6 +511,12 @@ extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
     ctx->fill_chunk = value;
     return HARP_OK;
   }
+  if (option == HARP_OPT_INVERSES) {
+    if (value < 0 || value > 2) return -3;
+    ctx->inv_policy = value;
+    ctx->inv_beside = (value != 0) ? 1 : 0;
+    return HARP_OK;
+  }
   if (option == HARP_OPT_SPLITK_MAX) {
     if (value < 1 || value > 8) return -3;
     ctx->splitk_max = value;
@@ -537,6 +543,7 @@ extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
     case HARP_OPT_PANEL_ROWS: *value = ctx->panel_rows; return HARP_OK;
     case HARP_OPT_FILL_CHUNK: *value = ctx->fill_chunk; return HARP_OK;
     case HARP_OPT_SPLITK_MAX: *value = ctx->splitk_max; return HARP_OK;
+    case HARP_OPT_INVERSES: *value = ctx->inv_policy; return HARP_OK;
     case HARP_OPT_TC_FALLBACKS:
       *value = (int)std::min<long>(tc_fallbacks(), 2147483647L);
       return HARP_OK;

@@ -47,8 +47,9 @@ HARP_OPT_FILL_CHUNK = 5
 HARP_OPT_SPLITK_MAX = 6
 HARP_OPT_BATCH_DEVICE_US = 7
 HARP_OPT_TC_FALLBACKS = 8
+HARP_OPT_INVERSES = 9
 KNOBS = {"panel_rows": HARP_OPT_PANEL_ROWS, "fill_chunk": HARP_OPT_FILL_CHUNK,
-         "splitk_max": HARP_OPT_SPLITK_MAX}
+         "splitk_max": HARP_OPT_SPLITK_MAX, "inverses": HARP_OPT_INVERSES}
 
 _lib = None
 
@@ -357,7 +358,8 @@ class Harp:
         return {k: m for m, k in PIVOT.items()}[v.value]
 
     def set_knob(self, name: str, value: int):
-        """A tile-shape knob: 'panel_rows', 'fill_chunk' or 'splitk_max'."""
+        """A scheduling knob: 'panel_rows', 'fill_chunk', 'splitk_max' (tile
+        shapes) or 'inverses' (0 after, 1 beside, 2 beside unless batched)."""
         _check("harp_ctx_set_option",
                lib().harp_ctx_set_option(self._h, KNOBS[name], int(value)))
 

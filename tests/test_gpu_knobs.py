@@ -39,9 +39,10 @@ def _dev(p):
 def test_option_ranges(H):
     with H.Harp(0, max_N=256, max_nrhs=16) as h:
         assert h.knob("panel_rows") == 192 and h.knob("fill_chunk") == 0
-        assert h.knob("splitk_max") == 8
+        assert h.knob("splitk_max") == 8 and h.knob("inverses") == 2
         for name, bad in (("panel_rows", 16), ("panel_rows", 512), ("fill_chunk", -1),
-                          ("splitk_max", 0), ("splitk_max", 9)):
+                          ("splitk_max", 0), ("splitk_max", 9), ("inverses", 3),
+                          ("inverses", -1)):
             with pytest.raises(H.HarpError):
                 h.set_knob(name, bad)
         h.set_knob("splitk_max", 2)
@@ -60,7 +61,7 @@ def test_fill_chunk_bit_identical(H):
         h.sync()
 
 
-@pytest.mark.parametrize("knobs", [{"panel_rows": 96}, {"panel_rows": 384},
+@pytest.mark.parametrize("knobs", [{"panel_rows": 96}, {"panel_rows": 384}, {"inverses": 0},
                                    {"splitk_max": 1}, {"splitk_max": 2, "panel_rows": 128,
                                                        "fill_chunk": 3}])
 def test_solve_meets_bar_for_every_knob(H, knobs):

@@ -12,7 +12,8 @@ from paper_1702_03781_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_wideband_batch_matches_oracle():
+@pytest.mark.parametrize("inverses", [2, 1])
+def test_wideband_batch_matches_oracle(inverses):
     from paper_1702_03781_gb300 import build
     build.build()
     from paper_1702_03781_gb300 import harp as H
@@ -24,6 +25,8 @@ def test_wideband_batch_matches_oracle():
                          torch.from_numpy(probs[i].self_blocks).to(d)) for i in pick]
     max_N = max(it.N for it in items)
     ctxs = [H.Harp(0, max_N=max_N, max_nrhs=256) for _ in range(3)]
+    for c in ctxs:
+        c.set_knob("inverses", inverses)  # 1: built beside each factorisation
     H.solve_batch(ctxs, items, prec="mixed")
     for i, it in zip(pick, items):
         p = probs[i]
