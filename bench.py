@@ -315,22 +315,50 @@ def _peaks():
         return {}
 
 
-def cpu_baseline(steps: int = 1):
-    """The FP64 oracle as it stands: fill + LU solve of the full station
-    (one frequency per step) on this host's cores."""
+def cpu_baseline(steps: int = 3, single_thread: bool = True, lapack_context: bool = True):
+    """The FP64 oracle as it stands: fill + LU solve of the full station (one
+    frequency per run) on this host's cores, the median of `steps` runs;
+    beside it (context, not the baseline) one run of the oracle on a single
+    thread, and numpy's LAPACK zgesv on the oracle's Z (median of 3)."""
     import numpy as np
     import oracle
     from paper_1702_03781_gb300 import synth
     p = synth.station()
-    ts = []
-    for _ in range(steps):
+
+    def run():
         t0 = time.perf_counter()
         Z = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
         oracle.solve(Z, p.V)
-        ts.append(time.perf_counter() - t0)
-    return {"value": 1e3 * statistics.mean(ts), "unit": "ms", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"full station frequency (N=3072, 256 RHS) fill + LU solve, {steps} run(s)"}
+        return time.perf_counter() - t0, Z
+
+    cores = oracle.num_threads()
+    ts = []
+    Z = None
+    for _ in range(steps):
+        t, Z = run()
+        ts.append(t)
+    out = {"value": 1e3 * statistics.median(ts), "unit": "ms", "cores": cores, "kind": "oracle",
+           "runs_ms": [round(1e3 * t, 1) for t in ts],
+           "sample": f"full station frequency (N=3072, 256 RHS) fill + LU solve, median of "
+                     f"{steps} run(s) on {cores} threads"}
+    if single_thread:
+        oracle.set_threads(1)
+        try:
+            t1, _ = run()
+        finally:
+            oracle.set_threads(cores)
+        out["single_thread_ms"] = round(1e3 * t1, 1)
+    if lapack_context:
+        tl = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            np.linalg.solve(Z, p.V)
+            tl.append(time.perf_counter() - t0)
+        out["context_numpy_zgesv_ms"] = round(1e3 * statistics.median(tl), 1)
+        out["context_note"] = ("numpy LAPACK zgesv of the oracle's Z for the 256 port RHS "
+                               "(solve only, median of 3): a tuned CPU library for scale, "
+                               "not the baseline")
+    return out
 
 
 def run_reference(args):
@@ -338,8 +366,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        cpu_baseline(1)
-    cb = cpu_baseline(args.steps)
+        cpu_baseline(1, single_thread=False, lapack_context=False)
+    cb = cpu_baseline(args.steps, single_thread=False, lapack_context=False)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cb["value"], "higher_is_better": False, "scaling": "weak",
@@ -553,7 +581,7 @@ def main():
         if not args.no_wideband:
             line["wideband"] = wideband_throughput(local)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(1)
+            line["cpu_baseline"] = cpu_baseline(3)
         print(json.dumps(line))
     h.close()
     if ws > 1:

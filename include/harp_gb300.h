@@ -455,6 +455,27 @@ int harp_bsr_to_dense(int Na, int Nm, const long* row_ptr, const int* col_idx, l
 int harp_port_objective(int Na, int Nm, const double* X, int ldx, double* P, double* J,
                         double* W, int ldw, void* stream);
 
+/* Impedance reading of the synthesis objective (the same passage; the port
+ * impedance is the inverse of the port response P = E^T X):
+ *   Y = P^-1  (Na x Na, c128; the FP64 solve of P Y = I on ctx),
+ *   J = sum_mn |Y_mn|^2   (one double, device memory),
+ *   G = -Y^H Y Y^H        (Na x Na, c128; dJ = 2 Re tr(G^H dP)),
+ *   W = E conj(G)         (N x Na, c128; the right-hand side of the adjoint
+ *                          solve Z^T Lambda = W, as for harp_port_objective).
+ *   ctx     a context with max_N >= Na and max_nrhs >= Na; its factorisation
+ *           is replaced by P's (use a context other than the one holding
+ *           Z's factors)                                    [1]
+ *   Na, Nm  antennas, MBFs per antenna                      [2, 3]
+ *   P, ldp  c128 Na x Na port response (harp_port_objective) [4, 5]
+ *   Y, ldy  output                                          [6, 7]
+ *   J       output (device double)                          [8]
+ *   G, ldg  output                                          [9, 10]
+ *   W, ldw  output, ldw >= Na Nm; also the scratch of Y^H Y [11, 12]
+ * Returns mbf_solve's status for P (+i on an exactly zero pivot); the rest
+ * is asynchronous on `stream`. */
+int harp_port_impedance(harp_ctx* ctx, int Na, int Nm, const double* P, int ldp, double* Y,
+                        int ldy, double* J, double* G, int ldg, double* W, int ldw, void* stream);
+
 /* ---- Patterns (Section II-C) ---------------------------------------------
  * Embedded element patterns of the ports from the solution of the port
  * excitations: Eq. 5 with the sums swapped as in Eq. 6,

@@ -13,9 +13,11 @@
 //
 // Operands are first copied into "K-major" hi/lo planes (row r of the MMA
 // operand holds its K values contiguously, K padded to a multiple of 32,
-// planes [re_hi, im_hi, re_lo, im_lo]); the kernel loads 32-wide K tiles of
-// them with TMA (128-byte swizzle, one 3-D tensor map per operand with the
-// plane as third coordinate) into a two-stage shared-memory ring.
+// planes [re_hi, im_hi, re_lo, im_lo]); the kernel loads 16-wide K tiles of
+// them with TMA (64-byte swizzle, one 3-D tensor map per operand with the
+// plane as third coordinate) into a two-stage shared-memory ring of 48 KB
+// stages, so that two CTAs share an SM and one's epilogue (the C
+// read-modify-write) overlaps the other's loads and MMAs.
 // Warp roles: warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma
 // (single thread, accumulators in TMEM) and commits each stage back to the
 // producer; then all four warps read the accumulators with tcgen05.ld
@@ -34,11 +36,12 @@ namespace harp {
 
 constexpr int TC_BM = 128;  // rows of C per CTA (TMEM lanes)
 constexpr int TC_BN = 64;   // columns of C per CTA
-constexpr int TC_BK = 32;   // K per stage: one 128-byte swizzle atom of fp32
+constexpr int TC_BK = 16;   // K per stage: one 64-byte swizzle atom of fp32
+constexpr int TC_KPAD = 32; // K padding of the split planes (a multiple of TC_BK)
 constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 128;
-constexpr int TC_A_PLANE = TC_BM * TC_BK * 4;  // 16 KB
-constexpr int TC_B_PLANE = TC_BN * TC_BK * 4;  //  8 KB
+constexpr int TC_A_PLANE = TC_BM * TC_BK * 4;  // 8 KB
+constexpr int TC_B_PLANE = TC_BN * TC_BK * 4;  // 4 KB
 constexpr long long TC_WAIT_CYCLES = 1LL << 30;  // ~0.5 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -83,14 +86,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_64B).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;           // descriptor version
+  d |= (uint64_t)4 << 61;           // 64-byte swizzle
   return d;
 }
 
@@ -135,7 +138,7 @@ struct TcArgs {
 };
 
 template <bool THREE>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
     tc_cgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     TcArgs a) {
   constexpr int NP = THREE ? 4 : 2;  // planes per operand
@@ -224,21 +227,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t Ab = st, Bb = st + NP * TC_A_PLANE;
 #pragma unroll
         for (int j = 0; j < TC_BK / 8; ++j) {
-          const uint32_t ko = 32u * j;  // 8 tf32 = 32 bytes along K inside the atom
-          const uint64_t arh = sw128_desc(Ab + 0 * TC_A_PLANE + ko);
-          const uint64_t aih = sw128_desc(Ab + 1 * TC_A_PLANE + ko);
-          const uint64_t brh = sw128_desc(Bb + 0 * TC_B_PLANE + ko);
-          const uint64_t bih = sw128_desc(Bb + 1 * TC_B_PLANE + ko);
+          const uint32_t ko = 32u * j;  // 8 tf32 = 32 bytes along K inside the 64-byte atom
+          const uint64_t arh = sw64_desc(Ab + 0 * TC_A_PLANE + ko);
+          const uint64_t aih = sw64_desc(Ab + 1 * TC_A_PLANE + ko);
+          const uint64_t brh = sw64_desc(Bb + 0 * TC_B_PLANE + ko);
+          const uint64_t bih = sw64_desc(Bb + 1 * TC_B_PLANE + ko);
           const uint32_t acc = first ? 0u : 1u;
           mma_tf32(d_re, arh, brh, ID, acc);
           mma_tf32(d_im, arh, bih, ID, acc);
           mma_tf32(d_re, aih, bih, IDN, 1u);
           mma_tf32(d_im, aih, brh, ID, 1u);
           if (THREE) {
-            const uint64_t arl = sw128_desc(Ab + 2 * TC_A_PLANE + ko);
-            const uint64_t ail = sw128_desc(Ab + 3 * TC_A_PLANE + ko);
-            const uint64_t brl = sw128_desc(Bb + 2 * TC_B_PLANE + ko);
-            const uint64_t bil = sw128_desc(Bb + 3 * TC_B_PLANE + ko);
+            const uint64_t arl = sw64_desc(Ab + 2 * TC_A_PLANE + ko);
+            const uint64_t ail = sw64_desc(Ab + 3 * TC_A_PLANE + ko);
+            const uint64_t brl = sw64_desc(Bb + 2 * TC_B_PLANE + ko);
+            const uint64_t bil = sw64_desc(Bb + 3 * TC_B_PLANE + ko);
             mma_tf32(d_re, arh, brl, ID, 1u);
             mma_tf32(d_re, arl, brh, ID, 1u);
             mma_tf32(d_re, aih, bil, IDN, 1u);
@@ -372,17 +375,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 3-D map over planes [NP][rows][Kp] fp32, box (32, box_rows, 1), 128B swizzle.
+// 3-D map over planes [NP][rows][Kp] fp32, box (16, box_rows, 1), 64B swizzle.
 static bool make_map_ld(CUtensorMap* m, float* base, int rows, int Kp, long ld, size_t plane,
                         int NP, int box_rows) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NP};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)plane * 4};
-  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};  // 64 bytes of K
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -428,7 +431,7 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   if (batch < 1 || batch > 65535) return HARP_E_UNSUPPORTED;
   const bool three = (mode == GEMM_TC_3XTF32);
   const int NP = three ? 4 : 2;
-  const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
+  const int Kp = (K + TC_KPAD - 1) / TC_KPAD * TC_KPAD;
   const size_t pa = (size_t)M * Kp, pb = (size_t)N * Kp;
   if ((size_t)batch * NP * pa > g_tc.a_floats || (size_t)batch * NP * pb > g_tc.b_floats)
     return HARP_E_UNSUPPORTED;
@@ -469,6 +472,8 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   if (!attr_set[three ? 1 : 0]) {
     HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
+    // the largest shared-memory carveout, so that two CTAs fit on an SM
+    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr_set[three ? 1 : 0] = true;
   }
   dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
@@ -501,8 +506,9 @@ __global__ void splitk_reduce_kernel(int M, int N, int S, const float* __restric
 }
 
 // K splits for a product of `tiles` output tiles and nk k-tiles: the count
-// (at most the solve's cap, 8 by default; at least 8 k-tiles each) that
-// minimises the waves of one-CTA-per-SM work, ceil(tiles S / SMs) / S.
+// (at most the solve's cap, 8 by default; at least 16 k-tiles, K = 256,
+// each) that minimises the waves of two-CTAs-per-SM work,
+// ceil(tiles S / (2 SMs)) / S.
 static int splitk_count(int tiles, int nk) {
   static int sms = 0;
   if (!sms) {
@@ -513,9 +519,9 @@ static int splitk_count(int tiles, int nk) {
   }
   int best = 1;
   double best_t = 1.0;
-  for (int S = 2; S <= g_splitk_max && nk / S >= 8; ++S) {
+  for (int S = 2; S <= g_splitk_max && nk / S >= 16; ++S) {
     if (nk % S) continue;
-    const double t = (double)((tiles * S + sms - 1) / sms) / S;
+    const double t = (double)((tiles * S + 2 * sms - 1) / (2 * sms)) / S;
     if (t < best_t - 1e-9) {
       best_t = t;
       best = S;
@@ -573,7 +579,7 @@ int tc_split_block(int R, int Kc, CView<float> V, float* out, long ldo, size_t p
 int tc_split_operand(int R, int K, CView<float> V, float* out, size_t out_floats, int mode,
                      cudaStream_t st) {
   const bool three = (mode == GEMM_TC_3XTF32);
-  const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
+  const int Kp = (K + TC_KPAD - 1) / TC_KPAD * TC_KPAD;
   const size_t pl = (size_t)R * Kp;
   if ((size_t)(three ? 4 : 2) * pl > out_floats) return HARP_E_UNSUPPORTED;
   ProfScope ps(HARP_K_OTHER, 0.0, st);
@@ -593,7 +599,7 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   if (M < 64 || N < 64 || K < 32 || !g_tc.b || !a_split) return HARP_E_UNSUPPORTED;
   const bool three = (mode == GEMM_TC_3XTF32);
   const int NP = three ? 4 : 2;
-  const int Kp = (K + TC_BK - 1) / TC_BK * TC_BK;
+  const int Kp = (K + TC_KPAD - 1) / TC_KPAD * TC_KPAD;
   const size_t pb = (size_t)N * Kp;
   if ((size_t)NP * pb > g_tc.b_floats) return HARP_E_UNSUPPORTED;
   {
@@ -604,7 +610,7 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   }
   // A's planes: row stride a_ld and plane stride a_plane when it is a block
   // of larger split planes (K extent Kp, a multiple of the k-tile)
-  if (a_ld > 0 && (K % TC_BK != 0 || a_ld < Kp || a_ld % 4 != 0)) return HARP_E_UNSUPPORTED;
+  if (a_ld > 0 && (K % TC_KPAD != 0 || a_ld < Kp || a_ld % 4 != 0)) return HARP_E_UNSUPPORTED;
   CUtensorMap ma, mb;
   if (!make_map_ld(&ma, const_cast<float*>(a_split), M, Kp, a_ld > 0 ? a_ld : Kp,
                    a_ld > 0 ? a_plane : (size_t)M * Kp, NP, TC_BM) ||
@@ -646,6 +652,8 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   if (!attr_set[three ? 1 : 0]) {
     HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
+    // the largest shared-memory carveout, so that two CTAs fit on an SM
+    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr_set[three ? 1 : 0] = true;
   }
   dim3 grid(gx, gy, S);

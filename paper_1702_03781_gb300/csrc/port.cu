@@ -49,9 +49,108 @@ __global__ void port_adjoint_rhs_kernel(int Na, int Nm, const double2* X, long l
   W[(size_t)i + (size_t)n * ldw] = v;
 }
 
+// C = alpha op(A) op(B) for small complex FP64 matrices (n x n, the port
+// response's size): op(X) = X or X^H. 16 x 16 output tiles, K in 16-wide
+// shared-memory chunks.
+constexpr int kZt = 16;
+__global__ void zgemm_small_kernel(int n, int ha, const double2* __restrict__ A, long lda, int hb,
+                                   const double2* __restrict__ B, long ldb, double alpha,
+                                   double2* __restrict__ C, long ldc) {
+  __shared__ double2 As[kZt][kZt + 1], Bs[kZt][kZt + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.y * kZt + ty, j = blockIdx.x * kZt + tx;
+  double cr = 0.0, ci = 0.0;
+  for (int k0 = 0; k0 < n; k0 += kZt) {
+    {  // As[ty][tx] = op(A)(i, k0 + tx)
+      const int k = k0 + tx;
+      double2 v = make_double2(0.0, 0.0);
+      if (i < n && k < n) {
+        v = ha ? A[(size_t)k + (size_t)i * lda] : A[(size_t)i + (size_t)k * lda];
+        if (ha) v.y = -v.y;
+      }
+      As[ty][tx] = v;
+    }
+    {  // Bs[ty][tx] = op(B)(k0 + ty, j)
+      const int k = k0 + ty;
+      double2 v = make_double2(0.0, 0.0);
+      if (k < n && j < n) {
+        v = hb ? B[(size_t)j + (size_t)k * ldb] : B[(size_t)k + (size_t)j * ldb];
+        if (hb) v.y = -v.y;
+      }
+      Bs[ty][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kZt; ++kk) {
+      const double2 a = As[ty][kk], b = Bs[kk][tx];
+      cr += a.x * b.x - a.y * b.y;
+      ci += a.x * b.y + a.y * b.x;
+    }
+    __syncthreads();
+  }
+  if (i < n && j < n) C[(size_t)i + (size_t)j * ldc] = make_double2(alpha * cr, alpha * ci);
+}
+
+// W = E conj(G): conj(G_mn) at row m*Nm of column n, zero elsewhere.
+__global__ void port_impedance_rhs_kernel(int Na, int Nm, const double2* G, long ldg, double2* W,
+                                          long ldw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // row of W
+  const int n = blockIdx.y;                             // column
+  if (i >= Na * Nm) return;
+  double2 v = make_double2(0.0, 0.0);
+  if (i % Nm == 0) {
+    const double2 g = G[(size_t)(i / Nm) + (size_t)n * ldg];
+    v = make_double2(g.x, -g.y);
+  }
+  W[(size_t)i + (size_t)n * ldw] = v;
+}
+
 }  // namespace harp
 
 using namespace harp;
+
+extern "C" int harp_port_impedance(harp_ctx* ctx, int Na, int Nm, const double* P, int ldp,
+                                   double* Y, int ldy, double* J, double* G, int ldg, double* W,
+                                   int ldw, void* stream) {
+  if (!ctx) return -1;
+  if (Na < 1) return -2;
+  if (Nm < 1) return -3;
+  if (!P) return -4;
+  if (ldp < Na) return -5;
+  if (!Y) return -6;
+  if (ldy < Na) return -7;
+  if (!J) return -8;
+  if (!G) return -9;
+  if (ldg < Na) return -10;
+  if (!W) return -11;
+  if (ldw < (long)Na * Nm) return -12;
+  if (Na > 65535) return HARP_E_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  // Y = P^-1: the FP64 solve of P Y = I (the identity is the port
+  // excitation of a system with one basis function per port)
+  int iters = 0;
+  double resid = 0.0;
+  const int s = mbf_solve(ctx, Na, P, ldp, nullptr, Na, Na, Y, ldy, 'N', HARP_FP64, 0.0, 0,
+                          &iters, &resid, stream);
+  if (s != HARP_OK) return s;
+  const dim3 blk(kZt, kZt), grid((Na + kZt - 1) / kZt, (Na + kZt - 1) / kZt);
+  ProfScope ps(HARP_K_OTHER, 0.0, st);
+  port_objective_kernel<<<1, kPortThreads, 0, st>>>(Na, 1, reinterpret_cast<const double2*>(Y), ldy,
+                                                    nullptr, J);  // J = sum |Y|^2
+  HARP_LAUNCHED();
+  // T = Y^H Y in W's storage (W is written last), then G = -T Y^H
+  double2* T = reinterpret_cast<double2*>(W);
+  const double2* Yc = reinterpret_cast<const double2*>(Y);
+  zgemm_small_kernel<<<grid, blk, 0, st>>>(Na, 1, Yc, ldy, 0, Yc, ldy, 1.0, T, ldw);
+  HARP_LAUNCHED();
+  zgemm_small_kernel<<<grid, blk, 0, st>>>(Na, 0, T, ldw, 1, Yc, ldy, -1.0,
+                                           reinterpret_cast<double2*>(G), ldg);
+  HARP_LAUNCHED();
+  port_impedance_rhs_kernel<<<dim3(((long)Na * Nm + 255) / 256, Na), 256, 0, st>>>(
+      Na, Nm, reinterpret_cast<const double2*>(G), ldg, reinterpret_cast<double2*>(W), ldw);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
 
 extern "C" int harp_port_objective(int Na, int Nm, const double* X, int ldx, double* P, double* J,
                                    double* W, int ldw, void* stream) {

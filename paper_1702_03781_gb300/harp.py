@@ -97,6 +97,8 @@ def lib():
         L.harp_solve_batch.restype = i
         L.harp_port_objective.argtypes = [i, i, vp, i, vp, vp, vp, i, vp]
         L.harp_port_objective.restype = i
+        L.harp_port_impedance.argtypes = [vp, i, i, vp, i, vp, i, vp, vp, i, vp, i, vp]
+        L.harp_port_impedance.restype = i
         L.harp_fill_adjoint_noalloc.argtypes = [i, i, i, i, vp, d, vp, vp, vp, i, i, vp, i, vp]
         L.harp_fill_adjoint_noalloc.restype = i
         L.harp_profile_begin.argtypes = [vp, ct.c_uint]
@@ -531,6 +533,26 @@ def port_objective(X: torch.Tensor, Na: int, Nm: int, want_P: bool = True, want_
         Na, Nm, _ptr(X), _ld(X), _ptr(P), _ptr(J), _ptr(W), _ld(W) if W is not None else N,
         _stream(stream)))
     return P, J, W
+
+
+def port_impedance(ctx: "Harp", P: torch.Tensor, Nm: int, stream=None):
+    """(Y, J, G, W) of the impedance reading of the port objective: Y = P^-1
+    (FP64 solve on `ctx`, whose factorisation it replaces), J = sum |Y|^2
+    (0-d float64 tensor), G = -Y^H Y Y^H, W = E conj(G) (N x Na, the adjoint
+    right-hand side). Computed by the library's kernels."""
+    if P.dim() != 2 or P.shape[0] != P.shape[1]:
+        raise ValueError(f"P must be square, got {tuple(P.shape)}")
+    Na = P.shape[0]
+    P = as_colmajor(P.to(torch.complex128))
+    dev = P.device
+    Y = colmajor_empty(Na, Na, torch.complex128, dev)
+    G = colmajor_empty(Na, Na, torch.complex128, dev)
+    W = colmajor_empty(Na * Nm, Na, torch.complex128, dev)
+    J = torch.empty((), dtype=torch.float64, device=dev)
+    _check("harp_port_impedance", lib().harp_port_impedance(
+        ctx.handle, Na, Nm, _ptr(P), _ld(P), _ptr(Y), _ld(Y), _ptr(J), _ptr(G), _ld(G), _ptr(W),
+        _ld(W), _stream(stream)))
+    return Y, J, G, W
 
 
 NOALLOC_MAX_NA = 512

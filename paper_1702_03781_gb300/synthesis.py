@@ -77,3 +77,44 @@ def layout_gradients(harp, problems, prec="mixed", max_iter=60):
         J.backward()
         out.append((float(J.detach()), x.grad, info))
     return out
+
+
+class PortImpedanceObjective(torch.autograd.Function):
+    """J = PortImpedanceObjective.apply(pos, harp, harp_p, freq_hz, coef,
+    self_blocks, prec, max_iter): the impedance reading of the synthesis
+    objective, J = sum_mn |(P^-1)_mn|^2 with P = E^T Z^-1 E.
+
+    `harp` holds Z's factorisation for the backward pass (as for
+    PortObjective); `harp_p` is a second context (max_N >= Na) on which P is
+    inverted. The backward pass is PortObjective's with the adjoint
+    right-hand side E conj(G), G = -Y^H Y Y^H, Y = P^-1.
+    """
+
+    @staticmethod
+    def forward(ctx, pos, harp, harp_p, freq_hz, coef, self_blocks, prec="mixed", max_iter=10):
+        Nm = coef.shape[0]
+        Na = pos.shape[0]
+        Z = harp.fill(pos.detach(), freq_hz, coef, self_blocks,
+                      prec="fp64" if prec == "fp64" else "mixed")
+        X, _ = harp.solve(Z, None, nrhs=Na, prec=prec, max_iter=max_iter)
+        P, _, _ = H.port_objective(X, Na, Nm, want_P=True, want_W=False)
+        _, J, _, W = H.port_impedance(harp_p, P, Nm)
+        ctx.harp, ctx.freq_hz, ctx.prec, ctx.max_iter = harp, freq_hz, prec, max_iter
+        ctx.save_for_backward(pos.detach(), coef, X, W)
+        return J
+
+    @staticmethod
+    def backward(ctx, gJ):
+        pos, coef, X, W = ctx.saved_tensors
+        h = ctx.harp
+        Lam, _ = h.solve(None, W, prec=ctx.prec, trans="T", max_iter=ctx.max_iter)
+        grad = h.fill_adjoint(pos, ctx.freq_hz, coef, Lam, X, prec="fp64")
+        return grad * gJ, None, None, None, None, None, None, None
+
+
+def port_impedance_objective(pos, harp, harp_p, freq_hz, coef, self_blocks, prec="mixed",
+                             max_iter=10):
+    """J (0-d float64 tensor) of the impedance reading; see
+    PortImpedanceObjective."""
+    return PortImpedanceObjective.apply(pos, harp, harp_p, freq_hz, coef, self_blocks, prec,
+                                        max_iter)

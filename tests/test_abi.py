@@ -129,3 +129,24 @@ def test_empty_and_degenerate_sizes_rejected_on_the_host(libpath):
     assert L.harp_port_objective(4, 2, h, 7, h, h, h, 8, None) == -4
     assert L.harp_port_objective(4, 2, h, 8, h, None, h, 8, None) == -6
     assert L.harp_port_objective(4, 2, h, 8, h, h, h, 7, None) == -8
+
+    L.harp_port_impedance.argtypes = [vp, i, i, vp, i, vp, i, vp, vp, i, vp, i, vp]
+    imp = dict(ctx=h, Na=4, Nm=2, P=h, ldp=4, Y=h, ldy=4, J=h, G=h, ldg=4, W=h, ldw=8)
+
+    def impedance(**kw):
+        a = dict(imp, **kw)
+        return L.harp_port_impedance(a["ctx"], a["Na"], a["Nm"], a["P"], a["ldp"], a["Y"],
+                                     a["ldy"], a["J"], a["G"], a["ldg"], a["W"], a["ldw"], None)
+
+    assert impedance(ctx=None) == -1
+    assert impedance(Na=0) == -2
+    assert impedance(Nm=0) == -3
+    assert impedance(P=None) == -4
+    assert impedance(ldp=3) == -5
+    assert impedance(Y=None) == -6
+    assert impedance(ldy=3) == -7
+    assert impedance(J=None) == -8
+    assert impedance(G=None) == -9
+    assert impedance(ldg=3) == -10
+    assert impedance(W=None) == -11
+    assert impedance(ldw=7) == -12
