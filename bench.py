@@ -227,7 +227,7 @@ def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int
     """Config 5's synthesis batch: J and dJ/dpos for seeded random layouts
     1..n_layouts (seeds 5001..5008) of 1024 antennas x 16 MBFs at 110 MHz
     (N = 16384, 1024 ports): forward fill + mixed solve, transposed solve
-    with the cached factors, FP64 adjoint kernel. The layouts are sharded
+    with the cached factors, adjoint kernel (G in double-float). The layouts are sharded
     over the ranks (replicas.shard); each rank times its own with CUDA
     events (one layout per event pair) after one untimed gradient of its
     first layout; the whole job's time is the slowest rank's. The adjoint
@@ -268,7 +268,9 @@ def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int
                            "adjoint": [i["adjoint"]["iters"] for _, _, i in res]},
            "timing": "CUDA events per layout (forward + backward), after one untimed layout"}
     if prof and prof["launches"]:
-        out["adjoint_roofline"] = roofline.entry("adjoint", "fp64", prof, peaks)
+        # G = Lambda X^T (nrhs of the nrhs + K terms per pair) runs in
+        # double-float on the FP32 pipe; the coefficient contraction in FP64
+        out["adjoint_roofline"] = roofline.entry("adjoint", "ff2", prof, peaks)
     return out
 
 

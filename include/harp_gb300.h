@@ -315,8 +315,14 @@ int harp_wait_check(harp_ctx* ctx, int release, void* stream);
  *   Lambda, X    c128 N x nrhs, same leading dimension ld     [9, 10, 11]
  *   nrhs                                                       [12]
  *   grad_pos     double [Na][2], overwritten                   [13]
- *   prec         HARP_FP64, or a mixed mode (FP32 contraction with
- *                FP64 accumulation of the per-pair sums)       [14] */
+ *   prec         how G = Lambda X^T is contracted: HARP_FP64 in FP64;
+ *                a mixed mode in double-float on the FP32 pipe (the
+ *                operands split into float pairs, error-free products,
+ *                Dot2 accumulation: FP64-accurate), using the context's
+ *                float-float scratch when N <= max_N, nrhs <= max_nrhs and
+ *                N nrhs <= max_N^2, else in FP64; HARP_FP32 in FP32. The
+ *                contraction with the coefficients and the per-pair
+ *                derivative sums are FP64 in every mode     [14] */
 int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
                       double freq_hz, const double* coef, const double* Lambda, const double* X,
                       int ld, int nrhs, double* grad_pos, int prec, void* stream);
@@ -564,7 +570,10 @@ int harp_model_fit(int Nm, int P, int Q, int Nd, int Nalpha, const double* d, co
  * (a runtime query, with the device current); make that first call before
  * any stream capture. All calls share the one array: each call clears what
  * it uses, and calls whose work overlaps on the GPU (different streams)
- * race on it, so serialise them. */
+ * race on it, so serialise them. Precision: HARP_FP64 contracts G = Lambda
+ * X^T in FP64 as harp_fill_adjoint does; every other mode contracts it in
+ * FP32 (harp_fill_adjoint's HARP_FP32 kernel): the double-float contraction
+ * of harp_fill_adjoint's mixed modes needs a context's scratch. */
 #define HARP_NOALLOC_MAX_NA 512
 int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos, double freq_hz,
                               const double* coef, const double* Lambda, const double* X, int ld,

@@ -16,10 +16,19 @@
 // CTA forms G for the tile (contraction over the right-hand sides, X rows of
 // antenna n staged in shared memory in chunks), then H (contraction over
 // (T, S) with the coefficient table), then the per-pair derivative sums.
+//
+// Precision of G: FP64 (HARP_FP64), FP32 (HARP_FP32), or, in the mixed
+// modes, double-float on the FP32 pipe: Lambda and X are first split into
+// float pairs (hi + lo, 48 bits), every product is formed error-free
+// (Dekker's product via FMA plus the cross terms) and summed into a
+// double-float accumulator (Ogita-Rump-Oishi Dot2), which is FP64-accurate
+// for these sums at about five times the FP64 pipe's rate on GB300. H and
+// the derivative sums stay in FP64.
 #include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
+#include "ff.cuh"
 #include "prof.cuh"
 
 namespace harp {
@@ -39,10 +48,28 @@ struct AdjArgs {
   long ld;
   double* gpair;  // [m][n][2]
   int BA, n_mtiles, n_items;
+  // double-float G: Lambda and X split into (re_hi, re_lo, im_hi, im_lo),
+  // column r of the right-hand sides at r * N
+  const float4* Lsp;
+  const float4* Xsp;
 };
 
-template <typename R>
+// dst[r N + i] = the float pairs of src[i + r ld] (real, then imaginary).
+__global__ void adjoint_split_kernel(int N, int nrhs, const double2* __restrict__ src, long ld,
+                                     float4* __restrict__ dst) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)N * nrhs) return;
+  const long r = e / N, i = e - r * N;
+  const double2 v = src[i + r * ld];
+  float rh, rl, ih, il;
+  ff_split(v.x, rh, rl);
+  ff_split(v.y, ih, il);
+  dst[e] = make_float4(rh, rl, ih, il);
+}
+
+template <typename R, bool FF>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
+  static_assert(!FF || sizeof(R) == 8, "double-float G feeds the FP64 stages");
   using C = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nm = a.Nm, Nm2 = Nm * Nm, K = a.K, BA = a.BA;
@@ -50,25 +77,63 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
   C* Hs = Gs + (size_t)BA * Nm2;           // [BA][K]
   C* Xs = Hs + (size_t)BA * K;             // [kRChunk][Nm]
   double* geo = reinterpret_cast<double*>(Xs + (size_t)kRChunk * Nm);  // [BA][4]
+  // double-float G only: the tile's Lambda rows for one chunk of right-hand
+  // sides, [kRChunk][BA * Nm]
+  float4* Lf = reinterpret_cast<float4*>(geo + 4 * (size_t)BA);
 
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int n = item / a.n_mtiles;
     const int m0 = (item - n * a.n_mtiles) * BA;
-    const int nG = BA * Nm2;
     // G tile = Lambda rows of the tile times X rows of antenna n (transposed)
     // Each thread owns outputs e = tid + j*blockDim (T fastest).
     constexpr int kMaxOut = 24;
-    C acc[kMaxOut];
+    const int nG = BA * Nm2;
     const int nmine = (nG - (int)threadIdx.x + kAdjThreads - 1) / kAdjThreads;
+    if constexpr (FF) {
+      float4* Xf = reinterpret_cast<float4*>(Xs);  // [kRChunk][Nm], same bytes
+      const long N = (long)a.Na * Nm;
+      float Sr[kMaxOut], er[kMaxOut], Si[kMaxOut], ei[kMaxOut];
 #pragma unroll
-    for (int j = 0; j < kMaxOut; ++j) acc[j] = mk<R>(0, 0);
-    for (int r0 = 0; r0 < a.nrhs; r0 += kRChunk) {
-      const int rc = min(kRChunk, a.nrhs - r0);
-      __syncthreads();
-      for (int e = threadIdx.x; e < rc * Nm; e += blockDim.x) {
-        const int rr = e / Nm, S = e - rr * Nm;
-        const double2 v = a.X[(size_t)n * Nm + S + (size_t)(r0 + rr) * a.ld];
-        Xs[rr * Nm + S] = mk<R>((R)v.x, (R)v.y);
+      for (int j = 0; j < kMaxOut; ++j) Sr[j] = er[j] = Si[j] = ei[j] = 0.f;
+      for (int r0 = 0; r0 < a.nrhs; r0 += kRChunk) {
+        const int rc = min(kRChunk, a.nrhs - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rc * Nm; e += blockDim.x) {
+          const int rr = e / Nm, S = e - rr * Nm;
+          Xf[rr * Nm + S] = a.Xsp[(size_t)n * Nm + S + (size_t)(r0 + rr) * N];
+        }
+        {
+          const int rows = min(BA, a.Na - m0) * Nm;  // the tile's Lambda rows
+          for (int e = threadIdx.x; e < rc * rows; e += blockDim.x) {
+            const int rr = e / rows, q = e - rr * rows;
+            Lf[rr * BA * Nm + q] = a.Lsp[(size_t)m0 * Nm + q + (size_t)(r0 + rr) * N];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kMaxOut; ++j) {
+          if (j >= nmine) break;
+          const int e = threadIdx.x + j * kAdjThreads;
+          const int T = e % Nm, rest = e / Nm;
+          const int S = rest % Nm, mi = rest / Nm;
+          const int m = m0 + mi;
+          if (m >= a.Na) continue;
+          const float4* lrow = Lf + mi * Nm + T;
+          float sr = Sr[j], tr = er[j], si = Si[j], ti = ei[j];
+          for (int rr = 0; rr < rc; ++rr) {
+            const float4 l = lrow[rr * BA * Nm];
+            const float4 x = Xf[rr * Nm + S];
+            // re += lr xr - li xi, im += lr xi + li xr
+            ff2_mac(sr, tr, l.x, l.y, x.x, x.y);
+            ff2_mac(sr, tr, -l.z, -l.w, x.z, x.w);
+            ff2_mac(si, ti, l.x, l.y, x.z, x.w);
+            ff2_mac(si, ti, l.z, l.w, x.x, x.y);
+          }
+          Sr[j] = sr;
+          er[j] = tr;
+          Si[j] = si;
+          ei[j] = ti;
+        }
       }
       __syncthreads();
 #pragma unroll
@@ -77,25 +142,48 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
         const int e = threadIdx.x + j * kAdjThreads;
         const int T = e % Nm, rest = e / Nm;
         const int S = rest % Nm, mi = rest / Nm;
-        const int m = m0 + mi;
-        if (m >= a.Na) continue;
-        const double2* lrow = a.Lam + (size_t)m * Nm + T;
-        C s = acc[j];
-        for (int rr = 0; rr < rc; ++rr) {
-          const double2 l = lrow[(size_t)(r0 + rr) * a.ld];
-          cfma(s, mk<R>((R)l.x, (R)l.y), Xs[rr * Nm + S]);
-        }
-        acc[j] = s;
+        Gs[(size_t)mi * Nm2 + T + Nm * S] =
+            mk<R>((R)((double)Sr[j] + (double)er[j]), (R)((double)Si[j] + (double)ei[j]));
       }
-    }
-    __syncthreads();
+    } else {
+      C acc[kMaxOut];
 #pragma unroll
-    for (int j = 0; j < kMaxOut; ++j) {
-      if (j >= nmine) break;
-      const int e = threadIdx.x + j * kAdjThreads;
-      const int T = e % Nm, rest = e / Nm;
-      const int S = rest % Nm, mi = rest / Nm;
-      Gs[(size_t)mi * Nm2 + T + Nm * S] = acc[j];
+      for (int j = 0; j < kMaxOut; ++j) acc[j] = mk<R>(0, 0);
+      for (int r0 = 0; r0 < a.nrhs; r0 += kRChunk) {
+        const int rc = min(kRChunk, a.nrhs - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rc * Nm; e += blockDim.x) {
+          const int rr = e / Nm, S = e - rr * Nm;
+          const double2 v = a.X[(size_t)n * Nm + S + (size_t)(r0 + rr) * a.ld];
+          Xs[rr * Nm + S] = mk<R>((R)v.x, (R)v.y);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kMaxOut; ++j) {
+          if (j >= nmine) break;
+          const int e = threadIdx.x + j * kAdjThreads;
+          const int T = e % Nm, rest = e / Nm;
+          const int S = rest % Nm, mi = rest / Nm;
+          const int m = m0 + mi;
+          if (m >= a.Na) continue;
+          const double2* lrow = a.Lam + (size_t)m * Nm + T;
+          C s = acc[j];
+          for (int rr = 0; rr < rc; ++rr) {
+            const double2 l = lrow[(size_t)(r0 + rr) * a.ld];
+            cfma(s, mk<R>((R)l.x, (R)l.y), Xs[rr * Nm + S]);
+          }
+          acc[j] = s;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kMaxOut; ++j) {
+        if (j >= nmine) break;
+        const int e = threadIdx.x + j * kAdjThreads;
+        const int T = e % Nm, rest = e / Nm;
+        const int S = rest % Nm, mi = rest / Nm;
+        Gs[(size_t)mi * Nm2 + T + Nm * S] = acc[j];
+      }
     }
     // geometry of the tile's pairs
     for (int mi = threadIdx.x; mi < BA; mi += blockDim.x) {
@@ -196,7 +284,7 @@ __global__ void adjoint_reduce_kernel(int Na, const double* gpair, double* grad)
   grad[2 * m + 1] = gy;
 }
 
-template <typename R>
+template <typename R, bool FF>
 static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st) {
   using C = cplx_t<R>;
   const int Nm2 = a.Nm * a.Nm;
@@ -204,22 +292,23 @@ static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st) {
   size_t smem = 0;
   for (; BA >= 1; BA /= 2) {
     smem = ((size_t)BA * Nm2 + (size_t)BA * a.K + (size_t)kRChunk * a.Nm) * sizeof(C) +
-           (size_t)BA * 4 * sizeof(double);
+           (size_t)BA * 4 * sizeof(double) +
+           (FF ? (size_t)kRChunk * BA * a.Nm * sizeof(float4) : 0);
     if (smem <= std::min<size_t>(ctx->smem_optin, 200 * 1024) && BA * Nm2 <= 24 * kAdjThreads) break;
   }
   if (BA < 1) return HARP_E_UNSUPPORTED;
   a.BA = BA;
   a.n_mtiles = (a.Na + BA - 1) / BA;
   a.n_items = a.Na * a.n_mtiles;
-  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R>,
+  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R, FF>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R>, kAdjThreads,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R, FF>, kAdjThreads,
                                                 smem);
   const int grid = std::min(a.n_items, ctx->num_sms * std::max(1, per_sm));
   ProfScope ps(HARP_K_ADJOINT,
                8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
-  adjoint_pairs_kernel<R><<<grid, kAdjThreads, smem, st>>>(a);
+  adjoint_pairs_kernel<R, FF><<<grid, kAdjThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -276,11 +365,34 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
   a.X = reinterpret_cast<const double2*>(X);
   a.ld = ld;
   a.gpair = ctx->gpair;
+  a.Lsp = nullptr;
+  a.Xsp = nullptr;
   HARP_CUDA(cudaMemsetAsync(ctx->gpair, 0, need, st));
-  if (prec == HARP_FP64)
-    HARP_TRY(launch_adjoint<double>(ctx, a, st));
-  else
-    HARP_TRY(launch_adjoint<float>(ctx, a, st));
+  // mixed modes: G in double-float, the split operands in the context's
+  // float-float scratch (Lambda: 4 max_N max_nrhs floats; X: 4 max_N^2)
+  const long Nl = (long)Na * Nm;
+  const bool ff = (prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32) && ctx->xff && ctx->zff &&
+                  Nl <= ctx->max_N && nrhs <= ctx->max_nrhs &&
+                  Nl * nrhs <= (long)ctx->max_N * ctx->max_N;
+  if (ff) {
+    float4* lsp = reinterpret_cast<float4*>(ctx->xff);
+    float4* xsp = reinterpret_cast<float4*>(ctx->zff);
+    {
+      ProfScope ps(HARP_K_OTHER, 0.0, st);
+      const unsigned blocks = (unsigned)((Nl * nrhs + 255) / 256);
+      adjoint_split_kernel<<<blocks, 256, 0, st>>>((int)Nl, nrhs, a.Lam, ld, lsp);
+      HARP_LAUNCHED();
+      adjoint_split_kernel<<<blocks, 256, 0, st>>>((int)Nl, nrhs, a.X, ld, xsp);
+      HARP_LAUNCHED();
+    }
+    a.Lsp = lsp;
+    a.Xsp = xsp;
+    HARP_TRY((launch_adjoint<double, true>(ctx, a, st)));
+  } else if (prec == HARP_FP32) {
+    HARP_TRY((launch_adjoint<float, false>(ctx, a, st)));
+  } else {
+    HARP_TRY((launch_adjoint<double, false>(ctx, a, st)));
+  }
   adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, ctx->gpair, grad_pos);
   HARP_LAUNCHED();
   return HARP_OK;
@@ -346,15 +458,15 @@ int launch_adjoint_noalloc(int device, AdjArgs a, cudaStream_t st) {
   a.BA = BA;
   a.n_mtiles = (a.Na + BA - 1) / BA;
   a.n_items = a.Na * a.n_mtiles;
-  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R>,
+  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
-  HARP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R>,
+  HARP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R, false>,
                                                           kAdjThreads, smem));
   const int grid = std::min(a.n_items, sms * std::max(1, per_sm));
   ProfScope ps(HARP_K_ADJOINT,
                8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
-  adjoint_pairs_kernel<R><<<grid, kAdjThreads, smem, st>>>(a);
+  adjoint_pairs_kernel<R, false><<<grid, kAdjThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -391,6 +503,8 @@ extern "C" int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const dou
   // is read even without it
   HARP_CUDA(cudaMemsetAsync(scratch, 0, used, st));
   AdjArgs a;
+  a.Lsp = nullptr;
+  a.Xsp = nullptr;
   a.Na = Na;
   a.Nm = Nm;
   a.P = P;

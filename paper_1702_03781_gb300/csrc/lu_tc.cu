@@ -133,16 +133,23 @@ struct TcArgs {
   long crs, ccs;
   long cstride;  // element offset of product z's C (grid z)
   int* err;
-  int ksplit;    // grid z splits K (one product, nk k-tiles each) instead of batching
+  int ksplit;    // 1: grid z splits K (one product, nk k-tiles each) instead of
+                 // batching; 2: grid y runs over chunks of the row tiles' k ranges
   int tri;       // A triangular: 1 upper (row i zero below k = i), 2 lower (zero above)
+  // ksplit 2: row tile t owns chunks [slot_base[t], slot_base[t + 1]) of ck
+  // k-tiles each over its nonzero k range; chunk s writes its partial tile
+  // (128 x N, column-major, ld 128) at cre/cim + s * cstride
+  int ck, ntiles;
+  int slot_base[129];
 };
 
-template <bool THREE>
-__global__ void __launch_bounds__(TC_THREADS, 2)
+template <bool THREE, int BN>
+__global__ void __launch_bounds__(TC_THREADS, BN == 64 ? 2 : 1)
     tc_cgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     TcArgs a) {
   constexpr int NP = THREE ? 4 : 2;  // planes per operand
-  constexpr int STAGE = NP * (TC_A_PLANE + TC_B_PLANE);
+  constexpr int B_PLANE = BN * TC_BK * 4;
+  constexpr int STAGE = NP * (TC_A_PLANE + B_PLANE);
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
   __shared__ uint32_t tmem_slot;
@@ -152,19 +159,31 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (*reinterpret_cast<volatile int*>(a.err)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;  // 1024-byte aligned tiles
-  const int i0 = blockIdx.y * TC_BM, j0 = blockIdx.x * TC_BN;
+  // chunked split: this CTA's row tile (the chunks are few, a linear scan)
+  int ty = blockIdx.y, chunk = 0;
+  if (a.ksplit == 2) {
+    ty = 0;
+    while (ty + 1 < a.ntiles && a.slot_base[ty + 1] <= (int)blockIdx.y) ++ty;
+    chunk = (int)blockIdx.y - a.slot_base[ty];
+  }
+  const int i0 = ty * TC_BM, j0 = blockIdx.x * BN;
   // batched: grid z is the product (its planes in the split operands);
   // split K: grid z is the K range, all of one product
   const int pz = a.ksplit ? 0 : blockIdx.z * NP;
-  const int kt0 = a.ksplit ? blockIdx.z * a.nk : 0;
+  const int kt0 = (a.ksplit == 1) ? blockIdx.z * a.nk : 0;
   // k-tiles [kb, ke) of this CTA's range (relative to kt0): with a
   // triangular A the tiles that are zero for all of its rows are skipped
   int kb = 0, ke = a.nk;
   if (a.tri == 1) kb = max(0, i0 / TC_BK - kt0);
   if (a.tri == 2) ke = min(a.nk, (i0 + TC_BM + TC_BK - 1) / TC_BK - kt0);
+  if (a.ksplit == 2) {
+    kb += chunk * a.ck;
+    ke = min(ke, kb + a.ck);
+  }
   const bool empty = (kb >= ke);
-  float* cre = a.cre + blockIdx.z * a.cstride;
-  float* cim = a.cim + blockIdx.z * a.cstride;
+  const long zoff = (a.ksplit == 2) ? (long)blockIdx.y : (long)blockIdx.z;
+  float* cre = a.cre + zoff * a.cstride;
+  float* cim = a.cim + zoff * a.cstride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -179,7 +198,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(&tmem_slot)),
-                 "r"(2 * TC_BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -187,7 +206,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const uint32_t d_re = tmem, d_im = tmem + TC_BN;
+  const uint32_t d_re = tmem, d_im = tmem + BN;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -202,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         mbar_expect_tx(fb, STAGE);
         for (int q = 0; q < NP; ++q) {
           tma_load_3d(st + q * TC_A_PLANE, &tmA, fb, (kt0 + kt) * TC_BK, i0, pz + q);
-          tma_load_3d(st + NP * TC_A_PLANE + q * TC_B_PLANE, &tmB, fb, (kt0 + kt) * TC_BK, j0,
+          tma_load_3d(st + NP * TC_A_PLANE + q * B_PLANE, &tmB, fb, (kt0 + kt) * TC_BK, j0,
                       pz + q);
         }
         issued = j + 1;
@@ -215,8 +234,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer (single thread)
-      constexpr uint32_t ID = tf32_idesc(TC_BM, TC_BN, false);
-      constexpr uint32_t IDN = tf32_idesc(TC_BM, TC_BN, true);
+      constexpr uint32_t ID = tf32_idesc(TC_BM, BN, false);
+      constexpr uint32_t IDN = tf32_idesc(TC_BM, BN, true);
       bool first = true;
       for (int kt = kb; kt < ke; ++kt) {
         const int it = kt - kb;  // ring iteration, as the producer counts them
@@ -230,8 +249,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           const uint32_t ko = 32u * j;  // 8 tf32 = 32 bytes along K inside the 64-byte atom
           const uint64_t arh = sw64_desc(Ab + 0 * TC_A_PLANE + ko);
           const uint64_t aih = sw64_desc(Ab + 1 * TC_A_PLANE + ko);
-          const uint64_t brh = sw64_desc(Bb + 0 * TC_B_PLANE + ko);
-          const uint64_t bih = sw64_desc(Bb + 1 * TC_B_PLANE + ko);
+          const uint64_t brh = sw64_desc(Bb + 0 * B_PLANE + ko);
+          const uint64_t bih = sw64_desc(Bb + 1 * B_PLANE + ko);
           const uint32_t acc = first ? 0u : 1u;
           mma_tf32(d_re, arh, brh, ID, acc);
           mma_tf32(d_im, arh, bih, ID, acc);
@@ -240,8 +259,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           if (THREE) {
             const uint64_t arl = sw64_desc(Ab + 2 * TC_A_PLANE + ko);
             const uint64_t ail = sw64_desc(Ab + 3 * TC_A_PLANE + ko);
-            const uint64_t brl = sw64_desc(Bb + 2 * TC_B_PLANE + ko);
-            const uint64_t bil = sw64_desc(Bb + 3 * TC_B_PLANE + ko);
+            const uint64_t brl = sw64_desc(Bb + 2 * B_PLANE + ko);
+            const uint64_t bil = sw64_desc(Bb + 3 * B_PLANE + ko);
             mma_tf32(d_re, arh, brl, ID, 1u);
             mma_tf32(d_re, arl, brh, ID, 1u);
             mma_tf32(d_re, aih, bil, IDN, 1u);
@@ -267,7 +286,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   const int gi = i0 + r;
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
 #pragma unroll 1
-  for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+  for (int c0 = 0; c0 < BN; c0 += 16) {
     uint32_t vr[16], vi[16];
     TC_LD16(d_re + lane_off + c0, vr);
     TC_LD16(d_im + lane_off + c0, vi);
@@ -275,7 +294,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     if (ok && gi < a.M) {
       // All loads of the chunk are issued before any store, so the 32 L2
       // round trips overlap instead of serialising behind possible aliasing.
-      const long o0 = (long)gi * a.crs + (long)(j0 + c0) * a.ccs;
+      // (A chunk's partial tile is indexed by the row within the tile.)
+      const long o0 = (long)(a.ksplit == 2 ? r : gi) * a.crs + (long)(j0 + c0) * a.ccs;
       const int nj = min(16, a.N - (j0 + c0));
       float cr[16], ci[16];
       if (a.beta != 0.f) {
@@ -310,7 +330,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * TC_BN)
+                 "r"(2 * BN)
                  : "memory");
   }
 }
@@ -423,6 +443,25 @@ void tc_get_workspace(float** a, size_t* a_floats, float** b, size_t* b_floats, 
   *err = g_tc.err;
 }
 
+// Kernel attributes of one instantiation, set once per process (which also
+// keeps the call out of captured graphs): the dynamic shared memory of its
+// stages and the largest carveout (two CTAs per SM for the 64-wide tile).
+template <bool THREE, int BN>
+static int tc_kernel_attrs(void (**kern)(const CUtensorMap, const CUtensorMap, TcArgs),
+                           size_t* smem) {
+  constexpr int NP = THREE ? 4 : 2;
+  *kern = tc_cgemm_kernel<THREE, BN>;
+  *smem = (size_t)TC_STAGES * NP * (TC_A_PLANE + BN * TC_BK * 4) + 1024;
+  static bool done = false;
+  if (!done) {
+    HARP_CUDA(cudaFuncSetAttribute(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)*smem));
+    HARP_CUDA(cudaFuncSetAttribute(*kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    done = true;
+  }
+  return HARP_OK;
+}
+
 int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> B, float beta,
                  CView<float> C, int mode, cudaStream_t st, long sA, long sB, long sC,
                  int batch) {
@@ -463,19 +502,12 @@ int cgemm_tc_f32(int M, int N, int K, float alpha, CView<float> A, CView<float> 
   args.err = g_tc.err;
   args.ksplit = 0;
   args.tri = 0;
-  const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
-  const size_t smem = (size_t)TC_STAGES * stage + 1024;
-  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
-      three ? tc_cgemm_kernel<true> : tc_cgemm_kernel<false>;
-  static bool attr_set[2] = {false, false};  // per instantiation, set once (also keeps
-                                             // the call out of captured graphs)
-  if (!attr_set[three ? 1 : 0]) {
-    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
-    // the largest shared-memory carveout, so that two CTAs fit on an SM
-    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr_set[three ? 1 : 0] = true;
-  }
+  args.ck = 0;
+  args.ntiles = 0;
+  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) = nullptr;
+  size_t smem = 0;
+  HARP_TRY(three ? tc_kernel_attrs<true, TC_BN>(&kern, &smem)
+                 : tc_kernel_attrs<false, TC_BN>(&kern, &smem));
   dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
   ProfScope ps(HARP_K_GEMM, 8.0 * M * (double)N * K * batch, st);
   kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
@@ -494,6 +526,37 @@ __global__ void splitk_reduce_kernel(int M, int N, int S, const float* __restric
   for (int z = 0; z < S; ++z) {
     sr += ws[o + z * mn];
     si += ws[o + (S + z) * mn];
+  }
+  const size_t c = (size_t)i * C.rs + (size_t)j * C.cs;
+  float cr = alpha * sr, ci = alpha * si;
+  if (beta != 0.f) {
+    cr = fmaf(beta, C.re[c], cr);
+    ci = fmaf(beta, C.im[c], ci);
+  }
+  C.re[c] = cr;
+  C.im[c] = ci;
+}
+
+// C = alpha * (sum of the chunk partials of each row's tile) + beta * C:
+// row i belongs to tile t = i / 128, whose chunks s in [slot_base[t],
+// slot_base[t + 1]) hold 128 x N partial tiles (column-major, ld 128) at
+// re + s 128 N and im + s 128 N; a tile without chunks contributes 0.
+struct TcChunkSum {
+  int ntiles;
+  int slot_base[129];
+};
+
+__global__ void chunk_reduce_kernel(int M, int N, TcChunkSum cs, const float* __restrict__ re,
+                                    const float* __restrict__ im, float alpha, float beta,
+                                    CView<float> C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= M) return;
+  const int t = i / TC_BM, r = i - t * TC_BM;
+  float sr = 0.f, si = 0.f;
+  for (int s = cs.slot_base[t]; s < cs.slot_base[t + 1]; ++s) {
+    const size_t o = (size_t)s * TC_BM * N + r + (size_t)j * TC_BM;
+    sr += re[o];
+    si += im[o];
   }
   const size_t c = (size_t)i * C.rs + (size_t)j * C.cs;
   float cr = alpha * sr, ci = alpha * si;
@@ -611,15 +674,24 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   // A's planes: row stride a_ld and plane stride a_plane when it is a block
   // of larger split planes (K extent Kp, a multiple of the k-tile)
   if (a_ld > 0 && (K % TC_KPAD != 0 || a_ld < Kp || a_ld % 4 != 0)) return HARP_E_UNSUPPORTED;
+  // The refinement's solve products (a triangular A times many right-hand
+  // sides) take 128 x 256 output tiles, one CTA per SM, with each row
+  // tile's nonzero k range cut into equal chunks, so that the SMs get equal
+  // work whatever the triangle leaves each row tile; the other products
+  // 128 x 64 tiles, two CTAs per SM, K split evenly when the grid is small.
+  const int gy = (M + TC_BM - 1) / TC_BM;
+  const int nk = Kp / TC_BK;
+  const bool wide = split_k && a_tri != 0 && N >= 256 && gy <= 128 && g_tc.a;
+  const int BN = wide ? 256 : TC_BN;
   CUtensorMap ma, mb;
   if (!make_map_ld(&ma, const_cast<float*>(a_split), M, Kp, a_ld > 0 ? a_ld : Kp,
                    a_ld > 0 ? a_plane : (size_t)M * Kp, NP, TC_BM) ||
-      !make_map(&mb, g_tc.b, N, Kp, NP, TC_BN))
+      !make_map(&mb, g_tc.b, N, Kp, NP, BN))
     return HARP_E_UNSUPPORTED;
   TcArgs args;
   args.M = M;
   args.N = N;
-  args.nk = Kp / TC_BK;
+  args.nk = nk;
   args.alpha = alpha;
   args.beta = beta;
   args.cre = C.re;
@@ -630,38 +702,85 @@ int cgemm_tc_f32_asplit(int M, int N, int K, float alpha, const float* a_split, 
   args.err = g_tc.err;
   args.ksplit = 0;
   args.tri = a_tri;
-  const int gx = (N + TC_BN - 1) / TC_BN, gy = (M + TC_BM - 1) / TC_BM;
-  int S = split_k ? splitk_count(gx * gy, args.nk) : 1;
-  if ((size_t)2 * S * M * N > g_tc.a_floats || !g_tc.a) S = 1;
-  if (S > 1) {
-    args.nk /= S;
-    args.ksplit = 1;
+  args.ck = 0;
+  args.ntiles = 0;
+  const int gx = (N + BN - 1) / BN;
+  int S = 1, nslots = 0;
+  if (wide) {
+    // chunk length: the triangle's k-tiles over about one CTA per SM, at
+    // least 16 k-tiles (K = 256) per chunk
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          sms < 1)
+        sms = 1;
+    }
+    long total = 0;
+    for (int t = 0; t < gy; ++t) {
+      const int i0 = t * TC_BM;
+      const int kb = (a_tri == 1) ? std::min(nk, i0 / TC_BK) : 0;
+      const int ke = (a_tri == 2) ? std::min(nk, (i0 + TC_BM + TC_BK - 1) / TC_BK) : nk;
+      total += std::max(0, ke - kb);
+    }
+    const int ck = std::max<int>(16, (int)((total * gx + sms - 1) / sms));
+    for (int t = 0; t < gy; ++t) {
+      const int i0 = t * TC_BM;
+      const int kb = (a_tri == 1) ? std::min(nk, i0 / TC_BK) : 0;
+      const int ke = (a_tri == 2) ? std::min(nk, (i0 + TC_BM + TC_BK - 1) / TC_BK) : nk;
+      args.slot_base[t] = nslots;
+      nslots += (std::max(0, ke - kb) + ck - 1) / ck;
+    }
+    args.slot_base[gy] = nslots;
+    if (nslots < 1 || (size_t)2 * nslots * TC_BM * N > g_tc.a_floats) return HARP_E_UNSUPPORTED;
+    args.ksplit = 2;
+    args.ck = ck;
+    args.ntiles = gy;
     args.alpha = 1.f;
     args.beta = 0.f;
     args.cre = g_tc.a;
-    args.cim = g_tc.a + (size_t)S * M * N;
+    args.cim = g_tc.a + (size_t)nslots * TC_BM * N;
     args.crs = 1;
-    args.ccs = M;
-    args.cstride = (long)M * N;
+    args.ccs = TC_BM;
+    args.cstride = (long)TC_BM * N;
+  } else {
+    S = split_k ? splitk_count(gx * gy, nk) : 1;
+    if ((size_t)2 * S * M * N > g_tc.a_floats || !g_tc.a) S = 1;
+    if (S > 1) {
+      args.nk = nk / S;
+      args.ksplit = 1;
+      args.alpha = 1.f;
+      args.beta = 0.f;
+      args.cre = g_tc.a;
+      args.cim = g_tc.a + (size_t)S * M * N;
+      args.crs = 1;
+      args.ccs = M;
+      args.cstride = (long)M * N;
+    }
   }
-  const int stage = NP * (TC_A_PLANE + TC_B_PLANE);
-  const size_t smem = (size_t)TC_STAGES * stage + 1024;
-  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) =
-      three ? tc_cgemm_kernel<true> : tc_cgemm_kernel<false>;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[three ? 1 : 0]) {
-    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)((size_t)TC_STAGES * 4 * (TC_A_PLANE + TC_B_PLANE) + 1024)));
-    // the largest shared-memory carveout, so that two CTAs fit on an SM
-    HARP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr_set[three ? 1 : 0] = true;
-  }
-  dim3 grid(gx, gy, S);
+  void (*kern)(const CUtensorMap, const CUtensorMap, TcArgs) = nullptr;
+  size_t smem = 0;
+  if (wide)
+    HARP_TRY(three ? tc_kernel_attrs<true, 256>(&kern, &smem)
+                   : tc_kernel_attrs<false, 256>(&kern, &smem));
+  else
+    HARP_TRY(three ? tc_kernel_attrs<true, TC_BN>(&kern, &smem)
+                   : tc_kernel_attrs<false, TC_BN>(&kern, &smem));
+  const dim3 grid(gx, wide ? nslots : gy, S);
   // a triangular A: the algorithmic work is half the full product's
   ProfScope ps(HARP_K_GEMM, (a_tri ? 4.0 : 8.0) * M * (double)N * K, st);
   kern<<<grid, TC_THREADS, smem, st>>>(ma, mb, args);
   HARP_LAUNCHED();
-  if (S > 1) {
+  if (wide) {
+    TcChunkSum cs;
+    cs.ntiles = gy;
+    for (int t = 0; t <= gy; ++t) cs.slot_base[t] = args.slot_base[t];
+    chunk_reduce_kernel<<<dim3((M + 255) / 256, N), 256, 0, st>>>(M, N, cs, g_tc.a,
+                                                                  g_tc.a + (size_t)nslots * TC_BM * N,
+                                                                  alpha, beta, C);
+    HARP_LAUNCHED();
+  } else if (S > 1) {
     splitk_reduce_kernel<<<dim3((M + 255) / 256, N), 256, 0, st>>>(M, N, S, g_tc.a, alpha, beta, C);
     HARP_LAUNCHED();
   }

@@ -47,11 +47,14 @@ class PortObjective(torch.autograd.Function):
         # refinement in the mixed mode)
         Lam, adj = h.solve(None, W, prec=ctx.prec, trans="T", max_iter=ctx.max_iter)
         ctx.info["adjoint"] = adj
-        # The contraction G = Lambda X^T with the recomputed derivatives runs
-        # in FP64: summed over ~Na partners per antenna with cancellation, an
-        # FP32 contraction leaves ~1e-6 relative error in the gradient at the
-        # station size, above the synthesis tolerance.
-        grad = h.fill_adjoint(pos, ctx.freq_hz, coef, Lam, X, prec="fp64")
+        # The contraction G = Lambda X^T with the recomputed derivatives is
+        # FP64-accurate: in FP64 on the FP64 path, in double-float on the
+        # FP32 pipe on the mixed path (summed over ~Na partners per antenna
+        # with cancellation, a plain FP32 contraction leaves ~1e-6 relative
+        # error in the gradient at the station size, above the synthesis
+        # tolerance).
+        grad = h.fill_adjoint(pos, ctx.freq_hz, coef, Lam, X,
+                              prec="fp64" if ctx.prec == "fp64" else "mixed")
         return grad * gJ, None, None, None, None, None, None, None
 
 
@@ -108,7 +111,8 @@ class PortImpedanceObjective(torch.autograd.Function):
         pos, coef, X, W = ctx.saved_tensors
         h = ctx.harp
         Lam, _ = h.solve(None, W, prec=ctx.prec, trans="T", max_iter=ctx.max_iter)
-        grad = h.fill_adjoint(pos, ctx.freq_hz, coef, Lam, X, prec="fp64")
+        grad = h.fill_adjoint(pos, ctx.freq_hz, coef, Lam, X,
+                              prec="fp64" if ctx.prec == "fp64" else "mixed")
         return grad * gJ, None, None, None, None, None, None, None
 
 

@@ -7,7 +7,9 @@ the cached factors, adjoint kernel) against the oracle's
 port_impedance_objective_grad.
 
 Tolerances: the kernel outputs within 1e-12 relative (an FP64 solve and
-FP64 products of a well-conditioned 37 x 37 matrix); J within 1e-10; the
+FP64 products of a well-conditioned 37 x 37 matrix); J within 1e-10 on the
+small case and within 2 cond(P) times the measured relative difference of
+P at the station (J inherits P's error amplified by P's conditioning); the
 gradient within 1e-9 (FP64 path) and 1e-6 (mixed path) relative 2-norm,
 the bars of the admittance reading (test_gpu_synthesis.py).
 """
@@ -70,14 +72,29 @@ def test_impedance_gradient_small(ctxs, prec, tol):
 
 
 def test_impedance_gradient_station(ctxs):
+    """The station: J = sum |Y|^2 with Y = P^-1 carries P's relative error
+    amplified by 2 cond(P) (a first-order bound), so J's bar is that bound
+    on the measured difference between the library's P and the oracle's
+    (itself within the solution's 1e-10 bar); the gradient keeps the mixed
+    path's 1e-6."""
+    from paper_1702_03781_gb300 import harp as H
     from paper_1702_03781_gb300.synthesis import port_impedance_objective
     h, hp = ctxs
     p = synth.station()
     d = "cuda:0"
-    x = torch.from_numpy(p.pos).to(d).requires_grad_(True)
-    J = port_impedance_objective(x, h, hp, p.freq_hz, torch.from_numpy(p.coef).to(d),
-                                 torch.from_numpy(p.self_blocks).to(d), prec="mixed")
+    pos, coef, sb = (torch.from_numpy(a).to(d) for a in (p.pos, p.coef, p.self_blocks))
+    Zo = oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks)
+    Po = oracle.solve(Zo, p.V)[np.arange(p.Na) * p.Nm, :]  # E^T X
+    X, _ = h.solve(h.fill(pos, p.freq_hz, coef, sb, prec="mixed"), None, nrhs=p.Na,
+                   prec="mixed")
+    Pg, _, _ = H.port_objective(X, p.Na, p.Nm, want_W=False)
+    dP = _rel(Pg.cpu().numpy(), Po)
+    assert dP <= 1e-10
+    kappa = float(np.linalg.cond(Po))
+    x = pos.clone().requires_grad_(True)
+    J = port_impedance_objective(x, h, hp, p.freq_hz, coef, sb, prec="mixed")
     J.backward()
     Jo, go = oracle.port_impedance_objective_grad(p.pos, p.freq_hz, p.coef, p.self_blocks)
-    assert float(J.detach()) == pytest.approx(Jo, rel=1e-10)
+    tol = max(1e-10, 2.0 * kappa * dP)
+    assert abs(float(J.detach()) - Jo) / Jo <= tol, (kappa, dP)
     assert _rel(x.grad.cpu().numpy(), go) <= 1e-6
