@@ -188,10 +188,12 @@ int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, do
  * pending status after the factorisation: HARP_E_COINCIDENT or
  * HARP_E_NONFINITE left by the fill, or HARP_E_NONFINITE when Z or V holds a
  * NaN or an infinity (checked as they are copied in); X is then not
- * written. The FP32 factorisation also runs
- * work on streams of the context (the trailing updates, and the factor
- * inverses built panel by panel beside it); that work is ordered before
- * anything the call later enqueues on `stream`. Returns +i on an exactly zero pivot
+ * written. The FP32 factorisation runs on streams of the context: its panel
+ * chain on the highest-priority one, its trailing updates on a middle
+ * priority, the factor inverses built panel by panel beside it (and the
+ * background FP64 fill) on the lowest, so that the critical chain gets the
+ * SMs first; all of it is ordered after the caller's earlier work on
+ * `stream` and before anything the call later enqueues there. Returns +i on an exactly zero pivot
  * in column i, HARP_E_NOCONV when tol was not met within max_iter steps: X
  * then holds the iterate with the smallest backward error seen and
  * resid_out that error. */

@@ -194,6 +194,11 @@ struct harp_ctx {
   // Look-ahead LU: side stream for the trailing updates and event pools
   // (panel factored / trailing update done), n_events each.
   cudaStream_t side;
+  // the FP32 factorisation's critical chain (highest priority; forked from
+  // and joined to the caller's stream), and its fork/join events
+  cudaStream_t lu_stream;
+  cudaEvent_t ev_lu_fork, ev_lu_join;
+  int lu_fork;  // run the chain on lu_stream (0 inside a batch of several contexts)
   // Stream of the FP64-accurate fill of Z64 in the mixed modes, which runs
   // beside the factorisation (it needs only the FP32 matrix); ev_fill_fork
   // orders it after the caller's earlier work, ev_z64 marks Z64 complete.

@@ -48,6 +48,9 @@ static void free_all(harp_ctx* c) {
   if (c->blk_uinv) cudaFree(c->blk_uinv);
   if (c->eep_ws) cudaFree(c->eep_ws);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->lu_stream) cudaStreamDestroy(c->lu_stream);
+  if (c->ev_lu_fork) cudaEventDestroy(c->ev_lu_fork);
+  if (c->ev_lu_join) cudaEventDestroy(c->ev_lu_join);
   if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
   for (int q = 0; q < 2; ++q) {
     if (c->inv_stream[q]) cudaStreamDestroy(c->inv_stream[q]);
@@ -182,19 +185,37 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   c->fill_chunk = 0;
   c->splitk_max = 8;
   if (ok && cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
-  if (ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) ok = false;
-  if (ok && cudaStreamCreateWithFlags(&c->fill_stream, cudaStreamNonBlocking) != cudaSuccess)
+  // stream priorities: the factorisation's panel chain first, then its far
+  // trailing updates; the background Z64 fill and the inverse chains last
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = prio_greatest = 0;
+  }
+  const int prio_mid = (prio_least + prio_greatest) / 2;
+  if (ok && cudaStreamCreateWithPriority(&c->lu_stream, cudaStreamNonBlocking, prio_greatest) !=
+                cudaSuccess)
+    ok = false;
+  if (ok && (cudaEventCreateWithFlags(&c->ev_lu_fork, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&c->ev_lu_join, cudaEventDisableTiming) != cudaSuccess))
+    ok = false;
+  if (ok && cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_mid) != cudaSuccess)
+    ok = false;
+  if (ok && cudaStreamCreateWithPriority(&c->fill_stream, cudaStreamNonBlocking, prio_least) !=
+                cudaSuccess)
     ok = false;
   if (ok && (cudaEventCreateWithFlags(&c->ev_fill_fork, cudaEventDisableTiming) != cudaSuccess ||
              cudaEventCreateWithFlags(&c->ev_z64, cudaEventDisableTiming) != cudaSuccess))
     ok = false;
   for (int q = 0; ok && q < 2; ++q)
-    if (cudaStreamCreateWithFlags(&c->inv_stream[q], cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithPriority(&c->inv_stream[q], cudaStreamNonBlocking, prio_least) !=
+            cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_inv[q], cudaEventDisableTiming) != cudaSuccess)
       ok = false;
   c->finv_incremental = 0;
   c->inv_beside = 1;
   c->inv_policy = 2;
+  c->lu_fork = 1;
   if (ok) {
     c->n_events = max_N / 16 + 2;
     if (cudaMalloc((void**)&c->pmap, (size_t)c->n_events * kPmapInts * sizeof(int)) != cudaSuccess)

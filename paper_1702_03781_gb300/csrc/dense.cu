@@ -1410,8 +1410,19 @@ int lu_factor(harp_ctx* ctx, int N, R* re, R* im, long ld, int* ipiv, int* perm,
     HARP_LAUNCHED();
   }
   if constexpr (std::is_same<R, float>::value) {
-    if (ctx->side && mode != GEMM_SIMT)
-      return lu_factor_lookahead(ctx, N, re, im, ld, ipiv, perm, zero_col, mode, st);
+    if (ctx->side && mode != GEMM_SIMT) {
+      if (!ctx->lu_stream || !ctx->lu_fork)
+        return lu_factor_lookahead(ctx, N, re, im, ld, ipiv, perm, zero_col, mode, st);
+      // the chain on the context's highest-priority stream, after the
+      // caller's work and before anything the caller enqueues next
+      HARP_CUDA(cudaEventRecord(ctx->ev_lu_fork, st));
+      HARP_CUDA(cudaStreamWaitEvent(ctx->lu_stream, ctx->ev_lu_fork, 0));
+      const int s =
+          lu_factor_lookahead(ctx, N, re, im, ld, ipiv, perm, zero_col, mode, ctx->lu_stream);
+      HARP_CUDA(cudaEventRecord(ctx->ev_lu_join, ctx->lu_stream));
+      HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_lu_join, 0));
+      return s;
+    }
   }
   CView<R> A = planes<R>(re, im, ld);
   for (int k = 0, nb = 0; k < N; k += nb) {
