@@ -223,6 +223,36 @@ def method_work(N: int, nrhs: int, K: int, prof: dict, info: dict, peaks: dict,
     return out
 
 
+def synthesis_station(device: int, reps: int = 5) -> dict:
+    """Config 4: J and dJ/dpos of the station (256 antennas x 12 MBFs, N =
+    3072) through the autograd Function (forward fill + mixed solve,
+    transposed solve with the cached factors, adjoint kernel), median of
+    `reps` gradients timed with CUDA events after two untimed ones."""
+    import torch
+    from paper_1702_03781_gb300 import harp as H
+    from paper_1702_03781_gb300 import synth
+    from paper_1702_03781_gb300.synthesis import port_objective
+    p = synth.station()
+    d = torch.device("cuda", device)
+    coef = torch.from_numpy(p.coef).to(d)
+    sb = torch.from_numpy(p.self_blocks).to(d)
+    stream = torch.cuda.current_stream()
+    ms = []
+    with H.Harp(device, max_N=p.N, max_nrhs=p.Na) as h:
+        for i in range(2 + reps):
+            x = torch.from_numpy(p.pos).to(d).requires_grad_(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            J = port_objective(x, h, p.freq_hz, coef, sb, prec="mixed")
+            J.backward()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 2:
+                ms.append(e0.elapsed_time(e1))
+    return {"N": p.N, "ports": p.Na, "ms_per_gradient": round(statistics.median(ms), 3),
+            "timing": f"CUDA events around forward + backward, median of {reps} after 2"}
+
+
 def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int = 8) -> dict:
     """Config 5's synthesis batch: J and dJ/dpos for seeded random layouts
     1..n_layouts (seeds 5001..5008) of 1024 antennas x 16 MBFs at 110 MHz
@@ -578,6 +608,8 @@ def main():
                              t_mixed)
         line["method_work"] = method
         line["eep"] = eep_throughput(h, p, X, dev, peaks)
+        if not args.no_synthesis:
+            line["synthesis_station"] = synthesis_station(local)
         if synth_batch is not None:
             line["synthesis_batch"] = synth_batch
         if not args.no_wideband:

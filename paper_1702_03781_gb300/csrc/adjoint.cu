@@ -49,10 +49,24 @@ struct AdjArgs {
   double* gpair;  // [m][n][2]
   int BA, n_mtiles, n_items;
   // double-float G: Lambda and X split into (re_hi, re_lo, im_hi, im_lo),
-  // column r of the right-hand sides at r * N
+  // column r of the right-hand sides at r * N; the coefficients likewise
+  // ([T][S][k] as coef)
   const float4* Lsp;
   const float4* Xsp;
+  const float4* Csp;
 };
+
+// dst[i] = the float pairs of src[i] (real, then imaginary).
+__global__ void split_c128_kernel(long n, const double2* __restrict__ src,
+                                  float4* __restrict__ dst) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = src[i];
+  float rh, rl, ih, il;
+  ff_split(v.x, rh, rl);
+  ff_split(v.y, ih, il);
+  dst[i] = make_float4(rh, rl, ih, il);
+}
 
 // dst[r N + i] = the float pairs of src[i + r ld] (real, then imaginary).
 __global__ void adjoint_split_kernel(int N, int nrhs, const double2* __restrict__ src, long ld,
@@ -142,8 +156,10 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
         const int e = threadIdx.x + j * kAdjThreads;
         const int T = e % Nm, rest = e / Nm;
         const int S = rest % Nm, mi = rest / Nm;
-        Gs[(size_t)mi * Nm2 + T + Nm * S] =
-            mk<R>((R)((double)Sr[j] + (double)er[j]), (R)((double)Si[j] + (double)ei[j]));
+        // G as a normalised float pair (hi + lo = S + e) for the H sums
+        const float hr = __fadd_rn(Sr[j], er[j]), lr = __fsub_rn(er[j], __fsub_rn(hr, Sr[j]));
+        const float hi = __fadd_rn(Si[j], ei[j]), li = __fsub_rn(ei[j], __fsub_rn(hi, Si[j]));
+        reinterpret_cast<float4*>(Gs)[(size_t)mi * Nm2 + T + Nm * S] = make_float4(hr, lr, hi, li);
       }
     } else {
       C acc[kMaxOut];
@@ -199,17 +215,33 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
       geo[4 * mi + 2] = r;
     }
     __syncthreads();
-    // H[mi][k] = sum_TS G[mi][TS] c_k^{TS}
+    // H[mi][k] = sum_TS G[mi][TS] c_k^{TS} (double-float with G)
     for (int e = threadIdx.x; e < BA * K; e += blockDim.x) {
       const int mi = e / K, kk = e - mi * K;
-      C h = mk<R>(0, 0);
-      const C* g = Gs + (size_t)mi * Nm2;
-      for (int S = 0; S < Nm; ++S)
-        for (int T = 0; T < Nm; ++T) {
-          const double2 c = a.coef[((size_t)T * Nm + S) * K + kk];
-          cfma(h, g[T + Nm * S], mk<R>((R)c.x, (R)c.y));
-        }
-      Hs[(size_t)mi * K + kk] = h;
+      if constexpr (FF) {
+        float hr = 0.f, er_ = 0.f, hi = 0.f, ei_ = 0.f;
+        const float4* g = reinterpret_cast<const float4*>(Gs) + (size_t)mi * Nm2;
+        for (int S = 0; S < Nm; ++S)
+          for (int T = 0; T < Nm; ++T) {
+            const float4 gv = g[T + Nm * S];
+            const float4 c = a.Csp[((size_t)T * Nm + S) * K + kk];
+            // re += gr cr - gi ci, im += gr ci + gi cr
+            ff2_mac(hr, er_, gv.x, gv.y, c.x, c.y);
+            ff2_mac(hr, er_, -gv.z, -gv.w, c.z, c.w);
+            ff2_mac(hi, ei_, gv.x, gv.y, c.z, c.w);
+            ff2_mac(hi, ei_, gv.z, gv.w, c.x, c.y);
+          }
+        Hs[(size_t)mi * K + kk] = mk<R>((R)((double)hr + (double)er_), (R)((double)hi + (double)ei_));
+      } else {
+        C h = mk<R>(0, 0);
+        const C* g = Gs + (size_t)mi * Nm2;
+        for (int S = 0; S < Nm; ++S)
+          for (int T = 0; T < Nm; ++T) {
+            const double2 c = a.coef[((size_t)T * Nm + S) * K + kk];
+            cfma(h, g[T + Nm * S], mk<R>((R)c.x, (R)c.y));
+          }
+        Hs[(size_t)mi * K + kk] = h;
+      }
     }
     __syncthreads();
     // per-pair derivative sums (FP64), one thread per pair
@@ -367,13 +399,15 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
   a.gpair = ctx->gpair;
   a.Lsp = nullptr;
   a.Xsp = nullptr;
+  a.Csp = nullptr;
   HARP_CUDA(cudaMemsetAsync(ctx->gpair, 0, need, st));
   // mixed modes: G in double-float, the split operands in the context's
   // float-float scratch (Lambda: 4 max_N max_nrhs floats; X: 4 max_N^2)
   const long Nl = (long)Na * Nm;
   const bool ff = (prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32) && ctx->xff && ctx->zff &&
-                  Nl <= ctx->max_N && nrhs <= ctx->max_nrhs &&
-                  Nl * nrhs <= (long)ctx->max_N * ctx->max_N;
+                  ctx->tc_b && Nl <= ctx->max_N && nrhs <= ctx->max_nrhs &&
+                  Nl * nrhs <= (long)ctx->max_N * ctx->max_N &&
+                  (size_t)4 * Nm * Nm * a.K <= ctx->tc_b_floats;
   if (ff) {
     float4* lsp = reinterpret_cast<float4*>(ctx->xff);
     float4* xsp = reinterpret_cast<float4*>(ctx->zff);
@@ -384,9 +418,15 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
       HARP_LAUNCHED();
       adjoint_split_kernel<<<blocks, 256, 0, st>>>((int)Nl, nrhs, a.X, ld, xsp);
       HARP_LAUNCHED();
+      // the coefficient table into the (idle) tensor-core B workspace
+      const long nc = (long)Nm * Nm * a.K;
+      split_c128_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+          nc, a.coef, reinterpret_cast<float4*>(ctx->tc_b));
+      HARP_LAUNCHED();
     }
     a.Lsp = lsp;
     a.Xsp = xsp;
+    a.Csp = reinterpret_cast<const float4*>(ctx->tc_b);
     HARP_TRY((launch_adjoint<double, true>(ctx, a, st)));
   } else if (prec == HARP_FP32) {
     HARP_TRY((launch_adjoint<float, false>(ctx, a, st)));
@@ -505,6 +545,7 @@ extern "C" int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const dou
   AdjArgs a;
   a.Lsp = nullptr;
   a.Xsp = nullptr;
+  a.Csp = nullptr;
   a.Na = Na;
   a.Nm = Nm;
   a.P = P;

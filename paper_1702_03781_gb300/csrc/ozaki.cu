@@ -21,8 +21,9 @@
 //
 // Combination. The pair results of one group g = t + u share the weight
 // 2^-bg; they are added exactly in integers (re = rr - ii, im = ri + ir),
-// and the groups are combined in FP64 by Horner's rule from the smallest
-// weight up, then scaled back by 2^(sig_i + tau_j). Only the pairs with
+// four groups at a time are combined exactly in 64-bit integers, and those
+// blocks in FP64 by Horner's rule from the smallest weight up, then scaled
+// back by 2^(sig_i + tau_j). Only the pairs with
 // t + u <= G are formed; oz_groups picks G from the accuracy the caller
 // needs (the dropped groups are below the FP64 rounding of the result).
 //
@@ -482,15 +483,29 @@ __global__ void oz_combine_kernel(int N, int nrhs, const int* __restrict__ slots
   double ar = first ? 0.0 : acc_re[o];
   double ai = first ? 0.0 : acc_im[o];
   const double w = ldexp(1.0, -b);
-  for (int g = 0; g < c.ng; ++g) {
-    long long s_re = 0, s_im = 0;
-    for (int p = c.gstart[g]; p < c.gstart[g + 1]; ++p) {
-      const int* sl = slots + (long)c.slot[p] * slot_stride;
-      s_re += sl[o];
-      s_im += sl[(long)nrhs * N + o];
+  // Horner from the smallest weight, four groups at a time: a group's sum of
+  // pair results is an int32 below 2^29 (at most 12 pairs of |v| <= 2^25),
+  // so four consecutive groups combine exactly into the int64
+  // B = sum_j S_j 2^(b j) < 2^(30 + 3b), which a double holds exactly for
+  // b <= 7 (K > 1024; one rounding otherwise); then
+  // acc = 2^(-b (n-1)) (acc w + B), the scaling exact.
+  for (int g0 = 0; g0 < c.ng; g0 += 4) {
+    const int n = min(4, c.ng - g0);
+    long long br = 0, bi = 0;
+    for (int j = 0; j < n; ++j) {
+      int s_re = 0, s_im = 0;
+      for (int p = c.gstart[g0 + j]; p < c.gstart[g0 + j + 1]; ++p) {
+        const int* sl = slots + (long)c.slot[p] * slot_stride;
+        s_re += sl[o];
+        s_im += sl[(long)nrhs * N + o];
+      }
+      const long long m = 1LL << (b * j);
+      br += (long long)s_re * m;
+      bi += (long long)s_im * m;
     }
-    ar = fma(ar, w, (double)s_re);
-    ai = fma(ai, w, (double)s_im);
+    const double sc = ldexp(1.0, -b * (n - 1));
+    ar = fma(ar, w, (double)br) * sc;
+    ai = fma(ai, w, (double)bi) * sc;
   }
   if (!last) {
     acc_re[o] = ar;
