@@ -268,6 +268,10 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  * refinement): 0 after the factorisation, 1 beside it (block column by
  * block column on two more streams, as each panel is done), 2 beside it
  * except in a harp_solve_batch of several contexts (default).
+ * HARP_OPT_FILL_CLUSTERS: how many GPC-sized (16-CTA) clusters the
+ * background FP64 fill of the mixed modes runs on beside the factorisation
+ * (0..64; 0, the default: about half of those the GPU holds; more than it
+ * holds means all of them).
  * HARP_OPT_TC_FALLBACKS (get only, process-wide): FP32 products in a
  * tensor-core mode whose shapes the tensor cores take (M, N >= 64,
  * K >= 32) but which ran on the CUDA cores because the tensor-core path
@@ -279,6 +283,7 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 #define HARP_OPT_BATCH_DEVICE_US 7
 #define HARP_OPT_TC_FALLBACKS 8
 #define HARP_OPT_INVERSES 9
+#define HARP_OPT_FILL_CLUSTERS 10
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

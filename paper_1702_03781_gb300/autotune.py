@@ -9,7 +9,9 @@ is cut, never what is computed:
   * splitk_max  -- the cap on the K splits of the solve's tensor-core
                    products;
   * inverses    -- where the factor inverses are built: 0 after the
-                   factorisation, 1 beside it, 2 beside it unless batched.
+                   factorisation, 1 beside it, 2 beside it unless batched;
+  * fill_clusters -- GPC-sized clusters of the background FP64 fill (0:
+                   about half of those the GPU holds).
 For a problem class (N, Nm, K) the tuner times one mixed fill + solve of
 the port excitations with CUDA events (median of a few repetitions, after
 a warm-up) and walks the knobs one at a time from the defaults (coordinate
@@ -32,9 +34,10 @@ from . import harp as H
 from . import synth
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
-DEFAULTS = {"panel_rows": 192, "fill_chunk": 0, "splitk_max": 8, "inverses": 2}
+DEFAULTS = {"panel_rows": 192, "fill_chunk": 0, "splitk_max": 8, "inverses": 2,
+            "fill_clusters": 0}
 SPACE = {"panel_rows": [96, 128, 192, 256, 384], "fill_chunk": [0, 6, 4, 3, 2],
-         "splitk_max": [8, 4, 2, 1], "inverses": [2, 0]}
+         "splitk_max": [8, 4, 2, 1], "inverses": [2, 0], "fill_clusters": [0, 2, 3, 5, 7]}
 MARGIN = 0.01  # a change must save more than 1 % of the step
 
 

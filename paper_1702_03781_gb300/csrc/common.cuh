@@ -233,6 +233,9 @@ struct harp_ctx {
   // HARP_OPT_INVERSES: 0 after, 1 beside, 2 beside unless in a batch of
   // several contexts (default)
   int inv_policy;
+  // HARP_OPT_FILL_CLUSTERS: GPC-sized clusters of the background FP64 fill
+  // (0: about half of those a GPU holds)
+  int fill_clusters;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;

@@ -364,7 +364,8 @@ static int launch_fill_ff(const harp_ctx* ctx, FillArgs a, int TN, size_t smem, 
   if (slots >= 2) {
     // about half of the cluster slots (4 of the 7 a GB300 holds), split over
     // the source chunks
-    const int q = std::max(1, ((slots + 1) / 2) / nchunks);
+    const int want = (ctx->fill_clusters > 0) ? std::min(ctx->fill_clusters, slots) : (slots + 1) / 2;
+    const int q = std::max(1, want / nchunks);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16 * q, nchunks);
     cfg.blockDim = dim3(kFillThreads);

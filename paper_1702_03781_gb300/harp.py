@@ -48,8 +48,10 @@ HARP_OPT_SPLITK_MAX = 6
 HARP_OPT_BATCH_DEVICE_US = 7
 HARP_OPT_TC_FALLBACKS = 8
 HARP_OPT_INVERSES = 9
+HARP_OPT_FILL_CLUSTERS = 10
 KNOBS = {"panel_rows": HARP_OPT_PANEL_ROWS, "fill_chunk": HARP_OPT_FILL_CHUNK,
-         "splitk_max": HARP_OPT_SPLITK_MAX, "inverses": HARP_OPT_INVERSES}
+         "splitk_max": HARP_OPT_SPLITK_MAX, "inverses": HARP_OPT_INVERSES,
+         "fill_clusters": HARP_OPT_FILL_CLUSTERS}
 
 _lib = None
 
@@ -361,7 +363,9 @@ class Harp:
 
     def set_knob(self, name: str, value: int):
         """A scheduling knob: 'panel_rows', 'fill_chunk', 'splitk_max' (tile
-        shapes) or 'inverses' (0 after, 1 beside, 2 beside unless batched)."""
+        shapes), 'inverses' (0 after, 1 beside, 2 beside unless batched) or
+        'fill_clusters' (GPC-sized clusters of the background FP64 fill, 0:
+        about half)."""
         _check("harp_ctx_set_option",
                lib().harp_ctx_set_option(self._h, KNOBS[name], int(value)))
 

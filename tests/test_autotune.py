@@ -39,7 +39,7 @@ def test_apply_defaults_and_cached(monkeypatch, tmp_path):
     path.write_text(json.dumps(cache))
     c2 = FakeCtx()
     got = autotune.apply(c2, 64, 4, 45, cache=autotune.load(str(path)))
-    assert got == {"panel_rows": 96, "fill_chunk": 0, "splitk_max": 2, "inverses": 2}
+    assert got == dict(autotune.DEFAULTS, panel_rows=96, splitk_max=2)
     assert c2.knobs == got
 
 

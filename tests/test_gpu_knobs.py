@@ -42,7 +42,7 @@ def test_option_ranges(H):
         assert h.knob("splitk_max") == 8 and h.knob("inverses") == 2
         for name, bad in (("panel_rows", 16), ("panel_rows", 512), ("fill_chunk", -1),
                           ("splitk_max", 0), ("splitk_max", 9), ("inverses", 3),
-                          ("inverses", -1)):
+                          ("inverses", -1), ("fill_clusters", -1), ("fill_clusters", 65)):
             with pytest.raises(H.HarpError):
                 h.set_knob(name, bad)
         h.set_knob("splitk_max", 2)
@@ -62,6 +62,7 @@ def test_fill_chunk_bit_identical(H):
 
 
 @pytest.mark.parametrize("knobs", [{"panel_rows": 96}, {"panel_rows": 384}, {"inverses": 0},
+                                   {"fill_clusters": 2}, {"fill_clusters": 7},
                                    {"splitk_max": 1}, {"splitk_max": 2, "panel_rows": 128,
                                                        "fill_chunk": 3}])
 def test_solve_meets_bar_for_every_knob(H, knobs):
