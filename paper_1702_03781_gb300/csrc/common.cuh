@@ -190,6 +190,12 @@ struct harp_ctx {
   // replayed on the caller's stream.
   cudaGraphExec_t solve_graph[2];
   int solve_key[2][4];
+  // the refinement's two per-correction segments as graphs: the correction
+  // (by trans) and the residual update (by digit-group count, or by the
+  // float-float accumulator), with their keys; seen: run once uncaptured
+  cudaGraphExec_t ref_graph[18];
+  int ref_key[18][6];
+  int ref_seen[18];
 
   // Look-ahead LU: side stream for the trailing updates and event pools
   // (panel factored / trailing update done), n_events each.

@@ -43,6 +43,8 @@ static void free_all(harp_ctx* c) {
     if (p) cudaFree(p);
   for (int g = 0; g < 2; ++g)
     if (c->solve_graph[g]) cudaGraphExecDestroy(c->solve_graph[g]);
+  for (int g = 0; g < 18; ++g)
+    if (c->ref_graph[g]) cudaGraphExecDestroy(c->ref_graph[g]);
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->fin) cudaFree(c->fin);
   if (c->blk_uinv) cudaFree(c->blk_uinv);

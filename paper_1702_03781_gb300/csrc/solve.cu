@@ -145,6 +145,61 @@ static int solve32(harp_ctx* ctx, int N, int nrhs, char trans, int mode, bool fi
   return HARP_OK;
 }
 
+// One of the refinement's per-correction segments (body(s) enqueues it on
+// s): the first time a key is seen it runs directly; the second time it is
+// captured on the context's stream and instantiated; afterwards the graph
+// is replayed on st. Bodies read and write only the context's buffers,
+// which never move, so a graph stays valid for its key. Nothing is captured
+// while the profiler records launches.
+template <typename F>
+static int replay_segment(harp_ctx* ctx, int slot, const int* key, F&& body, cudaStream_t st) {
+  if (profiling_active()) return body(st);
+  bool same = ctx->ref_seen[slot] != 0;
+  for (int q = 0; q < 6 && same; ++q) same = (ctx->ref_key[slot][q] == key[q]);
+  if (!same) {
+    if (ctx->ref_graph[slot]) {
+      cudaGraphExecDestroy(ctx->ref_graph[slot]);
+      ctx->ref_graph[slot] = nullptr;
+    }
+    for (int q = 0; q < 6; ++q) ctx->ref_key[slot][q] = key[q];
+    ctx->ref_seen[slot] = 1;
+    return body(st);
+  }
+  if (!ctx->ref_graph[slot]) {
+    cudaGraph_t graph = nullptr;
+    HARP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int s = body(ctx->stream);
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (s != HARP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      ctx->ref_seen[slot] = 0;
+      return s;
+    }
+    HARP_CUDA(e);
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->ref_graph[slot], graph, 0);
+    cudaGraphDestroy(graph);
+    HARP_CUDA(ei);
+  }
+  HARP_CUDA(cudaGraphLaunch(ctx->ref_graph[slot], st));
+  return HARP_OK;
+}
+
+// The FP32 triangular solves of one correction without the solve graph
+// (for capture inside a segment).
+static int solve32_direct(harp_ctx* ctx, int N, int nrhs, char trans, int mode, cudaStream_t st) {
+  const long ldw = ctx->max_N;
+  const size_t NN = (size_t)ctx->max_N * ctx->max_N;
+  const float* fi = ctx->finv;
+  const bool pre = (ctx->finv_split_mode == mode);
+  const float* lsp = pre ? ctx->finv_split : nullptr;
+  const float* usp = pre ? ctx->finv_split + ctx->finv_split_floats : nullptr;
+  const CView<float> Li = linv_view(ctx), Ui = planes<float>(const_cast<float*>(fi) + 2 * NN,
+                                                             const_cast<float*>(fi) + 3 * NN,
+                                                             ctx->max_N);
+  return lu_solve_inv<float>(N, nrhs, Li, Ui, ctx->perm, (float*)ctx->w_re, (float*)ctx->w_im,
+                             ldw, (float*)ctx->t_re, (float*)ctx->t_im, trans, mode, st, lsp, usp);
+}
+
 }  // namespace harp
 
 using namespace harp;
@@ -344,13 +399,14 @@ static int solve_factored(harp_ctx* ctx, int N, const double* V, int ldv, int nr
   double bwd = INFINITY, best = INFINITY;
   int it = 0;
   bool converged = false;
+  // the stopping test's inputs for the first residual; after a correction
+  // the update segment forms them (X's column maxima are then those formed
+  // for the size of the correction: X has not changed since)
+  HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, st));
+  HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
+  HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
+                            cudaMemcpyDeviceToHost, st));
   for (;;) {
-    HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, st));
-    // after a correction, colmax_x already holds X's column maxima (formed
-    // for the size of the correction; X has not changed since)
-    if (it == 0) HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
-    HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
-                              cudaMemcpyDeviceToHost, st));
     HARP_CUDA(cudaStreamSynchronize(st));
     const double* h = ctx->red_host;
     const double znorm = h[0];
@@ -379,30 +435,52 @@ static int solve_factored(harp_ctx* ctx, int N, const double* V, int ldv, int nr
       break;
     }
     if (it >= max_iter) break;
-    // D = (LU32)^{-1} R; X += D
-    HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->r_re, ctx->r_im, ldw, wre, wim, ldw, st));
-    HARP_TRY(solve32(ctx, N, nrhs, tr ? 'T' : 'N', mode, false, st));
-    HARP_TRY(add_planes<float>(N, nrhs, ctx->x_re, ctx->x_im, ldw, wre, wim, ldw, st));
-    // size of the correction against the iterate (host needs it to choose
-    // the accumulator of the update)
-    HARP_TRY(colmax_cabs1_f32(N, nrhs, wre, wim, ldw, colmax_r, st));
-    HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, st));
-    HARP_CUDA(cudaMemcpyAsync(ctx->red_host + 16, colmax_r, sizeof(double) * 2 * (size_t)nrhs,
-                              cudaMemcpyDeviceToHost, st));
+    // correction segment: D = (LU32)^{-1} R; X += D; the size of the
+    // correction against the iterate (which picks the update's digit groups
+    // or accumulator) to the host
+    {
+      const char tch = tr ? 'T' : 'N';
+      const int key[6] = {N, nrhs, mode, tr ? 1 : 0, ctx->finv_split_mode == mode ? 1 : 0,
+                          ctx->finv_incremental};
+      HARP_TRY(replay_segment(ctx, tr ? 1 : 0, key, [&](cudaStream_t s) {
+        HARP_TRY(planes_to_planes<double, float>(N, nrhs, ctx->r_re, ctx->r_im, ldw, wre, wim, ldw,
+                                                 s));
+        HARP_TRY(solve32_direct(ctx, N, nrhs, tch, mode, s));
+        HARP_TRY(add_planes<float>(N, nrhs, ctx->x_re, ctx->x_im, ldw, wre, wim, ldw, s));
+        HARP_TRY(colmax_cabs1_f32(N, nrhs, wre, wim, ldw, colmax_r, s));
+        HARP_TRY(colmax_cabs1(N, nrhs, ctx->x_re, ctx->x_im, ldw, colmax_x, s));
+        HARP_CUDA(cudaMemcpyAsync(ctx->red_host + 16, colmax_r, sizeof(double) * 2 * (size_t)nrhs,
+                                  cudaMemcpyDeviceToHost, s));
+        return (int)HARP_OK;
+      }, st));
+    }
     HARP_CUDA(cudaStreamSynchronize(st));
     double rho = 0.0;
     for (int j = 0; j < nrhs; ++j) {
       const double dj = h[16 + j], xj = h[16 + nrhs + j];
       rho = std::max(rho, (dj == 0.0) ? 0.0 : dj / xj);
     }
-    if (slices) {
-      HARP_TRY(oz_residual(ctx, N, nrhs, wre, wim, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
-                           ctx->r_im, ldw, rho, HARP_K_RESID_UPDATE, st));
-    } else {
-      HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, st));
-      HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
-                           ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms, st,
-                           !(rho <= kDot2Rho)));
+    // update segment: R -= Z D, then the stopping test's inputs to the host
+    {
+      const int variant = slices ? std::min(oz_groups(N, ctx->oz_bits, rho), ctx->oz_slices + 1)
+                                 : (rho <= kDot2Rho ? 14 : 15);
+      const int slot = 2 + std::max(0, std::min(variant, 15));
+      const int key[6] = {N, nrhs, variant, slices ? 1 : 0, tr ? 1 : 0, 0};
+      HARP_TRY(replay_segment(ctx, slot, key, [&](cudaStream_t s) {
+        if (slices) {
+          HARP_TRY(oz_residual(ctx, N, nrhs, wre, wim, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
+                               ctx->r_im, ldw, rho, HARP_K_RESID_UPDATE, s));
+        } else {
+          HARP_TRY(split_f32_planes(N, nrhs, wre, wim, ldw, xhl, s));
+          HARP_TRY(residual_ff(N, nrhs, zhl, ars, acs, xhl, ldw, ctx->r_re, ctx->r_im, ctx->r_re,
+                               ctx->r_im, ldw, ctx->rpart, ctx->rpart + 8 * NR, 8, ctx->num_sms,
+                               s, !(rho <= kDot2Rho)));
+        }
+        HARP_TRY(colmax_cabs1(N, nrhs, ctx->r_re, ctx->r_im, ldw, colmax_r, s));
+        HARP_CUDA(cudaMemcpyAsync(ctx->red_host, ctx->red, sizeof(double) * (16 + 2 * (size_t)nrhs),
+                                  cudaMemcpyDeviceToHost, s));
+        return (int)HARP_OK;
+      }, st));
     }
     ++it;
   }
