@@ -272,6 +272,15 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  * background FP64 fill of the mixed modes runs on beside the factorisation
  * (0..64; 0, the default: about half of those the GPU holds; more than it
  * holds means all of them).
+ * HARP_OPT_FILL64: how the background fill of the mixed modes forms the
+ * FP64-accurate Z (Eq. 3 in Eq. 4): 0 float-float products on the CUDA
+ * cores (the GPC-sized clusters above), 1 exact digit products on the bf16
+ * tensor cores, combined in integers (needs the tensor-core residual's
+ * buffers, K <= 128 and P, Q < 32; otherwise it falls back to 0), 2 (the
+ * default) digit products inside a harp_solve_batch of several contexts,
+ * float-float otherwise. The digit products take a quarter of the time on
+ * the whole GPU; the float-float kernel, confined to half of the GPCs,
+ * overlaps a single factorisation better.
  * HARP_OPT_TC_FALLBACKS (get only, process-wide): FP32 products in a
  * tensor-core mode whose shapes the tensor cores take (M, N >= 64,
  * K >= 32) but which ran on the CUDA cores because the tensor-core path
@@ -284,6 +293,7 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 #define HARP_OPT_TC_FALLBACKS 8
 #define HARP_OPT_INVERSES 9
 #define HARP_OPT_FILL_CLUSTERS 10
+#define HARP_OPT_FILL64 11
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

@@ -242,6 +242,11 @@ struct harp_ctx {
   // HARP_OPT_FILL_CLUSTERS: GPC-sized clusters of the background FP64 fill
   // (0: about half of those a GPU holds)
   int fill_clusters;
+  // HARP_OPT_FILL64: 0 float-float background fill, 1 exact digit products,
+  // 2 digit products inside a batch of several contexts (default);
+  // fill64_now: what the next fill uses (the batch sets it for its run)
+  int fill64;
+  int fill64_now;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;

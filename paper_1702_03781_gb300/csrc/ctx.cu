@@ -218,6 +218,8 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   c->inv_beside = 1;
   c->inv_policy = 2;
   c->fill_clusters = 0;
+  c->fill64 = 2;
+  c->fill64_now = 0;
   c->lu_fork = 1;
   if (ok) {
     c->n_events = max_N / 16 + 2;

@@ -551,10 +551,17 @@ extern "C" int harp_fill(harp_ctx* ctx, int Na, int Nm, int P, int Q, const doub
     // caller's earlier work (a previous solve may still read Z64).
     HARP_CUDA(cudaEventRecord(ctx->ev_fill_fork, st));
     HARP_CUDA(cudaStreamWaitEvent(ctx->fill_stream, ctx->ev_fill_fork, 0));
-    s = fill_dispatch(ctx, Na, Nm, P, Q, reinterpret_cast<const double*>(fb), freq_hz,
-                      reinterpret_cast<const double*>(fb + o_coef),
-                      reinterpret_cast<const double*>(fb + o_self), self_stride, ctx->z64,
-                      ctx->ld64, nullptr, 0, 1, ctx->fill_stream, ctx->dstatus + 3, true);
+    s = HARP_E_UNSUPPORTED;
+    if (ctx->fill64_now)
+      s = oz_fill_z64(ctx, Na, Nm, P, Q, reinterpret_cast<const double*>(fb),
+                      2.0 * kPi * freq_hz / kC0, reinterpret_cast<const double2*>(fb + o_coef),
+                      reinterpret_cast<const double2*>(fb + o_self), self_stride, ctx->z64,
+                      ctx->ld64, ctx->dstatus + 3, ctx->fill_stream);
+    if (s == HARP_E_UNSUPPORTED)
+      s = fill_dispatch(ctx, Na, Nm, P, Q, reinterpret_cast<const double*>(fb), freq_hz,
+                        reinterpret_cast<const double*>(fb + o_coef),
+                        reinterpret_cast<const double*>(fb + o_self), self_stride, ctx->z64,
+                        ctx->ld64, nullptr, 0, 1, ctx->fill_stream, ctx->dstatus + 3, true);
     if (s != HARP_OK) return s;
     // and, when the refinement uses the tensor-core residual, the digit
     // slices of Z64 for trans 'N' solves, on the same stream

@@ -69,6 +69,10 @@ __device__ __forceinline__ int exp_above(double v) {
   const int eb = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
   return (eb == 0 ? 1 : eb) - 1022;
 }
+// v != 0 from the bits (an integer test, off the FP64 pipe)
+__device__ __forceinline__ bool oz_nz(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) != 0;
+}
 __device__ __forceinline__ int exp_above_f(float v) {
   const int eb = (int)((__float_as_uint(v) >> 23) & 0xff);
   return (eb == 0 ? 1 : eb) - 126;
@@ -155,14 +159,29 @@ __global__ void oz_rownorm_kernel(int N, int nch, const double* __restrict__ par
 
 // Digits of one value of a row (column) whose largest exponent is e
 // (|v| < 2^e). The scaled value w = v 2^-(e+1) (|w| < 1/2) is taken to the
-// 64-bit fixed point X = round(w 2^63) (|X| < 2^62; bits below 2^-63 of the
-// scale are dropped, ~2^-61 of the row's largest entry), and out[t * pstride],
-// t < s, gets the signed base-2^b digits from the top, each the
-// round-to-nearest quotient of the remainder by 2^(63 - b(t+1)), so
-// |digit| <= 2^(b-1). Integer arithmetic: the FP64 pipe runs at 1/64 rate.
+// 64-bit fixed point X = round(w 2^63) (|X| <= 2^62; bits below 2^-63 of
+// the scale are dropped, ~2^-61 of the row's largest entry), and
+// out[t * pstride], t < s, gets the signed base-2^b digits from the top,
+// each the round-to-nearest quotient of the remainder by 2^(63 - b(t+1)),
+// so |digit| <= 2^(b-1). Integer arithmetic only (the FP64 pipe runs at
+// 1/64 rate): X comes from the bits of v, v = +-mant 2^(ef - 1075), so
+// X = mant 2^(ef - 1013 - e); as |v| < 2^e the mantissa moves left at most
+// 9 places, and a right move rounds half away from zero (within half a
+// unit, which is all the digit bound needs). The digits fit an int32.
 __device__ __forceinline__ void oz_digits(double v, int e, int b, int s, __nv_bfloat16* out,
                                           size_t pstride) {
-  long long X = oz_none(e) ? 0LL : __double2ll_rn(ldexp(v, 62 - e));
+  const long long bits = __double_as_longlong(v);
+  int ef = (int)((bits >> 52) & 0x7ff);
+  unsigned long long mant = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  if (ef) mant |= 1ull << 52;
+  else ef = 1;
+  const int sh = ef - 1013 - e;
+  long long X = 0;
+  if (!oz_none(e) && mant != 0) {
+    if (sh >= 0) X = (long long)(mant << sh);
+    else if (sh > -63) X = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
+    if (bits < 0) X = -X;
+  }
   int shift = 63;
   for (int t = 0; t < s; ++t) {
     shift -= b;
@@ -174,7 +193,7 @@ __device__ __forceinline__ void oz_digits(double v, int e, int b, int s, __nv_bf
       d = X << (-shift);
       X = 0;
     }
-    out[(size_t)t * pstride] = __float2bfloat16_rn((float)d);
+    out[(size_t)t * pstride] = __float2bfloat16_rn((float)(int)d);
   }
 }
 
@@ -334,11 +353,16 @@ struct OzArgs {
   int* err;
   int* slots;        // [slot][plane][j][i], i contiguous (N), j < nrhs
   long slot_stride;  // 2 * nrhs * N
-  unsigned char pt[kOzMaxPairs], pu[kOzMaxPairs], ps[kOzMaxPairs];  // slice t, u; slot
+  unsigned char pt[kOzMaxPairs], pu[kOzMaxPairs];  // slice t, u of each pair
+  // product y sums the pairs pfirst[y] .. pfirst[y+1]-1 in its accumulators
+  // (exact while their count times K 2^(2b-2) stays within 2^24) and
+  // writes slot ps[y]
+  unsigned char pfirst[kOzMaxPairs + 1], ps[kOzMaxPairs];
 };
 
-// grid (tiles_m * tiles_n, npairs): blockIdx.y picks the slice pair, so the
-// CTAs of one pair (same A slice) run together and share it in L2.
+// grid (tiles_m * tiles_n, nproducts): blockIdx.y picks the product (one
+// slice pair, or several of one group), so the CTAs of one product run
+// together and share its A slices in L2.
 __global__ void __launch_bounds__(OZ_THREADS, 2)
     oz_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const __grid_constant__ OzArgs a) {
@@ -350,8 +374,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
   const uint32_t base = (oz_su32(smem_raw) + 1023u) & ~1023u;
   const int tm = blockIdx.x % a.tiles_m, tn = blockIdx.x / a.tiles_m;
   const int i0 = tm * OZ_BM, j0 = tn * OZ_BN;
-  const int q = blockIdx.y;
-  const int t = a.pt[q], u = a.pu[q];
+  const int y = blockIdx.y;
+  const int q0 = a.pfirst[y], nl = (a.pfirst[y + 1] - q0) * a.nk;  // k tiles over the pairs
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -382,9 +406,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
     if (lane == 0) {
       // ---- TMA producer
       int issued = 0;
-      for (int kt = 0; kt < a.nk; ++kt) {
-        const int s = kt % OZ_STAGES, use = kt / OZ_STAGES;
+      for (int L = 0; L < nl; ++L) {
+        const int s = L % OZ_STAGES, use = L / OZ_STAGES;
         if (use > 0 && !oz_wait(oz_su32(&bar_empty[s]), (use - 1) & 1, a.err)) break;
+        const int qi = L / a.nk, kt = L - qi * a.nk;
+        const int t = a.pt[q0 + qi], u = a.pu[q0 + qi];
         const uint32_t st = base + s * OZ_STAGE;
         const uint32_t fb = oz_su32(&bar_full[s]);
         oz_expect_tx(fb, OZ_STAGE);
@@ -392,7 +418,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
         oz_tma_3d(st + OZ_A_PLANE, &tmA, fb, kt * OZ_BK, i0, 2 * t + 1);
         oz_tma_3d(st + 2 * OZ_A_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u);
         oz_tma_3d(st + 2 * OZ_A_PLANE + OZ_B_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u + 1);
-        issued = kt + 1;
+        issued = L + 1;
       }
       for (int kt = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); kt < issued; ++kt)
         oz_wait(oz_su32(&bar_full[kt % OZ_STAGES]), (kt / OZ_STAGES) & 1, a.err);
@@ -402,7 +428,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
     if (lane == 0) {
       // ---- MMA issuer (single thread)
       constexpr uint32_t ID = bf16_idesc(OZ_BM, 2 * OZ_BN);
-      for (int kt = 0; kt < a.nk; ++kt) {
+      for (int kt = 0; kt < nl; ++kt) {
         const int s = kt % OZ_STAGES, use = kt / OZ_STAGES;
         if (!oz_wait(oz_su32(&bar_full[s]), use & 1, a.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -429,7 +455,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int gi = i0 + warp * 32 + lane;
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-  int* sre = a.slots + (long)a.ps[q] * a.slot_stride;
+  int* sre = a.slots + (long)a.ps[y] * a.slot_stride;
   int* sim = sre + (long)a.nrhs * a.N;
 #pragma unroll 1
   for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
@@ -522,6 +548,257 @@ __global__ void oz_combine_kernel(int N, int nrhs, const int* __restrict__ slots
   const long r = (long)j * ldr + i;
   rr[r] = sr[r] - vr;
   ri[r] = si[r] - vi;
+}
+
+// ---------------------------------------------------------------------------
+// The FP64-accurate fill (Eq. 3 in Eq. 4) as an exact-slice product on the
+// tensor cores. Per ordered antenna pair (m, n), m != n,
+//   Z^{mn}_TS = sum_k C[i][k] Phi[k][j],  i = T + Nm S,  j = m + Na n,
+// with C[i][k] = c_{pq}^{TS} (k = (p + P)(Q + 1) + q, the table's order) and
+// Phi[k][j] = e^{-jkr} e^{j p alpha} d^q of the pair: a product of
+// Nm^2 x K by K x Na^2, cut into digits like the residual's (rows of C and
+// columns of Phi scaled by their largest exponent), the pair products
+// formed by oz_mma_kernel, the groups combined exactly and written to Z64's
+// blocks. The basis is never stored: the digit kernel forms each column in
+// FP64 from the pair's geometry.
+
+// Digits of C: out[(2t + p) * plane + i * Kp + k] for rows i < Np (zero from
+// Nm^2) and k < Kp (zero from K); rexp[i] the row's exponent. One warp per
+// row.
+__global__ void oz_fill_slice_c_kernel(int Nm, int K, int Kp, int Np,
+                                       const double2* __restrict__ coef, int b, int s,
+                                       int* rexp, __nv_bfloat16* out, size_t plane) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= Np) return;
+  const int Nm2 = Nm * Nm;
+  const int T = i % Nm, S = i / Nm;
+  const double2* row = coef + ((size_t)T * Nm + S) * K;
+  int e = OZ_NOEXP;
+  if (i < Nm2)
+    for (int k = lane; k < K; k += 32) {
+      const double2 v = row[k];
+      if (v.x != 0.0) e = max(e, exp_above(v.x));
+      if (v.y != 0.0) e = max(e, exp_above(v.y));
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+  if (lane == 0) rexp[i] = e;
+  for (int k = lane; k < Kp; k += 32) {
+    const double2 v = (i < Nm2 && k < K) ? row[k] : make_double2(0.0, 0.0);
+    __nv_bfloat16* o = out + (size_t)i * Kp + k;
+    oz_digits(v.x, e, b, s, o, 2 * plane);
+    oz_digits(v.y, e, b, s, o + plane, 2 * plane);
+  }
+}
+
+// Digits of Phi for the pair columns j0 .. j0 + nc - 1 (padded to ncp with
+// zero columns): out[(2u + p) * plane + jj * Kp + k], cexp[jj] the column's
+// exponent. A block of 8 warps takes 32 columns. First each lane of warp 0
+// forms one column's factors in FP64 (Eq. 3, 4): the geometry, E_p =
+// e^{-jkr} e^{j p alpha} for |p| <= P and d^q for q <= Q, into shared
+// memory (one warp for all 32: the FP64 pipe's cost is per warp
+// instruction). Then each warp takes 4 of the columns: its lanes form the
+// basis values phi_{p,q} = E_p d^q of their k (k = lane + 32 i, at most 4
+// when K <= 128), the warp their largest exponent, and the digits
+// (coalesced along k). Diagonal pairs (m == n) are zero columns (the self
+// blocks are written apart); coincident antennas are flagged and give zero
+// columns. Shared memory: 32 columns of (2P + 1) complex and (Q + 1) real
+// factors.
+__global__ void __launch_bounds__(256) oz_fill_slice_phi_kernel(
+    int Na, int P, int Q, int K, int Kp, const double* __restrict__ pos, double kw, int j0, int nc,
+    int ncp, int b, int s, int* status, int* cexp, __nv_bfloat16* out, size_t plane) {
+  extern __shared__ double2 oz_fac[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ne = 2 * P + 1, nq = Q + 1;
+  const int per_col = ne + (nq + 1) / 2;  // double2 slots per column
+  double2* E = oz_fac;
+  const int jb = blockIdx.x * 32;  // first column of the block
+  if (warp == 0) {
+    const int jj = jb + lane;
+    const int j = j0 + jj;
+    const int m = j % Na, n = j / Na;
+    bool valid = (jj < nc) && (n < Na) && (m != n);
+    double r = 0.0, dx = 0.0, dy = 0.0;
+    if (valid) {
+      dx = pos[2 * m] - pos[2 * n];
+      dy = pos[2 * m + 1] - pos[2 * n + 1];
+      r = hypot(dx, dy);
+      if (r == 0.0) {
+        atomicOr(status, ST_COINCIDENT);
+        valid = false;
+      }
+    }
+    double2* Ec = E + (size_t)lane * per_col;
+    double* Dc = reinterpret_cast<double*>(Ec + ne);
+    if (valid) {
+      const double d = 1.0 / r;
+      const double zr = dx * d, zi = dy * d;
+      double sn, cs;
+      sincos(kw * r, &sn, &cs);
+      const double phr = cs, phi = -sn;
+      Ec[P] = make_double2(phr, phi);
+      double pr = 1.0, pi = 0.0;  // (e^{j alpha})^p
+      for (int p = 1; p <= P; ++p) {
+        const double tr = pr * zr - pi * zi;
+        pi = pr * zi + pi * zr;
+        pr = tr;
+        Ec[P + p] = make_double2(phr * pr - phi * pi, phr * pi + phi * pr);
+        Ec[P - p] = make_double2(phr * pr + phi * pi, phi * pr - phr * pi);
+      }
+      double dq = 1.0;
+      for (int q = 0; q < nq; ++q) {
+        Dc[q] = dq;
+        dq *= d;
+      }
+    } else {
+      for (int p = 0; p < ne; ++p) Ec[p] = make_double2(0.0, 0.0);
+      for (int q = 0; q < nq; ++q) Dc[q] = 0.0;
+    }
+  }
+  __syncthreads();
+  constexpr int kPer = 4;
+  int kp[kPer], kq[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int k = lane + 32 * i;
+    kp[i] = (k < K) ? k / nq : -1;
+    kq[i] = (k < K) ? k - (k / nq) * nq : 0;
+  }
+  for (int c = warp; c < 32; c += (blockDim.x >> 5)) {
+    const double2* Ec = E + (size_t)c * per_col;
+    const double* Dc = reinterpret_cast<const double*>(Ec + ne);
+    double vr[kPer], vi[kPer];
+    int e = OZ_NOEXP;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      vr[i] = 0.0;
+      vi[i] = 0.0;
+      if (kp[i] >= 0) {
+        const double2 ep = Ec[kp[i]];
+        const double dd = Dc[kq[i]];
+        vr[i] = ep.x * dd;
+        vi[i] = ep.y * dd;
+      }
+      if (oz_nz(vr[i])) e = max(e, exp_above(vr[i]));
+      if (oz_nz(vi[i])) e = max(e, exp_above(vi[i]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+    const int jj = jb + c;
+    if (lane == 0) cexp[jj] = e;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int k = lane + 32 * i;
+      if (k >= Kp) break;
+      __nv_bfloat16* o = out + (size_t)jj * Kp + k;
+      oz_digits(vr[i], e, b, s, o, 2 * plane);
+      oz_digits(vi[i], e, b, s, o + plane, 2 * plane);
+    }
+  }
+}
+
+// The double nearest to a 2^x (a a signed 128-bit integer; ties to even),
+// by integer operations: the bit length, the top 53 bits rounded on the
+// bits below them, the exponent and sign put in place. Results outside the
+// normal range (not met by Z's entries) go through ldexp.
+__device__ __forceinline__ double oz_i128_to_double(__int128 a, int x) {
+  if (a == 0) return 0.0;
+  const unsigned long long sign = (a < 0) ? (1ull << 63) : 0ull;
+  const unsigned __int128 u = (a < 0) ? (unsigned __int128)(-a) : (unsigned __int128)a;
+  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  unsigned long long mant;
+  int ex = x;  // |a| 2^x = mant 2^ex
+  if (nb <= 53) {
+    mant = lo << (53 - nb);
+    ex -= 53 - nb;
+  } else {
+    const int sh = nb - 53;
+    mant = (unsigned long long)(u >> sh);
+    const unsigned __int128 rem = u & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    ex += sh;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++ex;
+    }
+  }
+  const int ef = ex + 52 + 1023;  // mant in [2^52, 2^53)
+  if (ef >= 1 && ef <= 2046)
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)ef << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  const double v = ldexp((double)mant, ex);
+  return sign ? -v : v;
+}
+
+// Groups -> the pair blocks of Z64 for the chunk's columns, one round (every
+// product in the slots). Thread idx = jj Nm^2 + i, i = T + Nm S fastest (the
+// slots' layout: coalesced reads, the block's columns written in runs of
+// Nm). All product results are loaded first (independent loads in flight),
+// then summed exactly in a 128-bit integer in units of the smallest group's
+// weight (product y of group ordinal g, counted from g_max, enters times
+// 2^(b g); at most 16 products of |v| < 2^26 and g <= 11, b <= 8: below
+// 2^118), and the sum is rounded once to FP64 with the scale
+// 2^((er + 1) + (ec + 1) - b g_max): integer work only, off the FP64 pipe.
+constexpr int kOzFillMaxProd = 16;
+struct OzFillCombine {
+  int np;                               // products
+  unsigned char slot[kOzFillMaxProd];   // slot of product y
+  unsigned char shift[kOzFillMaxProd];  // b times its group ordinal
+};
+
+__global__ void oz_fill_combine_kernel(int Na, int Nm, int j0, int nc, const int* __restrict__ slots,
+                                       long slot_stride, const __grid_constant__ OzFillCombine c,
+                                       int b, int gmax, const int* __restrict__ rexp,
+                                       const int* __restrict__ cexp, double2* Z, long ldz) {
+  const int Nm2 = Nm * Nm;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)nc * Nm2) return;
+  const int jj = (int)(idx / Nm2), i = (int)(idx - (long)jj * Nm2);
+  const int j = j0 + jj, m = j % Na, n = j / Na;
+  if (m == n || n >= Na) return;
+  const int er = rexp[i], ec = cexp[jj];
+  double vr = 0.0, vi = 0.0;
+  if (!oz_none(er) && !oz_none(ec)) {
+    int vre[kOzFillMaxProd], vim[kOzFillMaxProd];
+#pragma unroll
+    for (int y = 0; y < kOzFillMaxProd; ++y) {
+      vre[y] = 0;
+      vim[y] = 0;
+      if (y < c.np) {
+        const int* sl = slots + (long)c.slot[y] * slot_stride;
+        vre[y] = sl[idx];
+        vim[y] = sl[(long)nc * Nm2 + idx];
+      }
+    }
+    __int128 ar = 0, ai = 0;
+#pragma unroll
+    for (int y = 0; y < kOzFillMaxProd; ++y) {
+      if (y < c.np) {
+        const int sh = c.shift[y];
+        ar += (__int128)((unsigned __int128)(__int128)vre[y] << sh);
+        ai += (__int128)((unsigned __int128)(__int128)vim[y] << sh);
+      }
+    }
+    const int x = (er + 1) + (ec + 1) - b * gmax;
+    vr = oz_i128_to_double(ar, x);
+    vi = oz_i128_to_double(ai, x);
+  }
+  const int T = i % Nm, S = i / Nm;
+  Z[(size_t)m * Nm + T + ((size_t)n * Nm + S) * ldz] = make_double2(vr, vi);
+}
+
+// The self blocks onto the diagonal blocks of Z64: thread (e, m), e = T + Nm S.
+__global__ void oz_fill_self_kernel(int Na, int Nm, const double2* __restrict__ self,
+                                    long self_stride, double2* Z, long ldz) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (e >= Nm * Nm) return;
+  const int T = e % Nm, S = e / Nm;
+  Z[(size_t)m * Nm + T + ((size_t)m * Nm + S) * ldz] =
+      self[(size_t)m * self_stride + T + (size_t)S * Nm];
 }
 
 // ---------------------------------------------------------------------------
@@ -695,7 +972,9 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
         a.pt[k] = pt[k];
         a.pu[k] = pu[k];
         a.ps[k] = psl[k];
+        a.pfirst[k] = (unsigned char)k;
       }
+      a.pfirst[np] = (unsigned char)np;
       ProfScope ps(prof_kind, 8.0 * np * (double)N * N * nrhs, st);
       oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024, st>>>(
           ma, mb, a);
@@ -709,6 +988,124 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
       HARP_LAUNCHED();
     }
     first = false;
+  }
+  return HARP_OK;
+}
+
+// The FP64-accurate fill on the tensor cores (see oz_fill_slice_c_kernel
+// and what follows): HARP_E_UNSUPPORTED when the residual's buffers are
+// absent or too small for it, or the model is outside the kernels' limits
+// (K <= 128, P, Q < 32); the caller then uses the float-float kernel.
+int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, double kw,
+                const double2* coef, const double2* self, long self_stride, double2* Z, long ldz,
+                int* status, cudaStream_t st) {
+  if (!ctx->oz_a || !ctx->oz_y || !ctx->oz_slots || !ctx->oz_rexp || !ctx->oz_part)
+    return HARP_E_UNSUPPORTED;
+  const int K = (2 * P + 1) * (Q + 1);
+  if (K > 128 || P > 31 || Q > 31) return HARP_E_UNSUPPORTED;
+  const int Nm2 = Nm * Nm;
+  if (Na > 65535) return HARP_E_UNSUPPORTED;  // grid rows of the self-block kernel
+  const int b = oz_digit_bits(K);
+  const int G = oz_groups(K, b, 1.0);
+  const int sl = G - 1;
+  if (sl > ctx->oz_max_slices) return HARP_E_UNSUPPORTED;
+  const int Kp = (K + OZ_BK - 1) / OZ_BK * OZ_BK;
+  const int Np = (Nm2 + OZ_BM - 1) / OZ_BM * OZ_BM;
+  if (Np > ctx->max_N) return HARP_E_UNSUPPORTED;  // row exponents in oz_rexp
+  // buffer capacities (bf16 elements, ints), as ctx.cu sizes them
+  const size_t kpN = ((size_t)ctx->max_N + 63) / 64 * 64, npN = ((size_t)ctx->max_N + 127) / 128 * 128;
+  const size_t rpN = ((size_t)ctx->max_nrhs + 63) / 64 * 64;
+  const size_t a_cap = 2 * (size_t)ctx->oz_max_slices * npN * kpN;
+  const size_t y_cap = 2 * (size_t)ctx->oz_max_slices * rpN * kpN;
+  const size_t slot_cap = (size_t)ctx->oz_slot_pairs * 2 * (size_t)ctx->max_N * ctx->max_nrhs;
+  const size_t cexp_cap = 2 * 32 * (size_t)ctx->max_N;  // oz_part as ints
+  if (2 * (size_t)sl * Np * Kp > a_cap) return HARP_E_UNSUPPORTED;
+  // The pairs (t, u), t + u = g, in descending groups, one round. The pairs
+  // of a group add up in one product's FP32 accumulators while the sum stays
+  // an exact integer: each pair's real products are below K 2^(2b-2), so
+  // runs of up to 2^24 / (K 2^(2b-2)) pairs (10 at K = 102, b = 8).
+  const long run = std::max<long>(1, (1L << 24) / ((long)K << (2 * b - 2)));
+  OzArgs a;
+  OzFillCombine c;
+  int np = 0, nprod = 0;
+  a.pfirst[0] = 0;
+  for (int g = G; g >= 2; --g) {
+    const int tlo = std::max(1, g - sl), thi = std::min(g - 1, sl);
+    for (int t = tlo; t <= thi; ++t) {
+      if (np >= kOzMaxPairs) return HARP_E_UNSUPPORTED;
+      a.pt[np] = (unsigned char)(t - 1);
+      a.pu[np] = (unsigned char)(g - t - 1);
+      ++np;
+      if (t == thi || np - a.pfirst[nprod] == run) {
+        if (nprod >= kOzFillMaxProd) return HARP_E_UNSUPPORTED;
+        a.ps[nprod] = (unsigned char)nprod;
+        c.slot[nprod] = (unsigned char)nprod;
+        c.shift[nprod] = (unsigned char)(b * (G - g));
+        a.pfirst[++nprod] = (unsigned char)np;
+      }
+    }
+  }
+  c.np = nprod;
+  if (nprod < 1 || b * (G - 2) > 88) return HARP_E_UNSUPPORTED;
+  // pair columns per round: up to 8192 (enough basis blocks to spread the
+  // FP64 geometry over the SMs; the round's products, ~75 MB at 144 MBF
+  // pairs, mostly stay in L2), within the digit and slot buffers
+  long chunk = 8192;
+  chunk = std::min<long>(chunk, (long)(y_cap / (2 * (size_t)sl * Kp)) / OZ_BN * OZ_BN);
+  chunk = std::min<long>(chunk, (long)(slot_cap / ((size_t)nprod * 2 * Nm2)) / OZ_BN * OZ_BN);
+  chunk = std::min<long>(chunk, (long)cexp_cap / OZ_BN * OZ_BN);
+  if (chunk < OZ_BN) return HARP_E_UNSUPPORTED;
+  __nv_bfloat16* adig = (__nv_bfloat16*)ctx->oz_a;
+  __nv_bfloat16* ydig = (__nv_bfloat16*)ctx->oz_y;
+  const size_t plane_a = (size_t)Np * Kp;
+  int* cexp = reinterpret_cast<int*>(ctx->oz_part);
+  {
+    ProfScope ps(HARP_K_OTHER, 0.0, st);
+    oz_fill_slice_c_kernel<<<(Np + 7) / 8, 256, 0, st>>>(Nm, K, Kp, Np, coef, b, sl, ctx->oz_rexp,
+                                                         adig, plane_a);
+    HARP_LAUNCHED();
+    oz_fill_self_kernel<<<dim3((Nm2 + 127) / 128, Na), 128, 0, st>>>(Na, Nm, self, self_stride, Z,
+                                                                      ldz);
+    HARP_LAUNCHED();
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    HARP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   OZ_STAGES * OZ_STAGE + 1024));
+    attr_set = true;
+  }
+  // the basis kernel's factor table: 32 columns
+  const size_t phi_smem = 32 * (size_t)(2 * P + 1 + (Q + 2) / 2) * sizeof(double2);
+  if (phi_smem > 48 * 1024)
+    HARP_CUDA(cudaFuncSetAttribute(oz_fill_slice_phi_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phi_smem));
+  CUtensorMap ma;
+  if (!oz_map(&ma, adig, Np, Kp, 2 * sl, OZ_BM)) return HARP_E_UNSUPPORTED;
+  const long npairs = (long)Na * Na;
+  const int tiles_m = Np / OZ_BM;
+  ProfScope ps(HARP_K_FILL_FF, 8.0 * Nm2 * (double)K * Na * (Na - 1), st);
+  for (long j0 = 0; j0 < npairs; j0 += chunk) {
+    const int nc = (int)std::min<long>(chunk, npairs - j0);
+    const int ncp = (nc + OZ_BN - 1) / OZ_BN * OZ_BN;
+    const size_t plane_y = (size_t)ncp * Kp;
+    oz_fill_slice_phi_kernel<<<ncp / 32, 256, phi_smem, st>>>(
+        Na, P, Q, K, Kp, pos, kw, (int)j0, nc, ncp, b, sl, status, cexp, ydig, plane_y);
+    HARP_LAUNCHED();
+    CUtensorMap mb;
+    if (!oz_map(&mb, ydig, ncp, Kp, 2 * sl, OZ_BN)) return HARP_E_UNSUPPORTED;
+    a.N = Nm2;
+    a.nrhs = nc;
+    a.nk = Kp / OZ_BK;
+    a.tiles_m = tiles_m;
+    a.err = ctx->dstatus + 2;
+    a.slots = ctx->oz_slots;
+    a.slot_stride = 2L * nc * Nm2;
+    oz_mma_kernel<<<dim3(tiles_m * (ncp / OZ_BN), nprod), OZ_THREADS,
+                    OZ_STAGES * OZ_STAGE + 1024, st>>>(ma, mb, a);
+    HARP_LAUNCHED();
+    oz_fill_combine_kernel<<<(unsigned)(((long)nc * Nm2 + 255) / 256), 256, 0, st>>>(
+        Na, Nm, (int)j0, nc, ctx->oz_slots, 2L * nc * Nm2, c, b, G, ctx->oz_rexp, cexp, Z, ldz);
+    HARP_LAUNCHED();
   }
   return HARP_OK;
 }

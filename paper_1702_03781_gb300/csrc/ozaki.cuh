@@ -26,4 +26,12 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
                 const double* sr, const double* si, double* rr, double* ri, long ldr, double rho,
                 int prof_kind, cudaStream_t st);
 
+// The FP64-accurate fill of Z (Eq. 3 in Eq. 4) on the tensor cores by exact
+// digit products: Z64's pair blocks and self blocks, coincident antennas or-ed
+// into *status. HARP_E_UNSUPPORTED when it does not apply (the caller falls
+// back to the float-float kernel).
+int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, double kw,
+                const double2* coef, const double2* self, long self_stride, double2* Z, long ldz,
+                int* status, cudaStream_t st);
+
 }  // namespace harp

@@ -49,9 +49,10 @@ HARP_OPT_BATCH_DEVICE_US = 7
 HARP_OPT_TC_FALLBACKS = 8
 HARP_OPT_INVERSES = 9
 HARP_OPT_FILL_CLUSTERS = 10
+HARP_OPT_FILL64 = 11
 KNOBS = {"panel_rows": HARP_OPT_PANEL_ROWS, "fill_chunk": HARP_OPT_FILL_CHUNK,
          "splitk_max": HARP_OPT_SPLITK_MAX, "inverses": HARP_OPT_INVERSES,
-         "fill_clusters": HARP_OPT_FILL_CLUSTERS}
+         "fill_clusters": HARP_OPT_FILL_CLUSTERS, "fill64": HARP_OPT_FILL64}
 
 _lib = None
 
@@ -365,7 +366,9 @@ class Harp:
         """A scheduling knob: 'panel_rows', 'fill_chunk', 'splitk_max' (tile
         shapes), 'inverses' (0 after, 1 beside, 2 beside unless batched) or
         'fill_clusters' (GPC-sized clusters of the background FP64 fill, 0:
-        about half)."""
+        about half) or 'fill64' (how the background fill forms the
+        FP64-accurate matrix: 0 float-float, 1 exact digit products on the
+        tensor cores, 2 digit products inside a batch of several contexts)."""
         _check("harp_ctx_set_option",
                lib().harp_ctx_set_option(self._h, KNOBS[name], int(value)))
 
