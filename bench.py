@@ -134,10 +134,11 @@ def wideband_throughput(device: int, n_ctx: int | None = None, n_freq: int = 64)
     mid = sorted(probs, key=lambda q: q.N)[len(probs) // 2]
     ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n_ctx)]
     knobs = [autotune.apply(c, mid.N, mid.Nm, mid.K, cache) for c in ctxs][0]
-    if tuned and "inverses" in tuned:
-        for c in ctxs:
-            c.set_knob("inverses", int(tuned["inverses"]))
-        knobs = dict(knobs, inverses=int(tuned["inverses"]))
+    for name in ("inverses", "fill64"):
+        if tuned and name in tuned:
+            for c in ctxs:
+                c.set_knob(name, int(tuned[name]))
+            knobs = dict(knobs, **{name: int(tuned[name])})
     H.solve_batch(ctxs, items[-n_ctx:], prec="mixed")
     torch.cuda.synchronize()
     t0 = time.perf_counter()

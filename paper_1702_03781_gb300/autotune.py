@@ -121,11 +121,12 @@ def tune_problem(p, device: int = 0, reps: int = 3, log=None) -> dict:
 
 def tune_batch_workers(problems, device: int = 0, candidates=(2, 3, 4, 6), cache=None,
                        log=None) -> dict:
-    """The number of worker contexts and where they build their factor
-    inverses (after the factorisation, or beside it on two more streams)
-    for a batch of problems: device time of one batch call after a warm-up
-    batch, each context's other knobs from the cache for the batch's median
-    problem class."""
+    """The number of worker contexts, where they build their factor inverses
+    (after the factorisation, or beside it on two more streams) and how
+    their background FP64 fill runs (digit products on the tensor cores, or
+    the float-float kernel) for a batch of problems: device time of one
+    batch call after a warm-up batch, each context's other knobs from the
+    cache for the batch's median problem class."""
     cache = load() if cache is None else cache
     dev = f"cuda:{device}"
     items = [H.BatchItem(torch.from_numpy(q.pos).to(dev), q.freq_hz,
@@ -136,20 +137,24 @@ def tune_batch_workers(problems, device: int = 0, candidates=(2, 3, 4, 6), cache
     res = {}
     for n in candidates:
         for inv in (2, 1):
-            ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n)]
-            for c in ctxs:
-                apply(c, mid.N, mid.Nm, mid.K, cache)
-                c.set_knob("inverses", inv)
-            H.solve_batch(ctxs, items[-n:], prec="mixed")
-            H.solve_batch(ctxs, items, prec="mixed", check=False)
-            res[(n, inv)] = ctxs[0].batch_device_ms() / len(items)
-            if log:
-                log(f"  workers={n} inverses={inv}: {res[(n, inv)]:.3f} ms per problem")
-            for c in ctxs:
-                c.close()
+            for f64 in (2, 0):
+                ctxs = [H.Harp(device, max_N=max_N, max_nrhs=256) for _ in range(n)]
+                for c in ctxs:
+                    apply(c, mid.N, mid.Nm, mid.K, cache)
+                    c.set_knob("inverses", inv)
+                    c.set_knob("fill64", f64)
+                H.solve_batch(ctxs, items[-n:], prec="mixed")
+                H.solve_batch(ctxs, items, prec="mixed", check=False)
+                res[(n, inv, f64)] = ctxs[0].batch_device_ms() / len(items)
+                if log:
+                    log(f"  workers={n} inverses={inv} fill64={f64}: "
+                        f"{res[(n, inv, f64)]:.3f} ms per problem")
+                for c in ctxs:
+                    c.close()
     best = min(res, key=res.get)
-    return {"workers": best[0], "inverses": best[1], "ms_per_problem": round(res[best], 4),
-            "trials": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in res.items()},
+    return {"workers": best[0], "inverses": best[1], "fill64": best[2],
+            "ms_per_problem": round(res[best], 4),
+            "trials": {f"{k[0]}x{k[1]}x{k[2]}": round(v, 4) for k, v in res.items()},
             "class": key(mid.N, mid.Nm, mid.K)}
 
 
@@ -158,6 +163,8 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=CACHE)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="retune only the wideband batch's workers, keeping the cached classes")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -165,7 +172,7 @@ def main(argv=None) -> int:
     cache = load(args.out)
     wb = synth.wideband()
     mid = sorted(wb, key=lambda q: q.N)[len(wb) // 2]  # the class the batch's contexts use
-    classes = [synth.station(), mid] + [wb[i] for i in (0, 21, 42, 63)]
+    classes = [] if args.batch_only else [synth.station(), mid] + [wb[i] for i in (0, 21, 42, 63)]
     for p in classes:
         log(f"tuning {p.name} (N={p.N}, Nm={p.Nm}, K={p.K})")
         cache[key(p.N, p.Nm, p.K)] = tune_problem(p, reps=args.reps, log=log)

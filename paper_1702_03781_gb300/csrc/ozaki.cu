@@ -486,19 +486,61 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
-// Groups -> FP64. For each group g of the chunk (descending g), the integer
-// pair results are summed exactly (int64) and folded in by Horner's rule,
-// acc = acc 2^-b + S_g. The last chunk scales acc by 2^(sig_i + tau_j - 2b)
-// and writes R = S - acc.
+// The double nearest to a 2^x (a a signed 128-bit integer; ties to even),
+// by integer operations: the bit length, the top 53 bits rounded on the
+// bits below them, the exponent and sign put in place. Results outside the
+// normal range (not met by Z's entries) go through ldexp.
+__device__ __forceinline__ double oz_i128_to_double(__int128 a, int x) {
+  if (a == 0) return 0.0;
+  const unsigned long long sign = (a < 0) ? (1ull << 63) : 0ull;
+  const unsigned __int128 u = (a < 0) ? (unsigned __int128)(-a) : (unsigned __int128)a;
+  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  unsigned long long mant;
+  int ex = x;  // |a| 2^x = mant 2^ex
+  if (nb <= 53) {
+    mant = lo << (53 - nb);
+    ex -= 53 - nb;
+  } else {
+    const int sh = nb - 53;
+    mant = (unsigned long long)(u >> sh);
+    const unsigned __int128 rem = u & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    ex += sh;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++ex;
+    }
+  }
+  const int ef = ex + 52 + 1023;  // mant in [2^52, 2^53)
+  if (ef >= 1 && ef <= 2046)
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)ef << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  const double v = ldexp((double)mant, ex);
+  return sign ? -v : v;
+}
+
+// Groups -> FP64. The pair results of a chunk of groups (descending g, from
+// g_hi to g_lo) are loaded 16 at a time (independent loads in flight) and
+// summed exactly in a 128-bit integer in units of the chunk's smallest
+// weight, unit(g_hi): pair p of group g enters times 2^shift[p], shift =
+// b (g_hi - g) (at most 78 pairs of |v| < 2^26 and shifts up to 88: below
+// 2^121). A single chunk (the usual case) is rounded once, straight to
+// R = S - I 2^((sig_i + 1) + (tau_j + 1) - b g_hi); with several, the
+// running sum acc (units of the last chunk's g_lo) is carried in FP64,
+// acc = acc 2^-(span + b) + I 2^-span, span = b (g_hi - g_lo), and the
+// last chunk (g_lo = 2) writes R = S - acc 2^((sig_i + 1) + (tau_j + 1) - 2b).
 struct OzCombine {
-  int ng;                       // groups in this chunk
-  int gstart[kOzMaxG + 1];      // pair slots of group c: [gstart[c], gstart[c+1])
-  unsigned char slot[kOzMaxPairs];
+  int np;                              // pairs in this chunk
+  int span;                            // b (g_hi - g_lo)
+  unsigned char slot[kOzMaxPairs];     // slot of pair p
+  unsigned char shift[kOzMaxPairs];    // b (g_hi - g) of pair p's group
 };
 
 __global__ void oz_combine_kernel(int N, int nrhs, const int* __restrict__ slots, long slot_stride,
-                                  const __grid_constant__ OzCombine c, int b, int first, int last,
-                                  double* __restrict__ acc_re, double* __restrict__ acc_im,
+                                  const __grid_constant__ OzCombine c, int b, int ghi, int first,
+                                  int last, double* __restrict__ acc_re, double* __restrict__ acc_im,
                                   const int* __restrict__ rexp, const int* __restrict__ cexp,
                                   const double* sr, const double* si, double* rr, double* ri,
                                   long ldr) {
@@ -506,44 +548,54 @@ __global__ void oz_combine_kernel(int N, int nrhs, const int* __restrict__ slots
   const int j = blockIdx.y;
   if (i >= N) return;
   const long o = (long)j * N + i;
-  double ar = first ? 0.0 : acc_re[o];
-  double ai = first ? 0.0 : acc_im[o];
-  const double w = ldexp(1.0, -b);
-  // Horner from the smallest weight, four groups at a time: a group's sum of
-  // pair results is an int32 below 2^29 (at most 12 pairs of |v| <= 2^25),
-  // so four consecutive groups combine exactly into the int64
-  // B = sum_j S_j 2^(b j) < 2^(30 + 3b), which a double holds exactly for
-  // b <= 7 (K > 1024; one rounding otherwise); then
-  // acc = 2^(-b (n-1)) (acc w + B), the scaling exact.
-  for (int g0 = 0; g0 < c.ng; g0 += 4) {
-    const int n = min(4, c.ng - g0);
-    long long br = 0, bi = 0;
-    for (int j = 0; j < n; ++j) {
-      int s_re = 0, s_im = 0;
-      for (int p = c.gstart[g0 + j]; p < c.gstart[g0 + j + 1]; ++p) {
-        const int* sl = slots + (long)c.slot[p] * slot_stride;
-        s_re += sl[o];
-        s_im += sl[(long)nrhs * N + o];
+  __int128 ar = 0, ai = 0;
+  for (int p0 = 0; p0 < c.np; p0 += 16) {
+    int vre[16], vim[16];
+#pragma unroll
+    for (int y = 0; y < 16; ++y) {
+      vre[y] = 0;
+      vim[y] = 0;
+      if (p0 + y < c.np) {
+        const int* sl = slots + (long)c.slot[p0 + y] * slot_stride;
+        vre[y] = sl[o];
+        vim[y] = sl[(long)nrhs * N + o];
       }
-      const long long m = 1LL << (b * j);
-      br += (long long)s_re * m;
-      bi += (long long)s_im * m;
     }
-    const double sc = ldexp(1.0, -b * (n - 1));
-    ar = fma(ar, w, (double)br) * sc;
-    ai = fma(ai, w, (double)bi) * sc;
-  }
-  if (!last) {
-    acc_re[o] = ar;
-    acc_im[o] = ai;
-    return;
+#pragma unroll
+    for (int y = 0; y < 16; ++y) {
+      if (p0 + y < c.np) {
+        const int sh = c.shift[p0 + y];
+        ar += (__int128)((unsigned __int128)(__int128)vre[y] << sh);
+        ai += (__int128)((unsigned __int128)(__int128)vim[y] << sh);
+      }
+    }
   }
   const int er = rexp[i], ec = cexp[j];
+  const bool none = oz_none(er) || oz_none(ec);
   double vr = 0.0, vi = 0.0;
-  if (!oz_none(er) && !oz_none(ec)) {
-    const int e = (er + 1) + (ec + 1) - 2 * b;
-    vr = ldexp(ar, e);
-    vi = ldexp(ai, e);
+  if (first && last) {
+    if (!none) {
+      const int x = (er + 1) + (ec + 1) - b * ghi;
+      vr = oz_i128_to_double(ar, x);
+      vi = oz_i128_to_double(ai, x);
+    }
+  } else {
+    double cr = oz_i128_to_double(ar, -c.span), ci = oz_i128_to_double(ai, -c.span);
+    if (!first) {
+      const double w = ldexp(1.0, -(c.span + b));
+      cr = fma(acc_re[o], w, cr);
+      ci = fma(acc_im[o], w, ci);
+    }
+    if (!last) {
+      acc_re[o] = cr;
+      acc_im[o] = ci;
+      return;
+    }
+    if (!none) {
+      const int e = (er + 1) + (ec + 1) - 2 * b;
+      vr = ldexp(cr, e);
+      vi = ldexp(ci, e);
+    }
   }
   const long r = (long)j * ldr + i;
   rr[r] = sr[r] - vr;
@@ -696,41 +748,6 @@ __global__ void __launch_bounds__(256) oz_fill_slice_phi_kernel(
       oz_digits(vi[i], e, b, s, o + plane, 2 * plane);
     }
   }
-}
-
-// The double nearest to a 2^x (a a signed 128-bit integer; ties to even),
-// by integer operations: the bit length, the top 53 bits rounded on the
-// bits below them, the exponent and sign put in place. Results outside the
-// normal range (not met by Z's entries) go through ldexp.
-__device__ __forceinline__ double oz_i128_to_double(__int128 a, int x) {
-  if (a == 0) return 0.0;
-  const unsigned long long sign = (a < 0) ? (1ull << 63) : 0ull;
-  const unsigned __int128 u = (a < 0) ? (unsigned __int128)(-a) : (unsigned __int128)a;
-  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-  unsigned long long mant;
-  int ex = x;  // |a| 2^x = mant 2^ex
-  if (nb <= 53) {
-    mant = lo << (53 - nb);
-    ex -= 53 - nb;
-  } else {
-    const int sh = nb - 53;
-    mant = (unsigned long long)(u >> sh);
-    const unsigned __int128 rem = u & ((((unsigned __int128)1) << sh) - 1);
-    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-    ex += sh;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++ex;
-    }
-  }
-  const int ef = ex + 52 + 1023;  // mant in [2^52, 2^53)
-  if (ef >= 1 && ef <= 2046)
-    return __longlong_as_double(
-        (long long)(sign | ((unsigned long long)ef << 52) | (mant & 0xFFFFFFFFFFFFFull)));
-  const double v = ldexp((double)mant, ex);
-  return sign ? -v : v;
 }
 
 // Groups -> the pair blocks of Z64 for the chunk's columns, one round (every
@@ -939,23 +956,25 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
     a.slots = ctx->oz_slots;
     a.slot_stride = slot_stride;
     int np = 0;
-    c.ng = 0;
-    c.gstart[0] = 0;
+    const int ghi = g;
     while (g >= 2) {
       const int tlo = std::max(1, g - sy), thi = std::min(g - 1, ctx->oz_slices);
       const int cnt = std::max(0, thi - tlo + 1);
       if (np > 0 && np + cnt > ctx->oz_slot_pairs) break;
-      if (cnt > ctx->oz_slot_pairs) return HARP_E_UNSUPPORTED;
+      if (cnt > ctx->oz_slot_pairs || np + cnt > kOzMaxPairs) return HARP_E_UNSUPPORTED;
       for (int t = tlo; t <= thi; ++t) {
         c.slot[np] = (unsigned char)np;
+        c.shift[np] = (unsigned char)(b * (ghi - g));
         a.pt[np] = (unsigned char)(t - 1);
         a.pu[np] = (unsigned char)(g - t - 1);
         a.ps[np] = (unsigned char)np;
         ++np;
       }
-      c.gstart[++c.ng] = np;
       --g;
     }
+    c.np = np;
+    c.span = b * (ghi - (g + 1));
+    if (c.span > 88) return HARP_E_UNSUPPORTED;
     const bool last = (g < 2);
     if (np > 0) {
       // order the products by A slice so that one slice is live in L2 at a time
@@ -983,7 +1002,7 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
     {
       ProfScope ps(HARP_K_OTHER, 0.0, st);
       oz_combine_kernel<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(
-          N, nrhs, ctx->oz_slots, slot_stride, c, b, first ? 1 : 0, last ? 1 : 0, ctx->oz_acc,
+          N, nrhs, ctx->oz_slots, slot_stride, c, b, ghi, first ? 1 : 0, last ? 1 : 0, ctx->oz_acc,
           ctx->oz_acc + (size_t)N * nrhs, ctx->oz_rexp, ctx->oz_cexp, sr, si, rr, ri, ldr);
       HARP_LAUNCHED();
     }
