@@ -646,18 +646,21 @@ __global__ void oz_fill_slice_c_kernel(int Nm, int K, int Kp, int Np,
 
 // Digits of Phi for the pair columns j0 .. j0 + nc - 1 (padded to ncp with
 // zero columns): out[(2u + p) * plane + jj * Kp + k], cexp[jj] the column's
-// exponent. A block of 8 warps takes 32 columns. First each lane of warp 0
-// forms one column's factors in FP64 (Eq. 3, 4): the geometry, E_p =
-// e^{-jkr} e^{j p alpha} for |p| <= P and d^q for q <= Q, into shared
-// memory (one warp for all 32: the FP64 pipe's cost is per warp
-// instruction). Then each warp takes 4 of the columns: its lanes form the
+// exponent. A block of 4 warps takes kPhiCols = 16 columns. First lanes
+// 0..15 of warp 0 form one column's factors each in FP64 (Eq. 3, 4): the
+// geometry, E_p = e^{-jkr} e^{j p alpha} for |p| <= P and d^q for q <= Q,
+// into shared memory (one warp for all: the FP64 pipe's cost is per warp
+// instruction; 16 columns a block so that several blocks share an SM and
+// one block's FP64 chain overlaps the others' digits). Then each warp takes
+// 4 of the columns: its lanes form the
 // basis values phi_{p,q} = E_p d^q of their k (k = lane + 32 i, at most 4
 // when K <= 128), the warp their largest exponent, and the digits
 // (coalesced along k). Diagonal pairs (m == n) are zero columns (the self
 // blocks are written apart); coincident antennas are flagged and give zero
-// columns. Shared memory: 32 columns of (2P + 1) complex and (Q + 1) real
+// columns. Shared memory: 16 columns of (2P + 1) complex and (Q + 1) real
 // factors.
-__global__ void __launch_bounds__(256) oz_fill_slice_phi_kernel(
+constexpr int kPhiCols = 16;
+__global__ void __launch_bounds__(128) oz_fill_slice_phi_kernel(
     int Na, int P, int Q, int K, int Kp, const double* __restrict__ pos, double kw, int j0, int nc,
     int ncp, int b, int s, int* status, int* cexp, __nv_bfloat16* out, size_t plane) {
   extern __shared__ double2 oz_fac[];
@@ -665,8 +668,8 @@ __global__ void __launch_bounds__(256) oz_fill_slice_phi_kernel(
   const int ne = 2 * P + 1, nq = Q + 1;
   const int per_col = ne + (nq + 1) / 2;  // double2 slots per column
   double2* E = oz_fac;
-  const int jb = blockIdx.x * 32;  // first column of the block
-  if (warp == 0) {
+  const int jb = blockIdx.x * kPhiCols;  // first column of the block
+  if (warp == 0 && lane < kPhiCols) {
     const int jj = jb + lane;
     const int j = j0 + jj;
     const int m = j % Na, n = j / Na;
@@ -717,7 +720,7 @@ __global__ void __launch_bounds__(256) oz_fill_slice_phi_kernel(
     kp[i] = (k < K) ? k / nq : -1;
     kq[i] = (k < K) ? k - (k / nq) * nq : 0;
   }
-  for (int c = warp; c < 32; c += (blockDim.x >> 5)) {
+  for (int c = warp; c < kPhiCols; c += (blockDim.x >> 5)) {
     const double2* Ec = E + (size_t)c * per_col;
     const double* Dc = reinterpret_cast<const double*>(Ec + ne);
     double vr[kPer], vi[kPer];
@@ -751,19 +754,21 @@ __global__ void __launch_bounds__(256) oz_fill_slice_phi_kernel(
 }
 
 // Groups -> the pair blocks of Z64 for the chunk's columns, one round (every
-// product in the slots). Thread idx = jj Nm^2 + i, i = T + Nm S fastest (the
-// slots' layout: coalesced reads, the block's columns written in runs of
-// Nm). All product results are loaded first (independent loads in flight),
-// then summed exactly in a 128-bit integer in units of the smallest group's
-// weight (product y of group ordinal g, counted from g_max, enters times
-// 2^(b g); at most 16 products of |v| < 2^26 and g <= 11, b <= 8: below
-// 2^118), and the sum is rounded once to FP64 with the scale
-// 2^((er + 1) + (ec + 1) - b g_max): integer work only, off the FP64 pipe.
+// product in the slots). Block jj takes pair column jj, thread i = T + Nm S
+// of its Nm^2 entries (the slots' layout: coalesced reads, the block's
+// columns written in runs of Nm). All product results are loaded first
+// (independent loads in flight), then summed exactly in units of the
+// smallest group's weight: product y of group ordinal g (counted from
+// g_max) enters times 2^(b g), into one of three int64 parts by
+// 32-bit steps of that shift (each part below 16 2^26 2^31 = 2^61), and
+// the parts are joined in a 128-bit integer (at most 2^26 2^88 16 < 2^118)
+// and rounded once to FP64 with the scale 2^((er + 1) + (ec + 1) - b g_max):
+// integer work only, off the FP64 pipe.
 constexpr int kOzFillMaxProd = 16;
 struct OzFillCombine {
   int np;                               // products
   unsigned char slot[kOzFillMaxProd];   // slot of product y
-  unsigned char shift[kOzFillMaxProd];  // b times its group ordinal
+  unsigned char shift[kOzFillMaxProd];  // b times its group ordinal (< 96)
 };
 
 __global__ void oz_fill_combine_kernel(int Na, int Nm, int j0, int nc, const int* __restrict__ slots,
@@ -771,11 +776,11 @@ __global__ void oz_fill_combine_kernel(int Na, int Nm, int j0, int nc, const int
                                        int b, int gmax, const int* __restrict__ rexp,
                                        const int* __restrict__ cexp, double2* Z, long ldz) {
   const int Nm2 = Nm * Nm;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)nc * Nm2) return;
-  const int jj = (int)(idx / Nm2), i = (int)(idx - (long)jj * Nm2);
-  const int j = j0 + jj, m = j % Na, n = j / Na;
+  const int jj = blockIdx.x, i = threadIdx.x;
+  if (i >= Nm2) return;
+  const int j = j0 + jj, n = j / Na, m = j - n * Na;
   if (m == n || n >= Na) return;
+  const long idx = (long)jj * Nm2 + i;
   const int er = rexp[i], ec = cexp[jj];
   double vr = 0.0, vi = 0.0;
   if (!oz_none(er) && !oz_none(ec)) {
@@ -790,20 +795,34 @@ __global__ void oz_fill_combine_kernel(int Na, int Nm, int j0, int nc, const int
         vim[y] = sl[(long)nc * Nm2 + idx];
       }
     }
-    __int128 ar = 0, ai = 0;
+    long long r0 = 0, r1 = 0, r2 = 0, i0 = 0, i1 = 0, i2 = 0;
 #pragma unroll
     for (int y = 0; y < kOzFillMaxProd; ++y) {
       if (y < c.np) {
-        const int sh = c.shift[y];
-        ar += (__int128)((unsigned __int128)(__int128)vre[y] << sh);
-        ai += (__int128)((unsigned __int128)(__int128)vim[y] << sh);
+        const int sh = c.shift[y], s5 = sh & 31;
+        const long long tr = (long long)vre[y] * (1LL << s5);
+        const long long ti = (long long)vim[y] * (1LL << s5);
+        if (sh < 32) {
+          r0 += tr;
+          i0 += ti;
+        } else if (sh < 64) {
+          r1 += tr;
+          i1 += ti;
+        } else {
+          r2 += tr;
+          i2 += ti;
+        }
       }
     }
+    const __int128 ar = (__int128)r0 + (__int128)r1 * ((__int128)1 << 32) +
+                        (__int128)r2 * ((__int128)1 << 64);
+    const __int128 ai = (__int128)i0 + (__int128)i1 * ((__int128)1 << 32) +
+                        (__int128)i2 * ((__int128)1 << 64);
     const int x = (er + 1) + (ec + 1) - b * gmax;
     vr = oz_i128_to_double(ar, x);
     vi = oz_i128_to_double(ai, x);
   }
-  const int T = i % Nm, S = i / Nm;
+  const int S = i / Nm, T = i - S * Nm;
   Z[(size_t)m * Nm + T + ((size_t)n * Nm + S) * ldz] = make_double2(vr, vi);
 }
 
@@ -1065,7 +1084,8 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
     }
   }
   c.np = nprod;
-  if (nprod < 1 || b * (G - 2) > 88) return HARP_E_UNSUPPORTED;
+  // one combine block per pair column (Nm^2 threads)
+  if (nprod < 1 || b * (G - 2) > 88 || Nm2 > 1024) return HARP_E_UNSUPPORTED;
   // pair columns per round: up to 8192 (enough basis blocks to spread the
   // FP64 geometry over the SMs; the round's products, ~75 MB at 144 MBF
   // pairs, mostly stay in L2), within the digit and slot buffers
@@ -1093,8 +1113,8 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
                                    OZ_STAGES * OZ_STAGE + 1024));
     attr_set = true;
   }
-  // the basis kernel's factor table: 32 columns
-  const size_t phi_smem = 32 * (size_t)(2 * P + 1 + (Q + 2) / 2) * sizeof(double2);
+  // the basis kernel's factor table: kPhiCols columns
+  const size_t phi_smem = kPhiCols * (size_t)(2 * P + 1 + (Q + 2) / 2) * sizeof(double2);
   if (phi_smem > 48 * 1024)
     HARP_CUDA(cudaFuncSetAttribute(oz_fill_slice_phi_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phi_smem));
@@ -1107,7 +1127,7 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
     const int nc = (int)std::min<long>(chunk, npairs - j0);
     const int ncp = (nc + OZ_BN - 1) / OZ_BN * OZ_BN;
     const size_t plane_y = (size_t)ncp * Kp;
-    oz_fill_slice_phi_kernel<<<ncp / 32, 256, phi_smem, st>>>(
+    oz_fill_slice_phi_kernel<<<ncp / kPhiCols, 128, phi_smem, st>>>(
         Na, P, Q, K, Kp, pos, kw, (int)j0, nc, ncp, b, sl, status, cexp, ydig, plane_y);
     HARP_LAUNCHED();
     CUtensorMap mb;
@@ -1122,7 +1142,7 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
     oz_mma_kernel<<<dim3(tiles_m * (ncp / OZ_BN), nprod), OZ_THREADS,
                     OZ_STAGES * OZ_STAGE + 1024, st>>>(ma, mb, a);
     HARP_LAUNCHED();
-    oz_fill_combine_kernel<<<(unsigned)(((long)nc * Nm2 + 255) / 256), 256, 0, st>>>(
+    oz_fill_combine_kernel<<<nc, (Nm2 + 31) / 32 * 32, 0, st>>>(
         Na, Nm, (int)j0, nc, ctx->oz_slots, 2L * nc * Nm2, c, b, G, ctx->oz_rexp, cexp, Z, ldz);
     HARP_LAUNCHED();
   }
