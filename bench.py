@@ -341,6 +341,55 @@ def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:
             "timing": "CUDA events around harp_eep, median of 5 after 2 warm-ups"}
 
 
+def digit_fill(h, p, dev, peaks: dict, reps: int = 5) -> dict:
+    """The FP64-accurate Z64 fill as exact digit products on the tensor
+    cores (option fill64 = 1, the default inside batches of several
+    contexts), timed standalone at the station: device time of its class
+    (the rounds of basis digits, group products and combine; CUDA events,
+    median of `reps` after 2 warm-ups), the method's rate (8 Nm^2 K per
+    ordered pair) and the executed digit products (8 Np Kp per pair column
+    and digit pair, rows padded to 128 and K to 64) against the bf16 peak."""
+    import math
+    import torch
+    from paper_1702_03781_gb300 import roofline
+    pos, coef, sb = (torch.from_numpy(x).to(dev) for x in (p.pos, p.coef, p.self_blocks))
+    kind = roofline.KINDS.index("fill_ff")
+    prev = h.knob("fill64")
+    h.set_knob("fill64", 1)
+    try:
+        for _ in range(2):
+            h.fill(pos, p.freq_hz, coef, sb, prec="mixed")
+            h.z64(p.N)
+        ms = []
+        for _ in range(reps):
+            roofline.begin(h, 1 << kind)
+            h.fill(pos, p.freq_hz, coef, sb, prec="mixed")
+            h.z64(p.N)
+            ms.append(roofline.end(h)["fill_ff"]["ms"])
+    finally:
+        h.set_knob("fill64", prev)
+    t = statistics.median(ms)
+    K, Nm2 = p.K, p.Nm * p.Nm
+    b = min(8, (24 - math.ceil(math.log2(max(K, 1)))) // 2 + 1)
+    G = next(g for g in range(2, 14)
+             if b * (g - 1) >= 53 + 0.5 * math.log2(K) + math.log2(g))
+    pairs = G * (G - 1) // 2
+    Np, Kp = -(-Nm2 // 128) * 128, -(-K // 64) * 64
+    method = 8.0 * Nm2 * K * p.Na * (p.Na - 1)
+    executed = 8.0 * Np * Kp * (p.Na * p.Na) * pairs
+    _, peak, unit, note = roofline.peak_for("residual", "tensor_bf16", peaks)
+    return {"ms": round(t, 4), "method_flops": method,
+            "method_tflops": round(method / (t * 1e-3) / 1e12, 3),
+            "fp64_pipe_tflops": round(roofline.FP64_PEAK_TFLOPS, 3),
+            "digit_bits": b, "groups": G, "digit_pairs": pairs,
+            "digit_product_flops": executed,
+            "digit_product_tflops": round(executed / (t * 1e-3) / 1e12, 2),
+            "digit_product_frac_bf16": round(executed / (t * 1e-3) / 1e12 / peak, 4),
+            "peak": round(peak, 1), "unit": unit, "peak_source": note + " (of measured)",
+            "timing": "class fill_ff (CUDA events) of a standalone mixed fill with fill64 = 1, "
+                      "median of 5 after 2 warm-ups"}
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -609,6 +658,7 @@ def main():
                              t_mixed)
         line["method_work"] = method
         line["eep"] = eep_throughput(h, p, X, dev, peaks)
+        line["digit_fill"] = digit_fill(h, p, dev, peaks)
         if not args.no_synthesis:
             line["synthesis_station"] = synthesis_station(local)
         if synth_batch is not None:

@@ -53,11 +53,11 @@ ProfScope::~ProfScope() {
   }
 }
 
-// Whether any kernel class used by the triangular solves is being recorded
-// (their captured graph would hide the launches from the recorder).
-bool profiling_active() {
-  return (g_prof.mask & ((1u << HARP_K_GEMM) | (1u << HARP_K_TRSM) | (1u << HARP_K_OTHER))) != 0;
-}
+// Whether any kernel class is being recorded: the refinement's captured
+// graphs (the triangular solves, the correction and residual-update
+// segments) would hide their launches from the recorder, so they run
+// uncaptured meanwhile.
+bool profiling_active() { return g_prof.mask != 0; }
 
 }  // namespace harp
 
