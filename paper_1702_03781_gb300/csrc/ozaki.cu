@@ -37,6 +37,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <vector>
@@ -839,6 +840,21 @@ __global__ void oz_fill_self_kernel(int Na, int Nm, const double2* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // Host side.
+
+// The digit-product kernel's shared-memory limit, set once per device (the
+// attribute belongs to the current device; contexts on several devices and
+// the batch's worker threads call this concurrently).
+static int oz_mma_attr() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  HARP_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return HARP_OK;
+  HARP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 OZ_STAGES * OZ_STAGE + 1024));
+  done.fetch_or(bit);
+  return HARP_OK;
+}
 static PFN_cuTensorMapEncodeTiled_v12000 oz_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
@@ -953,12 +969,7 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
   if (!oz_map(&ma, ctx->oz_a, Np, Kp, 2 * ctx->oz_slices, OZ_BM) ||
       !oz_map(&mb, ctx->oz_y, nrhs_p, Kp, 2 * sy, OZ_BN))
     return HARP_E_UNSUPPORTED;
-  static bool attr_set = false;
-  if (!attr_set) {
-    HARP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   OZ_STAGES * OZ_STAGE + 1024));
-    attr_set = true;
-  }
+  HARP_TRY(oz_mma_attr());
   const int tiles_m = Np / OZ_BM, tiles_n = nrhs_p / OZ_BN;
   const long slot_stride = 2L * nrhs * N;
   // Groups in descending g, cut into chunks of at most oz_slot_pairs pairs.
@@ -1107,12 +1118,7 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
                                                                       ldz);
     HARP_LAUNCHED();
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    HARP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   OZ_STAGES * OZ_STAGE + 1024));
-    attr_set = true;
-  }
+  HARP_TRY(oz_mma_attr());
   // the basis kernel's factor table: kPhiCols columns
   const size_t phi_smem = kPhiCols * (size_t)(2 * P + 1 + (Q + 2) / 2) * sizeof(double2);
   if (phi_smem > 48 * 1024)
