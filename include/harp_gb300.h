@@ -281,6 +281,12 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
  * float-float otherwise. The digit products take a quarter of the time on
  * the whole GPU; the float-float kernel, confined to half of the GPCs,
  * overlaps a single factorisation better.
+ * HARP_OPT_ADJOINT_G: how harp_fill_adjoint forms G = Lambda X^T in the
+ * mixed modes: 1 (the default) exact digit products on the bf16 tensor
+ * cores, rounded once to FP64, in chunks of source antennas (needs the
+ * tensor-core residual's buffers, whose Z64 slices it replaces: the next
+ * solve slices Z64 again; it first waits for the context's pending
+ * background fill); 0 double-float products on the CUDA cores.
  * HARP_OPT_TC_FALLBACKS (get only, process-wide): FP32 products in a
  * tensor-core mode whose shapes the tensor cores take (M, N >= 64,
  * K >= 32) but which ran on the CUDA cores because the tensor-core path
@@ -294,6 +300,7 @@ int mbf_solve(harp_ctx* ctx, int N, const void* Z, int ldz, const double* V, int
 #define HARP_OPT_INVERSES 9
 #define HARP_OPT_FILL_CLUSTERS 10
 #define HARP_OPT_FILL64 11
+#define HARP_OPT_ADJOINT_G 12
 int harp_ctx_set_option(harp_ctx* ctx, int option, int value);
 int harp_ctx_get_option(harp_ctx* ctx, int option, int* value);
 

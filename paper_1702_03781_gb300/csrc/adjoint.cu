@@ -18,7 +18,10 @@
 // (T, S) with the coefficient table), then the per-pair derivative sums.
 //
 // Precision of G: FP64 (HARP_FP64), FP32 (HARP_FP32), or, in the mixed
-// modes, double-float on the FP32 pipe: Lambda and X are first split into
+// modes, exact digit products on the bf16 tensor cores rounded once to FP64
+// (ozaki.cu: oz_gram_*, option HARP_OPT_ADJOINT_G, the default where the
+// context holds the tensor-core residual's buffers), or double-float on the
+// FP32 pipe: Lambda and X are first split into
 // float pairs (hi + lo, 48 bits), every product is formed error-free
 // (Dekker's product via FMA plus the cross terms) and summed into a
 // double-float accumulator (Ogita-Rump-Oishi Dot2), which is FP64-accurate
@@ -29,6 +32,7 @@
 
 #include "common.cuh"
 #include "ff.cuh"
+#include "ozaki.cuh"
 #include "prof.cuh"
 
 namespace harp {
@@ -54,6 +58,11 @@ struct AdjArgs {
   const float4* Lsp;
   const float4* Xsp;
   const float4* Csp;
+  // the source antennas of this launch, n0 .. n0 + nn - 1; with G given
+  // (digit products): its columns of those antennas, G[i + (j - n0 Nm) ldg]
+  int n0, nn;
+  const double2* Gc;
+  long ldg;
 };
 
 // dst[i] = the float pairs of src[i] (real, then imaginary).
@@ -81,9 +90,10 @@ __global__ void adjoint_split_kernel(int N, int nrhs, const double2* __restrict_
   dst[e] = make_float4(rh, rl, ih, il);
 }
 
-template <typename R, bool FF>
+template <typename R, bool FF, bool LOADG>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
   static_assert(!FF || sizeof(R) == 8, "double-float G feeds the FP64 stages");
+  static_assert(!LOADG || FF, "a given G feeds the double-float H sums");
   using C = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nm = a.Nm, Nm2 = Nm * Nm, K = a.K, BA = a.BA;
@@ -96,14 +106,29 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
   float4* Lf = reinterpret_cast<float4*>(geo + 4 * (size_t)BA);
 
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    const int n = item / a.n_mtiles;
-    const int m0 = (item - n * a.n_mtiles) * BA;
+    const int nl = item / a.n_mtiles;
+    const int n = a.n0 + nl;
+    const int m0 = (item - nl * a.n_mtiles) * BA;
     // G tile = Lambda rows of the tile times X rows of antenna n (transposed)
     // Each thread owns outputs e = tid + j*blockDim (T fastest).
     constexpr int kMaxOut = 24;
     const int nG = BA * Nm2;
     const int nmine = (nG - (int)threadIdx.x + kAdjThreads - 1) / kAdjThreads;
-    if constexpr (FF) {
+    if constexpr (LOADG) {
+      // the tile's G blocks from the digit products, as float pairs
+      __syncthreads();  // the previous item's readers of Gs, Hs and geo are done
+      for (int e = threadIdx.x; e < nG; e += blockDim.x) {
+        const int mi = e / Nm2, ts = e - mi * Nm2;
+        const int S = ts / Nm, T = ts - S * Nm;
+        const int m = m0 + mi;
+        double2 v = make_double2(0.0, 0.0);
+        if (m < a.Na) v = a.Gc[(size_t)m * Nm + T + ((size_t)nl * Nm + S) * a.ldg];
+        float hr, lr, hi, li;
+        ff_split(v.x, hr, lr);
+        ff_split(v.y, hi, li);
+        reinterpret_cast<float4*>(Gs)[(size_t)mi * Nm2 + T + Nm * S] = make_float4(hr, lr, hi, li);
+      }
+    } else if constexpr (FF) {
       float4* Xf = reinterpret_cast<float4*>(Xs);  // [kRChunk][Nm], same bytes
       const long N = (long)a.Na * Nm;
       float Sr[kMaxOut], er[kMaxOut], Si[kMaxOut], ei[kMaxOut];
@@ -316,8 +341,11 @@ __global__ void adjoint_reduce_kernel(int Na, const double* gpair, double* grad)
   grad[2 * m + 1] = gy;
 }
 
-template <typename R, bool FF>
-static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st) {
+// The pair kernel for the source antennas a.n0 .. a.n0 + a.nn - 1; `prof`:
+// record it as the adjoint class (off when the caller records the whole
+// digit-product path as one).
+template <typename R, bool FF, bool LOADG>
+static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st, bool prof = true) {
   using C = cplx_t<R>;
   const int Nm2 = a.Nm * a.Nm;
   int BA = 32;
@@ -325,22 +353,22 @@ static int launch_adjoint(harp_ctx* ctx, AdjArgs a, cudaStream_t st) {
   for (; BA >= 1; BA /= 2) {
     smem = ((size_t)BA * Nm2 + (size_t)BA * a.K + (size_t)kRChunk * a.Nm) * sizeof(C) +
            (size_t)BA * 4 * sizeof(double) +
-           (FF ? (size_t)kRChunk * BA * a.Nm * sizeof(float4) : 0);
+           ((FF && !LOADG) ? (size_t)kRChunk * BA * a.Nm * sizeof(float4) : 0);
     if (smem <= std::min<size_t>(ctx->smem_optin, 200 * 1024) && BA * Nm2 <= 24 * kAdjThreads) break;
   }
   if (BA < 1) return HARP_E_UNSUPPORTED;
   a.BA = BA;
   a.n_mtiles = (a.Na + BA - 1) / BA;
-  a.n_items = a.Na * a.n_mtiles;
-  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R, FF>,
+  a.n_items = a.nn * a.n_mtiles;
+  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R, FF, LOADG>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R, FF>, kAdjThreads,
-                                                smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R, FF, LOADG>,
+                                                kAdjThreads, smem);
   const int grid = std::min(a.n_items, ctx->num_sms * std::max(1, per_sm));
-  ProfScope ps(HARP_K_ADJOINT,
+  ProfScope ps(prof ? HARP_K_ADJOINT : -1,
                8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
-  adjoint_pairs_kernel<R, FF><<<grid, kAdjThreads, smem, st>>>(a);
+  adjoint_pairs_kernel<R, FF, LOADG><<<grid, kAdjThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -400,6 +428,10 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
   a.Lsp = nullptr;
   a.Xsp = nullptr;
   a.Csp = nullptr;
+  a.n0 = 0;
+  a.nn = Na;
+  a.Gc = nullptr;
+  a.ldg = 0;
   HARP_CUDA(cudaMemsetAsync(ctx->gpair, 0, need, st));
   // mixed modes: G in double-float, the split operands in the context's
   // float-float scratch (Lambda: 4 max_N max_nrhs floats; X: 4 max_N^2)
@@ -408,7 +440,57 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
                   ctx->tc_b && Nl <= ctx->max_N && nrhs <= ctx->max_nrhs &&
                   Nl * nrhs <= (long)ctx->max_N * ctx->max_N &&
                   (size_t)4 * Nm * Nm * a.K <= ctx->tc_b_floats;
-  if (ff) {
+  // mixed modes with the tensor-core residual's buffers: G by exact digit
+  // products, in chunks of source antennas (columns of G) that the buffers
+  // hold, each followed by the pair kernel on those antennas
+  const bool mixed = (prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32);
+  int gcols = (mixed && ctx->adj_g == 1 && ctx->tc_b && Nl <= ctx->max_N &&
+               (size_t)4 * Nm * Nm * a.K <= ctx->tc_b_floats)
+                  ? std::min<long>(oz_gram_max_cols(ctx, (int)Nl, nrhs), Nl)
+                  : 0;
+  if (gcols >= Nm) {
+    // the context's buffer for G's columns, grown on demand; without it,
+    // the residual's accumulator (max_N max_nrhs complex) holds fewer
+    const size_t want = (size_t)Nl * gcols * sizeof(double2);
+    if (ctx->gbuf_bytes < want) {
+      HARP_CUDA(cudaStreamSynchronize(st));  // a previous call may still use it
+      if (ctx->gbuf) cudaFree(ctx->gbuf);
+      ctx->gbuf = nullptr;
+      ctx->gbuf_bytes = 0;
+      if (cudaMalloc(&ctx->gbuf, want) == cudaSuccess) {
+        ctx->gbuf_bytes = want;
+      } else {
+        cudaGetLastError();
+        ctx->gbuf = nullptr;
+      }
+    }
+    if (!ctx->gbuf)
+      gcols = (int)std::min<long>(gcols, (long)ctx->max_N * ctx->max_nrhs / Nl);
+  }
+  if (gcols >= Nm) {
+    // after the context's pending background fill, which may still use the
+    // residual's buffers (the next solve slices Z64 again)
+    if (ctx->ev_z64) HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_z64, 0));
+    ProfScope ps(HARP_K_ADJOINT,
+                 8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
+    const long nc = (long)Nm * Nm * a.K;
+    split_c128_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+        nc, a.coef, reinterpret_cast<float4*>(ctx->tc_b));
+    HARP_LAUNCHED();
+    a.Csp = reinterpret_cast<const float4*>(ctx->tc_b);
+    HARP_TRY(oz_gram_prepare(ctx, (int)Nl, nrhs, a.Lam, ld, a.X, ld, st));
+    double2* Gc = reinterpret_cast<double2*>(ctx->gbuf ? ctx->gbuf : (void*)ctx->oz_acc);
+    const int na_chunk = gcols / Nm;
+    for (int n0 = 0; n0 < Na; n0 += na_chunk) {
+      const int nn = std::min(na_chunk, Na - n0);
+      HARP_TRY(oz_gram_chunk(ctx, (int)Nl, nrhs, a.X, ld, n0 * Nm, nn * Nm, Gc, Nl, st));
+      a.n0 = n0;
+      a.nn = nn;
+      a.Gc = Gc;
+      a.ldg = Nl;
+      HARP_TRY((launch_adjoint<double, true, true>(ctx, a, st, false)));
+    }
+  } else if (ff) {
     float4* lsp = reinterpret_cast<float4*>(ctx->xff);
     float4* xsp = reinterpret_cast<float4*>(ctx->zff);
     {
@@ -427,11 +509,11 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
     a.Lsp = lsp;
     a.Xsp = xsp;
     a.Csp = reinterpret_cast<const float4*>(ctx->tc_b);
-    HARP_TRY((launch_adjoint<double, true>(ctx, a, st)));
+    HARP_TRY((launch_adjoint<double, true, false>(ctx, a, st)));
   } else if (prec == HARP_FP32) {
-    HARP_TRY((launch_adjoint<float, false>(ctx, a, st)));
+    HARP_TRY((launch_adjoint<float, false, false>(ctx, a, st)));
   } else {
-    HARP_TRY((launch_adjoint<double, false>(ctx, a, st)));
+    HARP_TRY((launch_adjoint<double, false, false>(ctx, a, st)));
   }
   adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, ctx->gpair, grad_pos);
   HARP_LAUNCHED();
@@ -498,15 +580,16 @@ int launch_adjoint_noalloc(int device, AdjArgs a, cudaStream_t st) {
   a.BA = BA;
   a.n_mtiles = (a.Na + BA - 1) / BA;
   a.n_items = a.Na * a.n_mtiles;
-  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R, false>,
+  HARP_CUDA(cudaFuncSetAttribute(adjoint_pairs_kernel<R, false, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
-  HARP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pairs_kernel<R, false>,
+  HARP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
+                                                          adjoint_pairs_kernel<R, false, false>,
                                                           kAdjThreads, smem));
   const int grid = std::min(a.n_items, sms * std::max(1, per_sm));
   ProfScope ps(HARP_K_ADJOINT,
                8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
-  adjoint_pairs_kernel<R, false><<<grid, kAdjThreads, smem, st>>>(a);
+  adjoint_pairs_kernel<R, false, false><<<grid, kAdjThreads, smem, st>>>(a);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -546,6 +629,10 @@ extern "C" int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const dou
   a.Lsp = nullptr;
   a.Xsp = nullptr;
   a.Csp = nullptr;
+  a.n0 = 0;
+  a.nn = Na;
+  a.Gc = nullptr;
+  a.ldg = 0;
   a.Na = Na;
   a.Nm = Nm;
   a.P = P;

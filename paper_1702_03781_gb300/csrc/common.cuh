@@ -168,6 +168,10 @@ struct harp_ctx {
   // Adjoint per-pair partial gradients, Na x Na x 2 doubles (lazily sized).
   double* gpair;
   size_t gpair_bytes;
+  // columns of G = Lambda X^T for the digit-product adjoint (allocated on
+  // first use)
+  void* gbuf;
+  size_t gbuf_bytes;
 
   // Stream and c64 matrix buffer used by the batch scheduler (batch.cu).
   cudaStream_t stream;
@@ -247,6 +251,9 @@ struct harp_ctx {
   // fill64_now: what the next fill uses (the batch sets it for its run)
   int fill64;
   int fill64_now;
+  // HARP_OPT_ADJOINT_G: the mixed adjoint's G = Lambda X^T by 1 digit
+  // products on the tensor cores (default), 0 double-float on the CUDA cores
+  int adj_g;
   cudaEvent_t* ev_fac;
   cudaEvent_t* ev_big;
   int n_events;

@@ -47,6 +47,7 @@ static void free_all(harp_ctx* c) {
     if (c->ref_graph[g]) cudaGraphExecDestroy(c->ref_graph[g]);
   if (c->zbuf) cudaFree(c->zbuf);
   if (c->fin) cudaFree(c->fin);
+  if (c->gbuf) cudaFree(c->gbuf);
   if (c->blk_uinv) cudaFree(c->blk_uinv);
   if (c->eep_ws) cudaFree(c->eep_ws);
   if (c->side) cudaStreamDestroy(c->side);
@@ -219,6 +220,7 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   c->inv_policy = 2;
   c->fill_clusters = 0;
   c->fill64 = 2;
+  c->adj_g = 1;
   c->fill64_now = 0;
   c->lu_fork = 1;
   if (ok) {

@@ -80,19 +80,21 @@ __device__ __forceinline__ int exp_above_f(float v) {
 }
 
 // ---------------------------------------------------------------------------
-// Row exponents of op(Z) (max over the row of the exponents of |re|, |im|,
-// atomically max-ed into emax[i], which starts at OZ_NOEXP) and partial row
-// sums of |re| + |im| per K chunk (part[chunk * N + i]). Element (i, k) of
+// Row exponents of op(Z), N rows of Kd entries (max over the row of the
+// exponents of |re|, |im|, atomically max-ed into emax[i], which starts at
+// OZ_NOEXP) and, when part is given, partial row sums of |re| + |im| per K
+// chunk (part[chunk * N + i]). Element (i, k) of
 // op(Z) is z[i * ars + k * acs] (c128 units); lanes run along whichever of
 // i and k is contiguous.
-__global__ void __launch_bounds__(256) oz_rowexp_kernel(int N, const double2* __restrict__ z,
-                                                        long ars, long acs, int kchunk,
-                                                        int* emax, double* part) {
+__global__ void __launch_bounds__(256) oz_rowexp_kernel(int N, int Kd,
+                                                        const double2* __restrict__ z, long ars,
+                                                        long acs, int kchunk, int* emax,
+                                                        double* part) {
   __shared__ double ssum[8][33];
   __shared__ int sexp[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int i0 = blockIdx.x * 32;
-  const int kc0 = blockIdx.y * kchunk, kc1 = min(N, kc0 + kchunk);
+  const int kc0 = blockIdx.y * kchunk, kc1 = min(Kd, kc0 + kchunk);
   if (ars == 1) {
     // rows contiguous: lane = row, warps step along k
     const int i = i0 + tx;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(256) oz_rowexp_kernel(int N, const double2* __
         t += ssum[w][tx];
         m = max(m, sexp[w][tx]);
       }
-      part[(long)blockIdx.y * N + i] = t;
+      if (part) part[(long)blockIdx.y * N + i] = t;
       if (!oz_none(m)) atomicMax(&emax[i], m);
     }
   } else {
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) oz_rowexp_kernel(int N, const double2* __
         e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
       }
       if (tx == 0) {
-        part[(long)blockIdx.y * N + i] = s;
+        if (part) part[(long)blockIdx.y * N + i] = s;
         if (!oz_none(e)) atomicMax(&emax[i], e);
       }
     }
@@ -198,11 +200,12 @@ __device__ __forceinline__ void oz_digits(double v, int e, int b, int s, __nv_bf
   }
 }
 
-// Digits of op(Z): out[(2t + p) * plane + i * Kp + k] (p = 0 re, 1 im) for
-// rows i < Np, zero for rows N <= i < Np and columns N <= k < Kp. A 32 x 32
+// Digits of op(Z) (N rows of Kd entries): out[(2t + p) * plane + i * Kp + k]
+// (p = 0 re, 1 im) for rows i < Np, zero for rows N <= i < Np and columns
+// Kd <= k < Kp. A 32 x 32
 // tile goes through shared memory so that both the reads of Z and the
 // K-major writes are coalesced.
-__global__ void __launch_bounds__(256) oz_slice_a_kernel(int N, int Np, int Kp,
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(int N, int Kd, int Np, int Kp,
                                                          const double2* __restrict__ z,
                                                          long ars, long acs,
                                                          const int* __restrict__ emax, int b,
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(int N, int Np, int Kp,
     const int il = (ars == 1) ? tx : l, kl = (ars == 1) ? l : tx;
     const int i = i0 + il, k = k0 + kl;
     double2 v = make_double2(0.0, 0.0);
-    if (i < N && k < N) v = z[(long)i * ars + (long)k * acs];
+    if (i < N && k < Kd) v = z[(long)i * ars + (long)k * acs];
     tr[il][kl] = v.x;
     ti[il][kl] = v.y;
   }
@@ -827,6 +830,61 @@ __global__ void oz_fill_combine_kernel(int Na, int Nm, int j0, int nc, const int
   Z[(size_t)m * Nm + T + ((size_t)n * Nm + S) * ldz] = make_double2(vr, vi);
 }
 
+// ---------------------------------------------------------------------------
+// G = Lambda X^T (the adjoint's contraction over the right-hand sides) as
+// exact digit products: the rows of Lambda are the A operand (oz_prepare's
+// layout, K = nrhs), the rows of X in a chunk of columns of G the B operand.
+// Product results -> G[i + jj ldg] (FP64 complex) for i < N, jj < ncols:
+// loaded 16 at a time and summed exactly in a 128-bit integer at their
+// group's weight, 2^shift[y] with shift = b (g_max - g) (at most 78 products
+// of |v| < 2^26 and shifts up to 88: below 2^121), then rounded once with
+// the scale 2^((sig_i + 1) + (tau_j + 1) - b g_max).
+struct OzGramCombine {
+  int np;
+  unsigned char slot[kOzMaxPairs];
+  unsigned char shift[kOzMaxPairs];
+};
+
+__global__ void oz_gram_combine_kernel(int N, int ncols, const int* __restrict__ slots,
+                                       long slot_stride, const __grid_constant__ OzGramCombine c,
+                                       int b, int gmax, const int* __restrict__ rexp,
+                                       const int* __restrict__ cexp, double2* G, long ldg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jj = blockIdx.y;
+  if (i >= N) return;
+  const long o = (long)jj * N + i;
+  const int er = rexp[i], ec = cexp[jj];
+  double vr = 0.0, vi = 0.0;
+  if (!oz_none(er) && !oz_none(ec)) {
+    __int128 ar = 0, ai = 0;
+    for (int p0 = 0; p0 < c.np; p0 += 16) {
+      int vre[16], vim[16];
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        vre[y] = 0;
+        vim[y] = 0;
+        if (p0 + y < c.np) {
+          const int* sl = slots + (long)c.slot[p0 + y] * slot_stride;
+          vre[y] = sl[o];
+          vim[y] = sl[(long)ncols * N + o];
+        }
+      }
+#pragma unroll
+      for (int y = 0; y < 16; ++y) {
+        if (p0 + y < c.np) {
+          const int sh = c.shift[p0 + y];
+          ar += (__int128)((unsigned __int128)(__int128)vre[y] << sh);
+          ai += (__int128)((unsigned __int128)(__int128)vim[y] << sh);
+        }
+      }
+    }
+    const int x = (er + 1) + (ec + 1) - b * gmax;
+    vr = oz_i128_to_double(ar, x);
+    vi = oz_i128_to_double(ai, x);
+  }
+  G[(long)jj * ldg + i] = make_double2(vr, vi);
+}
+
 // The self blocks onto the diagonal blocks of Z64: thread (e, m), e = T + Nm S.
 __global__ void oz_fill_self_kernel(int Na, int Nm, const double2* __restrict__ self,
                                     long self_stride, double2* Z, long ldz) {
@@ -928,15 +986,15 @@ int oz_prepare(harp_ctx* ctx, int N, const double2* z, long ld, bool trans, doub
   const int nch = (N + kchunk - 1) / kchunk;
   ProfScope ps(HARP_K_OTHER, 0.0, st);
   HARP_CUDA(cudaMemsetAsync(ctx->oz_rexp, 0x80, sizeof(int) * N, st));  // "no entry"
-  oz_rowexp_kernel<<<dim3((N + 31) / 32, nch), 256, 0, st>>>(N, z, ars, acs, kchunk, ctx->oz_rexp,
-                                                            ctx->oz_part);
+  oz_rowexp_kernel<<<dim3((N + 31) / 32, nch), 256, 0, st>>>(N, N, z, ars, acs, kchunk,
+                                                            ctx->oz_rexp, ctx->oz_part);
   HARP_LAUNCHED();
   HARP_CUDA(cudaMemsetAsync(znorm, 0, sizeof(double), st));
   oz_rownorm_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, nch, ctx->oz_part, znorm);
   HARP_LAUNCHED();
   const size_t plane = (size_t)Np * Kp;
   oz_slice_a_kernel<<<dim3(Kp / 32, Np / 32), 256, 0, st>>>(
-      N, Np, Kp, z, ars, acs, ctx->oz_rexp, b, s, (__nv_bfloat16*)ctx->oz_a, plane);
+      N, N, Np, Kp, z, ars, acs, ctx->oz_rexp, b, s, (__nv_bfloat16*)ctx->oz_a, plane);
   HARP_LAUNCHED();
   ctx->oz_N = N;
   ctx->oz_bits = b;
@@ -1152,6 +1210,127 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
         Na, Nm, (int)j0, nc, ctx->oz_slots, 2L * nc * Nm2, c, b, G, ctx->oz_rexp, cexp, Z, ldz);
     HARP_LAUNCHED();
   }
+  return HARP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// G = Lambda X^T by exact digit products (oz_gram_combine_kernel). The
+// operands are N x nrhs, column-major; K = nrhs.
+struct OzGramPlan {
+  int b, G, s, Kp, Np, nprod;
+  OzArgs a;           // pairs and products (N, nrhs, slots filled per chunk)
+  OzGramCombine c;
+};
+
+static int oz_gram_plan(const harp_ctx* ctx, int N, int nrhs, OzGramPlan* pl) {
+  if (!ctx->oz_a || !ctx->oz_y || !ctx->oz_slots || !ctx->oz_rexp || !ctx->oz_part)
+    return HARP_E_UNSUPPORTED;
+  if (N < 1 || nrhs < 1 || N > ctx->max_N) return HARP_E_UNSUPPORTED;
+  pl->b = oz_digit_bits(nrhs);
+  pl->G = oz_groups(nrhs, pl->b, 1.0);
+  pl->s = pl->G - 1;
+  if (pl->s > ctx->oz_max_slices) return HARP_E_UNSUPPORTED;
+  pl->Kp = (nrhs + OZ_BK - 1) / OZ_BK * OZ_BK;
+  pl->Np = (N + OZ_BM - 1) / OZ_BM * OZ_BM;
+  const size_t kpN = ((size_t)ctx->max_N + 63) / 64 * 64, npN = ((size_t)ctx->max_N + 127) / 128 * 128;
+  if (2 * (size_t)pl->s * pl->Np * pl->Kp > 2 * (size_t)ctx->oz_max_slices * npN * kpN)
+    return HARP_E_UNSUPPORTED;
+  // pairs t + u = g in descending groups; a product sums up to `run` pairs
+  // of one group while its FP32 accumulator stays an exact integer
+  const int b = pl->b, G = pl->G, sl = pl->s;
+  const long run = std::max<long>(1, (1L << 24) / ((long)nrhs << (2 * b - 2)));
+  int np = 0, nprod = 0;
+  pl->a.pfirst[0] = 0;
+  for (int g = G; g >= 2; --g) {
+    const int tlo = std::max(1, g - sl), thi = std::min(g - 1, sl);
+    for (int t = tlo; t <= thi; ++t) {
+      if (np >= kOzMaxPairs) return HARP_E_UNSUPPORTED;
+      pl->a.pt[np] = (unsigned char)(t - 1);
+      pl->a.pu[np] = (unsigned char)(g - t - 1);
+      ++np;
+      if (t == thi || np - pl->a.pfirst[nprod] == run) {
+        pl->a.ps[nprod] = (unsigned char)nprod;
+        pl->c.slot[nprod] = (unsigned char)nprod;
+        pl->c.shift[nprod] = (unsigned char)(b * (G - g));
+        pl->a.pfirst[++nprod] = (unsigned char)np;
+      }
+    }
+  }
+  if (nprod < 1 || b * (G - 2) > 88) return HARP_E_UNSUPPORTED;
+  pl->nprod = nprod;
+  pl->c.np = nprod;
+  return HARP_OK;
+}
+
+int oz_gram_max_cols(const harp_ctx* ctx, int N, int nrhs) {
+  OzGramPlan pl;
+  if (oz_gram_plan(ctx, N, nrhs, &pl) != HARP_OK) return 0;
+  const size_t kpN = ((size_t)ctx->max_N + 63) / 64 * 64;
+  const size_t rpN = ((size_t)ctx->max_nrhs + 63) / 64 * 64;
+  const size_t y_cap = 2 * (size_t)ctx->oz_max_slices * rpN * kpN;
+  const size_t slot_cap = (size_t)ctx->oz_slot_pairs * 2 * (size_t)ctx->max_N * ctx->max_nrhs;
+  size_t cols = y_cap / (2 * (size_t)pl.s * pl.Kp) / OZ_BN * OZ_BN;
+  cols = std::min(cols, slot_cap / ((size_t)pl.nprod * 2 * N));
+  return (int)std::min<size_t>(cols, 65535);  // grid rows of the combine
+}
+
+int oz_gram_prepare(harp_ctx* ctx, int N, int nrhs, const double2* Lam, long ldl,
+                    const double2* X, long ldx, cudaStream_t st) {
+  OzGramPlan pl;
+  HARP_TRY(oz_gram_plan(ctx, N, nrhs, &pl));
+  // the A buffer no longer holds the slices of Z64
+  ctx->oz_N = -1;
+  ctx->oz_ticket = -1;
+  int* xexp = reinterpret_cast<int*>(ctx->oz_part);
+  HARP_CUDA(cudaMemsetAsync(ctx->oz_rexp, 0x80, sizeof(int) * N, st));  // "no entry"
+  HARP_CUDA(cudaMemsetAsync(xexp, 0x80, sizeof(int) * N, st));
+  const int kchunk = (nrhs + OZ_KCH - 1) / OZ_KCH;
+  const int nch = (nrhs + kchunk - 1) / kchunk;
+  oz_rowexp_kernel<<<dim3((N + 31) / 32, nch), 256, 0, st>>>(N, nrhs, Lam, 1, ldl, kchunk,
+                                                            ctx->oz_rexp, nullptr);
+  HARP_LAUNCHED();
+  oz_rowexp_kernel<<<dim3((N + 31) / 32, nch), 256, 0, st>>>(N, nrhs, X, 1, ldx, kchunk, xexp,
+                                                            nullptr);
+  HARP_LAUNCHED();
+  oz_slice_a_kernel<<<dim3(pl.Kp / 32, pl.Np / 32), 256, 0, st>>>(
+      N, nrhs, pl.Np, pl.Kp, Lam, 1, ldl, ctx->oz_rexp, pl.b, pl.s, (__nv_bfloat16*)ctx->oz_a,
+      (size_t)pl.Np * pl.Kp);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+int oz_gram_chunk(harp_ctx* ctx, int N, int nrhs, const double2* X, long ldx, int j0, int ncols,
+                  double2* G, long ldg, cudaStream_t st) {
+  OzGramPlan pl;
+  HARP_TRY(oz_gram_plan(ctx, N, nrhs, &pl));
+  if (ncols < 1 || ncols > oz_gram_max_cols(ctx, N, nrhs) || j0 < 0 || j0 + ncols > N)
+    return HARP_E_UNSUPPORTED;
+  const int* xexp = reinterpret_cast<const int*>(ctx->oz_part);
+  const int ncp = (ncols + OZ_BN - 1) / OZ_BN * OZ_BN;
+  __nv_bfloat16* ydig = (__nv_bfloat16*)ctx->oz_y;
+  // digits of the chunk's rows of X (the B operand)
+  oz_slice_a_kernel<<<dim3(pl.Kp / 32, ncp / 32), 256, 0, st>>>(
+      ncols, nrhs, ncp, pl.Kp, X + j0, 1, ldx, xexp + j0, pl.b, pl.s, ydig, (size_t)ncp * pl.Kp);
+  HARP_LAUNCHED();
+  HARP_TRY(oz_mma_attr());
+  CUtensorMap ma, mb;
+  if (!oz_map(&ma, ctx->oz_a, pl.Np, pl.Kp, 2 * pl.s, OZ_BM) ||
+      !oz_map(&mb, ydig, ncp, pl.Kp, 2 * pl.s, OZ_BN))
+    return HARP_E_UNSUPPORTED;
+  OzArgs& a = pl.a;
+  a.N = N;
+  a.nrhs = ncols;
+  a.nk = pl.Kp / OZ_BK;
+  a.tiles_m = pl.Np / OZ_BM;
+  a.err = ctx->dstatus + 2;
+  a.slots = ctx->oz_slots;
+  a.slot_stride = 2L * ncols * N;
+  oz_mma_kernel<<<dim3(a.tiles_m * (ncp / OZ_BN), pl.nprod), OZ_THREADS,
+                  OZ_STAGES * OZ_STAGE + 1024, st>>>(ma, mb, a);
+  HARP_LAUNCHED();
+  oz_gram_combine_kernel<<<dim3((N + 255) / 256, ncols), 256, 0, st>>>(
+      N, ncols, ctx->oz_slots, 2L * ncols * N, pl.c, pl.b, pl.G, ctx->oz_rexp, xexp + j0, G, ldg);
+  HARP_LAUNCHED();
   return HARP_OK;
 }
 

@@ -34,4 +34,17 @@ int oz_fill_z64(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos, 
                 const double2* coef, const double2* self, long self_stride, double2* Z, long ldz,
                 int* status, cudaStream_t st);
 
+// G = Lambda X^T (N x nrhs operands, column-major; G's columns are rows of
+// X) as exact digit products on the tensor cores, FP64-accurate: prepare
+// slices Lambda into the residual's A buffer (resetting its Z64 slices) and
+// takes the row exponents of both; each chunk then forms columns
+// j0 .. j0 + ncols - 1 of G (at most oz_gram_max_cols, 0 when the buffers do
+// not serve) into G[i + jj ldg] (the caller's N x ncols buffer).
+// HARP_E_UNSUPPORTED when it does not apply.
+int oz_gram_max_cols(const harp_ctx* ctx, int N, int nrhs);
+int oz_gram_prepare(harp_ctx* ctx, int N, int nrhs, const double2* Lam, long ldl,
+                    const double2* X, long ldx, cudaStream_t st);
+int oz_gram_chunk(harp_ctx* ctx, int N, int nrhs, const double2* X, long ldx, int j0, int ncols,
+                  double2* G, long ldg, cudaStream_t st);
+
 }  // namespace harp

@@ -34,7 +34,7 @@ cudaEvent_t take_event() {
 }  // namespace
 
 ProfScope::ProfScope(int k, double f, cudaStream_t s) : kind(k), flops(f), st(s), slot(-1) {
-  if (!(g_prof.mask & (1u << k))) return;
+  if (k < 0 || k >= 32 || !(g_prof.mask & (1u << k))) return;  // k < 0: not recorded
   cudaEvent_t e0 = take_event(), e1 = take_event();
   if (!e0 || !e1) return;
   if (cudaEventRecord(e0, st) != cudaSuccess) {

@@ -589,6 +589,11 @@ extern "C" int harp_ctx_set_option(harp_ctx* ctx, int option, int value) {
     ctx->fill_chunk = value;
     return HARP_OK;
   }
+  if (option == HARP_OPT_ADJOINT_G) {
+    if (value < 0 || value > 1) return -3;
+    ctx->adj_g = value;
+    return HARP_OK;
+  }
   if (option == HARP_OPT_FILL64) {
     if (value < 0 || value > 2) return -3;
     ctx->fill64 = value;
@@ -635,6 +640,7 @@ extern "C" int harp_ctx_get_option(harp_ctx* ctx, int option, int* value) {
     case HARP_OPT_INVERSES: *value = ctx->inv_policy; return HARP_OK;
     case HARP_OPT_FILL_CLUSTERS: *value = ctx->fill_clusters; return HARP_OK;
     case HARP_OPT_FILL64: *value = ctx->fill64; return HARP_OK;
+    case HARP_OPT_ADJOINT_G: *value = ctx->adj_g; return HARP_OK;
     case HARP_OPT_TC_FALLBACKS:
       *value = (int)std::min<long>(tc_fallbacks(), 2147483647L);
       return HARP_OK;

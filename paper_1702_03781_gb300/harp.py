@@ -50,9 +50,11 @@ HARP_OPT_TC_FALLBACKS = 8
 HARP_OPT_INVERSES = 9
 HARP_OPT_FILL_CLUSTERS = 10
 HARP_OPT_FILL64 = 11
+HARP_OPT_ADJOINT_G = 12
 KNOBS = {"panel_rows": HARP_OPT_PANEL_ROWS, "fill_chunk": HARP_OPT_FILL_CHUNK,
          "splitk_max": HARP_OPT_SPLITK_MAX, "inverses": HARP_OPT_INVERSES,
-         "fill_clusters": HARP_OPT_FILL_CLUSTERS, "fill64": HARP_OPT_FILL64}
+         "fill_clusters": HARP_OPT_FILL_CLUSTERS, "fill64": HARP_OPT_FILL64,
+         "adjoint_g": HARP_OPT_ADJOINT_G}
 
 _lib = None
 
@@ -368,7 +370,9 @@ class Harp:
         'fill_clusters' (GPC-sized clusters of the background FP64 fill, 0:
         about half) or 'fill64' (how the background fill forms the
         FP64-accurate matrix: 0 float-float, 1 exact digit products on the
-        tensor cores, 2 digit products inside a batch of several contexts)."""
+        tensor cores, 2 digit products inside a batch of several contexts)
+        or 'adjoint_g' (the mixed adjoint's G = Lambda X^T: 1 digit products
+        on the tensor cores, 0 double-float on the CUDA cores)."""
         _check("harp_ctx_set_option",
                lib().harp_ctx_set_option(self._h, KNOBS[name], int(value)))
 

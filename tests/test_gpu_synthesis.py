@@ -129,19 +129,56 @@ def test_station_gradient_32_coordinates_vs_richardson_differences(harp):
     assert np.linalg.norm(ga - fd) / np.linalg.norm(fd) <= 1e-6
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-10), ("fp32", 1e-4)])
-def test_adjoint_contraction_modes_vs_oracle(harp, prec, tol):
-    """The adjoint kernel's three contractions of G = Lambda X^T at the
-    station size, on seeded random Lambda and X, against the oracle's
-    contraction: FP64 and the mixed modes' double-float contraction (error-
-    free products, Dot2 sums on the FP32 pipe) within 1e-10 relative 2-norm;
-    FP32 within 1e-4."""
+@pytest.mark.parametrize("prec,tol,adj_g", [("fp64", 1e-10, 1), ("mixed", 1e-10, 1),
+                                            ("mixed", 1e-10, 0), ("fp32", 1e-4, 1)])
+def test_adjoint_contraction_modes_vs_oracle(harp, prec, tol, adj_g):
+    """The adjoint's contractions of G = Lambda X^T at the station size, on
+    seeded random Lambda and X, against the oracle's contraction: FP64, the
+    mixed modes' exact digit products on the tensor cores (adjoint_g = 1,
+    rounded once to FP64) and their double-float contraction (adjoint_g = 0:
+    error-free products, Dot2 sums on the FP32 pipe) within 1e-10 relative
+    2-norm; FP32 within 1e-4."""
     p = synth.station()
     pos, coef, _ = _dev(p)
     rng = np.random.default_rng(6061)
     Lam = synth.complex_normal(rng, (p.N, p.Na))
     X = synth.complex_normal(rng, (p.N, p.Na))
-    g = harp.fill_adjoint(pos, p.freq_hz, coef, torch.from_numpy(Lam).cuda(),
-                          torch.from_numpy(X).cuda(), prec=prec)
+    harp.set_knob("adjoint_g", adj_g)
+    try:
+        g = harp.fill_adjoint(pos, p.freq_hz, coef, torch.from_numpy(Lam).cuda(),
+                              torch.from_numpy(X).cuda(), prec=prec)
+    finally:
+        harp.set_knob("adjoint_g", 1)
     go = oracle.grad_from_adjoint(p.pos, p.freq_hz, p.coef, Lam, X)
     assert np.linalg.norm(g.cpu().numpy() - go) / np.linalg.norm(go) <= tol
+
+
+@pytest.mark.parametrize("Na,Nm,P,Q,nrhs", [(42, 5, 3, 2, 16), (17, 3, 2, 1, 7), (9, 1, 1, 1, 3)])
+def test_adjoint_digit_products_in_chunks_vs_oracle(Na, Nm, P, Q, nrhs):
+    """The digit-product G through a context sized to the problem (max_N = N,
+    max_nrhs = Na), whose buffers hold only max_nrhs columns of G at a time:
+    several chunks of G's columns
+    with a ragged last one, odd right-hand-side counts (K padded to 64),
+    Nm = 1, against the oracle within 1e-10; then the same context's mixed
+    solve, whose residual slices of Z64 the adjoint replaced, still meets the
+    oracle's solution within 1e-10."""
+    from paper_1702_03781_gb300.harp import Harp
+    p = synth.small(Na, Nm, P=P, Q=Q, seed_cfg=64)
+    pos, coef, sb = _dev(p)
+    rng = np.random.default_rng(6062 + Na)
+    Lam = synth.complex_normal(rng, (p.N, nrhs))
+    X = synth.complex_normal(rng, (p.N, nrhs))
+    go = oracle.grad_from_adjoint(p.pos, p.freq_hz, p.coef, Lam, X)
+    with Harp(0, max_N=p.N, max_nrhs=p.Na) as h:
+        assert h.knob("adjoint_g") == 1
+        Z = h.fill(pos, p.freq_hz, coef, sb, prec="mixed")
+        X1, _ = h.solve(Z, None, nrhs=p.Na, prec="mixed", max_iter=10)
+        g = h.fill_adjoint(pos, p.freq_hz, coef, torch.from_numpy(Lam).cuda(),
+                           torch.from_numpy(X).cuda(), prec="mixed")
+        assert np.linalg.norm(g.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-10
+        X2, info = h.solve(Z, None, nrhs=p.Na, prec="mixed", max_iter=10)
+        assert info["status"] == 0
+    Xo = oracle.solve(oracle.fill(p.pos, p.freq_hz, p.coef, p.self_blocks), p.V)
+    for Xg in (X1, X2):
+        Xg = Xg.cpu().numpy()
+        assert np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo) <= 1e-10
