@@ -258,7 +258,8 @@ def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int
     """Config 5's synthesis batch: J and dJ/dpos for seeded random layouts
     1..n_layouts (seeds 5001..5008) of 1024 antennas x 16 MBFs at 110 MHz
     (N = 16384, 1024 ports): forward fill + mixed solve, transposed solve
-    with the cached factors, adjoint kernel (G in double-float). The layouts are sharded
+    with the cached factors, adjoint (G by exact digit products on the tensor cores). The
+    layouts are sharded
     over the ranks (replicas.shard); each rank times its own with CUDA
     events (one layout per event pair) after one untimed gradient of its
     first layout; the whole job's time is the slowest rank's. The adjoint
@@ -286,6 +287,7 @@ def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         prof = roofline.end(h)["adjoint"]
+        digits = h.knob("adjoint_g") == 1
     total = replicas.max_over_ranks(sum(ms), torch.device("cuda", device))
     out = {"layouts": n_layouts, "seeds": [5001 + i for i in range(n_layouts)], "N": 16384,
            "ports": 1024, "ranks": ws,
@@ -299,10 +301,37 @@ def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int
                            "adjoint": [i["adjoint"]["iters"] for _, _, i in res]},
            "timing": "CUDA events per layout (forward + backward), after one untimed layout"}
     if prof and prof["launches"]:
-        # G = Lambda X^T (nrhs of the nrhs + K terms per pair) runs in
-        # double-float on the FP32 pipe; the coefficient contraction in FP64
-        out["adjoint_roofline"] = roofline.entry("adjoint", "ff2", prof, peaks)
+        out["adjoint_roofline"] = adjoint_roofline(prof, peaks, digits, 16384, 1024)
     return out
+
+
+def adjoint_roofline(prof: dict, peaks: dict, digits: bool, N: int, nrhs: int) -> dict:
+    """The adjoint class over the timed layouts. With digit products (the
+    default in the mixed modes), G = Lambda X^T (nrhs of the nrhs + K terms
+    per pair) runs as exact bf16 digit products: their executed flops
+    (8 Np Kp N per digit pair, rows padded to 128 and the right-hand sides to
+    64) against the measured bf16 peak, beside the method's rate (8 Na (Na-1)
+    Nm^2 (nrhs + K) per launch); the coefficient contraction stays in
+    double-float. Otherwise G runs in double-float on the FP32 pipe."""
+    from paper_1702_03781_gb300 import roofline
+    if not digits:
+        return roofline.entry("adjoint", "ff2", prof, peaks)
+    _, G, pairs = _digit_plan(nrhs)
+    Np, Kp = -(-N // 128) * 128, -(-nrhs // 64) * 64
+    n = max(1, prof["launches"])
+    ms = prof["ms"] / n
+    executed = 8.0 * Np * Kp * N * pairs
+    _, peak, unit, note = roofline.peak_for("adjoint", "tensor_bf16", peaks)
+    achieved = executed / (ms * 1e-3) / 1e12
+    return {"kernel": "adjoint", "impl": "digits", "bound": "tensor",
+            "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
+            "frac": round(achieved / peak, 4), "traffic": None, "launches": prof["launches"],
+            "avg_launch_ms": round(ms, 3), "digit_pairs": pairs,
+            "digit_product_flops_per_launch": executed,
+            "method_flops_per_launch": prof["flops"] / n,
+            "method_tflops": round(prof["flops"] / n / (ms * 1e-3) / 1e12, 3),
+            "peak_source": note + " (of measured); the class also holds the combine and the "
+                                  "double-float coefficient contraction"}
 
 
 def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:
@@ -341,6 +370,17 @@ def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:
             "timing": "CUDA events around harp_eep, median of 5 after 2 warm-ups"}
 
 
+def _digit_plan(K: int):
+    """(digit bits b, groups G, digit pairs) of an exact-slice product over
+    K terms: the widest b <= 8 with K 2^(2b-2) <= 2^24, the smallest G with
+    b (G - 1) >= 53 + log2(sqrt K) + log2 G (the library's rule)."""
+    import math
+    b = min(8, (24 - math.ceil(math.log2(max(K, 1)))) // 2 + 1)
+    G = next(g for g in range(2, 14)
+             if b * (g - 1) >= 53 + 0.5 * math.log2(max(K, 1)) + math.log2(g))
+    return b, G, G * (G - 1) // 2
+
+
 def digit_fill(h, p, dev, peaks: dict, reps: int = 5) -> dict:
     """The FP64-accurate Z64 fill as exact digit products on the tensor
     cores (option fill64 = 1, the default inside batches of several
@@ -349,7 +389,6 @@ def digit_fill(h, p, dev, peaks: dict, reps: int = 5) -> dict:
     median of `reps` after 2 warm-ups), the method's rate (8 Nm^2 K per
     ordered pair) and the executed digit products (8 Np Kp per pair column
     and digit pair, rows padded to 128 and K to 64) against the bf16 peak."""
-    import math
     import torch
     from paper_1702_03781_gb300 import roofline
     pos, coef, sb = (torch.from_numpy(x).to(dev) for x in (p.pos, p.coef, p.self_blocks))
@@ -370,10 +409,7 @@ def digit_fill(h, p, dev, peaks: dict, reps: int = 5) -> dict:
         h.set_knob("fill64", prev)
     t = statistics.median(ms)
     K, Nm2 = p.K, p.Nm * p.Nm
-    b = min(8, (24 - math.ceil(math.log2(max(K, 1)))) // 2 + 1)
-    G = next(g for g in range(2, 14)
-             if b * (g - 1) >= 53 + 0.5 * math.log2(K) + math.log2(g))
-    pairs = G * (G - 1) // 2
+    b, G, pairs = _digit_plan(K)
     Np, Kp = -(-Nm2 // 128) * 128, -(-K // 64) * 64
     method = 8.0 * Nm2 * K * p.Na * (p.Na - 1)
     executed = 8.0 * Np * Kp * (p.Na * p.Na) * pairs

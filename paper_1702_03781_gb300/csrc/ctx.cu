@@ -146,7 +146,7 @@ extern "C" int harp_ctx_create(harp_ctx** out, int device, int max_N, int max_nr
   if (ok) {
     // Tensor-core residual buffers: optional (the float-float residual
     // serves when they do not fit).
-    const int S = oz_groups(max_N, oz_digit_bits(max_N), 1.0) - 1;
+    const int S = oz_groups(max_N, oz_resid_bits(max_N), 1.0) - 1;
     const size_t kp = ((size_t)max_N + 63) / 64 * 64, np = ((size_t)max_N + 127) / 128 * 128;
     const size_t rp = ((size_t)max_nrhs + 63) / 64 * 64;
     const size_t per_pair = 2 * NR * sizeof(int);

@@ -490,6 +490,179 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
+// K-split pair products, for K above the exact range of one FP32 sum. K runs
+// in chunks of kc k-tiles whose digit products stay below 2^24 in the FP32
+// accumulators (kc 64 2^(2b-2) <= 2^24: 16 k-tiles at b = 8), so the digits
+// can stay 8 bits wide at any K, which needs fewer digit pairs than
+// narrowing them (at K = 3072: 36 pairs instead of 45; at K = 16384, 36
+// instead of 66). The chunks alternate between two TMEM regions (512
+// columns, one CTA per SM): the MMA warp fills one while the four epilogue
+// warps move the other's exact integers into int32 register sums (at most
+// 2 K 2^14 < 2^31). Warps: 0-3 epilogue (TMEM lanes 32 w ..), 4 TMA
+// producer, 5 MMA issuer; four smem stages. Every wait is bounded; after a
+// failed wait the warps leave their loops (warp-uniformly around the
+// collective TMEM loads) and the error flag stays set.
+constexpr int OZK_STAGES = 4;
+constexpr int OZK_THREADS = 192;
+
+__global__ void __launch_bounds__(OZK_THREADS, 1)
+    oz_mma_ks_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ OzArgs a, int kc) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[OZK_STAGES], bar_empty[OZK_STAGES], bar_tfull[2],
+      bar_tempty[2];
+  __shared__ uint32_t tmem_slot;
+  if (*reinterpret_cast<volatile int*>(a.err)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (oz_su32(smem_raw) + 1023u) & ~1023u;
+  const int tm = blockIdx.x % a.tiles_m, tn = blockIdx.x / a.tiles_m;
+  const int i0 = tm * OZ_BM, j0 = tn * OZ_BN;
+  const int y = blockIdx.y;
+  const int q0 = a.pfirst[y], nl = (a.pfirst[y + 1] - q0) * a.nk;  // k tiles over the pairs
+  const int nch = (nl + kc - 1) / kc;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZK_STAGES; ++s) {
+      oz_mbar_init(oz_su32(&bar_full[s]), 1);
+      oz_mbar_init(oz_su32(&bar_empty[s]), 1);
+    }
+    for (int r = 0; r < 2; ++r) {
+      oz_mbar_init(oz_su32(&bar_tfull[r]), 1);
+      oz_mbar_init(oz_su32(&bar_tempty[r]), 4);  // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     oz_su32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int issued = 0;
+      for (int L = 0; L < nl; ++L) {
+        const int s = L % OZK_STAGES, use = L / OZK_STAGES;
+        if (use > 0 && !oz_wait(oz_su32(&bar_empty[s]), (use - 1) & 1, a.err)) break;
+        const int qi = L / a.nk, kt = L - qi * a.nk;
+        const int t = a.pt[q0 + qi], u = a.pu[q0 + qi];
+        const uint32_t st = base + s * OZ_STAGE;
+        const uint32_t fb = oz_su32(&bar_full[s]);
+        oz_expect_tx(fb, OZ_STAGE);
+        oz_tma_3d(st, &tmA, fb, kt * OZ_BK, i0, 2 * t);
+        oz_tma_3d(st + OZ_A_PLANE, &tmA, fb, kt * OZ_BK, i0, 2 * t + 1);
+        oz_tma_3d(st + 2 * OZ_A_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u);
+        oz_tma_3d(st + 2 * OZ_A_PLANE + OZ_B_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u + 1);
+        issued = L + 1;
+      }
+      // the copies still in flight land before the CTA leaves
+      for (int L = (issued > OZK_STAGES ? issued - OZK_STAGES : 0); L < issued; ++L)
+        oz_wait(oz_su32(&bar_full[L % OZK_STAGES]), (L / OZK_STAGES) & 1, a.err);
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---- MMA issuer: chunk c into TMEM region c & 1
+      constexpr uint32_t ID = bf16_idesc(OZ_BM, 2 * OZ_BN);
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int r = c & 1;
+        if (c >= 2 && !oz_wait(oz_su32(&bar_tempty[r]), ((c >> 1) - 1) & 1, a.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d0 = tmem + 256u * r, d1 = d0 + 128;
+        const int L1 = min(nl, (c + 1) * kc);
+        for (int L = c * kc; L < L1; ++L) {
+          const int s = L % OZK_STAGES, use = L / OZK_STAGES;
+          if (!oz_wait(oz_su32(&bar_full[s]), use & 1, a.err)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * OZ_STAGE;
+#pragma unroll
+          for (int j = 0; j < OZ_BK / 16; ++j) {
+            const uint32_t ko = 32u * j;
+            const uint64_t are = oz_desc(st + ko);
+            const uint64_t aim = oz_desc(st + OZ_A_PLANE + ko);
+            const uint64_t by = oz_desc(st + 2 * OZ_A_PLANE + ko);
+            const uint32_t acc = (L == c * kc && j == 0) ? 0u : 1u;
+            oz_mma(d0, are, by, ID, acc);
+            oz_mma(d1, aim, by, ID, acc);
+          }
+          oz_commit(oz_su32(&bar_empty[s]));
+        }
+        if (ok) oz_commit(oz_su32(&bar_tfull[r]));
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps: chunk results -> exact int32 sums -> slots
+    int sre_acc[OZ_BN], sim_acc[OZ_BN];
+#pragma unroll
+    for (int c = 0; c < OZ_BN; ++c) sre_acc[c] = sim_acc[c] = 0;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      const int r = c & 1;
+      ok = __all_sync(0xffffffffu, oz_wait(oz_su32(&bar_tfull[r]), (c >> 1) & 1, a.err));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d0 = tmem + 256u * r + lane_off, d1 = d0 + 128;
+#pragma unroll
+      for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+        uint32_t rr[16], ri[16], ir[16], ii[16];
+        OZ_LD16(d0 + c0, rr);
+        OZ_LD16(d0 + OZ_BN + c0, ri);
+        OZ_LD16(d1 + c0, ir);
+        OZ_LD16(d1 + OZ_BN + c0, ii);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          sre_acc[c0 + k] += __float2int_rn(__uint_as_float(rr[k])) -
+                             __float2int_rn(__uint_as_float(ii[k]));
+          sim_acc[c0 + k] += __float2int_rn(__uint_as_float(ri[k])) +
+                             __float2int_rn(__uint_as_float(ir[k]));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&bar_tempty[r]))
+                     : "memory");
+    }
+    const int gi = i0 + warp * 32 + lane;
+    if (ok && gi < a.N) {
+      int* sre = a.slots + (long)a.ps[y] * a.slot_stride;
+      int* sim = sre + (long)a.nrhs * a.N;
+#pragma unroll
+      for (int c = 0; c < OZ_BN; ++c) {
+        const int j = j0 + c;
+        if (j < a.nrhs) {
+          const long o = (long)j * a.N + gi;
+          sre[o] = sre_acc[c];
+          sim[o] = sim_acc[c];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The double nearest to a 2^x (a a signed 128-bit integer; ties to even),
 // by integer operations: the bit length, the top 53 bits rounded on the
 // bits below them, the exponent and sign put in place. Results outside the
@@ -910,6 +1083,8 @@ static int oz_mma_attr() {
   if (done.load() & bit) return HARP_OK;
   HARP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  OZ_STAGES * OZ_STAGE + 1024));
+  HARP_CUDA(cudaFuncSetAttribute(oz_mma_ks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 OZK_STAGES * OZ_STAGE + 1024));
   done.fetch_or(bit);
   return HARP_OK;
 }
@@ -955,6 +1130,15 @@ int oz_digit_bits(int K) {
   return std::min(8, b);
 }
 
+// The residual's digits: 8 bits at any K, the products running in K chunks
+// of kOzSplitTiles k-tiles (64 2^14 16 = 2^24) when K is longer
+// (oz_mma_ks_kernel).
+int oz_resid_bits(int K) {
+  (void)K;
+  return 8;
+}
+constexpr int kOzSplitTiles = 16;
+
 int oz_groups(int K, int b, double rho) {
   // Smallest G with b (G - 1) >= 53 + log2(sqrt K) + log2 G + log2 rho. The
   // first dropped group (G pair sums of digits below 2^(b-1), weight
@@ -976,7 +1160,7 @@ int oz_prepare(harp_ctx* ctx, int N, const double2* z, long ld, bool trans, doub
                cudaStream_t st) {
   if (!ctx->oz_a) return HARP_E_UNSUPPORTED;
   ctx->oz_ticket = -1;  // the caller marks slices made from a fill's Z64
-  const int b = oz_digit_bits(N);
+  const int b = oz_resid_bits(N);
   const int s = oz_groups(N, b, 1.0) - 1;
   if (s > ctx->oz_max_slices) return HARP_E_UNSUPPORTED;
   const int Kp = (N + OZ_BK - 1) / OZ_BK * OZ_BK;
@@ -1083,8 +1267,12 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
       }
       a.pfirst[np] = (unsigned char)np;
       ProfScope ps(prof_kind, 8.0 * np * (double)N * N * nrhs, st);
-      oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024, st>>>(
-          ma, mb, a);
+      if (a.nk > kOzSplitTiles)
+        oz_mma_ks_kernel<<<dim3(tiles_m * tiles_n, np), OZK_THREADS, OZK_STAGES * OZ_STAGE + 1024,
+                           st>>>(ma, mb, a, kOzSplitTiles);
+      else
+        oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024,
+                        st>>>(ma, mb, a);
       HARP_LAUNCHED();
     }
     {

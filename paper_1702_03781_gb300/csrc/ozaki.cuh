@@ -11,6 +11,8 @@ constexpr int kOzMaxPairs = kOzMaxG * (kOzMaxG - 1) / 2;
 
 // Digit width for a K-long product (exact FP32 accumulation, bf16 digits).
 int oz_digit_bits(int K);
+// The residual's digit width (its products split K into exact chunks).
+int oz_resid_bits(int K);
 // Groups G needed for a residual whose correction is rho times the iterate.
 int oz_groups(int K, int b, double rho);
 int oz_pairs(int G);
