@@ -495,19 +495,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
 // accumulators (kc 64 2^(2b-2) <= 2^24: 16 k-tiles at b = 8), so the digits
 // can stay 8 bits wide at any K, which needs fewer digit pairs than
 // narrowing them (at K = 3072: 36 pairs instead of 45; at K = 16384, 36
-// instead of 66). The chunks alternate between two TMEM regions (512
+// instead of 66). Persistent: CTA c takes tiles c, c + gridDim.x, ... (the
+// non-persistent kernel's order: blockIdx.x fastest, then the product), and
+// the chunks of all its tiles alternate between two TMEM regions (512
 // columns, one CTA per SM): the MMA warp fills one while the four epilogue
 // warps move the other's exact integers into int32 register sums (at most
-// 2 K 2^14 < 2^31). Warps: 0-3 epilogue (TMEM lanes 32 w ..), 4 TMA
-// producer, 5 MMA issuer; four smem stages. Every wait is bounded; after a
-// failed wait the warps leave their loops (warp-uniformly around the
-// collective TMEM loads) and the error flag stays set.
+// 2 K 2^14 < 2^31), so a tile's slot writes overlap the next tile's
+// products. Warps: 0-3 epilogue (TMEM lanes 32 w ..), 4 TMA producer, 5 MMA
+// issuer; four smem stages. Every wait is bounded; after a failed wait the
+// warps leave their loops (warp-uniformly around the collective TMEM
+// loads) and the error flag stays set.
 constexpr int OZK_STAGES = 4;
 constexpr int OZK_THREADS = 192;
 
 __global__ void __launch_bounds__(OZK_THREADS, 1)
     oz_mma_ks_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ OzArgs a, int kc) {
+                     const __grid_constant__ OzArgs a, int kc, int tiles_xy, int ntiles) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[OZK_STAGES], bar_empty[OZK_STAGES], bar_tfull[2],
       bar_tempty[2];
@@ -515,11 +518,6 @@ __global__ void __launch_bounds__(OZK_THREADS, 1)
   if (*reinterpret_cast<volatile int*>(a.err)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (oz_su32(smem_raw) + 1023u) & ~1023u;
-  const int tm = blockIdx.x % a.tiles_m, tn = blockIdx.x / a.tiles_m;
-  const int i0 = tm * OZ_BM, j0 = tn * OZ_BN;
-  const int y = blockIdx.y;
-  const int q0 = a.pfirst[y], nl = (a.pfirst[y + 1] - q0) * a.nk;  // k tiles over the pairs
-  const int nch = (nl + kc - 1) / kc;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZK_STAGES; ++s) {
@@ -548,108 +546,135 @@ __global__ void __launch_bounds__(OZK_THREADS, 1)
 
   if (warp == 4) {
     if (lane == 0) {
-      // ---- TMA producer
-      int issued = 0;
-      for (int L = 0; L < nl; ++L) {
-        const int s = L % OZK_STAGES, use = L / OZK_STAGES;
-        if (use > 0 && !oz_wait(oz_su32(&bar_empty[s]), (use - 1) & 1, a.err)) break;
-        const int qi = L / a.nk, kt = L - qi * a.nk;
-        const int t = a.pt[q0 + qi], u = a.pu[q0 + qi];
-        const uint32_t st = base + s * OZ_STAGE;
-        const uint32_t fb = oz_su32(&bar_full[s]);
-        oz_expect_tx(fb, OZ_STAGE);
-        oz_tma_3d(st, &tmA, fb, kt * OZ_BK, i0, 2 * t);
-        oz_tma_3d(st + OZ_A_PLANE, &tmA, fb, kt * OZ_BK, i0, 2 * t + 1);
-        oz_tma_3d(st + 2 * OZ_A_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u);
-        oz_tma_3d(st + 2 * OZ_A_PLANE + OZ_B_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u + 1);
-        issued = L + 1;
+      // ---- TMA producer: every k-tile of every tile, one ring
+      long issued = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int bx = tile % tiles_xy, y = tile / tiles_xy;
+        const int i0 = (bx % a.tiles_m) * OZ_BM, j0 = (bx / a.tiles_m) * OZ_BN;
+        const int q0 = a.pfirst[y], nl = (a.pfirst[y + 1] - q0) * a.nk;
+        for (int L = 0; L < nl; ++L) {
+          const int s = (int)(issued % OZK_STAGES);
+          const long use = issued / OZK_STAGES;
+          if (use > 0 && !oz_wait(oz_su32(&bar_empty[s]), (uint32_t)((use - 1) & 1), a.err)) {
+            ok = false;
+            break;
+          }
+          const int qi = L / a.nk, kt = L - qi * a.nk;
+          const int t = a.pt[q0 + qi], u = a.pu[q0 + qi];
+          const uint32_t st = base + s * OZ_STAGE;
+          const uint32_t fb = oz_su32(&bar_full[s]);
+          oz_expect_tx(fb, OZ_STAGE);
+          oz_tma_3d(st, &tmA, fb, kt * OZ_BK, i0, 2 * t);
+          oz_tma_3d(st + OZ_A_PLANE, &tmA, fb, kt * OZ_BK, i0, 2 * t + 1);
+          oz_tma_3d(st + 2 * OZ_A_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u);
+          oz_tma_3d(st + 2 * OZ_A_PLANE + OZ_B_PLANE, &tmB, fb, kt * OZ_BK, j0, 2 * u + 1);
+          ++issued;
+        }
       }
       // the copies still in flight land before the CTA leaves
-      for (int L = (issued > OZK_STAGES ? issued - OZK_STAGES : 0); L < issued; ++L)
-        oz_wait(oz_su32(&bar_full[L % OZK_STAGES]), (L / OZK_STAGES) & 1, a.err);
+      for (long L = (issued > OZK_STAGES ? issued - OZK_STAGES : 0); L < issued; ++L)
+        oz_wait(oz_su32(&bar_full[L % OZK_STAGES]), (uint32_t)((L / OZK_STAGES) & 1), a.err);
     }
     __syncwarp();
   } else if (warp == 5) {
     if (lane == 0) {
-      // ---- MMA issuer: chunk c into TMEM region c & 1
+      // ---- MMA issuer: chunk gc (counted over the CTA's tiles) into TMEM
+      // region gc & 1
       constexpr uint32_t ID = bf16_idesc(OZ_BM, 2 * OZ_BN);
       bool ok = true;
-      for (int c = 0; c < nch && ok; ++c) {
-        const int r = c & 1;
-        if (c >= 2 && !oz_wait(oz_su32(&bar_tempty[r]), ((c >> 1) - 1) & 1, a.err)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d0 = tmem + 256u * r, d1 = d0 + 128;
-        const int L1 = min(nl, (c + 1) * kc);
-        for (int L = c * kc; L < L1; ++L) {
-          const int s = L % OZK_STAGES, use = L / OZK_STAGES;
-          if (!oz_wait(oz_su32(&bar_full[s]), use & 1, a.err)) {
+      long gL = 0, gc = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int y = tile / tiles_xy;
+        const int nl = (a.pfirst[y + 1] - a.pfirst[y]) * a.nk;
+        for (int c0 = 0; c0 < nl && ok; c0 += kc, ++gc) {
+          const int r = (int)(gc & 1);
+          if (gc >= 2 &&
+              !oz_wait(oz_su32(&bar_tempty[r]), (uint32_t)(((gc >> 1) - 1) & 1), a.err)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t st = base + s * OZ_STAGE;
+          const uint32_t d0 = tmem + 256u * r, d1 = d0 + 128;
+          const int L1 = min(nl, c0 + kc);
+          for (int L = c0; L < L1; ++L, ++gL) {
+            const int s = (int)(gL % OZK_STAGES);
+            if (!oz_wait(oz_su32(&bar_full[s]), (uint32_t)((gL / OZK_STAGES) & 1), a.err)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = base + s * OZ_STAGE;
 #pragma unroll
-          for (int j = 0; j < OZ_BK / 16; ++j) {
-            const uint32_t ko = 32u * j;
-            const uint64_t are = oz_desc(st + ko);
-            const uint64_t aim = oz_desc(st + OZ_A_PLANE + ko);
-            const uint64_t by = oz_desc(st + 2 * OZ_A_PLANE + ko);
-            const uint32_t acc = (L == c * kc && j == 0) ? 0u : 1u;
-            oz_mma(d0, are, by, ID, acc);
-            oz_mma(d1, aim, by, ID, acc);
+            for (int j = 0; j < OZ_BK / 16; ++j) {
+              const uint32_t ko = 32u * j;
+              const uint64_t are = oz_desc(st + ko);
+              const uint64_t aim = oz_desc(st + OZ_A_PLANE + ko);
+              const uint64_t by = oz_desc(st + 2 * OZ_A_PLANE + ko);
+              const uint32_t acc = (L == c0 && j == 0) ? 0u : 1u;
+              oz_mma(d0, are, by, ID, acc);
+              oz_mma(d1, aim, by, ID, acc);
+            }
+            oz_commit(oz_su32(&bar_empty[s]));
           }
-          oz_commit(oz_su32(&bar_empty[s]));
+          if (ok) oz_commit(oz_su32(&bar_tfull[r]));
         }
-        if (ok) oz_commit(oz_su32(&bar_tfull[r]));
       }
     }
     __syncwarp();
   } else {
-    // ---- epilogue warps: chunk results -> exact int32 sums -> slots
-    int sre_acc[OZ_BN], sim_acc[OZ_BN];
-#pragma unroll
-    for (int c = 0; c < OZ_BN; ++c) sre_acc[c] = sim_acc[c] = 0;
+    // ---- epilogue warps: each tile's chunks -> exact int32 sums -> slots
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-      const int r = c & 1;
-      ok = __all_sync(0xffffffffu, oz_wait(oz_su32(&bar_tfull[r]), (c >> 1) & 1, a.err));
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d0 = tmem + 256u * r + lane_off, d1 = d0 + 128;
+    long gc = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int bx = tile % tiles_xy, y = tile / tiles_xy;
+      const int i0 = (bx % a.tiles_m) * OZ_BM, j0 = (bx / a.tiles_m) * OZ_BN;
+      const int nl = (a.pfirst[y + 1] - a.pfirst[y]) * a.nk;
+      int sre_acc[OZ_BN], sim_acc[OZ_BN];
 #pragma unroll
-      for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-        uint32_t rr[16], ri[16], ir[16], ii[16];
-        OZ_LD16(d0 + c0, rr);
-        OZ_LD16(d0 + OZ_BN + c0, ri);
-        OZ_LD16(d1 + c0, ir);
-        OZ_LD16(d1 + OZ_BN + c0, ii);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int c = 0; c < OZ_BN; ++c) sre_acc[c] = sim_acc[c] = 0;
+      for (int c0 = 0; c0 < nl; c0 += kc, ++gc) {
+        const int r = (int)(gc & 1);
+        ok = __all_sync(0xffffffffu,
+                        oz_wait(oz_su32(&bar_tfull[r]), (uint32_t)((gc >> 1) & 1), a.err));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d0 = tmem + 256u * r + lane_off, d1 = d0 + 128;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          sre_acc[c0 + k] += __float2int_rn(__uint_as_float(rr[k])) -
-                             __float2int_rn(__uint_as_float(ii[k]));
-          sim_acc[c0 + k] += __float2int_rn(__uint_as_float(ri[k])) +
-                             __float2int_rn(__uint_as_float(ir[k]));
+        for (int c1 = 0; c1 < OZ_BN; c1 += 16) {
+          uint32_t rr[16], ri[16], ir[16], ii[16];
+          OZ_LD16(d0 + c1, rr);
+          OZ_LD16(d0 + OZ_BN + c1, ri);
+          OZ_LD16(d1 + c1, ir);
+          OZ_LD16(d1 + OZ_BN + c1, ii);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            sre_acc[c1 + k] += __float2int_rn(__uint_as_float(rr[k])) -
+                               __float2int_rn(__uint_as_float(ii[k]));
+            sim_acc[c1 + k] += __float2int_rn(__uint_as_float(ri[k])) +
+                               __float2int_rn(__uint_as_float(ir[k]));
+          }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&bar_tempty[r]))
+                       : "memory");
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0)
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&bar_tempty[r]))
-                     : "memory");
-    }
-    const int gi = i0 + warp * 32 + lane;
-    if (ok && gi < a.N) {
-      int* sre = a.slots + (long)a.ps[y] * a.slot_stride;
-      int* sim = sre + (long)a.nrhs * a.N;
+      const int gi = i0 + warp * 32 + lane;
+      if (ok && gi < a.N) {
+        int* sre = a.slots + (long)a.ps[y] * a.slot_stride;
+        int* sim = sre + (long)a.nrhs * a.N;
 #pragma unroll
-      for (int c = 0; c < OZ_BN; ++c) {
-        const int j = j0 + c;
-        if (j < a.nrhs) {
-          const long o = (long)j * a.N + gi;
-          sre[o] = sre_acc[c];
-          sim[o] = sim_acc[c];
+        for (int c = 0; c < OZ_BN; ++c) {
+          const int j = j0 + c;
+          if (j < a.nrhs) {
+            const long o = (long)j * a.N + gi;
+            sre[o] = sre_acc[c];
+            sim[o] = sim_acc[c];
+          }
         }
       }
     }
@@ -1267,10 +1292,12 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
       }
       a.pfirst[np] = (unsigned char)np;
       ProfScope ps(prof_kind, 8.0 * np * (double)N * N * nrhs, st);
-      if (a.nk > kOzSplitTiles)
-        oz_mma_ks_kernel<<<dim3(tiles_m * tiles_n, np), OZK_THREADS, OZK_STAGES * OZ_STAGE + 1024,
-                           st>>>(ma, mb, a, kOzSplitTiles);
-      else
+      if (a.nk > kOzSplitTiles) {
+        const int ntiles = tiles_m * tiles_n * np;
+        oz_mma_ks_kernel<<<std::min(ntiles, ctx->num_sms), OZK_THREADS,
+                           OZK_STAGES * OZ_STAGE + 1024, st>>>(ma, mb, a, kOzSplitTiles,
+                                                                tiles_m * tiles_n, ntiles);
+      } else
         oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024,
                         st>>>(ma, mb, a);
       HARP_LAUNCHED();
