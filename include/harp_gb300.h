@@ -340,13 +340,18 @@ int harp_wait_check(harp_ctx* ctx, int release, void* stream);
  *   nrhs                                                       [12]
  *   grad_pos     double [Na][2], overwritten                   [13]
  *   prec         how G = Lambda X^T is contracted: HARP_FP64 in FP64;
- *                a mixed mode in double-float on the FP32 pipe (the
- *                operands split into float pairs, error-free products,
- *                Dot2 accumulation: FP64-accurate), using the context's
+ *                a mixed mode as exact digit products on the bf16 tensor
+ *                cores rounded once to FP64 (HARP_OPT_ADJOINT_G = 1, the
+ *                default, where the context holds the tensor-core residual's
+ *                buffers; it waits for the context's pending background fill
+ *                and replaces the residual's slices of Z64, which the next
+ *                solve makes again), else in double-float on the FP32 pipe
+ *                (operands split into float pairs, error-free products,
+ *                Dot2 accumulation: FP64-accurate) using the context's
  *                float-float scratch when N <= max_N, nrhs <= max_nrhs and
  *                N nrhs <= max_N^2, else in FP64; HARP_FP32 in FP32. The
- *                contraction with the coefficients and the per-pair
- *                derivative sums are FP64 in every mode     [14] */
+ *                contraction with the coefficients is double-float (mixed)
+ *                or FP64, and the per-pair derivative sums are FP64   [14] */
 int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, const double* pos,
                       double freq_hz, const double* coef, const double* Lambda, const double* X,
                       int ld, int nrhs, double* grad_pos, int prec, void* stream);
@@ -620,8 +625,9 @@ int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const double* pos, d
 #define HARP_K_SWAP 5     /* row interchanges                                   */
 #define HARP_K_ADJOINT 6  /* harp_fill_adjoint kernels                          */
 #define HARP_K_OTHER 7    /* conversions, norms, permutations                   */
-#define HARP_K_RESID_UPDATE 8 /* residual updates R - Z D (double-float, small D) */
-#define HARP_K_FILL_FF 9  /* the mixed fill's FP64-accurate Z64 (float-float)    */
+#define HARP_K_RESID_UPDATE 8 /* residual updates R - Z D (small D)              */
+#define HARP_K_FILL_FF 9  /* the mixed fill's FP64-accurate Z64 (float-float or
+                             digit products)                                    */
 
 /* Start recording the classes whose bit (1 << HARP_K_*) is set in mask.
  * Process-wide; discards earlier records. */
