@@ -90,6 +90,75 @@ __global__ void adjoint_split_kernel(int N, int nrhs, const double2* __restrict_
   dst[e] = make_float4(rh, rl, ih, il);
 }
 
+// The per-pair derivative sums (FP64) from H_k (h[k hs]) of the pair whose
+// separation is (dx, dy), r = |(dx, dy)|: dZ/dr and dZ/dalpha contracted
+// with G, then the chain rule to the separation; (0, 0) for r = 0.
+template <typename HV>
+__device__ void adj_pair_grad(const AdjArgs& a, double dx, double dy, double r, const HV* h,
+                              long hs, double* gx, double* gy) {
+  *gx = 0.0;
+  *gy = 0.0;
+  if (!(r > 0.0)) return;
+  const double d = 1.0 / r;
+  double s, c;
+  sincos(a.k * r, &s, &c);
+  const double2 ph = make_double2(c, -s);
+  const double2 z = make_double2(dx * d, dy * d);
+  double2 zp = make_double2(1.0, 0.0);
+  double2 sum_r = make_double2(0, 0), sum_a = make_double2(0, 0);
+  for (int p = 0; p <= a.P; ++p) {
+    const double2 bp = cmul(ph, zp), bn = cmul(ph, cconj(zp));
+    double dq = 1.0;
+    for (int q = 0; q <= a.Q; ++q) {
+      // weight for dZ/dr: (-j kw - q d); for dZ/dalpha: (j p)
+      const double2 wr = make_double2(-(double)q * d, -a.k);
+      {
+        const HV hv = h[(long)((a.P + p) * a.nq + q) * hs];
+        const double2 hp = make_double2((double)hv.x * dq, (double)hv.y * dq);
+        const double2 t = cmul(hp, bp);
+        const double2 tr = cmul(t, wr);
+        sum_r.x += tr.x;
+        sum_r.y += tr.y;
+        sum_a.x += -(double)p * t.y;  // t * (j p)
+        sum_a.y += (double)p * t.x;
+      }
+      if (p > 0) {
+        const HV hv = h[(long)((a.P - p) * a.nq + q) * hs];
+        const double2 hp = make_double2((double)hv.x * dq, (double)hv.y * dq);
+        const double2 t = cmul(hp, bn);
+        const double2 tr = cmul(t, wr);
+        sum_r.x += tr.x;
+        sum_r.y += tr.y;
+        sum_a.x += (double)p * t.y;  // t * (-j p)
+        sum_a.y += -(double)p * t.x;
+      }
+      dq *= d;
+    }
+    zp = cmul(zp, z);
+  }
+  // dZ/dDx = dZ/dr dx/r + dZ/dalpha (-dy/r^2); dZ/dDy = dZ/dr dy/r + dZ/dalpha dx/r^2
+  *gx = -2.0 * (sum_r.x * (dx * d) + sum_a.x * (-dy * d * d));
+  *gy = -2.0 * (sum_r.x * (dy * d) + sum_a.x * (dx * d * d));
+}
+
+// The derivative sums of the chunk's pairs (m, n0 + nl) from H as the digit
+// products leave it, H[(m + Na nl) + k ldh]: one thread per pair.
+__global__ void adjoint_deriv_kernel(AdjArgs a, const double2* __restrict__ H, long ldh) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)a.Na * a.nn) return;
+  const int nl = (int)(e / a.Na), m = (int)(e - (long)nl * a.Na);
+  const int n = a.n0 + nl;
+  if (m == n) return;
+  const double dx = a.pos[2 * m] - a.pos[2 * n];
+  const double dy = a.pos[2 * m + 1] - a.pos[2 * n + 1];
+  const double r = hypot(dx, dy);
+  double gx, gy;
+  adj_pair_grad(a, dx, dy, r, H + e, ldh, &gx, &gy);
+  double* out = a.gpair + 2 * ((size_t)m * a.Na + n);
+  out[0] = gx;
+  out[1] = gy;
+}
+
 template <typename R, bool FF, bool LOADG>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
   static_assert(!FF || sizeof(R) == 8, "double-float G feeds the FP64 stages");
@@ -275,49 +344,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
       if (m >= a.Na || m == n) continue;
       const double dx = geo[4 * mi], dy = geo[4 * mi + 1], r = geo[4 * mi + 2];
       double gx = 0.0, gy = 0.0;
-      if (r > 0.0) {
-        const double d = 1.0 / r;
-        double s, c;
-        sincos(a.k * r, &s, &c);
-        const double2 ph = make_double2(c, -s);
-        const double2 z = make_double2(dx * d, dy * d);
-        double2 zp = make_double2(1.0, 0.0);
-        double2 sum_r = make_double2(0, 0), sum_a = make_double2(0, 0);
-        const C* h = Hs + (size_t)mi * K;
-        for (int p = 0; p <= a.P; ++p) {
-          const double2 bp = cmul(ph, zp), bn = cmul(ph, cconj(zp));
-          double dq = 1.0;
-          for (int q = 0; q <= a.Q; ++q) {
-            // weight for dZ/dr: (-j kw - q d); for dZ/dalpha: (j p)
-            const double2 wr = make_double2(-(double)q * d, -a.k);
-            {
-              const C hv = h[(a.P + p) * a.nq + q];
-              const double2 hp = make_double2((double)hv.x * dq, (double)hv.y * dq);
-              const double2 t = cmul(hp, bp);
-              const double2 tr = cmul(t, wr);
-              sum_r.x += tr.x;
-              sum_r.y += tr.y;
-              sum_a.x += -(double)p * t.y;  // t * (j p)
-              sum_a.y += (double)p * t.x;
-            }
-            if (p > 0) {
-              const C hv = h[(a.P - p) * a.nq + q];
-              const double2 hp = make_double2((double)hv.x * dq, (double)hv.y * dq);
-              const double2 t = cmul(hp, bn);
-              const double2 tr = cmul(t, wr);
-              sum_r.x += tr.x;
-              sum_r.y += tr.y;
-              sum_a.x += (double)p * t.y;  // t * (-j p)
-              sum_a.y += -(double)p * t.x;
-            }
-            dq *= d;
-          }
-          zp = cmul(zp, z);
-        }
-        // dZ/dDx = dZ/dr dx/r + dZ/dalpha (-dy/r^2); dZ/dDy = dZ/dr dy/r + dZ/dalpha dx/r^2
-        gx = -2.0 * (sum_r.x * (dx * d) + sum_a.x * (-dy * d * d));
-        gy = -2.0 * (sum_r.x * (dy * d) + sum_a.x * (dx * d * d));
-      }
+      adj_pair_grad(a, dx, dy, r, Hs + (size_t)mi * K, 1, &gx, &gy);
       double* out = a.gpair + 2 * ((size_t)m * a.Na + n);
       out[0] = gx;
       out[1] = gy;
@@ -444,14 +471,29 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
   // products, in chunks of source antennas (columns of G) that the buffers
   // hold, each followed by the pair kernel on those antennas
   const bool mixed = (prec == HARP_MIXED_3XTF32 || prec == HARP_MIXED_TF32);
-  int gcols = (mixed && ctx->adj_g == 1 && ctx->tc_b && Nl <= ctx->max_N &&
-               (size_t)4 * Nm * Nm * a.K <= ctx->tc_b_floats)
-                  ? std::min<long>(oz_gram_max_cols(ctx, (int)Nl, nrhs), Nl)
-                  : 0;
-  if (gcols >= Nm) {
-    // the context's buffer for G's columns, grown on demand; without it,
-    // the residual's accumulator (max_N max_nrhs complex) holds fewer
-    const size_t want = (size_t)Nl * gcols * sizeof(double2);
+  const int gcols = (mixed && ctx->adj_g == 1 && ctx->tc_b && Nl <= ctx->max_N &&
+                     (size_t)4 * Nm * Nm * a.K <= ctx->tc_b_floats)
+                        ? (int)std::min<long>(oz_gram_max_cols(ctx, (int)Nl, nrhs), Nl)
+                        : 0;
+  int na_chunk = gcols / Nm;
+  // H = G C^T by digit products too where its plan fits the slots (fewer
+  // source antennas a chunk if need be); its work buffer and H follow G's
+  // columns in the context's buffer
+  size_t hwork = 0;
+  if (na_chunk >= 1) {
+    int nnh = na_chunk;
+    while (nnh >= 1 && !(hwork = oz_adj_h_bytes(ctx, Na, Nm, a.K, nnh))) nnh /= 2;
+    if (hwork) na_chunk = nnh;
+  }
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t off_hw = 0, off_h = 0;
+  if (na_chunk >= 1) {
+    // the context's buffer, grown on demand; without it G's columns go to
+    // the residual's accumulator (max_N max_nrhs complex) and H stays on
+    // the CUDA cores
+    off_hw = al((size_t)Nl * na_chunk * Nm * sizeof(double2));
+    off_h = off_hw + (hwork ? al(hwork) : 0);
+    const size_t want = off_h + (hwork ? (size_t)Na * na_chunk * a.K * sizeof(double2) : 0);
     if (ctx->gbuf_bytes < want) {
       HARP_CUDA(cudaStreamSynchronize(st));  // a previous call may still use it
       if (ctx->gbuf) cudaFree(ctx->gbuf);
@@ -464,23 +506,31 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
         ctx->gbuf = nullptr;
       }
     }
-    if (!ctx->gbuf)
-      gcols = (int)std::min<long>(gcols, (long)ctx->max_N * ctx->max_nrhs / Nl);
+    if (!ctx->gbuf) {
+      hwork = 0;
+      na_chunk = (int)std::min<long>(na_chunk, (long)ctx->max_N * ctx->max_nrhs / Nl / Nm);
+    }
   }
-  if (gcols >= Nm) {
+  if (na_chunk >= 1) {
     // after the context's pending background fill, which may still use the
     // residual's buffers (the next solve slices Z64 again)
     if (ctx->ev_z64) HARP_CUDA(cudaStreamWaitEvent(st, ctx->ev_z64, 0));
     ProfScope ps(HARP_K_ADJOINT,
                  8.0 * a.Na * (double)(a.Na - 1) * a.Nm * a.Nm * (double)(a.nrhs + a.K), st);
-    const long nc = (long)Nm * Nm * a.K;
-    split_c128_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
-        nc, a.coef, reinterpret_cast<float4*>(ctx->tc_b));
-    HARP_LAUNCHED();
-    a.Csp = reinterpret_cast<const float4*>(ctx->tc_b);
+    char* gb = static_cast<char*>(ctx->gbuf);
+    void* hw = hwork ? gb + off_hw : nullptr;
+    double2* Hb = hwork ? reinterpret_cast<double2*>(gb + off_h) : nullptr;
+    if (hwork) {
+      HARP_TRY(oz_adj_h_prepare(ctx, Na, Nm, a.K, na_chunk, a.coef, hw, st));
+    } else {
+      const long nc = (long)Nm * Nm * a.K;
+      split_c128_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+          nc, a.coef, reinterpret_cast<float4*>(ctx->tc_b));
+      HARP_LAUNCHED();
+      a.Csp = reinterpret_cast<const float4*>(ctx->tc_b);
+    }
     HARP_TRY(oz_gram_prepare(ctx, (int)Nl, nrhs, a.Lam, ld, a.X, ld, st));
     double2* Gc = reinterpret_cast<double2*>(ctx->gbuf ? ctx->gbuf : (void*)ctx->oz_acc);
-    const int na_chunk = gcols / Nm;
     for (int n0 = 0; n0 < Na; n0 += na_chunk) {
       const int nn = std::min(na_chunk, Na - n0);
       HARP_TRY(oz_gram_chunk(ctx, (int)Nl, nrhs, a.X, ld, n0 * Nm, nn * Nm, Gc, Nl, st));
@@ -488,7 +538,14 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
       a.nn = nn;
       a.Gc = Gc;
       a.ldg = Nl;
-      HARP_TRY((launch_adjoint<double, true, true>(ctx, a, st, false)));
+      if (hwork) {
+        const long ldh = (long)Na * nn;
+        HARP_TRY(oz_adj_h_chunk(ctx, Na, Nm, a.K, nn, Gc, Nl, hw, Hb, ldh, st));
+        adjoint_deriv_kernel<<<(unsigned)((ldh + 127) / 128), 128, 0, st>>>(a, Hb, ldh);
+        HARP_LAUNCHED();
+      } else {
+        HARP_TRY((launch_adjoint<double, true, true>(ctx, a, st, false)));
+      }
     }
   } else if (ff) {
     float4* lsp = reinterpret_cast<float4*>(ctx->xff);

@@ -1083,6 +1083,46 @@ __global__ void oz_gram_combine_kernel(int N, int ncols, const int* __restrict__
   G[(long)jj * ldg + i] = make_double2(vr, vi);
 }
 
+// ---------------------------------------------------------------------------
+// The adjoint's coefficient contraction H[(m, n)][k] = sum_TS G^{mn}_TS c_k^{TS}
+// as exact digit products: the A operand is G pair-major (row r = m + Na nl
+// of the chunk's source antennas n = n0 + nl, K index ts = T Nm + S, the
+// table's order), the B operand the coefficient table transposed (row k, K
+// index ts: oz_slice_a with the table's own strides). One warp per A row: the row's largest
+// exponent, then its digits out[(2t + p) plane + r Kp + ts].
+__global__ void oz_slice_gpm_kernel(int Na, int Nm, int rows, int Rp, int Kp,
+                                    const double2* __restrict__ G, long ldg, int b, int s,
+                                    int* rexp, __nv_bfloat16* out, size_t plane) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= Rp) return;
+  const int Nm2 = Nm * Nm;
+  const int m = r % Na, nl = r / Na;
+  const bool in = r < rows;
+  const double2* g0 = G + (size_t)m * Nm + (size_t)nl * Nm * ldg;
+  int e = OZ_NOEXP;
+  if (in)
+    for (int ts = lane; ts < Nm2; ts += 32) {
+      const int T = ts / Nm, S = ts - T * Nm;  // the table's order, T S
+      const double2 v = g0[T + (size_t)S * ldg];
+      if (oz_nz(v.x)) e = max(e, exp_above(v.x));
+      if (oz_nz(v.y)) e = max(e, exp_above(v.y));
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+  if (lane == 0) rexp[r] = e;
+  for (int ts = lane; ts < Kp; ts += 32) {
+    double2 v = make_double2(0.0, 0.0);
+    if (in && ts < Nm2) {
+      const int T = ts / Nm, S = ts - T * Nm;
+      v = g0[T + (size_t)S * ldg];
+    }
+    __nv_bfloat16* o = out + (size_t)r * Kp + ts;
+    oz_digits(v.x, e, b, s, o, 2 * plane);
+    oz_digits(v.y, e, b, s, o + plane, 2 * plane);
+  }
+}
+
 // The self blocks onto the diagonal blocks of Z64: thread (e, m), e = T + Nm S.
 __global__ void oz_fill_self_kernel(int Na, int Nm, const double2* __restrict__ self,
                                     long self_stride, double2* Z, long ldz) {
@@ -1562,6 +1602,120 @@ int oz_gram_chunk(harp_ctx* ctx, int N, int nrhs, const double2* X, long ldx, in
       launch_pair_products(ctx, ma, mb, a, a.tiles_m * (ncp / OZ_BN), pl.nprod, pl.b, true, st));
   oz_gram_combine_kernel<<<dim3((N + 255) / 256, ncols), 256, 0, st>>>(
       N, ncols, ctx->oz_slots, 2L * ncols * N, pl.c, pl.b, pl.G, ctx->oz_rexp, xexp + j0, G, ldg);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// H = G_pm C^T (oz_slice_gpm_kernel) in a caller's work buffer, laid out as
+// [C^T digits | C^T row exponents | G_pm digits | G_pm row exponents].
+struct OzAdjHPlan {
+  int b, G, s, Kts, Kn, Rp, nprod;
+  size_t off_cexp, off_gdig, off_gexp, bytes;
+  OzArgs a;
+  OzGramCombine c;
+};
+
+static int oz_adj_h_plan(const harp_ctx* ctx, int Na, int Nm, int K, int nn, OzAdjHPlan* pl) {
+  if (!ctx->oz_slots) return HARP_E_UNSUPPORTED;
+  const int Nm2 = Nm * Nm;
+  if (K < 1 || K > 128 || Nm2 > 1024 || nn < 1) return HARP_E_UNSUPPORTED;
+  pl->b = 8;  // Nm^2 2^14 <= 2^24
+  pl->G = oz_groups(Nm2, pl->b, 1.0);
+  pl->s = pl->G - 1;
+  pl->Kts = (Nm2 + OZ_BK - 1) / OZ_BK * OZ_BK;
+  pl->Kn = 128;  // the K output columns, padded to two 64-wide tiles
+  const long rows = (long)Na * nn;
+  pl->Rp = (int)((rows + OZ_BM - 1) / OZ_BM * OZ_BM);
+  const int b = pl->b, G = pl->G, sl = pl->s;
+  const long run = std::max<long>(1, (1L << 24) / ((long)Nm2 << (2 * b - 2)));
+  int np = 0, nprod = 0;
+  pl->a.pfirst[0] = 0;
+  for (int g = G; g >= 2; --g) {
+    const int tlo = std::max(1, g - sl), thi = std::min(g - 1, sl);
+    for (int t = tlo; t <= thi; ++t) {
+      if (np >= kOzMaxPairs) return HARP_E_UNSUPPORTED;
+      pl->a.pt[np] = (unsigned char)(t - 1);
+      pl->a.pu[np] = (unsigned char)(g - t - 1);
+      ++np;
+      if (t == thi || np - pl->a.pfirst[nprod] == run) {
+        pl->a.ps[nprod] = (unsigned char)nprod;
+        pl->c.slot[nprod] = (unsigned char)nprod;
+        pl->c.shift[nprod] = (unsigned char)(b * (G - g));
+        pl->a.pfirst[++nprod] = (unsigned char)np;
+      }
+    }
+  }
+  if (nprod < 1 || b * (G - 2) > 88) return HARP_E_UNSUPPORTED;
+  pl->nprod = nprod;
+  pl->c.np = nprod;
+  const size_t slot_cap = (size_t)ctx->oz_slot_pairs * 2 * (size_t)ctx->max_N * ctx->max_nrhs;
+  if ((size_t)nprod * 2 * rows * K > slot_cap) return HARP_E_UNSUPPORTED;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t cdig = 2 * (size_t)sl * pl->Kn * pl->Kts * sizeof(__nv_bfloat16);
+  pl->off_cexp = al(cdig);
+  pl->off_gdig = al(pl->off_cexp + sizeof(int) * pl->Kn);
+  pl->off_gexp = al(pl->off_gdig + 2 * (size_t)sl * pl->Rp * pl->Kts * sizeof(__nv_bfloat16));
+  pl->bytes = al(pl->off_gexp + sizeof(int) * (size_t)pl->Rp);
+  return HARP_OK;
+}
+
+size_t oz_adj_h_bytes(const harp_ctx* ctx, int Na, int Nm, int K, int nn) {
+  OzAdjHPlan pl;
+  return oz_adj_h_plan(ctx, Na, Nm, K, nn, &pl) == HARP_OK ? pl.bytes : 0;
+}
+
+int oz_adj_h_prepare(harp_ctx* ctx, int Na, int Nm, int K, int nn, const double2* coef,
+                     void* work, cudaStream_t st) {
+  OzAdjHPlan pl;
+  HARP_TRY(oz_adj_h_plan(ctx, Na, Nm, K, nn, &pl));
+  char* w = static_cast<char*>(work);
+  int* cexp = reinterpret_cast<int*>(w + pl.off_cexp);
+  const int Nm2 = Nm * Nm;
+  HARP_CUDA(cudaMemsetAsync(cexp, 0x80, sizeof(int) * pl.Kn, st));  // "no entry"
+  // C^T: row k, entry ts at coef[ts K + k]
+  const int kchunk = (Nm2 + OZ_KCH - 1) / OZ_KCH;
+  const int nch = (Nm2 + kchunk - 1) / kchunk;
+  oz_rowexp_kernel<<<dim3((K + 31) / 32, nch), 256, 0, st>>>(K, Nm2, coef, 1, K, kchunk, cexp,
+                                                           nullptr);
+  HARP_LAUNCHED();
+  oz_slice_a_kernel<<<dim3(pl.Kts / 32, pl.Kn / 32), 256, 0, st>>>(
+      K, Nm2, pl.Kn, pl.Kts, coef, 1, K, cexp, pl.b, pl.s, (__nv_bfloat16*)w,
+      (size_t)pl.Kn * pl.Kts);
+  HARP_LAUNCHED();
+  return HARP_OK;
+}
+
+int oz_adj_h_chunk(harp_ctx* ctx, int Na, int Nm, int K, int nn, const double2* G, long ldg,
+                   void* work, double2* H, long ldh, cudaStream_t st) {
+  OzAdjHPlan pl;
+  HARP_TRY(oz_adj_h_plan(ctx, Na, Nm, K, nn, &pl));
+  char* w = static_cast<char*>(work);
+  const int* cexp = reinterpret_cast<const int*>(w + pl.off_cexp);
+  __nv_bfloat16* gdig = reinterpret_cast<__nv_bfloat16*>(w + pl.off_gdig);
+  int* gexp = reinterpret_cast<int*>(w + pl.off_gexp);
+  const int rows = Na * nn;
+  oz_slice_gpm_kernel<<<(pl.Rp + 7) / 8, 256, 0, st>>>(Na, Nm, rows, pl.Rp, pl.Kts, G, ldg, pl.b,
+                                                       pl.s, gexp, gdig,
+                                                       (size_t)pl.Rp * pl.Kts);
+  HARP_LAUNCHED();
+  HARP_TRY(oz_mma_attr());
+  CUtensorMap ma, mb;
+  if (!oz_map(&ma, gdig, pl.Rp, pl.Kts, 2 * pl.s, OZ_BM) ||
+      !oz_map(&mb, w, pl.Kn, pl.Kts, 2 * pl.s, OZ_BN))
+    return HARP_E_UNSUPPORTED;
+  OzArgs& a = pl.a;
+  a.N = rows;
+  a.nrhs = K;
+  a.nk = pl.Kts / OZ_BK;
+  a.tiles_m = pl.Rp / OZ_BM;
+  a.err = ctx->dstatus + 2;
+  a.slots = ctx->oz_slots;
+  a.slot_stride = 2L * K * rows;
+  HARP_TRY(launch_pair_products(ctx, ma, mb, a, a.tiles_m * (pl.Kn / OZ_BN), pl.nprod, pl.b,
+                                true, st));
+  oz_gram_combine_kernel<<<dim3((rows + 255) / 256, K), 256, 0, st>>>(
+      rows, K, ctx->oz_slots, 2L * K * rows, pl.c, pl.b, pl.G, gexp, cexp, H, ldh);
   HARP_LAUNCHED();
   return HARP_OK;
 }

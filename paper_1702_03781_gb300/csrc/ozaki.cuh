@@ -49,4 +49,16 @@ int oz_gram_prepare(harp_ctx* ctx, int N, int nrhs, const double2* Lam, long ldl
 int oz_gram_chunk(harp_ctx* ctx, int N, int nrhs, const double2* X, long ldx, int j0, int ncols,
                   double2* G, long ldg, cudaStream_t st);
 
+// The adjoint's coefficient contraction as exact digit products: for the
+// pairs (m, n0 + nl), m < Na, nl < nn, H[(m + Na nl) + k ldh] = sum_TS
+// G^{mn}_TS c_k^{TS} with G's columns of those antennas as oz_gram_chunk
+// leaves them (G[i + (nl Nm + S) ldg]). The work buffer (oz_adj_h_bytes, 0
+// when it does not apply: K <= 128, Nm^2 <= 1024, the slots hold the
+// chunk) keeps the table's digits between prepare and the chunks.
+size_t oz_adj_h_bytes(const harp_ctx* ctx, int Na, int Nm, int K, int nn);
+int oz_adj_h_prepare(harp_ctx* ctx, int Na, int Nm, int K, int nn, const double2* coef,
+                     void* work, cudaStream_t st);
+int oz_adj_h_chunk(harp_ctx* ctx, int Na, int Nm, int K, int nn, const double2* G, long ldg,
+                   void* work, double2* H, long ldh, cudaStream_t st);
+
 }  // namespace harp
