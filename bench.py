@@ -305,22 +305,25 @@ def synthesis_batch(device: int, ws: int, rank: int, peaks: dict, n_layouts: int
     return out
 
 
-def adjoint_roofline(prof: dict, peaks: dict, digits: bool, N: int, nrhs: int) -> dict:
+def adjoint_roofline(prof: dict, peaks: dict, digits: bool, N: int, nrhs: int,
+                     Na: int = 1024, Nm: int = 16) -> dict:
     """The adjoint class over the timed layouts. With digit products (the
-    default in the mixed modes), G = Lambda X^T (nrhs of the nrhs + K terms
-    per pair) runs as exact bf16 digit products: their executed flops
-    (8 Np Kp N per digit pair, rows padded to 128 and the right-hand sides to
-    64) against the measured bf16 peak, beside the method's rate (8 Na (Na-1)
-    Nm^2 (nrhs + K) per launch); the coefficient contraction stays in
-    double-float. Otherwise G runs in double-float on the FP32 pipe."""
+    default in the mixed modes), G = Lambda X^T and H = G C^T run as exact
+    bf16 digit products: their executed flops (G: 8 Np Kp N per digit pair,
+    rows padded to 128 and the right-hand sides to 64; H: 8 Na^2 128 Kts per
+    digit pair, the K outputs padded to 128 and Nm^2 to 64) against the
+    measured bf16 peak, beside the method's rate (8 Na (Na-1) Nm^2 (nrhs + K)
+    per launch). Otherwise G runs in double-float on the FP32 pipe."""
     from paper_1702_03781_gb300 import roofline
     if not digits:
         return roofline.entry("adjoint", "ff2", prof, peaks)
     _, G, pairs = _digit_plan(nrhs)
     Np, Kp = -(-N // 128) * 128, -(-nrhs // 64) * 64
+    _, _, pairs_h = _digit_plan(Nm * Nm)
+    Kts = -(-(Nm * Nm) // 64) * 64
     n = max(1, prof["launches"])
     ms = prof["ms"] / n
-    executed = 8.0 * Np * Kp * N * pairs
+    executed = 8.0 * Np * Kp * N * pairs + 8.0 * Na * Na * 128 * Kts * pairs_h
     _, peak, unit, note = roofline.peak_for("adjoint", "tensor_bf16", peaks)
     achieved = executed / (ms * 1e-3) / 1e12
     return {"kernel": "adjoint", "impl": "digits", "bound": "tensor",
@@ -330,8 +333,8 @@ def adjoint_roofline(prof: dict, peaks: dict, digits: bool, N: int, nrhs: int) -
             "digit_product_flops_per_launch": executed,
             "method_flops_per_launch": prof["flops"] / n,
             "method_tflops": round(prof["flops"] / n / (ms * 1e-3) / 1e12, 3),
-            "peak_source": note + " (of measured); the class also holds the combine and the "
-                                  "double-float coefficient contraction"}
+            "peak_source": note + " (of measured); the class also holds the slicing, the "
+                                  "integer combines and the per-pair derivative sums"}
 
 
 def eep_throughput(h, p, X, dev, peaks: dict, reps: int = 5) -> dict:

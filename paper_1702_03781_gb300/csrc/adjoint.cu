@@ -352,20 +352,30 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_pairs_kernel(AdjArgs a) {
   }
 }
 
-// grad[m] = sum_n g(m, n) - sum_n g(n, m), fixed order.
+// grad[m] = sum_n g(m, n) - sum_n g(n, m) in a fixed order (deterministic):
+// one warp per antenna m, lane l summing n = l, l + 32, ... in turn, then a
+// fixed shuffle tree over the lanes.
 __global__ void adjoint_reduce_kernel(int Na, const double* gpair, double* grad) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (m >= Na) return;
   double gx = 0.0, gy = 0.0;
-  for (int n = 0; n < Na; ++n) {
+  for (int n = lane; n < Na; n += 32) {
     if (n == m) continue;
-    const double* a = gpair + 2 * ((size_t)m * Na + n);
-    const double* b = gpair + 2 * ((size_t)n * Na + m);
-    gx += a[0] - b[0];
-    gy += a[1] - b[1];
+    const double2 a = *reinterpret_cast<const double2*>(gpair + 2 * ((size_t)m * Na + n));
+    const double2 b = *reinterpret_cast<const double2*>(gpair + 2 * ((size_t)n * Na + m));
+    gx += a.x - b.x;
+    gy += a.y - b.y;
   }
-  grad[2 * m] = gx;
-  grad[2 * m + 1] = gy;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    gx += __shfl_xor_sync(0xffffffffu, gx, off);
+    gy += __shfl_xor_sync(0xffffffffu, gy, off);
+  }
+  if (lane == 0) {
+    grad[2 * m] = gx;
+    grad[2 * m + 1] = gy;
+  }
 }
 
 // The pair kernel for the source antennas a.n0 .. a.n0 + a.nn - 1; `prof`:
@@ -572,7 +582,7 @@ extern "C" int harp_fill_adjoint(harp_ctx* ctx, int Na, int Nm, int P, int Q, co
   } else {
     HARP_TRY((launch_adjoint<double, false, false>(ctx, a, st)));
   }
-  adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, ctx->gpair, grad_pos);
+  adjoint_reduce_kernel<<<(Na + 7) / 8, 256, 0, st>>>(Na, ctx->gpair, grad_pos);
   HARP_LAUNCHED();
   return HARP_OK;
 }
@@ -708,7 +718,7 @@ extern "C" int harp_fill_adjoint_noalloc(int Na, int Nm, int P, int Q, const dou
     HARP_TRY(launch_adjoint_noalloc<double>(device, a, st));
   else
     HARP_TRY(launch_adjoint_noalloc<float>(device, a, st));
-  adjoint_reduce_kernel<<<(Na + 127) / 128, 128, 0, st>>>(Na, scratch, grad_pos);
+  adjoint_reduce_kernel<<<(Na + 7) / 8, 256, 0, st>>>(Na, scratch, grad_pos);
   HARP_LAUNCHED();
   return HARP_OK;
 }
