@@ -71,3 +71,14 @@ def test_clock_record_parsing():
         ["0, 1500, 2070, 800, 0x8, Active, Not Active, Active, Not Active\n"])
     assert slow["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
+
+
+@pytest.mark.parametrize("K,want", [(102, (8, 9, 36)), (144, (8, 9, 36)), (256, (8, 9, 36)),
+                                    (1024, (8, 9, 36)), (4096, (7, 10, 45)), (16384, (6, 12, 66))])
+def test_digit_plan_rule(K, want):
+    """The bench's restatement of the digit rule that sizes its digit-product
+    rooflines: 8-bit digits while K 2^(2b-2) <= 2^24 (one exact FP32 sum),
+    then the smallest group count G with b (G - 1) >= 53 + log2(sqrt K) +
+    log2 G, and G (G - 1) / 2 digit pairs; values worked out by hand (K = 102:
+    8 (G - 1) >= 53 + 3.34 + log2 G first holds at G = 9, 64 >= 59.5)."""
+    assert bench._digit_plan(K) == want
