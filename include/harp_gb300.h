@@ -98,8 +98,11 @@ unsigned long long harp_kernel_launches(void);
  * the reduced matrix used by the refinement, the LU factors, pivots and
  * factor inverses of the last factorisation, tensor-core operand planes,
  * solve buffers, and a stream and c64 matrix buffer for harp_solve_batch.
- * The exact-slice residual's buffers come on top when they fit (0.66 GB at
- * max_N = 3072, max_nrhs = 256, 2.2 GB in all at that size). Returns HARP_E_NOMEM when the allocation fails. One
+ * The exact-slice residual's buffers come on top when they fit (0.57 GB at
+ * max_N = 3072, max_nrhs = 256, 2.1 GB in all at that size); the mixed
+ * harp_fill_adjoint grows one more buffer on first use (G's columns and the
+ * coefficient contraction's operands, ~0.21 GB at the station). Returns
+ * HARP_E_NOMEM when the allocation fails. One
  * context serves one stream at a time. A process may hold several contexts,
  * all on one device: the library's one-time setup (kernel shared-memory
  * attributes, the SM count behind its split-K choice) is made for the first
