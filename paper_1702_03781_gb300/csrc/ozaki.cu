@@ -508,9 +508,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 2)
 constexpr int OZK_STAGES = 4;
 constexpr int OZK_THREADS = 192;
 
+// Unit `tile` of the persistent kernel -> (output tile bx, product y). order
+// 0: bx fastest, then the product; order 1 (products that mix A slices):
+// row block of A slowest, then the product, then the column block, so that
+// the A slices of a few row blocks are all that is live in L2.
+__device__ __forceinline__ void oz_unit(int tile, int tiles_xy, int tiles_m, int nprod, int order,
+                                        int* bx, int* y) {
+  if (order == 0) {
+    *bx = tile % tiles_xy;
+    *y = tile / tiles_xy;
+  } else {
+    const int tiles_n = tiles_xy / tiles_m;
+    const int rb = tile / (nprod * tiles_n), rem = tile - rb * (nprod * tiles_n);
+    *y = rem / tiles_n;
+    *bx = rb + (rem - *y * tiles_n) * tiles_m;
+  }
+}
+
 __global__ void __launch_bounds__(OZK_THREADS, 1)
     oz_mma_ks_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ OzArgs a, int kc, int tiles_xy, int ntiles) {
+                     const __grid_constant__ OzArgs a, int kc, int tiles_xy, int ntiles,
+                     int order) {
+  const int nprod = ntiles / tiles_xy;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[OZK_STAGES], bar_empty[OZK_STAGES], bar_tfull[2],
       bar_tempty[2];
@@ -550,7 +569,8 @@ __global__ void __launch_bounds__(OZK_THREADS, 1)
       long issued = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int bx = tile % tiles_xy, y = tile / tiles_xy;
+        int bx, y;
+        oz_unit(tile, tiles_xy, a.tiles_m, nprod, order, &bx, &y);
         const int i0 = (bx % a.tiles_m) * OZ_BM, j0 = (bx / a.tiles_m) * OZ_BN;
         const int q0 = a.pfirst[y], nl = (a.pfirst[y + 1] - q0) * a.nk;
         for (int L = 0; L < nl; ++L) {
@@ -585,7 +605,8 @@ __global__ void __launch_bounds__(OZK_THREADS, 1)
       bool ok = true;
       long gL = 0, gc = 0;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int y = tile / tiles_xy;
+        int bx, y;
+        oz_unit(tile, tiles_xy, a.tiles_m, nprod, order, &bx, &y);
         const int nl = (a.pfirst[y + 1] - a.pfirst[y]) * a.nk;
         for (int c0 = 0; c0 < nl && ok; c0 += kc, ++gc) {
           const int r = (int)(gc & 1);
@@ -628,7 +649,8 @@ __global__ void __launch_bounds__(OZK_THREADS, 1)
     bool ok = true;
     long gc = 0;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int bx = tile % tiles_xy, y = tile / tiles_xy;
+      int bx, y;
+      oz_unit(tile, tiles_xy, a.tiles_m, nprod, order, &bx, &y);
       const int i0 = (bx % a.tiles_m) * OZ_BM, j0 = (bx / a.tiles_m) * OZ_BN;
       const int nl = (a.pfirst[y + 1] - a.pfirst[y]) * a.nk;
       int sre_acc[OZ_BN], sim_acc[OZ_BN];
@@ -1200,7 +1222,7 @@ static int launch_pair_products(const harp_ctx* ctx, const CUtensorMap& ma, cons
   if (b == 8 && persistent) {
     const int ntiles = tiles_xy * nprod;
     oz_mma_ks_kernel<<<std::min(ntiles, ctx->num_sms), OZK_THREADS, OZK_STAGES * OZ_STAGE + 1024,
-                       st>>>(ma, mb, a, 16, tiles_xy, ntiles);
+                       st>>>(ma, mb, a, 16, tiles_xy, ntiles, 0);
   } else {
     oz_mma_kernel<<<dim3(tiles_xy, nprod), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024, st>>>(ma, mb,
                                                                                          a);
@@ -1299,7 +1321,24 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
   HARP_TRY(oz_mma_attr());
   const int tiles_m = Np / OZ_BM, tiles_n = nrhs_p / OZ_BN;
   const long slot_stride = 2L * nrhs * N;
-  // Groups in descending g, cut into chunks of at most oz_slot_pairs pairs.
+  // Groups in descending g, cut into chunks that the slot buffer holds. With
+  // K above one exact FP32 sum the products run on the K-split kernel. When
+  // the digit pairs do not fit the slots in one round (large N x nrhs), it
+  // also sums up to `run` pairs of a group in one slot (at most what int32
+  // holds, and at most 3 so that the persistent CTAs' units stay even),
+  // with the units ordered by row block of A: config 5's forward step 854
+  // -> 759 ms. Otherwise one pair a product, ordered by A slice (at the
+  // station the grouped form took 0.56-0.64 ms for the first residual
+  // instead of 0.52).
+  const bool split = (Kp / OZ_BK > kOzSplitTiles);
+  int all_pairs = 0;
+  for (int gg = G; gg >= 2; --gg)
+    all_pairs += std::max(0, std::min(gg - 1, ctx->oz_slices) - std::max(1, gg - sy) + 1);
+  const bool group = split && all_pairs > ctx->oz_slot_pairs;
+  const int run = group ? (int)std::min<long>(
+                              3, std::max<long>(1, (long)(0x7fffffff /
+                                                          ((long)2 * Kp << (2 * b - 2)))))
+                        : 1;
   int g = G;
   bool first = true;
   while (g >= 2) {
@@ -1314,6 +1353,74 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
     a.slot_stride = slot_stride;
     int np = 0;
     const int ghi = g;
+    if (split) {
+      // one product per run of a group's pairs: the K-split kernel sums them
+      // exactly in its int32 registers (each pair's real parts below
+      // 2 N 2^(2b-2)); one slot per product
+      int nprod = 0;
+      a.pfirst[0] = 0;
+      while (g >= 2) {
+        const int tlo = std::max(1, g - sy), thi = std::min(g - 1, ctx->oz_slices);
+        const int cnt = std::max(0, thi - tlo + 1);
+        const int prods = (cnt + run - 1) / run;
+        if (nprod > 0 && nprod + prods > ctx->oz_slot_pairs) break;
+        if (prods > ctx->oz_slot_pairs || np + cnt > kOzMaxPairs) return HARP_E_UNSUPPORTED;
+        for (int t = tlo; t <= thi; ++t) {
+          a.pt[np] = (unsigned char)(t - 1);
+          a.pu[np] = (unsigned char)(g - t - 1);
+          ++np;
+          if (t == thi || np - a.pfirst[nprod] == run) {
+            a.ps[nprod] = (unsigned char)nprod;
+            c.slot[nprod] = (unsigned char)nprod;
+            c.shift[nprod] = (unsigned char)(b * (ghi - g));
+            a.pfirst[++nprod] = (unsigned char)np;
+          }
+        }
+        --g;
+      }
+      c.np = nprod;
+      c.span = b * (ghi - (g + 1));
+      if (c.span > 88) return HARP_E_UNSUPPORTED;
+      const bool last = (g < 2);
+      if (nprod > 0) {
+        if (!group) {
+          // one pair a product: order them by A slice so that one slice is
+          // live in L2 at a time (a product's slot stays its own)
+          std::vector<int> ord(nprod);
+          for (int k = 0; k < nprod; ++k) ord[k] = k;
+          std::stable_sort(ord.begin(), ord.end(),
+                           [&](int x, int y) { return a.pt[x] < a.pt[y]; });
+          unsigned char pt[kOzMaxPairs], pu[kOzMaxPairs], psl[kOzMaxPairs];
+          for (int k = 0; k < nprod; ++k) {
+            pt[k] = a.pt[ord[k]];
+            pu[k] = a.pu[ord[k]];
+            psl[k] = a.ps[ord[k]];
+          }
+          for (int k = 0; k < nprod; ++k) {
+            a.pt[k] = pt[k];
+            a.pu[k] = pu[k];
+            a.ps[k] = psl[k];
+          }
+        }
+        // grouped products mix A slices: units ordered by row block of A
+        ProfScope ps(prof_kind, 8.0 * np * (double)N * N * nrhs, st);
+        const int ntiles = tiles_m * tiles_n * nprod;
+        oz_mma_ks_kernel<<<std::min(ntiles, ctx->num_sms), OZK_THREADS,
+                           OZK_STAGES * OZ_STAGE + 1024, st>>>(
+            ma, mb, a, kOzSplitTiles, tiles_m * tiles_n, ntiles, group ? 1 : 0);
+        HARP_LAUNCHED();
+      }
+      {
+        ProfScope ps(HARP_K_OTHER, 0.0, st);
+        oz_combine_kernel<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(
+            N, nrhs, ctx->oz_slots, slot_stride, c, b, ghi, first ? 1 : 0, last ? 1 : 0,
+            ctx->oz_acc, ctx->oz_acc + (size_t)N * nrhs, ctx->oz_rexp, ctx->oz_cexp, sr, si, rr,
+            ri, ldr);
+        HARP_LAUNCHED();
+      }
+      first = false;
+      continue;
+    }
     while (g >= 2) {
       const int tlo = std::max(1, g - sy), thi = std::min(g - 1, ctx->oz_slices);
       const int cnt = std::max(0, thi - tlo + 1);
@@ -1352,14 +1459,8 @@ int oz_residual(harp_ctx* ctx, int N, int nrhs, const float* yr, const float* yi
       }
       a.pfirst[np] = (unsigned char)np;
       ProfScope ps(prof_kind, 8.0 * np * (double)N * N * nrhs, st);
-      if (a.nk > kOzSplitTiles) {
-        const int ntiles = tiles_m * tiles_n * np;
-        oz_mma_ks_kernel<<<std::min(ntiles, ctx->num_sms), OZK_THREADS,
-                           OZK_STAGES * OZ_STAGE + 1024, st>>>(ma, mb, a, kOzSplitTiles,
-                                                                tiles_m * tiles_n, ntiles);
-      } else
-        oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024,
-                        st>>>(ma, mb, a);
+      oz_mma_kernel<<<dim3(tiles_m * tiles_n, np), OZ_THREADS, OZ_STAGES * OZ_STAGE + 1024, st>>>(
+          ma, mb, a);
       HARP_LAUNCHED();
     }
     {
